@@ -1,0 +1,240 @@
+/*
+ * tigas.h -- C ABI of the B300-native forward 3D Gaussian Splatting renderer.
+ *
+ * The library turns a GPU-resident Gaussian scene and a client's 6DoF pose
+ * into an RGBA8 frame at the resolution the client's ABR controller picks.
+ * This is the rendering engine of the paper's GPU backend (Sec. 4.1, Sec. 5.1
+ * "Rendering Engine"): scenes stay resident in device memory across requests
+ * (Sec. 4.1 "GPU Backend", persistent VRAM residency), every request is an
+ * isolated, stateless render task (Sec. 4.2), and requests carry the fields
+ * of the paper's POST /render body: azimuth, elevation, camera centre t,
+ * fx, fy, cx, cy, W, H (Sec. 5.2 "Client Interface").
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns a tigas_status.  No call aborts, traps or exits; on
+ *    error a message is available from tigas_last_error() (thread-local).
+ *  - Pointers that "may be host or device" are classified with
+ *    cudaPointerGetAttributes; memory the CUDA runtime does not know is
+ *    treated as pageable host memory.
+ *  - The library owns scene memory and its internal workspace.  The caller
+ *    owns every input array and every output buffer.
+ *  - cuda_stream arguments are cudaStream_t values passed as void* (NULL:
+ *    the library's own stream).
+ *  - Image layout: row-major, top row first, 4 bytes per pixel (R, G, B, A),
+ *    A = 1 - T (final transmittance), each channel floor(clamp(x,0,1)*255+0.5).
+ */
+#ifndef TIGAS_H
+#define TIGAS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TIGAS_OK = 0,
+    TIGAS_ERR_INVALID = 1,   /* bad argument: null, non-finite, out of range, bad handle */
+    TIGAS_ERR_OOM = 2,       /* device or pinned host allocation failed */
+    TIGAS_ERR_CUDA = 3,      /* a CUDA runtime call or kernel failed */
+    TIGAS_ERR_AGAIN = 4,     /* server: admission full, or request superseded */
+    TIGAS_ERR_OVERFLOW = 5,  /* pair count exceeded the fixed pair budget */
+    TIGAS_ERR_TIMEOUT = 6,   /* a bounded wait ran out */
+    TIGAS_ERR_NOT_FOUND = 7  /* unknown ticket */
+} tigas_status;
+
+/* Client pose (Sec. 5.1 "Rendering Engine", Sec. 5.2 request body):
+ * azimuth theta and elevation phi in radians, camera centre t in world units.
+ * Camera rotation R = R_y(theta) R_x(phi); camera axes x right, y down,
+ * z forward; world->camera transform T = [R^T, -R^T t; 0, 1]. */
+typedef struct {
+    double azimuth;
+    double elevation;
+    double t[3];
+} tigas_pose;
+
+/* Pinhole intrinsics in pixels at the requested width x height: u = fx x/z + cx,
+ * v = fy y/z + cy (Sec. 5.1 projection).  Pixel (i, j) is sampled at
+ * (i + 0.5, j + 0.5).  On an ABR resolution change the caller scales all four
+ * with the frame (Sec. 5.3), which keeps the field of view fixed. */
+typedef struct {
+    double fx, fy, cx, cy;
+} tigas_intrinsics;
+
+enum { TIGAS_STORAGE_FP32 = 0, TIGAS_STORAGE_FP16 = 1 };
+
+/* Scene description: raw per-Gaussian attributes as a 3DGS PLY holds them
+ * (Sec. 5.1 "PLY Model and Primitives").  All arrays float32, row-major:
+ *   means[n][3], log_scales[n][3], quats[n][4] (w,x,y,z; need not be unit),
+ *   opacity_logits[n], sh[n][16][3] (coefficients past sh_degree ignored).
+ * storage: TIGAS_STORAGE_FP32 keeps activated attributes in FP32 (236 B of
+ * payload per Gaussian); TIGAS_STORAGE_FP16 keeps positions in FP32 and
+ * opacity, scales, rotation and SH in FP16 (124 B of payload). */
+typedef struct {
+    uint64_t n;                   /* number of Gaussians, 1 .. 2^27 */
+    int sh_degree;                /* 0..3 */
+    int storage;                  /* TIGAS_STORAGE_* */
+    const float* means;
+    const float* log_scales;
+    const float* quats;
+    const float* opacity_logits;
+    const float* sh;
+    int inputs_on_device;         /* 1: the five arrays are device pointers */
+    float background[3];          /* RGB composited behind the Gaussians */
+} tigas_scene_desc;
+
+typedef struct tigas_scene tigas_scene;
+
+/* Upload and activate a scene (Sec. 5.1: scale = exp(s), opacity =
+ * sigmoid(logit), q / |q|) into the library's resident device layout.
+ * The caller keeps its arrays.  Synchronous.  Errors: INVALID (null, n out of
+ * range, sh_degree or storage invalid), OOM, CUDA. */
+tigas_status tigas_scene_load(const tigas_scene_desc* desc, tigas_scene** out_scene);
+
+/* Drop the caller's reference.  The scene's memory is released once no
+ * render or queued server request uses it (reference counting, Sec. 5.1
+ * "Dynamic Multi-Model Runtime").  NULL is INVALID. */
+tigas_status tigas_scene_free(tigas_scene* scene);
+
+/* Resident bytes of a scene's attribute storage. */
+tigas_status tigas_scene_bytes(const tigas_scene* scene, uint64_t* out_bytes);
+
+/* Render one frame (the hot path: preprocess, scan, duplicate-and-key emit,
+ * radix sort, tile ranges, per-tile blend).  out_rgba8: width*height*4 bytes,
+ * host or device.  Synchronous: returns after the frame is in out_rgba8.
+ * width, height in 1..8192.  Errors: INVALID, OOM, CUDA. */
+tigas_status tigas_render(tigas_scene* scene, const tigas_pose* pose, const tigas_intrinsics* intr,
+                          int width, int height, uint8_t* out_rgba8);
+
+enum {
+    TIGAS_SORT_DEPTH_FIRST = 0,  /* depth digits sorted per Gaussian, tile digits per pair (default) */
+    TIGAS_SORT_FULL64 = 1        /* every digit of the 64-bit (tile | depth) key sorted per pair */
+};
+
+typedef struct {
+    uint64_t n_visible;          /* (Gaussian, view) entries kept after culling */
+    uint64_t n_pairs;            /* (Gaussian, tile) pairs P */
+    uint32_t n_tiles;            /* 16x16 tiles in the frame(s) */
+    uint32_t sort_passes;        /* radix passes over the pair array */
+} tigas_frame_stats;
+
+/* tigas_render with options.
+ *   out_rgba8:     width*height*4 bytes, host or device, or NULL
+ *   out_rgba_f32:  width*height*4 floats (RGB + alpha before 8-bit encoding),
+ *                  host or device, or NULL (at least one output is required)
+ *   cuda_stream:   stream the work is ordered on; the call still returns only
+ *                  after the frame is complete
+ *   sort_mode:     TIGAS_SORT_*; both modes give the same tile lists
+ *   stats:         filled when non-NULL */
+tigas_status tigas_render_ex(tigas_scene* scene, const tigas_pose* pose, const tigas_intrinsics* intr,
+                             int width, int height, uint8_t* out_rgba8, float* out_rgba_f32,
+                             void* cuda_stream, int sort_mode, tigas_frame_stats* stats);
+
+/* Render n_views (1..64) poses of one scene in one fused launch set
+ * (batching): one preprocess pass reads the scene once for all views, one
+ * sort orders every view's pairs.  Views may have different resolutions.
+ * outs[v]: widths[v]*heights[v]*4 bytes, host or device.  Each result equals
+ * the frame a separate tigas_render call gives.  Synchronous.
+ * Errors: INVALID, OOM, CUDA. */
+tigas_status tigas_render_batch(tigas_scene* scene, int n_views, const tigas_pose* poses,
+                                const tigas_intrinsics* intrs, const int* widths, const int* heights,
+                                uint8_t* const* outs, void* cuda_stream);
+
+/* ------------------------------------------------------------------ debug */
+
+/* Intermediate results of one frame, for parity tests.  Host arrays, all
+ * caller-allocated; any may be NULL.
+ *   visible[n] (uint8), radius[n] (int32), rect[n*4] (int32: x_lo, y_lo,
+ *   x_hi, y_hi, half-open, in tiles), depth[n] (float32 view z),
+ *   uv[n*2] (float32), q[n] (float32 3 sqrt(lambda_max)),
+ *   values[pair_capacity] (uint32 Gaussian index, sorted by (tile, depth)),
+ *   ranges[n_tiles*2] (uint32 [start, end) per row-major tile),
+ *   rgba_f32[width*height*4].
+ * *out_pairs receives P; values are written only when P <= pair_capacity. */
+typedef struct {
+    uint8_t* visible;
+    int32_t* radius;
+    int32_t* rect;
+    float* depth;
+    float* uv;
+    float* q;
+    uint32_t* values;
+    uint64_t pair_capacity;
+    uint32_t* ranges;
+    float* rgba_f32;
+} tigas_debug_frame;
+
+tigas_status tigas_debug_render(tigas_scene* scene, const tigas_pose* pose, const tigas_intrinsics* intr,
+                                int width, int height, int sort_mode, tigas_debug_frame* out,
+                                uint64_t* out_pairs);
+
+/* Stable ascending LSD radix sort of n (key, value) pairs on the device (the
+ * sort of the hot path, exposed for testing), sorting key bits
+ * [begin_bit, end_bit) (0 <= begin_bit < end_bit <= 64).  keys: uint64,
+ * values: uint32; *_in and *_out are distinct device buffers of n elements;
+ * inputs are left unchanged.  Library-owned scratch.  Synchronous on
+ * cuda_stream.  Errors: INVALID, OOM, CUDA. */
+tigas_status tigas_sort_pairs_u64(const uint64_t* keys_in, const uint32_t* values_in, uint64_t* keys_out,
+                                  uint32_t* values_out, uint64_t n, int begin_bit, int end_bit,
+                                  void* cuda_stream);
+
+/* ---------------------------------------------------------------- serving */
+
+typedef struct {
+    uint64_t hbm_budget_bytes;   /* admission budget for in-flight workspace (0: 16 GiB) */
+    int max_batch;               /* requests fused into one launch set (1..64, 0: 16) */
+    int max_inflight;            /* launch sets in flight on separate streams (1..8, 0: 2) */
+    int batch_window_us;         /* how long a partial batch may wait for more requests (0: none) */
+} tigas_server_config;
+
+typedef struct tigas_server tigas_server;
+
+typedef struct {
+    uint64_t ticket;
+    uint64_t client_id;
+    int status;                  /* tigas_status of this request */
+    int width, height;
+    double submit_us;            /* host monotonic clock, microseconds */
+    double admit_us;             /* when the request entered a launch set */
+    double done_us;              /* when its frame was complete in its buffer */
+} tigas_completion;
+
+/* Start a server thread that keeps taking requests while earlier ones render
+ * (continuous batching, Sec. 5.1 multi-client runtime).  Errors: INVALID, OOM, CUDA. */
+tigas_status tigas_server_create(const tigas_server_config* cfg, tigas_server** out_server);
+
+/* Finish queued work (cancel=0) or complete queued requests with
+ * TIGAS_ERR_AGAIN (cancel=1), stop the thread and free the server. */
+tigas_status tigas_server_destroy(tigas_server* server, int cancel);
+
+/* Queue one render request.  out_rgba8 (host or device, w*h*4 bytes) must stay
+ * valid until the ticket completes.  A queued, not yet admitted request of the
+ * same client_id is superseded (completes with TIGAS_ERR_AGAIN): the newest
+ * pose wins, as each request is a stateless per-frame task (Sec. 4.2).
+ * Errors: INVALID, AGAIN (queue full). */
+tigas_status tigas_server_submit(tigas_server* server, tigas_scene* scene, const tigas_pose* pose,
+                                 const tigas_intrinsics* intr, int width, int height, uint8_t* out_rgba8,
+                                 uint64_t client_id, uint64_t* out_ticket);
+
+/* Collect up to max completions, waiting up to timeout_us (0: do not wait)
+ * for at least one.  *n_done receives the count (0 on timeout). */
+tigas_status tigas_server_poll(tigas_server* server, tigas_completion* out, int max, int timeout_us,
+                               int* n_done);
+
+/* ------------------------------------------------------------------ misc */
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* tigas_last_error(void);
+
+/* Library version string. */
+const char* tigas_version(void);
+
+/* Kernel launches issued by this process so far (all entry points). */
+uint64_t tigas_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TIGAS_H */

@@ -1,0 +1,342 @@
+// C ABI entry points (include/tigas.h): argument validation, host/device
+// buffer handling and error reporting around the frame pipeline.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pipeline.cuh"
+
+#define TIGAS_API extern "C" __attribute__((visibility("default")))
+
+namespace tigas {
+
+namespace {
+thread_local std::string t_last_error;
+}
+
+void set_error(const std::string& msg) { t_last_error = msg; }
+const char* last_error() { return t_last_error.c_str(); }
+
+tigas_status fail(const Status& s) {
+    set_error(s.msg);
+    return s.code;
+}
+tigas_status fail(tigas_status code, const std::string& msg) {
+    set_error(msg);
+    return code;
+}
+
+Status validate_view(const tigas_pose* pose, const tigas_intrinsics* k, int w, int h) {
+    if (!pose || !k) return {TIGAS_ERR_INVALID, "null pose or intrinsics"};
+    if (!std::isfinite(pose->azimuth) || !std::isfinite(pose->elevation) || !std::isfinite(pose->t[0]) ||
+        !std::isfinite(pose->t[1]) || !std::isfinite(pose->t[2]))
+        return {TIGAS_ERR_INVALID, "non-finite pose"};
+    if (!(std::isfinite(k->fx) && std::isfinite(k->fy) && std::isfinite(k->cx) && std::isfinite(k->cy)) ||
+        !(k->fx > 0) || !(k->fy > 0))
+        return {TIGAS_ERR_INVALID, "intrinsics must be finite with fx, fy > 0"};
+    if (w < 1 || h < 1 || w > kMaxDim || h > kMaxDim) return {TIGAS_ERR_INVALID, "width/height out of 1..8192"};
+    return {};
+}
+
+// Device buffer for a host output, grown on demand (one slot per output).
+Status staging(RenderContext& ctx, int slot, size_t bytes, uint8_t** out) {
+    if ((int)ctx.dev_staging.size() <= slot) {
+        ctx.dev_staging.resize(slot + 1, nullptr);
+        ctx.staging_bytes.resize(slot + 1, 0);
+    }
+    if (ctx.staging_bytes[slot] < bytes) {
+        if (ctx.dev_staging[slot]) cudaFree(ctx.dev_staging[slot]);
+        ctx.dev_staging[slot] = nullptr;
+        ctx.staging_bytes[slot] = 0;
+        TIGAS_CUDA_TRY(cudaMalloc(&ctx.dev_staging[slot], bytes));
+        ctx.staging_bytes[slot] = bytes;
+    }
+    *out = ctx.dev_staging[slot];
+    return {};
+}
+
+struct ContextGuard {
+    RenderContext* ctx = nullptr;
+    ~ContextGuard() {
+        if (ctx) release_context(ctx);
+    }
+};
+
+struct SceneGuard {
+    Scene* s = nullptr;
+    explicit SceneGuard(Scene* sc) : s(sc) {
+        if (s) scene_acquire(s);
+    }
+    ~SceneGuard() {
+        if (s) scene_release(s);
+    }
+};
+
+// Render V views synchronously; outputs may be host or device.
+Status do_render(Scene* scene, int V, const tigas_pose* poses, const tigas_intrinsics* intrs, const int* ws,
+                 const int* hs, uint8_t* const* outs8, float* const* outs32, cudaStream_t user_st, int sort_mode,
+                 tigas_frame_stats* stats, tigas_debug_frame* dbg, uint64_t* dbg_pairs) {
+    if (!scene) return {TIGAS_ERR_INVALID, "null scene"};
+    if (V < 1 || V > kMaxViews) return {TIGAS_ERR_INVALID, "n_views out of 1..64"};
+    if (sort_mode != TIGAS_SORT_DEPTH_FIRST && sort_mode != TIGAS_SORT_FULL64)
+        return {TIGAS_ERR_INVALID, "unknown sort mode"};
+    for (int v = 0; v < V; ++v) TIGAS_TRY(validate_view(&poses[v], &intrs[v], ws[v], hs[v]));
+    Status err;
+    ContextGuard g;
+    g.ctx = acquire_context(&err);
+    if (!g.ctx) return err;
+    RenderContext& ctx = *g.ctx;
+    cudaStream_t st = user_st ? user_st : ctx.stream;
+
+    FrameRequest req;
+    req.V = V;
+    req.sort_mode = sort_mode;
+    req.want_q = dbg != nullptr;
+    std::vector<uint8_t*> host8(V, nullptr);
+    std::vector<float*> host32(V, nullptr);
+    for (int v = 0; v < V; ++v) {
+        req.views[v] = make_view(poses[v], intrs[v], ws[v], hs[v], 0);
+        const size_t px = (size_t)ws[v] * hs[v];
+        uint8_t* o8 = outs8 ? outs8[v] : nullptr;
+        float* o32 = outs32 ? outs32[v] : nullptr;
+        if (o8 && !is_device_pointer(o8)) {
+            host8[v] = o8;
+            TIGAS_TRY(staging(ctx, 2 * v, px * 4, &o8));
+        }
+        if (o32 && !is_device_pointer(o32)) {
+            host32[v] = o32;
+            uint8_t* p = nullptr;
+            TIGAS_TRY(staging(ctx, 2 * v + 1, px * 16, &p));
+            o32 = reinterpret_cast<float*>(p);
+        }
+        req.views[v].out_rgba8 = o8;
+        req.views[v].out_rgba_f32 = o32;
+    }
+    FrameResult res;
+    TIGAS_TRY(render_frame(scene, req, ctx, st, &res));
+    for (int v = 0; v < V; ++v) {
+        const size_t px = (size_t)ws[v] * hs[v];
+        if (host8[v])
+            TIGAS_CUDA_TRY(cudaMemcpyAsync(host8[v], req.views[v].out_rgba8, px * 4, cudaMemcpyDeviceToHost, st));
+        if (host32[v])
+            TIGAS_CUDA_TRY(cudaMemcpyAsync(host32[v], req.views[v].out_rgba_f32, px * 16, cudaMemcpyDeviceToHost, st));
+    }
+    TIGAS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (ctx.h_flags[0] & 1u) return {TIGAS_ERR_OVERFLOW, "pair buffer overflow"};
+    if (ctx.h_flags[0] & 2u) return {TIGAS_ERR_CUDA, "tile id out of range in sorted keys"};
+
+    if (stats) {
+        uint32_t vis[kMaxViews];
+        TIGAS_CUDA_TRY(cudaMemcpy(vis, res.d_visible, sizeof(uint32_t) * V, cudaMemcpyDeviceToHost));
+        uint64_t nv = 0;
+        for (int v = 0; v < V; ++v) nv += vis[v];
+        stats->n_visible = nv;
+        stats->n_pairs = res.pairs;
+        stats->n_tiles = res.total_tiles;
+        stats->sort_passes = (uint32_t)res.sort_passes;
+    }
+    if (dbg) {
+        const uint32_t n = scene->view.n;
+        if (dbg_pairs) *dbg_pairs = res.pairs;
+        std::vector<uint32_t> tiles(n), dkey(n);
+        std::vector<uint2> rect(n);
+        std::vector<float4> geom(n);
+        std::vector<float> q(n);
+        TIGAS_CUDA_TRY(cudaMemcpy(tiles.data(), res.splats.tiles, n * 4ull, cudaMemcpyDeviceToHost));
+        TIGAS_CUDA_TRY(cudaMemcpy(dkey.data(), res.splats.depth_key, n * 4ull, cudaMemcpyDeviceToHost));
+        TIGAS_CUDA_TRY(cudaMemcpy(rect.data(), res.splats.rect, n * 8ull, cudaMemcpyDeviceToHost));
+        TIGAS_CUDA_TRY(cudaMemcpy(geom.data(), res.splats.geom, n * 16ull, cudaMemcpyDeviceToHost));
+        TIGAS_CUDA_TRY(cudaMemcpy(q.data(), res.splats.q_dbg, n * 4ull, cudaMemcpyDeviceToHost));
+        for (uint32_t i = 0; i < n; ++i) {
+            const bool vis = tiles[i] > 0;
+            if (dbg->visible) dbg->visible[i] = vis ? 1 : 0;
+            if (dbg->radius) dbg->radius[i] = vis ? (int32_t)ceilf(q[i]) : 0;
+            if (dbg->rect) {
+                int32_t* r = dbg->rect + 4 * (size_t)i;
+                if (vis) {
+                    r[0] = rect[i].x & 0xFFFF; r[1] = rect[i].x >> 16;
+                    r[2] = rect[i].y & 0xFFFF; r[3] = rect[i].y >> 16;
+                } else {
+                    r[0] = r[1] = r[2] = r[3] = 0;
+                }
+            }
+            if (dbg->depth) {
+                float d;
+                std::memcpy(&d, &dkey[i], 4);
+                dbg->depth[i] = vis ? d : 0.0f;
+            }
+            if (dbg->uv) {
+                dbg->uv[2 * (size_t)i] = vis ? geom[i].x : 0.0f;
+                dbg->uv[2 * (size_t)i + 1] = vis ? geom[i].y : 0.0f;
+            }
+            if (dbg->q) dbg->q[i] = q[i];
+        }
+        if (dbg->values && res.pairs <= dbg->pair_capacity && res.pairs)
+            TIGAS_CUDA_TRY(cudaMemcpy(dbg->values, res.values, res.pairs * 4, cudaMemcpyDeviceToHost));
+        if (dbg->ranges)
+            TIGAS_CUDA_TRY(cudaMemcpy(dbg->ranges, res.ranges, (size_t)res.total_tiles * 8, cudaMemcpyDeviceToHost));
+    }
+    return {};
+}
+
+}  // namespace tigas
+
+using namespace tigas;
+
+TIGAS_API const char* tigas_last_error(void) { return last_error(); }
+TIGAS_API const char* tigas_version(void) { return "tigas-b300 0.1 (sm_103a)"; }
+TIGAS_API uint64_t tigas_kernel_launches(void) { return g_launches.load(); }
+
+TIGAS_API tigas_status tigas_scene_load(const tigas_scene_desc* d, tigas_scene** out) {
+    set_error("");
+    if (!d || !out) return fail(TIGAS_ERR_INVALID, "null argument");
+    *out = nullptr;
+    if (d->n < 1 || d->n > (1ull << 27)) return fail(TIGAS_ERR_INVALID, "n out of 1..2^27");
+    if (d->sh_degree < 0 || d->sh_degree > 3) return fail(TIGAS_ERR_INVALID, "sh_degree out of 0..3");
+    if (d->storage != TIGAS_STORAGE_FP32 && d->storage != TIGAS_STORAGE_FP16)
+        return fail(TIGAS_ERR_INVALID, "unknown storage");
+    if (!d->means || !d->log_scales || !d->quats || !d->opacity_logits || !d->sh)
+        return fail(TIGAS_ERR_INVALID, "null attribute array");
+    for (int c = 0; c < 3; ++c)
+        if (!std::isfinite(d->background[c])) return fail(TIGAS_ERR_INVALID, "non-finite background");
+    const uint32_t n = (uint32_t)d->n;
+    const int C = d->storage == TIGAS_STORAGE_FP32 ? kChunksF32 : kChunksF16;
+    const size_t chunk_count = (size_t)((n + 31) / 32) * 32 * C;
+    auto* s = new Scene();
+    s->view.n = n;
+    s->view.sh_degree = d->sh_degree;
+    s->view.storage = d->storage;
+    for (int c = 0; c < 3; ++c) s->view.bg[c] = d->background[c];
+    s->bytes = chunk_count * 16;
+    cudaError_t e = cudaMalloc(&s->chunks, s->bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return fail(TIGAS_ERR_OOM, "scene allocation failed");
+    }
+    s->view.chunks = s->chunks;
+    const float *m = d->means, *ls = d->log_scales, *q = d->quats, *op = d->opacity_logits, *sh = d->sh;
+    float* staging_buf = nullptr;
+    auto finish = [&](const Status& st) -> tigas_status {
+        if (staging_buf) cudaFree(staging_buf);
+        if (!st.ok()) {
+            cudaFree(s->chunks);
+            delete s;
+            return fail(st);
+        }
+        *out = reinterpret_cast<tigas_scene*>(s);
+        return TIGAS_OK;
+    };
+    if (!d->inputs_on_device) {
+        const size_t words = (size_t)n * (3 + 3 + 4 + 1 + 48);
+        e = cudaMalloc(&staging_buf, words * 4);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            staging_buf = nullptr;
+            return finish({TIGAS_ERR_OOM, "staging allocation failed"});
+        }
+        float* p = staging_buf;
+        const float* src[5] = {m, ls, q, op, sh};
+        const size_t len[5] = {3ull * n, 3ull * n, 4ull * n, 1ull * n, 48ull * n};
+        const float** dst[5] = {&m, &ls, &q, &op, &sh};
+        for (int k = 0; k < 5; ++k) {
+            e = cudaMemcpy(p, src[k], len[k] * 4, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return finish({TIGAS_ERR_CUDA, cudaGetErrorString(e)});
+            *dst[k] = p;
+            p += len[k];
+        }
+    }
+    Status st = launch_scene_pack(m, ls, q, op, sh, n, d->sh_degree, d->storage, s->chunks, 0);
+    if (st.ok()) {
+        e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) st = {TIGAS_ERR_CUDA, cudaGetErrorString(e)};
+    }
+    return finish(st);
+}
+
+TIGAS_API tigas_status tigas_scene_free(tigas_scene* scene) {
+    if (!scene) return fail(TIGAS_ERR_INVALID, "null scene");
+    scene_release(reinterpret_cast<Scene*>(scene));
+    return TIGAS_OK;
+}
+
+TIGAS_API tigas_status tigas_scene_bytes(const tigas_scene* scene, uint64_t* out) {
+    if (!scene || !out) return fail(TIGAS_ERR_INVALID, "null argument");
+    *out = reinterpret_cast<const Scene*>(scene)->bytes;
+    return TIGAS_OK;
+}
+
+TIGAS_API tigas_status tigas_render_ex(tigas_scene* scene, const tigas_pose* pose, const tigas_intrinsics* intr,
+                                       int width, int height, uint8_t* out_rgba8, float* out_rgba_f32,
+                                       void* cuda_stream, int sort_mode, tigas_frame_stats* stats) {
+    set_error("");
+    if (!out_rgba8 && !out_rgba_f32) return fail(TIGAS_ERR_INVALID, "no output buffer");
+    SceneGuard sg(reinterpret_cast<Scene*>(scene));
+    Status st = do_render(sg.s, 1, pose, intr, &width, &height, &out_rgba8, &out_rgba_f32, (cudaStream_t)cuda_stream,
+                          sort_mode, stats, nullptr, nullptr);
+    return st.ok() ? TIGAS_OK : fail(st);
+}
+
+TIGAS_API tigas_status tigas_render(tigas_scene* scene, const tigas_pose* pose, const tigas_intrinsics* intr,
+                                    int width, int height, uint8_t* out_rgba8) {
+    if (!out_rgba8) return fail(TIGAS_ERR_INVALID, "null output");
+    return tigas_render_ex(scene, pose, intr, width, height, out_rgba8, nullptr, nullptr, TIGAS_SORT_DEPTH_FIRST,
+                           nullptr);
+}
+
+TIGAS_API tigas_status tigas_render_batch(tigas_scene* scene, int n_views, const tigas_pose* poses,
+                                          const tigas_intrinsics* intrs, const int* widths, const int* heights,
+                                          uint8_t* const* outs, void* cuda_stream) {
+    set_error("");
+    if (!poses || !intrs || !widths || !heights || !outs) return fail(TIGAS_ERR_INVALID, "null argument");
+    if (n_views < 1 || n_views > kMaxViews) return fail(TIGAS_ERR_INVALID, "n_views out of 1..64");
+    for (int v = 0; v < n_views; ++v)
+        if (!outs[v]) return fail(TIGAS_ERR_INVALID, "null output buffer");
+    SceneGuard sg(reinterpret_cast<Scene*>(scene));
+    Status st = do_render(sg.s, n_views, poses, intrs, widths, heights, outs, nullptr, (cudaStream_t)cuda_stream,
+                          TIGAS_SORT_DEPTH_FIRST, nullptr, nullptr, nullptr);
+    return st.ok() ? TIGAS_OK : fail(st);
+}
+
+TIGAS_API tigas_status tigas_debug_render(tigas_scene* scene, const tigas_pose* pose, const tigas_intrinsics* intr,
+                                          int width, int height, int sort_mode, tigas_debug_frame* out,
+                                          uint64_t* out_pairs) {
+    set_error("");
+    if (!out) return fail(TIGAS_ERR_INVALID, "null debug output");
+    SceneGuard sg(reinterpret_cast<Scene*>(scene));
+    float* f32 = out->rgba_f32;
+    uint8_t* none = nullptr;
+    Status st = do_render(sg.s, 1, pose, intr, &width, &height, &none, f32 ? &f32 : nullptr, nullptr, sort_mode,
+                          nullptr, out, out_pairs);
+    return st.ok() ? TIGAS_OK : fail(st);
+}
+
+TIGAS_API tigas_status tigas_sort_pairs_u64(const uint64_t* keys_in, const uint32_t* values_in, uint64_t* keys_out,
+                                            uint32_t* values_out, uint64_t n, int begin_bit, int end_bit,
+                                            void* cuda_stream) {
+    set_error("");
+    if (n > 0 && (!keys_in || !values_in || !keys_out || !values_out)) return fail(TIGAS_ERR_INVALID, "null buffer");
+    if (begin_bit < 0 || end_bit > 64 || begin_bit >= end_bit) return fail(TIGAS_ERR_INVALID, "bad bit range");
+    if (n >= 0xFFFFFFFFull) return fail(TIGAS_ERR_INVALID, "n too large");
+    if (n == 0) return TIGAS_OK;
+    if (keys_in == keys_out || values_in == values_out) return fail(TIGAS_ERR_INVALID, "in and out must differ");
+    Status err;
+    ContextGuard g;
+    g.ctx = acquire_context(&err);
+    if (!g.ctx) return fail(err);
+    cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : g.ctx->stream;
+    const size_t words = radix_tmp_words(n);
+    Status s = g.ctx->pairs.reserve(n * 12 + words * 4 + 4096);
+    if (!s.ok()) return fail(s);
+    g.ctx->pairs.reset();
+    uint64_t* ka = g.ctx->pairs.take<uint64_t>(n);
+    uint32_t* va = g.ctx->pairs.take<uint32_t>(n);
+    uint32_t* tmp = g.ctx->pairs.take<uint32_t>(words);
+    s = radix_sort<uint64_t>(keys_in, values_in, ka, va, keys_out, values_out, n, nullptr, begin_bit, end_bit, tmp, st,
+                             nullptr);
+    if (!s.ok()) return fail(s);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(TIGAS_ERR_CUDA, cudaGetErrorString(e));
+    return TIGAS_OK;
+}

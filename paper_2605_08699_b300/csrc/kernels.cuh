@@ -1,0 +1,61 @@
+// Launch interface of the hot-path kernels (all stream-ordered, no host sync).
+#pragma once
+
+#include "common.cuh"
+
+namespace tigas {
+
+// a0 / K7: activate raw attributes and pack them into the resident layout.
+Status launch_scene_pack(const float* means, const float* log_scales, const float* quats,
+                         const float* opacity_logits, const float* sh, uint32_t n, int sh_degree,
+                         int storage, uint4* chunks, cudaStream_t st);
+
+// K1: per-Gaussian preprocess for V views (Gaussian attributes read once).
+// views: device array of V ViewParams.  n_visible: device counters [V] (zeroed here).
+Status launch_preprocess(const SceneView& scene, const ViewParams* views, int V, const SplatArrays& out,
+                         uint32_t* n_visible, cudaStream_t st);
+
+// K2: exclusive scan of u32 counts.  out[k] = sum_{k' < k} in[order ? order[k'] : k'],
+// total64 = full sum (u64).  tmp: scratch of scan_tmp_words(n) words.
+size_t scan_tmp_words(uint64_t n);
+Status launch_scan_u32(const uint32_t* in, const uint32_t* order, uint32_t* out, uint64_t n,
+                       uint64_t* total64, uint32_t* tmp, cudaStream_t st);
+
+// K3: duplicate-and-key emit.  For each k < n_entries with e = order ? order[k] : k
+// and tiles[e] > 0, write the tiles of rect[e] (row-major) at offsets[k]..:
+//   32-bit keys: key = tile_base(view) + ty * TX + tx
+//   64-bit keys: key = (tile id << 32) | depth_key[e]
+// value = e.  Writes beyond pair_cap are dropped and set *overflow.
+Status launch_emit_u32(const uint32_t* order, const uint32_t* offsets, const SplatArrays& sp,
+                       const ViewParams* views, int V, uint32_t n_per_view, uint64_t n_entries,
+                       uint32_t* keys, uint32_t* values, uint64_t pair_cap, uint32_t* overflow,
+                       cudaStream_t st);
+Status launch_emit_u64(const uint32_t* offsets, const SplatArrays& sp, const ViewParams* views, int V,
+                       uint32_t n_per_view, uint64_t n_entries, uint64_t* keys, uint32_t* values,
+                       uint64_t pair_cap, uint32_t* overflow, cudaStream_t st);
+
+// K4: stable LSD radix sort of (key, value) pairs over key bits [begin, end).
+// The element count is min(*d_n, n_cap) when d_n is given, else n_cap.
+// values_in == nullptr means values 0..n-1.  keys_alt/values_alt are the
+// ping-pong buffers; the sorted result lands in (keys_out, values_out).
+// tmp: radix_tmp_words(n_cap) words.
+size_t radix_tmp_words(uint64_t n_cap);
+template <typename K>
+Status radix_sort(const K* keys_in, const uint32_t* values_in, K* keys_alt, uint32_t* values_alt,
+                  K* keys_out, uint32_t* values_out, uint64_t n_cap, const uint64_t* d_n, int begin_bit,
+                  int end_bit, uint32_t* tmp, cudaStream_t st, int* passes_out);
+
+// K5: tile ranges from sorted keys (tile = key >> shift).  ranges must hold
+// n_tiles uint2 and is zeroed here.  Keys outside [0, n_tiles) set *overflow.
+template <typename K>
+Status launch_ranges(const K* keys, uint64_t n_cap, const uint64_t* d_n, int shift, uint2* ranges,
+                     uint32_t n_tiles, uint32_t* overflow, cudaStream_t st);
+
+// K6: per-tile front-to-back blend of every view's tiles (grid = total_tiles).
+// values hold entry indices < n_entries.  bg: host RGB.
+// evals: optional device counter of list entries visited (instrumented run).
+Status launch_blend(const uint2* ranges, const uint32_t* values, const SplatArrays& sp,
+                    const ViewParams* views, int V, uint32_t total_tiles, uint32_t n_entries,
+                    const float* bg, unsigned long long* evals, cudaStream_t st);
+
+}  // namespace tigas

@@ -1,0 +1,257 @@
+// Frame pipeline orchestration (host side of the hot path).
+#include "pipeline.cuh"
+
+#include <cmath>
+#include <cstring>
+
+namespace tigas {
+
+std::atomic<uint64_t> g_launches{0};
+
+// ------------------------------------------------------------------ scene
+
+void scene_acquire(Scene* s) { s->refs.fetch_add(1, std::memory_order_relaxed); }
+
+void scene_release(Scene* s) {
+    if (s->refs.fetch_sub(1, std::memory_order_acq_rel) == 1) {
+        if (s->chunks) cudaFree(s->chunks);
+        delete s;
+    }
+}
+
+// ------------------------------------------------------------------ arena
+
+Status Arena::reserve(size_t bytes) {
+    if (bytes <= cap) return {};
+    if (base) {
+        cudaFree(base);
+        base = nullptr;
+        cap = 0;
+    }
+    size_t want = bytes + bytes / 4 + (1 << 20);
+    cudaError_t e = cudaMalloc(&base, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        base = nullptr;
+        e = cudaMalloc(&base, bytes);   // retry without headroom
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            base = nullptr;
+            return {TIGAS_ERR_OOM, "workspace allocation of " + std::to_string(bytes) + " bytes failed"};
+        }
+        want = bytes;
+    }
+    cap = want;
+    used = 0;
+    return {};
+}
+
+void Arena::release() {
+    if (base) cudaFree(base);
+    base = nullptr;
+    cap = used = 0;
+}
+
+// ----------------------------------------------------------------- camera
+
+ViewParams make_view(const tigas_pose& pose, const tigas_intrinsics& k, int width, int height, uint32_t tile_base) {
+    ViewParams v{};
+    const double ca = std::cos(pose.azimuth), sa = std::sin(pose.azimuth);
+    const double ce = std::cos(pose.elevation), se = std::sin(pose.elevation);
+    // R = R_y(az) R_x(el); columns: camera right, down, forward in world
+    const double R[9] = {ca, sa * se, sa * ce,
+                         0.0, ce, -se,
+                         -sa, ca * se, ca * ce};
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) v.Rt[3 * r + c] = (float)R[3 * c + r];
+    for (int c = 0; c < 3; ++c) v.campos[c] = (float)pose.t[c];
+    v.fx = (float)k.fx; v.fy = (float)k.fy; v.cx = (float)k.cx; v.cy = (float)k.cy;
+    v.limx = (float)(1.3 * width / (2.0 * k.fx));
+    v.limy = (float)(1.3 * height / (2.0 * k.fy));
+    v.W = width; v.H = height;
+    v.TX = (width + kTile - 1) / kTile;
+    v.TY = (height + kTile - 1) / kTile;
+    v.tile_base = tile_base;
+    return v;
+}
+
+// ---------------------------------------------------------------- context
+
+Status RenderContext::init() {
+    TIGAS_CUDA_TRY(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+    TIGAS_CUDA_TRY(cudaMallocHost(&h_total, sizeof(uint64_t) * 2));
+    TIGAS_CUDA_TRY(cudaMallocHost(&h_flags, sizeof(uint32_t) * 2));
+    TIGAS_CUDA_TRY(cudaMallocHost(&h_views, sizeof(ViewParams) * kMaxViews));
+    return {};
+}
+
+void RenderContext::destroy() {
+    fixed.release();
+    pairs.release();
+    for (auto* p : dev_staging)
+        if (p) cudaFree(p);
+    dev_staging.clear();
+    staging_bytes.clear();
+    if (h_total) cudaFreeHost(h_total);
+    if (h_flags) cudaFreeHost(h_flags);
+    if (h_views) cudaFreeHost(h_views);
+    if (stream) cudaStreamDestroy(stream);
+    h_total = nullptr; h_flags = nullptr; h_views = nullptr; stream = nullptr;
+}
+
+namespace {
+std::mutex g_pool_mu;
+std::vector<RenderContext*> g_pool;
+}  // namespace
+
+RenderContext* acquire_context(Status* err) {
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        if (!g_pool.empty()) {
+            RenderContext* c = g_pool.back();
+            g_pool.pop_back();
+            return c;
+        }
+    }
+    auto* c = new RenderContext();
+    Status s = c->init();
+    if (!s.ok()) {
+        c->destroy();
+        delete c;
+        if (err) *err = s;
+        return nullptr;
+    }
+    return c;
+}
+
+void release_context(RenderContext* ctx) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    g_pool.push_back(ctx);
+}
+
+bool is_device_pointer(const void* p) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// -------------------------------------------------------------- pipeline
+
+Status render_frame(Scene* scene, FrameRequest& req, RenderContext& ctx, cudaStream_t st, FrameResult* res) {
+    const int V = req.V;
+    const uint32_t n = scene->view.n;
+    const uint64_t E = (uint64_t)V * n;
+    if (E >= 0xFFFFFFFFull) return {TIGAS_ERR_INVALID, "views x Gaussians exceeds 2^32 entries"};
+    uint32_t total_tiles = 0;
+    for (int v = 0; v < V; ++v) {
+        req.views[v].tile_base = total_tiles;
+        total_tiles += (uint32_t)(req.views[v].TX * req.views[v].TY);
+    }
+    const int tile_bits = total_tiles <= 1 ? 1 : 32 - __builtin_clz(total_tiles - 1);
+    const bool full64 = req.sort_mode == TIGAS_SORT_FULL64;
+
+    // ---- per-entry workspace
+    const size_t presort_words = full64 ? 0 : radix_tmp_words(E);
+    const size_t scan_words = scan_tmp_words(E);
+    const size_t tmp_words = presort_words > scan_words ? presort_words : scan_words;
+    size_t fixed_bytes = sizeof(ViewParams) * kMaxViews + 64 * 256;
+    fixed_bytes += E * (16 + 16 + 4 + 4 + 4 + 8 + (req.want_q ? 4 : 0));
+    fixed_bytes += full64 ? 0 : E * 4 * 4;                 // depth-sort ping-pong + result
+    fixed_bytes += E * 4;                                  // offsets
+    fixed_bytes += tmp_words * 4;
+    fixed_bytes += sizeof(uint2) * (size_t)total_tiles;
+    TIGAS_TRY(ctx.fixed.reserve(fixed_bytes));
+    ctx.fixed.reset();
+    ViewParams* d_views = ctx.fixed.take<ViewParams>(kMaxViews);
+    uint64_t* d_total = ctx.fixed.take<uint64_t>(2);
+    uint32_t* d_flags = ctx.fixed.take<uint32_t>(2);
+    uint32_t* d_visible = ctx.fixed.take<uint32_t>(kMaxViews);
+    SplatArrays sp{};
+    sp.geom = ctx.fixed.take<float4>(E);
+    sp.appear = ctx.fixed.take<float4>(E);
+    sp.blue = ctx.fixed.take<float>(E);
+    sp.depth_key = ctx.fixed.take<uint32_t>(E);
+    sp.tiles = ctx.fixed.take<uint32_t>(E);
+    sp.rect = ctx.fixed.take<uint2>(E);
+    sp.q_dbg = req.want_q ? ctx.fixed.take<float>(E) : nullptr;
+    uint32_t* offsets = ctx.fixed.take<uint32_t>(E);
+    uint32_t *pk_alt = nullptr, *pv_alt = nullptr, *pk = nullptr, *order = nullptr;
+    if (!full64) {
+        pk_alt = ctx.fixed.take<uint32_t>(E);
+        pv_alt = ctx.fixed.take<uint32_t>(E);
+        pk = ctx.fixed.take<uint32_t>(E);
+        order = ctx.fixed.take<uint32_t>(E);
+    }
+    uint32_t* tmp = ctx.fixed.take<uint32_t>(tmp_words);
+    uint2* ranges = ctx.fixed.take<uint2>(total_tiles);
+
+    std::memcpy(ctx.h_views, req.views, sizeof(ViewParams) * V);
+    TIGAS_CUDA_TRY(cudaMemcpyAsync(d_views, ctx.h_views, sizeof(ViewParams) * V, cudaMemcpyHostToDevice, st));
+    TIGAS_CUDA_TRY(cudaMemsetAsync(d_flags, 0, sizeof(uint32_t) * 2, st));
+    if (sp.q_dbg) TIGAS_CUDA_TRY(cudaMemsetAsync(sp.q_dbg, 0, E * 4, st));
+
+    // K1
+    TIGAS_TRY(launch_preprocess(scene->view, d_views, V, sp, d_visible, st));
+
+    // depth digits first (one key per entry), or nothing here (FULL64)
+    if (!full64) {
+        int passes = 0;
+        TIGAS_TRY(radix_sort<uint32_t>(sp.depth_key, nullptr, pk_alt, pv_alt, pk, order, E, nullptr, 0, 32, tmp, st,
+                                       &passes));
+    }
+    // K2: pair offsets in emit order
+    TIGAS_TRY(launch_scan_u32(sp.tiles, order, offsets, E, d_total, tmp, st));
+    TIGAS_CUDA_TRY(cudaMemcpyAsync(ctx.h_total, d_total, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    TIGAS_CUDA_TRY(cudaStreamSynchronize(st));
+    const uint64_t P = ctx.h_total[0];
+    if (P >= 0xFFFFFFFFull) return {TIGAS_ERR_OVERFLOW, "pair count exceeds 2^32"};
+
+    // ---- per-pair workspace
+    const size_t kb = full64 ? 8 : 4;
+    const size_t sort_words = radix_tmp_words(P);
+    size_t pair_bytes = P * (kb * 3 + 4 * 3) + sort_words * 4 + 8 * 256;
+    TIGAS_TRY(ctx.pairs.reserve(pair_bytes));
+    ctx.pairs.reset();
+    void* keys_a = ctx.pairs.take<uint8_t>(P * kb);
+    void* keys_b = ctx.pairs.take<uint8_t>(P * kb);
+    void* keys_c = ctx.pairs.take<uint8_t>(P * kb);
+    uint32_t* vals_a = ctx.pairs.take<uint32_t>(P);
+    uint32_t* vals_b = ctx.pairs.take<uint32_t>(P);
+    uint32_t* vals_c = ctx.pairs.take<uint32_t>(P);
+    uint32_t* stmp = ctx.pairs.take<uint32_t>(sort_words);
+
+    int passes = 0;
+    if (!full64) {
+        // K3 in depth order, K4 on the tile digits only
+        TIGAS_TRY(launch_emit_u32(order, offsets, sp, d_views, V, n, E, (uint32_t*)keys_a, vals_a, P, d_flags, st));
+        TIGAS_TRY(radix_sort<uint32_t>((uint32_t*)keys_a, vals_a, (uint32_t*)keys_b, vals_b, (uint32_t*)keys_c, vals_c,
+                                       P, nullptr, 0, tile_bits, stmp, st, &passes));
+        TIGAS_TRY(launch_ranges<uint32_t>((uint32_t*)keys_c, P, nullptr, 0, ranges, total_tiles, d_flags, st));
+    } else {
+        // K3 in index order with 64-bit (tile | depth) keys, K4 on all significant bits
+        TIGAS_TRY(launch_emit_u64(offsets, sp, d_views, V, n, E, (uint64_t*)keys_a, vals_a, P, d_flags, st));
+        TIGAS_TRY(radix_sort<uint64_t>((uint64_t*)keys_a, vals_a, (uint64_t*)keys_b, vals_b, (uint64_t*)keys_c, vals_c,
+                                       P, nullptr, 0, 32 + tile_bits, stmp, st, &passes));
+        TIGAS_TRY(launch_ranges<uint64_t>((uint64_t*)keys_c, P, nullptr, 32, ranges, total_tiles, d_flags, st));
+    }
+    // K6
+    TIGAS_TRY(launch_blend(ranges, vals_c, sp, d_views, V, total_tiles, (uint32_t)E, scene->view.bg, req.d_evals, st));
+    TIGAS_CUDA_TRY(cudaMemcpyAsync(ctx.h_flags, d_flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+
+    if (res) {
+        res->pairs = P;
+        res->total_tiles = total_tiles;
+        res->sort_passes = passes;
+        res->values = vals_c;
+        res->ranges = ranges;
+        res->splats = sp;
+        res->d_visible = d_visible;
+    }
+    return {};
+}
+
+}  // namespace tigas
