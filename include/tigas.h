@@ -117,6 +117,8 @@ typedef struct {
     uint64_t n_pairs;            /* (Gaussian, tile) pairs P */
     uint32_t n_tiles;            /* 16x16 tiles in the frame(s) */
     uint32_t sort_passes;        /* radix passes over the pair array */
+    uint64_t blend_evals;        /* list entries evaluated, summed over pixels, up to each pixel's stop */
+    uint64_t blend_fetched;      /* list entries staged into shared memory by the blend */
 } tigas_frame_stats;
 
 /* tigas_render with options.
@@ -221,6 +223,21 @@ tigas_status tigas_server_submit(tigas_server* server, tigas_scene* scene, const
  * for at least one.  *n_done receives the count (0 on timeout). */
 tigas_status tigas_server_poll(tigas_server* server, tigas_completion* out, int max, int timeout_us,
                                int* n_done);
+
+/* ------------------------------------------------------------- profiling */
+
+/* Per-stage GPU time, measured with CUDA events recorded on the stream each
+ * stage is launched on (a start and a stop event per stage, so host gaps
+ * between stages are not charged to any stage).  Stages: 0 preprocess,
+ * 1 depth sort, 2 scan, 3 emit, 4 pair sort, 5 ranges, 6 blend, and 7 the
+ * whole frame (first stage start to last stage end).  Off by default. */
+enum { TIGAS_N_STAGES = 8 };
+tigas_status tigas_profile_enable(int enable);
+
+/* Accumulated milliseconds and recorded launch sets per stage since the last
+ * reset (ms[TIGAS_N_STAGES], calls[TIGAS_N_STAGES], either may be NULL);
+ * reset=1 clears the accumulators after reading. */
+tigas_status tigas_profile_read(double* ms, uint64_t* calls, int reset);
 
 /* ------------------------------------------------------------------ misc */
 

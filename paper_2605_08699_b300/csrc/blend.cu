@@ -50,7 +50,7 @@ __device__ inline uint8_t to_u8(float x) {
 __global__ void __launch_bounds__(kThreads)
 k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ values, SplatArrays sp,
         const ViewParams* __restrict__ views_g, int V, uint32_t n_entries, float bg_r, float bg_g, float bg_b,
-        unsigned long long* evals) {
+        unsigned long long* counters) {
     __shared__ BlendSmem sm;
     __shared__ uint32_t s_tb[kMaxViews];
     for (int k = threadIdx.x; k < V; k += kThreads) s_tb[k] = views_g[k].tile_base;
@@ -81,7 +81,7 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ values, S
 
     float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
     bool done = !inside;
-    uint32_t n_eval = 0;
+    uint32_t n_eval = 0, n_fetched = 0;
 
     auto stage = [&](int b, int buf) {
         uint32_t idx = start + (uint32_t)b * kBatch + threadIdx.x;
@@ -114,6 +114,7 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ values, S
         if (__syncthreads_count(done) == kThreads) break;
         const uint32_t rem = end - start - (uint32_t)b * kBatch;
         const int cnt = rem < (uint32_t)kBatch ? (int)rem : kBatch;
+        n_fetched += (uint32_t)cnt;
         for (int j = 0; j < cnt; ++j) {
             if (__all_sync(kFull, done)) break;
             const float4 gm = sm.geom[buf][j];
@@ -152,21 +153,23 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ values, S
         }
         if (vp.out_rgba_f32) reinterpret_cast<float4*>(vp.out_rgba_f32)[pix] = make_float4(r, gg, bb, a);
     }
-    if (evals) {
+    if (counters) {
         uint32_t s = n_eval;
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(kFull, s, d);
-        if (lane == 0 && s) atomicAdd(evals, (unsigned long long)s);
+        if (lane == 0 && s) atomicAdd(&counters[0], (unsigned long long)s);
+        if (threadIdx.x == 0 && n_fetched) atomicAdd(&counters[1], (unsigned long long)n_fetched);
     }
 }
 
 }  // namespace
 
 Status launch_blend(const uint2* ranges, const uint32_t* values, const SplatArrays& sp, const ViewParams* views,
-                    int V, uint32_t total_tiles, uint32_t n_entries, const float* bg, unsigned long long* evals,
+                    int V, uint32_t total_tiles, uint32_t n_entries, const float* bg, unsigned long long* counters,
                     cudaStream_t st) {
     if (total_tiles == 0) return {};
-    k_blend<<<total_tiles, kThreads, 0, st>>>(ranges, values, sp, views, V, n_entries, bg[0], bg[1], bg[2], evals);
+    k_blend<<<total_tiles, kThreads, 0, st>>>(ranges, values, sp, views, V, n_entries, bg[0], bg[1], bg[2],
+                                              counters);
     TIGAS_LAUNCHED();
     return {};
 }

@@ -93,6 +93,7 @@ Status do_render(Scene* scene, int V, const tigas_pose* poses, const tigas_intri
     req.V = V;
     req.sort_mode = sort_mode;
     req.want_q = dbg != nullptr;
+    req.want_counters = stats != nullptr;
     std::vector<uint8_t*> host8(V, nullptr);
     std::vector<float*> host32(V, nullptr);
     for (int v = 0; v < V; ++v) {
@@ -123,6 +124,7 @@ Status do_render(Scene* scene, int V, const tigas_pose* poses, const tigas_intri
             TIGAS_CUDA_TRY(cudaMemcpyAsync(host32[v], req.views[v].out_rgba_f32, px * 16, cudaMemcpyDeviceToHost, st));
     }
     TIGAS_CUDA_TRY(cudaStreamSynchronize(st));
+    collect_profile(ctx);
     if (ctx.h_flags[0] & 1u) return {TIGAS_ERR_OVERFLOW, "pair buffer overflow"};
     if (ctx.h_flags[0] & 2u) return {TIGAS_ERR_CUDA, "tile id out of range in sorted keys"};
 
@@ -135,6 +137,10 @@ Status do_render(Scene* scene, int V, const tigas_pose* poses, const tigas_intri
         stats->n_pairs = res.pairs;
         stats->n_tiles = res.total_tiles;
         stats->sort_passes = (uint32_t)res.sort_passes;
+        unsigned long long cnt[2] = {0, 0};
+        if (res.d_counters) TIGAS_CUDA_TRY(cudaMemcpy(cnt, res.d_counters, sizeof(cnt), cudaMemcpyDeviceToHost));
+        stats->blend_evals = cnt[0];
+        stats->blend_fetched = cnt[1];
     }
     if (dbg) {
         const uint32_t n = scene->view.n;
@@ -187,6 +193,16 @@ using namespace tigas;
 TIGAS_API const char* tigas_last_error(void) { return last_error(); }
 TIGAS_API const char* tigas_version(void) { return "tigas-b300 0.1 (sm_103a)"; }
 TIGAS_API uint64_t tigas_kernel_launches(void) { return g_launches.load(); }
+
+TIGAS_API tigas_status tigas_profile_enable(int enable) {
+    g_profile.store(enable != 0);
+    return TIGAS_OK;
+}
+
+TIGAS_API tigas_status tigas_profile_read(double* ms, uint64_t* calls, int reset) {
+    profile_read(ms, calls, reset != 0);
+    return TIGAS_OK;
+}
 
 TIGAS_API tigas_status tigas_scene_load(const tigas_scene_desc* d, tigas_scene** out) {
     set_error("");

@@ -81,6 +81,10 @@ k_emit(const uint32_t* __restrict__ order, const uint32_t* __restrict__ offsets,
     }
 }
 
+// ranges[t] = [first, last + 1) of tile t in the sorted keys; an empty tile
+// gets [s, s) with s the position where its keys would start, so starts are
+// the cumulative list lengths in tile order.  A thread at a key change from
+// tile a to tile b also fills the empty tiles a+1 .. b-1.
 template <typename K>
 __global__ void __launch_bounds__(256)
 k_ranges(const K* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, int shift, uint2* __restrict__ ranges,
@@ -94,8 +98,18 @@ k_ranges(const K* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, int sh
         atomicOr(overflow, 2u);
         return;
     }
-    if (i == 0 || (uint32_t)(keys[i - 1] >> shift) != t) ranges[t].x = (uint32_t)i;
-    if (i == n - 1 || (uint32_t)(keys[i + 1] >> shift) != t) ranges[t].y = (uint32_t)(i + 1);
+    const uint32_t prev = i == 0 ? 0xFFFFFFFFu : (uint32_t)(keys[i - 1] >> shift);
+    if (prev != t) {
+        ranges[t].x = (uint32_t)i;
+        const uint32_t first_gap = i == 0 ? 0u : prev + 1;
+        for (uint32_t e = first_gap; e < t && e < n_tiles; ++e) ranges[e] = make_uint2((uint32_t)i, (uint32_t)i);
+    }
+    if (i == n - 1) {
+        ranges[t].y = (uint32_t)n;
+        for (uint32_t e = t + 1; e < n_tiles; ++e) ranges[e] = make_uint2((uint32_t)n, (uint32_t)n);
+    } else if ((uint32_t)(keys[i + 1] >> shift) != t) {
+        ranges[t].y = (uint32_t)(i + 1);
+    }
 }
 
 }  // namespace

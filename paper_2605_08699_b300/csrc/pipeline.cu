@@ -7,6 +7,60 @@
 namespace tigas {
 
 std::atomic<uint64_t> g_launches{0};
+std::atomic<bool> g_profile{false};
+
+namespace {
+std::mutex g_prof_mu;
+double g_stage_ms[kNumStages + 1] = {};
+uint64_t g_stage_calls[kNumStages + 1] = {};
+}  // namespace
+
+void profile_accumulate(const float* ms, const bool* used, float frame_ms) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (int k = 0; k < kNumStages; ++k)
+        if (used[k]) {
+            g_stage_ms[k] += ms[k];
+            g_stage_calls[k] += 1;
+        }
+    g_stage_ms[kNumStages] += frame_ms;
+    g_stage_calls[kNumStages] += 1;
+}
+
+void profile_read(double* ms, uint64_t* calls, bool reset) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (int k = 0; k <= kNumStages; ++k) {
+        if (ms) ms[k] = g_stage_ms[k];
+        if (calls) calls[k] = g_stage_calls[k];
+        if (reset) {
+            g_stage_ms[k] = 0;
+            g_stage_calls[k] = 0;
+        }
+    }
+}
+
+void collect_profile(RenderContext& ctx) {
+    bool any = false;
+    float ms[kNumStages] = {};
+    int first = -1, last = -1;
+    for (int k = 0; k < kNumStages; ++k) {
+        if (!ctx.ev_used[k]) continue;
+        if (cudaEventElapsedTime(&ms[k], ctx.ev_start[k], ctx.ev_stop[k]) != cudaSuccess) {
+            cudaGetLastError();
+            ms[k] = 0;
+        }
+        if (first < 0) first = k;
+        last = k;
+        any = true;
+    }
+    if (!any) return;
+    float frame = 0;
+    if (cudaEventElapsedTime(&frame, ctx.ev_start[first], ctx.ev_stop[last]) != cudaSuccess) {
+        cudaGetLastError();
+        frame = 0;
+    }
+    profile_accumulate(ms, ctx.ev_used, frame);
+    for (int k = 0; k < kNumStages; ++k) ctx.ev_used[k] = false;
+}
 
 // ------------------------------------------------------------------ scene
 
@@ -82,6 +136,10 @@ Status RenderContext::init() {
     TIGAS_CUDA_TRY(cudaMallocHost(&h_total, sizeof(uint64_t) * 2));
     TIGAS_CUDA_TRY(cudaMallocHost(&h_flags, sizeof(uint32_t) * 2));
     TIGAS_CUDA_TRY(cudaMallocHost(&h_views, sizeof(ViewParams) * kMaxViews));
+    for (int k = 0; k < kNumStages; ++k) {
+        TIGAS_CUDA_TRY(cudaEventCreate(&ev_start[k]));
+        TIGAS_CUDA_TRY(cudaEventCreate(&ev_stop[k]));
+    }
     return {};
 }
 
@@ -96,6 +154,11 @@ void RenderContext::destroy() {
     if (h_flags) cudaFreeHost(h_flags);
     if (h_views) cudaFreeHost(h_views);
     if (stream) cudaStreamDestroy(stream);
+    for (int k = 0; k < kNumStages; ++k) {
+        if (ev_start[k]) cudaEventDestroy(ev_start[k]);
+        if (ev_stop[k]) cudaEventDestroy(ev_stop[k]);
+        ev_start[k] = ev_stop[k] = nullptr;
+    }
     h_total = nullptr; h_flags = nullptr; h_views = nullptr; stream = nullptr;
 }
 
@@ -142,6 +205,14 @@ bool is_device_pointer(const void* p) {
 // -------------------------------------------------------------- pipeline
 
 Status render_frame(Scene* scene, FrameRequest& req, RenderContext& ctx, cudaStream_t st, FrameResult* res) {
+    const bool prof = g_profile.load(std::memory_order_relaxed);
+    for (int k = 0; k < kNumStages; ++k) ctx.ev_used[k] = false;
+    auto mark = [&](Stage sg, bool begin) -> Status {
+        if (!prof) return {};
+        TIGAS_CUDA_TRY(cudaEventRecord(begin ? ctx.ev_start[sg] : ctx.ev_stop[sg], st));
+        if (!begin) ctx.ev_used[sg] = true;
+        return {};
+    };
     const int V = req.V;
     const uint32_t n = scene->view.n;
     const uint64_t E = (uint64_t)V * n;
@@ -168,6 +239,7 @@ Status render_frame(Scene* scene, FrameRequest& req, RenderContext& ctx, cudaStr
     ctx.fixed.reset();
     ViewParams* d_views = ctx.fixed.take<ViewParams>(kMaxViews);
     uint64_t* d_total = ctx.fixed.take<uint64_t>(2);
+    unsigned long long* d_counters = ctx.fixed.take<unsigned long long>(2);
     uint32_t* d_flags = ctx.fixed.take<uint32_t>(2);
     uint32_t* d_visible = ctx.fixed.take<uint32_t>(kMaxViews);
     SplatArrays sp{};
@@ -193,18 +265,25 @@ Status render_frame(Scene* scene, FrameRequest& req, RenderContext& ctx, cudaStr
     TIGAS_CUDA_TRY(cudaMemcpyAsync(d_views, ctx.h_views, sizeof(ViewParams) * V, cudaMemcpyHostToDevice, st));
     TIGAS_CUDA_TRY(cudaMemsetAsync(d_flags, 0, sizeof(uint32_t) * 2, st));
     if (sp.q_dbg) TIGAS_CUDA_TRY(cudaMemsetAsync(sp.q_dbg, 0, E * 4, st));
+    if (req.want_counters) TIGAS_CUDA_TRY(cudaMemsetAsync(d_counters, 0, sizeof(unsigned long long) * 2, st));
 
     // K1
+    TIGAS_TRY(mark(kStPreprocess, true));
     TIGAS_TRY(launch_preprocess(scene->view, d_views, V, sp, d_visible, st));
+    TIGAS_TRY(mark(kStPreprocess, false));
 
     // depth digits first (one key per entry), or nothing here (FULL64)
     if (!full64) {
         int passes = 0;
+        TIGAS_TRY(mark(kStDepthSort, true));
         TIGAS_TRY(radix_sort<uint32_t>(sp.depth_key, nullptr, pk_alt, pv_alt, pk, order, E, nullptr, 0, 32, tmp, st,
                                        &passes));
+        TIGAS_TRY(mark(kStDepthSort, false));
     }
     // K2: pair offsets in emit order
+    TIGAS_TRY(mark(kStScan, true));
     TIGAS_TRY(launch_scan_u32(sp.tiles, order, offsets, E, d_total, tmp, st));
+    TIGAS_TRY(mark(kStScan, false));
     TIGAS_CUDA_TRY(cudaMemcpyAsync(ctx.h_total, d_total, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
     TIGAS_CUDA_TRY(cudaStreamSynchronize(st));
     const uint64_t P = ctx.h_total[0];
@@ -227,19 +306,34 @@ Status render_frame(Scene* scene, FrameRequest& req, RenderContext& ctx, cudaStr
     int passes = 0;
     if (!full64) {
         // K3 in depth order, K4 on the tile digits only
+        TIGAS_TRY(mark(kStEmit, true));
         TIGAS_TRY(launch_emit_u32(order, offsets, sp, d_views, V, n, E, (uint32_t*)keys_a, vals_a, P, d_flags, st));
+        TIGAS_TRY(mark(kStEmit, false));
+        TIGAS_TRY(mark(kStPairSort, true));
         TIGAS_TRY(radix_sort<uint32_t>((uint32_t*)keys_a, vals_a, (uint32_t*)keys_b, vals_b, (uint32_t*)keys_c, vals_c,
                                        P, nullptr, 0, tile_bits, stmp, st, &passes));
+        TIGAS_TRY(mark(kStPairSort, false));
+        TIGAS_TRY(mark(kStRanges, true));
         TIGAS_TRY(launch_ranges<uint32_t>((uint32_t*)keys_c, P, nullptr, 0, ranges, total_tiles, d_flags, st));
+        TIGAS_TRY(mark(kStRanges, false));
     } else {
         // K3 in index order with 64-bit (tile | depth) keys, K4 on all significant bits
+        TIGAS_TRY(mark(kStEmit, true));
         TIGAS_TRY(launch_emit_u64(offsets, sp, d_views, V, n, E, (uint64_t*)keys_a, vals_a, P, d_flags, st));
+        TIGAS_TRY(mark(kStEmit, false));
+        TIGAS_TRY(mark(kStPairSort, true));
         TIGAS_TRY(radix_sort<uint64_t>((uint64_t*)keys_a, vals_a, (uint64_t*)keys_b, vals_b, (uint64_t*)keys_c, vals_c,
                                        P, nullptr, 0, 32 + tile_bits, stmp, st, &passes));
+        TIGAS_TRY(mark(kStPairSort, false));
+        TIGAS_TRY(mark(kStRanges, true));
         TIGAS_TRY(launch_ranges<uint64_t>((uint64_t*)keys_c, P, nullptr, 32, ranges, total_tiles, d_flags, st));
+        TIGAS_TRY(mark(kStRanges, false));
     }
     // K6
-    TIGAS_TRY(launch_blend(ranges, vals_c, sp, d_views, V, total_tiles, (uint32_t)E, scene->view.bg, req.d_evals, st));
+    TIGAS_TRY(mark(kStBlend, true));
+    TIGAS_TRY(launch_blend(ranges, vals_c, sp, d_views, V, total_tiles, (uint32_t)E, scene->view.bg,
+                           req.want_counters ? d_counters : nullptr, st));
+    TIGAS_TRY(mark(kStBlend, false));
     TIGAS_CUDA_TRY(cudaMemcpyAsync(ctx.h_flags, d_flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
 
     if (res) {
@@ -250,6 +344,7 @@ Status render_frame(Scene* scene, FrameRequest& req, RenderContext& ctx, cudaStr
         res->ranges = ranges;
         res->splats = sp;
         res->d_visible = d_visible;
+        res->d_counters = req.want_counters ? d_counters : nullptr;
     }
     return {};
 }

@@ -40,8 +40,18 @@ struct Arena {
 ViewParams make_view(const tigas_pose& pose, const tigas_intrinsics& k, int width, int height,
                      uint32_t tile_base);
 
+enum Stage { kStPreprocess, kStDepthSort, kStScan, kStEmit, kStPairSort, kStRanges, kStBlend, kNumStages };
+
+// Process-wide stage timing (tigas_profile_*).
+extern std::atomic<bool> g_profile;
+void profile_accumulate(const float* ms, const bool* used, float frame_ms);
+void profile_read(double* ms, uint64_t* calls, bool reset);
+
 // Render state of one in-flight frame or launch set: stream, arenas, pinned staging.
 struct RenderContext {
+    cudaEvent_t ev_start[kNumStages] = {};
+    cudaEvent_t ev_stop[kNumStages] = {};
+    bool ev_used[kNumStages] = {};
     cudaStream_t stream = nullptr;     // own stream (used when the caller passes none)
     Arena fixed;                       // per-entry buffers
     Arena pairs;                       // per-pair buffers
@@ -58,7 +68,7 @@ struct FrameRequest {
     int V = 1;
     ViewParams views[kMaxViews];       // out pointers must be device pointers (or null)
     int sort_mode = TIGAS_SORT_DEPTH_FIRST;
-    unsigned long long* d_evals = nullptr;   // optional instrumentation counter
+    bool want_counters = false;          // count blend evaluations / fetched entries
     bool want_q = false;
 };
 
@@ -71,7 +81,11 @@ struct FrameResult {
     const uint2* ranges = nullptr;
     SplatArrays splats{};
     uint32_t* d_visible = nullptr;
+    unsigned long long* d_counters = nullptr;   // [evals, fetched] when requested
 };
+
+// After the stream is synchronised: add this frame's stage times (profiling on).
+void collect_profile(RenderContext& ctx);
 
 // Run the whole hot path for req.V views of one scene on stream st.  Reads P
 // back once (after the scan) to size the pair buffers exactly.  Returns after

@@ -1,0 +1,374 @@
+"""ctypes binding of ``libtigas.so`` (declared in ``include/tigas.h``).
+
+Argument marshalling only: every step of the render path runs in the CUDA
+library.  Arrays may be numpy arrays (host memory) or torch tensors (host or
+device; only their data pointers and streams are used).  There is no CPU
+fallback: if the library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Any, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtigas.so")
+
+OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_AGAIN, ERR_OVERFLOW, ERR_TIMEOUT, ERR_NOT_FOUND = range(8)
+STORAGE_FP32, STORAGE_FP16 = 0, 1
+SORT_DEPTH_FIRST, SORT_FULL64 = 0, 1
+
+#: every symbol include/tigas.h declares
+EXPORTS = ["tigas_scene_load", "tigas_scene_free", "tigas_scene_bytes", "tigas_render", "tigas_render_ex",
+           "tigas_render_batch", "tigas_debug_render", "tigas_sort_pairs_u64", "tigas_server_create",
+           "tigas_server_destroy", "tigas_server_submit", "tigas_server_poll", "tigas_last_error",
+           "tigas_version", "tigas_kernel_launches", "tigas_profile_enable", "tigas_profile_read"]
+
+STAGES = ["preprocess", "depth_sort", "scan", "emit", "pair_sort", "ranges", "blend", "frame"]
+
+
+class TigasError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"tigas status {status}: {message}")
+        self.status = status
+
+
+class Pose(ctypes.Structure):
+    _fields_ = [("azimuth", ctypes.c_double), ("elevation", ctypes.c_double), ("t", ctypes.c_double * 3)]
+
+
+class Intrinsics(ctypes.Structure):
+    _fields_ = [("fx", ctypes.c_double), ("fy", ctypes.c_double), ("cx", ctypes.c_double), ("cy", ctypes.c_double)]
+
+
+class SceneDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("sh_degree", ctypes.c_int), ("storage", ctypes.c_int),
+                ("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
+                ("opacity_logits", ctypes.c_void_p), ("sh", ctypes.c_void_p), ("inputs_on_device", ctypes.c_int),
+                ("background", ctypes.c_float * 3)]
+
+
+class FrameStats(ctypes.Structure):
+    _fields_ = [("n_visible", ctypes.c_uint64), ("n_pairs", ctypes.c_uint64), ("n_tiles", ctypes.c_uint32),
+                ("sort_passes", ctypes.c_uint32), ("blend_evals", ctypes.c_uint64), ("blend_fetched", ctypes.c_uint64)]
+
+
+class DebugFrame(ctypes.Structure):
+    _fields_ = [("visible", ctypes.c_void_p), ("radius", ctypes.c_void_p), ("rect", ctypes.c_void_p),
+                ("depth", ctypes.c_void_p), ("uv", ctypes.c_void_p), ("q", ctypes.c_void_p),
+                ("values", ctypes.c_void_p), ("pair_capacity", ctypes.c_uint64), ("ranges", ctypes.c_void_p),
+                ("rgba_f32", ctypes.c_void_p)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_batch", ctypes.c_int), ("max_inflight", ctypes.c_int),
+                ("batch_window_us", ctypes.c_int)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("client_id", ctypes.c_uint64), ("status", ctypes.c_int),
+                ("width", ctypes.c_int), ("height", ctypes.c_int), ("submit_us", ctypes.c_double),
+                ("admit_us", ctypes.c_double), ("done_us", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libtigas.so (raises when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -m paper_2605_08699_b300.build`")
+    lib = ctypes.CDLL(path)
+    P, i, st = ctypes.c_void_p, ctypes.c_int, ctypes.c_int
+    sig = {
+        "tigas_scene_load": (st, [ctypes.POINTER(SceneDesc), ctypes.POINTER(P)]),
+        "tigas_scene_free": (st, [P]),
+        "tigas_scene_bytes": (st, [P, ctypes.POINTER(ctypes.c_uint64)]),
+        "tigas_render": (st, [P, ctypes.POINTER(Pose), ctypes.POINTER(Intrinsics), i, i, P]),
+        "tigas_render_ex": (st, [P, ctypes.POINTER(Pose), ctypes.POINTER(Intrinsics), i, i, P, P, P, i,
+                                 ctypes.POINTER(FrameStats)]),
+        "tigas_render_batch": (st, [P, i, ctypes.POINTER(Pose), ctypes.POINTER(Intrinsics), P, P, P, P]),
+        "tigas_debug_render": (st, [P, ctypes.POINTER(Pose), ctypes.POINTER(Intrinsics), i, i, i,
+                                    ctypes.POINTER(DebugFrame), ctypes.POINTER(ctypes.c_uint64)]),
+        "tigas_sort_pairs_u64": (st, [P, P, P, P, ctypes.c_uint64, i, i, P]),
+        "tigas_server_create": (st, [ctypes.POINTER(ServerConfig), ctypes.POINTER(P)]),
+        "tigas_server_destroy": (st, [P, i]),
+        "tigas_server_submit": (st, [P, P, ctypes.POINTER(Pose), ctypes.POINTER(Intrinsics), i, i, P,
+                                     ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
+        "tigas_server_poll": (st, [P, ctypes.POINTER(Completion), i, i, ctypes.POINTER(ctypes.c_int)]),
+        "tigas_last_error": (ctypes.c_char_p, []),
+        "tigas_version": (ctypes.c_char_p, []),
+        "tigas_kernel_launches": (ctypes.c_uint64, []),
+        "tigas_profile_enable": (st, [i]),
+        "tigas_profile_read": (st, [P, P, i]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int) -> None:
+    if status != OK:
+        raise TigasError(status, _lib.tigas_last_error().decode())
+
+
+def last_error() -> str:
+    return load_library().tigas_last_error().decode()
+
+
+def version() -> str:
+    return load_library().tigas_version().decode()
+
+
+def kernel_launches() -> int:
+    return int(load_library().tigas_kernel_launches())
+
+
+def profile_enable(on: bool = True) -> None:
+    """Per-stage CUDA-event timing of every later render (tigas_profile_enable)."""
+    _check(load_library().tigas_profile_enable(int(on)))
+
+
+def profile_read(reset: bool = False) -> dict:
+    """Accumulated GPU milliseconds and launch-set counts per stage."""
+    ms = (ctypes.c_double * len(STAGES))()
+    calls = (ctypes.c_uint64 * len(STAGES))()
+    _check(load_library().tigas_profile_read(ctypes.cast(ms, ctypes.c_void_p), ctypes.cast(calls, ctypes.c_void_p),
+                                             int(reset)))
+    return {name: {"ms": ms[k], "calls": int(calls[k])} for k, name in enumerate(STAGES)}
+
+
+# ------------------------------------------------------------ marshalling
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if _is_torch(x):
+        assert x.is_contiguous(), "tensor must be contiguous"
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"], "array must be C-contiguous"
+        return x.ctypes.data
+    if isinstance(x, int):
+        return x
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _on_device(x) -> bool:
+    return _is_torch(x) and x.is_cuda
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)   # torch.cuda.Stream
+
+
+def make_pose(p) -> Pose:
+    if isinstance(p, Pose):
+        return p
+    if hasattr(p, "azimuth"):
+        return Pose(p.azimuth, p.elevation, (ctypes.c_double * 3)(*p.t))
+    az, el, t = p
+    return Pose(az, el, (ctypes.c_double * 3)(*t))
+
+
+def make_intrinsics(k) -> Intrinsics:
+    if isinstance(k, Intrinsics):
+        return k
+    if hasattr(k, "fx"):
+        return Intrinsics(k.fx, k.fy, k.cx, k.cy)
+    return Intrinsics(*k)
+
+
+# ----------------------------------------------------------------- scenes
+
+
+class SceneHandle:
+    """A resident scene (``tigas_scene*``); free() drops the caller's reference."""
+
+    def __init__(self, handle: int, n: int, storage: int):
+        self.handle = handle
+        self.n = n
+        self.storage = storage
+
+    @property
+    def bytes(self) -> int:
+        out = ctypes.c_uint64()
+        _check(load_library().tigas_scene_bytes(self.handle, ctypes.byref(out)))
+        return int(out.value)
+
+    def free(self) -> None:
+        if self.handle:
+            _check(load_library().tigas_scene_free(self.handle))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+
+def scene_load(means, log_scales, quats, opacity_logits, sh, sh_degree: int = 3, storage: int = STORAGE_FP32,
+               background=(0.0, 0.0, 0.0)) -> SceneHandle:
+    """Upload raw attributes (float32, see tigas_scene_desc) and activate them."""
+    arrs = [means, log_scales, quats, opacity_logits, sh]
+    dev = [_on_device(a) for a in arrs]
+    if any(dev) and not all(dev):
+        raise ValueError("attribute arrays must be all host or all device")
+    if not dev[0]:
+        arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in arrs]
+    n = int(arrs[0].shape[0])
+    d = SceneDesc(n, sh_degree, storage, *[_ptr(a) for a in arrs], int(dev[0]), (ctypes.c_float * 3)(*background))
+    h = ctypes.c_void_p()
+    _check(load_library().tigas_scene_load(ctypes.byref(d), ctypes.byref(h)))
+    return SceneHandle(h.value, n, storage)
+
+
+def scene_from(s, storage: int = STORAGE_FP32, background=(0.0, 0.0, 0.0)) -> SceneHandle:
+    """Load an object with means/log_scales/quats/opacity_logits/sh/sh_degree attributes."""
+    return scene_load(s.means, s.log_scales, s.quats, s.opacity_logits, s.sh, s.sh_degree, storage, background)
+
+
+# ---------------------------------------------------------------- render
+
+
+def render(scene: SceneHandle, pose, intr, width: int, height: int, out=None):
+    """tigas_render.  Returns ``out`` (a new host [H, W, 4] uint8 array if None)."""
+    if out is None:
+        out = np.empty((height, width, 4), np.uint8)
+    _check(load_library().tigas_render(scene.handle, ctypes.byref(make_pose(pose)),
+                                       ctypes.byref(make_intrinsics(intr)), width, height, _ptr(out)))
+    return out
+
+
+def render_ex(scene: SceneHandle, pose, intr, width: int, height: int, out_rgba8=None, out_rgba_f32=None,
+              stream=None, sort_mode: int = SORT_DEPTH_FIRST) -> dict:
+    """tigas_render_ex; returns the frame statistics."""
+    stats = FrameStats()
+    _check(load_library().tigas_render_ex(scene.handle, ctypes.byref(make_pose(pose)),
+                                          ctypes.byref(make_intrinsics(intr)), width, height, _ptr(out_rgba8),
+                                          _ptr(out_rgba_f32), _stream(stream), sort_mode, ctypes.byref(stats)))
+    return {"n_visible": stats.n_visible, "n_pairs": stats.n_pairs, "n_tiles": stats.n_tiles,
+            "sort_passes": stats.sort_passes, "blend_evals": stats.blend_evals, "blend_fetched": stats.blend_fetched}
+
+
+def render_batch(scene: SceneHandle, poses: Sequence, intrs: Sequence, widths: Sequence[int],
+                 heights: Sequence[int], outs: Sequence, stream=None) -> None:
+    """tigas_render_batch: all views in one fused launch set."""
+    V = len(poses)
+    P = (Pose * V)(*[make_pose(p) for p in poses])
+    K = (Intrinsics * V)(*[make_intrinsics(k) for k in intrs])
+    W = (ctypes.c_int * V)(*widths)
+    H = (ctypes.c_int * V)(*heights)
+    O = (ctypes.c_void_p * V)(*[_ptr(o) for o in outs])
+    _check(load_library().tigas_render_batch(scene.handle, V, P, K, ctypes.cast(W, ctypes.c_void_p),
+                                             ctypes.cast(H, ctypes.c_void_p), ctypes.cast(O, ctypes.c_void_p),
+                                             _stream(stream)))
+
+
+def debug_render(scene: SceneHandle, pose, intr, width: int, height: int, sort_mode: int = SORT_DEPTH_FIRST,
+                 pair_capacity: int | None = None) -> dict:
+    """tigas_debug_render: per-Gaussian decisions, sorted tile lists, ranges, float frame."""
+    n = scene.n
+    tx, ty = (width + 15) // 16, (height + 15) // 16
+    cap = pair_capacity if pair_capacity is not None else max(1, 64 * n)
+    out = {
+        "visible": np.zeros(n, np.uint8), "radius": np.zeros(n, np.int32), "rect": np.zeros((n, 4), np.int32),
+        "depth": np.zeros(n, np.float32), "uv": np.zeros((n, 2), np.float32), "q": np.zeros(n, np.float32),
+        "values": np.zeros(cap, np.uint32), "ranges": np.zeros((tx * ty, 2), np.uint32),
+        "rgba_f32": np.zeros((height, width, 4), np.float32),
+    }
+    d = DebugFrame(*[_ptr(out[k]) for k in ["visible", "radius", "rect", "depth", "uv", "q", "values"]], cap,
+                   _ptr(out["ranges"]), _ptr(out["rgba_f32"]))
+    pairs = ctypes.c_uint64()
+    _check(load_library().tigas_debug_render(scene.handle, ctypes.byref(make_pose(pose)),
+                                             ctypes.byref(make_intrinsics(intr)), width, height, sort_mode,
+                                             ctypes.byref(d), ctypes.byref(pairs)))
+    P = int(pairs.value)
+    if P > cap:
+        return debug_render(scene, pose, intr, width, height, sort_mode, P)
+    out["pairs"] = P
+    out["values"] = out["values"][:P]
+    return out
+
+
+def sort_pairs_u64(keys_in, values_in, keys_out, values_out, n: int, begin_bit: int = 0, end_bit: int = 64,
+                   stream=None) -> None:
+    """tigas_sort_pairs_u64 on device buffers (torch tensors or raw pointers)."""
+    _check(load_library().tigas_sort_pairs_u64(_ptr(keys_in), _ptr(values_in), _ptr(keys_out), _ptr(values_out),
+                                               n, begin_bit, end_bit, _stream(stream)))
+
+
+# ---------------------------------------------------------------- server
+
+
+@dataclass
+class ServerCompletion:
+    ticket: int
+    client_id: int
+    status: int
+    width: int
+    height: int
+    submit_us: float
+    admit_us: float
+    done_us: float
+
+
+class Server:
+    """tigas_server: continuous batching of per-client render requests."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, max_batch: int = 0, max_inflight: int = 0,
+                 batch_window_us: int = 0):
+        cfg = ServerConfig(hbm_budget_bytes, max_batch, max_inflight, batch_window_us)
+        h = ctypes.c_void_p()
+        _check(load_library().tigas_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h.value
+        self._keep: dict[int, Any] = {}
+
+    def submit(self, scene: SceneHandle, pose, intr, width: int, height: int, out, client_id: int) -> int:
+        t = ctypes.c_uint64()
+        _check(_lib.tigas_server_submit(self.handle, scene.handle, ctypes.byref(make_pose(pose)),
+                                        ctypes.byref(make_intrinsics(intr)), width, height, _ptr(out), client_id,
+                                        ctypes.byref(t)))
+        self._keep[t.value] = out
+        return int(t.value)
+
+    def poll(self, max_n: int = 256, timeout_us: int = 0) -> list[ServerCompletion]:
+        buf = (Completion * max_n)()
+        k = ctypes.c_int()
+        _check(_lib.tigas_server_poll(self.handle, buf, max_n, timeout_us, ctypes.byref(k)))
+        res = []
+        for c in buf[:k.value]:
+            self._keep.pop(c.ticket, None)
+            res.append(ServerCompletion(c.ticket, c.client_id, c.status, c.width, c.height, c.submit_us,
+                                        c.admit_us, c.done_us))
+        return res
+
+    def destroy(self, cancel: bool = False) -> None:
+        if self.handle:
+            _check(_lib.tigas_server_destroy(self.handle, int(cancel)))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()

@@ -1,0 +1,90 @@
+"""The C-ABI library loads and exports every declared symbol (no GPU needed),
+and argument validation rejects bad input before any CUDA work."""
+import ctypes
+import math
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import paper_2605_08699_b300 as tg
+from paper_2605_08699_b300 import tigas as tb
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "tigas.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(tb.LIB_PATH):
+        from paper_2605_08699_b300 import build
+        build.build()
+    return tg.load_library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tigas_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declarations_match_binding():
+    assert declared_functions() == sorted(tb.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.check_output(["nm", "-D", "--defined-only", tb.LIB_PATH], text=True)
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    for name in declared_functions():
+        assert name in exported, name
+        assert getattr(lib, name) is not None
+    # nothing but the C ABI is exported
+    assert {e for e in exported if not e.startswith("tigas_")} <= {"_init", "_fini"}
+
+
+def test_version_and_counters(lib):
+    assert "sm_103a" in tg.version()
+    assert tg.kernel_launches() >= 0
+
+
+def _status(name, *args):
+    return getattr(tg.load_library(), name)(*args)
+
+
+def test_invalid_arguments_rejected_without_gpu(lib):
+    pose = tb.Pose(0.0, 0.0, (ctypes.c_double * 3)(0, 0, -3))
+    k = tb.Intrinsics(100, 100, 50, 50)
+    buf = np.zeros(16, np.uint8)
+    assert _status("tigas_render", None, ctypes.byref(pose), ctypes.byref(k), 2, 2, buf.ctypes.data) == tb.ERR_INVALID
+    assert "scene" in tg.last_error()
+    assert _status("tigas_scene_load", None, None) == tb.ERR_INVALID
+    d = tb.SceneDesc(0, 3, 0, None, None, None, None, None, 0, (ctypes.c_float * 3)(0, 0, 0))
+    h = ctypes.c_void_p()
+    assert _status("tigas_scene_load", ctypes.byref(d), ctypes.byref(h)) == tb.ERR_INVALID
+    d.n, d.sh_degree = 10, 4
+    assert _status("tigas_scene_load", ctypes.byref(d), ctypes.byref(h)) == tb.ERR_INVALID
+    assert "sh_degree" in tg.last_error()
+    d.sh_degree, d.storage = 3, 7
+    assert _status("tigas_scene_load", ctypes.byref(d), ctypes.byref(h)) == tb.ERR_INVALID
+    assert _status("tigas_scene_free", None) == tb.ERR_INVALID
+    assert _status("tigas_sort_pairs_u64", None, None, None, None, 5, 0, 64, None) == tb.ERR_INVALID
+    assert _status("tigas_sort_pairs_u64", None, None, None, None, 0, 10, 5, None) == tb.ERR_INVALID
+    cfg = tb.ServerConfig(0, 65, 1, 0)
+    s = ctypes.c_void_p()
+    assert _status("tigas_server_create", ctypes.byref(cfg), ctypes.byref(s)) == tb.ERR_INVALID
+    n = ctypes.c_int()
+    assert _status("tigas_server_poll", None, None, 0, 0, ctypes.byref(n)) == tb.ERR_INVALID
+
+
+def test_pose_validation_messages(lib):
+    from paper_2605_08699_b300.tigas import _check, TigasError
+    k = tb.Intrinsics(100, 100, 50, 50)
+    fake_scene = None
+    for pose, w, h in [(tb.Pose(math.nan, 0, (ctypes.c_double * 3)(0, 0, 0)), 4, 4),
+                       (tb.Pose(0, 0, (ctypes.c_double * 3)(0, math.inf, 0)), 4, 4)]:
+        st = _status("tigas_render_ex", fake_scene, ctypes.byref(pose), ctypes.byref(k), w, h, None, None, None, 0, None)
+        assert st == tb.ERR_INVALID
+    with pytest.raises(TigasError):
+        _check(tb.ERR_INVALID)
