@@ -1,0 +1,460 @@
+"""Benchmark: 1080p frames/s and p50/p99 latency of the forward 3DGS renderer
+on a 3M-Gaussian scene, served FP16 (batched launch sets) vs plain FP32.
+
+One step = one fused launch set of V 1080p views (V independent 6DoF
+trajectories) of the resident 3M-Gaussian FP16 scene through
+``tigas_render_batch``: preprocess, depth sort, scan, emit, pair sort, tile
+ranges and blend, outputs in device memory.  ``value`` = frames/s over the
+timed steps (CUDA events on the launching stream), ``e2e`` = the same call
+with pinned host output buffers (device->host copies inside the timed region).
+Also reported: the plain FP32 single-request path, the request server
+(closed-loop clients), per-stage CUDA-event times with the roofline of the
+dominant stage, GPU clocks, and the FP64 CPU oracle timed on the host cores.
+
+``--impl reference`` times the FP64 oracle (the only reference for this
+method) on the same workload, one bounded sample per step.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tigas|reference]
+Under torchrun each rank renders its own replica (weak scaling, no collective
+on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "1080p frames/s & p50/p99 latency, 3M Gaussians: served FP16 vs plain FP32"
+WORKLOAD = "3M Gaussians (64 anisotropic blobs, SH degree 3), 1920x1080, 6DoF random-walk trajectories"
+N_SM = 148
+FP32_LANES_PER_SM = 128
+
+
+def _peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        d["source"] = "measured"
+        return d
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0, "source": "fallback"}
+
+
+# ------------------------------------------------------------------ clocks
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "sm_min_mhz": min(sm),
+                "power_w_max": max(power), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------- CPU baseline
+
+
+def oracle_frame_sample(scene, pose, width: int, height: int, n_tiles_sample: int, seed: int = 0) -> dict:
+    """Time the FP64 oracle on one frame: full preprocess plus a sample of whole
+    16x16 tiles, scaled to the frame's tile count."""
+    import oracle
+    K = synth.default_intrinsics(width, height)
+    t0 = time.perf_counter()
+    pr = oracle.preprocess(scene, pose, K, width, height)
+    t_pre = time.perf_counter() - t0
+    TX, TY = pr.tiles_xy
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(TX * TY, size=min(n_tiles_sample, TX * TY), replace=False)
+    pix = []
+    for t in pick:
+        tx, ty = int(t % TX), int(t // TX)
+        for j in range(16):
+            for i in range(16):
+                x, y = tx * 16 + i, ty * 16 + j
+                if x < width and y < height:
+                    pix.append((x, y))
+    t0 = time.perf_counter()
+    oracle.render(pr, pixels=np.array(pix, np.int32))
+    t_tiles = time.perf_counter() - t0
+    frame_s = t_pre + t_tiles * (TX * TY) / len(pick)
+    return {"frame_s": frame_s, "preprocess_s": t_pre, "tiles_s": t_tiles, "tiles": len(pick),
+            "total_tiles": TX * TY, "wall_s": t_pre + t_tiles}
+
+
+def cpu_baseline(scene, poses, width, height, budget_s: float = 15.0) -> dict:
+    t_start = time.perf_counter()
+    frames = []
+    k = 0
+    while time.perf_counter() - t_start < budget_s and k < len(poses):
+        frames.append(oracle_frame_sample(scene, poses[k], width, height, 64, seed=k))
+        k += 1
+    est = [f["frame_s"] for f in frames]
+    return {"value": 1.0 / statistics.mean(est), "unit": "frames/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"{len(frames)} poses; per pose: FP64 preprocess of all {scene.n} Gaussians plus "
+                       f"64 whole 16x16 tiles composited, frame time scaled by {frames[0]['total_tiles']} "
+                       f"tiles / 64; {time.perf_counter() - t_start:.1f} s of CPU work")}
+
+
+# ---------------------------------------------------------------- roofline
+
+
+def roofline(stage_ms: dict, per_step: dict, peaks: dict, clocks: dict, steps: int) -> tuple[dict, dict]:
+    """Achieved rate of every stage and the roofline entry of the dominant one.
+    Algorithmic work per launch set (see the design notes):
+      preprocess  12 B per (Gaussian, view) + (A - 12) B per Gaussian + 52 B per kept entry
+      depth_sort  4 passes x 16 B per entry
+      scan        8 B per entry
+      emit        16 B per kept entry + 8 B per pair
+      pair_sort   passes x 16 B per pair
+      ranges      4 B per pair + 8 B per tile
+      blend       FP32: 14 flops per list entry evaluated (power, alpha, transmittance)
+                  + 8 flops per contribution; counted as 15 per evaluation"""
+    hbm = peaks["hbm_gbs"]
+    mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
+    fp32_peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    w = per_step
+    bytes_per = {
+        "preprocess": w["entries"] * 12 + w["gaussians"] * (w["attr_bytes"] - 12) + w["kept"] * 52,
+        "depth_sort": w["entries"] * 4 * 16,
+        "scan": w["entries"] * 8,
+        "emit": w["kept"] * 16 + w["pairs"] * 8,
+        "pair_sort": w["pairs"] * w["sort_passes"] * 16,
+        "ranges": w["pairs"] * 4 + w["tiles"] * 8,
+    }
+    stages = {}
+    for name, st in stage_ms.items():
+        if name == "frame" or st["calls"] == 0:
+            continue
+        ms = st["ms"] / st["calls"]
+        if name == "blend":
+            fl = w["evals"] * 15.0
+            ach = fl / (ms * 1e-3) / 1e12
+            stages[name] = {"ms": ms, "bound": "alu", "achieved": ach, "peak": fp32_peak_tflops,
+                            "unit": "TFLOP/s", "frac": ach / fp32_peak_tflops, "work": fl}
+        else:
+            b = bytes_per.get(name, 0)
+            ach = b / (ms * 1e-3) / 1e9
+            stages[name] = {"ms": ms, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                            "frac": ach / hbm, "work": b}
+    dom = max(stages, key=lambda k: stages[k]["ms"])
+    d = stages[dom]
+    roof = {"kernel": dom, "bound": d["bound"], "achieved": round(d["achieved"], 3), "peak": d["peak"],
+            "unit": d["unit"], "frac": round(d["frac"], 4), "traffic": None,
+            "peak_source": f"{peaks['source']} ({'hbm_gbs' if d['bound'] == 'hbm' else 'SMs x 128 FP32 lanes x 2 x median SM clock'})",
+            "share_of_frame": round(d["ms"] / max(1e-9, sum(s['ms'] for s in stages.values())), 4)}
+    return roof, {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}
+                  for k, v in stages.items()}
+
+
+# ---------------------------------------------------------------- GPU arm
+
+
+def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
+    import torch
+    import paper_2605_08699_b300 as tg
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    tg.load_library()
+    W, H, V = args.width, args.height, args.batch
+    scene = synth.config_scene(3, n=args.gaussians)
+    K = synth.default_intrinsics(W, H)
+    trajs = [synth.config_trajectory(3, i + 1000 * rank) for i in range(V)]
+    h16 = tg.scene_from(scene, storage=tg.STORAGE_FP16)
+    h32 = tg.scene_from(scene, storage=tg.STORAGE_FP32)
+    stream = torch.cuda.Stream(device=dev)
+    outs = [torch.empty((H, W, 4), dtype=torch.uint8, device=dev) for _ in range(V)]
+
+    def step(s, handle=h16, o=outs):
+        poses = [trajs[v][(s * 7 + v) % len(trajs[v])] for v in range(V)]
+        tg.render_batch(handle, poses, [K] * V, [W] * V, [H] * V, o, stream=stream)
+
+    for s in range(args.warmup):
+        step(s)
+    torch.cuda.synchronize()
+
+    # per-step workload (untimed): pairs, kept entries, blend evaluations
+    agg = {"pairs": 0, "kept": 0, "evals": 0, "fetched": 0, "sort_passes": 0}
+    for v in range(V):
+        stt = tg.render_ex(h16, trajs[v][(args.warmup * 7 + v) % 300], K, W, H, out_rgba8=outs[v])
+        for k in ("pairs", "evals", "fetched"):
+            agg[k] += stt["n_" + k] if k == "pairs" else stt["blend_" + k]
+        agg["kept"] += stt["n_visible"]
+        agg["sort_passes"] = stt["sort_passes"]
+    TX, TY = (W + 15) // 16, (H + 15) // 16
+    bits = max(1, math.ceil(math.log2(V * TX * TY)))
+    agg["sort_passes"] = (bits + 7) // 8        # the batch sorts global tile ids of all V views
+    per_step = {**agg, "entries": V * scene.n, "gaussians": scene.n, "attr_bytes": 124, "tiles": V * TX * TY}
+
+    # ---- timed region: device outputs, CUDA events on the launching stream
+    tg.profile_read(reset=True)
+    tg.profile_enable(True)
+    clk = ClockSampler(local_rank)
+    clk.start()
+    time.sleep(0.3)
+    launches0 = tg.kernel_launches()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ms_host = []
+    e0.record(stream)
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        step(args.warmup + s)
+        step_ms_host.append((time.perf_counter() - t0) * 1e3)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    elapsed_ms = e0.elapsed_time(e1)
+    launches = tg.kernel_launches() - launches0
+    clocks = clk.stop()
+    tg.profile_enable(False)
+    stage_ms = tg.profile_read(reset=True)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    frames = V * args.steps * world
+    value = frames / (elapsed_ms * 1e-3)
+
+    # ---- end to end: pinned host outputs, copies inside the timed region
+    houts = [torch.empty((H, W, 4), dtype=torch.uint8).pin_memory() for _ in range(V)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        step(args.warmup + s, o=houts)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": V * args.steps / e2e_s, "unit": "frames/s",
+           "h2d_bytes_per_step": V * (40 + 32 + 8 + 8), "d2h_bytes_per_step": V * W * H * 4}
+
+    # ---- plain FP32 single-request path, one frame at a time
+    lat32 = []
+    n32 = args.plain_frames
+    out1 = outs[0]
+    for i in range(3):
+        tg.render_ex(h32, trajs[0][i], K, W, H, out_rgba8=out1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(n32):
+        ta = time.perf_counter()
+        tg.render_ex(h32, trajs[i % V][(i * 7) % 300], K, W, H, out_rgba8=out1)
+        lat32.append((time.perf_counter() - ta) * 1e3)
+    plain_s = time.perf_counter() - t0
+    plain = {"frames_per_s": n32 / plain_s, "latency_ms_p50": float(np.percentile(lat32, 50)),
+             "latency_ms_p99": float(np.percentile(lat32, 99)), "frames": n32, "storage": "fp32",
+             "path": "tigas_render_ex, one request at a time"}
+
+    # ---- served FP16: request server, closed-loop clients
+    serving = None
+    if not args.no_serving:
+        serving = run_serving(tg, torch, dev, h16, K, W, H, trajs, args)
+
+    res = {"value": value, "elapsed_ms": elapsed_ms, "frames": frames, "per_step": per_step, "stage_ms": stage_ms,
+           "clocks": clocks, "launches": launches, "e2e": e2e, "plain_fp32": plain, "serving": serving,
+           "step_ms_host": step_ms_host, "scene": scene}
+    h16.free()
+    h32.free()
+    return res
+
+
+def run_serving(tg, torch, dev, h16, K, W, H, trajs, args) -> dict:
+    """Closed loop: C clients each keep one 1080p request in flight; the server
+    batches whatever is queued into fused launch sets as slots free up."""
+    C = args.clients
+    bufs = [torch.empty((H, W, 4), dtype=torch.uint8, device=dev) for _ in range(C)]
+    lat, n_done = [], 0
+    with tg.Server(max_batch=args.serve_batch, max_inflight=args.serve_inflight) as srv:
+        nxt = [0] * C
+        for c in range(C):
+            srv.submit(h16, trajs[c % len(trajs)][0], K, W, H, bufs[c], client_id=c)
+        t_end = time.perf_counter() + args.serve_seconds
+        t0 = time.perf_counter()
+        warm = 2 * C
+        while True:
+            for comp in srv.poll(256, timeout_us=200_000):
+                c = comp.client_id
+                if comp.status == 0:
+                    n_done += 1
+                    if n_done > warm:
+                        lat.append((comp.done_us - comp.submit_us) * 1e-3)
+                    if n_done == warm:
+                        t0 = time.perf_counter()
+                if time.perf_counter() < t_end:
+                    nxt[c] += 1
+                    srv.submit(h16, trajs[c % len(trajs)][(nxt[c] * 3) % 300], K, W, H, bufs[c], client_id=c)
+            if time.perf_counter() >= t_end:
+                break
+        t1 = time.perf_counter()
+        # drain
+        while True:
+            got = srv.poll(256, timeout_us=500_000)
+            if not got:
+                break
+    measured = len(lat)
+    return {"frames_per_s": measured / max(1e-9, t1 - t0), "latency_ms_p50": float(np.percentile(lat, 50)),
+            "latency_ms_p99": float(np.percentile(lat, 99)), "frames": measured, "clients": C,
+            "max_batch": args.serve_batch, "slots": args.serve_inflight, "storage": "fp16",
+            "latency": "submit to frame complete in the client's buffer"}
+
+
+# --------------------------------------------------------------- reference
+
+
+def run_reference(args) -> dict:
+    scene = synth.config_scene(3, n=args.gaussians)
+    poses = synth.config_trajectory(3, 0)
+    W, H = args.width, args.height
+    times = []
+    for s in range(args.warmup + args.steps):
+        r = oracle_frame_sample(scene, poses[(s * 7) % 300], W, H, 64, seed=s)
+        if s >= args.warmup:
+            times.append(r["frame_s"])
+    value = 1.0 / statistics.mean(times)
+    line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(times) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "gaussians": scene.n, "width": W, "height": H, "storage": "fp32 inputs",
+                       "parallelism": "host cores (OpenMP)"},
+            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "per step: FP64 preprocess of every Gaussian plus 64 whole 16x16 tiles "
+                                       "composited; frame time scaled by total tiles / 64"},
+            "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    return line
+
+
+# -------------------------------------------------------------------- main
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["tigas", "reference"], default="tigas")
+    ap.add_argument("--batch", type=int, default=8, help="views per fused launch set")
+    ap.add_argument("--gaussians", type=int, default=3_000_000)
+    ap.add_argument("--width", type=int, default=1920)
+    ap.add_argument("--height", type=int, default=1080)
+    ap.add_argument("--clients", type=int, default=16)
+    ap.add_argument("--serve-batch", type=int, default=8)
+    ap.add_argument("--serve-inflight", type=int, default=2)
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--plain-frames", type=int, default=64, help="frames of the plain FP32 single-request path")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    args.warmup = max(3, args.warmup)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        print(json.dumps(run_reference(args)), flush=True)
+        return 0
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    r = run_gpu(args, rank, world, local_rank)
+    if rank == 0:
+        peaks = _peaks()
+        roof, stages = roofline(r["stage_ms"], r["per_step"], peaks, r["clocks"], args.steps)
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            poses = synth.config_trajectory(3, 0)
+            cpu = cpu_baseline(r["scene"], [poses[(k * 37) % 300] for k in range(50)], args.width, args.height,
+                               args.cpu_seconds)
+        steps_ms = r["step_ms_host"]
+        line = {
+            "metric": METRIC, "value": round(r["value"], 2), "unit": "frames/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(r["elapsed_ms"] / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "gaussians": args.gaussians, "width": args.width, "height": args.height,
+                       "views_per_step": args.batch, "storage": "fp16 (positions fp32)", "sh_degree": 3,
+                       "path": "tigas_render_batch (fused launch set per step)",
+                       "l2": "inputs larger than L2: 384 MB resident scene, >1 GB of pair buffers per step",
+                       "parallelism": f"replicas x{world}"},
+            "latency_ms": {"p50_step": round(float(np.percentile(steps_ms, 50)), 3),
+                           "p99_step": round(float(np.percentile(steps_ms, 99)), 3),
+                           "note": "host time of one synchronous launch set of views_per_step frames"},
+            "served_fp16": r["serving"], "plain_fp32": r["plain_fp32"],
+            "roofline": roof, "stages": stages, "per_step": {k: int(v) for k, v in r["per_step"].items()},
+            "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": int(r["launches"]), "clocks": r["clocks"],
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
