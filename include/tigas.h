@@ -181,6 +181,30 @@ tigas_status tigas_sort_pairs_u64(const uint64_t* keys_in, const uint32_t* value
                                   uint32_t* values_out, uint64_t n, int begin_bit, int end_bit,
                                   void* cuda_stream);
 
+/* The same sort for callers that cannot let this library allocate device
+ * memory (applications that manage every byte of device memory through their
+ * own pools or budgets, or threads that must not take the device-wide
+ * synchronisation cudaMalloc/cudaFree can cause).  The paper has no
+ * counterpart; this is a library convenience.
+ *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ *     Its scratch (ping-pong buffers and digit tables, about 13 MB) is one
+ *     fixed device array that every GPU loading this library holds until the
+ *     process exits.
+ *   - n is limited to 1048576 (2^20) pairs; larger n returns
+ *     TIGAS_ERR_INVALID with a message naming the limit.
+ *   - The first call on a device looks up that device's scratch address
+ *     (cudaGetSymbolAddress) with the device current; make that first call
+ *     before any stream capture.
+ *   - Asynchronous: returns once the work is queued on cuda_stream (NULL: the
+ *     legacy default stream); outputs are ready when the stream gets there.
+ *   - All calls on a device share the scratch and it keeps the last call's
+ *     contents: calls whose work overlaps on the GPU (different streams or
+ *     host threads without ordering between them) race and corrupt each other.
+ * Arguments and result as tigas_sort_pairs_u64. */
+tigas_status tigas_sort_pairs_u64_noalloc(const uint64_t* keys_in, const uint32_t* values_in, uint64_t* keys_out,
+                                          uint32_t* values_out, uint64_t n, int begin_bit, int end_bit,
+                                          void* cuda_stream);
+
 /* ---------------------------------------------------------------- serving */
 
 typedef struct {

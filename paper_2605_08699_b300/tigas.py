@@ -25,7 +25,8 @@ SORT_DEPTH_FIRST, SORT_FULL64 = 0, 1
 EXPORTS = ["tigas_scene_load", "tigas_scene_free", "tigas_scene_bytes", "tigas_render", "tigas_render_ex",
            "tigas_render_batch", "tigas_debug_render", "tigas_sort_pairs_u64", "tigas_server_create",
            "tigas_server_destroy", "tigas_server_submit", "tigas_server_poll", "tigas_last_error",
-           "tigas_version", "tigas_kernel_launches", "tigas_profile_enable", "tigas_profile_read"]
+           "tigas_version", "tigas_kernel_launches", "tigas_profile_enable", "tigas_profile_read",
+           "tigas_sort_pairs_u64_noalloc"]
 
 STAGES = ["preprocess", "depth_sort", "scan", "emit", "pair_sort", "ranges", "blend", "frame"]
 
@@ -97,6 +98,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "tigas_debug_render": (st, [P, ctypes.POINTER(Pose), ctypes.POINTER(Intrinsics), i, i, i,
                                     ctypes.POINTER(DebugFrame), ctypes.POINTER(ctypes.c_uint64)]),
         "tigas_sort_pairs_u64": (st, [P, P, P, P, ctypes.c_uint64, i, i, P]),
+        "tigas_sort_pairs_u64_noalloc": (st, [P, P, P, P, ctypes.c_uint64, i, i, P]),
         "tigas_server_create": (st, [ctypes.POINTER(ServerConfig), ctypes.POINTER(P)]),
         "tigas_server_destroy": (st, [P, i]),
         "tigas_server_submit": (st, [P, P, ctypes.POINTER(Pose), ctypes.POINTER(Intrinsics), i, i, P,
