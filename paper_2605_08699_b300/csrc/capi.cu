@@ -127,6 +127,7 @@ Status do_render(Scene* scene, int V, const tigas_pose* poses, const tigas_intri
     collect_profile(ctx);
     if (ctx.h_flags[0] & 1u) return {TIGAS_ERR_OVERFLOW, "pair buffer overflow"};
     if (ctx.h_flags[0] & 2u) return {TIGAS_ERR_CUDA, "tile id out of range in sorted keys"};
+    if (ctx.h_flags[0] & 16u) return {TIGAS_ERR_TIMEOUT, "radix sort look-back wait ran out"};
 
     if (stats) {
         uint32_t vis[kMaxViews];
@@ -343,16 +344,21 @@ TIGAS_API tigas_status tigas_sort_pairs_u64(const uint64_t* keys_in, const uint3
     if (!g.ctx) return fail(err);
     cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : g.ctx->stream;
     const size_t words = radix_tmp_words(n);
-    Status s = g.ctx->pairs.reserve(n * 12 + words * 4 + 4096);
+    Status s = g.ctx->pairs.reserve(n * 12 + words * 4 + 8192);
     if (!s.ok()) return fail(s);
     g.ctx->pairs.reset();
     uint64_t* ka = g.ctx->pairs.take<uint64_t>(n);
     uint32_t* va = g.ctx->pairs.take<uint32_t>(n);
     uint32_t* tmp = g.ctx->pairs.take<uint32_t>(words);
-    s = radix_sort<uint64_t>(keys_in, values_in, ka, va, keys_out, values_out, n, nullptr, begin_bit, end_bit, tmp, st,
-                             nullptr);
-    if (!s.ok()) return fail(s);
-    cudaError_t e = cudaStreamSynchronize(st);
+    uint32_t* d_flags = g.ctx->pairs.take<uint32_t>(1);
+    cudaError_t e = cudaMemsetAsync(d_flags, 0, 4, st);
     if (e != cudaSuccess) return fail(TIGAS_ERR_CUDA, cudaGetErrorString(e));
+    s = radix_sort<uint64_t>(keys_in, values_in, ka, va, keys_out, values_out, n, nullptr, begin_bit, end_bit, tmp, st,
+                             nullptr, d_flags);
+    if (!s.ok()) return fail(s);
+    e = cudaMemcpyAsync(g.ctx->h_flags, d_flags, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(TIGAS_ERR_CUDA, cudaGetErrorString(e));
+    if (g.ctx->h_flags[0] & 16u) return fail(TIGAS_ERR_TIMEOUT, "radix sort look-back wait ran out");
     return TIGAS_OK;
 }

@@ -38,15 +38,19 @@ Status launch_emit_u64(const uint32_t* offsets, const SplatArrays& sp, const Vie
 // The element count is min(*d_n, n_cap) when d_n is given, else n_cap.
 // values_in == nullptr means values 0..n-1.  keys_alt/values_alt are the
 // ping-pong buffers; the sorted result lands in (keys_out, values_out).
-// tmp: radix_tmp_words(n_cap) words.
+// tmp: radix_tmp_words(n_cap) words.  flags (optional device word): bit 16 is
+// set when a look-back wait ran out (the result is then not to be trusted).
+// pre_hist (optional, device [passes][256]): the digit histograms of every
+// pass, already counted by the producer of the keys (skips one read).
 size_t radix_tmp_words(uint64_t n_cap);
 template <typename K>
 Status radix_sort(const K* keys_in, const uint32_t* values_in, K* keys_alt, uint32_t* values_alt,
                   K* keys_out, uint32_t* values_out, uint64_t n_cap, const uint64_t* d_n, int begin_bit,
-                  int end_bit, uint32_t* tmp, cudaStream_t st, int* passes_out);
+                  int end_bit, uint32_t* tmp, cudaStream_t st, int* passes_out, uint32_t* flags = nullptr,
+                  const uint32_t* pre_hist = nullptr);
 
-// K5: tile ranges from sorted keys (tile = key >> shift).  ranges must hold
-// n_tiles uint2 and is zeroed here.  Keys outside [0, n_tiles) set *overflow.
+// K5: tile ranges from sorted keys (tile = key >> shift), binary search per
+// tile.  ranges: n_tiles uint2.  A key outside [0, n_tiles) sets *overflow bit 2.
 template <typename K>
 Status launch_ranges(const K* keys, uint64_t n_cap, const uint64_t* d_n, int shift, uint2* ranges,
                      uint32_t n_tiles, uint32_t* overflow, cudaStream_t st);

@@ -277,7 +277,7 @@ Status render_frame(Scene* scene, FrameRequest& req, RenderContext& ctx, cudaStr
         int passes = 0;
         TIGAS_TRY(mark(kStDepthSort, true));
         TIGAS_TRY(radix_sort<uint32_t>(sp.depth_key, nullptr, pk_alt, pv_alt, pk, order, E, nullptr, 0, 32, tmp, st,
-                                       &passes));
+                                       &passes, d_flags));
         TIGAS_TRY(mark(kStDepthSort, false));
     }
     // K2: pair offsets in emit order
@@ -292,7 +292,7 @@ Status render_frame(Scene* scene, FrameRequest& req, RenderContext& ctx, cudaStr
     // ---- per-pair workspace
     const size_t kb = full64 ? 8 : 4;
     const size_t sort_words = radix_tmp_words(P);
-    size_t pair_bytes = P * (kb * 3 + 4 * 3) + sort_words * 4 + 8 * 256;
+    size_t pair_bytes = P * (kb * 3 + 4 * 3) + sort_words * 4 + 3 * 256 * 4 + 16 * 256;
     TIGAS_TRY(ctx.pairs.reserve(pair_bytes));
     ctx.pairs.reset();
     void* keys_a = ctx.pairs.take<uint8_t>(P * kb);
@@ -311,7 +311,7 @@ Status render_frame(Scene* scene, FrameRequest& req, RenderContext& ctx, cudaStr
         TIGAS_TRY(mark(kStEmit, false));
         TIGAS_TRY(mark(kStPairSort, true));
         TIGAS_TRY(radix_sort<uint32_t>((uint32_t*)keys_a, vals_a, (uint32_t*)keys_b, vals_b, (uint32_t*)keys_c, vals_c,
-                                       P, nullptr, 0, tile_bits, stmp, st, &passes));
+                                       P, nullptr, 0, tile_bits, stmp, st, &passes, d_flags));
         TIGAS_TRY(mark(kStPairSort, false));
         TIGAS_TRY(mark(kStRanges, true));
         TIGAS_TRY(launch_ranges<uint32_t>((uint32_t*)keys_c, P, nullptr, 0, ranges, total_tiles, d_flags, st));
@@ -323,7 +323,7 @@ Status render_frame(Scene* scene, FrameRequest& req, RenderContext& ctx, cudaStr
         TIGAS_TRY(mark(kStEmit, false));
         TIGAS_TRY(mark(kStPairSort, true));
         TIGAS_TRY(radix_sort<uint64_t>((uint64_t*)keys_a, vals_a, (uint64_t*)keys_b, vals_b, (uint64_t*)keys_c, vals_c,
-                                       P, nullptr, 0, 32 + tile_bits, stmp, st, &passes));
+                                       P, nullptr, 0, 32 + tile_bits, stmp, st, &passes, d_flags));
         TIGAS_TRY(mark(kStPairSort, false));
         TIGAS_TRY(mark(kStRanges, true));
         TIGAS_TRY(launch_ranges<uint64_t>((uint64_t*)keys_c, P, nullptr, 32, ranges, total_tiles, d_flags, st));

@@ -307,31 +307,20 @@ Status ensure_scatter_smem() {
     return {};
 }
 
-}  // namespace
-
-size_t radix_tmp_words(uint64_t n_cap) {
+size_t rts_tmp_words(uint64_t n_cap) {
     uint64_t tiles = sort_tiles(n_cap);
     if (tiles == 0) tiles = 1;
     uint64_t table = 256 * tiles;
     return 2 * table + scan_tmp_words(table);
 }
 
+// Reduce-then-scan passes: used for inputs of 2^30 elements or more (the
+// one-sweep status words hold 30-bit counts).
 template <typename K>
-Status radix_sort(const K* keys_in, const uint32_t* values_in, K* keys_alt, uint32_t* values_alt, K* keys_out,
-                  uint32_t* values_out, uint64_t n_cap, const uint64_t* d_n, int begin_bit, int end_bit,
-                  uint32_t* tmp, cudaStream_t st, int* passes_out) {
-    const int kbits = (int)(8 * sizeof(K));
-    if (begin_bit < 0 || end_bit > kbits || begin_bit > end_bit) return {TIGAS_ERR_INVALID, "bad sort bit range"};
-    if (n_cap >= 0xFFFFFFFFull) return {TIGAS_ERR_INVALID, "sort too large"};
+Status radix_sort_rts(const K* keys_in, const uint32_t* values_in, K* keys_alt, uint32_t* values_alt, K* keys_out,
+                      uint32_t* values_out, uint64_t n_cap, const uint64_t* d_n, int begin_bit, int end_bit,
+                      uint32_t* tmp, cudaStream_t st) {
     const int passes = (end_bit - begin_bit + 7) / 8;
-    if (passes_out) *passes_out = passes;
-    if (n_cap == 0) return {};
-    if (passes == 0) {
-        TIGAS_CUDA_TRY(cudaMemcpyAsync(keys_out, keys_in, n_cap * sizeof(K), cudaMemcpyDeviceToDevice, st));
-        if (values_in)
-            TIGAS_CUDA_TRY(cudaMemcpyAsync(values_out, values_in, n_cap * 4, cudaMemcpyDeviceToDevice, st));
-        return {};
-    }
     TIGAS_TRY(ensure_scatter_smem<K>());
     const size_t smem = sizeof(ScatterSmem<K>);
     const uint32_t tiles = sort_tiles(n_cap);
@@ -359,9 +348,377 @@ Status radix_sort(const K* keys_in, const uint32_t* values_in, K* keys_alt, uint
     return {};
 }
 
+}  // namespace
+
+// ------------------------------------------------------ one-sweep passes
+//
+// One read of the keys builds the global digit histogram of every pass.  Each
+// pass is then a single scatter kernel: a CTA claims the next chunk of keys
+// (chunk ids follow the order CTAs start in), ranks its keys stably, publishes
+// its per-digit counts, and finds the count of each digit in all earlier
+// chunks by decoupled look-back over their published counts.  A CTA only waits
+// on chunks claimed by CTAs that started before it, which publish before they
+// wait themselves, so the waits always end; each wait is still bounded: after
+// kSpinLimit polls the CTA records a timeout flag and goes on (its writes stay
+// inside the output by the bounds check, the host reports the error).
+
+namespace {
+
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagPre = 2u << 30;
+constexpr uint32_t kFlagMask = 3u << 30;
+constexpr uint32_t kValMask = (1u << 30) - 1;
+constexpr int kSpinLimit = 1 << 22;
+constexpr uint32_t kSortTimeoutFlag = 16u;
+
+template <typename K>
+struct OsCfg;
+template <>
+struct OsCfg<uint32_t> {
+    static constexpr int kT = 512, kI = 16;
+};
+template <>
+struct OsCfg<uint64_t> {
+    static constexpr int kT = 256, kI = 16;
+};
+
+__device__ inline uint32_t ld_relaxed(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ inline void st_relaxed(uint32_t* p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Lanes of the warp whose digit (nb bits) equals this lane's: the AND over the
+// digit's bits of the ballot of lanes agreeing on that bit (warp multisplit).
+__device__ inline uint32_t digit_peers(uint32_t d, int nb) {
+    uint32_t peers = kFull;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        if (b < nb) {
+            const bool bit = (d >> b) & 1u;
+            const uint32_t bal = __ballot_sync(kFull, bit);
+            peers &= bit ? bal : ~bal;
+        }
+    }
+    return peers;
+}
+
+// Exclusive scan of one value per thread over a CTA of T threads.
+template <int T>
+__device__ inline uint32_t cta_exclusive_scan(uint32_t x, uint32_t* ws /*[T/32 + 1]*/) {
+    constexpr int W = T / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t y = __shfl_up_sync(kFull, inc, d);
+        if (lane >= d) inc += y;
+    }
+    if (lane == 31) ws[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < W ? ws[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            uint32_t y = __shfl_up_sync(kFull, wi, d);
+            if (lane >= d) wi += y;
+        }
+        if (lane < W) ws[lane] = wi - w;
+        if (lane == W - 1) ws[W] = wi;
+    }
+    __syncthreads();
+    uint32_t r = ws[warp] + inc - x;
+    __syncthreads();
+    return r;
+}
+
+// Global digit histograms of every pass in one read (run-length aggregated
+// shared-memory counts, so keys with few distinct digits do not serialise).
+template <typename K>
+__global__ void __launch_bounds__(512)
+k_os_hist(const K* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, int begin_bit, int end_bit,
+          uint32_t* __restrict__ ghist) {
+    __shared__ uint32_t h[8][256];
+    const int passes = (end_bit - begin_bit + 7) / 8;
+    for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t n = count_of(n_cap, d_n);
+    uint32_t cur[8], run[8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) { cur[p] = 0xFFFFFFFFu; run[p] = 0; }
+    // 8 keys per thread per step, all loads issued before any count
+    constexpr int kB = 8;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * kB;
+    for (uint64_t i0 = ((uint64_t)blockIdx.x * blockDim.x) * kB + threadIdx.x; i0 < n; i0 += stride) {
+        K kv[kB];
+#pragma unroll
+        for (int b = 0; b < kB; ++b) {
+            const uint64_t i = i0 + (uint64_t)b * blockDim.x;
+            kv[b] = i < n ? keys[i] : K(0);
+        }
+#pragma unroll
+        for (int b = 0; b < kB; ++b) {
+            if (i0 + (uint64_t)b * blockDim.x >= n) break;
+#pragma unroll
+            for (int p = 0; p < 8; ++p) {
+                if (p < passes) {
+                    const int sh = begin_bit + 8 * p;
+                    const int nb = min(8, end_bit - sh);
+                    const uint32_t d = (uint32_t)(kv[b] >> sh) & ((1u << nb) - 1u);
+                    if (d == cur[p]) {
+                        ++run[p];
+                    } else {
+                        if (run[p]) atomicAdd(&h[p][cur[p]], run[p]);
+                        cur[p] = d;
+                        run[p] = 1;
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < 8; ++p)
+        if (p < passes && run[p]) atomicAdd(&h[p][cur[p]], run[p]);
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
+        uint32_t c = (&h[0][0])[i];
+        if (c) atomicAdd(&ghist[i], c);
+    }
+}
+
+// ghist[p][256] -> exclusive digit bases gbase[p][256]
+__global__ void __launch_bounds__(256) k_os_bases(const uint32_t* __restrict__ ghist, uint32_t* __restrict__ gbase,
+                                                  int passes) {
+    __shared__ uint32_t ws[9];
+    for (int p = 0; p < passes; ++p) {
+        uint32_t x = ghist[p * 256 + threadIdx.x];
+        uint32_t e = cta_exclusive_scan<256>(x, ws);
+        gbase[p * 256 + threadIdx.x] = e;
+    }
+}
+
+template <typename K>
+struct OsSmem {
+    static constexpr int T = OsCfg<K>::kT, I = OsCfg<K>::kI, N = T * I, W = T / 32;
+    K keys[N];
+    uint32_t vals[N];
+    uint32_t whist[W][256];
+    uint32_t dstart[256];
+    uint32_t gpos[256];
+    uint32_t ws[W + 1];
+    uint32_t chunk;
+};
+
+template <typename K>
+__global__ void __launch_bounds__(OsCfg<K>::kT)
+k_os_scatter(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, K* __restrict__ keys_out,
+             uint32_t* __restrict__ vals_out, uint64_t n_cap, const uint64_t* d_n, int shift, int nbits,
+             const uint32_t* __restrict__ gbase, uint32_t* status, uint32_t* chunk_counter, uint32_t* flags) {
+    const uint32_t mask = (1u << nbits) - 1u;
+    constexpr int T = OsCfg<K>::kT, I = OsCfg<K>::kI, N = T * I, W = T / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    OsSmem<K>& sm = *reinterpret_cast<OsSmem<K>*>(smem_raw);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) sm.chunk = atomicAdd(chunk_counter, 1u);
+    for (int k = threadIdx.x; k < W * 256; k += T) (&sm.whist[0][0])[k] = 0;
+    __syncthreads();
+    const uint32_t chunk = sm.chunk;
+    const uint32_t n = count_of(n_cap, d_n);
+    const uint64_t base = (uint64_t)chunk * N;
+    if (base >= n) return;   // CTA-uniform; no later chunk waits on it
+    const uint32_t valid = (n - base) < (uint64_t)N ? (uint32_t)(n - base) : (uint32_t)N;
+
+    K key[I];
+    uint32_t val[I];
+#pragma unroll
+    for (int r = 0; r < I; ++r) {
+        const uint32_t li = warp * (I * 32) + r * 32 + lane;
+        if (li < valid) {
+            key[r] = keys_in[base + li];
+            val[r] = vals_in ? vals_in[base + li] : (uint32_t)(base + li);
+        } else {
+            key[r] = ~K(0);
+            val[r] = 0;
+        }
+    }
+    uint32_t dr[I];
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int r = 0; r < I; ++r) {
+        const uint32_t d = (uint32_t)(key[r] >> shift) & mask;
+        const uint32_t peers = digit_peers(d, nbits);
+        const uint32_t before = sm.whist[warp][d];
+        __syncwarp();
+        if (lane == __ffs(peers) - 1) sm.whist[warp][d] = before + __popc(peers);
+        __syncwarp();
+        dr[r] = (d << 16) | (before + __popc(peers & lt));
+    }
+    __syncthreads();
+
+    // per digit: prefix over warps, the CTA's count, and look-back for earlier chunks
+    uint32_t cnt = 0;
+    if (threadIdx.x < 256) {
+        const uint32_t d = threadIdx.x;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const uint32_t c = sm.whist[w][d];
+            sm.whist[w][d] = cnt;
+            cnt += c;
+        }
+        // padding keys (digit == mask) are not part of this chunk's counts
+        if (d == mask) cnt -= (uint32_t)(N - valid);
+        uint32_t excl = 0;
+        uint32_t* my = status + (size_t)chunk * 256 + d;
+        if (chunk == 0) {
+            st_relaxed(my, kFlagPre | (cnt & kValMask));
+        } else {
+            st_relaxed(my, kFlagAgg | (cnt & kValMask));
+            int64_t j = (int64_t)chunk - 1;
+            int spins = 0;
+            while (j >= 0) {
+                const uint32_t sv = ld_relaxed(status + (size_t)j * 256 + d);
+                const uint32_t fl = sv & kFlagMask;
+                if (fl == 0) {
+                    if (++spins > kSpinLimit) {
+                        atomicOr(flags, kSortTimeoutFlag);
+                        break;
+                    }
+                    if (spins > 32) __nanosleep(32);
+                    continue;
+                }
+                excl += sv & kValMask;
+                if (fl == kFlagPre) break;
+                --j;
+            }
+            st_relaxed(my, kFlagPre | ((excl + cnt) & kValMask));
+        }
+        sm.gpos[d] = (d <= mask ? gbase[d] : 0u) + excl;
+    }
+    // restore the padding count for the in-tile layout (padding sorts last)
+    const uint32_t local_cnt = threadIdx.x < 256 ? cnt + ((threadIdx.x == mask) ? (uint32_t)(N - valid) : 0u) : 0u;
+    const uint32_t start = cta_exclusive_scan<T>(local_cnt, sm.ws);
+    if (threadIdx.x < 256) sm.dstart[threadIdx.x] = start;
+    __syncthreads();
+
+#pragma unroll
+    for (int r = 0; r < I; ++r) {
+        const uint32_t d = dr[r] >> 16;
+        const uint32_t pos = sm.dstart[d] + sm.whist[warp][d] + (dr[r] & 0xFFFFu);
+        sm.keys[pos] = key[r];
+        sm.vals[pos] = val[r];
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < I; ++k) {
+        const uint32_t j = k * T + threadIdx.x;
+        if (j < valid) {
+            const K kk = sm.keys[j];
+            const uint32_t d = (uint32_t)(kk >> shift) & mask;
+            const uint32_t g = sm.gpos[d] + (j - sm.dstart[d]);
+            if (g < n) {
+                keys_out[g] = kk;
+                vals_out[g] = sm.vals[j];
+            }
+        }
+    }
+}
+
+template <typename K>
+Status ensure_os_smem() {
+    static std::atomic<bool> done{false};
+    if (done.load()) return {};
+    TIGAS_CUDA_TRY(cudaFuncSetAttribute(k_os_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)sizeof(OsSmem<K>)));
+    done.store(true);
+    return {};
+}
+
+uint64_t os_chunks(uint64_t n_cap) { return (n_cap + 4095) / 4096; }   // upper bound for both key widths
+
+size_t os_tmp_words(uint64_t n_cap) { return 8 * 256 * 2 + 16 + os_chunks(n_cap) * 256; }
+
+template <typename K>
+Status radix_sort_onesweep(const K* keys_in, const uint32_t* values_in, K* keys_alt, uint32_t* values_alt,
+                           K* keys_out, uint32_t* values_out, uint64_t n_cap, const uint64_t* d_n, int begin_bit,
+                           int end_bit, uint32_t* tmp, cudaStream_t st, uint32_t* flags, const uint32_t* pre_hist) {
+    constexpr int T = OsCfg<K>::kT, N = OsCfg<K>::kT * OsCfg<K>::kI;
+    const int passes = (end_bit - begin_bit + 7) / 8;
+    TIGAS_TRY(ensure_os_smem<K>());
+    uint32_t* ghist = tmp;
+    uint32_t* gbase = tmp + 8 * 256;
+    uint32_t* counters = gbase + 8 * 256;
+    uint32_t* own_flags = counters + 8;
+    uint32_t* status = counters + 16;
+    if (!flags) flags = own_flags;
+    const uint64_t chunks = (n_cap + N - 1) / N;
+    if (pre_hist) {
+        TIGAS_CUDA_TRY(cudaMemsetAsync(gbase + 8 * 256, 0, 16 * sizeof(uint32_t), st));
+        ghist = const_cast<uint32_t*>(pre_hist);
+    } else {
+        TIGAS_CUDA_TRY(cudaMemsetAsync(tmp, 0, (8 * 256 * 2 + 16) * sizeof(uint32_t), st));
+        k_os_hist<K><<<2 * 148 * 4, 512, 0, st>>>(keys_in, n_cap, d_n, begin_bit, end_bit, ghist);
+        TIGAS_LAUNCHED();
+    }
+    k_os_bases<<<1, 256, 0, st>>>(ghist, gbase, passes);
+    TIGAS_LAUNCHED();
+    const K* src_k = keys_in;
+    const uint32_t* src_v = values_in;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = begin_bit + 8 * p;
+        const int nb = min(8, end_bit - shift);
+        const bool to_out = ((passes - 1 - p) % 2) == 0;
+        K* dk = to_out ? keys_out : keys_alt;
+        uint32_t* dv = to_out ? values_out : values_alt;
+        TIGAS_CUDA_TRY(cudaMemsetAsync(status, 0, chunks * 256 * sizeof(uint32_t), st));
+        k_os_scatter<K><<<(unsigned)chunks, T, sizeof(OsSmem<K>), st>>>(src_k, src_v, dk, dv, n_cap, d_n, shift,
+                                                                       nb, gbase + p * 256, status, counters + p,
+                                                                       flags);
+        TIGAS_LAUNCHED();
+        src_k = dk;
+        src_v = dv;
+    }
+    return {};
+}
+
+}  // namespace
+
+size_t radix_tmp_words(uint64_t n_cap) {
+    size_t a = rts_tmp_words(n_cap), b = os_tmp_words(n_cap);
+    return a > b ? a : b;
+}
+
+template <typename K>
+Status radix_sort(const K* keys_in, const uint32_t* values_in, K* keys_alt, uint32_t* values_alt, K* keys_out,
+                  uint32_t* values_out, uint64_t n_cap, const uint64_t* d_n, int begin_bit, int end_bit,
+                  uint32_t* tmp, cudaStream_t st, int* passes_out, uint32_t* flags, const uint32_t* pre_hist) {
+    const int kbits = (int)(8 * sizeof(K));
+    if (begin_bit < 0 || end_bit > kbits || begin_bit > end_bit) return {TIGAS_ERR_INVALID, "bad sort bit range"};
+    if (n_cap >= 0xFFFFFFFFull) return {TIGAS_ERR_INVALID, "sort too large"};
+    const int passes = (end_bit - begin_bit + 7) / 8;
+    if (passes_out) *passes_out = passes;
+    if (n_cap == 0) return {};
+    if (passes == 0) {
+        TIGAS_CUDA_TRY(cudaMemcpyAsync(keys_out, keys_in, n_cap * sizeof(K), cudaMemcpyDeviceToDevice, st));
+        if (values_in)
+            TIGAS_CUDA_TRY(cudaMemcpyAsync(values_out, values_in, n_cap * 4, cudaMemcpyDeviceToDevice, st));
+        return {};
+    }
+    if (n_cap < (1ull << 30))
+        return radix_sort_onesweep<K>(keys_in, values_in, keys_alt, values_alt, keys_out, values_out, n_cap, d_n,
+                                      begin_bit, end_bit, tmp, st, flags, pre_hist);
+    return radix_sort_rts<K>(keys_in, values_in, keys_alt, values_alt, keys_out, values_out, n_cap, d_n, begin_bit,
+                             end_bit, tmp, st);
+}
+
 template Status radix_sort<uint32_t>(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, uint32_t*, uint32_t*,
-                                     uint64_t, const uint64_t*, int, int, uint32_t*, cudaStream_t, int*);
+                                     uint64_t, const uint64_t*, int, int, uint32_t*, cudaStream_t, int*, uint32_t*,
+                                     const uint32_t*);
 template Status radix_sort<uint64_t>(const uint64_t*, const uint32_t*, uint64_t*, uint32_t*, uint64_t*, uint32_t*,
-                                     uint64_t, const uint64_t*, int, int, uint32_t*, cudaStream_t, int*);
+                                     uint64_t, const uint64_t*, int, int, uint32_t*, cudaStream_t, int*, uint32_t*,
+                                     const uint32_t*);
 
 }  // namespace tigas
