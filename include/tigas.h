@@ -107,14 +107,26 @@ tigas_status tigas_scene_bytes(const tigas_scene* scene, uint64_t* out_bytes);
 tigas_status tigas_render(tigas_scene* scene, const tigas_pose* pose, const tigas_intrinsics* intr,
                           int width, int height, uint8_t* out_rgba8);
 
+/* Schedules of the same method; all three give the same frame.
+ *  DEPTH_FIRST: the (tile | depth) LSD sort with its depth digits sorted once
+ *      per Gaussian before duplication and its tile digits per pair; every
+ *      tile's full list is built.
+ *  FULL64: 64-bit (tile | depth) keys emitted per pair in index order, every
+ *      significant digit sorted per pair; every tile's full list is built.
+ *  SLICED (what tigas_render, tigas_render_batch and the server use): the
+ *      depth-ordered Gaussians are cut into nearest-first slices and each
+ *      slice is emitted, sorted and blended only for tiles that still have a
+ *      pixel whose transmittance has not stopped; tile lists are never
+ *      materialised whole, so tigas_debug_render cannot return them. */
 enum {
-    TIGAS_SORT_DEPTH_FIRST = 0,  /* depth digits sorted per Gaussian, tile digits per pair (default) */
-    TIGAS_SORT_FULL64 = 1        /* every digit of the 64-bit (tile | depth) key sorted per pair */
+    TIGAS_SORT_DEPTH_FIRST = 0,
+    TIGAS_SORT_FULL64 = 1,
+    TIGAS_SORT_SLICED = 2
 };
 
 typedef struct {
     uint64_t n_visible;          /* (Gaussian, view) entries kept after culling */
-    uint64_t n_pairs;            /* (Gaussian, tile) pairs P */
+    uint64_t n_pairs;            /* (Gaussian, tile) pairs emitted (SLICED: summed over slices) */
     uint32_t n_tiles;            /* 16x16 tiles in the frame(s) */
     uint32_t sort_passes;        /* radix passes over the pair array */
     uint64_t blend_evals;        /* list entries evaluated, summed over pixels, up to each pixel's stop */

@@ -79,8 +79,10 @@ Status do_render(Scene* scene, int V, const tigas_pose* poses, const tigas_intri
                  tigas_frame_stats* stats, tigas_debug_frame* dbg, uint64_t* dbg_pairs) {
     if (!scene) return {TIGAS_ERR_INVALID, "null scene"};
     if (V < 1 || V > kMaxViews) return {TIGAS_ERR_INVALID, "n_views out of 1..64"};
-    if (sort_mode != TIGAS_SORT_DEPTH_FIRST && sort_mode != TIGAS_SORT_FULL64)
+    if (sort_mode != TIGAS_SORT_DEPTH_FIRST && sort_mode != TIGAS_SORT_FULL64 && sort_mode != TIGAS_SORT_SLICED)
         return {TIGAS_ERR_INVALID, "unknown sort mode"};
+    if (dbg && sort_mode == TIGAS_SORT_SLICED && (dbg->values || dbg->ranges))
+        return {TIGAS_ERR_INVALID, "the sliced schedule builds no whole tile lists: pass values = ranges = NULL"};
     for (int v = 0; v < V; ++v) TIGAS_TRY(validate_view(&poses[v], &intrs[v], ws[v], hs[v]));
     Status err;
     ContextGuard g;
@@ -179,9 +181,9 @@ Status do_render(Scene* scene, int V, const tigas_pose* poses, const tigas_intri
             }
             if (dbg->q) dbg->q[i] = q[i];
         }
-        if (dbg->values && res.pairs <= dbg->pair_capacity && res.pairs)
+        if (dbg->values && res.values && res.pairs <= dbg->pair_capacity && res.pairs)
             TIGAS_CUDA_TRY(cudaMemcpy(dbg->values, res.values, res.pairs * 4, cudaMemcpyDeviceToHost));
-        if (dbg->ranges)
+        if (dbg->ranges && res.ranges)
             TIGAS_CUDA_TRY(cudaMemcpy(dbg->ranges, res.ranges, (size_t)res.total_tiles * 8, cudaMemcpyDeviceToHost));
     }
     return {};
@@ -298,8 +300,7 @@ TIGAS_API tigas_status tigas_render_ex(tigas_scene* scene, const tigas_pose* pos
 TIGAS_API tigas_status tigas_render(tigas_scene* scene, const tigas_pose* pose, const tigas_intrinsics* intr,
                                     int width, int height, uint8_t* out_rgba8) {
     if (!out_rgba8) return fail(TIGAS_ERR_INVALID, "null output");
-    return tigas_render_ex(scene, pose, intr, width, height, out_rgba8, nullptr, nullptr, TIGAS_SORT_DEPTH_FIRST,
-                           nullptr);
+    return tigas_render_ex(scene, pose, intr, width, height, out_rgba8, nullptr, nullptr, TIGAS_SORT_SLICED, nullptr);
 }
 
 TIGAS_API tigas_status tigas_render_batch(tigas_scene* scene, int n_views, const tigas_pose* poses,
@@ -312,7 +313,7 @@ TIGAS_API tigas_status tigas_render_batch(tigas_scene* scene, int n_views, const
         if (!outs[v]) return fail(TIGAS_ERR_INVALID, "null output buffer");
     SceneGuard sg(reinterpret_cast<Scene*>(scene));
     Status st = do_render(sg.s, n_views, poses, intrs, widths, heights, outs, nullptr, (cudaStream_t)cuda_stream,
-                          TIGAS_SORT_DEPTH_FIRST, nullptr, nullptr, nullptr);
+                          TIGAS_SORT_SLICED, nullptr, nullptr, nullptr);
     return st.ok() ? TIGAS_OK : fail(st);
 }
 

@@ -41,17 +41,19 @@ ViewParams make_view(const tigas_pose& pose, const tigas_intrinsics& k, int widt
                      uint32_t tile_base);
 
 enum Stage { kStPreprocess, kStDepthSort, kStScan, kStEmit, kStPairSort, kStRanges, kStBlend, kNumStages };
+constexpr int kMaxSlices = 16;   // depth slices of the sliced schedule (and event pairs per stage)
 
 // Process-wide stage timing (tigas_profile_*).
 extern std::atomic<bool> g_profile;
-void profile_accumulate(const float* ms, const bool* used, float frame_ms);
+void profile_accumulate(const float* ms, const int* used, float frame_ms);
 void profile_read(double* ms, uint64_t* calls, bool reset);
 
 // Render state of one in-flight frame or launch set: stream, arenas, pinned staging.
 struct RenderContext {
-    cudaEvent_t ev_start[kNumStages] = {};
-    cudaEvent_t ev_stop[kNumStages] = {};
-    bool ev_used[kNumStages] = {};
+    cudaEvent_t ev_start[kNumStages][kMaxSlices] = {};
+    cudaEvent_t ev_stop[kNumStages][kMaxSlices] = {};
+    int ev_count[kNumStages] = {};     // start/stop pairs recorded per stage this frame
+    uint32_t* h_misc = nullptr;        // pinned readback of per-view counts
     cudaStream_t stream = nullptr;     // own stream (used when the caller passes none)
     Arena fixed;                       // per-entry buffers
     Arena pairs;                       // per-pair buffers
@@ -68,6 +70,7 @@ struct FrameRequest {
     int V = 1;
     ViewParams views[kMaxViews];       // out pointers must be device pointers (or null)
     int sort_mode = TIGAS_SORT_DEPTH_FIRST;
+    int n_slices = 8;                    // sliced schedule: geometric depth slices
     bool want_counters = false;          // count blend evaluations / fetched entries
     bool want_q = false;
 };

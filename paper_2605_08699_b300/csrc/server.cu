@@ -151,7 +151,7 @@ struct Server {
             }
             tigas_frame_stats stats{};
             Status st = do_render(scene, V, poses.data(), intrs.data(), ws.data(), hs.data(), outs.data(), nullptr,
-                                  nullptr, TIGAS_SORT_DEPTH_FIRST, &stats, nullptr, nullptr);
+                                  nullptr, TIGAS_SORT_SLICED, &stats, nullptr, nullptr);
             const double t_done = now_us();
 
             lk.lock();

@@ -1,0 +1,199 @@
+// Depth-sliced schedule of the hot path.
+//
+// The per-tile blend consumes a tile's depth-ordered list front to back and
+// stops once every pixel's transmittance has fallen below the threshold; in
+// dense scenes that happens after a small fraction of the list.  Here the
+// depth-ordered entries (all views) are cut into slices, nearest first.  Each
+// slice runs the same steps as the whole frame -- count, scan, duplicate-and-
+// key emit, radix sort by tile, tile ranges, blend -- but only for tiles that
+// still have a pixel running, with every pixel's (C, T) carried across slices.
+// Within a tile, all pairs of slice s precede those of slice s + 1 in depth
+// order and the stable sort keeps depth order inside a slice, so each pixel
+// composites the same entries in the same order as over the whole list: the
+// frame is identical, but pairs of tiles that already stopped are never
+// emitted, sorted or read.
+#include "kernels.cuh"
+#include "sliced.cuh"
+
+namespace tigas {
+
+namespace {
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+
+__device__ inline int view_of_tile(const uint32_t* s_tb, int V, uint32_t g) {
+    int lo = 0, hi = V;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_tb[mid] <= g) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ inline uint8_t to_u8(float x) {
+    return (uint8_t)__float2uint_rd(fminf(fmaxf(x, 0.0f), 1.0f) * 255.0f + 0.5f);
+}
+
+// State (C = 0, T = 1) and background outputs for every pixel; one CTA per tile.
+__global__ void __launch_bounds__(256)
+k_init_state(const ViewParams* __restrict__ views_g, int V, const uint64_t* __restrict__ pix_base, float4* state,
+             float bg_r, float bg_g, float bg_b) {
+    __shared__ uint32_t s_tb[kMaxViews];
+    for (int k = threadIdx.x; k < V; k += blockDim.x) s_tb[k] = views_g[k].tile_base;
+    __syncthreads();
+    const uint32_t g = blockIdx.x;
+    const int v = view_of_tile(s_tb, V, g);
+    const ViewParams& vp = views_g[v];
+    const uint32_t local = g - s_tb[v];
+    const int px = (int)(local % vp.TX) * kTile + (threadIdx.x & 15);
+    const int py = (int)(local / vp.TX) * kTile + (threadIdx.x >> 4);
+    if (px >= vp.W || py >= vp.H) return;
+    const size_t pix = (size_t)py * vp.W + px;
+    state[pix_base[v] + pix] = make_float4(0.f, 0.f, 0.f, 1.0f);
+    if (vp.out_rgba8)
+        reinterpret_cast<uchar4*>(vp.out_rgba8)[pix] = make_uchar4(to_u8(bg_r), to_u8(bg_g), to_u8(bg_b), 0);
+    if (vp.out_rgba_f32) reinterpret_cast<float4*>(vp.out_rgba_f32)[pix] = make_float4(bg_r, bg_g, bg_b, 0.f);
+}
+
+__device__ inline bool tile_done(const uint32_t* __restrict__ done, uint32_t t) {
+    return (done[t >> 5] >> (t & 31)) & 1u;
+}
+
+// counts[k - a] = tiles of entry order[k]'s rectangle that are not done.
+__global__ void __launch_bounds__(256)
+k_count_slice(const uint32_t* __restrict__ order, uint64_t a, uint64_t b, SplatArrays sp,
+              const ViewParams* __restrict__ views_g, int V, uint32_t n_per_view, const uint32_t* __restrict__ done,
+              uint32_t* __restrict__ counts) {
+    __shared__ uint32_t s_tb[kMaxViews], s_tx[kMaxViews];
+    for (int k = threadIdx.x; k < V; k += blockDim.x) {
+        s_tb[k] = views_g[k].tile_base;
+        s_tx[k] = (uint32_t)views_g[k].TX;
+    }
+    __syncthreads();
+    const uint64_t k = a + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= b) return;
+    const uint32_t e = order[k];
+    uint32_t c = 0;
+    if (sp.tiles[e]) {
+        const uint2 r = sp.rect[e];
+        const uint32_t xlo = r.x & 0xFFFFu, ylo = r.x >> 16, xhi = r.y & 0xFFFFu, yhi = r.y >> 16;
+        const uint32_t v = e / n_per_view;
+        for (uint32_t ty = ylo; ty < yhi; ++ty) {
+            const uint32_t row = s_tb[v] + ty * s_tx[v];
+            for (uint32_t tx = xlo; tx < xhi; ++tx) c += tile_done(done, row + tx) ? 0u : 1u;
+        }
+    }
+    counts[k - a] = c;
+}
+
+// Pairs (tile, entry) of the slice for tiles not done, in depth order.
+__global__ void __launch_bounds__(256)
+k_emit_slice(const uint32_t* __restrict__ order, uint64_t a, uint64_t b, const uint32_t* __restrict__ offsets,
+             SplatArrays sp, const ViewParams* __restrict__ views_g, int V, uint32_t n_per_view,
+             const uint32_t* __restrict__ done, uint32_t* __restrict__ keys, uint32_t* __restrict__ values,
+             uint64_t pair_cap, uint32_t* __restrict__ overflow) {
+    __shared__ uint32_t s_tb[kMaxViews], s_tx[kMaxViews];
+    for (int k = threadIdx.x; k < V; k += blockDim.x) {
+        s_tb[k] = views_g[k].tile_base;
+        s_tx[k] = (uint32_t)views_g[k].TX;
+    }
+    __syncthreads();
+    const uint64_t k = a + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= b) return;
+    const uint32_t e = order[k];
+    if (!sp.tiles[e]) return;
+    const uint2 r = sp.rect[e];
+    const uint32_t xlo = r.x & 0xFFFFu, ylo = r.x >> 16, xhi = r.y & 0xFFFFu, yhi = r.y >> 16;
+    const uint32_t v = e / n_per_view;
+    uint64_t pos = offsets[k - a];
+    for (uint32_t ty = ylo; ty < yhi; ++ty) {
+        const uint32_t row = s_tb[v] + ty * s_tx[v];
+        for (uint32_t tx = xlo; tx < xhi; ++tx) {
+            const uint32_t t = row + tx;
+            if (tile_done(done, t)) continue;
+            if (pos < pair_cap) {
+                keys[pos] = t;
+                values[pos] = e;
+            } else {
+                atomicOr(overflow, 1u);
+            }
+            ++pos;
+        }
+    }
+}
+
+// Tile ranges by binary search; tiles with pairs in this slice that are not
+// done are appended to the active list (order irrelevant: tiles are independent).
+__device__ inline uint64_t lower_bound_u32(const uint32_t* __restrict__ keys, uint64_t n, uint32_t t) {
+    uint64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (keys[mid] < t) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256)
+k_ranges_active(const uint32_t* __restrict__ keys, uint64_t n, uint2* __restrict__ ranges, uint32_t n_tiles,
+                const uint32_t* __restrict__ done, uint32_t* __restrict__ active, uint32_t* __restrict__ n_active,
+                uint32_t* __restrict__ overflow) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0 && n > 0 && keys[n - 1] >= n_tiles) atomicOr(overflow, 2u);
+    bool act = false;
+    if (t < n_tiles) {
+        const uint64_t lo = lower_bound_u32(keys, n, t);
+        const uint64_t hi = lower_bound_u32(keys, n, t + 1);
+        ranges[t] = make_uint2((uint32_t)lo, (uint32_t)hi);
+        act = hi > lo && !tile_done(done, t);
+    }
+    const uint32_t m = __ballot_sync(kFull, act);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    uint32_t base = 0;
+    if (lane == __ffs(m) - 1) base = atomicAdd(n_active, (uint32_t)__popc(m));
+    base = __shfl_sync(kFull, base, __ffs(m) - 1);
+    if (act) active[base + __popc(m & ((1u << lane) - 1u))] = t;
+}
+
+}  // namespace
+
+Status launch_init_state(const ViewParams* views, int V, uint32_t total_tiles, const uint64_t* pix_base,
+                         float4* state, const float* bg, cudaStream_t st) {
+    if (total_tiles == 0) return {};
+    k_init_state<<<total_tiles, 256, 0, st>>>(views, V, pix_base, state, bg[0], bg[1], bg[2]);
+    TIGAS_LAUNCHED();
+    return {};
+}
+
+Status launch_count_slice(const uint32_t* order, uint64_t a, uint64_t b, const SplatArrays& sp,
+                          const ViewParams* views, int V, uint32_t n_per_view, const uint32_t* done, uint32_t* counts,
+                          cudaStream_t st) {
+    if (b <= a) return {};
+    k_count_slice<<<(unsigned)((b - a + 255) / 256), 256, 0, st>>>(order, a, b, sp, views, V, n_per_view, done,
+                                                                    counts);
+    TIGAS_LAUNCHED();
+    return {};
+}
+
+Status launch_emit_slice(const uint32_t* order, uint64_t a, uint64_t b, const uint32_t* offsets,
+                         const SplatArrays& sp, const ViewParams* views, int V, uint32_t n_per_view,
+                         const uint32_t* done, uint32_t* keys, uint32_t* values, uint64_t pair_cap, uint32_t* overflow,
+                         cudaStream_t st) {
+    if (b <= a) return {};
+    k_emit_slice<<<(unsigned)((b - a + 255) / 256), 256, 0, st>>>(order, a, b, offsets, sp, views, V, n_per_view,
+                                                                   done, keys, values, pair_cap, overflow);
+    TIGAS_LAUNCHED();
+    return {};
+}
+
+Status launch_ranges_active(const uint32_t* keys, uint64_t n, uint2* ranges, uint32_t n_tiles, const uint32_t* done,
+                            uint32_t* active, uint32_t* n_active, uint32_t* overflow, cudaStream_t st) {
+    if (n_tiles == 0) return {};
+    TIGAS_CUDA_TRY(cudaMemsetAsync(n_active, 0, sizeof(uint32_t), st));
+    k_ranges_active<<<(n_tiles + 255) / 256, 256, 0, st>>>(keys, n, ranges, n_tiles, done, active, n_active,
+                                                           overflow);
+    TIGAS_LAUNCHED();
+    return {};
+}
+
+}  // namespace tigas

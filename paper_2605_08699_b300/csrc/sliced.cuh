@@ -1,0 +1,44 @@
+// Launch interface of the depth-sliced schedule (see sliced.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace tigas {
+
+// (C, T) = (0, 1) for every pixel of every view, background in the outputs.
+// pix_base[v]: offset of view v's first pixel in `state`.
+Status launch_init_state(const ViewParams* views, int V, uint32_t total_tiles, const uint64_t* pix_base,
+                         float4* state, const float* bg, cudaStream_t st);
+
+// counts[k - a]: not-done tiles in the rectangle of entry order[k], k in [a, b).
+Status launch_count_slice(const uint32_t* order, uint64_t a, uint64_t b, const SplatArrays& sp,
+                          const ViewParams* views, int V, uint32_t n_per_view, const uint32_t* done, uint32_t* counts,
+                          cudaStream_t st);
+
+// (tile, entry) pairs of entries [a, b) for tiles not done, at offsets[k - a].
+Status launch_emit_slice(const uint32_t* order, uint64_t a, uint64_t b, const uint32_t* offsets,
+                         const SplatArrays& sp, const ViewParams* views, int V, uint32_t n_per_view,
+                         const uint32_t* done, uint32_t* keys, uint32_t* values, uint64_t pair_cap, uint32_t* overflow,
+                         cudaStream_t st);
+
+// Tile ranges of the slice's sorted keys, and the list of tiles with pairs
+// that are not done (*n_active entries of `active`, zeroed here).
+Status launch_ranges_active(const uint32_t* keys, uint64_t n, uint2* ranges, uint32_t n_tiles, const uint32_t* done,
+                            uint32_t* active, uint32_t* n_active, uint32_t* overflow, cudaStream_t st);
+
+// Blend of the active tiles of one slice: persistent CTAs take tiles from the
+// active list, composite the slice's entries onto each pixel's carried state,
+// store the state and the outputs, and mark tiles whose pixels all stopped.
+struct SliceBlendArgs {
+    const uint32_t* active;
+    const uint32_t* n_active;
+    uint32_t* work_counter;     // zeroed by the launcher
+    float4* state;              // per pixel (C.rgb, T), T negated once the pixel stopped
+    const uint64_t* pix_base;   // per view
+    uint32_t* done;             // per-tile bitmap
+};
+Status launch_blend_slice(const uint2* ranges, const uint32_t* values, const SplatArrays& sp,
+                          const ViewParams* views, int V, uint32_t n_entries, const float* bg,
+                          unsigned long long* counters, const SliceBlendArgs& sl, cudaStream_t st);
+
+}  // namespace tigas

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libtigas.so")
 
 OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_AGAIN, ERR_OVERFLOW, ERR_TIMEOUT, ERR_NOT_FOUND = range(8)
 STORAGE_FP32, STORAGE_FP16 = 0, 1
-SORT_DEPTH_FIRST, SORT_FULL64 = 0, 1
+SORT_DEPTH_FIRST, SORT_FULL64, SORT_SLICED = 0, 1, 2
 
 #: every symbol include/tigas.h declares
 EXPORTS = ["tigas_scene_load", "tigas_scene_free", "tigas_scene_bytes", "tigas_render", "tigas_render_ex",
@@ -298,17 +298,23 @@ def debug_render(scene: SceneHandle, pose, intr, width: int, height: int, sort_m
         "values": np.zeros(cap, np.uint32), "ranges": np.zeros((tx * ty, 2), np.uint32),
         "rgba_f32": np.zeros((height, width, 4), np.float32),
     }
-    d = DebugFrame(*[_ptr(out[k]) for k in ["visible", "radius", "rect", "depth", "uv", "q", "values"]], cap,
-                   _ptr(out["ranges"]), _ptr(out["rgba_f32"]))
+    lists = sort_mode != SORT_SLICED
+    if not lists:
+        out["values"] = np.zeros(0, np.uint32)
+        out["ranges"] = np.zeros((0, 2), np.uint32)
+    d = DebugFrame(*[_ptr(out[k]) for k in ["visible", "radius", "rect", "depth", "uv", "q"]],
+                   _ptr(out["values"]) if lists else None, cap, _ptr(out["ranges"]) if lists else None,
+                   _ptr(out["rgba_f32"]))
     pairs = ctypes.c_uint64()
     _check(load_library().tigas_debug_render(scene.handle, ctypes.byref(make_pose(pose)),
                                              ctypes.byref(make_intrinsics(intr)), width, height, sort_mode,
                                              ctypes.byref(d), ctypes.byref(pairs)))
     P = int(pairs.value)
-    if P > cap:
+    if lists and P > cap:
         return debug_render(scene, pose, intr, width, height, sort_mode, P)
     out["pairs"] = P
-    out["values"] = out["values"][:P]
+    if lists:
+        out["values"] = out["values"][:P]
     return out
 
 

@@ -122,6 +122,33 @@ def test_sort_modes_give_identical_frames(h1):
     assert np.array_equal(a["rgba_f32"], b["rgba_f32"])
 
 
+# ------------------------------------------------- sliced schedule = full
+
+
+@pytest.mark.parametrize("k,w,h", [(0, 320, 240), (150, 320, 240), (299, 97, 61), (40, 1000, 3)])
+def test_sliced_schedule_gives_the_full_list_frame(h1, s1, k, w, h):
+    pose = synth.config_trajectory(1)[k]
+    K = synth.default_intrinsics(w, h)
+    full = tg.debug_render(h1, pose, K, w, h, sort_mode=tg.SORT_DEPTH_FIRST)
+    sliced = tg.debug_render(h1, pose, K, w, h, sort_mode=tg.SORT_SLICED)
+    assert np.array_equal(full["rgba_f32"], sliced["rgba_f32"])
+    assert np.array_equal(full["visible"], sliced["visible"]) and np.array_equal(full["rect"], sliced["rect"])
+    assert sliced["pairs"] <= full["pairs"]
+    parity.assert_colour(sliced["rgba_f32"], oracle.render(oracle.preprocess(s1, pose, K, w, h)))
+
+
+def test_sliced_debug_render_has_no_whole_lists(h1):
+    with pytest.raises(tg.TigasError):
+        tg.load_library()
+        from paper_2605_08699_b300 import tigas as tb
+        import ctypes
+        d = tb.DebugFrame(None, None, None, None, None, None, 1, 4, 1, None)
+        pairs = ctypes.c_uint64()
+        tb._check(tg.load_library().tigas_debug_render(h1.handle, ctypes.byref(tb.make_pose(synth.BASE_POSE)),
+                                                       ctypes.byref(tb.make_intrinsics(K1)), 320, 240,
+                                                       tg.SORT_SLICED, ctypes.byref(d), ctypes.byref(pairs)))
+
+
 # ---------------------------------------------------------------- colour
 
 
