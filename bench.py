@@ -162,15 +162,14 @@ def cpu_baseline(scene, poses, width, height, budget_s: float = 15.0) -> dict:
 
 def roofline(stage_ms: dict, per_step: dict, peaks: dict, clocks: dict, steps: int) -> tuple[dict, dict]:
     """Achieved rate of every stage and the roofline entry of the dominant one.
-    Algorithmic work per launch set (see the design notes):
+    Algorithmic work per launch set of the sliced schedule (see the design notes):
       preprocess  12 B per (Gaussian, view) + (A - 12) B per Gaussian + 52 B per kept entry
       depth_sort  4 passes x 16 B per entry
-      scan        8 B per entry
-      emit        16 B per kept entry + 8 B per pair
-      pair_sort   passes x 16 B per pair
-      ranges      4 B per pair + 8 B per tile
-      blend       FP32: 14 flops per list entry evaluated (power, alpha, transmittance)
-                  + 8 flops per contribution; counted as 15 per evaluation"""
+      scan        28 B per kept entry (slice count: order, tiles, rect, count; scan: 8 B)
+      emit        20 B per kept entry + 8 B per emitted pair
+      pair_sort   passes x 16 B per emitted pair
+      ranges      8 B per tile per slice
+      blend       FP32 flops: 8.5 per list entry evaluated + 9 per blended entry"""
     hbm = peaks["hbm_gbs"]
     mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
     fp32_peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
@@ -178,10 +177,10 @@ def roofline(stage_ms: dict, per_step: dict, peaks: dict, clocks: dict, steps: i
     bytes_per = {
         "preprocess": w["entries"] * 12 + w["gaussians"] * (w["attr_bytes"] - 12) + w["kept"] * 52,
         "depth_sort": w["entries"] * 4 * 16,
-        "scan": w["entries"] * 8,
-        "emit": w["kept"] * 16 + w["pairs"] * 8,
+        "scan": w["kept"] * 28,
+        "emit": w["kept"] * 20 + w["pairs"] * 8,
         "pair_sort": w["pairs"] * w["sort_passes"] * 16,
-        "ranges": w["pairs"] * 4 + w["tiles"] * 8,
+        "ranges": w["tiles"] * w["slices"] * 8,
     }
     stages = {}
     for name, st in stage_ms.items():
@@ -189,7 +188,7 @@ def roofline(stage_ms: dict, per_step: dict, peaks: dict, clocks: dict, steps: i
             continue
         ms = st["ms"] / st["calls"]
         if name == "blend":
-            fl = w["evals"] * 15.0
+            fl = w["evals"] * 8.5 + w["contribs"] * 9.0
             ach = fl / (ms * 1e-3) / 1e12
             stages[name] = {"ms": ms, "bound": "alu", "achieved": ach, "peak": fp32_peak_tflops,
                             "unit": "TFLOP/s", "frac": ach / fp32_peak_tflops, "work": fl}
@@ -234,18 +233,14 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
         step(s)
     torch.cuda.synchronize()
 
-    # per-step workload (untimed): pairs, kept entries, blend evaluations
-    agg = {"pairs": 0, "kept": 0, "evals": 0, "fetched": 0, "sort_passes": 0}
-    for v in range(V):
-        stt = tg.render_ex(h16, trajs[v][(args.warmup * 7 + v) % 300], K, W, H, out_rgba8=outs[v])
-        for k in ("pairs", "evals", "fetched"):
-            agg[k] += stt["n_" + k] if k == "pairs" else stt["blend_" + k]
-        agg["kept"] += stt["n_visible"]
-        agg["sort_passes"] = stt["sort_passes"]
+    # per-step workload (untimed): one launch set of the same kind as a timed step
+    st0 = tg.render_batch(h16, [trajs[v][(args.warmup * 7 + v) % len(trajs[v])] for v in range(V)], [K] * V,
+                          [W] * V, [H] * V, outs, stream=stream, sort_mode=tg.SORT_SLICED)
     TX, TY = (W + 15) // 16, (H + 15) // 16
-    bits = max(1, math.ceil(math.log2(V * TX * TY)))
-    agg["sort_passes"] = (bits + 7) // 8        # the batch sorts global tile ids of all V views
-    per_step = {**agg, "entries": V * scene.n, "gaussians": scene.n, "attr_bytes": 124, "tiles": V * TX * TY}
+    per_step = {"pairs": st0["n_pairs"], "kept": st0["n_visible"], "evals": st0["blend_evals"],
+                "fetched": st0["blend_fetched"], "contribs": st0["blend_contribs"], "sort_passes": st0["sort_passes"],
+                "entries": V * scene.n, "gaussians": scene.n, "attr_bytes": 124, "tiles": V * TX * TY,
+                "slices": 8}
 
     # ---- timed region: device outputs, CUDA events on the launching stream
     tg.profile_read(reset=True)
@@ -440,11 +435,12 @@ def main(argv=None) -> int:
             "config": {"workload": WORKLOAD, "gaussians": args.gaussians, "width": args.width, "height": args.height,
                        "views_per_step": args.batch, "storage": "fp16 (positions fp32)", "sh_degree": 3,
                        "path": "tigas_render_batch (fused launch set per step)",
-                       "l2": "inputs larger than L2: 384 MB resident scene, >1 GB of pair buffers per step",
+                       "l2": "inputs larger than L2 (126 MB): 384 MB resident scene, 1.2 GB of per-view splat arrays per step",
                        "parallelism": f"replicas x{world}"},
             "latency_ms": {"p50_step": round(float(np.percentile(steps_ms, 50)), 3),
                            "p99_step": round(float(np.percentile(steps_ms, 99)), 3),
                            "note": "host time of one synchronous launch set of views_per_step frames"},
+            "schedule": "depth-sliced (8 nearest-first slices, tiles that stopped are dropped)",
             "served_fp16": r["serving"], "plain_fp32": r["plain_fp32"],
             "roofline": roof, "stages": stages, "per_step": {k: int(v) for k, v in r["per_step"].items()},
             "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": int(r["launches"]), "clocks": r["clocks"],

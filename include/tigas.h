@@ -131,6 +131,7 @@ typedef struct {
     uint32_t sort_passes;        /* radix passes over the pair array */
     uint64_t blend_evals;        /* list entries evaluated, summed over pixels, up to each pixel's stop */
     uint64_t blend_fetched;      /* list entries staged into shared memory by the blend */
+    uint64_t blend_contribs;     /* evaluations that blended (alpha >= 1/255, pixel not stopped) */
 } tigas_frame_stats;
 
 /* tigas_render with options.
@@ -154,6 +155,12 @@ tigas_status tigas_render_ex(tigas_scene* scene, const tigas_pose* pose, const t
 tigas_status tigas_render_batch(tigas_scene* scene, int n_views, const tigas_pose* poses,
                                 const tigas_intrinsics* intrs, const int* widths, const int* heights,
                                 uint8_t* const* outs, void* cuda_stream);
+
+/* tigas_render_batch with a schedule (TIGAS_SORT_*) and statistics summed
+ * over the views (stats may be NULL). */
+tigas_status tigas_render_batch_ex(tigas_scene* scene, int n_views, const tigas_pose* poses,
+                                   const tigas_intrinsics* intrs, const int* widths, const int* heights,
+                                   uint8_t* const* outs, void* cuda_stream, int sort_mode, tigas_frame_stats* stats);
 
 /* ------------------------------------------------------------------ debug */
 

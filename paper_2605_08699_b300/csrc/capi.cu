@@ -140,10 +140,11 @@ Status do_render(Scene* scene, int V, const tigas_pose* poses, const tigas_intri
         stats->n_pairs = res.pairs;
         stats->n_tiles = res.total_tiles;
         stats->sort_passes = (uint32_t)res.sort_passes;
-        unsigned long long cnt[2] = {0, 0};
+        unsigned long long cnt[3] = {0, 0, 0};
         if (res.d_counters) TIGAS_CUDA_TRY(cudaMemcpy(cnt, res.d_counters, sizeof(cnt), cudaMemcpyDeviceToHost));
         stats->blend_evals = cnt[0];
         stats->blend_fetched = cnt[1];
+        stats->blend_contribs = cnt[2];
     }
     if (dbg) {
         const uint32_t n = scene->view.n;
@@ -314,6 +315,21 @@ TIGAS_API tigas_status tigas_render_batch(tigas_scene* scene, int n_views, const
     SceneGuard sg(reinterpret_cast<Scene*>(scene));
     Status st = do_render(sg.s, n_views, poses, intrs, widths, heights, outs, nullptr, (cudaStream_t)cuda_stream,
                           TIGAS_SORT_SLICED, nullptr, nullptr, nullptr);
+    return st.ok() ? TIGAS_OK : fail(st);
+}
+
+TIGAS_API tigas_status tigas_render_batch_ex(tigas_scene* scene, int n_views, const tigas_pose* poses,
+                                             const tigas_intrinsics* intrs, const int* widths, const int* heights,
+                                             uint8_t* const* outs, void* cuda_stream, int sort_mode,
+                                             tigas_frame_stats* stats) {
+    set_error("");
+    if (!poses || !intrs || !widths || !heights || !outs) return fail(TIGAS_ERR_INVALID, "null argument");
+    if (n_views < 1 || n_views > kMaxViews) return fail(TIGAS_ERR_INVALID, "n_views out of 1..64");
+    for (int v = 0; v < n_views; ++v)
+        if (!outs[v]) return fail(TIGAS_ERR_INVALID, "null output buffer");
+    SceneGuard sg(reinterpret_cast<Scene*>(scene));
+    Status st = do_render(sg.s, n_views, poses, intrs, widths, heights, outs, nullptr, (cudaStream_t)cuda_stream,
+                          sort_mode, stats, nullptr, nullptr);
     return st.ok() ? TIGAS_OK : fail(st);
 }
 

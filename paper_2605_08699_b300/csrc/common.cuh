@@ -103,9 +103,11 @@ struct ViewParams {
 };
 
 // Per-view preprocess output, indexed by entry e = view * n + gaussian.
+// The blend evaluates alpha = min(0.99, 2^(a' dx^2 + b' dx dy + c' dy^2 + log2 o))
+// = min(0.99, o exp(power)).
 struct SplatArrays {
     float4* geom;         // (u, v, a', b')   a' = -A/2 log2e, b' = -B log2e
-    float4* appear;       // (c', opacity, r, g)  c' = -C/2 log2e
+    float4* appear;       // (c', log2(opacity), r, g)  c' = -C/2 log2e
     float* blue;          // b
     uint32_t* depth_key;  // float bits of view z, 0xFFFFFFFF when culled
     uint32_t* tiles;      // tiles touched (0 when culled)

@@ -57,8 +57,8 @@ Status launch_ranges(const K* keys, uint64_t n_cap, const uint64_t* d_n, int shi
 
 // K6: per-tile front-to-back blend of every view's tiles (grid = total_tiles).
 // values hold entry indices < n_entries.  bg: host RGB.
-// counters: optional device [evals, fetched]: list entries evaluated per pixel up
-// to its stop, and entries staged into shared memory.
+// counters: optional device [evals, fetched, blends]: list entries evaluated per
+// pixel up to its stop, entries staged into shared memory, entries blended.
 Status launch_blend(const uint2* ranges, const uint32_t* values, const SplatArrays& sp,
                     const ViewParams* views, int V, uint32_t total_tiles, uint32_t n_entries,
                     const float* bg, unsigned long long* counters, cudaStream_t st);

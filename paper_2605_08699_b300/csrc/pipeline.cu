@@ -263,7 +263,7 @@ Status render_frame(Scene* scene, FrameRequest& req, RenderContext& ctx, cudaStr
     ctx.fixed.reset();
     ViewParams* d_views = ctx.fixed.take<ViewParams>(kMaxViews);
     uint64_t* d_total = ctx.fixed.take<uint64_t>(2);
-    unsigned long long* d_counters = ctx.fixed.take<unsigned long long>(2);
+    unsigned long long* d_counters = ctx.fixed.take<unsigned long long>(4);
     uint32_t* d_flags = ctx.fixed.take<uint32_t>(2);
     uint32_t* d_visible = ctx.fixed.take<uint32_t>(kMaxViews);
     SplatArrays sp{};
@@ -289,7 +289,7 @@ Status render_frame(Scene* scene, FrameRequest& req, RenderContext& ctx, cudaStr
     TIGAS_CUDA_TRY(cudaMemcpyAsync(d_views, ctx.h_views, sizeof(ViewParams) * V, cudaMemcpyHostToDevice, st));
     TIGAS_CUDA_TRY(cudaMemsetAsync(d_flags, 0, sizeof(uint32_t) * 2, st));
     if (sp.q_dbg) TIGAS_CUDA_TRY(cudaMemsetAsync(sp.q_dbg, 0, E * 4, st));
-    if (req.want_counters) TIGAS_CUDA_TRY(cudaMemsetAsync(d_counters, 0, sizeof(unsigned long long) * 2, st));
+    if (req.want_counters) TIGAS_CUDA_TRY(cudaMemsetAsync(d_counters, 0, sizeof(unsigned long long) * 4, st));
 
     // K1
     TIGAS_TRY(mark(kStPreprocess, true));
@@ -397,11 +397,11 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
 
     // ---- per-entry and per-pixel workspace
     const size_t presort_words = radix_tmp_words(E);
-    const size_t scan_words = scan_tmp_words(E);
+    const size_t scan_words = scan_tmp_words(E + 1);
     const size_t tmp_words = presort_words > scan_words ? presort_words : scan_words;
     size_t fixed_bytes = sizeof(ViewParams) * kMaxViews + 80 * 256;
     fixed_bytes += E * (16 + 16 + 4 + 4 + 4 + 8 + (req.want_q ? 4 : 0));
-    fixed_bytes += E * 4 * 4 + E * 4 * 2;                 // depth sort buffers, counts, offsets
+    fixed_bytes += E * 4 * 4 + E * 4 * 2 + 8 + E * 8;     // depth sort buffers, counts, offsets, rects
     fixed_bytes += tmp_words * 4;
     fixed_bytes += (sizeof(uint2) + 4) * (size_t)total_tiles + done_words * 4;
     fixed_bytes += total_pix * 16 + sizeof(uint64_t) * kMaxViews;
@@ -409,7 +409,7 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     ctx.fixed.reset();
     ViewParams* d_views = ctx.fixed.take<ViewParams>(kMaxViews);
     uint64_t* d_total = ctx.fixed.take<uint64_t>(2);
-    unsigned long long* d_counters = ctx.fixed.take<unsigned long long>(2);
+    unsigned long long* d_counters = ctx.fixed.take<unsigned long long>(4);
     uint32_t* d_flags = ctx.fixed.take<uint32_t>(2);
     uint32_t* d_visible = ctx.fixed.take<uint32_t>(kMaxViews);
     uint32_t* d_misc = ctx.fixed.take<uint32_t>(4);       // [n_active, work counter]
@@ -426,8 +426,9 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     uint32_t* pv_alt = ctx.fixed.take<uint32_t>(E);
     uint32_t* pk = ctx.fixed.take<uint32_t>(E);
     uint32_t* order = ctx.fixed.take<uint32_t>(E);
-    uint32_t* counts = ctx.fixed.take<uint32_t>(E);
-    uint32_t* offsets = ctx.fixed.take<uint32_t>(E);
+    uint32_t* counts = ctx.fixed.take<uint32_t>(E + 1);
+    uint32_t* offsets = ctx.fixed.take<uint32_t>(E + 1);
+    uint2* rect_sorted = ctx.fixed.take<uint2>(E);
     uint32_t* tmp = ctx.fixed.take<uint32_t>(tmp_words);
     uint2* ranges = ctx.fixed.take<uint2>(total_tiles);
     uint32_t* active = ctx.fixed.take<uint32_t>(total_tiles);
@@ -442,7 +443,7 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     TIGAS_CUDA_TRY(cudaMemsetAsync(d_flags, 0, sizeof(uint32_t) * 2, st));
     TIGAS_CUDA_TRY(cudaMemsetAsync(done, 0, done_words * 4, st));
     if (sp.q_dbg) TIGAS_CUDA_TRY(cudaMemsetAsync(sp.q_dbg, 0, E * 4, st));
-    if (req.want_counters) TIGAS_CUDA_TRY(cudaMemsetAsync(d_counters, 0, sizeof(unsigned long long) * 2, st));
+    if (req.want_counters) TIGAS_CUDA_TRY(cudaMemsetAsync(d_counters, 0, sizeof(unsigned long long) * 4, st));
 
     TIGAS_TRY(mark(kStPreprocess, true));
     TIGAS_TRY(launch_preprocess(scene->view, d_views, V, sp, d_visible, st));
@@ -457,6 +458,9 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     TIGAS_CUDA_TRY(cudaStreamSynchronize(st));
     uint64_t K = 0;
     for (int v = 0; v < V; ++v) K += ctx.h_misc[v];
+    TIGAS_TRY(mark(kStScan, true));
+    TIGAS_TRY(launch_permute_rects(order, K, sp, n, rect_sorted, st));
+    TIGAS_TRY(mark(kStScan, false));
 
     // geometric slice ends: K / 64 ... K
     uint64_t ends[kMaxSlices];
@@ -472,8 +476,10 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
         const uint64_t b = ends[i] > a ? ends[i] : a;
         if (b == a) continue;
         TIGAS_TRY(mark(kStScan, true));
-        TIGAS_TRY(launch_count_slice(order, a, b, sp, d_views, V, n, done, counts, st));
-        TIGAS_TRY(launch_scan_u32(counts, nullptr, offsets, b - a, d_total, tmp, st));
+        TIGAS_TRY(launch_count_slice(rect_sorted, a, b, d_views, V, done, counts, st));
+        // one extra zero count makes offsets[b - a] the slice total
+        TIGAS_CUDA_TRY(cudaMemsetAsync(counts + (b - a), 0, sizeof(uint32_t), st));
+        TIGAS_TRY(launch_scan_u32(counts, nullptr, offsets, b - a + 1, d_total, tmp, st));
         TIGAS_TRY(mark(kStScan, false));
         TIGAS_CUDA_TRY(cudaMemcpyAsync(ctx.h_total, d_total, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
         TIGAS_CUDA_TRY(cudaStreamSynchronize(st));
@@ -492,7 +498,8 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
             uint32_t* vals_c = ctx.pairs.take<uint32_t>(P);
             uint32_t* stmp = ctx.pairs.take<uint32_t>(sort_words);
             TIGAS_TRY(mark(kStEmit, true));
-            TIGAS_TRY(launch_emit_slice(order, a, b, offsets, sp, d_views, V, n, done, keys_a, vals_a, P, d_flags, st));
+            TIGAS_TRY(launch_emit_slice(order, rect_sorted, a, b, offsets, d_views, V, done, keys_a, vals_a, P, d_flags,
+                                        st));
             TIGAS_TRY(mark(kStEmit, false));
             TIGAS_TRY(mark(kStPairSort, true));
             TIGAS_TRY(radix_sort<uint32_t>(keys_a, vals_a, keys_b, vals_b, keys_c, vals_c, P, nullptr, 0, tile_bits,

@@ -245,7 +245,8 @@ k_preprocess(SceneView scene, const ViewParams* __restrict__ views_g, int V, Spl
                     if (out.q_dbg) out.q_dbg[e] = q;
                     if (tiles > 0) {
                         out.geom[e] = make_float4(u, vv, -0.5f * kLog2e * conA, -kLog2e * conB);
-                        reinterpret_cast<float2*>(out.appear)[2 * e] = make_float2(-0.5f * kLog2e * conC, a.o);
+                        reinterpret_cast<float2*>(out.appear)[2 * e] =
+                            make_float2(-0.5f * kLog2e * conC, log2f(a.o));
                         out.rect[e] = make_uint2((uint32_t)xlo | ((uint32_t)ylo << 16),
                                                  (uint32_t)xhi | ((uint32_t)yhi << 16));
                         out.depth_key[e] = __float_as_uint(pz);

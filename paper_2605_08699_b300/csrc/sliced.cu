@@ -59,11 +59,40 @@ __device__ inline bool tile_done(const uint32_t* __restrict__ done, uint32_t t) 
     return (done[t >> 5] >> (t & 31)) & 1u;
 }
 
+// Bits of bitmap word w that lie in [lo, hi).
+__device__ inline uint32_t word_mask(uint32_t w, uint32_t lo, uint32_t hi) {
+    const uint32_t wlo = w << 5;
+    const uint32_t a = lo > wlo ? lo - wlo : 0u;
+    const uint32_t b = hi - wlo < 32u ? hi - wlo : 32u;
+    const uint32_t upto_b = b >= 32u ? 0xFFFFFFFFu : ((1u << b) - 1u);
+    return upto_b & ~((1u << a) - 1u);
+}
+
+// Not-done tiles among tile ids [lo, hi).
+__device__ inline uint32_t count_running(const uint32_t* __restrict__ done, uint32_t lo, uint32_t hi) {
+    uint32_t c = 0;
+    for (uint32_t w = lo >> 5; (w << 5) < hi; ++w) c += __popc(~done[w] & word_mask(w, lo, hi));
+    return c;
+}
+
+// Depth-ordered rectangles of the kept entries, packed with their view:
+//   x = x_lo | x_hi << 10 | view << 20,  y = y_lo | y_hi << 10   (10 bits: TX, TY <= 512)
+__global__ void __launch_bounds__(256)
+k_permute_rects(const uint32_t* __restrict__ order, uint64_t K, SplatArrays sp, uint32_t n_per_view,
+                uint2* __restrict__ rect_sorted) {
+    const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const uint32_t e = order[k];
+    const uint2 r = sp.rect[e];
+    const uint32_t v = e / n_per_view;
+    rect_sorted[k] = make_uint2((r.x & 0x3FFu) | ((r.y & 0x3FFu) << 10) | (v << 20),
+                                ((r.x >> 16) & 0x3FFu) | (((r.y >> 16) & 0x3FFu) << 10));
+}
+
 // counts[k - a] = tiles of entry order[k]'s rectangle that are not done.
 __global__ void __launch_bounds__(256)
-k_count_slice(const uint32_t* __restrict__ order, uint64_t a, uint64_t b, SplatArrays sp,
-              const ViewParams* __restrict__ views_g, int V, uint32_t n_per_view, const uint32_t* __restrict__ done,
-              uint32_t* __restrict__ counts) {
+k_count_slice(const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b, const ViewParams* __restrict__ views_g,
+              int V, const uint32_t* __restrict__ done, uint32_t* __restrict__ counts) {
     __shared__ uint32_t s_tb[kMaxViews], s_tx[kMaxViews];
     for (int k = threadIdx.x; k < V; k += blockDim.x) {
         s_tb[k] = views_g[k].tile_base;
@@ -72,24 +101,21 @@ k_count_slice(const uint32_t* __restrict__ order, uint64_t a, uint64_t b, SplatA
     __syncthreads();
     const uint64_t k = a + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= b) return;
-    const uint32_t e = order[k];
+    const uint2 r = rect_sorted[k];
+    const uint32_t xlo = r.x & 0x3FFu, xhi = (r.x >> 10) & 0x3FFu, v = r.x >> 20;
+    const uint32_t ylo = r.y & 0x3FFu, yhi = (r.y >> 10) & 0x3FFu;
     uint32_t c = 0;
-    if (sp.tiles[e]) {
-        const uint2 r = sp.rect[e];
-        const uint32_t xlo = r.x & 0xFFFFu, ylo = r.x >> 16, xhi = r.y & 0xFFFFu, yhi = r.y >> 16;
-        const uint32_t v = e / n_per_view;
-        for (uint32_t ty = ylo; ty < yhi; ++ty) {
-            const uint32_t row = s_tb[v] + ty * s_tx[v];
-            for (uint32_t tx = xlo; tx < xhi; ++tx) c += tile_done(done, row + tx) ? 0u : 1u;
-        }
+    for (uint32_t ty = ylo; ty < yhi; ++ty) {
+        const uint32_t row = s_tb[v] + ty * s_tx[v];
+        c += count_running(done, row + xlo, row + xhi);
     }
     counts[k - a] = c;
 }
 
 // Pairs (tile, entry) of the slice for tiles not done, in depth order.
 __global__ void __launch_bounds__(256)
-k_emit_slice(const uint32_t* __restrict__ order, uint64_t a, uint64_t b, const uint32_t* __restrict__ offsets,
-             SplatArrays sp, const ViewParams* __restrict__ views_g, int V, uint32_t n_per_view,
+k_emit_slice(const uint32_t* __restrict__ order, const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b,
+             const uint32_t* __restrict__ offsets, const ViewParams* __restrict__ views_g, int V,
              const uint32_t* __restrict__ done, uint32_t* __restrict__ keys, uint32_t* __restrict__ values,
              uint64_t pair_cap, uint32_t* __restrict__ overflow) {
     __shared__ uint32_t s_tb[kMaxViews], s_tx[kMaxViews];
@@ -100,24 +126,28 @@ k_emit_slice(const uint32_t* __restrict__ order, uint64_t a, uint64_t b, const u
     __syncthreads();
     const uint64_t k = a + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= b) return;
+    uint32_t c = offsets[k - a + 1] - offsets[k - a];
+    if (c == 0) return;
     const uint32_t e = order[k];
-    if (!sp.tiles[e]) return;
-    const uint2 r = sp.rect[e];
-    const uint32_t xlo = r.x & 0xFFFFu, ylo = r.x >> 16, xhi = r.y & 0xFFFFu, yhi = r.y >> 16;
-    const uint32_t v = e / n_per_view;
+    const uint2 r = rect_sorted[k];
+    const uint32_t xlo = r.x & 0x3FFu, xhi = (r.x >> 10) & 0x3FFu, v = r.x >> 20;
+    const uint32_t ylo = r.y & 0x3FFu, yhi = (r.y >> 10) & 0x3FFu;
     uint64_t pos = offsets[k - a];
     for (uint32_t ty = ylo; ty < yhi; ++ty) {
-        const uint32_t row = s_tb[v] + ty * s_tx[v];
-        for (uint32_t tx = xlo; tx < xhi; ++tx) {
-            const uint32_t t = row + tx;
-            if (tile_done(done, t)) continue;
-            if (pos < pair_cap) {
-                keys[pos] = t;
-                values[pos] = e;
-            } else {
-                atomicOr(overflow, 1u);
+        const uint32_t lo = s_tb[v] + ty * s_tx[v] + xlo, hi = lo + (xhi - xlo);
+        for (uint32_t w = lo >> 5; (w << 5) < hi; ++w) {
+            uint32_t m = ~done[w] & word_mask(w, lo, hi);
+            while (m) {
+                const uint32_t t = (w << 5) + (uint32_t)(__ffs(m) - 1);
+                m &= m - 1;
+                if (pos < pair_cap) {
+                    keys[pos] = t;
+                    values[pos] = e;
+                } else {
+                    atomicOr(overflow, 1u);
+                }
+                ++pos;
             }
-            ++pos;
         }
     }
 }
@@ -165,23 +195,28 @@ Status launch_init_state(const ViewParams* views, int V, uint32_t total_tiles, c
     return {};
 }
 
-Status launch_count_slice(const uint32_t* order, uint64_t a, uint64_t b, const SplatArrays& sp,
-                          const ViewParams* views, int V, uint32_t n_per_view, const uint32_t* done, uint32_t* counts,
-                          cudaStream_t st) {
-    if (b <= a) return {};
-    k_count_slice<<<(unsigned)((b - a + 255) / 256), 256, 0, st>>>(order, a, b, sp, views, V, n_per_view, done,
-                                                                    counts);
+Status launch_permute_rects(const uint32_t* order, uint64_t K, const SplatArrays& sp, uint32_t n_per_view,
+                            uint2* rect_sorted, cudaStream_t st) {
+    if (K == 0) return {};
+    k_permute_rects<<<(unsigned)((K + 255) / 256), 256, 0, st>>>(order, K, sp, n_per_view, rect_sorted);
     TIGAS_LAUNCHED();
     return {};
 }
 
-Status launch_emit_slice(const uint32_t* order, uint64_t a, uint64_t b, const uint32_t* offsets,
-                         const SplatArrays& sp, const ViewParams* views, int V, uint32_t n_per_view,
-                         const uint32_t* done, uint32_t* keys, uint32_t* values, uint64_t pair_cap, uint32_t* overflow,
-                         cudaStream_t st) {
+Status launch_count_slice(const uint2* rect_sorted, uint64_t a, uint64_t b, const ViewParams* views, int V,
+                          const uint32_t* done, uint32_t* counts, cudaStream_t st) {
     if (b <= a) return {};
-    k_emit_slice<<<(unsigned)((b - a + 255) / 256), 256, 0, st>>>(order, a, b, offsets, sp, views, V, n_per_view,
-                                                                   done, keys, values, pair_cap, overflow);
+    k_count_slice<<<(unsigned)((b - a + 255) / 256), 256, 0, st>>>(rect_sorted, a, b, views, V, done, counts);
+    TIGAS_LAUNCHED();
+    return {};
+}
+
+Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64_t a, uint64_t b,
+                         const uint32_t* offsets, const ViewParams* views, int V, const uint32_t* done,
+                         uint32_t* keys, uint32_t* values, uint64_t pair_cap, uint32_t* overflow, cudaStream_t st) {
+    if (b <= a) return {};
+    k_emit_slice<<<(unsigned)((b - a + 255) / 256), 256, 0, st>>>(order, rect_sorted, a, b, offsets, views, V, done,
+                                                                   keys, values, pair_cap, overflow);
     TIGAS_LAUNCHED();
     return {};
 }

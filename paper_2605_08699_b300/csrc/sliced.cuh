@@ -10,16 +10,19 @@ namespace tigas {
 Status launch_init_state(const ViewParams* views, int V, uint32_t total_tiles, const uint64_t* pix_base,
                          float4* state, const float* bg, cudaStream_t st);
 
-// counts[k - a]: not-done tiles in the rectangle of entry order[k], k in [a, b).
-Status launch_count_slice(const uint32_t* order, uint64_t a, uint64_t b, const SplatArrays& sp,
-                          const ViewParams* views, int V, uint32_t n_per_view, const uint32_t* done, uint32_t* counts,
-                          cudaStream_t st);
+// rect_sorted[k] = packed rectangle and view of entry order[k], k < K (kept entries).
+Status launch_permute_rects(const uint32_t* order, uint64_t K, const SplatArrays& sp, uint32_t n_per_view,
+                            uint2* rect_sorted, cudaStream_t st);
 
-// (tile, entry) pairs of entries [a, b) for tiles not done, at offsets[k - a].
-Status launch_emit_slice(const uint32_t* order, uint64_t a, uint64_t b, const uint32_t* offsets,
-                         const SplatArrays& sp, const ViewParams* views, int V, uint32_t n_per_view,
-                         const uint32_t* done, uint32_t* keys, uint32_t* values, uint64_t pair_cap, uint32_t* overflow,
-                         cudaStream_t st);
+// counts[k - a]: not-done tiles in the rectangle of depth-ordered entry k, k in [a, b).
+Status launch_count_slice(const uint2* rect_sorted, uint64_t a, uint64_t b, const ViewParams* views, int V,
+                          const uint32_t* done, uint32_t* counts, cudaStream_t st);
+
+// (tile, entry) pairs of entries [a, b) for tiles not done, at offsets[k - a]
+// (offsets: exclusive scan of counts with b - a + 1 values).
+Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64_t a, uint64_t b,
+                         const uint32_t* offsets, const ViewParams* views, int V, const uint32_t* done,
+                         uint32_t* keys, uint32_t* values, uint64_t pair_cap, uint32_t* overflow, cudaStream_t st);
 
 // Tile ranges of the slice's sorted keys, and the list of tiles with pairs
 // that are not done (*n_active entries of `active`, zeroed here).

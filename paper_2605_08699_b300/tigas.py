@@ -26,7 +26,8 @@ EXPORTS = ["tigas_scene_load", "tigas_scene_free", "tigas_scene_bytes", "tigas_r
            "tigas_render_batch", "tigas_debug_render", "tigas_sort_pairs_u64", "tigas_server_create",
            "tigas_server_destroy", "tigas_server_submit", "tigas_server_poll", "tigas_last_error",
            "tigas_version", "tigas_kernel_launches", "tigas_profile_enable", "tigas_profile_read",
-           "tigas_sort_pairs_u64_noalloc"]
+           "tigas_sort_pairs_u64_noalloc",
+           "tigas_render_batch_ex"]
 
 STAGES = ["preprocess", "depth_sort", "scan", "emit", "pair_sort", "ranges", "blend", "frame"]
 
@@ -54,7 +55,8 @@ class SceneDesc(ctypes.Structure):
 
 class FrameStats(ctypes.Structure):
     _fields_ = [("n_visible", ctypes.c_uint64), ("n_pairs", ctypes.c_uint64), ("n_tiles", ctypes.c_uint32),
-                ("sort_passes", ctypes.c_uint32), ("blend_evals", ctypes.c_uint64), ("blend_fetched", ctypes.c_uint64)]
+                ("sort_passes", ctypes.c_uint32), ("blend_evals", ctypes.c_uint64), ("blend_fetched", ctypes.c_uint64),
+                ("blend_contribs", ctypes.c_uint64)]
 
 
 class DebugFrame(ctypes.Structure):
@@ -95,6 +97,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "tigas_render_ex": (st, [P, ctypes.POINTER(Pose), ctypes.POINTER(Intrinsics), i, i, P, P, P, i,
                                  ctypes.POINTER(FrameStats)]),
         "tigas_render_batch": (st, [P, i, ctypes.POINTER(Pose), ctypes.POINTER(Intrinsics), P, P, P, P]),
+        "tigas_render_batch_ex": (st, [P, i, ctypes.POINTER(Pose), ctypes.POINTER(Intrinsics), P, P, P, P, i,
+                                       ctypes.POINTER(FrameStats)]),
         "tigas_debug_render": (st, [P, ctypes.POINTER(Pose), ctypes.POINTER(Intrinsics), i, i, i,
                                     ctypes.POINTER(DebugFrame), ctypes.POINTER(ctypes.c_uint64)]),
         "tigas_sort_pairs_u64": (st, [P, P, P, P, ctypes.c_uint64, i, i, P]),
@@ -261,29 +265,42 @@ def render(scene: SceneHandle, pose, intr, width: int, height: int, out=None):
     return out
 
 
+def _stats_dict(stats: "FrameStats") -> dict:
+    return {"n_visible": stats.n_visible, "n_pairs": stats.n_pairs, "n_tiles": stats.n_tiles,
+            "sort_passes": stats.sort_passes, "blend_evals": stats.blend_evals, "blend_fetched": stats.blend_fetched,
+            "blend_contribs": stats.blend_contribs}
+
+
 def render_ex(scene: SceneHandle, pose, intr, width: int, height: int, out_rgba8=None, out_rgba_f32=None,
-              stream=None, sort_mode: int = SORT_DEPTH_FIRST) -> dict:
+              stream=None, sort_mode: int = SORT_SLICED) -> dict:
     """tigas_render_ex; returns the frame statistics."""
     stats = FrameStats()
     _check(load_library().tigas_render_ex(scene.handle, ctypes.byref(make_pose(pose)),
                                           ctypes.byref(make_intrinsics(intr)), width, height, _ptr(out_rgba8),
                                           _ptr(out_rgba_f32), _stream(stream), sort_mode, ctypes.byref(stats)))
-    return {"n_visible": stats.n_visible, "n_pairs": stats.n_pairs, "n_tiles": stats.n_tiles,
-            "sort_passes": stats.sort_passes, "blend_evals": stats.blend_evals, "blend_fetched": stats.blend_fetched}
+    return _stats_dict(stats)
 
 
 def render_batch(scene: SceneHandle, poses: Sequence, intrs: Sequence, widths: Sequence[int],
-                 heights: Sequence[int], outs: Sequence, stream=None) -> None:
-    """tigas_render_batch: all views in one fused launch set."""
+                 heights: Sequence[int], outs: Sequence, stream=None, sort_mode: int | None = None):
+    """tigas_render_batch: all views in one fused launch set.  With sort_mode
+    given, tigas_render_batch_ex is called and its statistics returned."""
     V = len(poses)
     P = (Pose * V)(*[make_pose(p) for p in poses])
     K = (Intrinsics * V)(*[make_intrinsics(k) for k in intrs])
     W = (ctypes.c_int * V)(*widths)
     H = (ctypes.c_int * V)(*heights)
     O = (ctypes.c_void_p * V)(*[_ptr(o) for o in outs])
+    if sort_mode is not None:
+        stats = FrameStats()
+        _check(load_library().tigas_render_batch_ex(scene.handle, V, P, K, ctypes.cast(W, ctypes.c_void_p),
+                                                    ctypes.cast(H, ctypes.c_void_p), ctypes.cast(O, ctypes.c_void_p),
+                                                    _stream(stream), sort_mode, ctypes.byref(stats)))
+        return _stats_dict(stats)
     _check(load_library().tigas_render_batch(scene.handle, V, P, K, ctypes.cast(W, ctypes.c_void_p),
                                              ctypes.cast(H, ctypes.c_void_p), ctypes.cast(O, ctypes.c_void_p),
                                              _stream(stream)))
+    return None
 
 
 def debug_render(scene: SceneHandle, pose, intr, width: int, height: int, sort_mode: int = SORT_DEPTH_FIRST,
