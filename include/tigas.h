@@ -282,6 +282,11 @@ tigas_status tigas_profile_enable(int enable);
  * reset=1 clears the accumulators after reading. */
 tigas_status tigas_profile_read(double* ms, uint64_t* calls, int reset);
 
+/* Launch sets of the sliced schedule are captured as CUDA graphs per shape
+ * (scene, view count and resolutions) and replayed; the first launch set of
+ * a shape runs without a graph.  enable=0 turns graphs off (default on). */
+tigas_status tigas_set_graphs(int enable);
+
 /* ------------------------------------------------------------------ misc */
 
 /* Message of the last failed call on this thread ("" if none). */

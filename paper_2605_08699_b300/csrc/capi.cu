@@ -117,7 +117,10 @@ Status do_render(Scene* scene, int V, const tigas_pose* poses, const tigas_intri
         req.views[v].out_rgba_f32 = o32;
     }
     FrameResult res;
-    TIGAS_TRY(render_frame(scene, req, ctx, st, &res));
+    bool done = false;
+    const bool try_graph = sort_mode == TIGAS_SORT_SLICED && !dbg && g_use_graphs.load();
+    if (try_graph) TIGAS_TRY(render_sliced_graph(scene, req, ctx, st, &res, &done));
+    if (!done) TIGAS_TRY(render_frame(scene, req, ctx, st, &res));
     for (int v = 0; v < V; ++v) {
         const size_t px = (size_t)ws[v] * hs[v];
         if (host8[v])
@@ -127,6 +130,28 @@ Status do_render(Scene* scene, int V, const tigas_pose* poses, const tigas_intri
     }
     TIGAS_CUDA_TRY(cudaStreamSynchronize(st));
     collect_profile(ctx);
+    if (res.graph_slices > 0) {
+        if (ctx.h_flags[0] & 1u) {
+            // a slice outgrew the captured pair capacity: render this frame exactly
+            // and capture again (with the new counts) on the next call
+            drop_graphs(ctx);
+            TIGAS_TRY(render_frame(scene, req, ctx, st, &res));
+            for (int v = 0; v < V; ++v) {
+                const size_t px = (size_t)ws[v] * hs[v];
+                if (host8[v])
+                    TIGAS_CUDA_TRY(cudaMemcpyAsync(host8[v], req.views[v].out_rgba8, px * 4, cudaMemcpyDeviceToHost, st));
+                if (host32[v])
+                    TIGAS_CUDA_TRY(
+                        cudaMemcpyAsync(host32[v], req.views[v].out_rgba_f32, px * 16, cudaMemcpyDeviceToHost, st));
+            }
+            TIGAS_CUDA_TRY(cudaStreamSynchronize(st));
+            collect_profile(ctx);
+        } else {
+            uint64_t P = 0;
+            for (int i = 0; i < res.graph_slices; ++i) P += ctx.h_total[i];
+            res.pairs = P;
+        }
+    }
     if (ctx.h_flags[0] & 1u) return {TIGAS_ERR_OVERFLOW, "pair buffer overflow"};
     if (ctx.h_flags[0] & 2u) return {TIGAS_ERR_CUDA, "tile id out of range in sorted keys"};
     if (ctx.h_flags[0] & 16u) return {TIGAS_ERR_TIMEOUT, "radix sort look-back wait ran out"};
@@ -195,6 +220,11 @@ Status do_render(Scene* scene, int V, const tigas_pose* poses, const tigas_intri
 using namespace tigas;
 
 TIGAS_API const char* tigas_last_error(void) { return last_error(); }
+TIGAS_API tigas_status tigas_set_graphs(int enable) {
+    g_use_graphs.store(enable != 0);
+    return TIGAS_OK;
+}
+
 TIGAS_API const char* tigas_version(void) { return "tigas-b300 0.1 (sm_103a)"; }
 TIGAS_API uint64_t tigas_kernel_launches(void) { return g_launches.load(); }
 

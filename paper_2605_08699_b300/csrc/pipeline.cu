@@ -9,6 +9,7 @@ namespace tigas {
 
 std::atomic<uint64_t> g_launches{0};
 std::atomic<bool> g_profile{false};
+std::atomic<bool> g_use_graphs{true};
 
 namespace {
 std::mutex g_prof_mu;
@@ -102,6 +103,7 @@ Status Arena::reserve(size_t bytes) {
     }
     cap = want;
     used = 0;
+    ++gen;
     return {};
 }
 
@@ -138,7 +140,7 @@ ViewParams make_view(const tigas_pose& pose, const tigas_intrinsics& k, int widt
 
 Status RenderContext::init() {
     TIGAS_CUDA_TRY(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
-    TIGAS_CUDA_TRY(cudaMallocHost(&h_total, sizeof(uint64_t) * 2));
+    TIGAS_CUDA_TRY(cudaMallocHost(&h_total, sizeof(uint64_t) * (kMaxSlices + 2)));
     TIGAS_CUDA_TRY(cudaMallocHost(&h_flags, sizeof(uint32_t) * 2));
     TIGAS_CUDA_TRY(cudaMallocHost(&h_views, (sizeof(ViewParams) + sizeof(uint64_t)) * kMaxViews));
     TIGAS_CUDA_TRY(cudaMallocHost(&h_misc, sizeof(uint32_t) * kMaxViews));
@@ -150,7 +152,10 @@ Status RenderContext::init() {
     return {};
 }
 
+void drop_graphs(RenderContext& ctx);
+
 void RenderContext::destroy() {
+    drop_graphs(*this);
     fixed.release();
     pairs.release();
     for (auto* p : dev_staging)
@@ -224,17 +229,23 @@ struct Marker {
         if (!on) return {};
         const int r = ctx.ev_count[sg];
         if (r >= kMaxSlices) return {};
-        TIGAS_CUDA_TRY(cudaEventRecord(begin ? ctx.ev_start[sg][r] : ctx.ev_stop[sg][r], st));
+        cudaEvent_t ev = begin ? ctx.ev_start[sg][r] : ctx.ev_stop[sg][r];
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        TIGAS_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+        // inside a capture a plain record only orders work; an external record
+        // node records the event each time the graph runs
+        if (cs == cudaStreamCaptureStatusActive)
+            TIGAS_CUDA_TRY(cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal));
+        else
+            TIGAS_CUDA_TRY(cudaEventRecord(ev, st));
         if (!begin) ctx.ev_count[sg] = r + 1;
         return {};
     }
 };
 }  // namespace
 
-Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, cudaStream_t st, FrameResult* res);
-
 Status render_frame(Scene* scene, FrameRequest& req, RenderContext& ctx, cudaStream_t st, FrameResult* res) {
-    if (req.sort_mode == TIGAS_SORT_SLICED) return render_frame_sliced(scene, req, ctx, st, res);
+    if (req.sort_mode == TIGAS_SORT_SLICED) return render_frame_sliced(scene, req, ctx, st, res, 0, nullptr);
     for (int k = 0; k < kNumStages; ++k) ctx.ev_count[k] = 0;
     Marker mark{ctx, st, g_profile.load(std::memory_order_relaxed)};
     const int V = req.V;
@@ -375,40 +386,95 @@ Status render_frame(Scene* scene, FrameRequest& req, RenderContext& ctx, cudaStr
 
 // Depth-sliced schedule: same kernels per slice, only for tiles with a pixel
 // still running; pixel state carried across slices (see sliced.cu).
-Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, cudaStream_t st, FrameResult* res) {
+//
+// Two ways to run it:
+//  - exact (static_cap == 0): the number of kept entries is read back once and
+//    the slices cut the kept entries; every slice's pair count is read back
+//    to size its buffers exactly (one host round trip per slice);
+//  - static (static_cap > 0): slices cut all entries (culled ones sort last
+//    and emit nothing), every kernel takes its counts from device memory and
+//    pair buffers have the fixed capacity static_cap; nothing waits on the
+//    host, so the launch sequence can be captured in a CUDA graph.  A slice
+//    with more pairs than the capacity sets the overflow flag (the caller
+//    re-renders exactly).  The arenas must already be reserved
+//    (sliced_workspace gives the sizes).
+namespace {
+
+struct SlicedLayout {
+    int V = 0, S = 0, tile_bits = 0;
+    uint64_t E = 0, total_pix = 0;
+    uint32_t total_tiles = 0, done_words = 0;
+    uint64_t pix_base[kMaxViews] = {};
+    size_t tmp_words = 0, fixed_bytes = 0;
+};
+
+SlicedLayout sliced_layout(const Scene* scene, FrameRequest& req) {
+    SlicedLayout L;
+    L.V = req.V;
+    L.E = (uint64_t)req.V * scene->view.n;
+    L.S = req.n_slices < 1 ? 1 : (req.n_slices > kMaxSlices ? kMaxSlices : req.n_slices);
+    for (int v = 0; v < L.V; ++v) {
+        req.views[v].tile_base = L.total_tiles;
+        L.total_tiles += (uint32_t)(req.views[v].TX * req.views[v].TY);
+        L.pix_base[v] = L.total_pix;
+        L.total_pix += (uint64_t)req.views[v].W * req.views[v].H;
+    }
+    L.tile_bits = L.total_tiles <= 1 ? 1 : 32 - __builtin_clz(L.total_tiles - 1);
+    L.done_words = (L.total_tiles + 31) / 32;
+    const size_t presort_words = radix_tmp_words(L.E);
+    const size_t scan_words = scan_tmp_words(L.E + 1);
+    L.tmp_words = presort_words > scan_words ? presort_words : scan_words;
+    const uint64_t E = L.E;
+    size_t b = sizeof(ViewParams) * kMaxViews + 96 * 256;
+    b += E * (16 + 16 + 4 + 4 + 4 + 8 + (req.want_q ? 4 : 0));
+    b += E * 4 * 4 + (E + 1) * 4 * 2 + E * 8;             // depth sort buffers, counts, offsets, rects
+    b += L.tmp_words * 4;
+    b += (sizeof(uint2) + 4) * (size_t)L.total_tiles + L.done_words * 4;
+    b += L.total_pix * 16 + sizeof(uint64_t) * kMaxViews * 2;
+    L.fixed_bytes = b;
+    return L;
+}
+
+size_t pair_bytes_for(uint64_t P) { return P * 24 + radix_tmp_words(P) * 4 + 16 * 256; }
+
+}  // namespace
+
+void sliced_stage_views(const Scene* scene, FrameRequest& req, RenderContext& ctx) {
+    SlicedLayout L = sliced_layout(scene, req);
+    char* hv = reinterpret_cast<char*>(ctx.h_views);
+    std::memcpy(hv, req.views, sizeof(ViewParams) * L.V);
+    std::memcpy(hv + sizeof(ViewParams) * kMaxViews, L.pix_base, sizeof(uint64_t) * L.V);
+}
+
+Status sliced_workspace(const Scene* scene, FrameRequest& req, uint64_t pair_cap, size_t* fixed_bytes,
+                        size_t* pair_bytes) {
+    SlicedLayout L = sliced_layout(scene, req);
+    *fixed_bytes = L.fixed_bytes;
+    *pair_bytes = pair_bytes_for(pair_cap);
+    return {};
+}
+
+Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, cudaStream_t st, FrameResult* res,
+                           uint64_t static_cap, uint64_t* slice_pairs) {
     for (int k = 0; k < kNumStages; ++k) ctx.ev_count[k] = 0;
     Marker mark{ctx, st, g_profile.load(std::memory_order_relaxed)};
-    const int V = req.V;
+    const bool stat = static_cap > 0;
     const uint32_t n = scene->view.n;
-    const uint64_t E = (uint64_t)V * n;
-    if (E >= 0xFFFFFFFFull) return {TIGAS_ERR_INVALID, "views x Gaussians exceeds 2^32 entries"};
-    const int S = req.n_slices < 1 ? 1 : (req.n_slices > kMaxSlices ? kMaxSlices : req.n_slices);
-    uint32_t total_tiles = 0;
-    uint64_t pix_base_h[kMaxViews];
-    uint64_t total_pix = 0;
-    for (int v = 0; v < V; ++v) {
-        req.views[v].tile_base = total_tiles;
-        total_tiles += (uint32_t)(req.views[v].TX * req.views[v].TY);
-        pix_base_h[v] = total_pix;
-        total_pix += (uint64_t)req.views[v].W * req.views[v].H;
-    }
-    const int tile_bits = total_tiles <= 1 ? 1 : 32 - __builtin_clz(total_tiles - 1);
-    const uint32_t done_words = (total_tiles + 31) / 32;
+    if ((uint64_t)req.V * n >= 0xFFFFFFFFull) return {TIGAS_ERR_INVALID, "views x Gaussians exceeds 2^32 entries"};
+    const SlicedLayout L = sliced_layout(scene, req);
+    const int V = L.V, S = L.S;
+    const uint64_t E = L.E;
+    const uint32_t total_tiles = L.total_tiles;
 
-    // ---- per-entry and per-pixel workspace
-    const size_t presort_words = radix_tmp_words(E);
-    const size_t scan_words = scan_tmp_words(E + 1);
-    const size_t tmp_words = presort_words > scan_words ? presort_words : scan_words;
-    size_t fixed_bytes = sizeof(ViewParams) * kMaxViews + 80 * 256;
-    fixed_bytes += E * (16 + 16 + 4 + 4 + 4 + 8 + (req.want_q ? 4 : 0));
-    fixed_bytes += E * 4 * 4 + E * 4 * 2 + 8 + E * 8;     // depth sort buffers, counts, offsets, rects
-    fixed_bytes += tmp_words * 4;
-    fixed_bytes += (sizeof(uint2) + 4) * (size_t)total_tiles + done_words * 4;
-    fixed_bytes += total_pix * 16 + sizeof(uint64_t) * kMaxViews;
-    TIGAS_TRY(ctx.fixed.reserve(fixed_bytes));
+    if (stat) {
+        if (ctx.fixed.cap < L.fixed_bytes || ctx.pairs.cap < pair_bytes_for(static_cap))
+            return {TIGAS_ERR_INVALID, "static sliced schedule needs its workspace reserved first"};
+    } else {
+        TIGAS_TRY(ctx.fixed.reserve(L.fixed_bytes));
+    }
     ctx.fixed.reset();
     ViewParams* d_views = ctx.fixed.take<ViewParams>(kMaxViews);
-    uint64_t* d_total = ctx.fixed.take<uint64_t>(2);
+    uint64_t* d_total = ctx.fixed.take<uint64_t>(kMaxSlices + 2);
     unsigned long long* d_counters = ctx.fixed.take<unsigned long long>(4);
     uint32_t* d_flags = ctx.fixed.take<uint32_t>(2);
     uint32_t* d_visible = ctx.fixed.take<uint32_t>(kMaxViews);
@@ -429,19 +495,20 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     uint32_t* counts = ctx.fixed.take<uint32_t>(E + 1);
     uint32_t* offsets = ctx.fixed.take<uint32_t>(E + 1);
     uint2* rect_sorted = ctx.fixed.take<uint2>(E);
-    uint32_t* tmp = ctx.fixed.take<uint32_t>(tmp_words);
+    uint32_t* tmp = ctx.fixed.take<uint32_t>(L.tmp_words);
     uint2* ranges = ctx.fixed.take<uint2>(total_tiles);
     uint32_t* active = ctx.fixed.take<uint32_t>(total_tiles);
-    uint32_t* done = ctx.fixed.take<uint32_t>(done_words);
-    float4* state = ctx.fixed.take<float4>(total_pix);
+    uint32_t* done = ctx.fixed.take<uint32_t>(L.done_words);
+    float4* state = ctx.fixed.take<float4>(L.total_pix);
 
-    std::memcpy(ctx.h_views, req.views, sizeof(ViewParams) * V);
-    TIGAS_CUDA_TRY(cudaMemcpyAsync(d_views, ctx.h_views, sizeof(ViewParams) * V, cudaMemcpyHostToDevice, st));
-    std::memcpy(reinterpret_cast<char*>(ctx.h_views) + sizeof(ViewParams) * V, pix_base_h, sizeof(uint64_t) * V);
-    TIGAS_CUDA_TRY(cudaMemcpyAsync(d_pix_base, reinterpret_cast<char*>(ctx.h_views) + sizeof(ViewParams) * V,
-                                   sizeof(uint64_t) * V, cudaMemcpyHostToDevice, st));
+    // host -> device: the view table and the views' pixel offsets (pinned staging)
+    sliced_stage_views(scene, req, ctx);
+    char* hv = reinterpret_cast<char*>(ctx.h_views);
+    TIGAS_CUDA_TRY(cudaMemcpyAsync(d_views, hv, sizeof(ViewParams) * V, cudaMemcpyHostToDevice, st));
+    TIGAS_CUDA_TRY(cudaMemcpyAsync(d_pix_base, hv + sizeof(ViewParams) * kMaxViews, sizeof(uint64_t) * V,
+                                   cudaMemcpyHostToDevice, st));
     TIGAS_CUDA_TRY(cudaMemsetAsync(d_flags, 0, sizeof(uint32_t) * 2, st));
-    TIGAS_CUDA_TRY(cudaMemsetAsync(done, 0, done_words * 4, st));
+    TIGAS_CUDA_TRY(cudaMemsetAsync(done, 0, L.done_words * 4, st));
     if (sp.q_dbg) TIGAS_CUDA_TRY(cudaMemsetAsync(sp.q_dbg, 0, E * 4, st));
     if (req.want_counters) TIGAS_CUDA_TRY(cudaMemsetAsync(d_counters, 0, sizeof(unsigned long long) * 4, st));
 
@@ -453,11 +520,16 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
                                    nullptr, d_flags));
     TIGAS_TRY(mark(kStDepthSort, false));
     TIGAS_TRY(launch_init_state(d_views, V, total_tiles, d_pix_base, state, scene->view.bg, st));
-    // kept entries: culled ones (depth key 0xFFFFFFFF) sort after all kept ones
-    TIGAS_CUDA_TRY(cudaMemcpyAsync(ctx.h_misc, d_visible, sizeof(uint32_t) * V, cudaMemcpyDeviceToHost, st));
-    TIGAS_CUDA_TRY(cudaStreamSynchronize(st));
-    uint64_t K = 0;
-    for (int v = 0; v < V; ++v) K += ctx.h_misc[v];
+
+    // entries the slices cut: kept ones only (exact), or all (static; culled
+    // ones sort after every kept one and have empty rectangles)
+    uint64_t K = E;
+    if (!stat) {
+        TIGAS_CUDA_TRY(cudaMemcpyAsync(ctx.h_misc, d_visible, sizeof(uint32_t) * V, cudaMemcpyDeviceToHost, st));
+        TIGAS_CUDA_TRY(cudaStreamSynchronize(st));
+        K = 0;
+        for (int v = 0; v < V; ++v) K += ctx.h_misc[v];
+    }
     TIGAS_TRY(mark(kStScan, true));
     TIGAS_TRY(launch_permute_rects(order, K, sp, n, rect_sorted, st));
     TIGAS_TRY(mark(kStScan, false));
@@ -472,52 +544,72 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     int passes = 0;
     uint64_t a = 0;
     SliceBlendArgs sl{active, d_misc, d_misc + 1, state, d_pix_base, done};
+    if (stat) {
+        // pair buffers for the fixed capacity, taken once
+        ctx.pairs.reset();
+    }
+    uint32_t *keys_a = nullptr, *keys_b = nullptr, *keys_c = nullptr, *vals_a = nullptr, *vals_b = nullptr,
+             *vals_c = nullptr, *stmp = nullptr;
+    auto take_pairs = [&](uint64_t cap) {
+        ctx.pairs.reset();
+        keys_a = ctx.pairs.take<uint32_t>(cap);
+        keys_b = ctx.pairs.take<uint32_t>(cap);
+        keys_c = ctx.pairs.take<uint32_t>(cap);
+        vals_a = ctx.pairs.take<uint32_t>(cap);
+        vals_b = ctx.pairs.take<uint32_t>(cap);
+        vals_c = ctx.pairs.take<uint32_t>(cap);
+        stmp = ctx.pairs.take<uint32_t>(radix_tmp_words(cap));
+    };
+    if (stat) take_pairs(static_cap);
     for (int i = 0; i < S; ++i) {
         const uint64_t b = ends[i] > a ? ends[i] : a;
+        if (slice_pairs) slice_pairs[i] = 0;
         if (b == a) continue;
+        uint64_t* d_P = d_total + i;
         TIGAS_TRY(mark(kStScan, true));
         TIGAS_TRY(launch_count_slice(rect_sorted, a, b, d_views, V, done, counts, st));
         // one extra zero count makes offsets[b - a] the slice total
         TIGAS_CUDA_TRY(cudaMemsetAsync(counts + (b - a), 0, sizeof(uint32_t), st));
-        TIGAS_TRY(launch_scan_u32(counts, nullptr, offsets, b - a + 1, d_total, tmp, st));
+        TIGAS_TRY(launch_scan_u32(counts, nullptr, offsets, b - a + 1, d_P, tmp, st));
         TIGAS_TRY(mark(kStScan, false));
-        TIGAS_CUDA_TRY(cudaMemcpyAsync(ctx.h_total, d_total, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
-        TIGAS_CUDA_TRY(cudaStreamSynchronize(st));
-        const uint64_t P = ctx.h_total[0];
-        if (P >= 0xFFFFFFFFull) return {TIGAS_ERR_OVERFLOW, "pair count exceeds 2^32"};
-        if (P > 0) {
+        uint64_t cap = static_cap;
+        if (!stat) {
+            TIGAS_CUDA_TRY(cudaMemcpyAsync(ctx.h_total, d_P, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+            TIGAS_CUDA_TRY(cudaStreamSynchronize(st));
+            const uint64_t P = ctx.h_total[0];
+            if (P >= 0xFFFFFFFFull) return {TIGAS_ERR_OVERFLOW, "pair count exceeds 2^32"};
+            if (slice_pairs) slice_pairs[i] = P;
+            if (P == 0) {
+                a = b;
+                continue;
+            }
             total_pairs += P;
-            const size_t sort_words = radix_tmp_words(P);
-            TIGAS_TRY(ctx.pairs.reserve(P * 24 + sort_words * 4 + 8 * 256));
-            ctx.pairs.reset();
-            uint32_t* keys_a = ctx.pairs.take<uint32_t>(P);
-            uint32_t* keys_b = ctx.pairs.take<uint32_t>(P);
-            uint32_t* keys_c = ctx.pairs.take<uint32_t>(P);
-            uint32_t* vals_a = ctx.pairs.take<uint32_t>(P);
-            uint32_t* vals_b = ctx.pairs.take<uint32_t>(P);
-            uint32_t* vals_c = ctx.pairs.take<uint32_t>(P);
-            uint32_t* stmp = ctx.pairs.take<uint32_t>(sort_words);
-            TIGAS_TRY(mark(kStEmit, true));
-            TIGAS_TRY(launch_emit_slice(order, rect_sorted, a, b, offsets, d_views, V, done, keys_a, vals_a, P, d_flags,
-                                        st));
-            TIGAS_TRY(mark(kStEmit, false));
-            TIGAS_TRY(mark(kStPairSort, true));
-            TIGAS_TRY(radix_sort<uint32_t>(keys_a, vals_a, keys_b, vals_b, keys_c, vals_c, P, nullptr, 0, tile_bits,
-                                           stmp, st, &passes, d_flags));
-            TIGAS_TRY(mark(kStPairSort, false));
-            TIGAS_TRY(mark(kStRanges, true));
-            TIGAS_TRY(launch_ranges_active(keys_c, P, ranges, total_tiles, done, active, d_misc, d_flags, st));
-            TIGAS_TRY(mark(kStRanges, false));
-            TIGAS_TRY(mark(kStBlend, true));
-            TIGAS_TRY(launch_blend_slice(ranges, vals_c, sp, d_views, V, (uint32_t)E, scene->view.bg,
-                                         req.want_counters ? d_counters : nullptr, sl, st));
-            TIGAS_TRY(mark(kStBlend, false));
+            TIGAS_TRY(ctx.pairs.reserve(pair_bytes_for(P)));
+            take_pairs(P);
+            cap = P;
         }
+        TIGAS_TRY(mark(kStEmit, true));
+        TIGAS_TRY(launch_emit_slice(order, rect_sorted, a, b, offsets, d_views, V, done, keys_a, vals_a, cap, d_flags,
+                                    st));
+        TIGAS_TRY(mark(kStEmit, false));
+        TIGAS_TRY(mark(kStPairSort, true));
+        TIGAS_TRY(radix_sort<uint32_t>(keys_a, vals_a, keys_b, vals_b, keys_c, vals_c, cap, stat ? d_P : nullptr, 0,
+                                       L.tile_bits, stmp, st, &passes, d_flags));
+        TIGAS_TRY(mark(kStPairSort, false));
+        TIGAS_TRY(mark(kStRanges, true));
+        TIGAS_TRY(launch_ranges_active(keys_c, cap, stat ? d_P : nullptr, ranges, total_tiles, done, active, d_misc,
+                                       d_flags, st));
+        TIGAS_TRY(mark(kStRanges, false));
+        TIGAS_TRY(mark(kStBlend, true));
+        TIGAS_TRY(launch_blend_slice(ranges, vals_c, sp, d_views, V, (uint32_t)E, scene->view.bg,
+                                     req.want_counters ? d_counters : nullptr, sl, st));
+        TIGAS_TRY(mark(kStBlend, false));
         a = b;
     }
     TIGAS_CUDA_TRY(cudaMemcpyAsync(ctx.h_flags, d_flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    if (stat) TIGAS_CUDA_TRY(cudaMemcpyAsync(ctx.h_total, d_total, sizeof(uint64_t) * S, cudaMemcpyDeviceToHost, st));
     if (res) {
-        res->pairs = total_pairs;
+        res->pairs = total_pairs;   // static: read ctx.h_total after the stream completes
         res->total_tiles = total_tiles;
         res->sort_passes = passes;
         res->values = nullptr;
@@ -527,6 +619,104 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
         res->d_counters = req.want_counters ? d_counters : nullptr;
     }
     return {};
+}
+
+
+// ------------------------------------------------------------- CUDA graphs
+
+namespace {
+std::vector<int64_t> graph_key(const Scene* scene, const FrameRequest& req) {
+    std::vector<int64_t> k = {(int64_t)(uintptr_t)scene, scene->view.storage, req.V, req.n_slices,
+                              req.want_counters ? 1 : 0, g_profile.load() ? 1 : 0};
+    for (int v = 0; v < req.V; ++v) {
+        k.push_back(req.views[v].W);
+        k.push_back(req.views[v].H);
+    }
+    return k;
+}
+}  // namespace
+
+Status render_sliced_graph(Scene* scene, FrameRequest& req, RenderContext& ctx, cudaStream_t st, FrameResult* res,
+                           bool* rendered) {
+    *rendered = false;
+    if (req.want_q) return {};
+    const std::vector<int64_t> key = graph_key(scene, req);
+    RenderContext::Graph* g = nullptr;
+    for (auto& e : ctx.graphs)
+        if (e.key == key) g = &e;
+    if (g && (g->fixed_gen != ctx.fixed.gen || g->pairs_gen != ctx.pairs.gen)) {
+        drop_graphs(ctx);   // an arena moved since the capture
+        g = nullptr;
+    }
+    if (g) {
+        sliced_stage_views(scene, req, ctx);
+        TIGAS_CUDA_TRY(cudaGraphLaunch(g->exec, st));
+        g_launches.fetch_add(g->launches, std::memory_order_relaxed);
+        for (int k = 0; k < kNumStages; ++k) ctx.ev_count[k] = g->ev_count[k];
+        if (res) {
+            *res = g->res;
+            res->graph_slices = g->slices;
+        }
+        *rendered = true;
+        return {};
+    }
+    // first frame of this shape: render exactly, learn the slices' pair counts
+    uint64_t sp[kMaxSlices] = {};
+    TIGAS_TRY(render_frame_sliced(scene, req, ctx, st, res, 0, sp));
+    TIGAS_CUDA_TRY(cudaStreamSynchronize(st));
+    *rendered = true;
+    int exact_counts[kNumStages];
+    for (int k = 0; k < kNumStages; ++k) exact_counts[k] = ctx.ev_count[k];
+    if (ctx.h_flags[0] != 0) return {};
+    uint64_t mx = 0;
+    for (int i = 0; i < kMaxSlices; ++i) mx = sp[i] > mx ? sp[i] : mx;
+    const uint64_t cap = mx + mx / 2 + 65536;
+    size_t fb = 0, pb = 0;
+    TIGAS_TRY(sliced_workspace(scene, req, cap, &fb, &pb));
+    TIGAS_TRY(ctx.fixed.reserve(fb));
+    TIGAS_TRY(ctx.pairs.reserve(pb));
+    // capture on the context's own stream
+    const uint64_t l0 = g_launches.load();
+    TIGAS_CUDA_TRY(cudaStreamBeginCapture(ctx.stream, cudaStreamCaptureModeThreadLocal));
+    FrameResult tmp_res;
+    Status s = render_frame_sliced(scene, req, ctx, ctx.stream, &tmp_res, cap, nullptr);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx.stream, &graph);
+    const uint64_t captured = g_launches.load() - l0;
+    g_launches.fetch_sub(captured, std::memory_order_relaxed);   // captured, not run
+    if (!s.ok()) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    if (e != cudaSuccess) return {TIGAS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e)};
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return {TIGAS_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e)};
+    RenderContext::Graph entry;
+    entry.key = key;
+    entry.exec = exec;
+    entry.cap = cap;
+    entry.launches = captured;
+    entry.slices = req.n_slices < 1 ? 1 : (req.n_slices > kMaxSlices ? kMaxSlices : req.n_slices);
+    entry.fixed_gen = ctx.fixed.gen;
+    entry.pairs_gen = ctx.pairs.gen;
+    entry.res = tmp_res;
+    for (int k = 0; k < kNumStages; ++k) entry.ev_count[k] = ctx.ev_count[k];
+    // nothing of the capture ran: the exact frame's events are the ones to read
+    for (int k = 0; k < kNumStages; ++k) ctx.ev_count[k] = exact_counts[k];
+    if (ctx.graphs.size() >= 8) {
+        cudaGraphExecDestroy(ctx.graphs.front().exec);
+        ctx.graphs.erase(ctx.graphs.begin());
+    }
+    ctx.graphs.push_back(entry);
+    return {};
+}
+
+void drop_graphs(RenderContext& ctx) {
+    for (auto& g : ctx.graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    ctx.graphs.clear();
 }
 
 }  // namespace tigas

@@ -24,6 +24,7 @@ struct Arena {
     char* base = nullptr;
     size_t cap = 0;
     size_t used = 0;
+    uint64_t gen = 0;               // bumped on every reallocation (captured graphs hold pointers)
     Status reserve(size_t bytes);   // call only when no work uses the arena
     void reset() { used = 0; }
     template <typename T>
@@ -48,6 +49,19 @@ extern std::atomic<bool> g_profile;
 void profile_accumulate(const float* ms, const int* used, float frame_ms);
 void profile_read(double* ms, uint64_t* calls, bool reset);
 
+struct FrameResult {
+    uint64_t pairs = 0;
+    uint32_t total_tiles = 0;
+    int sort_passes = 0;
+    // device pointers valid until the context is reused
+    const uint32_t* values = nullptr;    // sorted pair values (entries)
+    const uint2* ranges = nullptr;
+    SplatArrays splats{};
+    uint32_t* d_visible = nullptr;
+    unsigned long long* d_counters = nullptr;   // [evals, fetched, blends] when requested
+    int graph_slices = 0;                       // replayed graph: pairs = sum of ctx.h_total[0..slices)
+};
+
 // Render state of one in-flight frame or launch set: stream, arenas, pinned staging.
 struct RenderContext {
     cudaEvent_t ev_start[kNumStages][kMaxSlices] = {};
@@ -62,6 +76,18 @@ struct RenderContext {
     ViewParams* h_views = nullptr;     // pinned view table
     std::vector<uint8_t*> dev_staging; // device frames for host outputs
     std::vector<size_t> staging_bytes;
+    // captured sliced launch sets, keyed by their shape
+    struct Graph {
+        std::vector<int64_t> key;
+        cudaGraphExec_t exec = nullptr;
+        uint64_t cap = 0;
+        uint64_t launches = 0;
+        int ev_count[kNumStages] = {};
+        int slices = 0;
+        uint64_t fixed_gen = 0, pairs_gen = 0;
+        FrameResult res;
+    };
+    std::vector<Graph> graphs;
     Status init();
     void destroy();
 };
@@ -75,18 +101,6 @@ struct FrameRequest {
     bool want_q = false;
 };
 
-struct FrameResult {
-    uint64_t pairs = 0;
-    uint32_t total_tiles = 0;
-    int sort_passes = 0;
-    // device pointers valid until the context is reused
-    const uint32_t* values = nullptr;    // sorted pair values (entries)
-    const uint2* ranges = nullptr;
-    SplatArrays splats{};
-    uint32_t* d_visible = nullptr;
-    unsigned long long* d_counters = nullptr;   // [evals, fetched] when requested
-};
-
 // After the stream is synchronised: add this frame's stage times (profiling on).
 void collect_profile(RenderContext& ctx);
 
@@ -94,6 +108,26 @@ void collect_profile(RenderContext& ctx);
 // back once (after the scan) to size the pair buffers exactly.  Returns after
 // enqueuing the blend and the flag readback; the caller synchronises.
 Status render_frame(Scene* scene, FrameRequest& req, RenderContext& ctx, cudaStream_t st, FrameResult* res);
+
+// The depth-sliced schedule.  static_cap == 0: exact (host reads back counts);
+// static_cap > 0: device-side counts and fixed pair capacity, capturable in a
+// CUDA graph (workspace reserved beforehand, see sliced_workspace).
+// slice_pairs (host, n_slices entries, exact mode only): pairs per slice.
+Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, cudaStream_t st, FrameResult* res,
+                           uint64_t static_cap, uint64_t* slice_pairs);
+Status sliced_workspace(const Scene* scene, FrameRequest& req, uint64_t pair_cap, size_t* fixed_bytes,
+                        size_t* pair_bytes);
+// Write the launch set's view table and pixel offsets to the pinned staging
+// buffer the (captured) host-to-device copy reads.
+void sliced_stage_views(const Scene* scene, FrameRequest& req, RenderContext& ctx);
+
+// Render req through a CUDA graph of the static sliced schedule, capturing it
+// on first use of a shape (that first frame is rendered exactly).  *rendered
+// is false when graphs cannot serve this request (caller renders exactly).
+Status render_sliced_graph(Scene* scene, FrameRequest& req, RenderContext& ctx, cudaStream_t st, FrameResult* res,
+                           bool* rendered);
+extern std::atomic<bool> g_use_graphs;
+void drop_graphs(RenderContext& ctx);
 
 // Context pool used by the synchronous entry points.
 RenderContext* acquire_context(Status* err);

@@ -83,6 +83,10 @@ k_permute_rects(const uint32_t* __restrict__ order, uint64_t K, SplatArrays sp, 
     const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= K) return;
     const uint32_t e = order[k];
+    if (sp.tiles[e] == 0) {   // culled entry: empty rectangle
+        rect_sorted[k] = make_uint2(0u, 0u);
+        return;
+    }
     const uint2 r = sp.rect[e];
     const uint32_t v = e / n_per_view;
     rect_sorted[k] = make_uint2((r.x & 0x3FFu) | ((r.y & 0x3FFu) << 10) | (v << 20),
@@ -164,9 +168,11 @@ __device__ inline uint64_t lower_bound_u32(const uint32_t* __restrict__ keys, ui
 }
 
 __global__ void __launch_bounds__(256)
-k_ranges_active(const uint32_t* __restrict__ keys, uint64_t n, uint2* __restrict__ ranges, uint32_t n_tiles,
-                const uint32_t* __restrict__ done, uint32_t* __restrict__ active, uint32_t* __restrict__ n_active,
-                uint32_t* __restrict__ overflow) {
+k_ranges_active(const uint32_t* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, uint2* __restrict__ ranges,
+                uint32_t n_tiles, const uint32_t* __restrict__ done, uint32_t* __restrict__ active,
+                uint32_t* __restrict__ n_active, uint32_t* __restrict__ overflow) {
+    uint64_t n = d_n ? *d_n : n_cap;
+    if (n > n_cap) n = n_cap;
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0 && n > 0 && keys[n - 1] >= n_tiles) atomicOr(overflow, 2u);
     bool act = false;
@@ -221,11 +227,12 @@ Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64
     return {};
 }
 
-Status launch_ranges_active(const uint32_t* keys, uint64_t n, uint2* ranges, uint32_t n_tiles, const uint32_t* done,
-                            uint32_t* active, uint32_t* n_active, uint32_t* overflow, cudaStream_t st) {
+Status launch_ranges_active(const uint32_t* keys, uint64_t n_cap, const uint64_t* d_n, uint2* ranges,
+                            uint32_t n_tiles, const uint32_t* done, uint32_t* active, uint32_t* n_active,
+                            uint32_t* overflow, cudaStream_t st) {
     if (n_tiles == 0) return {};
     TIGAS_CUDA_TRY(cudaMemsetAsync(n_active, 0, sizeof(uint32_t), st));
-    k_ranges_active<<<(n_tiles + 255) / 256, 256, 0, st>>>(keys, n, ranges, n_tiles, done, active, n_active,
+    k_ranges_active<<<(n_tiles + 255) / 256, 256, 0, st>>>(keys, n_cap, d_n, ranges, n_tiles, done, active, n_active,
                                                            overflow);
     TIGAS_LAUNCHED();
     return {};

@@ -26,8 +26,10 @@ Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64
 
 // Tile ranges of the slice's sorted keys, and the list of tiles with pairs
 // that are not done (*n_active entries of `active`, zeroed here).
-Status launch_ranges_active(const uint32_t* keys, uint64_t n, uint2* ranges, uint32_t n_tiles, const uint32_t* done,
-                            uint32_t* active, uint32_t* n_active, uint32_t* overflow, cudaStream_t st);
+// The key count is min(*d_n, n_cap) when d_n is given, else n_cap.
+Status launch_ranges_active(const uint32_t* keys, uint64_t n_cap, const uint64_t* d_n, uint2* ranges,
+                            uint32_t n_tiles, const uint32_t* done, uint32_t* active, uint32_t* n_active,
+                            uint32_t* overflow, cudaStream_t st);
 
 // Blend of the active tiles of one slice: persistent CTAs take tiles from the
 // active list, composite the slice's entries onto each pixel's carried state,

@@ -27,7 +27,7 @@ EXPORTS = ["tigas_scene_load", "tigas_scene_free", "tigas_scene_bytes", "tigas_r
            "tigas_server_destroy", "tigas_server_submit", "tigas_server_poll", "tigas_last_error",
            "tigas_version", "tigas_kernel_launches", "tigas_profile_enable", "tigas_profile_read",
            "tigas_sort_pairs_u64_noalloc",
-           "tigas_render_batch_ex"]
+           "tigas_render_batch_ex", "tigas_set_graphs"]
 
 STAGES = ["preprocess", "depth_sort", "scan", "emit", "pair_sort", "ranges", "blend", "frame"]
 
@@ -112,6 +112,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "tigas_version": (ctypes.c_char_p, []),
         "tigas_kernel_launches": (ctypes.c_uint64, []),
         "tigas_profile_enable": (st, [i]),
+        "tigas_set_graphs": (st, [i]),
         "tigas_profile_read": (st, [P, P, i]),
     }
     for name, (res, args) in sig.items():
@@ -142,6 +143,11 @@ def kernel_launches() -> int:
 def profile_enable(on: bool = True) -> None:
     """Per-stage CUDA-event timing of every later render (tigas_profile_enable)."""
     _check(load_library().tigas_profile_enable(int(on)))
+
+
+def set_graphs(on: bool = True) -> None:
+    """Capture and replay CUDA graphs of the sliced schedule (tigas_set_graphs)."""
+    _check(load_library().tigas_set_graphs(int(on)))
 
 
 def profile_read(reset: bool = False) -> dict:

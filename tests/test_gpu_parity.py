@@ -260,6 +260,45 @@ def test_batch_equals_single_renders(h1, cuda):
         assert np.array_equal(ho, o.cpu().numpy())
 
 
+# ----------------------------------------------------------- CUDA graphs
+
+
+def _batch(h, poses, levels, cuda):
+    intrs = [synth.default_intrinsics(w, hh) for w, hh in levels]
+    outs = [torch.empty((hh, w, 4), dtype=torch.uint8, device=cuda) for w, hh in levels]
+    tg.render_batch(h, poses, intrs, [w for w, _ in levels], [hh for _, hh in levels], outs)
+    return [o.cpu().numpy() for o in outs]
+
+
+def test_graph_replay_equals_direct_launches(h1, cuda):
+    levels = [(480, 270), (320, 240), (97, 61)]
+    tr = synth.trajectory(11, 40)
+    tg.set_graphs(False)
+    ref = [_batch(h1, tr[i:i + 3], levels, cuda) for i in (0, 10, 20)]
+    tg.set_graphs(True)
+    got = [_batch(h1, tr[i:i + 3], levels, cuda) for i in (0, 10, 20)]   # capture, then two replays
+    for a, b in zip(ref, got):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+
+
+def test_graph_overflow_falls_back_to_exact(cuda, s1):
+    # capture on a far pose (few pairs), replay on a near one (far more pairs than
+    # the captured capacity): the frame must still be right
+    levels = [(320, 240)]
+    far = [synth.Pose(0.0, 0.0, (0.0, 0.0, -12.0))]
+    near = [synth.Pose(0.1, 0.05, (0.0, 0.0, -2.2))]
+    with tg.scene_from(s1) as h:
+        tg.set_graphs(False)
+        ref = _batch(h, near, levels, cuda)
+        tg.set_graphs(True)
+        _batch(h, far, levels, cuda)
+        _batch(h, far, levels, cuda)
+        got = _batch(h, near, levels, cuda)
+        got2 = _batch(h, near, levels, cuda)
+    assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[0], got2[0])
+
+
 # -------------------------------------------------------------- serving
 
 
