@@ -1,15 +1,19 @@
-// K6 per-tile blend: one 16x16 tile per CTA of 128 threads, two pixels per
-// thread (rows y and y + 4 of the thread's warp's 8x8 block).  The tile's
-// depth-ordered list is consumed in batches of 256 Gaussians gathered into
-// shared memory with cp.async, double-buffered (batch b+1 in flight while b is
-// composited), so each staged entry's shared-memory loads serve two pixels.
-// Each pixel composites front to back (the 3DGS rasterizer of Sec. 4.1):
-// alpha = min(0.99, o exp(power)), computed as 2^(power log2 e + log2 o);
-// entries with alpha < 1/255 are skipped before any exponential, and the
-// pixel stops before the entry that would bring T below 1e-4.  Warp votes make
-// the skip and the stop uniform: a warp skips the blend step when no lane
-// gains from an entry and leaves the batch once all its pixels have stopped;
-// the CTA leaves the list once all 256 pixels have stopped.
+// K6 per-tile blend, the 3DGS front-to-back compositing the backend relies
+// on (Sec. 4.1): one warp per 16x16 tile, 8 pixels per thread (column
+// lane % 16, rows lane / 16 + 2k), four independent tiles per CTA and no
+// CTA-wide barrier.  The tile's depth-ordered list is consumed in batches of
+// 32 entries that the warp gathers into shared memory with cp.async,
+// double-buffered (batch b+1 in flight while b is composited).
+//
+// For each staged entry the warp first tests the bounding box of its
+// alpha >= 1/255 region against the tile; a ballot over the batch keeps only
+// entries that can reach some pixel of the tile (a result-invariant skip:
+// every pixel the box excludes would skip the entry by the alpha test).  For
+// the kept entries each pixel computes alpha = min(0.99, o exp(power)) as
+// 2^(power log2 e + log2 o), skips alpha < 1/255 before any exponential, and
+// stops before the entry that would bring T below 1e-4.  A warp vote skips the
+// blend step when no pixel of the tile gains from an entry, and the warp
+// leaves the list once all 256 pixels have stopped.
 #include "kernels.cuh"
 #include "sliced.cuh"
 
@@ -17,16 +21,22 @@ namespace tigas {
 
 namespace {
 
-constexpr int kThreads = 128;
-constexpr int kBatch = 256;
+constexpr int kWarps = 4;                 // tiles per CTA
+constexpr int kThreads = 32 * kWarps;
+constexpr int kWB = 32;                   // entries per warp batch
+constexpr int kPix = 8;                   // pixels per thread
+#ifndef TIGAS_BLEND_MIN_BLOCKS
+#define TIGAS_BLEND_MIN_BLOCKS 5
+#endif
+constexpr int kMinBlocks = TIGAS_BLEND_MIN_BLOCKS;   // CTAs per SM the register budget targets
+constexpr uint32_t kFull = 0xFFFFFFFFu;
 // alpha >= 1/255  <=>  power log2 e + log2 o >= log2(1/255)
 constexpr float kMinLog2Alpha = -7.99435343685885793f;
-constexpr uint32_t kFull = 0xFFFFFFFFu;
 
-struct __align__(16) BlendSmem {
-    float4 geom[2][kBatch];
-    float4 appear[2][kBatch];
-    float blue[2][kBatch];
+struct __align__(16) WarpStage {
+    float4 geom[2][kWB];     // (u, v, a', b')
+    float4 appear[2][kWB];   // (c', log2 o, r, g)
+    float blue[2][kWB];
 };
 
 __device__ inline void cp_async16(void* smem, const void* gmem) {
@@ -51,34 +61,50 @@ __device__ inline uint8_t to_u8(float x) {
     return (uint8_t)__float2uint_rd(fminf(fmaxf(x, 0.0f), 1.0f) * 255.0f + 0.5f);
 }
 
-// SLICED = false: one CTA per tile (blockIdx.x), whole list, fresh pixels.
-// SLICED = true: persistent CTAs take tiles from the slice's active list,
-// start from and store back each pixel's (C, T), and mark finished tiles.
-// COUNT: accumulate list entries evaluated per pixel and entries staged.
+// Does the alpha >= 1/255 region of the entry meet the pixel-centre rectangle
+// [x0, x1] x [y0, y1]?  With q(d) = -(a' dx^2 + b' dx dy + c' dy^2) (positive
+// definite) the region is q(d) <= tau = log2 o - log2(1/255), an ellipse with
+// half-extents sqrt(tau (M^-1)_xx), sqrt(tau (M^-1)_yy), M = [[-a', -b'/2],
+// [-b'/2, -c']]; inflated by 1% + 0.05 px so FP32 rounding of the per-pixel
+// test can never put a contributing pixel outside it.
+__device__ inline bool alpha_box_meets(const float4& gm, const float4& ap, float x0, float x1, float y0, float y1) {
+    const float tau = ap.y - kMinLog2Alpha;
+    const float m00 = -gm.z, m11 = -ap.x, m01 = -0.5f * gm.w;
+    const float det = fmaf(m00, m11, -m01 * m01);
+    if (!(tau >= 0.0f) || !(det > 0.0f)) return false;
+    const float inv = tau / det;
+    const float hx = fmaf(sqrtf(m11 * inv), 1.01f, 0.05f);
+    const float hy = fmaf(sqrtf(m00 * inv), 1.01f, 0.05f);
+    return gm.x - hx <= x1 && gm.x + hx >= x0 && gm.y - hy <= y1 && gm.y + hy >= y0;
+}
+
+// SLICED = false: warp w of CTA b blends tile 4b + w over its whole list from
+// fresh pixels.  SLICED = true: persistent warps take tiles from the slice's
+// active list, start from and store back each pixel's (C, T), and mark tiles
+// whose pixels all stopped.  COUNT: accumulate list entries evaluated per
+// pixel (up to its stop), entries staged, and entries blended.
 template <bool SLICED, bool COUNT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
 k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ values, SplatArrays sp,
-        const ViewParams* __restrict__ views_g, int V, uint32_t n_entries, float bg_r, float bg_g, float bg_b,
-        unsigned long long* counters, SliceBlendArgs sl) {
-    __shared__ BlendSmem sm;
+        const ViewParams* __restrict__ views_g, int V, uint32_t total_tiles, uint32_t n_entries, float bg_r,
+        float bg_g, float bg_b, unsigned long long* counters, SliceBlendArgs sl) {
+    __shared__ WarpStage stage_sm[kWarps];
     __shared__ uint32_t s_tb[kMaxViews];
-    __shared__ uint32_t s_item;
     for (int k = threadIdx.x; k < V; k += kThreads) s_tb[k] = views_g[k].tile_base;
+    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t n_eval = 0, n_fetched = 0, n_blend = 0;
-    const uint32_t n_items = SLICED ? *sl.n_active : 1u;
+    WarpStage& sm = stage_sm[warp];
+    unsigned long long n_eval = 0, n_fetched = 0, n_blend = 0;
+    const uint32_t n_items = SLICED ? *sl.n_active : total_tiles;
+    uint32_t item = SLICED ? 0u : blockIdx.x * kWarps + warp;
     for (;;) {
-        uint32_t g;
         if (SLICED) {
-            __syncthreads();   // previous tile done with shared memory and s_item
-            if (threadIdx.x == 0) s_item = atomicAdd(sl.work_counter, 1u);
-            __syncthreads();
-            if (s_item >= n_items) break;
-            g = sl.active[s_item];
-        } else {
-            __syncthreads();
-            g = blockIdx.x;
+            uint32_t it = 0;
+            if (lane == 0) it = atomicAdd(sl.work_counter, 1u);
+            item = __shfl_sync(kFull, it, 0);
         }
+        if (item >= n_items) break;
+        const uint32_t g = SLICED ? sl.active[item] : item;
         int v = 0;
         {
             int lo = 0, hi = V;   // last view with tile_base <= g
@@ -92,48 +118,46 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ values, S
         const int W = vp.W, H = vp.H, TX = vp.TX;
         const uint32_t local = g - s_tb[v];
         const int ty = (int)(local / TX), tx = (int)(local % TX);
-        const int px = tx * kTile + (warp & 1) * 8 + (lane & 7);
-        const int py0 = ty * kTile + (warp >> 1) * 8 + (lane >> 3);
-        const int py1 = py0 + 4;
-        const bool in0 = px < W && py0 < H, in1 = px < W && py1 < H;
+        const int px = tx * kTile + (lane & 15);
+        const int py0 = ty * kTile + (lane >> 4);       // rows py0 + 2k
         const float pxf = (float)px + 0.5f, py0f = (float)py0 + 0.5f;
-        const size_t pix0 = (size_t)py0 * W + px, pix1 = (size_t)py1 * W + px;
+        const float tx0 = (float)(tx * kTile) + 0.5f, tx1 = tx0 + 15.0f;
+        const float ty0 = (float)(ty * kTile) + 0.5f, ty1 = ty0 + 15.0f;
+        const uint64_t sbase = SLICED ? sl.pix_base[v] : 0;
 
-        const uint2 rg = ranges[g];
-        const uint32_t start = rg.x, end = rg.y > rg.x ? rg.y : rg.x;
-        const int nb = (int)((end - start + kBatch - 1) / kBatch);
-
-        float T0 = 1.0f, r0 = 0.0f, g0 = 0.0f, b0 = 0.0f;
-        float T1 = 1.0f, r1 = 0.0f, g1 = 0.0f, b1 = 0.0f;
-        bool d0 = !in0, d1 = !in1;
-        if (SLICED) {
-            if (in0) {
-                const float4 s0 = sl.state[sl.pix_base[v] + pix0];
-                r0 = s0.x; g0 = s0.y; b0 = s0.z; T0 = fabsf(s0.w); d0 = s0.w < 0.0f;
-            }
-            if (in1) {
-                const float4 s1 = sl.state[sl.pix_base[v] + pix1];
-                r1 = s1.x; g1 = s1.y; b1 = s1.z; T1 = fabsf(s1.w); d1 = s1.w < 0.0f;
+        float T[kPix], cr[kPix], cg[kPix], cb[kPix];
+        uint32_t live = 0;   // bit k: pixel k still compositing
+#pragma unroll
+        for (int k = 0; k < kPix; ++k) {
+            T[k] = 1.0f; cr[k] = 0.0f; cg[k] = 0.0f; cb[k] = 0.0f;
+            const int py = py0 + 2 * k;
+            if (px < W && py < H) {
+                if (SLICED) {
+                    const float4 s0 = sl.state[sbase + (size_t)py * W + px];
+                    cr[k] = s0.x; cg[k] = s0.y; cb[k] = s0.z; T[k] = fabsf(s0.w);
+                    if (!(s0.w < 0.0f)) live |= 1u << k;
+                } else {
+                    live |= 1u << k;
+                }
             }
         }
 
+        const uint2 rg = ranges[g];
+        const uint32_t start = rg.x, end = rg.y > rg.x ? rg.y : rg.x;
+        const int nb = (int)((end - start + kWB - 1) / kWB);
         auto stage = [&](int b, int buf) {
-#pragma unroll
-            for (int h = 0; h < kBatch / kThreads; ++h) {
-                const int slot = h * kThreads + threadIdx.x;
-                const uint32_t idx = start + (uint32_t)b * kBatch + slot;
-                if (idx < end) {
-                    const uint32_t e = values[idx];
-                    if (e < n_entries) {
-                        cp_async16(&sm.geom[buf][slot], sp.geom + e);
-                        cp_async16(&sm.appear[buf][slot], sp.appear + e);
-                        cp_async4(&sm.blue[buf][slot], sp.blue + e);
-                    } else {
-                        // out-of-range entry (cannot happen for a consistent frame): contributes nothing
-                        sm.geom[buf][slot] = make_float4(-1e30f, -1e30f, 0.f, 0.f);
-                        sm.appear[buf][slot] = make_float4(0.f, -1e30f, 0.f, 0.f);
-                        sm.blue[buf][slot] = 0.f;
-                    }
+            const uint32_t idx = start + (uint32_t)b * kWB + lane;
+            if (idx < end) {
+                const uint32_t e = values[idx];
+                if (e < n_entries) {
+                    cp_async16(&sm.geom[buf][lane], sp.geom + e);
+                    cp_async16(&sm.appear[buf][lane], sp.appear + e);
+                    cp_async4(&sm.blue[buf][lane], sp.blue + e);
+                } else {
+                    // out-of-range entry (cannot happen for a consistent frame): contributes nothing
+                    sm.geom[buf][lane] = make_float4(-1e30f, -1e30f, 0.f, 0.f);
+                    sm.appear[buf][lane] = make_float4(0.f, -1e30f, 0.f, 0.f);
+                    sm.blue[buf][lane] = 0.f;
                 }
             }
             cp_async_commit();
@@ -148,94 +172,100 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ values, S
             } else {
                 cp_async_wait<0>();
             }
-            // all pixels of the tile stopped: leave the list
-            if (__syncthreads_count(d0 && d1) == kThreads) break;
-            const uint32_t rem = end - start - (uint32_t)b * kBatch;
-            const int cnt = rem < (uint32_t)kBatch ? (int)rem : kBatch;
-            if (COUNT) n_fetched += (uint32_t)cnt;
-#pragma unroll 4
-            for (int j = 0; j < cnt; ++j) {
-                if ((j & 3) == 0 && __all_sync(kFull, d0 && d1)) break;
-                const float4 gm = sm.geom[buf][j];     // (u, v, a', b')
-                const float4 ap = sm.appear[buf][j];   // (c', log2 o, r, g)
+            const uint32_t rem = end - start - (uint32_t)b * kWB;
+            const int cnt = rem < (uint32_t)kWB ? (int)rem : kWB;
+            // the lane's own staged entry: can it reach any pixel of the tile?
+            const bool meets = lane < cnt && alpha_box_meets(sm.geom[buf][lane], sm.appear[buf][lane], tx0, tx1, ty0, ty1);
+            uint32_t kept = __ballot_sync(kFull, meets);
+            __syncwarp();   // every lane's copies visible to the warp
+            if (__all_sync(kFull, live == 0)) break;
+            if (COUNT) n_fetched += (uint64_t)cnt;
+            int counted = 0;   // entries of this batch already counted as evaluated
+            bool stopped = false;
+            while (kept) {
+                const int j = __ffs(kept) - 1;
+                kept &= kept - 1;
+                if (COUNT) {
+                    // entries up to and including j meet the pixels still running before j
+                    n_eval += (uint64_t)(j + 1 - counted) * (uint64_t)__popc(live);
+                    counted = j + 1;
+                }
+                const float4 gm = sm.geom[buf][j];
+                const float4 ap = sm.appear[buf][j];
                 const float dx = gm.x - pxf;
-                const float dy0 = gm.y - py0f;
-                const float dy1 = dy0 - 4.0f;
                 const float adx = gm.z * dx, bdx = gm.w * dx;
-                // power log2 e = a' dx^2 + dy (b' dx + c' dy)
-                const float p0 = fmaf(adx, dx, dy0 * fmaf(ap.x, dy0, bdx));
-                const float p1 = fmaf(adx, dx, dy1 * fmaf(ap.x, dy1, bdx));
-                const float e0 = p0 + ap.y, e1 = p1 + ap.y;
-                const bool c0 = !d0 && p0 <= 0.0f && e0 >= kMinLog2Alpha;
-                const bool c1 = !d1 && p1 <= 0.0f && e1 >= kMinLog2Alpha;
-                if (COUNT) n_eval += (d0 ? 0u : 1u) + (d1 ? 0u : 1u);
-                if (__any_sync(kFull, c0 || c1)) {
-                    const float cb = sm.blue[buf][j];
-                    if (c0) {
-                        const float alpha = fminf(0.99f, ex2_approx(e0));
-                        const float tT = fmaf(-T0, alpha, T0);
-                        if (tT < 1e-4f) {
-                            d0 = true;
-                        } else {
-                            if (COUNT) ++n_blend;
-                            const float w = alpha * T0;
-                            r0 = fmaf(ap.z, w, r0);
-                            g0 = fmaf(ap.w, w, g0);
-                            b0 = fmaf(cb, w, b0);
-                            T0 = tT;
+                const float dyb = gm.y - py0f;
+                float e[kPix];
+                uint32_t con = 0;
+#pragma unroll
+                for (int k = 0; k < kPix; ++k) {
+                    const float dy = dyb - 2.0f * (float)k;
+                    // power log2 e = a' dx^2 + dy (b' dx + c' dy)
+                    const float p = fmaf(adx, dx, dy * fmaf(ap.x, dy, bdx));
+                    e[k] = p + ap.y;
+                    if (((live >> k) & 1u) && p <= 0.0f && e[k] >= kMinLog2Alpha) con |= 1u << k;
+                }
+                if (__any_sync(kFull, con != 0)) {
+                    const float cbl = sm.blue[buf][j];
+#pragma unroll
+                    for (int k = 0; k < kPix; ++k) {
+                        if ((con >> k) & 1u) {
+                            const float alpha = fminf(0.99f, ex2_approx(e[k]));
+                            const float tT = fmaf(-T[k], alpha, T[k]);
+                            if (tT < 1e-4f) {
+                                live &= ~(1u << k);
+                            } else {
+                                if (COUNT) ++n_blend;
+                                const float w = alpha * T[k];
+                                cr[k] = fmaf(ap.z, w, cr[k]);
+                                cg[k] = fmaf(ap.w, w, cg[k]);
+                                cb[k] = fmaf(cbl, w, cb[k]);
+                                T[k] = tT;
+                            }
                         }
                     }
-                    if (c1) {
-                        const float alpha = fminf(0.99f, ex2_approx(e1));
-                        const float tT = fmaf(-T1, alpha, T1);
-                        if (tT < 1e-4f) {
-                            d1 = true;
-                        } else {
-                            if (COUNT) ++n_blend;
-                            const float w = alpha * T1;
-                            r1 = fmaf(ap.z, w, r1);
-                            g1 = fmaf(ap.w, w, g1);
-                            b1 = fmaf(cb, w, b1);
-                            T1 = tT;
-                        }
+                    if (__all_sync(kFull, live == 0)) {
+                        stopped = true;
+                        break;
                     }
                 }
             }
-            __syncthreads();   // buffer `buf` is refilled by the next iteration's stage
+            if (COUNT && !stopped) n_eval += (uint64_t)(cnt - counted) * (uint64_t)__popc(live);
+            __syncwarp();   // buffer `buf` is refilled by the next iteration's stage
         }
         cp_async_wait<0>();
+        __syncwarp();
 
-        if (in0) {
-            if (SLICED) sl.state[sl.pix_base[v] + pix0] = make_float4(r0, g0, b0, d0 ? -T0 : T0);
-            const float r = fmaf(T0, bg_r, r0), gg = fmaf(T0, bg_g, g0), bb = fmaf(T0, bg_b, b0), a = 1.0f - T0;
-            if (vp.out_rgba8)
-                reinterpret_cast<uchar4*>(vp.out_rgba8)[pix0] = make_uchar4(to_u8(r), to_u8(gg), to_u8(bb), to_u8(a));
-            if (vp.out_rgba_f32) reinterpret_cast<float4*>(vp.out_rgba_f32)[pix0] = make_float4(r, gg, bb, a);
-        }
-        if (in1) {
-            if (SLICED) sl.state[sl.pix_base[v] + pix1] = make_float4(r1, g1, b1, d1 ? -T1 : T1);
-            const float r = fmaf(T1, bg_r, r1), gg = fmaf(T1, bg_g, g1), bb = fmaf(T1, bg_b, b1), a = 1.0f - T1;
-            if (vp.out_rgba8)
-                reinterpret_cast<uchar4*>(vp.out_rgba8)[pix1] = make_uchar4(to_u8(r), to_u8(gg), to_u8(bb), to_u8(a));
-            if (vp.out_rgba_f32) reinterpret_cast<float4*>(vp.out_rgba_f32)[pix1] = make_float4(r, gg, bb, a);
+#pragma unroll
+        for (int k = 0; k < kPix; ++k) {
+            const int py = py0 + 2 * k;
+            if (px < W && py < H) {
+                const size_t pix = (size_t)py * W + px;
+                if (SLICED) sl.state[sbase + pix] = make_float4(cr[k], cg[k], cb[k], ((live >> k) & 1u) ? T[k] : -T[k]);
+                const float r = fmaf(T[k], bg_r, cr[k]), gg = fmaf(T[k], bg_g, cg[k]);
+                const float bb = fmaf(T[k], bg_b, cb[k]), a = 1.0f - T[k];
+                if (vp.out_rgba8)
+                    reinterpret_cast<uchar4*>(vp.out_rgba8)[pix] = make_uchar4(to_u8(r), to_u8(gg), to_u8(bb), to_u8(a));
+                if (vp.out_rgba_f32) reinterpret_cast<float4*>(vp.out_rgba_f32)[pix] = make_float4(r, gg, bb, a);
+            }
         }
         if (SLICED) {
-            if (__syncthreads_count(d0 && d1) == kThreads && threadIdx.x == 0)
-                atomicOr(&sl.done[g >> 5], 1u << (g & 31));
+            if (__all_sync(kFull, live == 0) && lane == 0) atomicOr(&sl.done[g >> 5], 1u << (g & 31));
         } else {
             break;
         }
     }
     if (COUNT && counters) {
-        uint32_t s = n_eval;
 #pragma unroll
-        for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(kFull, s, d);
-        if (lane == 0 && s) atomicAdd(&counters[0], (unsigned long long)s);
-        uint32_t c = n_blend;
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(kFull, c, d);
-        if (lane == 0 && c) atomicAdd(&counters[2], (unsigned long long)c);
-        if (threadIdx.x == 0 && n_fetched) atomicAdd(&counters[1], (unsigned long long)n_fetched);
+        for (int d = 16; d > 0; d >>= 1) {
+            n_eval += __shfl_xor_sync(kFull, n_eval, d);
+            n_blend += __shfl_xor_sync(kFull, n_blend, d);
+        }
+        if (lane == 0) {
+            if (n_eval) atomicAdd(&counters[0], n_eval);
+            if (n_fetched) atomicAdd(&counters[1], n_fetched);
+            if (n_blend) atomicAdd(&counters[2], n_blend);
+        }
     }
 }
 
@@ -245,12 +275,13 @@ Status launch_blend(const uint2* ranges, const uint32_t* values, const SplatArra
                     int V, uint32_t total_tiles, uint32_t n_entries, const float* bg, unsigned long long* counters,
                     cudaStream_t st) {
     if (total_tiles == 0) return {};
+    const unsigned grid = (total_tiles + kWarps - 1) / kWarps;
     if (counters)
-        k_blend<false, true><<<total_tiles, kThreads, 0, st>>>(ranges, values, sp, views, V, n_entries, bg[0], bg[1],
-                                                               bg[2], counters, SliceBlendArgs{});
+        k_blend<false, true><<<grid, kThreads, 0, st>>>(ranges, values, sp, views, V, total_tiles, n_entries, bg[0],
+                                                        bg[1], bg[2], counters, SliceBlendArgs{});
     else
-        k_blend<false, false><<<total_tiles, kThreads, 0, st>>>(ranges, values, sp, views, V, n_entries, bg[0], bg[1],
-                                                                bg[2], nullptr, SliceBlendArgs{});
+        k_blend<false, false><<<grid, kThreads, 0, st>>>(ranges, values, sp, views, V, total_tiles, n_entries, bg[0],
+                                                         bg[1], bg[2], nullptr, SliceBlendArgs{});
     TIGAS_LAUNCHED();
     return {};
 }
@@ -269,11 +300,11 @@ Status launch_blend_slice(const uint2* ranges, const uint32_t* values, const Spl
     }
     TIGAS_CUDA_TRY(cudaMemsetAsync(sl.work_counter, 0, sizeof(uint32_t), st));
     if (counters)
-        k_blend<true, true><<<grid, kThreads, 0, st>>>(ranges, values, sp, views, V, n_entries, bg[0], bg[1], bg[2],
+        k_blend<true, true><<<grid, kThreads, 0, st>>>(ranges, values, sp, views, V, 0, n_entries, bg[0], bg[1], bg[2],
                                                        counters, sl);
     else
-        k_blend<true, false><<<grid, kThreads, 0, st>>>(ranges, values, sp, views, V, n_entries, bg[0], bg[1], bg[2],
-                                                        nullptr, sl);
+        k_blend<true, false><<<grid, kThreads, 0, st>>>(ranges, values, sp, views, V, 0, n_entries, bg[0], bg[1],
+                                                        bg[2], nullptr, sl);
     TIGAS_LAUNCHED();
     return {};
 }
