@@ -6,9 +6,10 @@
 // double-buffered (batch b+1 in flight while b is composited).
 //
 // For each staged entry the warp first tests the bounding box of its
-// alpha >= 1/255 region against the tile; a ballot over the batch keeps only
-// entries that can reach some pixel of the tile (a result-invariant skip:
-// every pixel the box excludes would skip the entry by the alpha test).  For
+// alpha >= 1/255 region against the bounding box of the tile's pixels that are
+// still compositing; a ballot over the batch keeps only entries that can reach
+// one of them (a result-invariant skip: a pixel the box excludes would skip
+// the entry by the alpha test, a pixel that stopped ignores it).  For
 // the kept entries each pixel computes alpha = min(0.99, o exp(power)) as
 // 2^(power log2 e + log2 o), skips alpha < 1/255 before any exponential, and
 // stops before the entry that would bring T below 1e-4.  A warp vote skips the
@@ -26,7 +27,7 @@ constexpr int kThreads = 32 * kWarps;
 constexpr int kWB = 32;                   // entries per warp batch
 constexpr int kPix = 8;                   // pixels per thread
 #ifndef TIGAS_BLEND_MIN_BLOCKS
-#define TIGAS_BLEND_MIN_BLOCKS 5
+#define TIGAS_BLEND_MIN_BLOCKS 6
 #endif
 constexpr int kMinBlocks = TIGAS_BLEND_MIN_BLOCKS;   // CTAs per SM the register budget targets
 constexpr uint32_t kFull = 0xFFFFFFFFu;
@@ -95,7 +96,8 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ values, S
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpStage& sm = stage_sm[warp];
     unsigned long long n_eval = 0, n_fetched = 0, n_blend = 0;
-    const uint32_t n_items = SLICED ? *sl.n_active : total_tiles;
+    const uint32_t n_long = SLICED ? sl.n_active[0] : 0u;
+    const uint32_t n_items = SLICED ? n_long + sl.n_active[1] : total_tiles;
     uint32_t item = SLICED ? 0u : blockIdx.x * kWarps + warp;
     for (;;) {
         if (SLICED) {
@@ -104,7 +106,7 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ values, S
             item = __shfl_sync(kFull, it, 0);
         }
         if (item >= n_items) break;
-        const uint32_t g = SLICED ? sl.active[item] : item;
+        const uint32_t g = SLICED ? sl.active[item < n_long ? item : sl.n_tiles - 1 - (item - n_long)] : item;
         int v = 0;
         {
             int lo = 0, hi = V;   // last view with tile_base <= g
@@ -121,8 +123,7 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ values, S
         const int px = tx * kTile + (lane & 15);
         const int py0 = ty * kTile + (lane >> 4);       // rows py0 + 2k
         const float pxf = (float)px + 0.5f, py0f = (float)py0 + 0.5f;
-        const float tx0 = (float)(tx * kTile) + 0.5f, tx1 = tx0 + 15.0f;
-        const float ty0 = (float)(ty * kTile) + 0.5f, ty1 = ty0 + 15.0f;
+        const float tx0 = (float)(tx * kTile) + 0.5f, ty0 = (float)(ty * kTile) + 0.5f;   // first pixel centre
         const uint64_t sbase = SLICED ? sl.pix_base[v] : 0;
 
         float T[kPix], cr[kPix], cg[kPix], cb[kPix];
@@ -174,11 +175,18 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ values, S
             }
             const uint32_t rem = end - start - (uint32_t)b * kWB;
             const int cnt = rem < (uint32_t)kWB ? (int)rem : kWB;
-            // the lane's own staged entry: can it reach any pixel of the tile?
-            const bool meets = lane < cnt && alpha_box_meets(sm.geom[buf][lane], sm.appear[buf][lane], tx0, tx1, ty0, ty1);
+            if (__all_sync(kFull, live == 0)) break;
+            // bounding box of the pixels still compositing (at least one is)
+            const uint32_t col = lane & 15, row = lane >> 4;
+            const uint32_t c_lo = __reduce_min_sync(kFull, live ? col : 16u);
+            const uint32_t c_hi = __reduce_max_sync(kFull, live ? col : 0u);
+            const uint32_t r_lo = __reduce_min_sync(kFull, live ? row + 2u * (uint32_t)(__ffs(live) - 1) : 16u);
+            const uint32_t r_hi = __reduce_max_sync(kFull, live ? row + 2u * (uint32_t)(31 - __clz(live)) : 0u);
+            // the lane's own staged entry: can it reach one of those pixels?
+            const bool meets = lane < cnt && alpha_box_meets(sm.geom[buf][lane], sm.appear[buf][lane], tx0 + (float)c_lo,
+                                                             tx0 + (float)c_hi, ty0 + (float)r_lo, ty0 + (float)r_hi);
             uint32_t kept = __ballot_sync(kFull, meets);
             __syncwarp();   // every lane's copies visible to the warp
-            if (__all_sync(kFull, live == 0)) break;
             if (COUNT) n_fetched += (uint64_t)cnt;
             int counted = 0;   // entries of this batch already counted as evaluated
             bool stopped = false;

@@ -478,7 +478,7 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     unsigned long long* d_counters = ctx.fixed.take<unsigned long long>(4);
     uint32_t* d_flags = ctx.fixed.take<uint32_t>(2);
     uint32_t* d_visible = ctx.fixed.take<uint32_t>(kMaxViews);
-    uint32_t* d_misc = ctx.fixed.take<uint32_t>(4);       // [n_active, work counter]
+    uint32_t* d_misc = ctx.fixed.take<uint32_t>(4);       // [long tiles, short tiles, work counter]
     uint64_t* d_pix_base = ctx.fixed.take<uint64_t>(kMaxViews);
     SplatArrays sp{};
     sp.geom = ctx.fixed.take<float4>(E);
@@ -543,7 +543,7 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     uint64_t total_pairs = 0;
     int passes = 0;
     uint64_t a = 0;
-    SliceBlendArgs sl{active, d_misc, d_misc + 1, state, d_pix_base, done};
+    SliceBlendArgs sl{active, d_misc, d_misc + 2, state, d_pix_base, done, total_tiles};
     if (stat) {
         // pair buffers for the fixed capacity, taken once
         ctx.pairs.reset();

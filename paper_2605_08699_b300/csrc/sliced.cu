@@ -156,8 +156,10 @@ k_emit_slice(const uint32_t* __restrict__ order, const uint2* __restrict__ rect_
     }
 }
 
-// Tile ranges by binary search; tiles with pairs in this slice that are not
-// done are appended to the active list (order irrelevant: tiles are independent).
+// Tile ranges by binary search.  Tiles with pairs in this slice that are not
+// done form the active list: tiles with at least kHeavyTile pairs from the
+// front (count n_active[0]), the others from the back (count n_active[1]), so
+// that the blend's dynamic scheduler starts the longest lists first.
 __device__ inline uint64_t lower_bound_u32(const uint32_t* __restrict__ keys, uint64_t n, uint32_t t) {
     uint64_t lo = 0, hi = n;
     while (lo < hi) {
@@ -175,20 +177,30 @@ k_ranges_active(const uint32_t* __restrict__ keys, uint64_t n_cap, const uint64_
     if (n > n_cap) n = n_cap;
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0 && n > 0 && keys[n - 1] >= n_tiles) atomicOr(overflow, 2u);
-    bool act = false;
+    bool act = false, heavy = false;
     if (t < n_tiles) {
         const uint64_t lo = lower_bound_u32(keys, n, t);
         const uint64_t hi = lower_bound_u32(keys, n, t + 1);
         ranges[t] = make_uint2((uint32_t)lo, (uint32_t)hi);
         act = hi > lo && !tile_done(done, t);
+        heavy = act && hi - lo >= kHeavyTile;
     }
-    const uint32_t m = __ballot_sync(kFull, act);
-    if (!m) return;
     const int lane = threadIdx.x & 31;
-    uint32_t base = 0;
-    if (lane == __ffs(m) - 1) base = atomicAdd(n_active, (uint32_t)__popc(m));
-    base = __shfl_sync(kFull, base, __ffs(m) - 1);
-    if (act) active[base + __popc(m & ((1u << lane) - 1u))] = t;
+    const uint32_t below = (1u << lane) - 1u;
+    const uint32_t mh = __ballot_sync(kFull, heavy);
+    const uint32_t ml = __ballot_sync(kFull, act && !heavy);
+    if (mh) {
+        uint32_t base = 0;
+        if (lane == __ffs(mh) - 1) base = atomicAdd(&n_active[0], (uint32_t)__popc(mh));
+        base = __shfl_sync(kFull, base, __ffs(mh) - 1);
+        if (heavy) active[base + __popc(mh & below)] = t;
+    }
+    if (ml) {
+        uint32_t base = 0;
+        if (lane == __ffs(ml) - 1) base = atomicAdd(&n_active[1], (uint32_t)__popc(ml));
+        base = __shfl_sync(kFull, base, __ffs(ml) - 1);
+        if (act && !heavy) active[n_tiles - 1 - (base + __popc(ml & below))] = t;
+    }
 }
 
 }  // namespace
@@ -231,7 +243,7 @@ Status launch_ranges_active(const uint32_t* keys, uint64_t n_cap, const uint64_t
                             uint32_t n_tiles, const uint32_t* done, uint32_t* active, uint32_t* n_active,
                             uint32_t* overflow, cudaStream_t st) {
     if (n_tiles == 0) return {};
-    TIGAS_CUDA_TRY(cudaMemsetAsync(n_active, 0, sizeof(uint32_t), st));
+    TIGAS_CUDA_TRY(cudaMemsetAsync(n_active, 0, 2 * sizeof(uint32_t), st));
     k_ranges_active<<<(n_tiles + 255) / 256, 256, 0, st>>>(keys, n_cap, d_n, ranges, n_tiles, done, active, n_active,
                                                            overflow);
     TIGAS_LAUNCHED();

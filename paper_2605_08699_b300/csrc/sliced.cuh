@@ -5,6 +5,8 @@
 
 namespace tigas {
 
+constexpr uint32_t kHeavyTile = 128;   // pairs of a slice that make a tile "long"
+
 // (C, T) = (0, 1) for every pixel of every view, background in the outputs.
 // pix_base[v]: offset of view v's first pixel in `state`.
 Status launch_init_state(const ViewParams* views, int V, uint32_t total_tiles, const uint64_t* pix_base,
@@ -25,7 +27,9 @@ Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64
                          uint32_t* keys, uint32_t* values, uint64_t pair_cap, uint32_t* overflow, cudaStream_t st);
 
 // Tile ranges of the slice's sorted keys, and the list of tiles with pairs
-// that are not done (*n_active entries of `active`, zeroed here).
+// that are not done: n_active[0] tiles with >= kHeavyTile pairs at the front
+// of `active`, n_active[1] others at its back (active[n_tiles - 1 - k]);
+// both counts are zeroed here.
 // The key count is min(*d_n, n_cap) when d_n is given, else n_cap.
 Status launch_ranges_active(const uint32_t* keys, uint64_t n_cap, const uint64_t* d_n, uint2* ranges,
                             uint32_t n_tiles, const uint32_t* done, uint32_t* active, uint32_t* n_active,
@@ -36,11 +40,12 @@ Status launch_ranges_active(const uint32_t* keys, uint64_t n_cap, const uint64_t
 // store the state and the outputs, and mark tiles whose pixels all stopped.
 struct SliceBlendArgs {
     const uint32_t* active;
-    const uint32_t* n_active;
+    const uint32_t* n_active;   // [long tiles at the front, short tiles at the back]
     uint32_t* work_counter;     // zeroed by the launcher
     float4* state;              // per pixel (C.rgb, T), T negated once the pixel stopped
     const uint64_t* pix_base;   // per view
     uint32_t* done;             // per-tile bitmap
+    uint32_t n_tiles;           // capacity of `active` (all tiles of the launch set)
 };
 Status launch_blend_slice(const uint2* ranges, const uint32_t* values, const SplatArrays& sp,
                           const ViewParams* views, int V, uint32_t n_entries, const float* bg,
