@@ -306,9 +306,12 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     serving = None
     if not args.no_serving:
         serving = run_serving(tg, torch, dev, h16, K, W, H, trajs, args)
+    trace = None
+    if not args.no_serving and args.trace_seconds > 0:
+        trace = run_serving_trace(tg, torch, dev, args)
 
     res = {"value": value, "elapsed_ms": elapsed_ms, "frames": frames, "per_step": per_step, "stage_ms": stage_ms,
-           "clocks": clocks, "launches": launches, "e2e": e2e, "plain_fp32": plain, "serving": serving,
+           "clocks": clocks, "launches": launches, "e2e": e2e, "plain_fp32": plain, "serving": serving, "trace": trace,
            "step_ms_host": step_ms_host, "scene": scene}
     h16.free()
     h32.free()
@@ -355,6 +358,98 @@ def run_serving(tg, torch, dev, h16, K, W, H, trajs, args) -> dict:
             "latency": "submit to frame complete in the client's buffer"}
 
 
+def run_serving_trace(tg, torch, dev, args) -> dict:
+    """Open-loop multi-client trace through the request server, twice: served
+    FP16 (batched launch sets, overlapping slots) and plain FP32 (one request
+    at a time, same server code with max_batch = max_inflight = 1).
+
+    Clients request at fixed Poisson rates; client c uses scene c mod 4 of
+    1M/2M/3M/6M Gaussians; each request's resolution comes from the client's
+    Latency ABR over its simulated download throughput, so both arms render
+    the same requests.  A queued request of a client is superseded by its
+    next one (latest pose wins)."""
+    from paper_2605_08699_b300.abr import assign_levels
+
+    tr = synth.serving_trace(n_clients=args.trace_clients, seconds=args.trace_seconds)
+    levels = synth.ABR_LEVELS
+    lvl = assign_levels(tr.client, tr.bw, levels)
+    intr = [synth.default_intrinsics(w, h) for w, h in levels]
+    n_pose = int(math.ceil(args.trace_seconds * 90)) + 2
+    trajs = [synth.trajectory(synth.BASE_SEED + 600 + c, n_poses=n_pose) for c in range(args.trace_clients)]
+    sizes = [int(x) for x in args.trace_scenes.split(",")]
+    raw = [synth.make_scene(n, seed=synth.BASE_SEED + 5 + 10 * i) for i, n in enumerate(sizes)]
+    W1, H1 = levels[-1]
+    bufs = [[torch.empty(W1 * H1 * 4, dtype=torch.uint8, device=dev) for _ in range(3)]
+            for _ in range(args.trace_clients)]
+    warm = min(1.0, 0.2 * tr.seconds)
+
+    def replay(handles, max_batch, max_inflight):
+        lat, wait, px, n_ok, n_sup, n_err = [], [], 0, 0, 0, 0
+        lag = []
+        rot = [0] * args.trace_clients
+        R, i, outstanding = tr.t.size, 0, 0
+        with tg.Server(max_batch=max_batch, max_inflight=max_inflight) as srv:
+            t0 = time.perf_counter()
+            while True:
+                now = time.perf_counter() - t0
+                while i < R and tr.t[i] <= now:
+                    c, l = int(tr.client[i]), int(lvl[i])
+                    w, h = levels[l]
+                    b = bufs[c][rot[c] % 3]
+                    rot[c] += 1
+                    srv.submit(handles[int(tr.scene[i])], trajs[c][int(tr.pose_index[i])], intr[l], w, h, b,
+                               client_id=c)
+                    if tr.t[i] >= warm:
+                        lag.append(time.perf_counter() - t0 - tr.t[i])
+                    i += 1
+                    outstanding += 1
+                dt = (tr.t[i] - (time.perf_counter() - t0)) if i < R else 0.2
+                for comp in srv.poll(1024, timeout_us=max(0, int(dt * 1e6)) if dt > 2e-4 else 0):
+                    outstanding -= 1
+                    if comp.submit_us * 1e-6 - t0 < warm:
+                        continue
+                    if comp.status == 0:
+                        n_ok += 1
+                        px += comp.width * comp.height
+                        lat.append((comp.done_us - comp.submit_us) * 1e-3)
+                        wait.append((comp.admit_us - comp.submit_us) * 1e-3)
+                    elif comp.status == 4:
+                        n_sup += 1
+                    else:
+                        n_err += 1
+                if i >= R and outstanding == 0:
+                    break
+        T = tr.seconds - warm
+        lat = np.array(lat) if lat else np.array([float("nan")])
+        return {"frames_per_s": n_ok / T, "megapixels_per_s": px / T / 1e6,
+                "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+                "queue_ms_p50": float(np.percentile(wait, 50)) if wait else None,
+                "frames": n_ok, "superseded": n_sup, "errors": n_err,
+                "submit_lag_ms_p99": float(np.percentile(lag, 99) * 1e3) if lag else None}
+
+    out = {"trace": f"{args.trace_clients} clients, Poisson arrivals at U[60,90] Hz each, {tr.seconds:g} s "
+                    f"(first {warm:g} s not counted), scenes {args.trace_scenes} Gaussians round-robin, "
+                    "resolutions from each client's Latency ABR (ladder f x 1920x1080, 0.2 B/px, "
+                    "bandwidth redrawn every second, ln N(ln 22.4 Mbit/s, 0.75) clipped to [5, 100])",
+           "requests": int(tr.t.size), "offered_per_s": tr.t.size / tr.seconds,
+           "level_mix": {f"{w}x{h}": int(np.sum(lvl == k)) for k, (w, h) in enumerate(levels)},
+           "latency": "submit to frame complete in the client's buffer (server clock)"}
+    hs = [tg.scene_from(r, storage=tg.STORAGE_FP16) for r in raw]
+    try:
+        out["served_fp16"] = dict(replay(hs, args.serve_batch, args.serve_inflight),
+                                  max_batch=args.serve_batch, slots=args.serve_inflight, storage="fp16")
+    finally:
+        for h in hs:
+            h.free()
+    hs = [tg.scene_from(r, storage=tg.STORAGE_FP32) for r in raw]
+    try:
+        out["plain_fp32"] = dict(replay(hs, 1, 1), max_batch=1, slots=1, storage="fp32")
+    finally:
+        for h in hs:
+            h.free()
+    return out
+
+
 # --------------------------------------------------------------- reference
 
 
@@ -398,6 +493,9 @@ def main(argv=None) -> int:
     ap.add_argument("--serve-inflight", type=int, default=2)
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--trace-seconds", type=float, default=10.0, help="open-loop serving trace length (0: skip)")
+    ap.add_argument("--trace-clients", type=int, default=64)
+    ap.add_argument("--trace-scenes", default="1000000,2000000,3000000,6000000")
     ap.add_argument("--plain-frames", type=int, default=64, help="frames of the plain FP32 single-request path")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -441,7 +539,7 @@ def main(argv=None) -> int:
                            "p99_step": round(float(np.percentile(steps_ms, 99)), 3),
                            "note": "host time of one synchronous launch set of views_per_step frames"},
             "schedule": "depth-sliced (8 nearest-first slices, tiles that stopped are dropped)",
-            "served_fp16": r["serving"], "plain_fp32": r["plain_fp32"],
+            "served_fp16": r["serving"], "plain_fp32": r["plain_fp32"], "serving_trace": r["trace"],
             "roofline": roof, "stages": stages, "per_step": {k: int(v) for k, v in r["per_step"].items()},
             "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": int(r["launches"]), "clocks": r["clocks"],
         }

@@ -283,8 +283,13 @@ tigas_status tigas_profile_enable(int enable);
 tigas_status tigas_profile_read(double* ms, uint64_t* calls, int reset);
 
 /* Launch sets of the sliced schedule are captured as CUDA graphs per shape
- * (scene, view count and resolutions) and replayed; the first launch set of
- * a shape runs without a graph.  enable=0 turns graphs off (default on). */
+ * (scene, view count and resolutions) when a shape appears a second time, and
+ * replayed from then on.  A shape's first launch set runs directly with a
+ * pair capacity per slice taken from the largest slice seen so far (exactly,
+ * with a host round trip per slice, while nothing has been seen); a launch
+ * set that outgrows its capacity is rendered again exactly before the call
+ * returns.  enable=0 turns graphs off (default on).  Every call also makes the
+ * idle render contexts forget their graphs, seen shapes and capacities. */
 tigas_status tigas_set_graphs(int enable);
 
 /* ------------------------------------------------------------------ misc */

@@ -132,9 +132,13 @@ Status do_render(Scene* scene, int V, const tigas_pose* poses, const tigas_intri
     collect_profile(ctx);
     if (res.graph_slices > 0) {
         if (ctx.h_flags[0] & 1u) {
-            // a slice outgrew the captured pair capacity: render this frame exactly
-            // and capture again (with the new counts) on the next call
-            drop_graphs(ctx);
+            // a slice outgrew the fixed pair capacity: render this frame exactly;
+            // a graph is captured again (with the new counts) on the next call,
+            // a direct launch set takes a larger capacity next time
+            if (res.direct_static)
+                ctx.slice_ratio *= 2.0;
+            else
+                drop_graphs(ctx);
             TIGAS_TRY(render_frame(scene, req, ctx, st, &res));
             for (int v = 0; v < V; ++v) {
                 const size_t px = (size_t)ws[v] * hs[v];
@@ -147,9 +151,14 @@ Status do_render(Scene* scene, int V, const tigas_pose* poses, const tigas_intri
             TIGAS_CUDA_TRY(cudaStreamSynchronize(st));
             collect_profile(ctx);
         } else {
-            uint64_t P = 0;
-            for (int i = 0; i < res.graph_slices; ++i) P += ctx.h_total[i];
+            uint64_t P = 0, mx = 0;
+            for (int i = 0; i < res.graph_slices; ++i) {
+                P += ctx.h_total[i];
+                mx = ctx.h_total[i] > mx ? ctx.h_total[i] : mx;
+            }
             res.pairs = P;
+            const double scale = pair_scale(scene, req);
+            if (scale > 0.0 && (double)mx / scale > ctx.slice_ratio) ctx.slice_ratio = (double)mx / scale;
         }
     }
     if (ctx.h_flags[0] & 1u) return {TIGAS_ERR_OVERFLOW, "pair buffer overflow"};
@@ -222,6 +231,7 @@ using namespace tigas;
 TIGAS_API const char* tigas_last_error(void) { return last_error(); }
 TIGAS_API tigas_status tigas_set_graphs(int enable) {
     g_use_graphs.store(enable != 0);
+    forget_launch_sets();
     return TIGAS_OK;
 }
 

@@ -207,6 +207,15 @@ void release_context(RenderContext* ctx) {
     g_pool.push_back(ctx);
 }
 
+void forget_launch_sets() {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (RenderContext* c : g_pool) {
+        drop_graphs(*c);
+        c->seen_keys.clear();
+        c->slice_ratio = 0.0;
+    }
+}
+
 bool is_device_pointer(const void* p) {
     cudaPointerAttributes a;
     cudaError_t e = cudaPointerGetAttributes(&a, p);
@@ -508,6 +517,7 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     TIGAS_CUDA_TRY(cudaMemcpyAsync(d_pix_base, hv + sizeof(ViewParams) * kMaxViews, sizeof(uint64_t) * V,
                                    cudaMemcpyHostToDevice, st));
     TIGAS_CUDA_TRY(cudaMemsetAsync(d_flags, 0, sizeof(uint32_t) * 2, st));
+    TIGAS_CUDA_TRY(cudaMemsetAsync(d_total, 0, sizeof(uint64_t) * (kMaxSlices + 2), st));   // empty slices count 0
     TIGAS_CUDA_TRY(cudaMemsetAsync(done, 0, L.done_words * 4, st));
     if (sp.q_dbg) TIGAS_CUDA_TRY(cudaMemsetAsync(sp.q_dbg, 0, E * 4, st));
     if (req.want_counters) TIGAS_CUDA_TRY(cudaMemsetAsync(d_counters, 0, sizeof(unsigned long long) * 4, st));
@@ -660,7 +670,32 @@ Status render_sliced_graph(Scene* scene, FrameRequest& req, RenderContext& ctx, 
         *rendered = true;
         return {};
     }
-    // first frame of this shape: render exactly, learn the slices' pair counts
+    const double scale = pair_scale(scene, req);
+    bool seen = false;
+    for (auto& k : ctx.seen_keys) seen = seen || k == key;
+    if (!seen) {
+        // first launch set of this shape: no capture (shapes that do not repeat,
+        // as in a server's mixed-resolution batches, would pay it every time)
+        if (ctx.seen_keys.size() >= 64) ctx.seen_keys.erase(ctx.seen_keys.begin());
+        ctx.seen_keys.push_back(key);
+        if (ctx.slice_ratio > 0.0) {
+            // fixed capacity from the largest slice seen so far: no host round trips;
+            // an overflow is caught after the stream completes and rendered exactly
+            const uint64_t cap = (uint64_t)(1.5 * ctx.slice_ratio * scale) + 65536;
+            size_t fb = 0, pb = 0;
+            TIGAS_TRY(sliced_workspace(scene, req, cap, &fb, &pb));
+            TIGAS_TRY(ctx.fixed.reserve(fb));
+            TIGAS_TRY(ctx.pairs.reserve(pb));
+            TIGAS_TRY(render_frame_sliced(scene, req, ctx, st, res, cap, nullptr));
+            if (res) {
+                res->graph_slices = req.n_slices < 1 ? 1 : (req.n_slices > kMaxSlices ? kMaxSlices : req.n_slices);
+                res->direct_static = true;
+            }
+            *rendered = true;
+            return {};
+        }
+    }
+    // render exactly and learn the slices' pair counts; capture when the shape repeats
     uint64_t sp[kMaxSlices] = {};
     TIGAS_TRY(render_frame_sliced(scene, req, ctx, st, res, 0, sp));
     TIGAS_CUDA_TRY(cudaStreamSynchronize(st));
@@ -670,6 +705,8 @@ Status render_sliced_graph(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     if (ctx.h_flags[0] != 0) return {};
     uint64_t mx = 0;
     for (int i = 0; i < kMaxSlices; ++i) mx = sp[i] > mx ? sp[i] : mx;
+    if (scale > 0.0 && (double)mx / scale > ctx.slice_ratio) ctx.slice_ratio = (double)mx / scale;
+    if (!seen) return {};
     const uint64_t cap = mx + mx / 2 + 65536;
     size_t fb = 0, pb = 0;
     TIGAS_TRY(sliced_workspace(scene, req, cap, &fb, &pb));
@@ -711,6 +748,15 @@ Status render_sliced_graph(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     }
     ctx.graphs.push_back(entry);
     return {};
+}
+
+double pair_scale(const Scene* scene, const FrameRequest& req) {
+    double s = 0.0;
+    for (int v = 0; v < req.V; ++v) {
+        const double f = std::sqrt((double)req.views[v].W * req.views[v].H / (1920.0 * 1080.0));
+        s += (1.0 + 3.0 * f) * (1.0 + 3.0 * f) / 16.0;
+    }
+    return s * (double)scene->view.n;
 }
 
 void drop_graphs(RenderContext& ctx) {

@@ -60,6 +60,7 @@ struct FrameResult {
     uint32_t* d_visible = nullptr;
     unsigned long long* d_counters = nullptr;   // [evals, fetched, blends] when requested
     int graph_slices = 0;                       // replayed graph: pairs = sum of ctx.h_total[0..slices)
+    bool direct_static = false;                 // fixed-capacity launch set run directly, not from a graph
 };
 
 // Render state of one in-flight frame or launch set: stream, arenas, pinned staging.
@@ -88,6 +89,10 @@ struct RenderContext {
         FrameResult res;
     };
     std::vector<Graph> graphs;
+    // launch-set shapes seen once (captured on their second appearance)
+    std::vector<std::vector<int64_t>> seen_keys;
+    // largest slice pair count seen, per entry and unit of view scale (pair_scale)
+    double slice_ratio = 0.0;
     Status init();
     void destroy();
 };
@@ -128,6 +133,11 @@ Status render_sliced_graph(Scene* scene, FrameRequest& req, RenderContext& ctx, 
                            bool* rendered);
 extern std::atomic<bool> g_use_graphs;
 void drop_graphs(RenderContext& ctx);
+// Idle contexts drop their graphs, the shapes they have seen and the learned
+// slice capacity.
+void forget_launch_sets();
+// Pair-count scale of a launch set: sum over views of n (1 + 3 sqrt(W H / 1080p))^2 / 16.
+double pair_scale(const Scene* scene, const FrameRequest& req);
 
 // Context pool used by the synchronous entry points.
 RenderContext* acquire_context(Status* err);

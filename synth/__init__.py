@@ -197,3 +197,50 @@ def trajectory(seed: int, n_poses: int = 300, start: Pose = BASE_POSE, step_t: f
 
 def config_trajectory(k: int, i: int = 0, n_poses: int = 300) -> list[Pose]:
     return trajectory(BASE_SEED + 100 + k + 1000 * i, n_poses)
+
+
+@dataclass
+class ServingTrace:
+    """Open-loop request trace of a multi-client serving run, sorted by arrival.
+
+    Per request: arrival time (s), client, scene index, index into the
+    client's pose trajectory (90 Hz samples), and the client's link bandwidth
+    (bytes/s) in the one-second regime the request falls in."""
+    t: np.ndarray            # float64 [R]
+    client: np.ndarray       # int32 [R]
+    scene: np.ndarray        # int32 [R]
+    pose_index: np.ndarray   # int32 [R]
+    bw: np.ndarray           # float64 [R], bytes/s
+    rates_hz: np.ndarray     # float64 [C]
+    seconds: float
+    n_scenes: int
+
+
+def serving_trace(seed: int = BASE_SEED + 500, n_clients: int = 64, seconds: float = 10.0,
+                  rate_lo: float = 60.0, rate_hi: float = 90.0, n_scenes: int = 4,
+                  bw_median_mbit: float = 22.4, bw_log_sigma: float = 0.75,
+                  bw_lo_mbit: float = 5.0, bw_hi_mbit: float = 100.0) -> ServingTrace:
+    """Clients with a fixed request rate ~ U[rate_lo, rate_hi] Hz and Poisson
+    arrivals; client c renders scene c mod n_scenes (round robin); each client's
+    bandwidth is redrawn every second with ln(bw) ~ N(ln median, sigma),
+    clipped to [lo, hi] Mbit/s."""
+    rates = rate_lo + (rate_hi - rate_lo) * uniforms(seed, 11, n_clients)
+    n_sec = int(math.ceil(seconds))
+    z = normals(seed, 12, n_clients * n_sec).reshape(n_clients, n_sec)
+    bw_mbit = np.clip(np.exp(math.log(bw_median_mbit) + bw_log_sigma * z), bw_lo_mbit, bw_hi_mbit)
+    ts, cs, ps, bs = [], [], [], []
+    for c in range(n_clients):
+        m = int(rates[c] * seconds * 1.5) + 64
+        u = uniforms(seed + 1 + c, 13, m)
+        arr = np.cumsum(-np.log1p(-u) / rates[c])
+        arr = arr[arr < seconds]
+        ts.append(arr)
+        cs.append(np.full(arr.size, c, np.int32))
+        ps.append(np.floor(arr * 90.0).astype(np.int32))
+        bs.append(bw_mbit[c, np.minimum(np.floor(arr).astype(np.int64), n_sec - 1)] * 1e6 / 8.0)
+    t = np.concatenate(ts)
+    o = np.argsort(t, kind="stable")
+    client = np.concatenate(cs)[o]
+    return ServingTrace(t=t[o], client=client, scene=(client % n_scenes).astype(np.int32),
+                        pose_index=np.concatenate(ps)[o], bw=np.concatenate(bs)[o], rates_hz=rates,
+                        seconds=float(seconds), n_scenes=n_scenes)

@@ -276,7 +276,8 @@ def test_graph_replay_equals_direct_launches(h1, cuda):
     tg.set_graphs(False)
     ref = [_batch(h1, tr[i:i + 3], levels, cuda) for i in (0, 10, 20)]
     tg.set_graphs(True)
-    got = [_batch(h1, tr[i:i + 3], levels, cuda) for i in (0, 10, 20)]   # capture, then two replays
+    # first: direct fixed-capacity launch set; second: exact + capture; third: replay
+    got = [_batch(h1, tr[i:i + 3], levels, cuda) for i in (0, 10, 20)]
     for a, b in zip(ref, got):
         for x, y in zip(a, b):
             assert np.array_equal(x, y)
@@ -297,6 +298,21 @@ def test_graph_overflow_falls_back_to_exact(cuda, s1):
         got = _batch(h, near, levels, cuda)
         got2 = _batch(h, near, levels, cuda)
     assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[0], got2[0])
+
+
+def test_direct_fixed_capacity_overflow_renders_exactly(cuda, s1):
+    # the capacity learned on a far pose is far too small for a new shape on a
+    # near pose: the direct launch set overflows and the frame is rendered exactly
+    far = [synth.Pose(0.0, 0.0, (0.0, 0.0, -12.0))]
+    near = [synth.Pose(0.1, 0.05, (0.0, 0.0, -2.2))]
+    with tg.scene_from(s1) as h:
+        tg.set_graphs(False)
+        ref = _batch(h, near, [(300, 200)], cuda)
+        tg.set_graphs(True)   # idle contexts forget learned capacities
+        _batch(h, far, [(320, 240)], cuda)
+        got = [_batch(h, near, [(300, 200)], cuda) for _ in range(3)]   # direct, exact + capture, replay
+    for g in got:
+        assert np.array_equal(ref[0], g[0])
 
 
 # -------------------------------------------------------------- serving
