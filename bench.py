@@ -210,6 +210,19 @@ def roofline(stage_ms: dict, per_step: dict, peaks: dict, clocks: dict, steps: i
 # ---------------------------------------------------------------- GPU arm
 
 
+def aggregate_over_ranks(elapsed_ms: float, frames: int, world: int, device=None) -> tuple[float, int]:
+    """Whole-job timing: the slowest rank's time and every rank's frames
+    (ranks render independent replicas; this is the only collective)."""
+    if world <= 1:
+        return float(elapsed_ms), int(frames)
+    import torch
+    t = torch.tensor([float(elapsed_ms)], dtype=torch.float64, device=device)
+    n = torch.tensor([int(frames)], dtype=torch.int64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    torch.distributed.all_reduce(n, op=torch.distributed.ReduceOp.SUM)
+    return float(t.item()), int(n.item())
+
+
 def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     import torch
     import paper_2605_08699_b300 as tg
@@ -230,6 +243,11 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
         tg.render_batch(handle, poses, [K] * V, [W] * V, [H] * V, o, stream=stream)
 
     tg.profile_enable(True)        # stage events are part of the captured launch sets: same shape as timed
+    schedule = tg.get_schedule()
+    if not args.no_autotune:
+        # untimed: pick the sliced schedule for this launch-set shape (with the stage events on, as timed)
+        sets = [[trajs[v][(s * 7 + v + 150) % len(trajs[v])] for v in range(V)] for s in range(8)]
+        schedule, _ = tg.autotune(h16, sets, [K] * V, [W] * V, [H] * V, outs, iters=4)
     for s in range(args.warmup):
         step(s)
     torch.cuda.synchronize()
@@ -241,7 +259,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     per_step = {"pairs": st0["n_pairs"], "kept": st0["n_visible"], "evals": st0["blend_evals"],
                 "fetched": st0["blend_fetched"], "contribs": st0["blend_contribs"], "sort_passes": st0["sort_passes"],
                 "entries": V * scene.n, "gaussians": scene.n, "attr_bytes": 124, "tiles": V * TX * TY,
-                "slices": 8}
+                "slices": schedule["n_slices"]}
 
     # ---- timed region: device outputs, CUDA events on the launching stream
     tg.profile_read(reset=True)
@@ -249,6 +267,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     clk.start()
     time.sleep(0.3)
     launches0 = tg.kernel_launches()
+    rerenders0 = tg.exact_rerenders()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -265,14 +284,11 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
         torch.distributed.barrier()
     elapsed_ms = e0.elapsed_time(e1)
     launches = tg.kernel_launches() - launches0
+    rerenders = tg.exact_rerenders() - rerenders0
     clocks = clk.stop()
     tg.profile_enable(False)
     stage_ms = tg.profile_read(reset=True)
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    frames = V * args.steps * world
+    elapsed_ms, frames = aggregate_over_ranks(elapsed_ms, V * args.steps, world, dev)
     value = frames / (elapsed_ms * 1e-3)
 
     # ---- end to end: pinned host outputs, copies inside the timed region
@@ -282,7 +298,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     for s in range(args.steps):
         step(args.warmup + s, o=houts)
     e2e_s = time.perf_counter() - t0
-    e2e = {"value": V * args.steps / e2e_s, "unit": "frames/s",
+    e2e_ms, e2e_frames = aggregate_over_ranks(e2e_s * 1e3, V * args.steps, world, dev)
+    e2e = {"value": e2e_frames / (e2e_ms * 1e-3), "unit": "frames/s",
            "h2d_bytes_per_step": V * (40 + 32 + 8 + 8), "d2h_bytes_per_step": V * W * H * 4}
 
     # ---- plain FP32 single-request path, one frame at a time
@@ -310,7 +327,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     if not args.no_serving and args.trace_seconds > 0:
         trace = run_serving_trace(tg, torch, dev, args)
 
-    res = {"value": value, "elapsed_ms": elapsed_ms, "frames": frames, "per_step": per_step, "stage_ms": stage_ms,
+    res = {"schedule": schedule, "rerenders": rerenders, "value": value, "elapsed_ms": elapsed_ms, "frames": frames, "per_step": per_step, "stage_ms": stage_ms,
            "clocks": clocks, "launches": launches, "e2e": e2e, "plain_fp32": plain, "serving": serving, "trace": trace,
            "step_ms_host": step_ms_host, "scene": scene}
     h16.free()
@@ -493,6 +510,7 @@ def main(argv=None) -> int:
     ap.add_argument("--serve-inflight", type=int, default=2)
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule")
     ap.add_argument("--trace-seconds", type=float, default=10.0, help="open-loop serving trace length (0: skip)")
     ap.add_argument("--trace-clients", type=int, default=64)
     ap.add_argument("--trace-scenes", default="1000000,2000000,3000000,6000000")
@@ -538,7 +556,9 @@ def main(argv=None) -> int:
             "latency_ms": {"p50_step": round(float(np.percentile(steps_ms, 50)), 3),
                            "p99_step": round(float(np.percentile(steps_ms, 99)), 3),
                            "note": "host time of one synchronous launch set of views_per_step frames"},
-            "schedule": "depth-sliced (8 nearest-first slices, tiles that stopped are dropped)",
+            "schedule": dict(r["schedule"], kind="depth-sliced: nearest-first geometric slices, tiles whose "
+                                                  "pixels all stopped are dropped", autotuned=not args.no_autotune,
+                             exact_rerenders_timed=r["rerenders"]),
             "served_fp16": r["serving"], "plain_fp32": r["plain_fp32"], "serving_trace": r["trace"],
             "roofline": roof, "stages": stages, "per_step": {k: int(v) for k, v in r["per_step"].items()},
             "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": int(r["launches"]), "clocks": r["clocks"],

@@ -282,6 +282,57 @@ tigas_status tigas_profile_enable(int enable);
  * reset=1 clears the accumulators after reading. */
 tigas_status tigas_profile_read(double* ms, uint64_t* calls, int reset);
 
+/* ------------------------------------------------------------ scheduling */
+
+/* Parameters of the depth-sliced schedule every launch set takes.  Frames do
+ * not depend on them (only the time to render them does).
+ *  n_slices:          depth slices, 1..16 (default 8)
+ *  first_slice_inv:   the nearest slice holds 1/first_slice_inv of the kept
+ *                     entries, later ones grow geometrically to all of them,
+ *                     1..4096 (default 64)
+ *  blend_ctas_per_sm: persistent blend CTAs per SM, 0..64; 0 or more than
+ *                     fit means as many as fit (default 0) */
+typedef struct {
+    int n_slices;
+    int first_slice_inv;
+    int blend_ctas_per_sm;
+} tigas_schedule;
+
+/* Set / read the process-wide schedule.  Errors: INVALID (out of range).
+ * Launch sets already in flight keep the schedule they started with. */
+tigas_status tigas_set_schedule(const tigas_schedule* schedule);
+tigas_status tigas_get_schedule(tigas_schedule* schedule);
+
+/* Autotuner of the batching step: renders launch sets of n_views views
+ * (device RGBA8 outputs, resolutions widths/heights[n_views]), cycling through
+ * n_sets (1..1024) pose sets (poses and intrs hold n_sets * n_views entries,
+ * set-major) so that the timing covers varying pair counts, under each
+ * candidate schedule (slices 4, 6, 8,
+ * 12, 16 x first slice 1/16, 1/64, 1/256 x blend CTAs per SM all or 4), two
+ * untimed launch sets then `iters` (1..100) timed ones each; the four with
+ * the lowest median host time per launch set run 2 iters + 1 more times each,
+ * interleaved, and the lowest median of those wins.  It becomes the
+ * process-wide schedule and is written to *best (best_ms: its median).  Call
+ * it while no other render is running.  Errors: INVALID, and those of
+ * tigas_render_batch (the schedule in force before the call is restored). */
+tigas_status tigas_autotune(tigas_scene* scene, int n_sets, int n_views, const tigas_pose* poses,
+                            const tigas_intrinsics* intrs, const int* widths, const int* heights,
+                            uint8_t* const* outs_rgba8, int iters, tigas_schedule* best, double* best_ms);
+
+/* Launch sets that ran with a fixed pair capacity (graph replay or a shape's
+ * first launch set), outgrew it and were rendered again exactly, since load. */
+uint64_t tigas_exact_rerenders(void);
+
+/* Failure-detection hook for tests (no counterpart in the paper).  Runs one
+ * block of the radix sort's scatter pass whose decoupled look-back waits on
+ * digit counts of a preceding chunk that no block ever publishes; each wait
+ * gives up after spin_limit polls (1..2^20) and the block records the same
+ * timeout flag a real sort would.  Returns TIGAS_ERR_TIMEOUT when the flag
+ * was recorded (the expected outcome; the device stays usable), TIGAS_OK if
+ * it was not, INVALID for a bad limit, OOM/CUDA otherwise.  Synchronous;
+ * allocates and frees its own ~140 KB of device memory. */
+tigas_status tigas_debug_sort_wait_timeout(int spin_limit);
+
 /* Launch sets of the sliced schedule are captured as CUDA graphs per shape
  * (scene, view count and resolutions) when a shape appears a second time, and
  * replayed from then on.  A shape's first launch set runs directly with a

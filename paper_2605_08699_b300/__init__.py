@@ -1,12 +1,19 @@
 """B300-native forward 3D Gaussian Splatting renderer behind a C ABI.
 
 The compute path lives in ``libtigas.so`` (``csrc/``, sm_103a CUDA); this
-package is its Python binding (``tigas.py``) and build script (``build.py``).
+package is its Python binding (``tigas.py``), the serving loop's resolution
+controller (``abr.py``) and the build script (``build.py``).
 """
-from .tigas import (SORT_DEPTH_FIRST, SORT_FULL64, SORT_SLICED, STORAGE_FP16, STORAGE_FP32, TigasError, Server, SceneHandle,
-                    debug_render, kernel_launches, last_error, load_library, make_intrinsics, profile_enable, profile_read, set_graphs, make_pose, render,
-                    render_batch, render_ex, scene_from, scene_load, sort_pairs_u64, version)
+from .tigas import (ERR_AGAIN, ERR_CUDA, ERR_INVALID, ERR_NOT_FOUND, ERR_OOM, ERR_OVERFLOW, ERR_TIMEOUT, OK,
+                    SORT_DEPTH_FIRST, SORT_FULL64, SORT_SLICED, STAGES, STORAGE_FP16, STORAGE_FP32, SceneHandle,
+                    Server, TigasError, autotune, debug_render, debug_sort_wait_timeout, exact_rerenders, get_schedule,
+                    kernel_launches, last_error, load_library, make_intrinsics, make_pose, profile_enable,
+                    profile_read, render, render_batch, render_ex, scene_from, scene_load, set_graphs, set_schedule,
+                    sort_pairs_u64, version)
 
-__all__ = ["SORT_DEPTH_FIRST", "SORT_FULL64", "SORT_SLICED", "STORAGE_FP16", "STORAGE_FP32", "TigasError", "Server", "SceneHandle",
-           "debug_render", "kernel_launches", "last_error", "load_library", "make_intrinsics", "profile_enable", "profile_read", "set_graphs", "make_pose", "render",
-           "render_batch", "render_ex", "scene_from", "scene_load", "sort_pairs_u64", "version"]
+__all__ = ["ERR_AGAIN", "ERR_CUDA", "ERR_INVALID", "ERR_NOT_FOUND", "ERR_OOM", "ERR_OVERFLOW", "ERR_TIMEOUT", "OK",
+           "SORT_DEPTH_FIRST", "SORT_FULL64", "SORT_SLICED", "STAGES", "STORAGE_FP16", "STORAGE_FP32", "SceneHandle",
+           "Server", "TigasError", "autotune", "debug_render", "debug_sort_wait_timeout", "exact_rerenders", "get_schedule",
+           "kernel_launches", "last_error", "load_library", "make_intrinsics", "make_pose", "profile_enable",
+           "profile_read", "render", "render_batch", "render_ex", "scene_from", "scene_load", "set_graphs",
+           "set_schedule", "sort_pairs_u64", "version"]

@@ -296,16 +296,23 @@ Status launch_blend(const uint2* ranges, const uint32_t* values, const SplatArra
 
 Status launch_blend_slice(const uint2* ranges, const uint32_t* values, const SplatArrays& sp,
                           const ViewParams* views, int V, uint32_t n_entries, const float* bg,
-                          unsigned long long* counters, const SliceBlendArgs& sl, cudaStream_t st) {
-    static int grid = 0;
-    if (grid == 0) {
-        int per_sm = 0;
-        TIGAS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_blend<true, false>, kThreads, 0));
-        int dev = 0, sms = 0;
-        TIGAS_CUDA_TRY(cudaGetDevice(&dev));
-        TIGAS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        grid = (per_sm > 0 ? per_sm : 1) * sms;
-    }
+                          unsigned long long* counters, const SliceBlendArgs& sl, int ctas_per_sm,
+                          cudaStream_t st) {
+    struct Fit {
+        int per_sm = 1, sms = 0;   // CTAs per SM that fit, SM count
+        cudaError_t err = cudaSuccess;
+    };
+    static const Fit f = [] {   // thread-safe one-time query
+        Fit r;
+        int per_sm = 0, dev = 0;
+        r.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_blend<true, false>, kThreads, 0);
+        if (r.err == cudaSuccess) r.err = cudaGetDevice(&dev);
+        if (r.err == cudaSuccess) r.err = cudaDeviceGetAttribute(&r.sms, cudaDevAttrMultiProcessorCount, dev);
+        r.per_sm = per_sm > 0 ? per_sm : 1;
+        return r;
+    }();
+    TIGAS_CUDA_TRY(f.err);
+    const int grid = (ctas_per_sm > 0 && ctas_per_sm < f.per_sm ? ctas_per_sm : f.per_sm) * f.sms;
     TIGAS_CUDA_TRY(cudaMemsetAsync(sl.work_counter, 0, sizeof(uint32_t), st));
     if (counters)
         k_blend<true, true><<<grid, kThreads, 0, st>>>(ranges, values, sp, views, V, 0, n_entries, bg[0], bg[1], bg[2],

@@ -1,5 +1,7 @@
 // C ABI entry points (include/tigas.h): argument validation, host/device
 // buffer handling and error reporting around the frame pipeline.
+#include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -94,6 +96,10 @@ Status do_render(Scene* scene, int V, const tigas_pose* poses, const tigas_intri
     FrameRequest req;
     req.V = V;
     req.sort_mode = sort_mode;
+    const Schedule sched = current_schedule();
+    req.n_slices = sched.n_slices;
+    req.first_slice_inv = sched.first_slice_inv;
+    req.blend_ctas_per_sm = sched.blend_ctas_per_sm;
     req.want_q = dbg != nullptr;
     req.want_counters = stats != nullptr;
     std::vector<uint8_t*> host8(V, nullptr);
@@ -139,6 +145,7 @@ Status do_render(Scene* scene, int V, const tigas_pose* poses, const tigas_intri
                 ctx.slice_ratio *= 2.0;
             else
                 drop_graphs(ctx);
+            g_exact_rerenders.fetch_add(1, std::memory_order_relaxed);
             TIGAS_TRY(render_frame(scene, req, ctx, st, &res));
             for (int v = 0; v < V; ++v) {
                 const size_t px = (size_t)ws[v] * hs[v];
@@ -232,6 +239,124 @@ TIGAS_API const char* tigas_last_error(void) { return last_error(); }
 TIGAS_API tigas_status tigas_set_graphs(int enable) {
     g_use_graphs.store(enable != 0);
     forget_launch_sets();
+    return TIGAS_OK;
+}
+
+namespace {
+Status check_schedule(const tigas_schedule* s) {
+    if (!s) return {TIGAS_ERR_INVALID, "null schedule"};
+    if (s->n_slices < 1 || s->n_slices > kMaxSlices) return {TIGAS_ERR_INVALID, "n_slices out of 1..16"};
+    if (s->first_slice_inv < 1 || s->first_slice_inv > 4096) return {TIGAS_ERR_INVALID, "first_slice_inv out of 1..4096"};
+    if (s->blend_ctas_per_sm < 0 || s->blend_ctas_per_sm > 64) return {TIGAS_ERR_INVALID, "blend_ctas_per_sm out of 0..64"};
+    return {};
+}
+}  // namespace
+
+TIGAS_API tigas_status tigas_set_schedule(const tigas_schedule* s) {
+    Status c = check_schedule(s);
+    if (!c.ok()) return fail(c);
+    set_schedule(Schedule{s->n_slices, s->first_slice_inv, s->blend_ctas_per_sm});
+    return TIGAS_OK;
+}
+
+TIGAS_API tigas_status tigas_get_schedule(tigas_schedule* s) {
+    if (!s) return fail(TIGAS_ERR_INVALID, "null schedule");
+    const Schedule c = current_schedule();
+    s->n_slices = c.n_slices;
+    s->first_slice_inv = c.first_slice_inv;
+    s->blend_ctas_per_sm = c.blend_ctas_per_sm;
+    return TIGAS_OK;
+}
+
+TIGAS_API tigas_status tigas_autotune(tigas_scene* scene, int n_sets, int n_views, const tigas_pose* poses,
+                                      const tigas_intrinsics* intrs, const int* widths, const int* heights,
+                                      uint8_t* const* outs_rgba8, int iters, tigas_schedule* best,
+                                      double* best_ms) {
+    if (!scene || !poses || !intrs || !widths || !heights || !outs_rgba8) return fail(TIGAS_ERR_INVALID, "null argument");
+    if (n_views < 1 || n_views > kMaxViews) return fail(TIGAS_ERR_INVALID, "n_views out of 1..64");
+    if (n_sets < 1 || n_sets > 1024) return fail(TIGAS_ERR_INVALID, "n_sets out of 1..1024");
+    if (iters < 1 || iters > 100) return fail(TIGAS_ERR_INVALID, "iters out of 1..100");
+    for (int v = 0; v < n_views; ++v)
+        if (!outs_rgba8[v] || !is_device_pointer(outs_rgba8[v]))
+            return fail(TIGAS_ERR_INVALID, "autotune outputs must be device buffers");
+    Scene* sc = reinterpret_cast<Scene*>(scene);
+    SceneGuard sg(sc);
+    const Schedule saved = current_schedule();
+    static const int kSlices[] = {4, 6, 8, 12, 16};
+    static const int kFirst[] = {16, 64, 256};
+    static const int kCtas[] = {0, 4};
+    std::vector<Schedule> cands;
+    for (int ns : kSlices)
+        for (int fi : kFirst)
+            for (int ct : kCtas) cands.push_back(Schedule{ns, fi, ct});
+    std::vector<std::vector<double>> times(cands.size());
+    int next_set = 0;
+    // one launch set (the next pose set) under schedule c; untimed ones warm up
+    // (a shape's first launch set runs directly, the second is captured)
+    auto run = [&](size_t c, bool timed) -> Status {
+        set_schedule(cands[c]);
+        const size_t off = (size_t)next_set * n_views;
+        next_set = (next_set + 1) % n_sets;
+        const auto t0 = std::chrono::steady_clock::now();
+        Status s = do_render(sc, n_views, poses + off, intrs + off, widths, heights, outs_rgba8, nullptr, nullptr,
+                             TIGAS_SORT_SLICED, nullptr, nullptr, nullptr);
+        const auto t1 = std::chrono::steady_clock::now();
+        if (timed) times[c].push_back(std::chrono::duration<double, std::milli>(t1 - t0).count());
+        return s;
+    };
+    auto median = [](std::vector<double> t) {
+        std::sort(t.begin(), t.end());
+        return t.empty() ? 1e300 : t[t.size() / 2];
+    };
+    // round 1: every candidate, two untimed then `iters` timed launch sets
+    for (size_t c = 0; c < cands.size(); ++c)
+        for (int it = 0; it < iters + 2; ++it) {
+            Status s = run(c, it >= 2);
+            if (!s.ok()) {
+                set_schedule(saved);
+                return fail(s);
+            }
+        }
+    // round 2: the four fastest again, interleaved so that drift hits them alike
+    std::vector<size_t> order(cands.size());
+    for (size_t c = 0; c < cands.size(); ++c) order[c] = c;
+    std::sort(order.begin(), order.end(), [&](size_t a, size_t b) { return median(times[a]) < median(times[b]); });
+    order.resize(std::min<size_t>(4, order.size()));
+    for (size_t c : order) times[c].clear();
+    for (int round = 0; round < 2 * iters + 1; ++round)
+        for (size_t c : order) {
+            Status s = run(c, true);
+            if (!s.ok()) {
+                set_schedule(saved);
+                return fail(s);
+            }
+        }
+    Schedule win = saved;
+    double win_ms = 1e300;
+    for (size_t c : order) {
+        const double m = median(times[c]);
+        if (m < win_ms) {
+            win_ms = m;
+            win = cands[c];
+        }
+    }
+    set_schedule(win);
+    if (best) {
+        best->n_slices = win.n_slices;
+        best->first_slice_inv = win.first_slice_inv;
+        best->blend_ctas_per_sm = win.blend_ctas_per_sm;
+    }
+    if (best_ms) *best_ms = win_ms;
+    return TIGAS_OK;
+}
+
+TIGAS_API uint64_t tigas_exact_rerenders(void) { return g_exact_rerenders.load(); }
+
+TIGAS_API tigas_status tigas_debug_sort_wait_timeout(int spin_limit) {
+    bool timed_out = false;
+    Status s = debug_lookback_timeout(spin_limit, &timed_out);
+    if (!s.ok()) return fail(s);
+    if (timed_out) return fail(TIGAS_ERR_TIMEOUT, "radix sort look-back wait ran out");
     return TIGAS_OK;
 }
 

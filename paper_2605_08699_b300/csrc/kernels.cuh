@@ -51,6 +51,10 @@ Status radix_sort(const K* keys_in, const uint32_t* values_in, K* keys_alt, uint
 
 // K5: tile ranges from sorted keys (tile = key >> shift), binary search per
 // tile.  ranges: n_tiles uint2.  A key outside [0, n_tiles) sets *overflow bit 2.
+// Test hook: one radix-sort scatter CTA whose look-back waits on a chunk that
+// no CTA publishes; *timed_out tells whether it recorded the timeout flag.
+Status debug_lookback_timeout(int spin_limit, bool* timed_out);
+
 template <typename K>
 Status launch_ranges(const K* keys, uint64_t n_cap, const uint64_t* d_n, int shift, uint2* ranges,
                      uint32_t n_tiles, uint32_t* overflow, cudaStream_t st);

@@ -8,8 +8,24 @@
 namespace tigas {
 
 std::atomic<uint64_t> g_launches{0};
+std::atomic<uint64_t> g_exact_rerenders{0};
 std::atomic<bool> g_profile{false};
 std::atomic<bool> g_use_graphs{true};
+
+namespace {
+std::mutex g_sched_mu;
+Schedule g_sched;
+}  // namespace
+
+Schedule current_schedule() {
+    std::lock_guard<std::mutex> lk(g_sched_mu);
+    return g_sched;
+}
+
+void set_schedule(const Schedule& s) {
+    std::lock_guard<std::mutex> lk(g_sched_mu);
+    g_sched = s;
+}
 
 namespace {
 std::mutex g_prof_mu;
@@ -547,7 +563,7 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     // geometric slice ends: K / 64 ... K
     uint64_t ends[kMaxSlices];
     for (int i = 0; i < S; ++i) {
-        const double f = S == 1 ? 1.0 : std::pow(64.0, (double)(i - (S - 1)) / (double)(S - 1));
+        const double f = S == 1 ? 1.0 : std::pow((double)req.first_slice_inv, (double)(i - (S - 1)) / (double)(S - 1));
         ends[i] = i == S - 1 ? K : (uint64_t)std::ceil(f * (double)K);
     }
     uint64_t total_pairs = 0;
@@ -612,7 +628,7 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
         TIGAS_TRY(mark(kStRanges, false));
         TIGAS_TRY(mark(kStBlend, true));
         TIGAS_TRY(launch_blend_slice(ranges, vals_c, sp, d_views, V, (uint32_t)E, scene->view.bg,
-                                     req.want_counters ? d_counters : nullptr, sl, st));
+                                     req.want_counters ? d_counters : nullptr, sl, req.blend_ctas_per_sm, st));
         TIGAS_TRY(mark(kStBlend, false));
         a = b;
     }
@@ -637,7 +653,8 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
 namespace {
 std::vector<int64_t> graph_key(const Scene* scene, const FrameRequest& req) {
     std::vector<int64_t> k = {(int64_t)(uintptr_t)scene, scene->view.storage, req.V, req.n_slices,
-                              req.want_counters ? 1 : 0, g_profile.load() ? 1 : 0};
+                              req.first_slice_inv, req.blend_ctas_per_sm, req.want_counters ? 1 : 0,
+                              g_profile.load() ? 1 : 0};
     for (int v = 0; v < req.V; ++v) {
         k.push_back(req.views[v].W);
         k.push_back(req.views[v].H);

@@ -102,6 +102,8 @@ struct FrameRequest {
     ViewParams views[kMaxViews];       // out pointers must be device pointers (or null)
     int sort_mode = TIGAS_SORT_DEPTH_FIRST;
     int n_slices = 8;                    // sliced schedule: geometric depth slices
+    int first_slice_inv = 64;            // the nearest slice holds 1/first_slice_inv of the entries
+    int blend_ctas_per_sm = 0;           // persistent blend CTAs per SM (0: as many as fit)
     bool want_counters = false;          // count blend evaluations / fetched entries
     bool want_q = false;
 };
@@ -132,6 +134,15 @@ void sliced_stage_views(const Scene* scene, FrameRequest& req, RenderContext& ct
 Status render_sliced_graph(Scene* scene, FrameRequest& req, RenderContext& ctx, cudaStream_t st, FrameResult* res,
                            bool* rendered);
 extern std::atomic<bool> g_use_graphs;
+extern std::atomic<uint64_t> g_exact_rerenders;   // fixed-capacity launch sets rendered again exactly
+// Schedule parameters every launch set takes (tigas_set_schedule / tigas_autotune).
+struct Schedule {
+    int n_slices = 8;
+    int first_slice_inv = 64;
+    int blend_ctas_per_sm = 0;
+};
+Schedule current_schedule();
+void set_schedule(const Schedule& s);
 void drop_graphs(RenderContext& ctx);
 // Idle contexts drop their graphs, the shapes they have seen and the learned
 // slice capacity.

@@ -38,6 +38,7 @@ Status launch_ranges_active(const uint32_t* keys, uint64_t n_cap, const uint64_t
 // Blend of the active tiles of one slice: persistent CTAs take tiles from the
 // active list, composite the slice's entries onto each pixel's carried state,
 // store the state and the outputs, and mark tiles whose pixels all stopped.
+// ctas_per_sm: persistent CTAs per SM (0 or more than fit: as many as fit).
 struct SliceBlendArgs {
     const uint32_t* active;
     const uint32_t* n_active;   // [long tiles at the front, short tiles at the back]
@@ -49,6 +50,7 @@ struct SliceBlendArgs {
 };
 Status launch_blend_slice(const uint2* ranges, const uint32_t* values, const SplatArrays& sp,
                           const ViewParams* views, int V, uint32_t n_entries, const float* bg,
-                          unsigned long long* counters, const SliceBlendArgs& sl, cudaStream_t st);
+                          unsigned long long* counters, const SliceBlendArgs& sl, int ctas_per_sm,
+                          cudaStream_t st);
 
 }  // namespace tigas

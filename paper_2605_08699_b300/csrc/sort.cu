@@ -12,6 +12,8 @@
 //   3. scatter: each tile ranks its keys stably (warp match + per-warp digit
 //               counters), reorders them in shared memory, and writes runs of
 //               equal digits to their global offsets (coalesced).
+#include <vector>
+
 #include "kernels.cuh"
 
 namespace tigas {
@@ -517,7 +519,8 @@ template <typename K>
 __global__ void __launch_bounds__(OsCfg<K>::kT)
 k_os_scatter(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, K* __restrict__ keys_out,
              uint32_t* __restrict__ vals_out, uint64_t n_cap, const uint64_t* d_n, int shift, int nbits,
-             const uint32_t* __restrict__ gbase, uint32_t* status, uint32_t* chunk_counter, uint32_t* flags) {
+             const uint32_t* __restrict__ gbase, uint32_t* status, uint32_t* chunk_counter, uint32_t* flags,
+             int spin_limit) {
     const uint32_t mask = (1u << nbits) - 1u;
     constexpr int T = OsCfg<K>::kT, I = OsCfg<K>::kI, N = T * I, W = T / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -583,7 +586,7 @@ k_os_scatter(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in
                 const uint32_t sv = ld_relaxed(status + (size_t)j * 256 + d);
                 const uint32_t fl = sv & kFlagMask;
                 if (fl == 0) {
-                    if (++spins > kSpinLimit) {
+                    if (++spins > spin_limit) {
                         atomicOr(flags, kSortTimeoutFlag);
                         break;
                     }
@@ -676,7 +679,7 @@ Status radix_sort_onesweep(const K* keys_in, const uint32_t* values_in, K* keys_
         TIGAS_CUDA_TRY(cudaMemsetAsync(status, 0, chunks * 256 * sizeof(uint32_t), st));
         k_os_scatter<K><<<(unsigned)chunks, T, sizeof(OsSmem<K>), st>>>(src_k, src_v, dk, dv, n_cap, d_n, shift,
                                                                        nb, gbase + p * 256, status, counters + p,
-                                                                       flags);
+                                                                       flags, kSpinLimit);
         TIGAS_LAUNCHED();
         src_k = dk;
         src_v = dv;
@@ -685,6 +688,54 @@ Status radix_sort_onesweep(const K* keys_in, const uint32_t* values_in, K* keys_
 }
 
 }  // namespace
+
+// One scatter CTA of a two-chunk, one-pass sort that claims chunk 1 while no
+// CTA ever runs chunk 0: its look-back waits on counts nobody publishes, so
+// every wait runs out after spin_limit polls and the CTA sets the timeout flag.
+// All of its accesses stay in bounds: the digit bases come from the histogram
+// of both chunks, so every scattered position is below 2N.
+Status debug_lookback_timeout(int spin_limit, bool* timed_out) {
+    using K = uint32_t;
+    constexpr int T = OsCfg<K>::kT, N = OsCfg<K>::kT * OsCfg<K>::kI;
+    *timed_out = false;
+    if (spin_limit < 1 || spin_limit > (1 << 20)) return {TIGAS_ERR_INVALID, "spin limit out of 1..2^20"};
+    TIGAS_TRY(ensure_os_smem<K>());
+    const uint64_t n = 2 * (uint64_t)N;
+    const size_t words = 2 * n + 256 + 256 + 2 * 256 + 8;
+    uint32_t* buf = nullptr;
+    TIGAS_CUDA_TRY(cudaMalloc(&buf, words * sizeof(uint32_t)));
+    uint32_t* keys = buf;
+    uint32_t* out = keys + n;
+    uint32_t* ghist = buf + 2 * n;
+    uint32_t* gbase = ghist + 256;
+    uint32_t* status = gbase + 256;
+    uint32_t* misc = status + 2 * 256;   // [chunk counter, flags]
+    Status st;
+    std::vector<uint32_t> h(n);
+    for (uint64_t i = 0; i < n; ++i) h[i] = (uint32_t)((i * 2654435761u) >> 7);
+    cudaError_t e = cudaMemcpy(keys, h.data(), n * 4, cudaMemcpyHostToDevice);
+    uint32_t* sorted_vals = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&sorted_vals, n * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(ghist, 0, (256 + 256 + 2 * 256) * sizeof(uint32_t));
+    const uint32_t misc_init[2] = {1u, 0u};   // the only CTA claims chunk 1
+    if (e == cudaSuccess) e = cudaMemcpy(misc, misc_init, sizeof(misc_init), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_os_hist<K><<<4, 512>>>(keys, n, nullptr, 0, 8, ghist);
+        k_os_bases<<<1, 256>>>(ghist, gbase, 1);
+        k_os_scatter<K><<<1, T, sizeof(OsSmem<K>)>>>(keys, nullptr, out, sorted_vals, n, nullptr, 0, 8, gbase, status,
+                                                     misc, misc + 1, spin_limit);
+        g_launches.fetch_add(3, std::memory_order_relaxed);
+        e = cudaGetLastError();
+    }
+    uint32_t flags = 0;
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&flags, misc + 1, sizeof(flags), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) st = {TIGAS_ERR_CUDA, std::string("look-back timeout probe: ") + cudaGetErrorString(e)};
+    if (sorted_vals) cudaFree(sorted_vals);
+    cudaFree(buf);
+    *timed_out = (flags & kSortTimeoutFlag) != 0;
+    return st;
+}
 
 size_t radix_tmp_words(uint64_t n_cap) {
     size_t a = rts_tmp_words(n_cap), b = os_tmp_words(n_cap);

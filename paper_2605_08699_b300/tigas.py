@@ -27,7 +27,8 @@ EXPORTS = ["tigas_scene_load", "tigas_scene_free", "tigas_scene_bytes", "tigas_r
            "tigas_server_destroy", "tigas_server_submit", "tigas_server_poll", "tigas_last_error",
            "tigas_version", "tigas_kernel_launches", "tigas_profile_enable", "tigas_profile_read",
            "tigas_sort_pairs_u64_noalloc",
-           "tigas_render_batch_ex", "tigas_set_graphs"]
+           "tigas_render_batch_ex", "tigas_set_graphs", "tigas_debug_sort_wait_timeout",
+           "tigas_set_schedule", "tigas_get_schedule", "tigas_autotune", "tigas_exact_rerenders"]
 
 STAGES = ["preprocess", "depth_sort", "scan", "emit", "pair_sort", "ranges", "blend", "frame"]
 
@@ -64,6 +65,14 @@ class DebugFrame(ctypes.Structure):
                 ("depth", ctypes.c_void_p), ("uv", ctypes.c_void_p), ("q", ctypes.c_void_p),
                 ("values", ctypes.c_void_p), ("pair_capacity", ctypes.c_uint64), ("ranges", ctypes.c_void_p),
                 ("rgba_f32", ctypes.c_void_p)]
+
+
+class Schedule(ctypes.Structure):
+    _fields_ = [("n_slices", ctypes.c_int), ("first_slice_inv", ctypes.c_int), ("blend_ctas_per_sm", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {"n_slices": self.n_slices, "first_slice_inv": self.first_slice_inv,
+                "blend_ctas_per_sm": self.blend_ctas_per_sm}
 
 
 class ServerConfig(ctypes.Structure):
@@ -113,6 +122,13 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "tigas_kernel_launches": (ctypes.c_uint64, []),
         "tigas_profile_enable": (st, [i]),
         "tigas_set_graphs": (st, [i]),
+        "tigas_debug_sort_wait_timeout": (st, [i]),
+        "tigas_set_schedule": (st, [ctypes.POINTER(Schedule)]),
+        "tigas_get_schedule": (st, [ctypes.POINTER(Schedule)]),
+        "tigas_exact_rerenders": (ctypes.c_uint64, []),
+        "tigas_autotune": (st, [P, i, i, ctypes.POINTER(Pose), ctypes.POINTER(Intrinsics), ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_void_p), i,
+                                ctypes.POINTER(Schedule), ctypes.POINTER(ctypes.c_double)]),
         "tigas_profile_read": (st, [P, P, i]),
     }
     for name, (res, args) in sig.items():
@@ -148,6 +164,12 @@ def profile_enable(on: bool = True) -> None:
 def set_graphs(on: bool = True) -> None:
     """Capture and replay CUDA graphs of the sliced schedule (tigas_set_graphs)."""
     _check(load_library().tigas_set_graphs(int(on)))
+
+
+def debug_sort_wait_timeout(spin_limit: int) -> int:
+    """Run the radix sort's look-back timeout hook; returns the tigas status
+    (TIMEOUT = 6 is the expected outcome)."""
+    return int(load_library().tigas_debug_sort_wait_timeout(int(spin_limit)))
 
 
 def profile_read(reset: bool = False) -> dict:
@@ -307,6 +329,43 @@ def render_batch(scene: SceneHandle, poses: Sequence, intrs: Sequence, widths: S
                                              ctypes.cast(H, ctypes.c_void_p), ctypes.cast(O, ctypes.c_void_p),
                                              _stream(stream)))
     return None
+
+
+def set_schedule(n_slices: int = 8, first_slice_inv: int = 64, blend_ctas_per_sm: int = 0) -> None:
+    """tigas_set_schedule: the depth-sliced schedule every launch set takes."""
+    _check(load_library().tigas_set_schedule(ctypes.byref(Schedule(n_slices, first_slice_inv, blend_ctas_per_sm))))
+
+
+def get_schedule() -> dict:
+    s = Schedule()
+    _check(load_library().tigas_get_schedule(ctypes.byref(s)))
+    return s.as_dict()
+
+
+def exact_rerenders() -> int:
+    """Fixed-capacity launch sets that overflowed and were rendered again exactly."""
+    return int(load_library().tigas_exact_rerenders())
+
+
+def autotune(scene: SceneHandle, pose_sets: Sequence[Sequence], intrs: Sequence, widths: Sequence[int],
+             heights: Sequence[int], outs: Sequence, iters: int = 3) -> tuple[dict, float]:
+    """tigas_autotune: time the candidate schedules on launch sets of these
+    resolutions, cycling through pose_sets (each a list of one pose per view),
+    and keep the fastest; returns (schedule, median ms per launch set)."""
+    V = len(widths)
+    S = len(pose_sets)
+    if any(len(ps) != V for ps in pose_sets) or len(intrs) != V:
+        raise ValueError("every pose set and the intrinsics need one entry per view")
+    P = (Pose * (S * V))(*[make_pose(p) for ps in pose_sets for p in ps])
+    K = (Intrinsics * (S * V))(*[make_intrinsics(k) for _ in range(S) for k in intrs])
+    W = (ctypes.c_int * V)(*widths)
+    H = (ctypes.c_int * V)(*heights)
+    O = (ctypes.c_void_p * V)(*[_ptr(o) for o in outs])
+    best = Schedule()
+    ms = ctypes.c_double()
+    _check(load_library().tigas_autotune(scene.handle, S, V, P, K, W, H, O, iters, ctypes.byref(best),
+                                         ctypes.byref(ms)))
+    return best.as_dict(), float(ms.value)
 
 
 def debug_render(scene: SceneHandle, pose, intr, width: int, height: int, sort_mode: int = SORT_DEPTH_FIRST,

@@ -88,3 +88,18 @@ def test_pose_validation_messages(lib):
         assert st == tb.ERR_INVALID
     with pytest.raises(TigasError):
         _check(tb.ERR_INVALID)
+
+
+def test_schedule_set_get_and_range_checks():
+    tg.load_library()
+    before = tg.get_schedule()
+    try:
+        tg.set_schedule(12, 256, 3)
+        assert tg.get_schedule() == {"n_slices": 12, "first_slice_inv": 256, "blend_ctas_per_sm": 3}
+        for bad in [(0, 64, 0), (17, 64, 0), (8, 0, 0), (8, 5000, 0), (8, 64, -1), (8, 64, 65)]:
+            with pytest.raises(tg.TigasError) as e:
+                tg.set_schedule(*bad)
+            assert e.value.status == tg.ERR_INVALID
+        assert tg.get_schedule()["n_slices"] == 12   # a rejected call changes nothing
+    finally:
+        tg.set_schedule(**before)

@@ -399,3 +399,58 @@ def test_full_size_3m_1080p_sampled(cuda, s3, storage):
         extra = {"vs_fp32_oracle": parity.colour_stats(got, ref32)}
         assert extra["vs_fp32_oracle"]["psnr_rgb"] >= 50.0
     _diag("full_size_colour", {"storage": storage, **st, "pairs": dbg["pairs"], **extra})
+
+
+# ------------------------------------------------------- failure detection
+
+
+def test_sort_lookback_wait_times_out_and_device_stays_usable(h1, s1):
+    # a look-back wait on counts that nobody publishes gives up and reports
+    assert tg.debug_sort_wait_timeout(2048) == tg.ERR_TIMEOUT
+    # the context is still usable: a normal frame renders and matches the oracle
+    pose = synth.config_trajectory(1)[0]
+    w, h = 160, 120
+    img = np.zeros((h, w, 4), np.float32)
+    tg.render_ex(h1, pose, synth.default_intrinsics(w, h), w, h, out_rgba_f32=img)
+    ref = oracle.render(oracle.preprocess(s1, pose, synth.default_intrinsics(w, h), w, h))
+    parity.assert_colour(img, ref)
+    assert tg.debug_sort_wait_timeout(0) == tg.ERR_INVALID
+
+
+# ------------------------------------------------------------- scheduling
+
+
+def test_frames_do_not_depend_on_the_schedule(h1, cuda):
+    levels = [(480, 270), (97, 61)]
+    tr = synth.trajectory(17, 20)
+    base = tg.get_schedule()
+    try:
+        ref = _batch(h1, tr[3:5], levels, cuda)
+        for sch in [(1, 1, 0), (4, 16, 0), (16, 256, 1), (12, 4096, 4)]:
+            tg.set_schedule(*sch)
+            for _ in range(3):   # direct, exact + capture, replay
+                got = _batch(h1, tr[3:5], levels, cuda)
+                for a, b in zip(ref, got):
+                    assert np.array_equal(a, b), sch
+    finally:
+        tg.set_schedule(**base)
+
+
+def test_autotune_picks_a_candidate_and_keeps_frames(h1, cuda):
+    levels = [(320, 240), (320, 240)]
+    tr = synth.trajectory(19, 10)
+    intrs = [synth.default_intrinsics(w, h) for w, h in levels]
+    outs = [torch.empty((h, w, 4), dtype=torch.uint8, device=cuda) for w, h in levels]
+    base = tg.get_schedule()
+    try:
+        ref = _batch(h1, tr[:2], levels, cuda)
+        best, ms = tg.autotune(h1, [tr[:2], tr[4:6]], intrs, [w for w, _ in levels], [h for _, h in levels], outs,
+                               iters=1)
+        assert best["n_slices"] in (4, 6, 8, 12, 16) and best["first_slice_inv"] in (16, 64, 256)
+        assert best["blend_ctas_per_sm"] in (0, 4) and 0 < ms < 1e4
+        assert tg.get_schedule() == best
+        got = _batch(h1, tr[:2], levels, cuda)
+        for a, b in zip(ref, got):
+            assert np.array_equal(a, b)
+    finally:
+        tg.set_schedule(**base)
