@@ -319,6 +319,33 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
              "latency_ms_p99": float(np.percentile(lat32, 99)), "frames": n32, "storage": "fp32",
              "path": "tigas_render_ex, one request at a time"}
 
+    # ---- batching workload: 32 views of mixed ABR levels in one launch set
+    batching = None
+    if not args.no_serving:
+        Vb = 32
+        lv = [synth.ABR_LEVELS[v % 6] for v in range(Vb)]
+        kb = [synth.default_intrinsics(w, h) for w, h in lv]
+        tb = [synth.config_trajectory(4, v + 1000 * rank) for v in range(Vb)]
+        ob = [torch.empty((h, w, 4), dtype=torch.uint8, device=dev) for w, h in lv]
+
+        def bstep(s):
+            tg.render_batch(h16, [tb[v][(s * 5 + v) % 300] for v in range(Vb)], kb, [w for w, _ in lv],
+                            [h for _, h in lv], ob, stream=stream)
+        for s in range(4):
+            bstep(s)
+        torch.cuda.synchronize()
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nb = max(5, args.steps // 2)
+        b0.record(stream)
+        for s in range(nb):
+            bstep(4 + s)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        bms = b0.elapsed_time(b1) / nb
+        batching = {"views": Vb, "levels": "6 ABR levels x 1920x1080, uniform mix", "storage": "fp16",
+                    "ms_per_launch_set": round(bms, 3), "frames_per_s": round(Vb / bms * 1e3, 1),
+                    "megapixels_per_s": round(sum(w * h for w, h in lv) / bms * 1e-3, 1)}
+
     # ---- served FP16: request server, closed-loop clients
     serving = None
     if not args.no_serving:
@@ -329,6 +356,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
 
     res = {"schedule": schedule, "rerenders": rerenders, "value": value, "elapsed_ms": elapsed_ms, "frames": frames, "per_step": per_step, "stage_ms": stage_ms,
            "clocks": clocks, "launches": launches, "e2e": e2e, "plain_fp32": plain, "serving": serving, "trace": trace,
+           "batching": batching,
            "step_ms_host": step_ms_host, "scene": scene}
     h16.free()
     h32.free()
@@ -560,6 +588,7 @@ def main(argv=None) -> int:
                                                   "pixels all stopped are dropped", autotuned=not args.no_autotune,
                              exact_rerenders_timed=r["rerenders"]),
             "served_fp16": r["serving"], "plain_fp32": r["plain_fp32"], "serving_trace": r["trace"],
+            "batching_32_mixed": r["batching"],
             "roofline": roof, "stages": stages, "per_step": {k: int(v) for k, v in r["per_step"].items()},
             "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": int(r["launches"]), "clocks": r["clocks"],
         }
