@@ -165,8 +165,9 @@ def roofline(stage_ms: dict, per_step: dict, peaks: dict, clocks: dict, steps: i
     Algorithmic work per launch set of the sliced schedule (see the design notes):
       preprocess  12 B per (Gaussian, view) + (A - 12) B per Gaussian + 52 B per kept entry
       depth_sort  4 passes x 16 B per entry
-      scan        28 B per kept entry (slice count: order, tiles, rect, count; scan: 8 B)
-      emit        20 B per kept entry + 8 B per emitted pair
+      scan        40 B per kept entry: rectangle permute (order 4 B + rect gather 8 B + write 8 B),
+                  slice count (rect 8 B + count 4 B), count scan (4 B + 4 B)
+      emit        16 B per kept entry (order, rect, offset) + 8 B per emitted pair
       pair_sort   passes x 16 B per emitted pair
       ranges      8 B per tile per slice
       blend       FP32 flops: 8.5 per list entry evaluated + 9 per blended entry"""
@@ -177,8 +178,8 @@ def roofline(stage_ms: dict, per_step: dict, peaks: dict, clocks: dict, steps: i
     bytes_per = {
         "preprocess": w["entries"] * 12 + w["gaussians"] * (w["attr_bytes"] - 12) + w["kept"] * 52,
         "depth_sort": w["entries"] * 4 * 16,
-        "scan": w["kept"] * 28,
-        "emit": w["kept"] * 20 + w["pairs"] * 8,
+        "scan": w["kept"] * 40,
+        "emit": w["kept"] * 16 + w["pairs"] * 8,
         "pair_sort": w["pairs"] * w["sort_passes"] * 16,
         "ranges": w["tiles"] * w["slices"] * 8,
     }
@@ -243,8 +244,11 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
         tg.render_batch(handle, poses, [K] * V, [W] * V, [H] * V, o, stream=stream)
 
     tg.profile_enable(True)        # stage events are part of the captured launch sets: same shape as timed
+    if args.schedule:
+        n_sl, first, ctas = (int(x) for x in args.schedule.split(","))
+        tg.set_schedule(n_sl, first, ctas)
     schedule = tg.get_schedule()
-    if not args.no_autotune:
+    if not args.no_autotune and not args.schedule:
         # untimed: pick the sliced schedule for this launch-set shape (with the stage events on, as timed)
         sets = [[trajs[v][(s * 7 + v + 150) % len(trajs[v])] for v in range(V)] for s in range(8)]
         schedule, _ = tg.autotune(h16, sets, [K] * V, [W] * V, [H] * V, outs, iters=4)
@@ -539,6 +543,8 @@ def main(argv=None) -> int:
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule")
+    ap.add_argument("--schedule", default="", help="fixed schedule 'slices,first_slice_inv,blend_ctas_per_sm' "
+                                                   "(no autotuning)")
     ap.add_argument("--trace-seconds", type=float, default=10.0, help="open-loop serving trace length (0: skip)")
     ap.add_argument("--trace-clients", type=int, default=64)
     ap.add_argument("--trace-scenes", default="1000000,2000000,3000000,6000000")
@@ -585,7 +591,7 @@ def main(argv=None) -> int:
                            "p99_step": round(float(np.percentile(steps_ms, 99)), 3),
                            "note": "host time of one synchronous launch set of views_per_step frames"},
             "schedule": dict(r["schedule"], kind="depth-sliced: nearest-first geometric slices, tiles whose "
-                                                  "pixels all stopped are dropped", autotuned=not args.no_autotune,
+                                                  "pixels all stopped are dropped", autotuned=not (args.no_autotune or args.schedule),
                              exact_rerenders_timed=r["rerenders"]),
             "served_fp16": r["serving"], "plain_fp32": r["plain_fp32"], "serving_trace": r["trace"],
             "batching_32_mixed": r["batching"],
