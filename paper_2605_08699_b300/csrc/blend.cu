@@ -1,7 +1,8 @@
 // K6 per-tile blend, the 3DGS front-to-back compositing the backend relies
 // on (Sec. 4.1): one warp per 16x16 tile, 8 pixels per thread (column
-// lane % 16, rows lane / 16 + 2k), four independent tiles per CTA and no
-// CTA-wide barrier.  The tile's depth-ordered list is consumed in batches of
+// lane % 16, rows lane / 16 + 2k), four independent warps per CTA and no
+// CTA-wide barrier; a tile with a long list in a slice is split into four
+// 16x4 strips (2 pixels per thread) that separate warps composite at once.  The tile's depth-ordered list is consumed in batches of
 // 32 entries that the warp gathers into shared memory with cp.async,
 // double-buffered (batch b+1 in flight while b is composited).
 //
@@ -79,11 +80,167 @@ __device__ inline bool alpha_box_meets(const float4& gm, const float4& ap, float
     return gm.x - hx <= x1 && gm.x + hx >= x0 && gm.y - hy <= y1 && gm.y + hy >= y0;
 }
 
+struct BlendCounts {
+    unsigned long long eval = 0, fetched = 0, blend = 0;
+};
+
+// One warp composites tile g's list onto 2 NP pixel rows of the tile, starting
+// at row0: thread lane takes column lane % 16 and rows row0 + lane / 16 + 2k,
+// k < NP.  SLICED: start from and store back each pixel's carried (C, T).
+// Returns (warp-uniform) whether every pixel of these rows has stopped.
+template <bool SLICED, bool COUNT, int NP>
+__device__ __forceinline__ bool blend_rows(WarpStage& sm, int lane, const uint2* __restrict__ ranges,
+                                           const uint32_t* __restrict__ values, const SplatArrays& sp,
+                                           const ViewParams& vp, uint32_t g, uint32_t local, int row0,
+                                           uint64_t sbase, uint32_t n_entries, float bg_r, float bg_g, float bg_b,
+                                           const SliceBlendArgs& sl, BlendCounts& cnt) {
+    const int W = vp.W, H = vp.H, TX = vp.TX;
+    const int ty = (int)(local / TX), tx = (int)(local % TX);
+    const uint32_t col = lane & 15, row = (uint32_t)row0 + (lane >> 4);   // rows row + 2k of the tile
+    const int px = tx * kTile + (int)col;
+    const int py0 = ty * kTile + (int)row;
+    const float pxf = (float)px + 0.5f, py0f = (float)py0 + 0.5f;
+    const float tx0 = (float)(tx * kTile) + 0.5f, ty0 = (float)(ty * kTile) + 0.5f;   // first pixel centre
+
+    float T[NP], cr[NP], cg[NP], cb[NP];
+    uint32_t live = 0;   // bit k: pixel k still compositing
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        T[k] = 1.0f; cr[k] = 0.0f; cg[k] = 0.0f; cb[k] = 0.0f;
+        const int py = py0 + 2 * k;
+        if (px < W && py < H) {
+            if (SLICED) {
+                const float4 s0 = sl.state[sbase + (size_t)py * W + px];
+                cr[k] = s0.x; cg[k] = s0.y; cb[k] = s0.z; T[k] = fabsf(s0.w);
+                if (!(s0.w < 0.0f)) live |= 1u << k;
+            } else {
+                live |= 1u << k;
+            }
+        }
+    }
+
+    const uint2 rg = ranges[g];
+    const uint32_t start = rg.x, end = rg.y > rg.x ? rg.y : rg.x;
+    const int nb = (int)((end - start + kWB - 1) / kWB);
+    auto stage = [&](int b, int buf) {
+        const uint32_t idx = start + (uint32_t)b * kWB + lane;
+        if (idx < end) {
+            const uint32_t e = values[idx];
+            if (e < n_entries) {
+                cp_async16(&sm.geom[buf][lane], sp.geom + e);
+                cp_async16(&sm.appear[buf][lane], sp.appear + e);
+                cp_async4(&sm.blue[buf][lane], sp.blue + e);
+            } else {
+                // out-of-range entry (cannot happen for a consistent frame): contributes nothing
+                sm.geom[buf][lane] = make_float4(-1e30f, -1e30f, 0.f, 0.f);
+                sm.appear[buf][lane] = make_float4(0.f, -1e30f, 0.f, 0.f);
+                sm.blue[buf][lane] = 0.f;
+            }
+        }
+        cp_async_commit();
+    };
+
+    if (nb > 0) stage(0, 0);
+    for (int b = 0; b < nb; ++b) {
+        const int buf = b & 1;
+        if (b + 1 < nb) {
+            stage(b + 1, buf ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        const uint32_t rem = end - start - (uint32_t)b * kWB;
+        const int n_b = rem < (uint32_t)kWB ? (int)rem : kWB;
+        if (__all_sync(kFull, live == 0)) break;
+        // bounding box of the pixels still compositing (at least one is)
+        const uint32_t c_lo = __reduce_min_sync(kFull, live ? col : 16u);
+        const uint32_t c_hi = __reduce_max_sync(kFull, live ? col : 0u);
+        const uint32_t r_lo = __reduce_min_sync(kFull, live ? row + 2u * (uint32_t)(__ffs(live) - 1) : 16u);
+        const uint32_t r_hi = __reduce_max_sync(kFull, live ? row + 2u * (uint32_t)(31 - __clz(live)) : 0u);
+        // the lane's own staged entry: can it reach one of those pixels?
+        const bool meets = lane < n_b && alpha_box_meets(sm.geom[buf][lane], sm.appear[buf][lane], tx0 + (float)c_lo,
+                                                         tx0 + (float)c_hi, ty0 + (float)r_lo, ty0 + (float)r_hi);
+        uint32_t kept = __ballot_sync(kFull, meets);
+        __syncwarp();   // every lane's copies visible to the warp
+        if (COUNT) cnt.fetched += (uint64_t)n_b;
+        int counted = 0;   // entries of this batch already counted as evaluated
+        bool stopped = false;
+        while (kept) {
+            const int j = __ffs(kept) - 1;
+            kept &= kept - 1;
+            if (COUNT) {
+                // entries up to and including j meet the pixels still running before j
+                cnt.eval += (uint64_t)(j + 1 - counted) * (uint64_t)__popc(live);
+                counted = j + 1;
+            }
+            const float4 gm = sm.geom[buf][j];
+            const float4 ap = sm.appear[buf][j];
+            const float dx = gm.x - pxf;
+            const float adx = gm.z * dx, bdx = gm.w * dx;
+            const float dyb = gm.y - py0f;
+            float e[NP];
+            uint32_t con = 0;
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                const float dy = dyb - 2.0f * (float)k;
+                // power log2 e = a' dx^2 + dy (b' dx + c' dy)
+                const float p = fmaf(adx, dx, dy * fmaf(ap.x, dy, bdx));
+                e[k] = p + ap.y;
+                if (((live >> k) & 1u) && p <= 0.0f && e[k] >= kMinLog2Alpha) con |= 1u << k;
+            }
+            if (__any_sync(kFull, con != 0)) {
+                const float cbl = sm.blue[buf][j];
+#pragma unroll
+                for (int k = 0; k < NP; ++k) {
+                    if ((con >> k) & 1u) {
+                        const float alpha = fminf(0.99f, ex2_approx(e[k]));
+                        const float tT = fmaf(-T[k], alpha, T[k]);
+                        if (tT < 1e-4f) {
+                            live &= ~(1u << k);
+                        } else {
+                            if (COUNT) ++cnt.blend;
+                            const float w = alpha * T[k];
+                            cr[k] = fmaf(ap.z, w, cr[k]);
+                            cg[k] = fmaf(ap.w, w, cg[k]);
+                            cb[k] = fmaf(cbl, w, cb[k]);
+                            T[k] = tT;
+                        }
+                    }
+                }
+                if (__all_sync(kFull, live == 0)) {
+                    stopped = true;
+                    break;
+                }
+            }
+        }
+        if (COUNT && !stopped) cnt.eval += (uint64_t)(n_b - counted) * (uint64_t)__popc(live);
+        __syncwarp();   // buffer `buf` is refilled by the next iteration's stage
+    }
+    cp_async_wait<0>();
+    __syncwarp();
+
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const int py = py0 + 2 * k;
+        if (px < W && py < H) {
+            const size_t pix = (size_t)py * W + px;
+            if (SLICED) sl.state[sbase + pix] = make_float4(cr[k], cg[k], cb[k], ((live >> k) & 1u) ? T[k] : -T[k]);
+            const float r = fmaf(T[k], bg_r, cr[k]), gg = fmaf(T[k], bg_g, cg[k]);
+            const float bb = fmaf(T[k], bg_b, cb[k]), a = 1.0f - T[k];
+            if (vp.out_rgba8)
+                reinterpret_cast<uchar4*>(vp.out_rgba8)[pix] = make_uchar4(to_u8(r), to_u8(gg), to_u8(bb), to_u8(a));
+            if (vp.out_rgba_f32) reinterpret_cast<float4*>(vp.out_rgba_f32)[pix] = make_float4(r, gg, bb, a);
+        }
+    }
+    return __all_sync(kFull, live == 0);
+}
+
 // SLICED = false: warp w of CTA b blends tile 4b + w over its whole list from
-// fresh pixels.  SLICED = true: persistent warps take tiles from the slice's
-// active list, start from and store back each pixel's (C, T), and mark tiles
-// whose pixels all stopped.  COUNT: accumulate list entries evaluated per
-// pixel (up to its stop), entries staged, and entries blended.
+// fresh pixels.  SLICED = true: persistent warps take items from the slice's
+// active list (a whole tile, or one 4-row strip of a long tile), carry each
+// pixel's (C, T) across slices, and mark tiles whose pixels all stopped.
+// COUNT: accumulate list entries evaluated per pixel (up to its stop), entries
+// staged, and entries blended.
 template <bool SLICED, bool COUNT>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
 k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ values, SplatArrays sp,
@@ -95,7 +252,7 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ values, S
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpStage& sm = stage_sm[warp];
-    unsigned long long n_eval = 0, n_fetched = 0, n_blend = 0;
+    BlendCounts cnt;
     const uint32_t n_long = SLICED ? sl.n_active[0] : 0u;
     const uint32_t n_items = SLICED ? n_long + sl.n_active[1] : total_tiles;
     uint32_t item = SLICED ? 0u : blockIdx.x * kWarps + warp;
@@ -106,7 +263,9 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ values, S
             item = __shfl_sync(kFull, it, 0);
         }
         if (item >= n_items) break;
-        const uint32_t g = SLICED ? sl.active[item < n_long ? item : sl.n_tiles - 1 - (item - n_long)] : item;
+        const uint32_t raw = SLICED ? sl.active[item < n_long ? item : sl.active_cap - 1 - (item - n_long)] : item;
+        const uint32_t g = raw & kTileMask;
+        const uint32_t strip = raw >> kStripShift;   // 0: whole tile, s + 1: rows 4s..4s+3
         int v = 0;
         {
             int lo = 0, hi = V;   // last view with tile_base <= g
@@ -117,153 +276,26 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ values, S
             v = lo;
         }
         const ViewParams& vp = views_g[v];
-        const int W = vp.W, H = vp.H, TX = vp.TX;
         const uint32_t local = g - s_tb[v];
-        const int ty = (int)(local / TX), tx = (int)(local % TX);
-        const int px = tx * kTile + (lane & 15);
-        const int py0 = ty * kTile + (lane >> 4);       // rows py0 + 2k
-        const float pxf = (float)px + 0.5f, py0f = (float)py0 + 0.5f;
-        const float tx0 = (float)(tx * kTile) + 0.5f, ty0 = (float)(ty * kTile) + 0.5f;   // first pixel centre
         const uint64_t sbase = SLICED ? sl.pix_base[v] : 0;
-
-        float T[kPix], cr[kPix], cg[kPix], cb[kPix];
-        uint32_t live = 0;   // bit k: pixel k still compositing
-#pragma unroll
-        for (int k = 0; k < kPix; ++k) {
-            T[k] = 1.0f; cr[k] = 0.0f; cg[k] = 0.0f; cb[k] = 0.0f;
-            const int py = py0 + 2 * k;
-            if (px < W && py < H) {
-                if (SLICED) {
-                    const float4 s0 = sl.state[sbase + (size_t)py * W + px];
-                    cr[k] = s0.x; cg[k] = s0.y; cb[k] = s0.z; T[k] = fabsf(s0.w);
-                    if (!(s0.w < 0.0f)) live |= 1u << k;
-                } else {
-                    live |= 1u << k;
-                }
-            }
-        }
-
-        const uint2 rg = ranges[g];
-        const uint32_t start = rg.x, end = rg.y > rg.x ? rg.y : rg.x;
-        const int nb = (int)((end - start + kWB - 1) / kWB);
-        auto stage = [&](int b, int buf) {
-            const uint32_t idx = start + (uint32_t)b * kWB + lane;
-            if (idx < end) {
-                const uint32_t e = values[idx];
-                if (e < n_entries) {
-                    cp_async16(&sm.geom[buf][lane], sp.geom + e);
-                    cp_async16(&sm.appear[buf][lane], sp.appear + e);
-                    cp_async4(&sm.blue[buf][lane], sp.blue + e);
-                } else {
-                    // out-of-range entry (cannot happen for a consistent frame): contributes nothing
-                    sm.geom[buf][lane] = make_float4(-1e30f, -1e30f, 0.f, 0.f);
-                    sm.appear[buf][lane] = make_float4(0.f, -1e30f, 0.f, 0.f);
-                    sm.blue[buf][lane] = 0.f;
-                }
-            }
-            cp_async_commit();
-        };
-
-        if (nb > 0) stage(0, 0);
-        for (int b = 0; b < nb; ++b) {
-            const int buf = b & 1;
-            if (b + 1 < nb) {
-                stage(b + 1, buf ^ 1);
-                cp_async_wait<1>();
-            } else {
-                cp_async_wait<0>();
-            }
-            const uint32_t rem = end - start - (uint32_t)b * kWB;
-            const int cnt = rem < (uint32_t)kWB ? (int)rem : kWB;
-            if (__all_sync(kFull, live == 0)) break;
-            // bounding box of the pixels still compositing (at least one is)
-            const uint32_t col = lane & 15, row = lane >> 4;
-            const uint32_t c_lo = __reduce_min_sync(kFull, live ? col : 16u);
-            const uint32_t c_hi = __reduce_max_sync(kFull, live ? col : 0u);
-            const uint32_t r_lo = __reduce_min_sync(kFull, live ? row + 2u * (uint32_t)(__ffs(live) - 1) : 16u);
-            const uint32_t r_hi = __reduce_max_sync(kFull, live ? row + 2u * (uint32_t)(31 - __clz(live)) : 0u);
-            // the lane's own staged entry: can it reach one of those pixels?
-            const bool meets = lane < cnt && alpha_box_meets(sm.geom[buf][lane], sm.appear[buf][lane], tx0 + (float)c_lo,
-                                                             tx0 + (float)c_hi, ty0 + (float)r_lo, ty0 + (float)r_hi);
-            uint32_t kept = __ballot_sync(kFull, meets);
-            __syncwarp();   // every lane's copies visible to the warp
-            if (COUNT) n_fetched += (uint64_t)cnt;
-            int counted = 0;   // entries of this batch already counted as evaluated
-            bool stopped = false;
-            while (kept) {
-                const int j = __ffs(kept) - 1;
-                kept &= kept - 1;
-                if (COUNT) {
-                    // entries up to and including j meet the pixels still running before j
-                    n_eval += (uint64_t)(j + 1 - counted) * (uint64_t)__popc(live);
-                    counted = j + 1;
-                }
-                const float4 gm = sm.geom[buf][j];
-                const float4 ap = sm.appear[buf][j];
-                const float dx = gm.x - pxf;
-                const float adx = gm.z * dx, bdx = gm.w * dx;
-                const float dyb = gm.y - py0f;
-                float e[kPix];
-                uint32_t con = 0;
-#pragma unroll
-                for (int k = 0; k < kPix; ++k) {
-                    const float dy = dyb - 2.0f * (float)k;
-                    // power log2 e = a' dx^2 + dy (b' dx + c' dy)
-                    const float p = fmaf(adx, dx, dy * fmaf(ap.x, dy, bdx));
-                    e[k] = p + ap.y;
-                    if (((live >> k) & 1u) && p <= 0.0f && e[k] >= kMinLog2Alpha) con |= 1u << k;
-                }
-                if (__any_sync(kFull, con != 0)) {
-                    const float cbl = sm.blue[buf][j];
-#pragma unroll
-                    for (int k = 0; k < kPix; ++k) {
-                        if ((con >> k) & 1u) {
-                            const float alpha = fminf(0.99f, ex2_approx(e[k]));
-                            const float tT = fmaf(-T[k], alpha, T[k]);
-                            if (tT < 1e-4f) {
-                                live &= ~(1u << k);
-                            } else {
-                                if (COUNT) ++n_blend;
-                                const float w = alpha * T[k];
-                                cr[k] = fmaf(ap.z, w, cr[k]);
-                                cg[k] = fmaf(ap.w, w, cg[k]);
-                                cb[k] = fmaf(cbl, w, cb[k]);
-                                T[k] = tT;
-                            }
-                        }
-                    }
-                    if (__all_sync(kFull, live == 0)) {
-                        stopped = true;
-                        break;
-                    }
-                }
-            }
-            if (COUNT && !stopped) n_eval += (uint64_t)(cnt - counted) * (uint64_t)__popc(live);
-            __syncwarp();   // buffer `buf` is refilled by the next iteration's stage
-        }
-        cp_async_wait<0>();
-        __syncwarp();
-
-#pragma unroll
-        for (int k = 0; k < kPix; ++k) {
-            const int py = py0 + 2 * k;
-            if (px < W && py < H) {
-                const size_t pix = (size_t)py * W + px;
-                if (SLICED) sl.state[sbase + pix] = make_float4(cr[k], cg[k], cb[k], ((live >> k) & 1u) ? T[k] : -T[k]);
-                const float r = fmaf(T[k], bg_r, cr[k]), gg = fmaf(T[k], bg_g, cg[k]);
-                const float bb = fmaf(T[k], bg_b, cb[k]), a = 1.0f - T[k];
-                if (vp.out_rgba8)
-                    reinterpret_cast<uchar4*>(vp.out_rgba8)[pix] = make_uchar4(to_u8(r), to_u8(gg), to_u8(bb), to_u8(a));
-                if (vp.out_rgba_f32) reinterpret_cast<float4*>(vp.out_rgba_f32)[pix] = make_float4(r, gg, bb, a);
-            }
-        }
-        if (SLICED) {
-            if (__all_sync(kFull, live == 0) && lane == 0) atomicOr(&sl.done[g >> 5], 1u << (g & 31));
+        if (!SLICED || strip == 0) {
+            const bool all = blend_rows<SLICED, COUNT, kPix>(sm, lane, ranges, values, sp, vp, g, local, 0, sbase,
+                                                             n_entries, bg_r, bg_g, bg_b, sl, cnt);
+            if (!SLICED) break;
+            if (all && lane == 0) atomicOr(&sl.done[g >> 5], 1u << (g & 31));
         } else {
-            break;
+            const uint32_t bit = 1u << (strip - 1);
+            const bool all = blend_rows<SLICED, COUNT, 2>(sm, lane, ranges, values, sp, vp, g, local,
+                                                          4 * (int)(strip - 1), sbase, n_entries, bg_r, bg_g, bg_b,
+                                                          sl, cnt);
+            if (all && lane == 0) {
+                const uint32_t old = atomicOr(&sl.strips[g], bit);
+                if ((old | bit) == 0xFu) atomicOr(&sl.done[g >> 5], 1u << (g & 31));
+            }
         }
     }
     if (COUNT && counters) {
+        unsigned long long n_eval = cnt.eval, n_blend = cnt.blend;
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) {
             n_eval += __shfl_xor_sync(kFull, n_eval, d);
@@ -271,7 +303,7 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ values, S
         }
         if (lane == 0) {
             if (n_eval) atomicAdd(&counters[0], n_eval);
-            if (n_fetched) atomicAdd(&counters[1], n_fetched);
+            if (cnt.fetched) atomicAdd(&counters[1], cnt.fetched);
             if (n_blend) atomicAdd(&counters[2], n_blend);
         }
     }

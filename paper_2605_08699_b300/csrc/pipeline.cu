@@ -454,7 +454,7 @@ SlicedLayout sliced_layout(const Scene* scene, FrameRequest& req) {
     b += E * (16 + 16 + 4 + 4 + 4 + 8 + (req.want_q ? 4 : 0));
     b += E * 4 * 4 + (E + 1) * 4 * 2 + E * 8;             // depth sort buffers, counts, offsets, rects
     b += L.tmp_words * 4;
-    b += (sizeof(uint2) + 4) * (size_t)L.total_tiles + L.done_words * 4;
+    b += (sizeof(uint2) + 4 * 4 + 4) * (size_t)L.total_tiles + L.done_words * 4;   // ranges, active, strips
     b += L.total_pix * 16 + sizeof(uint64_t) * kMaxViews * 2;
     L.fixed_bytes = b;
     return L;
@@ -522,7 +522,8 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     uint2* rect_sorted = ctx.fixed.take<uint2>(E);
     uint32_t* tmp = ctx.fixed.take<uint32_t>(L.tmp_words);
     uint2* ranges = ctx.fixed.take<uint2>(total_tiles);
-    uint32_t* active = ctx.fixed.take<uint32_t>(total_tiles);
+    uint32_t* active = ctx.fixed.take<uint32_t>(4 * (size_t)total_tiles);   // long tiles as 4 strips each
+    uint32_t* strips = ctx.fixed.take<uint32_t>(total_tiles);
     uint32_t* done = ctx.fixed.take<uint32_t>(L.done_words);
     float4* state = ctx.fixed.take<float4>(L.total_pix);
 
@@ -535,6 +536,7 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     TIGAS_CUDA_TRY(cudaMemsetAsync(d_flags, 0, sizeof(uint32_t) * 2, st));
     TIGAS_CUDA_TRY(cudaMemsetAsync(d_total, 0, sizeof(uint64_t) * (kMaxSlices + 2), st));   // empty slices count 0
     TIGAS_CUDA_TRY(cudaMemsetAsync(done, 0, L.done_words * 4, st));
+    TIGAS_CUDA_TRY(cudaMemsetAsync(strips, 0, (size_t)total_tiles * 4, st));
     if (sp.q_dbg) TIGAS_CUDA_TRY(cudaMemsetAsync(sp.q_dbg, 0, E * 4, st));
     if (req.want_counters) TIGAS_CUDA_TRY(cudaMemsetAsync(d_counters, 0, sizeof(unsigned long long) * 4, st));
 
@@ -569,7 +571,7 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     uint64_t total_pairs = 0;
     int passes = 0;
     uint64_t a = 0;
-    SliceBlendArgs sl{active, d_misc, d_misc + 2, state, d_pix_base, done, total_tiles};
+    SliceBlendArgs sl{active, d_misc, d_misc + 2, state, d_pix_base, done, strips, 4 * total_tiles};
     if (stat) {
         // pair buffers for the fixed capacity, taken once
         ctx.pairs.reset();

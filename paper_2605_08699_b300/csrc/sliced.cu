@@ -157,9 +157,10 @@ k_emit_slice(const uint32_t* __restrict__ order, const uint2* __restrict__ rect_
 }
 
 // Tile ranges by binary search.  Tiles with pairs in this slice that are not
-// done form the active list: tiles with at least kHeavyTile pairs from the
-// front (count n_active[0]), the others from the back (count n_active[1]), so
-// that the blend's dynamic scheduler starts the longest lists first.
+// done form the active list: a tile with at least kHeavyTile pairs as four
+// strips of 4 pixel rows from the front (count n_active[0]), so that four
+// warps share its long list and the blend's dynamic scheduler starts them
+// first; the other tiles whole from the back (count n_active[1]).
 __device__ inline uint64_t lower_bound_u32(const uint32_t* __restrict__ keys, uint64_t n, uint32_t t) {
     uint64_t lo = 0, hi = n;
     while (lo < hi) {
@@ -191,15 +192,19 @@ k_ranges_active(const uint32_t* __restrict__ keys, uint64_t n_cap, const uint64_
     const uint32_t ml = __ballot_sync(kFull, act && !heavy);
     if (mh) {
         uint32_t base = 0;
-        if (lane == __ffs(mh) - 1) base = atomicAdd(&n_active[0], (uint32_t)__popc(mh));
+        if (lane == __ffs(mh) - 1) base = atomicAdd(&n_active[0], 4u * (uint32_t)__popc(mh));
         base = __shfl_sync(kFull, base, __ffs(mh) - 1);
-        if (heavy) active[base + __popc(mh & below)] = t;
+        if (heavy) {
+            const uint32_t at = base + 4u * (uint32_t)__popc(mh & below);
+#pragma unroll
+            for (uint32_t s = 0; s < 4; ++s) active[at + s] = t | ((s + 1u) << kStripShift);
+        }
     }
     if (ml) {
         uint32_t base = 0;
         if (lane == __ffs(ml) - 1) base = atomicAdd(&n_active[1], (uint32_t)__popc(ml));
         base = __shfl_sync(kFull, base, __ffs(ml) - 1);
-        if (act && !heavy) active[n_tiles - 1 - (base + __popc(ml & below))] = t;
+        if (act && !heavy) active[4u * n_tiles - 1u - (base + __popc(ml & below))] = t;
     }
 }
 

@@ -6,6 +6,10 @@
 namespace tigas {
 
 constexpr uint32_t kHeavyTile = 128;   // pairs of a slice that make a tile "long"
+// Active-list items: a tile id (whole tile) or tile id | (s + 1) << kStripShift
+// for strip s (pixel rows 4s..4s+3) of a long tile.
+constexpr int kStripShift = 28;
+constexpr uint32_t kTileMask = (1u << kStripShift) - 1u;
 
 // (C, T) = (0, 1) for every pixel of every view, background in the outputs.
 // pix_base[v]: offset of view v's first pixel in `state`.
@@ -27,9 +31,10 @@ Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64
                          uint32_t* keys, uint32_t* values, uint64_t pair_cap, uint32_t* overflow, cudaStream_t st);
 
 // Tile ranges of the slice's sorted keys, and the list of tiles with pairs
-// that are not done: n_active[0] tiles with >= kHeavyTile pairs at the front
-// of `active`, n_active[1] others at its back (active[n_tiles - 1 - k]);
-// both counts are zeroed here.
+// that are not done: each tile with >= kHeavyTile pairs as its 4 strips at the
+// front of `active` (n_active[0] items), the other tiles whole at its back
+// (active[4 n_tiles - 1 - k], n_active[1] items); both counts are zeroed here.
+// `active` holds 4 n_tiles items.
 // The key count is min(*d_n, n_cap) when d_n is given, else n_cap.
 Status launch_ranges_active(const uint32_t* keys, uint64_t n_cap, const uint64_t* d_n, uint2* ranges,
                             uint32_t n_tiles, const uint32_t* done, uint32_t* active, uint32_t* n_active,
@@ -46,7 +51,8 @@ struct SliceBlendArgs {
     float4* state;              // per pixel (C.rgb, T), T negated once the pixel stopped
     const uint64_t* pix_base;   // per view
     uint32_t* done;             // per-tile bitmap
-    uint32_t n_tiles;           // capacity of `active` (all tiles of the launch set)
+    uint32_t* strips;           // per tile: bit s set once strip s's pixels all stopped
+    uint32_t active_cap;        // capacity of `active` (4 x all tiles of the launch set)
 };
 Status launch_blend_slice(const uint2* ranges, const uint32_t* values, const SplatArrays& sp,
                           const ViewParams* views, int V, uint32_t n_entries, const float* bg,
