@@ -362,7 +362,10 @@ Status radix_sort_rts(const K* keys_in, const uint32_t* values_in, K* keys_alt, 
 // on chunks claimed by CTAs that started before it, which publish before they
 // wait themselves, so the waits always end; each wait is still bounded: after
 // kSpinLimit polls the CTA records a timeout flag and goes on (its writes stay
-// inside the output by the bounds check, the host reports the error).
+// inside the output by the bounds check, the host reports the error).  The
+// look-back reads kLookWin predecessors per round, so a CTA of the first wave
+// (whose predecessors have mostly published only their own counts) needs
+// about 1/kLookWin of the dependent round trips of a one-by-one walk.
 
 namespace {
 
@@ -371,6 +374,10 @@ constexpr uint32_t kFlagPre = 2u << 30;
 constexpr uint32_t kFlagMask = 3u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
 constexpr int kSpinLimit = 1 << 22;
+#ifndef TIGAS_LOOK_WINDOW
+#define TIGAS_LOOK_WINDOW 8
+#endif
+constexpr int kLookWin = TIGAS_LOOK_WINDOW;   // predecessor chunks read per look-back round
 constexpr uint32_t kSortTimeoutFlag = 16u;
 
 template <typename K>
@@ -580,22 +587,36 @@ k_os_scatter(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in
             st_relaxed(my, kFlagPre | (cnt & kValMask));
         } else {
             st_relaxed(my, kFlagAgg | (cnt & kValMask));
+            // walk back kLookWin chunks per round (independent loads in flight):
+            // add aggregates until an inclusive prefix, re-poll a chunk not yet published
             int64_t j = (int64_t)chunk - 1;
             int spins = 0;
             while (j >= 0) {
-                const uint32_t sv = ld_relaxed(status + (size_t)j * 256 + d);
-                const uint32_t fl = sv & kFlagMask;
-                if (fl == 0) {
+                uint32_t sv[kLookWin];
+#pragma unroll
+                for (int t = 0; t < kLookWin; ++t)
+                    sv[t] = j - t >= 0 ? ld_relaxed(status + (size_t)(j - t) * 256 + d) : kFlagPre;
+                bool found = false, stalled = false;
+#pragma unroll
+                for (int t = 0; t < kLookWin; ++t) {
+                    if (found || stalled) continue;
+                    const uint32_t fl = sv[t] & kFlagMask;
+                    if (fl == 0) {
+                        stalled = true;
+                        continue;
+                    }
+                    excl += sv[t] & kValMask;
+                    --j;
+                    found = fl == kFlagPre;
+                }
+                if (found) break;
+                if (stalled) {
                     if (++spins > spin_limit) {
                         atomicOr(flags, kSortTimeoutFlag);
                         break;
                     }
                     if (spins > 32) __nanosleep(32);
-                    continue;
                 }
-                excl += sv & kValMask;
-                if (fl == kFlagPre) break;
-                --j;
             }
             st_relaxed(my, kFlagPre | ((excl + cnt) & kValMask));
         }
