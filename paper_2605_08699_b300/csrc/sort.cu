@@ -384,11 +384,11 @@ template <typename K>
 struct OsCfg;
 template <>
 struct OsCfg<uint32_t> {
-    static constexpr int kT = 512, kI = 16;
+    static constexpr int kT = 512, kI = 16, kMinBlocks = 2;   // two CTAs per SM: <= 64 registers
 };
 template <>
 struct OsCfg<uint64_t> {
-    static constexpr int kT = 256, kI = 16;
+    static constexpr int kT = 256, kI = 16, kMinBlocks = 2;
 };
 
 __device__ inline uint32_t ld_relaxed(const uint32_t* p) {
@@ -523,7 +523,7 @@ struct OsSmem {
 };
 
 template <typename K>
-__global__ void __launch_bounds__(OsCfg<K>::kT)
+__global__ void __launch_bounds__(OsCfg<K>::kT, OsCfg<K>::kMinBlocks)
 k_os_scatter(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, K* __restrict__ keys_out,
              uint32_t* __restrict__ vals_out, uint64_t n_cap, const uint64_t* d_n, int shift, int nbits,
              const uint32_t* __restrict__ gbase, uint32_t* status, uint32_t* chunk_counter, uint32_t* flags,
@@ -657,6 +657,8 @@ Status ensure_os_smem() {
     if (done.load()) return {};
     TIGAS_CUDA_TRY(cudaFuncSetAttribute(k_os_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)sizeof(OsSmem<K>)));
+    // the largest shared-memory carveout, so that two CTAs fit per SM
+    TIGAS_CUDA_TRY(cudaFuncSetAttribute(k_os_scatter<K>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     done.store(true);
     return {};
 }
