@@ -94,6 +94,12 @@ k_permute_rects(const uint32_t* __restrict__ order, uint64_t K, SplatArrays sp, 
 }
 
 // counts[k - a] = tiles of entry order[k]'s rectangle that are not done.
+// A lane counts a small rectangle itself; a rectangle of more than kBigRows
+// bitmap-word reads is counted by the whole warp (rows spread over the lanes,
+// one reduction), so that a few Gaussians close to the camera do not hold a
+// warp for thousands of serial reads.
+constexpr uint32_t kBigRows = 12;
+
 __global__ void __launch_bounds__(256)
 k_count_slice(const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b, const ViewParams* __restrict__ views_g,
               int V, const uint32_t* __restrict__ done, uint32_t* __restrict__ counts) {
@@ -103,20 +109,44 @@ k_count_slice(const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b, con
         s_tx[k] = (uint32_t)views_g[k].TX;
     }
     __syncthreads();
+    const int lane = threadIdx.x & 31;
     const uint64_t k = a + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= b) return;
-    const uint2 r = rect_sorted[k];
+    const bool in = k < b;
+    const uint2 r = in ? rect_sorted[k] : make_uint2(0u, 0u);
     const uint32_t xlo = r.x & 0x3FFu, xhi = (r.x >> 10) & 0x3FFu, v = r.x >> 20;
     const uint32_t ylo = r.y & 0x3FFu, yhi = (r.y >> 10) & 0x3FFu;
+    const uint32_t rows = yhi > ylo ? yhi - ylo : 0u;
+    const bool big = rows * (((xhi - xlo) >> 5) + 2u) > kBigRows;
     uint32_t c = 0;
-    for (uint32_t ty = ylo; ty < yhi; ++ty) {
-        const uint32_t row = s_tb[v] + ty * s_tx[v];
-        c += count_running(done, row + xlo, row + xhi);
+    if (!big) {
+        for (uint32_t ty = ylo; ty < yhi; ++ty) {
+            const uint32_t row = s_tb[v] + ty * s_tx[v];
+            c += count_running(done, row + xlo, row + xhi);
+        }
     }
-    counts[k - a] = c;
+    uint32_t m = __ballot_sync(kFull, big);
+    while (m) {
+        const int j = __ffs(m) - 1;
+        m &= m - 1;
+        const uint32_t rx = __shfl_sync(kFull, r.x, j), ry = __shfl_sync(kFull, r.y, j);
+        const uint32_t jxlo = rx & 0x3FFu, jxhi = (rx >> 10) & 0x3FFu, jv = rx >> 20;
+        const uint32_t jylo = ry & 0x3FFu, jyhi = (ry >> 10) & 0x3FFu;
+        uint32_t part = 0;
+        for (uint32_t ty = jylo + lane; ty < jyhi; ty += 32) {
+            const uint32_t row = s_tb[jv] + ty * s_tx[jv];
+            part += count_running(done, row + jxlo, row + jxhi);
+        }
+        const uint32_t tot = __reduce_add_sync(kFull, part);
+        if (lane == j) c = tot;
+    }
+    if (in) counts[k - a] = c;
 }
 
-// Pairs (tile, entry) of the slice for tiles not done, in depth order.
+// Pairs (tile, entry) of the slice for tiles not done, in depth order.  The
+// warp writes one entry's pairs at a time: lanes take 32 consecutive tiles of
+// the rectangle (row-major), and those not done are written to consecutive
+// positions (a ballot ranks them), so stores are coalesced and a large
+// rectangle costs area / 32 steps instead of area steps of one lane.
 __global__ void __launch_bounds__(256)
 k_emit_slice(const uint32_t* __restrict__ order, const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b,
              const uint32_t* __restrict__ offsets, const ViewParams* __restrict__ views_g, int V,
@@ -128,30 +158,56 @@ k_emit_slice(const uint32_t* __restrict__ order, const uint2* __restrict__ rect_
         s_tx[k] = (uint32_t)views_g[k].TX;
     }
     __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
     const uint64_t k = a + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= b) return;
-    uint32_t c = offsets[k - a + 1] - offsets[k - a];
-    if (c == 0) return;
-    const uint32_t e = order[k];
-    const uint2 r = rect_sorted[k];
-    const uint32_t xlo = r.x & 0x3FFu, xhi = (r.x >> 10) & 0x3FFu, v = r.x >> 20;
-    const uint32_t ylo = r.y & 0x3FFu, yhi = (r.y >> 10) & 0x3FFu;
-    uint64_t pos = offsets[k - a];
-    for (uint32_t ty = ylo; ty < yhi; ++ty) {
-        const uint32_t lo = s_tb[v] + ty * s_tx[v] + xlo, hi = lo + (xhi - xlo);
-        for (uint32_t w = lo >> 5; (w << 5) < hi; ++w) {
-            uint32_t m = ~done[w] & word_mask(w, lo, hi);
-            while (m) {
-                const uint32_t t = (w << 5) + (uint32_t)(__ffs(m) - 1);
-                m &= m - 1;
-                if (pos < pair_cap) {
-                    keys[pos] = t;
-                    values[pos] = e;
+    uint32_t pos = 0, c = 0;
+    if (k < b) {
+        pos = offsets[k - a];
+        c = offsets[k - a + 1] - pos;
+    }
+    uint32_t m = __ballot_sync(kFull, c > 0);
+    if (!m) return;   // warp-uniform
+    uint32_t e = 0;
+    uint2 r = make_uint2(0u, 0u);
+    if (c > 0) {
+        e = order[k];
+        r = rect_sorted[k];
+    }
+    while (m) {
+        const int j = __ffs(m) - 1;
+        m &= m - 1;
+        const uint32_t rx = __shfl_sync(kFull, r.x, j), ry = __shfl_sync(kFull, r.y, j);
+        const uint32_t je = __shfl_sync(kFull, e, j), jpos = __shfl_sync(kFull, pos, j);
+        const uint32_t jc = __shfl_sync(kFull, c, j);
+        const uint32_t xlo = rx & 0x3FFu, xhi = (rx >> 10) & 0x3FFu, v = rx >> 20;
+        const uint32_t ylo = ry & 0x3FFu, yhi = (ry >> 10) & 0x3FFu;
+        const uint32_t w = xhi - xlo, area = w * (yhi - ylo);
+        const uint32_t tx = s_tx[v], t0 = s_tb[v] + ylo * tx + xlo;
+        const float rinv = 1.0f / (float)w;
+        uint32_t written = 0;
+        for (uint32_t f0 = 0; f0 < area && written < jc; f0 += 32) {
+            const uint32_t f = f0 + (uint32_t)lane;
+            bool live = false;
+            uint32_t t = 0;
+            if (f < area) {
+                uint32_t row = (uint32_t)((float)f * rinv);   // f / w, corrected below (f < 2^20)
+                if (row * w > f) --row;
+                else if ((row + 1u) * w <= f) ++row;
+                t = t0 + row * tx + (f - row * w);
+                live = !((done[t >> 5] >> (t & 31)) & 1u);
+            }
+            const uint32_t bm = __ballot_sync(kFull, live);
+            if (live) {
+                const uint64_t p = (uint64_t)jpos + written + __popc(bm & lt);
+                if (p < pair_cap) {
+                    keys[p] = t;
+                    values[p] = je;
                 } else {
                     atomicOr(overflow, 1u);
                 }
-                ++pos;
             }
+            written += __popc(bm);
         }
     }
 }
