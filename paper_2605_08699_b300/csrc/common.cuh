@@ -97,7 +97,7 @@ struct ViewParams {
     float limx, limy;     // 1.3 * W / (2 fx), 1.3 * H / (2 fy)
     int W, H, TX, TY;
     uint32_t tile_base;   // first global tile id of this view
-    uint32_t pad_;
+    uint32_t sat_base;    // sliced schedule: offset of this view's running-tile table ((TY+1) x (TX+1))
     uint8_t* out_rgba8;   // device pointer or null
     float* out_rgba_f32;  // device pointer or null
 };

@@ -428,7 +428,7 @@ namespace {
 struct SlicedLayout {
     int V = 0, S = 0, tile_bits = 0;
     uint64_t E = 0, total_pix = 0;
-    uint32_t total_tiles = 0, done_words = 0;
+    uint32_t total_tiles = 0, done_words = 0, total_sat = 0;
     uint64_t pix_base[kMaxViews] = {};
     size_t tmp_words = 0, fixed_bytes = 0;
 };
@@ -441,6 +441,8 @@ SlicedLayout sliced_layout(const Scene* scene, FrameRequest& req) {
     for (int v = 0; v < L.V; ++v) {
         req.views[v].tile_base = L.total_tiles;
         L.total_tiles += (uint32_t)(req.views[v].TX * req.views[v].TY);
+        req.views[v].sat_base = L.total_sat;
+        L.total_sat += (uint32_t)((req.views[v].TX + 1) * (req.views[v].TY + 1));
         L.pix_base[v] = L.total_pix;
         L.total_pix += (uint64_t)req.views[v].W * req.views[v].H;
     }
@@ -455,6 +457,7 @@ SlicedLayout sliced_layout(const Scene* scene, FrameRequest& req) {
     b += E * 4 * 4 + (E + 1) * 4 * 2 + E * 8;             // depth sort buffers, counts, offsets, rects
     b += L.tmp_words * 4;
     b += (sizeof(uint2) + 4 * 4 + 4) * (size_t)L.total_tiles + L.done_words * 4;   // ranges, active, strips
+    b += (size_t)L.total_sat * 4;                                                   // running-tile tables
     b += L.total_pix * 16 + sizeof(uint64_t) * kMaxViews * 2;
     L.fixed_bytes = b;
     return L;
@@ -524,6 +527,7 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     uint2* ranges = ctx.fixed.take<uint2>(total_tiles);
     uint32_t* active = ctx.fixed.take<uint32_t>(4 * (size_t)total_tiles);   // long tiles as 4 strips each
     uint32_t* strips = ctx.fixed.take<uint32_t>(total_tiles);
+    uint32_t* sat = ctx.fixed.take<uint32_t>(L.total_sat);
     uint32_t* done = ctx.fixed.take<uint32_t>(L.done_words);
     float4* state = ctx.fixed.take<float4>(L.total_pix);
 
@@ -595,7 +599,8 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
         if (b == a) continue;
         uint64_t* d_P = d_total + i;
         TIGAS_TRY(mark(kStScan, true));
-        TIGAS_TRY(launch_count_slice(rect_sorted, a, b, d_views, V, done, counts, st));
+        TIGAS_TRY(launch_running_sat(d_views, V, done, sat, st));
+        TIGAS_TRY(launch_count_slice(rect_sorted, a, b, d_views, V, sat, counts, st));
         // one extra zero count makes offsets[b - a] the slice total
         TIGAS_CUDA_TRY(cudaMemsetAsync(counts + (b - a), 0, sizeof(uint32_t), st));
         TIGAS_TRY(launch_scan_u32(counts, nullptr, offsets, b - a + 1, d_P, tmp, st));

@@ -59,22 +59,6 @@ __device__ inline bool tile_done(const uint32_t* __restrict__ done, uint32_t t) 
     return (done[t >> 5] >> (t & 31)) & 1u;
 }
 
-// Bits of bitmap word w that lie in [lo, hi).
-__device__ inline uint32_t word_mask(uint32_t w, uint32_t lo, uint32_t hi) {
-    const uint32_t wlo = w << 5;
-    const uint32_t a = lo > wlo ? lo - wlo : 0u;
-    const uint32_t b = hi - wlo < 32u ? hi - wlo : 32u;
-    const uint32_t upto_b = b >= 32u ? 0xFFFFFFFFu : ((1u << b) - 1u);
-    return upto_b & ~((1u << a) - 1u);
-}
-
-// Not-done tiles among tile ids [lo, hi).
-__device__ inline uint32_t count_running(const uint32_t* __restrict__ done, uint32_t lo, uint32_t hi) {
-    uint32_t c = 0;
-    for (uint32_t w = lo >> 5; (w << 5) < hi; ++w) c += __popc(~done[w] & word_mask(w, lo, hi));
-    return c;
-}
-
 // Depth-ordered rectangles of the kept entries, packed with their view:
 //   x = x_lo | x_hi << 10 | view << 20,  y = y_lo | y_hi << 10   (10 bits: TX, TY <= 512)
 __global__ void __launch_bounds__(256)
@@ -93,53 +77,57 @@ k_permute_rects(const uint32_t* __restrict__ order, uint64_t K, SplatArrays sp, 
                                 ((r.x >> 16) & 0x3FFu) | (((r.y >> 16) & 0x3FFu) << 10));
 }
 
-// counts[k - a] = tiles of entry order[k]'s rectangle that are not done.
-// A lane counts a small rectangle itself; a rectangle of more than kBigRows
-// bitmap-word reads is counted by the whole warp (rows spread over the lanes,
-// one reduction), so that a few Gaussians close to the camera do not hold a
-// warp for thousands of serial reads.
-constexpr uint32_t kBigRows = 12;
-
-__global__ void __launch_bounds__(256)
-k_count_slice(const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b, const ViewParams* __restrict__ views_g,
-              int V, const uint32_t* __restrict__ done, uint32_t* __restrict__ counts) {
-    __shared__ uint32_t s_tb[kMaxViews], s_tx[kMaxViews];
-    for (int k = threadIdx.x; k < V; k += blockDim.x) {
-        s_tb[k] = views_g[k].tile_base;
-        s_tx[k] = (uint32_t)views_g[k].TX;
+// Running-tile table of each view (one CTA per view): first every row's
+// prefix count of tiles not done, then the prefix down every column.
+__global__ void __launch_bounds__(512)
+k_running_sat(const ViewParams* __restrict__ views_g, const uint32_t* __restrict__ done, uint32_t* __restrict__ sat) {
+    const ViewParams& vp = views_g[blockIdx.x];
+    const uint32_t TX = (uint32_t)vp.TX, TY = (uint32_t)vp.TY, W1 = TX + 1;
+    uint32_t* s = sat + vp.sat_base;
+    for (uint32_t x = threadIdx.x; x <= TX; x += blockDim.x) s[x] = 0u;
+    for (uint32_t y = threadIdx.x; y < TY; y += blockDim.x) {
+        uint32_t* row = s + (y + 1) * W1;
+        const uint32_t t0 = vp.tile_base + y * TX;
+        uint32_t c = 0;
+        row[0] = 0u;
+        for (uint32_t x = 0; x < TX; ++x) {
+            const uint32_t t = t0 + x;
+            c += ((done[t >> 5] >> (t & 31)) & 1u) ^ 1u;
+            row[x + 1] = c;
+        }
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31;
+    for (uint32_t x = threadIdx.x + 1; x <= TX; x += blockDim.x) {
+        uint32_t c = 0;
+        for (uint32_t y = 1; y <= TY; ++y) {
+            c += s[y * W1 + x];
+            s[y * W1 + x] = c;
+        }
+    }
+}
+
+// counts[k - a] = tiles of entry order[k]'s rectangle that are not done.
+__global__ void __launch_bounds__(256)
+k_count_slice(const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b, const ViewParams* __restrict__ views_g,
+              int V, const uint32_t* __restrict__ sat, uint32_t* __restrict__ counts) {
+    __shared__ uint32_t s_sb[kMaxViews], s_w1[kMaxViews];
+    for (int k = threadIdx.x; k < V; k += blockDim.x) {
+        s_sb[k] = views_g[k].sat_base;
+        s_w1[k] = (uint32_t)views_g[k].TX + 1u;
+    }
+    __syncthreads();
     const uint64_t k = a + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool in = k < b;
-    const uint2 r = in ? rect_sorted[k] : make_uint2(0u, 0u);
+    if (k >= b) return;
+    const uint2 r = rect_sorted[k];
     const uint32_t xlo = r.x & 0x3FFu, xhi = (r.x >> 10) & 0x3FFu, v = r.x >> 20;
     const uint32_t ylo = r.y & 0x3FFu, yhi = (r.y >> 10) & 0x3FFu;
-    const uint32_t rows = yhi > ylo ? yhi - ylo : 0u;
-    const bool big = rows * (((xhi - xlo) >> 5) + 2u) > kBigRows;
     uint32_t c = 0;
-    if (!big) {
-        for (uint32_t ty = ylo; ty < yhi; ++ty) {
-            const uint32_t row = s_tb[v] + ty * s_tx[v];
-            c += count_running(done, row + xlo, row + xhi);
-        }
+    if (xhi > xlo && yhi > ylo) {
+        const uint32_t* s = sat + s_sb[v];
+        const uint32_t w1 = s_w1[v];
+        c = s[yhi * w1 + xhi] - s[ylo * w1 + xhi] - s[yhi * w1 + xlo] + s[ylo * w1 + xlo];
     }
-    uint32_t m = __ballot_sync(kFull, big);
-    while (m) {
-        const int j = __ffs(m) - 1;
-        m &= m - 1;
-        const uint32_t rx = __shfl_sync(kFull, r.x, j), ry = __shfl_sync(kFull, r.y, j);
-        const uint32_t jxlo = rx & 0x3FFu, jxhi = (rx >> 10) & 0x3FFu, jv = rx >> 20;
-        const uint32_t jylo = ry & 0x3FFu, jyhi = (ry >> 10) & 0x3FFu;
-        uint32_t part = 0;
-        for (uint32_t ty = jylo + lane; ty < jyhi; ty += 32) {
-            const uint32_t row = s_tb[jv] + ty * s_tx[jv];
-            part += count_running(done, row + jxlo, row + jxhi);
-        }
-        const uint32_t tot = __reduce_add_sync(kFull, part);
-        if (lane == j) c = tot;
-    }
-    if (in) counts[k - a] = c;
+    counts[k - a] = c;
 }
 
 // Pairs (tile, entry) of the slice for tiles not done, in depth order.  The
@@ -282,10 +270,16 @@ Status launch_permute_rects(const uint32_t* order, uint64_t K, const SplatArrays
     return {};
 }
 
+Status launch_running_sat(const ViewParams* views, int V, const uint32_t* done, uint32_t* sat, cudaStream_t st) {
+    k_running_sat<<<V, 512, 0, st>>>(views, done, sat);
+    TIGAS_LAUNCHED();
+    return {};
+}
+
 Status launch_count_slice(const uint2* rect_sorted, uint64_t a, uint64_t b, const ViewParams* views, int V,
-                          const uint32_t* done, uint32_t* counts, cudaStream_t st) {
+                          const uint32_t* sat, uint32_t* counts, cudaStream_t st) {
     if (b <= a) return {};
-    k_count_slice<<<(unsigned)((b - a + 255) / 256), 256, 0, st>>>(rect_sorted, a, b, views, V, done, counts);
+    k_count_slice<<<(unsigned)((b - a + 255) / 256), 256, 0, st>>>(rect_sorted, a, b, views, V, sat, counts);
     TIGAS_LAUNCHED();
     return {};
 }

@@ -20,9 +20,14 @@ Status launch_init_state(const ViewParams* views, int V, uint32_t total_tiles, c
 Status launch_permute_rects(const uint32_t* order, uint64_t K, const SplatArrays& sp, uint32_t n_per_view,
                             uint2* rect_sorted, cudaStream_t st);
 
-// counts[k - a]: not-done tiles in the rectangle of depth-ordered entry k, k in [a, b).
+// Per view, the summed-area table of tiles not done: sat[sat_base + y (TX+1) + x]
+// = not-done tiles in columns [0, x) of rows [0, y).
+Status launch_running_sat(const ViewParams* views, int V, const uint32_t* done, uint32_t* sat, cudaStream_t st);
+
+// counts[k - a]: not-done tiles in the rectangle of depth-ordered entry k, k in [a, b)
+// (four reads of the running-tile table).
 Status launch_count_slice(const uint2* rect_sorted, uint64_t a, uint64_t b, const ViewParams* views, int V,
-                          const uint32_t* done, uint32_t* counts, cudaStream_t st);
+                          const uint32_t* sat, uint32_t* counts, cudaStream_t st);
 
 // (tile, entry) pairs of entries [a, b) for tiles not done, at offsets[k - a]
 // (offsets: exclusive scan of counts with b - a + 1 values).
