@@ -378,6 +378,7 @@ constexpr int kSpinLimit = 1 << 22;
 #define TIGAS_LOOK_WINDOW 8
 #endif
 constexpr int kLookWin = TIGAS_LOOK_WINDOW;   // predecessor chunks read per look-back round
+
 constexpr uint32_t kSortTimeoutFlag = 16u;
 
 template <typename K>
@@ -448,19 +449,20 @@ __device__ inline uint32_t cta_exclusive_scan(uint32_t x, uint32_t* ws /*[T/32 +
 // Global digit histograms of every pass in one read (run-length aggregated
 // shared-memory counts, so keys with few distinct digits do not serialise).
 template <typename K>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(512, 2)
 k_os_hist(const K* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, int begin_bit, int end_bit,
           uint32_t* __restrict__ ghist) {
-    __shared__ uint32_t h[8][256];
+    constexpr int kP = (int)sizeof(K);   // most passes this key width can need
+    __shared__ uint32_t h[kP][256];
     const int passes = (end_bit - begin_bit + 7) / 8;
     for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
     const uint32_t n = count_of(n_cap, d_n);
-    uint32_t cur[8], run[8];
+    uint32_t cur[kP], run[kP];
 #pragma unroll
-    for (int p = 0; p < 8; ++p) { cur[p] = 0xFFFFFFFFu; run[p] = 0; }
-    // 8 keys per thread per step, all loads issued before any count
-    constexpr int kB = 8;
+    for (int p = 0; p < kP; ++p) { cur[p] = 0xFFFFFFFFu; run[p] = 0; }
+    // 4 keys per thread per step, all loads issued before any count
+    constexpr int kB = 4;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * kB;
     for (uint64_t i0 = ((uint64_t)blockIdx.x * blockDim.x) * kB + threadIdx.x; i0 < n; i0 += stride) {
         K kv[kB];
@@ -473,7 +475,7 @@ k_os_hist(const K* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, int b
         for (int b = 0; b < kB; ++b) {
             if (i0 + (uint64_t)b * blockDim.x >= n) break;
 #pragma unroll
-            for (int p = 0; p < 8; ++p) {
+            for (int p = 0; p < kP; ++p) {
                 if (p < passes) {
                     const int sh = begin_bit + 8 * p;
                     const int nb = min(8, end_bit - sh);
@@ -490,7 +492,7 @@ k_os_hist(const K* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, int b
         }
     }
 #pragma unroll
-    for (int p = 0; p < 8; ++p)
+    for (int p = 0; p < kP; ++p)
         if (p < passes && run[p]) atomicAdd(&h[p][cur[p]], run[p]);
     __syncthreads();
     for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
@@ -560,6 +562,8 @@ k_os_scatter(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in
 #pragma unroll
     for (int r = 0; r < I; ++r) {
         const uint32_t d = (uint32_t)(key[r] >> shift) & mask;
+        // peers by one ballot per digit bit (measured faster here than match.any
+        // with shared-memory atomics)
         const uint32_t peers = digit_peers(d, nbits);
         const uint32_t before = sm.whist[warp][d];
         __syncwarp();
