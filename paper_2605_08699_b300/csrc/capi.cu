@@ -206,8 +206,8 @@ Status do_render(Scene* scene, int V, const tigas_pose* poses, const tigas_intri
             if (dbg->rect) {
                 int32_t* r = dbg->rect + 4 * (size_t)i;
                 if (vis) {
-                    r[0] = rect[i].x & 0xFFFF; r[1] = rect[i].x >> 16;
-                    r[2] = rect[i].y & 0xFFFF; r[3] = rect[i].y >> 16;
+                    r[0] = rect[i].x & 0x3FF; r[1] = rect[i].y & 0x3FF;
+                    r[2] = (rect[i].x >> 10) & 0x3FF; r[3] = (rect[i].y >> 10) & 0x3FF;
                 } else {
                     r[0] = r[1] = r[2] = r[3] = 0;
                 }

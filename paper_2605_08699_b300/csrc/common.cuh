@@ -111,8 +111,9 @@ struct SplatArrays {
     float* blue;          // b
     uint32_t* depth_key;  // float bits of view z, 0xFFFFFFFF when culled
     uint32_t* tiles;      // tiles touched (0 when culled)
-    uint2* rect;          // (x_lo | y_lo << 16, x_hi | y_hi << 16)
+    uint2* rect;          // (x_lo | x_hi << 10 | view << 20, y_lo | y_hi << 10); (0, 0) when culled
     float* q_dbg;         // optional: 3 sqrt(lambda) per entry (parity diagnostics)
+    uint32_t* key_range;  // optional: [min, max] of the kept depth keys of the launch set
 };
 
 __host__ __device__ inline uint32_t ceil_div_u32(uint32_t a, uint32_t b) { return (a + b - 1) / b; }

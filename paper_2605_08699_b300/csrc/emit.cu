@@ -53,7 +53,7 @@ k_emit(const uint32_t* __restrict__ order, const uint32_t* __restrict__ offsets,
             off = offsets[k];
             if (cnt) {
                 const uint2 r = sp.rect[e];
-                const uint32_t xlo = r.x & 0xFFFFu, ylo = r.x >> 16, xhi = r.y & 0xFFFFu;
+                const uint32_t xlo = r.x & 0x3FFu, ylo = r.y & 0x3FFu, xhi = (r.x >> 10) & 0x3FFu;
                 const uint32_t v = e / n_per_view;
                 const uint32_t w = xhi - xlo;
                 base = vt[v].tile_base + ylo * vt[v].TX + xlo;

@@ -40,14 +40,24 @@ Status launch_emit_u64(const uint32_t* offsets, const SplatArrays& sp, const Vie
 // ping-pong buffers; the sorted result lands in (keys_out, values_out).
 // tmp: radix_tmp_words(n_cap) words.  flags (optional device word): bit 16 is
 // set when a look-back wait ran out (the result is then not to be trusted).
-// pre_hist (optional, device [passes][256]): the digit histograms of every
-// pass, already counted by the producer of the keys (skips one read).
+// A pass whose digit is the same for every key is skipped on the device.
+// ex (optional, 32-bit keys only):
+//   key_range: device [kmin, kmax] of the keys other than 0xFFFFFFFF; digits
+//     are taken from k - kmin (0xFFFFFFFF -> kmax - kmin + 1), the same order,
+//     so keys spanning less than 2^24 need three passes;
+//   pay_in / pay_alt / pay_out: an 8-byte payload per key moved with it.
+struct SortExtras {
+    const uint32_t* key_range = nullptr;
+    const uint2* pay_in = nullptr;
+    uint2* pay_alt = nullptr;
+    uint2* pay_out = nullptr;
+};
 size_t radix_tmp_words(uint64_t n_cap);
 template <typename K>
 Status radix_sort(const K* keys_in, const uint32_t* values_in, K* keys_alt, uint32_t* values_alt,
                   K* keys_out, uint32_t* values_out, uint64_t n_cap, const uint64_t* d_n, int begin_bit,
                   int end_bit, uint32_t* tmp, cudaStream_t st, int* passes_out, uint32_t* flags = nullptr,
-                  const uint32_t* pre_hist = nullptr);
+                  const SortExtras* ex = nullptr);
 
 // K5: tile ranges from sorted keys (tile = key >> shift), binary search per
 // tile.  ranges: n_tiles uint2.  A key outside [0, n_tiles) sets *overflow bit 2.

@@ -454,7 +454,7 @@ SlicedLayout sliced_layout(const Scene* scene, FrameRequest& req) {
     const uint64_t E = L.E;
     size_t b = sizeof(ViewParams) * kMaxViews + 96 * 256;
     b += E * (16 + 16 + 4 + 4 + 4 + 8 + (req.want_q ? 4 : 0));
-    b += E * 4 * 4 + (E + 1) * 4 * 2 + E * 8;             // depth sort buffers, counts, offsets, rects
+    b += E * 4 * 4 + (E + 1) * 4 * 2 + E * 8 * 2;         // depth sort buffers, counts, offsets, rects (2)
     b += L.tmp_words * 4;
     b += (sizeof(uint2) + 4 * 4 + 4) * (size_t)L.total_tiles + L.done_words * 4;   // ranges, active, strips
     b += (size_t)L.total_sat * 4;                                                   // running-tile tables
@@ -523,6 +523,8 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     uint32_t* counts = ctx.fixed.take<uint32_t>(E + 1);
     uint32_t* offsets = ctx.fixed.take<uint32_t>(E + 1);
     uint2* rect_sorted = ctx.fixed.take<uint2>(E);
+    uint2* rect_alt = ctx.fixed.take<uint2>(E);
+    sp.key_range = ctx.fixed.take<uint32_t>(2);
     uint32_t* tmp = ctx.fixed.take<uint32_t>(L.tmp_words);
     uint2* ranges = ctx.fixed.take<uint2>(total_tiles);
     uint32_t* active = ctx.fixed.take<uint32_t>(4 * (size_t)total_tiles);   // long tiles as 4 strips each
@@ -548,8 +550,16 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     TIGAS_TRY(launch_preprocess(scene->view, d_views, V, sp, d_visible, st));
     TIGAS_TRY(mark(kStPreprocess, false));
     TIGAS_TRY(mark(kStDepthSort, true));
+    // depth order of every entry; its packed rectangle travels with it (no gather
+    // afterwards), and digits count from the smallest kept depth key, so depths
+    // spanning less than 2^24 key steps skip the fourth pass on the device
+    SortExtras dex;
+    dex.key_range = sp.key_range;
+    dex.pay_in = sp.rect;
+    dex.pay_alt = rect_alt;
+    dex.pay_out = rect_sorted;
     TIGAS_TRY(radix_sort<uint32_t>(sp.depth_key, nullptr, pk_alt, pv_alt, pk, order, E, nullptr, 0, 32, tmp, st,
-                                   nullptr, d_flags));
+                                   nullptr, d_flags, &dex));
     TIGAS_TRY(mark(kStDepthSort, false));
     TIGAS_TRY(launch_init_state(d_views, V, total_tiles, d_pix_base, state, scene->view.bg, st));
 
@@ -562,9 +572,6 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
         K = 0;
         for (int v = 0; v < V; ++v) K += ctx.h_misc[v];
     }
-    TIGAS_TRY(mark(kStScan, true));
-    TIGAS_TRY(launch_permute_rects(order, K, sp, n, rect_sorted, st));
-    TIGAS_TRY(mark(kStScan, false));
 
     // geometric slice ends: K / 64 ... K
     uint64_t ends[kMaxSlices];

@@ -179,6 +179,7 @@ k_preprocess(SceneView scene, const ViewParams* __restrict__ views_g, int V, Spl
     const uint32_t n = scene.n;
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     uint64_t vis_mask = 0;
+    uint32_t kmin = 0xFFFFFFFFu, kmax = 0u;   // depth keys this thread kept
     Attr a;
     if (i < n) {
         float S[6];
@@ -247,15 +248,21 @@ k_preprocess(SceneView scene, const ViewParams* __restrict__ views_g, int V, Spl
                         out.geom[e] = make_float4(u, vv, -0.5f * kLog2e * conA, -kLog2e * conB);
                         reinterpret_cast<float2*>(out.appear)[2 * e] =
                             make_float2(-0.5f * kLog2e * conC, log2f(a.o));
-                        out.rect[e] = make_uint2((uint32_t)xlo | ((uint32_t)ylo << 16),
-                                                 (uint32_t)xhi | ((uint32_t)yhi << 16));
-                        out.depth_key[e] = __float_as_uint(pz);
+                        out.rect[e] = make_uint2((uint32_t)xlo | ((uint32_t)xhi << 10) | ((uint32_t)v << 20),
+                                                 (uint32_t)ylo | ((uint32_t)yhi << 10));
+                        const uint32_t key = __float_as_uint(pz);
+                        out.depth_key[e] = key;
+                        kmin = min(kmin, key);
+                        kmax = max(kmax, key);
                         vis_mask |= 1ull << v;
                     }
                 }
             }
             out.tiles[e] = tiles;
-            if (tiles == 0) out.depth_key[e] = 0xFFFFFFFFu;
+            if (tiles == 0) {
+                out.depth_key[e] = 0xFFFFFFFFu;
+                out.rect[e] = make_uint2(0u, 0u);   // empty rectangle
+            }
         }
     }
     // colour for the views that kept this Gaussian
@@ -277,6 +284,14 @@ k_preprocess(SceneView scene, const ViewParams* __restrict__ views_g, int V, Spl
             atomicAdd(&vis_count[v], 1u);
         }
     }
+    if (out.key_range) {
+        kmin = __reduce_min_sync(0xFFFFFFFFu, kmin);
+        kmax = __reduce_max_sync(0xFFFFFFFFu, kmax);
+        if ((threadIdx.x & 31) == 0 && kmin <= kmax) {
+            atomicMin(&out.key_range[0], kmin);
+            atomicMax(&out.key_range[1], kmax);
+        }
+    }
     __syncthreads();
     if (n_visible)
         for (int k = threadIdx.x; k < V; k += blockDim.x)
@@ -289,6 +304,10 @@ Status launch_preprocess(const SceneView& scene, const ViewParams* views, int V,
                          uint32_t* n_visible, cudaStream_t st) {
     if (V < 1 || V > kMaxViews) return {TIGAS_ERR_INVALID, "view count out of range"};
     if (n_visible) TIGAS_CUDA_TRY(cudaMemsetAsync(n_visible, 0, sizeof(uint32_t) * V, st));
+    if (out.key_range) {   // [min, max] of the kept depth keys: start from [0xFFFFFFFF, 0]
+        TIGAS_CUDA_TRY(cudaMemsetAsync(out.key_range, 0xFF, sizeof(uint32_t), st));
+        TIGAS_CUDA_TRY(cudaMemsetAsync(out.key_range + 1, 0, sizeof(uint32_t), st));
+    }
     if (scene.n == 0) return {};
     dim3 grid(ceil_div_u32(scene.n, 256));
     if (scene.storage == TIGAS_STORAGE_FP32)

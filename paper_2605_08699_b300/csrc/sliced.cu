@@ -59,24 +59,6 @@ __device__ inline bool tile_done(const uint32_t* __restrict__ done, uint32_t t) 
     return (done[t >> 5] >> (t & 31)) & 1u;
 }
 
-// Depth-ordered rectangles of the kept entries, packed with their view:
-//   x = x_lo | x_hi << 10 | view << 20,  y = y_lo | y_hi << 10   (10 bits: TX, TY <= 512)
-__global__ void __launch_bounds__(256)
-k_permute_rects(const uint32_t* __restrict__ order, uint64_t K, SplatArrays sp, uint32_t n_per_view,
-                uint2* __restrict__ rect_sorted) {
-    const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= K) return;
-    const uint32_t e = order[k];
-    if (sp.tiles[e] == 0) {   // culled entry: empty rectangle
-        rect_sorted[k] = make_uint2(0u, 0u);
-        return;
-    }
-    const uint2 r = sp.rect[e];
-    const uint32_t v = e / n_per_view;
-    rect_sorted[k] = make_uint2((r.x & 0x3FFu) | ((r.y & 0x3FFu) << 10) | (v << 20),
-                                ((r.x >> 16) & 0x3FFu) | (((r.y >> 16) & 0x3FFu) << 10));
-}
-
 // Running-tile table of each view (one CTA per view): first every row's
 // prefix count of tiles not done, then the prefix down every column.
 __global__ void __launch_bounds__(512)
@@ -258,14 +240,6 @@ Status launch_init_state(const ViewParams* views, int V, uint32_t total_tiles, c
                          float4* state, const float* bg, cudaStream_t st) {
     if (total_tiles == 0) return {};
     k_init_state<<<total_tiles, 256, 0, st>>>(views, V, pix_base, state, bg[0], bg[1], bg[2]);
-    TIGAS_LAUNCHED();
-    return {};
-}
-
-Status launch_permute_rects(const uint32_t* order, uint64_t K, const SplatArrays& sp, uint32_t n_per_view,
-                            uint2* rect_sorted, cudaStream_t st) {
-    if (K == 0) return {};
-    k_permute_rects<<<(unsigned)((K + 255) / 256), 256, 0, st>>>(order, K, sp, n_per_view, rect_sorted);
     TIGAS_LAUNCHED();
     return {};
 }

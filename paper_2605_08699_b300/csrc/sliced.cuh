@@ -16,10 +16,6 @@ constexpr uint32_t kTileMask = (1u << kStripShift) - 1u;
 Status launch_init_state(const ViewParams* views, int V, uint32_t total_tiles, const uint64_t* pix_base,
                          float4* state, const float* bg, cudaStream_t st);
 
-// rect_sorted[k] = packed rectangle and view of entry order[k], k < K (kept entries).
-Status launch_permute_rects(const uint32_t* order, uint64_t K, const SplatArrays& sp, uint32_t n_per_view,
-                            uint2* rect_sorted, cudaStream_t st);
-
 // Per view, the summed-area table of tiles not done: sat[sat_base + y (TX+1) + x]
 // = not-done tiles in columns [0, x) of rows [0, y).
 Status launch_running_sat(const ViewParams* views, int V, const uint32_t* done, uint32_t* sat, cudaStream_t st);

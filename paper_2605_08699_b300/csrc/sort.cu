@@ -381,15 +381,47 @@ constexpr int kLookWin = TIGAS_LOOK_WINDOW;   // predecessor chunks read per loo
 
 constexpr uint32_t kSortTimeoutFlag = 16u;
 
-template <typename K>
+// Tile shape of a scatter pass: T threads x I keys.  With an 8-byte payload a
+// CTA takes half the keys so that keys, values and payloads still fit two CTAs
+// per SM.
+template <typename K, bool PAY>
 struct OsCfg;
-template <>
-struct OsCfg<uint32_t> {
-    static constexpr int kT = 512, kI = 16, kMinBlocks = 2;   // two CTAs per SM: <= 64 registers
+template <bool PAY>
+struct OsCfg<uint32_t, PAY> {
+    static constexpr int kT = 512, kI = PAY ? 8 : 16, kMinBlocks = 2;   // two CTAs per SM: <= 64 registers
 };
-template <>
-struct OsCfg<uint64_t> {
+template <bool PAY>
+struct OsCfg<uint64_t, PAY> {
+    static_assert(!PAY, "payloads are carried by 32-bit key sorts only");
     static constexpr int kT = 256, kI = 16, kMinBlocks = 2;
+};
+
+// Where one pass reads and writes (device memory, written by k_os_bases once
+// every pass's digit histogram is known).  A pass whose digit is the same for
+// all keys is an identity permutation and is skipped; the passes that run
+// ping-pong so that the last one writes the output buffers.
+struct OsRoute {
+    const void* src_k;
+    const uint32_t* src_v;   // null: the value is the key's input position
+    const uint2* src_p;      // null: no payload
+    void* dst_k;
+    uint32_t* dst_v;
+    uint2* dst_p;
+    uint32_t active;
+    uint32_t pad;
+};
+constexpr int kRouteWords = (int)(sizeof(OsRoute) / 4);
+
+struct OsBuffers {
+    const void* in_k;
+    const uint32_t* in_v;
+    const uint2* in_p;
+    void* alt_k;
+    uint32_t* alt_v;
+    uint2* alt_p;
+    void* out_k;
+    uint32_t* out_v;
+    uint2* out_p;
 };
 
 __device__ inline uint32_t ld_relaxed(const uint32_t* p) {
@@ -400,6 +432,24 @@ __device__ inline uint32_t ld_relaxed(const uint32_t* p) {
 __device__ inline void st_relaxed(uint32_t* p, uint32_t v) {
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+
+// The value whose digits are sorted.  With a key range [kmin, kmax] (32-bit
+// keys only): k - kmin, and 0xFFFFFFFF (the "culled" key) -> kmax - kmin + 1,
+// an order-preserving map onto [0, kmax - kmin + 1], so the high digits of
+// keys spanning less than 2^24 are all zero and their pass is skipped.
+struct KeyMap {
+    uint32_t kmin = 0, span = 0;
+    bool on = false;
+    __device__ inline void load(const uint32_t* range) {
+        on = range != nullptr;
+        if (on) {
+            kmin = range[0];
+            span = range[1] - kmin + 1u;
+        }
+    }
+    __device__ inline uint32_t operator()(uint32_t k) const { return !on ? k : (k == 0xFFFFFFFFu ? span : k - kmin); }
+    __device__ inline uint64_t operator()(uint64_t k) const { return k; }
+};
 
 // Lanes of the warp whose digit (nb bits) equals this lane's: the AND over the
 // digit's bits of the ballot of lanes agreeing on that bit (warp multisplit).
@@ -430,18 +480,17 @@ __device__ inline uint32_t cta_exclusive_scan(uint32_t x, uint32_t* ws /*[T/32 +
     if (lane == 31) ws[warp] = inc;
     __syncthreads();
     if (warp == 0) {
-        uint32_t w = lane < W ? ws[lane] : 0u;
-        uint32_t wi = w;
+        uint32_t v = lane < W ? ws[lane] : 0u;
+        uint32_t iv = v;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            uint32_t y = __shfl_up_sync(kFull, wi, d);
-            if (lane >= d) wi += y;
+            uint32_t y = __shfl_up_sync(kFull, iv, d);
+            if (lane >= d) iv += y;
         }
-        if (lane < W) ws[lane] = wi - w;
-        if (lane == W - 1) ws[W] = wi;
+        if (lane < W) ws[lane] = iv - v;
     }
     __syncthreads();
-    uint32_t r = ws[warp] + inc - x;
+    const uint32_t r = ws[warp] + inc - x;
     __syncthreads();
     return r;
 }
@@ -451,11 +500,13 @@ __device__ inline uint32_t cta_exclusive_scan(uint32_t x, uint32_t* ws /*[T/32 +
 template <typename K>
 __global__ void __launch_bounds__(512, 2)
 k_os_hist(const K* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, int begin_bit, int end_bit,
-          uint32_t* __restrict__ ghist) {
+          uint32_t* __restrict__ ghist, const uint32_t* __restrict__ range) {
     constexpr int kP = (int)sizeof(K);   // most passes this key width can need
     __shared__ uint32_t h[kP][256];
     const int passes = (end_bit - begin_bit + 7) / 8;
     for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+    KeyMap km;
+    km.load(range);
     __syncthreads();
     const uint32_t n = count_of(n_cap, d_n);
     uint32_t cur[kP], run[kP];
@@ -469,7 +520,7 @@ k_os_hist(const K* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, int b
 #pragma unroll
         for (int b = 0; b < kB; ++b) {
             const uint64_t i = i0 + (uint64_t)b * blockDim.x;
-            kv[b] = i < n ? keys[i] : K(0);
+            kv[b] = i < n ? km(keys[i]) : K(0);
         }
 #pragma unroll
         for (int b = 0; b < kB; ++b) {
@@ -501,22 +552,54 @@ k_os_hist(const K* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, int b
     }
 }
 
-// ghist[p][256] -> exclusive digit bases gbase[p][256]
+// ghist[p][256] -> exclusive digit bases gbase[p][256], and every pass's route:
+// pass 0 always runs, a later pass only if more than one of its digits occurs.
 __global__ void __launch_bounds__(256) k_os_bases(const uint32_t* __restrict__ ghist, uint32_t* __restrict__ gbase,
-                                                  int passes) {
+                                                  int passes, OsRoute* __restrict__ routes, OsBuffers bufs) {
     __shared__ uint32_t ws[9];
+    __shared__ uint32_t act[8];
     for (int p = 0; p < passes; ++p) {
-        uint32_t x = ghist[p * 256 + threadIdx.x];
-        uint32_t e = cta_exclusive_scan<256>(x, ws);
+        const uint32_t x = ghist[p * 256 + threadIdx.x];
+        const uint32_t e = cta_exclusive_scan<256>(x, ws);
         gbase[p * 256 + threadIdx.x] = e;
+        const int nz = __syncthreads_count(x != 0u);
+        if (threadIdx.x == 0) act[p] = (p == 0 || nz > 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int n_act = 0;
+        for (int p = 0; p < passes; ++p) n_act += (int)act[p];
+        const void* sk = bufs.in_k;
+        const uint32_t* sv = bufs.in_v;
+        const uint2* spp = bufs.in_p;
+        int i = 0;
+        for (int p = 0; p < passes; ++p) {
+            OsRoute r{};
+            r.active = act[p];
+            if (act[p]) {
+                const bool to_out = ((n_act - 1 - i) % 2) == 0;
+                r.src_k = sk;
+                r.src_v = sv;
+                r.src_p = spp;
+                r.dst_k = to_out ? bufs.out_k : bufs.alt_k;
+                r.dst_v = to_out ? bufs.out_v : bufs.alt_v;
+                r.dst_p = bufs.in_p ? (to_out ? bufs.out_p : bufs.alt_p) : nullptr;
+                sk = r.dst_k;
+                sv = r.dst_v;
+                spp = r.dst_p;
+                ++i;
+            }
+            routes[p] = r;
+        }
     }
 }
 
-template <typename K>
+template <typename K, bool PAY>
 struct OsSmem {
-    static constexpr int T = OsCfg<K>::kT, I = OsCfg<K>::kI, N = T * I, W = T / 32;
+    static constexpr int T = OsCfg<K, PAY>::kT, I = OsCfg<K, PAY>::kI, N = T * I, W = T / 32;
     K keys[N];
     uint32_t vals[N];
+    uint2 pays[PAY ? N : 1];
     uint32_t whist[W][256];
     uint32_t dstart[256];
     uint32_t gpos[256];
@@ -524,17 +607,25 @@ struct OsSmem {
     uint32_t chunk;
 };
 
-template <typename K>
-__global__ void __launch_bounds__(OsCfg<K>::kT, OsCfg<K>::kMinBlocks)
-k_os_scatter(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, K* __restrict__ keys_out,
-             uint32_t* __restrict__ vals_out, uint64_t n_cap, const uint64_t* d_n, int shift, int nbits,
+template <typename K, bool PAY, bool MAP>
+__global__ void __launch_bounds__(OsCfg<K, PAY>::kT, OsCfg<K, PAY>::kMinBlocks)
+k_os_scatter(const OsRoute* __restrict__ route, uint64_t n_cap, const uint64_t* d_n, int shift, int nbits,
              const uint32_t* __restrict__ gbase, uint32_t* status, uint32_t* chunk_counter, uint32_t* flags,
-             int spin_limit) {
+             int spin_limit, const uint32_t* __restrict__ range) {
+    if (route->active == 0u) return;   // identity pass: skipped by every CTA
+    const K* __restrict__ keys_in = static_cast<const K*>(route->src_k);
+    const uint32_t* __restrict__ vals_in = route->src_v;
+    const uint2* __restrict__ pays_in = route->src_p;
+    K* __restrict__ keys_out = static_cast<K*>(route->dst_k);
+    uint32_t* __restrict__ vals_out = route->dst_v;
+    uint2* __restrict__ pays_out = route->dst_p;
     const uint32_t mask = (1u << nbits) - 1u;
-    constexpr int T = OsCfg<K>::kT, I = OsCfg<K>::kI, N = T * I, W = T / 32;
+    constexpr int T = OsCfg<K, PAY>::kT, I = OsCfg<K, PAY>::kI, N = T * I, W = T / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    OsSmem<K>& sm = *reinterpret_cast<OsSmem<K>*>(smem_raw);
+    OsSmem<K, PAY>& sm = *reinterpret_cast<OsSmem<K, PAY>*>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    KeyMap km;
+    if (MAP) km.load(range);
     if (threadIdx.x == 0) sm.chunk = atomicAdd(chunk_counter, 1u);
     for (int k = threadIdx.x; k < W * 256; k += T) (&sm.whist[0][0])[k] = 0;
     __syncthreads();
@@ -546,22 +637,33 @@ k_os_scatter(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in
 
     K key[I];
     uint32_t val[I];
+    uint2 pay[PAY ? I : 1];
 #pragma unroll
     for (int r = 0; r < I; ++r) {
         const uint32_t li = warp * (I * 32) + r * 32 + lane;
         if (li < valid) {
             key[r] = keys_in[base + li];
             val[r] = vals_in ? vals_in[base + li] : (uint32_t)(base + li);
+            if (PAY) pay[r] = pays_in[base + li];
         } else {
             key[r] = ~K(0);
             val[r] = 0;
+            if (PAY) pay[r] = make_uint2(0u, 0u);
         }
     }
     uint32_t dr[I];
     const uint32_t lt = lanemask_lt();
 #pragma unroll
     for (int r = 0; r < I; ++r) {
-        const uint32_t d = (uint32_t)(key[r] >> shift) & mask;
+        const uint32_t li = warp * (I * 32) + r * 32 + lane;
+        (void)li;
+        // padding keys take the largest digit so that they sort after every key
+        // (without a key map their all-ones key gives it already)
+        uint32_t d;
+        if constexpr (MAP)
+            d = li < valid ? (uint32_t)(km(key[r]) >> shift) & mask : mask;
+        else
+            d = (uint32_t)(key[r] >> shift) & mask;
         // peers by one ballot per digit bit (measured faster here than match.any
         // with shared-memory atomics)
         const uint32_t peers = digit_peers(d, nbits);
@@ -638,6 +740,7 @@ k_os_scatter(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in
         const uint32_t pos = sm.dstart[d] + sm.whist[warp][d] + (dr[r] & 0xFFFFu);
         sm.keys[pos] = key[r];
         sm.vals[pos] = val[r];
+        if (PAY) sm.pays[pos] = pay[r];
     }
     __syncthreads();
 #pragma unroll 4
@@ -645,71 +748,67 @@ k_os_scatter(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in
         const uint32_t j = k * T + threadIdx.x;
         if (j < valid) {
             const K kk = sm.keys[j];
-            const uint32_t d = (uint32_t)(kk >> shift) & mask;
+            const uint32_t d = (uint32_t)((MAP ? km(kk) : kk) >> shift) & mask;
             const uint32_t g = sm.gpos[d] + (j - sm.dstart[d]);
             if (g < n) {
                 keys_out[g] = kk;
                 vals_out[g] = sm.vals[j];
+                if (PAY) pays_out[g] = sm.pays[j];
             }
         }
     }
 }
 
-template <typename K>
+template <typename K, bool PAY, bool MAP>
 Status ensure_os_smem() {
     static std::atomic<bool> done{false};
     if (done.load()) return {};
-    TIGAS_CUDA_TRY(cudaFuncSetAttribute(k_os_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)sizeof(OsSmem<K>)));
+    TIGAS_CUDA_TRY(cudaFuncSetAttribute(k_os_scatter<K, PAY, MAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)sizeof(OsSmem<K, PAY>)));
     // the largest shared-memory carveout, so that two CTAs fit per SM
-    TIGAS_CUDA_TRY(cudaFuncSetAttribute(k_os_scatter<K>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    TIGAS_CUDA_TRY(
+        cudaFuncSetAttribute(k_os_scatter<K, PAY, MAP>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     done.store(true);
     return {};
 }
 
-uint64_t os_chunks(uint64_t n_cap) { return (n_cap + 4095) / 4096; }   // upper bound for both key widths
+uint64_t os_chunks(uint64_t n_cap) { return (n_cap + 4095) / 4096; }   // upper bound for every tile shape
 
-size_t os_tmp_words(uint64_t n_cap) { return 8 * 256 * 2 + 16 + os_chunks(n_cap) * 256; }
+// tmp layout: ghist [8][256], gbase [8][256], chunk counters [8], flags [8],
+// routes [8], status [chunks][256]
+constexpr size_t kOsHead = 8 * 256 * 2 + 16 + 8 * kRouteWords;
+size_t os_tmp_words(uint64_t n_cap) { return kOsHead + os_chunks(n_cap) * 256; }
 
-template <typename K>
+template <typename K, bool PAY, bool MAP>
 Status radix_sort_onesweep(const K* keys_in, const uint32_t* values_in, K* keys_alt, uint32_t* values_alt,
                            K* keys_out, uint32_t* values_out, uint64_t n_cap, const uint64_t* d_n, int begin_bit,
-                           int end_bit, uint32_t* tmp, cudaStream_t st, uint32_t* flags, const uint32_t* pre_hist) {
-    constexpr int T = OsCfg<K>::kT, N = OsCfg<K>::kT * OsCfg<K>::kI;
+                           int end_bit, uint32_t* tmp, cudaStream_t st, uint32_t* flags, const SortExtras* ex) {
+    constexpr int T = OsCfg<K, PAY>::kT, N = OsCfg<K, PAY>::kT * OsCfg<K, PAY>::kI;
     const int passes = (end_bit - begin_bit + 7) / 8;
-    TIGAS_TRY(ensure_os_smem<K>());
+    TIGAS_TRY((ensure_os_smem<K, PAY, MAP>()));
     uint32_t* ghist = tmp;
     uint32_t* gbase = tmp + 8 * 256;
     uint32_t* counters = gbase + 8 * 256;
     uint32_t* own_flags = counters + 8;
-    uint32_t* status = counters + 16;
+    OsRoute* routes = reinterpret_cast<OsRoute*>(counters + 16);
+    uint32_t* status = tmp + kOsHead;
     if (!flags) flags = own_flags;
+    const uint32_t* range = MAP ? ex->key_range : nullptr;
     const uint64_t chunks = (n_cap + N - 1) / N;
-    if (pre_hist) {
-        TIGAS_CUDA_TRY(cudaMemsetAsync(gbase + 8 * 256, 0, 16 * sizeof(uint32_t), st));
-        ghist = const_cast<uint32_t*>(pre_hist);
-    } else {
-        TIGAS_CUDA_TRY(cudaMemsetAsync(tmp, 0, (8 * 256 * 2 + 16) * sizeof(uint32_t), st));
-        k_os_hist<K><<<2 * 148 * 4, 512, 0, st>>>(keys_in, n_cap, d_n, begin_bit, end_bit, ghist);
-        TIGAS_LAUNCHED();
-    }
-    k_os_bases<<<1, 256, 0, st>>>(ghist, gbase, passes);
+    TIGAS_CUDA_TRY(cudaMemsetAsync(tmp, 0, (8 * 256 * 2 + 16) * sizeof(uint32_t), st));
+    k_os_hist<K><<<2 * 148 * 4, 512, 0, st>>>(keys_in, n_cap, d_n, begin_bit, end_bit, ghist, range);
     TIGAS_LAUNCHED();
-    const K* src_k = keys_in;
-    const uint32_t* src_v = values_in;
+    OsBuffers bufs{keys_in, values_in, PAY ? ex->pay_in : nullptr, keys_alt, values_alt, PAY ? ex->pay_alt : nullptr,
+                   keys_out, values_out, PAY ? ex->pay_out : nullptr};
+    k_os_bases<<<1, 256, 0, st>>>(ghist, gbase, passes, routes, bufs);
+    TIGAS_LAUNCHED();
     for (int p = 0; p < passes; ++p) {
         const int shift = begin_bit + 8 * p;
         const int nb = min(8, end_bit - shift);
-        const bool to_out = ((passes - 1 - p) % 2) == 0;
-        K* dk = to_out ? keys_out : keys_alt;
-        uint32_t* dv = to_out ? values_out : values_alt;
         TIGAS_CUDA_TRY(cudaMemsetAsync(status, 0, chunks * 256 * sizeof(uint32_t), st));
-        k_os_scatter<K><<<(unsigned)chunks, T, sizeof(OsSmem<K>), st>>>(src_k, src_v, dk, dv, n_cap, d_n, shift,
-                                                                       nb, gbase + p * 256, status, counters + p,
-                                                                       flags, kSpinLimit);
+        k_os_scatter<K, PAY, MAP><<<(unsigned)chunks, T, sizeof(OsSmem<K, PAY>), st>>>(
+            routes + p, n_cap, d_n, shift, nb, gbase + p * 256, status, counters + p, flags, kSpinLimit, range);
         TIGAS_LAUNCHED();
-        src_k = dk;
-        src_v = dv;
     }
     return {};
 }
@@ -723,12 +822,13 @@ Status radix_sort_onesweep(const K* keys_in, const uint32_t* values_in, K* keys_
 // of both chunks, so every scattered position is below 2N.
 Status debug_lookback_timeout(int spin_limit, bool* timed_out) {
     using K = uint32_t;
-    constexpr int T = OsCfg<K>::kT, N = OsCfg<K>::kT * OsCfg<K>::kI;
+    constexpr int T = OsCfg<K, false>::kT, N = OsCfg<K, false>::kT * OsCfg<K, false>::kI;
     *timed_out = false;
     if (spin_limit < 1 || spin_limit > (1 << 20)) return {TIGAS_ERR_INVALID, "spin limit out of 1..2^20"};
-    TIGAS_TRY(ensure_os_smem<K>());
+    TIGAS_TRY((ensure_os_smem<K, false, false>()));
     const uint64_t n = 2 * (uint64_t)N;
-    const size_t words = 2 * n + 256 + 256 + 2 * 256 + 8;
+    const size_t route_words = 2 * kRouteWords;
+    const size_t words = 2 * n + 256 + 256 + 2 * 256 + 8 + route_words;
     uint32_t* buf = nullptr;
     TIGAS_CUDA_TRY(cudaMalloc(&buf, words * sizeof(uint32_t)));
     uint32_t* keys = buf;
@@ -736,7 +836,8 @@ Status debug_lookback_timeout(int spin_limit, bool* timed_out) {
     uint32_t* ghist = buf + 2 * n;
     uint32_t* gbase = ghist + 256;
     uint32_t* status = gbase + 256;
-    uint32_t* misc = status + 2 * 256;   // [chunk counter, flags]
+    uint32_t* misc = status + 2 * 256;                               // [chunk counter, flags, ...]
+    OsRoute* route = reinterpret_cast<OsRoute*>(misc + 8);           // 8-byte aligned: 2n + 1032 words
     Status st;
     std::vector<uint32_t> h(n);
     for (uint64_t i = 0; i < n; ++i) h[i] = (uint32_t)((i * 2654435761u) >> 7);
@@ -747,10 +848,11 @@ Status debug_lookback_timeout(int spin_limit, bool* timed_out) {
     const uint32_t misc_init[2] = {1u, 0u};   // the only CTA claims chunk 1
     if (e == cudaSuccess) e = cudaMemcpy(misc, misc_init, sizeof(misc_init), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
-        k_os_hist<K><<<4, 512>>>(keys, n, nullptr, 0, 8, ghist);
-        k_os_bases<<<1, 256>>>(ghist, gbase, 1);
-        k_os_scatter<K><<<1, T, sizeof(OsSmem<K>)>>>(keys, nullptr, out, sorted_vals, n, nullptr, 0, 8, gbase, status,
-                                                     misc, misc + 1, spin_limit);
+        OsBuffers bufs{keys, nullptr, nullptr, out, sorted_vals, nullptr, out, sorted_vals, nullptr};
+        k_os_hist<K><<<4, 512>>>(keys, n, nullptr, 0, 8, ghist, nullptr);
+        k_os_bases<<<1, 256>>>(ghist, gbase, 1, route, bufs);
+        k_os_scatter<K, false, false><<<1, T, sizeof(OsSmem<K, false>)>>>(route, n, nullptr, 0, 8, gbase, status,
+                                                                          misc, misc + 1, spin_limit, nullptr);
         g_launches.fetch_add(3, std::memory_order_relaxed);
         e = cudaGetLastError();
     }
@@ -772,10 +874,13 @@ size_t radix_tmp_words(uint64_t n_cap) {
 template <typename K>
 Status radix_sort(const K* keys_in, const uint32_t* values_in, K* keys_alt, uint32_t* values_alt, K* keys_out,
                   uint32_t* values_out, uint64_t n_cap, const uint64_t* d_n, int begin_bit, int end_bit,
-                  uint32_t* tmp, cudaStream_t st, int* passes_out, uint32_t* flags, const uint32_t* pre_hist) {
+                  uint32_t* tmp, cudaStream_t st, int* passes_out, uint32_t* flags, const SortExtras* ex) {
     const int kbits = (int)(8 * sizeof(K));
     if (begin_bit < 0 || end_bit > kbits || begin_bit > end_bit) return {TIGAS_ERR_INVALID, "bad sort bit range"};
     if (n_cap >= 0xFFFFFFFFull) return {TIGAS_ERR_INVALID, "sort too large"};
+    const bool pay = ex && ex->pay_in;
+    if (ex && (sizeof(K) != 4 || (pay && (!ex->pay_alt || !ex->pay_out))))
+        return {TIGAS_ERR_INVALID, "key range and payload need 32-bit keys and all three payload buffers"};
     const int passes = (end_bit - begin_bit + 7) / 8;
     if (passes_out) *passes_out = passes;
     if (n_cap == 0) return {};
@@ -783,20 +888,38 @@ Status radix_sort(const K* keys_in, const uint32_t* values_in, K* keys_alt, uint
         TIGAS_CUDA_TRY(cudaMemcpyAsync(keys_out, keys_in, n_cap * sizeof(K), cudaMemcpyDeviceToDevice, st));
         if (values_in)
             TIGAS_CUDA_TRY(cudaMemcpyAsync(values_out, values_in, n_cap * 4, cudaMemcpyDeviceToDevice, st));
+        if (pay) TIGAS_CUDA_TRY(cudaMemcpyAsync(ex->pay_out, ex->pay_in, n_cap * 8, cudaMemcpyDeviceToDevice, st));
         return {};
     }
-    if (n_cap < (1ull << 30))
-        return radix_sort_onesweep<K>(keys_in, values_in, keys_alt, values_alt, keys_out, values_out, n_cap, d_n,
-                                      begin_bit, end_bit, tmp, st, flags, pre_hist);
+    if (n_cap < (1ull << 30)) {
+        if constexpr (sizeof(K) == 4) {
+            const bool map = ex && ex->key_range;
+            if (pay && map)
+                return radix_sort_onesweep<K, true, true>(keys_in, values_in, keys_alt, values_alt, keys_out,
+                                                          values_out, n_cap, d_n, begin_bit, end_bit, tmp, st, flags,
+                                                          ex);
+            if (pay)
+                return radix_sort_onesweep<K, true, false>(keys_in, values_in, keys_alt, values_alt, keys_out,
+                                                           values_out, n_cap, d_n, begin_bit, end_bit, tmp, st,
+                                                           flags, ex);
+            if (map)
+                return radix_sort_onesweep<K, false, true>(keys_in, values_in, keys_alt, values_alt, keys_out,
+                                                           values_out, n_cap, d_n, begin_bit, end_bit, tmp, st,
+                                                           flags, ex);
+        }
+        return radix_sort_onesweep<K, false, false>(keys_in, values_in, keys_alt, values_alt, keys_out, values_out,
+                                                    n_cap, d_n, begin_bit, end_bit, tmp, st, flags, ex);
+    }
+    if (ex) return {TIGAS_ERR_INVALID, "key range and payload need fewer than 2^30 keys"};
     return radix_sort_rts<K>(keys_in, values_in, keys_alt, values_alt, keys_out, values_out, n_cap, d_n, begin_bit,
                              end_bit, tmp, st);
 }
 
 template Status radix_sort<uint32_t>(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, uint32_t*, uint32_t*,
                                      uint64_t, const uint64_t*, int, int, uint32_t*, cudaStream_t, int*, uint32_t*,
-                                     const uint32_t*);
+                                     const SortExtras*);
 template Status radix_sort<uint64_t>(const uint64_t*, const uint32_t*, uint64_t*, uint32_t*, uint64_t*, uint32_t*,
                                      uint64_t, const uint64_t*, int, int, uint32_t*, cudaStream_t, int*, uint32_t*,
-                                     const uint32_t*);
+                                     const SortExtras*);
 
 }  // namespace tigas
