@@ -12,7 +12,8 @@
 // one of them (a result-invariant skip: a pixel the box excludes would skip
 // the entry by the alpha test, a pixel that stopped ignores it).  For
 // the kept entries each pixel computes alpha = min(0.99, o exp(power)) as
-// 2^(power log2 e + log2 o), skips alpha < 1/255 before any exponential, and
+// 2^(power log2 e + log2 o) (two FMAs per pixel after the row-independent part),
+// skips alpha < 1/255 before any exponential, and
 // stops before the entry that would bring T below 1e-4.  A warp vote skips the
 // blend step when no pixel of the tile gains from an entry, and the warp
 // leaves the list once all 256 pixels have stopped.
@@ -176,23 +177,26 @@ __device__ __forceinline__ bool blend_rows(WarpStage& sm, int lane, const uint2*
             const float4 gm = sm.geom[buf][j];
             const float4 ap = sm.appear[buf][j];
             const float dx = gm.x - pxf;
-            const float adx = gm.z * dx, bdx = gm.w * dx;
+            const float bdx = gm.w * dx;
+            // log2(o exp(power)) = (a' dx^2 + log2 o) + dy (b' dx + c' dy); the
+            // quadratic form is negative definite, so power <= 0 needs no test
+            const float p0 = fmaf(gm.z * dx, dx, ap.y);
             const float dyb = gm.y - py0f;
             float e[NP];
-            uint32_t con = 0;
+            bool con[NP];
+            bool anyc = false;
 #pragma unroll
             for (int k = 0; k < NP; ++k) {
                 const float dy = dyb - 2.0f * (float)k;
-                // power log2 e = a' dx^2 + dy (b' dx + c' dy)
-                const float p = fmaf(adx, dx, dy * fmaf(ap.x, dy, bdx));
-                e[k] = p + ap.y;
-                if (((live >> k) & 1u) && p <= 0.0f && e[k] >= kMinLog2Alpha) con |= 1u << k;
+                e[k] = fmaf(dy, fmaf(ap.x, dy, bdx), p0);
+                con[k] = ((live >> k) & 1u) && e[k] >= kMinLog2Alpha;
+                anyc |= con[k];
             }
-            if (__any_sync(kFull, con != 0)) {
+            if (__any_sync(kFull, anyc)) {
                 const float cbl = sm.blue[buf][j];
 #pragma unroll
                 for (int k = 0; k < NP; ++k) {
-                    if ((con >> k) & 1u) {
+                    if (con[k]) {
                         const float alpha = fminf(0.99f, ex2_approx(e[k]));
                         const float tT = fmaf(-T[k], alpha, T[k]);
                         if (tT < 1e-4f) {
