@@ -796,7 +796,10 @@ Status radix_sort_onesweep(const K* keys_in, const uint32_t* values_in, K* keys_
     const uint32_t* range = MAP ? ex->key_range : nullptr;
     const uint64_t chunks = (n_cap + N - 1) / N;
     TIGAS_CUDA_TRY(cudaMemsetAsync(tmp, 0, (8 * 256 * 2 + 16) * sizeof(uint32_t), st));
-    k_os_hist<K><<<2 * 148 * 4, 512, 0, st>>>(keys_in, n_cap, d_n, begin_bit, end_bit, ghist, range);
+    // enough CTAs for eight grid strides of 4 keys per thread, at most 8 per SM
+    const uint64_t hist_ctas = (n_cap + 512 * 4 * 8 - 1) / (512 * 4 * 8);
+    const unsigned hgrid = (unsigned)(hist_ctas < 148 ? 148 : (hist_ctas > 148 * 8 ? 148 * 8 : hist_ctas));
+    k_os_hist<K><<<hgrid, 512, 0, st>>>(keys_in, n_cap, d_n, begin_bit, end_bit, ghist, range);
     TIGAS_LAUNCHED();
     OsBuffers bufs{keys_in, values_in, PAY ? ex->pay_in : nullptr, keys_alt, values_alt, PAY ? ex->pay_alt : nullptr,
                    keys_out, values_out, PAY ? ex->pay_out : nullptr};
