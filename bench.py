@@ -164,9 +164,8 @@ def roofline(stage_ms: dict, per_step: dict, peaks: dict, clocks: dict, steps: i
     """Achieved rate of every stage and the roofline entry of the dominant one.
     Algorithmic work per launch set of the sliced schedule (see the design notes):
       preprocess  12 B per (Gaussian, view) + (A - 12) B per Gaussian + 52 B per kept entry
-      depth_sort  4 passes x 16 B per entry
-      scan        40 B per kept entry: rectangle permute (order 4 B + rect gather 8 B + write 8 B),
-                  slice count (rect 8 B + count 4 B), count scan (4 B + 4 B)
+      depth_sort  passes run x 32 B per entry (key, value and 8-byte rectangle, read and written)
+      scan        20 B per kept entry: slice count (rect 8 B + count 4 B), count scan (4 B + 4 B)
       emit        16 B per kept entry (order, rect, offset) + 8 B per emitted pair
       pair_sort   passes x 16 B per emitted pair
       ranges      8 B per tile per slice
@@ -177,8 +176,8 @@ def roofline(stage_ms: dict, per_step: dict, peaks: dict, clocks: dict, steps: i
     w = per_step
     bytes_per = {
         "preprocess": w["entries"] * 12 + w["gaussians"] * (w["attr_bytes"] - 12) + w["kept"] * 52,
-        "depth_sort": w["entries"] * 4 * 16,
-        "scan": w["kept"] * 40,
+        "depth_sort": w["entries"] * w["depth_passes"] * 32,
+        "scan": w["kept"] * 20,
         "emit": w["kept"] * 16 + w["pairs"] * 8,
         "pair_sort": w["pairs"] * w["sort_passes"] * 16,
         "ranges": w["tiles"] * w["slices"] * 8,
@@ -262,6 +261,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     TX, TY = (W + 15) // 16, (H + 15) // 16
     per_step = {"pairs": st0["n_pairs"], "kept": st0["n_visible"], "evals": st0["blend_evals"],
                 "fetched": st0["blend_fetched"], "contribs": st0["blend_contribs"], "sort_passes": st0["sort_passes"],
+                "depth_passes": st0["depth_sort_passes"],
                 "entries": V * scene.n, "gaussians": scene.n, "attr_bytes": 124, "tiles": V * TX * TY,
                 "slices": schedule["n_slices"]}
 

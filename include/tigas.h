@@ -132,6 +132,9 @@ typedef struct {
     uint64_t blend_evals;        /* list entries evaluated, summed over pixels, up to each pixel's stop */
     uint64_t blend_fetched;      /* list entries staged into shared memory by the blend */
     uint64_t blend_contribs;     /* evaluations that blended (alpha >= 1/255, pixel not stopped) */
+    uint32_t depth_sort_passes;  /* SLICED: radix passes the depth sort ran (passes whose digit is the
+                                    same for every key are skipped); 0 for the other schedules */
+    uint32_t reserved;
 } tigas_frame_stats;
 
 /* tigas_render with options.

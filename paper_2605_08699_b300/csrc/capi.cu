@@ -186,6 +186,7 @@ Status do_render(Scene* scene, int V, const tigas_pose* poses, const tigas_intri
         stats->blend_evals = cnt[0];
         stats->blend_fetched = cnt[1];
         stats->blend_contribs = cnt[2];
+        stats->depth_sort_passes = sort_mode == TIGAS_SORT_SLICED ? ctx.h_flags[1] : 0u;
     }
     if (dbg) {
         const uint32_t n = scene->view.n;

@@ -560,6 +560,9 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     dex.pay_out = rect_sorted;
     TIGAS_TRY(radix_sort<uint32_t>(sp.depth_key, nullptr, pk_alt, pv_alt, pk, order, E, nullptr, 0, 32, tmp, st,
                                    nullptr, d_flags, &dex));
+    // passes the depth sort ran (read before the slices' scans reuse tmp)
+    TIGAS_CUDA_TRY(cudaMemcpyAsync(ctx.h_flags + 1, radix_active_passes(tmp), sizeof(uint32_t),
+                                   cudaMemcpyDeviceToHost, st));
     TIGAS_TRY(mark(kStDepthSort, false));
     TIGAS_TRY(launch_init_state(d_views, V, total_tiles, d_pix_base, state, scene->view.bg, st));
 

@@ -555,7 +555,8 @@ k_os_hist(const K* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, int b
 // ghist[p][256] -> exclusive digit bases gbase[p][256], and every pass's route:
 // pass 0 always runs, a later pass only if more than one of its digits occurs.
 __global__ void __launch_bounds__(256) k_os_bases(const uint32_t* __restrict__ ghist, uint32_t* __restrict__ gbase,
-                                                  int passes, OsRoute* __restrict__ routes, OsBuffers bufs) {
+                                                  int passes, OsRoute* __restrict__ routes, OsBuffers bufs,
+                                                  uint32_t* __restrict__ n_active_out) {
     __shared__ uint32_t ws[9];
     __shared__ uint32_t act[8];
     for (int p = 0; p < passes; ++p) {
@@ -569,6 +570,7 @@ __global__ void __launch_bounds__(256) k_os_bases(const uint32_t* __restrict__ g
     if (threadIdx.x == 0) {
         int n_act = 0;
         for (int p = 0; p < passes; ++p) n_act += (int)act[p];
+        if (n_active_out) *n_active_out = (uint32_t)n_act;
         const void* sk = bufs.in_k;
         const uint32_t* sv = bufs.in_v;
         const uint2* spp = bufs.in_p;
@@ -803,7 +805,7 @@ Status radix_sort_onesweep(const K* keys_in, const uint32_t* values_in, K* keys_
     TIGAS_LAUNCHED();
     OsBuffers bufs{keys_in, values_in, PAY ? ex->pay_in : nullptr, keys_alt, values_alt, PAY ? ex->pay_alt : nullptr,
                    keys_out, values_out, PAY ? ex->pay_out : nullptr};
-    k_os_bases<<<1, 256, 0, st>>>(ghist, gbase, passes, routes, bufs);
+    k_os_bases<<<1, 256, 0, st>>>(ghist, gbase, passes, routes, bufs, counters + 15);
     TIGAS_LAUNCHED();
     for (int p = 0; p < passes; ++p) {
         const int shift = begin_bit + 8 * p;
@@ -853,7 +855,7 @@ Status debug_lookback_timeout(int spin_limit, bool* timed_out) {
     if (e == cudaSuccess) {
         OsBuffers bufs{keys, nullptr, nullptr, out, sorted_vals, nullptr, out, sorted_vals, nullptr};
         k_os_hist<K><<<4, 512>>>(keys, n, nullptr, 0, 8, ghist, nullptr);
-        k_os_bases<<<1, 256>>>(ghist, gbase, 1, route, bufs);
+        k_os_bases<<<1, 256>>>(ghist, gbase, 1, route, bufs, nullptr);
         k_os_scatter<K, false, false><<<1, T, sizeof(OsSmem<K, false>)>>>(route, n, nullptr, 0, 8, gbase, status,
                                                                           misc, misc + 1, spin_limit, nullptr);
         g_launches.fetch_add(3, std::memory_order_relaxed);
@@ -868,6 +870,8 @@ Status debug_lookback_timeout(int spin_limit, bool* timed_out) {
     *timed_out = (flags & kSortTimeoutFlag) != 0;
     return st;
 }
+
+const uint32_t* radix_active_passes(const uint32_t* tmp) { return tmp + 8 * 256 * 2 + 15; }
 
 size_t radix_tmp_words(uint64_t n_cap) {
     size_t a = rts_tmp_words(n_cap), b = os_tmp_words(n_cap);

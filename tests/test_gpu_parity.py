@@ -454,3 +454,26 @@ def test_autotune_picks_a_candidate_and_keeps_frames(h1, cuda):
             assert np.array_equal(a, b)
     finally:
         tg.set_schedule(**base)
+
+
+def test_depth_sort_skips_constant_high_digit(h1, cuda):
+    # the camera at distance 3 sees depths in about [2, 4]: the kept keys span
+    # far fewer than 2^24 steps, so the fourth pass is skipped
+    w, h = 160, 120
+    out = torch.empty((h, w, 4), dtype=torch.uint8, device=cuda)
+    st = tg.render_batch(h1, [synth.BASE_POSE], [synth.default_intrinsics(w, h)], [w], [h], [out],
+                         sort_mode=tg.SORT_SLICED)
+    assert st["depth_sort_passes"] == 3
+    # at the edge of the scene (near plane 0.2 to depths of about 2, 2^24.8 key
+    # steps in FP32 for this scene) the fourth pass runs
+    inside = synth.Pose(0.0, 0.0, (0.0, 0.0, -1.0))
+    st = tg.render_batch(h1, [inside], [synth.default_intrinsics(w, h)], [w], [h], [out], sort_mode=tg.SORT_SLICED)
+    assert st["depth_sort_passes"] == 4
+    # at full size the slices' scans reuse the sort's scratch: the count is read before them
+    s3 = synth.config_scene(3, n=1_000_000)
+    W, H = 1920, 1080
+    big = torch.empty((H, W, 4), dtype=torch.uint8, device=cuda)
+    with tg.scene_from(s3, storage=tg.STORAGE_FP16) as h3:
+        st = tg.render_batch(h3, [synth.config_trajectory(3)[0]] * 2, [synth.default_intrinsics(W, H)] * 2,
+                             [W] * 2, [H] * 2, [big, big], sort_mode=tg.SORT_SLICED)
+    assert st["depth_sort_passes"] in (3, 4)
