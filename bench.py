@@ -295,6 +295,46 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     elapsed_ms, frames = aggregate_over_ranks(elapsed_ms, V * args.steps, world, dev)
     value = frames / (elapsed_ms * 1e-3)
 
+    # ---- two launch sets in flight (two host threads, two streams, as the server's two slots)
+    concurrent = None
+    if args.inflight > 1:
+        import threading as _th
+        K2 = args.inflight
+        streams = [stream] + [torch.cuda.Stream(device=dev) for _ in range(K2 - 1)]
+        outs_k = [outs] + [[torch.empty((H, W, 4), dtype=torch.uint8, device=dev) for _ in range(V)]
+                           for _ in range(K2 - 1)]
+
+        def worker(k, n_steps, base):
+            torch.cuda.set_device(local_rank)
+            for s in range(n_steps):
+                poses = [trajs[v][((base + s * K2 + k) * 7 + v) % len(trajs[v])] for v in range(V)]
+                tg.render_batch(h16, poses, [K] * V, [W] * V, [H] * V, outs_k[k], stream=streams[k])
+
+        for k in range(K2):   # warm-up of every stream's context and graph
+            worker(k, 3, 0)
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(streams[0])
+        for k in range(1, K2):
+            streams[k].wait_event(c0)
+        n_each = max(1, args.steps)
+        ths = [_th.Thread(target=worker, args=(k, n_each, 100)) for k in range(K2)]
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
+        for k in range(1, K2):
+            ev = torch.cuda.Event()
+            ev.record(streams[k])
+            streams[0].wait_event(ev)
+        c1.record(streams[0])
+        torch.cuda.synchronize()
+        cms = c0.elapsed_time(c1)
+        concurrent = {"launch_sets_in_flight": K2, "frames": V * n_each * K2, "ms": round(cms, 3),
+                      "frames_per_s": round(V * n_each * K2 / (cms * 1e-3), 2),
+                      "note": "each host thread renders its own launch sets on its own stream; "
+                              "events on stream 0 after it waited for the others"}
+
     # ---- end to end: pinned host outputs, copies inside the timed region
     houts = [torch.empty((H, W, 4), dtype=torch.uint8).pin_memory() for _ in range(V)]
     torch.cuda.synchronize()
@@ -358,7 +398,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     if not args.no_serving and args.trace_seconds > 0:
         trace = run_serving_trace(tg, torch, dev, args)
 
-    res = {"schedule": schedule, "rerenders": rerenders, "value": value, "elapsed_ms": elapsed_ms, "frames": frames, "per_step": per_step, "stage_ms": stage_ms,
+    res = {"schedule": schedule, "rerenders": rerenders, "concurrent": concurrent, "value": value, "elapsed_ms": elapsed_ms, "frames": frames, "per_step": per_step, "stage_ms": stage_ms,
            "clocks": clocks, "launches": launches, "e2e": e2e, "plain_fp32": plain, "serving": serving, "trace": trace,
            "batching": batching,
            "step_ms_host": step_ms_host, "scene": scene}
@@ -543,6 +583,7 @@ def main(argv=None) -> int:
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule")
+    ap.add_argument("--inflight", type=int, default=2, help="also time this many launch sets in flight (1: skip)")
     ap.add_argument("--schedule", default="", help="fixed schedule 'slices,first_slice_inv,blend_ctas_per_sm' "
                                                    "(no autotuning)")
     ap.add_argument("--trace-seconds", type=float, default=10.0, help="open-loop serving trace length (0: skip)")
@@ -594,7 +635,7 @@ def main(argv=None) -> int:
                                                   "pixels all stopped are dropped", autotuned=not (args.no_autotune or args.schedule),
                              exact_rerenders_timed=r["rerenders"]),
             "served_fp16": r["serving"], "plain_fp32": r["plain_fp32"], "serving_trace": r["trace"],
-            "batching_32_mixed": r["batching"],
+            "batching_32_mixed": r["batching"], "in_flight": r["concurrent"],
             "roofline": roof, "stages": stages, "per_step": {k: int(v) for k, v in r["per_step"].items()},
             "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": int(r["launches"]), "clocks": r["clocks"],
         }

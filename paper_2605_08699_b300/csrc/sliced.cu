@@ -59,23 +59,32 @@ __device__ inline bool tile_done(const uint32_t* __restrict__ done, uint32_t t) 
     return (done[t >> 5] >> (t & 31)) & 1u;
 }
 
-// Running-tile table of each view (one CTA per view): first every row's
-// prefix count of tiles not done, then the prefix down every column.
-__global__ void __launch_bounds__(512)
+// Running-tile table of each view (one CTA per view): every row's prefix
+// count of tiles not done (a warp per row, 32 columns per step, ballot and
+// prefix popcount), then the prefix down every column.  Tables up to
+// kSatSmem words are built in shared memory and copied out once.
+constexpr uint32_t kSatSmem = 12288;   // 48 KB
+
+__global__ void __launch_bounds__(1024)
 k_running_sat(const ViewParams* __restrict__ views_g, const uint32_t* __restrict__ done, uint32_t* __restrict__ sat) {
+    __shared__ uint32_t tab[kSatSmem];
     const ViewParams& vp = views_g[blockIdx.x];
     const uint32_t TX = (uint32_t)vp.TX, TY = (uint32_t)vp.TY, W1 = TX + 1;
-    uint32_t* s = sat + vp.sat_base;
+    const bool in_smem = (TY + 1) * W1 <= kSatSmem;
+    uint32_t* s = in_smem ? tab : sat + vp.sat_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
     for (uint32_t x = threadIdx.x; x <= TX; x += blockDim.x) s[x] = 0u;
-    for (uint32_t y = threadIdx.x; y < TY; y += blockDim.x) {
+    for (uint32_t y = warp; y < TY; y += n_warps) {
         uint32_t* row = s + (y + 1) * W1;
         const uint32_t t0 = vp.tile_base + y * TX;
-        uint32_t c = 0;
-        row[0] = 0u;
-        for (uint32_t x = 0; x < TX; ++x) {
-            const uint32_t t = t0 + x;
-            c += ((done[t >> 5] >> (t & 31)) & 1u) ^ 1u;
-            row[x + 1] = c;
+        if (lane == 0) row[0] = 0u;
+        uint32_t carry = 0;
+        for (uint32_t x0 = 0; x0 < TX; x0 += 32) {
+            const uint32_t x = x0 + lane, t = t0 + x;
+            const bool run = x < TX && !((done[t >> 5] >> (t & 31)) & 1u);
+            const uint32_t b = __ballot_sync(0xFFFFFFFFu, run);
+            if (x < TX) row[x + 1] = carry + __popc(b & (0xFFFFFFFFu >> (31 - lane)));
+            carry += __popc(b);
         }
     }
     __syncthreads();
@@ -85,6 +94,11 @@ k_running_sat(const ViewParams* __restrict__ views_g, const uint32_t* __restrict
             c += s[y * W1 + x];
             s[y * W1 + x] = c;
         }
+    }
+    if (in_smem) {
+        __syncthreads();
+        uint32_t* g = sat + vp.sat_base;
+        for (uint32_t i = threadIdx.x; i < (TY + 1) * W1; i += blockDim.x) g[i] = tab[i];
     }
 }
 
@@ -245,7 +259,7 @@ Status launch_init_state(const ViewParams* views, int V, uint32_t total_tiles, c
 }
 
 Status launch_running_sat(const ViewParams* views, int V, const uint32_t* done, uint32_t* sat, cudaStream_t st) {
-    k_running_sat<<<V, 512, 0, st>>>(views, done, sat);
+    k_running_sat<<<V, 1024, 0, st>>>(views, done, sat);
     TIGAS_LAUNCHED();
     return {};
 }
