@@ -120,6 +120,10 @@ __device__ __forceinline__ bool blend_rows(WarpStage& sm, int lane, const uint2*
         }
     }
 
+    float thr[NP];   // per pixel: log2 of the smallest alpha that counts, or +inf (not compositing)
+#pragma unroll
+    for (int k = 0; k < NP; ++k) thr[k] = ((live >> k) & 1u) ? kMinLog2Alpha : __int_as_float(0x7f800000);
+
     const uint2 rg = ranges[g];
     const uint32_t start = rg.x, end = rg.y > rg.x ? rg.y : rg.x;
     const int nb = (int)((end - start + kWB - 1) / kWB);
@@ -189,7 +193,7 @@ __device__ __forceinline__ bool blend_rows(WarpStage& sm, int lane, const uint2*
             for (int k = 0; k < NP; ++k) {
                 const float dy = dyb - 2.0f * (float)k;
                 e[k] = fmaf(dy, fmaf(ap.x, dy, bdx), p0);
-                con[k] = ((live >> k) & 1u) && e[k] >= kMinLog2Alpha;
+                con[k] = e[k] >= thr[k];   // thr: the alpha cut-off, +inf once the pixel stopped
                 anyc |= con[k];
             }
             if (__any_sync(kFull, anyc)) {
@@ -201,6 +205,7 @@ __device__ __forceinline__ bool blend_rows(WarpStage& sm, int lane, const uint2*
                         const float tT = fmaf(-T[k], alpha, T[k]);
                         if (tT < 1e-4f) {
                             live &= ~(1u << k);
+                            thr[k] = __int_as_float(0x7f800000);
                         } else {
                             if (COUNT) ++cnt.blend;
                             const float w = alpha * T[k];
