@@ -114,6 +114,8 @@ struct SplatArrays {
     uint2* rect;          // (x_lo | x_hi << 10 | view << 20, y_lo | y_hi << 10); (0, 0) when culled
     float* q_dbg;         // optional: 3 sqrt(lambda) per entry (parity diagnostics)
     uint32_t* key_range;  // optional: [min, max] of the kept depth keys of the launch set
+    int tight_rect;       // 1: rect = the 3-sigma rectangle cut to the tiles the alpha >= 1/255 region
+                          // can reach (result-invariant; the sliced schedule), 0: the 3-sigma rectangle
 };
 
 __host__ __device__ inline uint32_t ceil_div_u32(uint32_t a, uint32_t b) { return (a + b - 1) / b; }

@@ -525,6 +525,7 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     uint2* rect_sorted = ctx.fixed.take<uint2>(E);
     uint2* rect_alt = ctx.fixed.take<uint2>(E);
     sp.key_range = ctx.fixed.take<uint32_t>(2);
+    sp.tight_rect = req.want_q ? 0 : 1;   // debug frames report the method's 3-sigma rectangles
     uint32_t* tmp = ctx.fixed.take<uint32_t>(L.tmp_words);
     uint2* ranges = ctx.fixed.take<uint2>(total_tiles);
     uint32_t* active = ctx.fixed.take<uint32_t>(4 * (size_t)total_tiles);   // long tiles as 4 strips each

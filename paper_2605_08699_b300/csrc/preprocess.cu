@@ -244,6 +244,19 @@ k_preprocess(SceneView scene, const ViewParams* __restrict__ views_g, int V, Spl
                     int yhi = min(vp.TY, floor_div16_clamped(vv + r, vp.TY) + 1);
                     if (xhi > xlo && yhi > ylo) tiles = (uint32_t)((xhi - xlo) * (yhi - ylo));
                     if (out.q_dbg) out.q_dbg[e] = q;
+                    if (tiles > 0 && out.tight_rect) {
+                        // only the tiles the alpha >= 1/255 ellipse d^T S^-1 d <= 2 ln(255 o) can
+                        // reach: its box has half-extents sqrt(tau S_xx), sqrt(tau S_yy), taken
+                        // 2 % + 1 px wider so that FP32 rounding in the blend cannot fall outside
+                        const float tau = 2.0f * logf(255.0f * a.o);
+                        const float hx = fmaf(sqrtf(fmaxf(tau, 0.0f) * ca), 1.02f, 1.0f);
+                        const float hy = fmaf(sqrtf(fmaxf(tau, 0.0f) * cc), 1.02f, 1.0f);
+                        xlo = max(xlo, floor_div16_clamped(u - hx, vp.TX));
+                        xhi = min(xhi, floor_div16_clamped(u + hx, vp.TX) + 1);
+                        ylo = max(ylo, floor_div16_clamped(vv - hy, vp.TY));
+                        yhi = min(yhi, floor_div16_clamped(vv + hy, vp.TY) + 1);
+                        if (xhi <= xlo || yhi <= ylo) xlo = xhi = ylo = yhi = 0;   // reaches no pixel
+                    }
                     if (tiles > 0) {
                         out.geom[e] = make_float4(u, vv, -0.5f * kLog2e * conA, -kLog2e * conB);
                         reinterpret_cast<float2*>(out.appear)[2 * e] =

@@ -137,6 +137,19 @@ def test_sliced_schedule_gives_the_full_list_frame(h1, s1, k, w, h):
     parity.assert_colour(sliced["rgba_f32"], oracle.render(oracle.preprocess(s1, pose, K, w, h)))
 
 
+@pytest.mark.parametrize("k,w,h", [(0, 320, 240), (150, 320, 240), (299, 97, 61), (40, 1000, 3), (75, 640, 360)])
+def test_sliced_fast_path_gives_the_full_list_frame(h1, k, w, h):
+    # the render path (no debug outputs) cuts every rectangle to the tiles its
+    # alpha >= 1/255 region can reach: the frame must not change by one bit
+    pose = synth.config_trajectory(1)[k]
+    K = synth.default_intrinsics(w, h)
+    full = tg.debug_render(h1, pose, K, w, h, sort_mode=tg.SORT_DEPTH_FIRST)
+    fast = np.zeros((h, w, 4), np.float32)
+    st = tg.render_ex(h1, pose, K, w, h, out_rgba_f32=fast, sort_mode=tg.SORT_SLICED)
+    assert np.array_equal(full["rgba_f32"], fast)
+    assert st["n_pairs"] <= full["pairs"]
+
+
 def test_sliced_debug_render_has_no_whole_lists(h1):
     with pytest.raises(tg.TigasError):
         tg.load_library()
