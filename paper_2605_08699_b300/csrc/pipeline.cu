@@ -320,6 +320,7 @@ Status render_frame(Scene* scene, FrameRequest& req, RenderContext& ctx, cudaStr
     }
     uint32_t* tmp = ctx.fixed.take<uint32_t>(tmp_words);
     uint2* ranges = ctx.fixed.take<uint2>(total_tiles);
+    if (ctx.fixed.over) return {TIGAS_ERR_CUDA, "workspace layout exceeds its reservation"};
 
     std::memcpy(ctx.h_views, req.views, sizeof(ViewParams) * V);
     TIGAS_CUDA_TRY(cudaMemcpyAsync(d_views, ctx.h_views, sizeof(ViewParams) * V, cudaMemcpyHostToDevice, st));
@@ -362,6 +363,7 @@ Status render_frame(Scene* scene, FrameRequest& req, RenderContext& ctx, cudaStr
     uint32_t* vals_b = ctx.pairs.take<uint32_t>(P);
     uint32_t* vals_c = ctx.pairs.take<uint32_t>(P);
     uint32_t* stmp = ctx.pairs.take<uint32_t>(sort_words);
+    if (ctx.fixed.over || ctx.pairs.over) return {TIGAS_ERR_CUDA, "workspace layout exceeds its reservation"};
 
     int passes = 0;
     if (!full64) {
@@ -533,6 +535,7 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     uint32_t* sat = ctx.fixed.take<uint32_t>(L.total_sat);
     uint32_t* done = ctx.fixed.take<uint32_t>(L.done_words);
     float4* state = ctx.fixed.take<float4>(L.total_pix);
+    if (ctx.fixed.over) return {TIGAS_ERR_CUDA, "sliced workspace layout exceeds its reservation"};
 
     // host -> device: the view table and the views' pixel offsets (pinned staging)
     sliced_stage_views(scene, req, ctx);
@@ -603,7 +606,10 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
         vals_c = ctx.pairs.take<uint32_t>(cap);
         stmp = ctx.pairs.take<uint32_t>(radix_tmp_words(cap));
     };
-    if (stat) take_pairs(static_cap);
+    if (stat) {
+        take_pairs(static_cap);
+        if (ctx.pairs.over) return {TIGAS_ERR_CUDA, "pair workspace layout exceeds its reservation"};
+    }
     for (int i = 0; i < S; ++i) {
         const uint64_t b = ends[i] > a ? ends[i] : a;
         if (slice_pairs) slice_pairs[i] = 0;
@@ -630,6 +636,7 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
             total_pairs += P;
             TIGAS_TRY(ctx.pairs.reserve(pair_bytes_for(P)));
             take_pairs(P);
+            if (ctx.pairs.over) return {TIGAS_ERR_CUDA, "pair workspace layout exceeds its reservation"};
             cap = P;
         }
         TIGAS_TRY(mark(kStEmit, true));

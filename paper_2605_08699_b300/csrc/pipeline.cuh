@@ -25,12 +25,17 @@ struct Arena {
     size_t cap = 0;
     size_t used = 0;
     uint64_t gen = 0;               // bumped on every reallocation (captured graphs hold pointers)
+    bool over = false;              // a take went past cap since the last reset (nothing may launch)
     Status reserve(size_t bytes);   // call only when no work uses the arena
-    void reset() { used = 0; }
+    void reset() {
+        used = 0;
+        over = false;
+    }
     template <typename T>
     T* take(size_t count) {
         size_t off = (used + 255) & ~size_t(255);
         used = off + count * sizeof(T);
+        if (used > cap) over = true;
         return reinterpret_cast<T*>(base + off);
     }
     void release();

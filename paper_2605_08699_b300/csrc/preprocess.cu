@@ -271,7 +271,7 @@ k_preprocess(SceneView scene, const ViewParams* __restrict__ views_g, int V, Spl
                     }
                 }
             }
-            out.tiles[e] = tiles;
+            if (!out.tight_rect) out.tiles[e] = tiles;   // the sliced render path reads rectangles only
             if (tiles == 0) {
                 out.depth_key[e] = 0xFFFFFFFFu;
                 out.rect[e] = make_uint2(0u, 0u);   // empty rectangle
