@@ -26,7 +26,11 @@ namespace {
 
 constexpr int kWarps = 4;                 // tiles per CTA
 constexpr int kThreads = 32 * kWarps;
-constexpr int kWB = 32;                   // entries per warp batch
+#ifndef TIGAS_BLEND_BATCH
+#define TIGAS_BLEND_BATCH 32
+#endif
+constexpr int kWB = TIGAS_BLEND_BATCH;    // entries per warp batch (at most 32: one per lane)
+static_assert(kWB >= 1 && kWB <= 32, "a batch holds one entry per lane at most");
 constexpr int kPix = 8;                   // pixels per thread
 #ifndef TIGAS_BLEND_MIN_BLOCKS
 #define TIGAS_BLEND_MIN_BLOCKS 6
@@ -129,7 +133,7 @@ __device__ __forceinline__ bool blend_rows(WarpStage& sm, int lane, const uint2*
     const int nb = (int)((end - start + kWB - 1) / kWB);
     auto stage = [&](int b, int buf) {
         const uint32_t idx = start + (uint32_t)b * kWB + lane;
-        if (idx < end) {
+        if (lane < kWB && idx < end) {   // one staged entry per lane of the batch
             const uint32_t e = values[idx];
             if (e < n_entries) {
                 cp_async16(&sm.geom[buf][lane], sp.geom + e);

@@ -5,7 +5,10 @@
 
 namespace tigas {
 
-constexpr uint32_t kHeavyTile = 128;   // pairs of a slice that make a tile "long"
+#ifndef TIGAS_HEAVY_TILE
+#define TIGAS_HEAVY_TILE 128
+#endif
+constexpr uint32_t kHeavyTile = TIGAS_HEAVY_TILE;   // pairs of a slice that make a tile "long"
 // Active-list items: a tile id (whole tile) or tile id | (s + 1) << kStripShift
 // for strip s (pixel rows 4s..4s+3) of a long tile.
 constexpr int kStripShift = 28;
