@@ -72,18 +72,37 @@ __device__ inline void load_shape(const uint4* __restrict__ ch, uint32_t i, Attr
     }
 }
 
+// SH coefficients of one Gaussian, [16][3] order.  FP32 storage keeps floats;
+// FP16 storage keeps the packed half pairs (24 registers instead of 48) and
+// converts each coefficient where it is used.
 template <int STORAGE>
-__device__ inline void load_sh(const uint4* __restrict__ ch, uint32_t i, int degree, float* c) {
+struct ShCoefs;
+template <>
+struct ShCoefs<TIGAS_STORAGE_FP32> {
+    float c[48];
+    __device__ inline float get(int i) const { return c[i]; }
+};
+template <>
+struct ShCoefs<TIGAS_STORAGE_FP16> {
+    uint32_t w[24];
+    __device__ inline float get(int i) const {
+        const float2 h = unpack_half2(w[i >> 1]);
+        return (i & 1) ? h.y : h.x;
+    }
+};
+
+template <int STORAGE>
+__device__ inline void load_sh(const uint4* __restrict__ ch, uint32_t i, int degree, ShCoefs<STORAGE>& sc) {
     const int n_float = 3 * (degree + 1) * (degree + 1);
-    if (STORAGE == TIGAS_STORAGE_FP32) {
+    if constexpr (STORAGE == TIGAS_STORAGE_FP32) {
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
             if (4 * k < n_float) {
                 uint4 v = __ldg(ch + chunk_index(i, 3 + k, kChunksF32));
-                c[4 * k] = __uint_as_float(v.x); c[4 * k + 1] = __uint_as_float(v.y);
-                c[4 * k + 2] = __uint_as_float(v.z); c[4 * k + 3] = __uint_as_float(v.w);
+                sc.c[4 * k] = __uint_as_float(v.x); sc.c[4 * k + 1] = __uint_as_float(v.y);
+                sc.c[4 * k + 2] = __uint_as_float(v.z); sc.c[4 * k + 3] = __uint_as_float(v.w);
             } else {
-                c[4 * k] = c[4 * k + 1] = c[4 * k + 2] = c[4 * k + 3] = 0.0f;
+                sc.c[4 * k] = sc.c[4 * k + 1] = sc.c[4 * k + 2] = sc.c[4 * k + 3] = 0.0f;
             }
         }
     } else {
@@ -91,12 +110,9 @@ __device__ inline void load_sh(const uint4* __restrict__ ch, uint32_t i, int deg
         for (int k = 0; k < 6; ++k) {
             if (8 * k < n_float) {
                 uint4 v = __ldg(ch + chunk_index(i, 2 + k, kChunksF16));
-                float2 a = unpack_half2(v.x), b = unpack_half2(v.y), d = unpack_half2(v.z), e = unpack_half2(v.w);
-                c[8 * k] = a.x; c[8 * k + 1] = a.y; c[8 * k + 2] = b.x; c[8 * k + 3] = b.y;
-                c[8 * k + 4] = d.x; c[8 * k + 5] = d.y; c[8 * k + 6] = e.x; c[8 * k + 7] = e.y;
+                sc.w[4 * k] = v.x; sc.w[4 * k + 1] = v.y; sc.w[4 * k + 2] = v.z; sc.w[4 * k + 3] = v.w;
             } else {
-#pragma unroll
-                for (int j = 0; j < 8; ++j) c[8 * k + j] = 0.0f;
+                sc.w[4 * k] = sc.w[4 * k + 1] = sc.w[4 * k + 2] = sc.w[4 * k + 3] = 0u;
             }
         }
     }
@@ -123,8 +139,9 @@ __device__ inline void covariance3d(const Attr& a, float* S) {
     S[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
 }
 
-// RGB from SH coefficients c[16*3] at unit direction (x, y, z).
-__device__ inline void sh_to_rgb(int degree, const float* c, float x, float y, float z, float* rgb) {
+// RGB from SH coefficients at unit direction (x, y, z).
+template <typename Coefs>
+__device__ inline void sh_to_rgb(int degree, const Coefs& c, float x, float y, float z, float* rgb) {
     float b[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) b[k] = 0.0f;
@@ -153,7 +170,7 @@ __device__ inline void sh_to_rgb(int degree, const float* c, float x, float y, f
     for (int ch = 0; ch < 3; ++ch) {
         float acc = 0.f;
 #pragma unroll
-        for (int k = 0; k < 16; ++k) acc = fmaf(b[k], c[3 * k + ch], acc);
+        for (int k = 0; k < 16; ++k) acc = fmaf(b[k], c.get(3 * k + ch), acc);
         rgb[ch] = fmaxf(acc + 0.5f, 0.0f);
     }
 }
@@ -166,7 +183,10 @@ __device__ inline int floor_div16_clamped(float x, int hi) {
 }
 
 template <int STORAGE>
-__global__ void __launch_bounds__(256)
+#ifndef TIGAS_PRE_MIN_BLOCKS
+#define TIGAS_PRE_MIN_BLOCKS 3
+#endif
+__global__ void __launch_bounds__(256, TIGAS_PRE_MIN_BLOCKS)
 k_preprocess(SceneView scene, const ViewParams* __restrict__ views_g, int V, SplatArrays out,
              uint32_t* __restrict__ n_visible) {
     __shared__ ViewParams views[kMaxViews];
@@ -280,7 +300,7 @@ k_preprocess(SceneView scene, const ViewParams* __restrict__ views_g, int V, Spl
     }
     // colour for the views that kept this Gaussian
     if (vis_mask) {
-        float c[48];
+        ShCoefs<STORAGE> c;
         load_sh<STORAGE>(scene.chunks, i, scene.sh_degree, c);
         uint64_t m = vis_mask;
         while (m) {
