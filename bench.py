@@ -390,6 +390,30 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
                     "ms_per_launch_set": round(bms, 3), "frames_per_s": round(Vb / bms * 1e3, 1),
                     "megapixels_per_s": round(sum(w * h for w, h in lv) / bms * 1e-3, 1)}
 
+    # ---- the paper's default colour model: SH degree 0 (same scene, DC terms only)
+    sh0 = None
+    if not args.no_serving:
+        import dataclasses
+        h0 = tg.scene_from(dataclasses.replace(scene, sh_degree=0), storage=tg.STORAGE_FP16)
+        try:
+            def step0(s):
+                tg.render_batch(h0, [trajs[v][(s * 7 + v) % len(trajs[v])] for v in range(V)], [K] * V, [W] * V,
+                                [H] * V, outs, stream=stream)
+            for s in range(4):
+                step0(s)
+            torch.cuda.synchronize()
+            z0, z1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            n0 = max(5, args.steps // 2)
+            z0.record(stream)
+            for s in range(n0):
+                step0(4 + s)
+            z1.record(stream)
+            torch.cuda.synchronize()
+            sh0 = {"frames_per_s": round(V * n0 / (z0.elapsed_time(z1) * 1e-3), 2), "sh_degree": 0,
+                   "note": "same scene and views, colour from the degree-0 term only (the paper's default)"}
+        finally:
+            h0.free()
+
     # ---- served FP16: request server, closed-loop clients
     serving = None
     if not args.no_serving:
@@ -400,7 +424,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
 
     res = {"schedule": schedule, "rerenders": rerenders, "concurrent": concurrent, "value": value, "elapsed_ms": elapsed_ms, "frames": frames, "per_step": per_step, "stage_ms": stage_ms,
            "clocks": clocks, "launches": launches, "e2e": e2e, "plain_fp32": plain, "serving": serving, "trace": trace,
-           "batching": batching,
+           "batching": batching, "sh0": sh0,
            "step_ms_host": step_ms_host, "scene": scene}
     h16.free()
     h32.free()
@@ -635,7 +659,7 @@ def main(argv=None) -> int:
                                                   "pixels all stopped are dropped", autotuned=not (args.no_autotune or args.schedule),
                              exact_rerenders_timed=r["rerenders"]),
             "served_fp16": r["serving"], "plain_fp32": r["plain_fp32"], "serving_trace": r["trace"],
-            "batching_32_mixed": r["batching"], "in_flight": r["concurrent"],
+            "batching_32_mixed": r["batching"], "in_flight": r["concurrent"], "sh_degree_0": r["sh0"],
             "roofline": roof, "stages": stages, "per_step": {k: int(v) for k, v in r["per_step"].items()},
             "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": int(r["launches"]), "clocks": r["clocks"],
         }

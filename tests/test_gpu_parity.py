@@ -369,6 +369,53 @@ def test_server_latest_pose_wins(cuda, h1):
     assert sum(s == tg.tigas.ERR_AGAIN for s in got.values()) >= 1
 
 
+def test_server_admission_budget_serialises_launch_sets(cuda, h1):
+    # a budget below any launch set's workspace admits one request at a time, and
+    # only while nothing else is in flight (a lone request is always admitted)
+    K = synth.default_intrinsics(160, 120)
+    tr = synth.trajectory(23, 8)
+    with tg.Server(hbm_budget_bytes=1, max_batch=4, max_inflight=2) as srv:
+        bufs = {}
+        for i, p in enumerate(tr):
+            b = torch.zeros((120, 160, 4), dtype=torch.uint8, device=cuda)
+            bufs[srv.submit(h1, p, K, 160, 120, b, client_id=i)] = (b, p)
+        done = []
+        while len(done) < len(tr):
+            done += srv.poll(16, timeout_us=2_000_000)
+    assert all(c.status == 0 for c in done)
+    spans = sorted((c.admit_us, c.done_us) for c in done)
+    assert len(set(spans)) == len(spans)   # one request per launch set
+    for (a0, d0), (a1, d1) in zip(spans, spans[1:]):
+        assert a1 >= d0                      # no two in flight
+    for c in done:
+        b, p = bufs[c.ticket]
+        assert np.array_equal(b.cpu().numpy(), tg.render(h1, p, K, 160, 120))
+
+
+def test_server_keeps_a_freed_scene_until_its_requests_finish(cuda, s1):
+    K = synth.default_intrinsics(160, 120)
+    tr = synth.trajectory(29, 6)
+    ref_scene = tg.scene_from(s1)
+    try:
+        refs = [tg.render(ref_scene, p, K, 160, 120) for p in tr]
+        with tg.Server(max_batch=2, max_inflight=1) as srv:
+            h = tg.scene_from(s1)
+            bufs = {}
+            for i, p in enumerate(tr):
+                b = torch.zeros((120, 160, 4), dtype=torch.uint8, device=cuda)
+                bufs[srv.submit(h, p, K, 160, 120, b, client_id=i)] = (b, i)
+            h.free()   # the caller's reference goes; queued requests hold theirs
+            done = []
+            while len(done) < len(tr):
+                done += srv.poll(16, timeout_us=2_000_000)
+        assert all(c.status == 0 for c in done)
+        for c in done:
+            b, i = bufs[c.ticket]
+            assert np.array_equal(b.cpu().numpy(), refs[i])
+    finally:
+        ref_scene.free()
+
+
 # ------------------------------------------------------- full-size sampled
 
 
