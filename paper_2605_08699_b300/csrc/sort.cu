@@ -386,9 +386,17 @@ constexpr uint32_t kSortTimeoutFlag = 16u;
 // per SM.
 template <typename K, bool PAY>
 struct OsCfg;
+#ifndef TIGAS_OS_THREADS
+#define TIGAS_OS_THREADS 512
+#endif
+#ifndef TIGAS_OS_ITEMS
+#define TIGAS_OS_ITEMS 16
+#endif
 template <bool PAY>
 struct OsCfg<uint32_t, PAY> {
-    static constexpr int kT = 512, kI = PAY ? 8 : 16, kMinBlocks = 2;   // two CTAs per SM: <= 64 registers
+    // 2 CTAs of 512 threads per SM (<= 64 registers); keys per thread halved with a payload
+    static constexpr int kT = PAY ? 512 : TIGAS_OS_THREADS, kI = PAY ? 8 : TIGAS_OS_ITEMS;
+    static constexpr int kMinBlocks = (2 * 512) / kT;
 };
 template <bool PAY>
 struct OsCfg<uint64_t, PAY> {
@@ -786,6 +794,7 @@ Status radix_sort_onesweep(const K* keys_in, const uint32_t* values_in, K* keys_
                            K* keys_out, uint32_t* values_out, uint64_t n_cap, const uint64_t* d_n, int begin_bit,
                            int end_bit, uint32_t* tmp, cudaStream_t st, uint32_t* flags, const SortExtras* ex) {
     constexpr int T = OsCfg<K, PAY>::kT, N = OsCfg<K, PAY>::kT * OsCfg<K, PAY>::kI;
+    static_assert(N >= 4096, "the status table (os_chunks) assumes chunks of at least 4096 keys");
     const int passes = (end_bit - begin_bit + 7) / 8;
     TIGAS_TRY((ensure_os_smem<K, PAY, MAP>()));
     uint32_t* ghist = tmp;
