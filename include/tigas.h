@@ -322,6 +322,27 @@ tigas_status tigas_autotune(tigas_scene* scene, int n_sets, int n_views, const t
                             const tigas_intrinsics* intrs, const int* widths, const int* heights,
                             uint8_t* const* outs_rgba8, int iters, tigas_schedule* best, double* best_ms);
 
+/* ---------------------------------------------------------- frame encoder */
+
+/* Baseline JPEG (ITU-T T.81 sequential DCT, Huffman) of one RGBA8 frame in a
+ * JFIF file: the payload the backend returns for a pose request (Sec. 4.1,
+ * 5.1; Table 1 lists the quality levels 10, 35, 65 and 90).  Alpha is
+ * ignored.
+ *  Encoding: JFIF YCbCr with 16-bit fixed-point weights, 4:2:0 chroma (the
+ *  rounded mean of each 2x2 group; the image extended to whole 16x16 MCUs by
+ *  repeating its last column/row), the T.81 FDCT with 13-bit fixed-point
+ *  weights, Annex K quantizer tables scaled by the quality (5000/q below 50,
+ *  200 - 2q above), nearest rounding, Annex K Huffman tables, a restart
+ *  marker every restart_mcus MCUs.
+ *   rgba:         width*height*4 bytes, host or device
+ *   quality:      1..100;  restart_mcus: 1..65535 (intervals are encoded in
+ *                 parallel: small intervals encode faster, each adds 2 bytes)
+ *   out:          host or device buffer of out_capacity bytes
+ *   *out_len:     the file length (also when it exceeds out_capacity)
+ * Synchronous.  Errors: INVALID, OVERFLOW (out_capacity < *out_len), OOM, CUDA. */
+tigas_status tigas_jpeg_encode(const uint8_t* rgba, int width, int height, int quality, int restart_mcus,
+                               uint8_t* out, uint64_t out_capacity, uint64_t* out_len, void* cuda_stream);
+
 /* Launch sets that ran with a fixed pair capacity (graph replay or a shape's
  * first launch set), outgrew it and were rendered again exactly, since load. */
 uint64_t tigas_exact_rerenders(void);

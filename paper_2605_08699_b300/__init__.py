@@ -6,14 +6,14 @@ controller (``abr.py``) and the build script (``build.py``).
 """
 from .tigas import (ERR_AGAIN, ERR_CUDA, ERR_INVALID, ERR_NOT_FOUND, ERR_OOM, ERR_OVERFLOW, ERR_TIMEOUT, OK,
                     SORT_DEPTH_FIRST, SORT_FULL64, SORT_SLICED, STAGES, STORAGE_FP16, STORAGE_FP32, SceneHandle,
-                    Server, TigasError, autotune, debug_render, debug_sort_wait_timeout, exact_rerenders, get_schedule,
+                    Server, TigasError, autotune, debug_render, debug_sort_wait_timeout, exact_rerenders, get_schedule, jpeg_encode,
                     kernel_launches, last_error, load_library, make_intrinsics, make_pose, profile_enable,
                     profile_read, render, render_batch, render_ex, scene_from, scene_load, set_graphs, set_schedule,
                     sort_pairs_u64, version)
 
 __all__ = ["ERR_AGAIN", "ERR_CUDA", "ERR_INVALID", "ERR_NOT_FOUND", "ERR_OOM", "ERR_OVERFLOW", "ERR_TIMEOUT", "OK",
            "SORT_DEPTH_FIRST", "SORT_FULL64", "SORT_SLICED", "STAGES", "STORAGE_FP16", "STORAGE_FP32", "SceneHandle",
-           "Server", "TigasError", "autotune", "debug_render", "debug_sort_wait_timeout", "exact_rerenders", "get_schedule",
+           "Server", "TigasError", "autotune", "debug_render", "debug_sort_wait_timeout", "exact_rerenders", "get_schedule", "jpeg_encode",
            "kernel_launches", "last_error", "load_library", "make_intrinsics", "make_pose", "profile_enable",
            "profile_read", "render", "render_batch", "render_ex", "scene_from", "scene_load", "set_graphs",
            "set_schedule", "sort_pairs_u64", "version"]

@@ -353,6 +353,18 @@ TIGAS_API tigas_status tigas_autotune(tigas_scene* scene, int n_sets, int n_view
 
 TIGAS_API uint64_t tigas_exact_rerenders(void) { return g_exact_rerenders.load(); }
 
+TIGAS_API tigas_status tigas_jpeg_encode(const uint8_t* rgba, int width, int height, int quality, int restart_mcus,
+                                         uint8_t* out, uint64_t out_capacity, uint64_t* out_len, void* cuda_stream) {
+    if (!rgba || !out || !out_len) return fail(TIGAS_ERR_INVALID, "null argument");
+    Status err;
+    ContextGuard g;
+    g.ctx = acquire_context(&err);
+    if (!g.ctx) return fail(err);
+    cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : g.ctx->stream;
+    Status s = jpeg_encode(*g.ctx, rgba, width, height, quality, restart_mcus, out, out_capacity, out_len, st);
+    return s.ok() ? TIGAS_OK : fail(s);
+}
+
 TIGAS_API tigas_status tigas_debug_sort_wait_timeout(int spin_limit) {
     bool timed_out = false;
     Status s = debug_lookback_timeout(spin_limit, &timed_out);

@@ -174,6 +174,7 @@ void RenderContext::destroy() {
     drop_graphs(*this);
     fixed.release();
     pairs.release();
+    jpeg.release();
     for (auto* p : dev_staging)
         if (p) cudaFree(p);
     dev_staging.clear();

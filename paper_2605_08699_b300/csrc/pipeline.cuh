@@ -77,6 +77,7 @@ struct RenderContext {
     cudaStream_t stream = nullptr;     // own stream (used when the caller passes none)
     Arena fixed;                       // per-entry buffers
     Arena pairs;                       // per-pair buffers
+    Arena jpeg;                        // frame encoder buffers
     uint64_t* h_total = nullptr;       // pinned readback of P
     uint32_t* h_flags = nullptr;       // pinned readback of overflow flags
     ViewParams* h_views = nullptr;     // pinned view table
@@ -160,5 +161,8 @@ RenderContext* acquire_context(Status* err);
 void release_context(RenderContext* ctx);
 
 bool is_device_pointer(const void* p);
+// Baseline JPEG of one RGBA8 frame (host or device in/out), synchronous on st.
+Status jpeg_encode(RenderContext& ctx, const uint8_t* rgba, int W, int H, int quality, int restart, uint8_t* out,
+                   uint64_t cap, uint64_t* out_len, cudaStream_t st);
 
 }  // namespace tigas

@@ -28,7 +28,8 @@ EXPORTS = ["tigas_scene_load", "tigas_scene_free", "tigas_scene_bytes", "tigas_r
            "tigas_version", "tigas_kernel_launches", "tigas_profile_enable", "tigas_profile_read",
            "tigas_sort_pairs_u64_noalloc",
            "tigas_render_batch_ex", "tigas_set_graphs", "tigas_debug_sort_wait_timeout",
-           "tigas_set_schedule", "tigas_get_schedule", "tigas_autotune", "tigas_exact_rerenders"]
+           "tigas_set_schedule", "tigas_get_schedule", "tigas_autotune", "tigas_exact_rerenders",
+           "tigas_jpeg_encode"]
 
 STAGES = ["preprocess", "depth_sort", "scan", "emit", "pair_sort", "ranges", "blend", "frame"]
 
@@ -127,6 +128,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "tigas_set_schedule": (st, [ctypes.POINTER(Schedule)]),
         "tigas_get_schedule": (st, [ctypes.POINTER(Schedule)]),
         "tigas_exact_rerenders": (ctypes.c_uint64, []),
+        "tigas_jpeg_encode": (st, [P, i, i, i, i, P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), P]),
         "tigas_autotune": (st, [P, i, i, ctypes.POINTER(Pose), ctypes.POINTER(Intrinsics), ctypes.POINTER(ctypes.c_int),
                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_void_p), i,
                                 ctypes.POINTER(Schedule), ctypes.POINTER(ctypes.c_double)]),
@@ -341,6 +343,23 @@ def get_schedule() -> dict:
     s = Schedule()
     _check(load_library().tigas_get_schedule(ctypes.byref(s)))
     return s.as_dict()
+
+
+def jpeg_encode(rgba, quality: int, restart_mcus: int = 2, out=None, stream=None) -> bytes | int:
+    """tigas_jpeg_encode of an [H, W, 4] uint8 frame (host array or device
+    tensor).  Without ``out`` returns the file as bytes; with a caller buffer
+    (host or device) returns the file length."""
+    H, W = int(rgba.shape[0]), int(rgba.shape[1])
+    n = ctypes.c_uint64()
+    if out is None:
+        buf = np.zeros(1024 + H * W * 4, np.uint8)
+        _check(load_library().tigas_jpeg_encode(_ptr(rgba), W, H, quality, restart_mcus, _ptr(buf), buf.nbytes,
+                                                ctypes.byref(n), _stream(stream)))
+        return buf[:n.value].tobytes()
+    cap = out.nbytes if hasattr(out, "nbytes") else out.numel() * out.element_size()
+    _check(load_library().tigas_jpeg_encode(_ptr(rgba), W, H, quality, restart_mcus, _ptr(out), cap, ctypes.byref(n),
+                                            _stream(stream)))
+    return int(n.value)
 
 
 def exact_rerenders() -> int:
