@@ -390,6 +390,29 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
                     "ms_per_launch_set": round(bms, 3), "frames_per_s": round(Vb / bms * 1e3, 1),
                     "megapixels_per_s": round(sum(w * h for w, h in lv) / bms * 1e-3, 1)}
 
+    # ---- frame encoder after the blend: JPEG of the step's frames (device in, device out)
+    jpeg = None
+    if not args.no_serving:
+        jbuf = torch.empty(8 << 20, dtype=torch.uint8, device=dev)
+        for q in (90, 65):
+            sizes = []
+            for o in outs[:2]:
+                tg.jpeg_encode(o, q, restart_mcus=2, out=jbuf, stream=stream)
+            torch.cuda.synchronize()
+            j0, j1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            j0.record(stream)
+            for o in outs:
+                sizes.append(tg.jpeg_encode(o, q, restart_mcus=2, out=jbuf, stream=stream))
+            j1.record(stream)
+            torch.cuda.synchronize()
+            jms = j0.elapsed_time(j1) / len(outs)
+            key = f"quality_{q}"
+            jpeg = jpeg or {"resolution": f"{W}x{H}", "restart_mcus": 2,
+                            "note": "tigas_jpeg_encode of each rendered frame, device buffers, synchronous calls"}
+            jpeg[key] = {"ms_per_frame": round(jms, 4), "frames_per_s": round(1e3 / jms, 1),
+                         "kbytes_mean": round(float(np.mean(sizes)) / 1024, 1),
+                         "input_gbs": round(W * H * 4 / (jms * 1e-3) / 1e9, 1)}
+
     # ---- the paper's default colour model: SH degree 0 (same scene, DC terms only)
     sh0 = None
     if not args.no_serving:
@@ -424,7 +447,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
 
     res = {"schedule": schedule, "rerenders": rerenders, "concurrent": concurrent, "value": value, "elapsed_ms": elapsed_ms, "frames": frames, "per_step": per_step, "stage_ms": stage_ms,
            "clocks": clocks, "launches": launches, "e2e": e2e, "plain_fp32": plain, "serving": serving, "trace": trace,
-           "batching": batching, "sh0": sh0,
+           "batching": batching, "sh0": sh0, "jpeg": jpeg,
            "step_ms_host": step_ms_host, "scene": scene}
     h16.free()
     h32.free()
@@ -660,6 +683,7 @@ def main(argv=None) -> int:
                              exact_rerenders_timed=r["rerenders"]),
             "served_fp16": r["serving"], "plain_fp32": r["plain_fp32"], "serving_trace": r["trace"],
             "batching_32_mixed": r["batching"], "in_flight": r["concurrent"], "sh_degree_0": r["sh0"],
+            "jpeg_encode": r["jpeg"],
             "roofline": roof, "stages": stages, "per_step": {k: int(v) for k, v in r["per_step"].items()},
             "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": int(r["launches"]), "clocks": r["clocks"],
         }
