@@ -41,7 +41,8 @@ typedef enum {
     TIGAS_ERR_AGAIN = 4,     /* server: admission full, or request superseded */
     TIGAS_ERR_OVERFLOW = 5,  /* pair count exceeded the fixed pair budget */
     TIGAS_ERR_TIMEOUT = 6,   /* a bounded wait ran out */
-    TIGAS_ERR_NOT_FOUND = 7  /* unknown ticket */
+    TIGAS_ERR_NOT_FOUND = 7, /* unknown ticket or model identifier */
+    TIGAS_ERR_IO = 8         /* a file or folder could not be opened or read */
 } tigas_status;
 
 /* Client pose (Sec. 5.1 "Rendering Engine", Sec. 5.2 request body):
@@ -342,6 +343,140 @@ tigas_status tigas_autotune(tigas_scene* scene, int n_sets, int n_views, const t
  * Synchronous.  Errors: INVALID, OVERFLOW (out_capacity < *out_len), OOM, CUDA. */
 tigas_status tigas_jpeg_encode(const uint8_t* rgba, int width, int height, int quality, int restart_mcus,
                                uint8_t* out, uint64_t out_capacity, uint64_t* out_len, void* cuda_stream);
+
+/* ---------------------------------------------------------------- models
+ * 3DGS PLY files (Sec. 4.1 and Sec. 5.1 "PLY Model and Primitives").  One
+ * vertex per Gaussian with the properties x y z, f_dc_0..2, f_rest_0..(3M-1),
+ * opacity, scale_0..2, rot_0..3 in any order (other properties such as
+ * nx ny nz are ignored), in binary_little_endian, binary_big_endian or ascii
+ * format, each of type char/uchar/short/ushort/int/uint/float/double.  The SH
+ * degree d follows from the f_rest count 3M, M = (d+1)^2 - 1 in {0, 3, 8, 15};
+ * f_rest is channel-major: f_rest_{c*M + j} is coefficient j + 1 of colour
+ * channel c, f_dc_c coefficient 0.  rot_0 is the quaternion's real part.
+ * Values are converted to float32 (round to nearest).  Elements other than
+ * "vertex" are skipped (in binary files, those before it may not hold lists). */
+typedef struct {
+    uint64_t n;             /* vertex count, 1 .. 2^27 */
+    uint64_t file_bytes;
+    uint64_t body_offset;   /* byte offset of the vertex block (binary) */
+    int sh_degree;          /* 0..3 */
+    int format;             /* 0 binary little endian, 1 binary big endian, 2 ascii */
+    uint32_t row_bytes;     /* bytes per binary vertex record */
+    uint32_t n_properties;  /* vertex properties in the file */
+} tigas_ply_info;
+
+/* Parse a PLY header (and check that a binary body is complete) without
+ * reading vertices.  Host only: needs no GPU.  Errors: INVALID (null, bad or
+ * unsupported header, missing property, f_rest count not 0/9/24/45,
+ * truncated), IO (cannot open). */
+tigas_status tigas_ply_probe(const char* path, tigas_ply_info* out);
+
+/* Decode a PLY's vertices into the raw attribute arrays of tigas_scene_desc
+ * (means[n][3], log_scales[n][3], quats[n][4], opacity_logits[n],
+ * sh[n][16][3], coefficients past the file's degree set to 0), n from
+ * tigas_ply_probe.  The body is streamed into device memory and de-interleaved
+ * by a kernel; with outputs_on_device = 0 the arrays are host memory and the
+ * result is copied back.  Synchronous.  Errors: as tigas_ply_probe, OOM, CUDA. */
+tigas_status tigas_ply_decode(const char* path, float* means, float* log_scales, float* quats,
+                              float* opacity_logits, float* sh, int outputs_on_device);
+
+/* tigas_ply_probe + decode + tigas_scene_load in one call, with the file's SH
+ * degree; the raw arrays never leave the device. */
+tigas_status tigas_scene_load_ply(const char* path, int storage, const float background[3],
+                                  tigas_scene** out_scene);
+
+/* Model registry (Sec. 4.1; Sec. 5.1 "Dynamic Multi-Model Runtime").  Models
+ * in root_dir are (a) each sub-folder holding a PLY -- the highest
+ * point_cloud/iteration_<k>/point_cloud.ply, else its first *.ply by name --
+ * with identifier and name = the folder name and preview = preview.png|.jpg|
+ * .jpeg in it; (b) each top-level <id>.ply without a same-named folder, with
+ * preview <id>.png|.jpg|.jpeg beside it.  Files whose header does not parse
+ * are skipped.  A model is loaded into HBM on its first acquire and shared
+ * by all later acquires; the registry holds one reference while it is
+ * loaded.  An eviction pass unloads every model with no outstanding acquire
+ * that has been idle for idle_timeout_s seconds.  With resident_budget_bytes
+ * > 0 a load first evicts idle models (least recently used first) until it
+ * fits, else fails with OOM.  All registry calls are thread-safe. */
+typedef struct tigas_registry tigas_registry;
+
+typedef struct {
+    char id[128];            /* truncated to 127 bytes */
+    char name[128];
+    char ply_path[1024];
+    char preview_path[1024]; /* "" when the model has no preview image */
+    uint64_t n;              /* Gaussians (from the header until loaded) */
+    uint64_t file_bytes;
+    uint64_t resident_bytes; /* 0 when not loaded */
+    uint64_t loads;          /* times loaded since the registry opened */
+    double idle_seconds;     /* loaded with no acquire outstanding: time since last use, else 0 */
+    int sh_degree;
+    int loaded;
+    int users;               /* acquires not yet released */
+    int reserved;
+} tigas_model_info;
+
+/* Open a registry over root_dir and scan it.  storage: TIGAS_STORAGE_*;
+ * idle_timeout_s >= 0; background: as in tigas_scene_desc.  Host only until
+ * the first acquire.  Errors: INVALID, IO (root_dir is not a readable folder). */
+tigas_status tigas_registry_open(const char* root_dir, int storage, double idle_timeout_s,
+                                 uint64_t resident_budget_bytes, const float background[3],
+                                 tigas_registry** out);
+/* Rescan root_dir: new models are added; known ones keep their state; ones
+ * whose files are gone are dropped once unloaded.  Outputs may be NULL. */
+tigas_status tigas_registry_scan(tigas_registry* reg, int* n_models, int* n_skipped);
+tigas_status tigas_registry_count(tigas_registry* reg, int* n_models);
+/* Metadata and state of model index (0 .. count-1, ordered by identifier). */
+tigas_status tigas_registry_info(tigas_registry* reg, int index, tigas_model_info* out);
+/* The model's resident scene, loading it first if needed (Synchronous; other
+ * models stay usable meanwhile; concurrent acquires of a model being loaded
+ * wait for that load).  *out_scene is a new reference: hand it back with
+ * tigas_registry_release (it may be submitted to a server meanwhile).
+ * Errors: NOT_FOUND (unknown identifier), OOM (budget or device), IO,
+ * INVALID (bad file), CUDA. */
+tigas_status tigas_registry_acquire(tigas_registry* reg, const char* model_id, tigas_scene** out_scene);
+/* Return an acquired scene.  INVALID if it was not acquired from reg or was
+ * already returned. */
+tigas_status tigas_registry_release(tigas_registry* reg, tigas_scene* scene);
+/* One eviction pass at the registry's current time; *n_evicted may be NULL. */
+tigas_status tigas_registry_evict_idle(tigas_registry* reg, int* n_evicted);
+/* Run the eviction pass every period_s seconds (> 0) on a background thread
+ * until tigas_registry_close. */
+tigas_status tigas_registry_start_eviction(tigas_registry* reg, double period_s);
+/* Test clock: now_s >= 0 fixes the registry's time in seconds; negative
+ * returns to the monotonic clock. */
+tigas_status tigas_registry_set_clock(tigas_registry* reg, double now_s);
+/* Stop the eviction thread, wait for loads in progress, drop the registry's
+ * references and free reg.  Scenes still acquired stay valid until each is
+ * freed with tigas_scene_free. */
+tigas_status tigas_registry_close(tigas_registry* reg);
+
+/* ------------------------------------------------------ quality metrics
+ * Post-session evaluation (Sec. 5.3 "Sampled OPFS Capture and Post-Session
+ * Materialization"; the PSNR and SSIM of Sec. 6).  Frames are RGBA8,
+ * row-major, host or device memory (detected per pointer). */
+
+/* Bilinear resample src (w x h) to dst (width x height), all four channels.
+ * Source coordinate of output pixel d: s = (d + 0.5) * w / width - 0.5, taken
+ * in 16.16 fixed point (floor), clamped to [0, w-1]; weights are the top 8
+ * fraction bits; each channel is ((a(256-fx) + b fx)(256-fy) + (c(256-fx) +
+ * d fx) fy + 2^15) >> 16, so the result is exact integer arithmetic.  Sizes
+ * 1..8192.  Synchronous.  Errors: INVALID, OOM, CUDA. */
+tigas_status tigas_resample_rgba8(const uint8_t* src, int w, int h, uint8_t* dst, int width, int height,
+                                  void* cuda_stream);
+
+/* SSIM (Wang et al., IEEE TIP 2004) and PSNR between frames a and b of
+ * width x height (11..8192 each; alpha ignored).  SSIM: per R, G, B channel,
+ * 11 x 11 Gaussian window with sigma 1.5 normalised to sum 1, C1 = (0.01 *
+ * 255)^2, C2 = (0.03 * 255)^2, at every window position inside the frame;
+ * *out_ssim is the mean over positions and channels.  Computed in FP32 with
+ * centred samples: within 1e-3 of the exact value per window and 1e-5 on
+ * the mean.  out_map (optional, host or device): [height-10][width-10] floats,
+ * the per-position SSIM averaged over channels.  *out_psnr = 10 log10(255^2 /
+ * MSE) over all pixels and the three channels (exact squared-error sum;
+ * +inf when the frames are equal).  Outputs may be NULL.  Synchronous.
+ * Errors: INVALID, OOM, CUDA. */
+tigas_status tigas_image_quality(const uint8_t* a, const uint8_t* b, int width, int height, float* out_map,
+                                 double* out_ssim, double* out_psnr, void* cuda_stream);
 
 /* Launch sets that ran with a fixed pair capacity (graph replay or a shape's
  * first launch set), outgrew it and were rendered again exactly, since load. */

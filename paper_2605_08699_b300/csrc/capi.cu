@@ -365,6 +365,28 @@ TIGAS_API tigas_status tigas_jpeg_encode(const uint8_t* rgba, int width, int hei
     return s.ok() ? TIGAS_OK : fail(s);
 }
 
+TIGAS_API tigas_status tigas_resample_rgba8(const uint8_t* src, int w, int h, uint8_t* dst, int width, int height,
+                                            void* cuda_stream) {
+    Status err;
+    ContextGuard g;
+    g.ctx = acquire_context(&err);
+    if (!g.ctx) return fail(err);
+    cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : g.ctx->stream;
+    Status s = resample_rgba8(*g.ctx, src, w, h, dst, width, height, st);
+    return s.ok() ? TIGAS_OK : fail(s);
+}
+
+TIGAS_API tigas_status tigas_image_quality(const uint8_t* a, const uint8_t* b, int width, int height, float* out_map,
+                                           double* out_ssim, double* out_psnr, void* cuda_stream) {
+    Status err;
+    ContextGuard g;
+    g.ctx = acquire_context(&err);
+    if (!g.ctx) return fail(err);
+    cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : g.ctx->stream;
+    Status s = image_quality(*g.ctx, a, b, width, height, out_map, out_ssim, out_psnr, st);
+    return s.ok() ? TIGAS_OK : fail(s);
+}
+
 TIGAS_API tigas_status tigas_debug_sort_wait_timeout(int spin_limit) {
     bool timed_out = false;
     Status s = debug_lookback_timeout(spin_limit, &timed_out);
@@ -399,36 +421,15 @@ TIGAS_API tigas_status tigas_scene_load(const tigas_scene_desc* d, tigas_scene**
     for (int c = 0; c < 3; ++c)
         if (!std::isfinite(d->background[c])) return fail(TIGAS_ERR_INVALID, "non-finite background");
     const uint32_t n = (uint32_t)d->n;
-    const int C = d->storage == TIGAS_STORAGE_FP32 ? kChunksF32 : kChunksF16;
-    const size_t chunk_count = (size_t)((n + 31) / 32) * 32 * C;
-    auto* s = new Scene();
-    s->view.n = n;
-    s->view.sh_degree = d->sh_degree;
-    s->view.storage = d->storage;
-    for (int c = 0; c < 3; ++c) s->view.bg[c] = d->background[c];
-    s->bytes = chunk_count * 16;
-    cudaError_t e = cudaMalloc(&s->chunks, s->bytes);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        delete s;
-        return fail(TIGAS_ERR_OOM, "scene allocation failed");
-    }
-    s->view.chunks = s->chunks;
     const float *m = d->means, *ls = d->log_scales, *q = d->quats, *op = d->opacity_logits, *sh = d->sh;
     float* staging_buf = nullptr;
     auto finish = [&](const Status& st) -> tigas_status {
         if (staging_buf) cudaFree(staging_buf);
-        if (!st.ok()) {
-            cudaFree(s->chunks);
-            delete s;
-            return fail(st);
-        }
-        *out = reinterpret_cast<tigas_scene*>(s);
-        return TIGAS_OK;
+        return st.ok() ? TIGAS_OK : fail(st);
     };
     if (!d->inputs_on_device) {
         const size_t words = (size_t)n * (3 + 3 + 4 + 1 + 48);
-        e = cudaMalloc(&staging_buf, words * 4);
+        cudaError_t e = cudaMalloc(&staging_buf, words * 4);
         if (e != cudaSuccess) {
             cudaGetLastError();
             staging_buf = nullptr;
@@ -445,11 +446,9 @@ TIGAS_API tigas_status tigas_scene_load(const tigas_scene_desc* d, tigas_scene**
             p += len[k];
         }
     }
-    Status st = launch_scene_pack(m, ls, q, op, sh, n, d->sh_degree, d->storage, s->chunks, 0);
-    if (st.ok()) {
-        e = cudaDeviceSynchronize();
-        if (e != cudaSuccess) st = {TIGAS_ERR_CUDA, cudaGetErrorString(e)};
-    }
+    Scene* s = nullptr;
+    Status st = scene_create(m, ls, q, op, sh, n, d->sh_degree, d->storage, d->background, 0, &s);
+    if (st.ok()) *out = reinterpret_cast<tigas_scene*>(s);
     return finish(st);
 }
 

@@ -19,6 +19,57 @@ struct Scene {
 void scene_acquire(Scene* s);
 void scene_release(Scene* s);
 
+// Resident bytes of a scene of n Gaussians in the given storage.
+size_t scene_bytes_for(uint64_t n, int storage);
+// New scene (one reference) from raw attribute arrays in device memory:
+// activate and pack on st, then synchronize st.
+Status scene_create(const float* means, const float* log_scales, const float* quats, const float* logits,
+                    const float* sh, uint32_t n, int sh_degree, int storage, const float bg[3], cudaStream_t st,
+                    Scene** out);
+
+// ------------------------------------------------------------ PLY models
+// A 3DGS vertex record maps to 59 raw fields in scene-description order:
+// x y z | scale_0..2 | rot_0..3 | opacity | SH coefficient k, channel c at
+// 11 + 3k + c (f_dc_c is k = 0; f_rest_{c*M+j} is k = j + 1, M = (d+1)^2 - 1).
+constexpr int kPlyFields = 59;
+enum PlyType : uint8_t { kPlyI8, kPlyU8, kPlyI16, kPlyU16, kPlyI32, kPlyU32, kPlyF32, kPlyF64, kPlyAbsent = 0xFF };
+enum PlyFormat { kPlyBinaryLE = 0, kPlyBinaryBE = 1, kPlyAscii = 2 };
+
+struct PlyLayout {
+    uint64_t n = 0;                  // vertex count
+    uint64_t body_offset = 0;        // byte offset of the vertex block (binary) or of the data (ascii)
+    uint64_t skip_lines = 0;         // ascii: lines of elements that precede the vertex element
+    uint64_t file_bytes = 0;
+    int format = kPlyBinaryLE;
+    int sh_degree = 0;               // from the count of f_rest_* properties (0, 9, 24, 45)
+    uint32_t row_bytes = 0;          // bytes of one binary vertex record
+    std::vector<uint8_t> prop_type;  // vertex properties in file order
+    std::vector<uint32_t> prop_offset;
+    int32_t field_prop[kPlyFields];  // vertex property feeding each field, -1 = absent (zero)
+};
+
+// Parse the header of a 3DGS PLY file (no body read beyond a size check).
+Status ply_probe(const char* path, PlyLayout* out);
+// Decode the vertex block into raw attribute arrays in device memory
+// (means[n][3], log_scales[n][3], quats[n][4], logits[n], sh[n][48]); synchronizes st.
+Status ply_decode(const char* path, const PlyLayout& lay, float* means, float* log_scales, float* quats,
+                  float* logits, float* sh, cudaStream_t st);
+// probe + decode + scene_create.
+Status scene_load_ply(const char* path, int storage, const float bg[3], Scene** out);
+
+// ------------------------------------------------------- quality metrics
+// Bilinear RGBA8 resample (w x h -> W x H), exact fixed-point arithmetic.
+Status launch_resample(const uint8_t* src, int w, int h, uint8_t* dst, int W, int H, cudaStream_t st);
+// Device scratch for launch_quality; its first two words receive the SSIM sum
+// over window positions and channels (double) and the squared error (u64).
+size_t quality_tmp_bytes(int W, int H);
+Status launch_quality(const uint8_t* a, const uint8_t* b, int W, int H, void* tmp, float* map, cudaStream_t st);
+struct RenderContext;
+Status resample_rgba8(RenderContext& ctx, const uint8_t* src, int w, int h, uint8_t* dst, int W, int H,
+                      cudaStream_t st);
+Status image_quality(RenderContext& ctx, const uint8_t* a, const uint8_t* b, int W, int H, float* map,
+                     double* ssim, double* psnr, cudaStream_t st);
+
 // Grow-only device buffer handed out in 256-byte aligned slices.
 struct Arena {
     char* base = nullptr;

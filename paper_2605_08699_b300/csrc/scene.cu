@@ -2,7 +2,7 @@
 // load (Sec. 5.1, "PLY Model and Primitives": scale = exp(s), opacity =
 // sigmoid(logit), unit quaternion) and packed into the resident AoSoA32
 // layout, in FP32 or in FP16 (positions stay FP32).
-#include "kernels.cuh"
+#include "pipeline.cuh"
 
 namespace tigas {
 
@@ -69,6 +69,42 @@ Status launch_scene_pack(const float* means, const float* log_scales, const floa
         k_scene_pack<TIGAS_STORAGE_FP16><<<grid, 256, 0, st>>>(means, log_scales, quats, opacity_logits, sh, n,
                                                                sh_degree, chunks);
     TIGAS_LAUNCHED();
+    return {};
+}
+
+size_t scene_bytes_for(uint64_t n, int storage) {
+    const int C = storage == TIGAS_STORAGE_FP32 ? kChunksF32 : kChunksF16;
+    return (size_t)((n + 31) / 32) * 32 * C * 16;
+}
+
+Status scene_create(const float* means, const float* log_scales, const float* quats, const float* logits,
+                    const float* sh, uint32_t n, int sh_degree, int storage, const float bg[3], cudaStream_t st,
+                    Scene** out) {
+    *out = nullptr;
+    auto* s = new Scene();
+    s->view.n = n;
+    s->view.sh_degree = sh_degree;
+    s->view.storage = storage;
+    for (int c = 0; c < 3; ++c) s->view.bg[c] = bg[c];
+    s->bytes = scene_bytes_for(n, storage);
+    cudaError_t e = cudaMalloc(&s->chunks, s->bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return {TIGAS_ERR_OOM, "scene allocation failed"};
+    }
+    s->view.chunks = s->chunks;
+    Status r = launch_scene_pack(means, log_scales, quats, logits, sh, n, sh_degree, storage, s->chunks, st);
+    if (r.ok()) {
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) r = {TIGAS_ERR_CUDA, cudaGetErrorString(e)};
+    }
+    if (!r.ok()) {
+        cudaFree(s->chunks);
+        delete s;
+        return r;
+    }
+    *out = s;
     return {};
 }
 

@@ -17,7 +17,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtigas.so")
 
-OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_AGAIN, ERR_OVERFLOW, ERR_TIMEOUT, ERR_NOT_FOUND = range(8)
+OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_AGAIN, ERR_OVERFLOW, ERR_TIMEOUT, ERR_NOT_FOUND, ERR_IO = range(9)
 STORAGE_FP32, STORAGE_FP16 = 0, 1
 SORT_DEPTH_FIRST, SORT_FULL64, SORT_SLICED = 0, 1, 2
 
@@ -29,7 +29,11 @@ EXPORTS = ["tigas_scene_load", "tigas_scene_free", "tigas_scene_bytes", "tigas_r
            "tigas_sort_pairs_u64_noalloc",
            "tigas_render_batch_ex", "tigas_set_graphs", "tigas_debug_sort_wait_timeout",
            "tigas_set_schedule", "tigas_get_schedule", "tigas_autotune", "tigas_exact_rerenders",
-           "tigas_jpeg_encode"]
+           "tigas_jpeg_encode", "tigas_ply_probe", "tigas_ply_decode", "tigas_scene_load_ply",
+           "tigas_registry_open", "tigas_registry_scan", "tigas_registry_count", "tigas_registry_info",
+           "tigas_registry_acquire", "tigas_registry_release", "tigas_registry_evict_idle",
+           "tigas_registry_start_eviction", "tigas_registry_set_clock", "tigas_registry_close",
+           "tigas_resample_rgba8", "tigas_image_quality"]
 
 STAGES = ["preprocess", "depth_sort", "scan", "emit", "pair_sort", "ranges", "blend", "frame"]
 
@@ -88,6 +92,20 @@ class Completion(ctypes.Structure):
                 ("admit_us", ctypes.c_double), ("done_us", ctypes.c_double)]
 
 
+class PlyInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("file_bytes", ctypes.c_uint64), ("body_offset", ctypes.c_uint64),
+                ("sh_degree", ctypes.c_int), ("format", ctypes.c_int), ("row_bytes", ctypes.c_uint32),
+                ("n_properties", ctypes.c_uint32)]
+
+
+class ModelInfo(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_char * 128), ("name", ctypes.c_char * 128), ("ply_path", ctypes.c_char * 1024),
+                ("preview_path", ctypes.c_char * 1024), ("n", ctypes.c_uint64), ("file_bytes", ctypes.c_uint64),
+                ("resident_bytes", ctypes.c_uint64), ("loads", ctypes.c_uint64), ("idle_seconds", ctypes.c_double),
+                ("sh_degree", ctypes.c_int), ("loaded", ctypes.c_int), ("users", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
+
+
 _lib = None
 
 
@@ -133,6 +151,22 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_void_p), i,
                                 ctypes.POINTER(Schedule), ctypes.POINTER(ctypes.c_double)]),
         "tigas_profile_read": (st, [P, P, i]),
+        "tigas_ply_probe": (st, [ctypes.c_char_p, ctypes.POINTER(PlyInfo)]),
+        "tigas_ply_decode": (st, [ctypes.c_char_p, P, P, P, P, P, i]),
+        "tigas_scene_load_ply": (st, [ctypes.c_char_p, i, P, ctypes.POINTER(P)]),
+        "tigas_registry_open": (st, [ctypes.c_char_p, i, ctypes.c_double, ctypes.c_uint64, P, ctypes.POINTER(P)]),
+        "tigas_registry_scan": (st, [P, ctypes.POINTER(i), ctypes.POINTER(i)]),
+        "tigas_registry_count": (st, [P, ctypes.POINTER(i)]),
+        "tigas_registry_info": (st, [P, i, ctypes.POINTER(ModelInfo)]),
+        "tigas_registry_acquire": (st, [P, ctypes.c_char_p, ctypes.POINTER(P)]),
+        "tigas_registry_release": (st, [P, P]),
+        "tigas_registry_evict_idle": (st, [P, ctypes.POINTER(i)]),
+        "tigas_registry_start_eviction": (st, [P, ctypes.c_double]),
+        "tigas_registry_set_clock": (st, [P, ctypes.c_double]),
+        "tigas_registry_close": (st, [P]),
+        "tigas_resample_rgba8": (st, [P, i, i, P, i, i, P]),
+        "tigas_image_quality": (st, [P, P, i, i, P, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -282,6 +316,164 @@ def scene_load(means, log_scales, quats, opacity_logits, sh, sh_degree: int = 3,
 def scene_from(s, storage: int = STORAGE_FP32, background=(0.0, 0.0, 0.0)) -> SceneHandle:
     """Load an object with means/log_scales/quats/opacity_logits/sh/sh_degree attributes."""
     return scene_load(s.means, s.log_scales, s.quats, s.opacity_logits, s.sh, s.sh_degree, storage, background)
+
+
+# ------------------------------------------------------------ PLY models
+
+PLY_FORMATS = ("binary_little_endian", "binary_big_endian", "ascii")
+
+
+def _path(p) -> bytes:
+    return os.fsencode(os.fspath(p))
+
+
+def ply_probe(path) -> dict:
+    """Header of a 3DGS PLY file (tigas_ply_probe; host only)."""
+    info = PlyInfo()
+    _check(load_library().tigas_ply_probe(_path(path), ctypes.byref(info)))
+    return {"n": int(info.n), "file_bytes": int(info.file_bytes), "body_offset": int(info.body_offset),
+            "sh_degree": info.sh_degree, "format": PLY_FORMATS[info.format], "row_bytes": int(info.row_bytes),
+            "n_properties": int(info.n_properties)}
+
+
+def ply_decode(path, out: dict | None = None) -> dict:
+    """Raw attribute arrays of a PLY (tigas_ply_decode).  ``out`` may hold
+    preallocated float32 arrays (all host numpy or all CUDA tensors) under the
+    keys means, log_scales, quats, opacity_logits, sh; else host arrays are made."""
+    n = ply_probe(path)["n"]
+    if out is None:
+        out = {"means": np.empty((n, 3), np.float32), "log_scales": np.empty((n, 3), np.float32),
+               "quats": np.empty((n, 4), np.float32), "opacity_logits": np.empty((n,), np.float32),
+               "sh": np.empty((n, 16, 3), np.float32)}
+    keys = ("means", "log_scales", "quats", "opacity_logits", "sh")
+    dev = [_on_device(out[k]) for k in keys]
+    if any(dev) and not all(dev):
+        raise ValueError("outputs must be all host or all device")
+    _check(load_library().tigas_ply_decode(_path(path), *[_ptr(out[k]) for k in keys], int(dev[0])))
+    return out
+
+
+def scene_load_ply(path, storage: int = STORAGE_FP32, background=(0.0, 0.0, 0.0)) -> SceneHandle:
+    """Load a 3DGS PLY straight into a resident scene (tigas_scene_load_ply)."""
+    bg = (ctypes.c_float * 3)(*background)
+    h = ctypes.c_void_p()
+    _check(load_library().tigas_scene_load_ply(_path(path), storage, ctypes.cast(bg, ctypes.c_void_p),
+                                               ctypes.byref(h)))
+    n = ply_probe(path)["n"]
+    return SceneHandle(h.value, n, storage)
+
+
+class RegistryScene(SceneHandle):
+    """A scene acquired from a Registry; free() hands it back (tigas_registry_release)."""
+
+    def __init__(self, registry: "Registry", handle: int, model_id: str, n: int, storage: int):
+        super().__init__(handle, n, storage)
+        self.registry = registry
+        self.model_id = model_id
+
+    def free(self) -> None:
+        if self.handle:
+            if self.registry.handle:
+                _check(load_library().tigas_registry_release(self.registry.handle, self.handle))
+            else:   # the registry was closed first: drop the reference directly
+                _check(load_library().tigas_scene_free(self.handle))
+            self.handle = None
+
+
+class Registry:
+    """Model registry over a folder of 3DGS models (tigas_registry_*): lazy
+    load on first acquire, shared and reference-counted while acquired,
+    unloaded after idle_timeout_s without users."""
+
+    def __init__(self, root, storage: int = STORAGE_FP16, idle_timeout_s: float = 60.0,
+                 resident_budget_bytes: int = 0, background=(0.0, 0.0, 0.0)):
+        self.storage = storage
+        bg = (ctypes.c_float * 3)(*background)
+        h = ctypes.c_void_p()
+        _check(load_library().tigas_registry_open(_path(root), storage, float(idle_timeout_s),
+                                                  int(resident_budget_bytes), ctypes.cast(bg, ctypes.c_void_p),
+                                                  ctypes.byref(h)))
+        self.handle = h.value
+
+    def scan(self) -> tuple[int, int]:
+        n, skipped = ctypes.c_int(), ctypes.c_int()
+        _check(load_library().tigas_registry_scan(self.handle, ctypes.byref(n), ctypes.byref(skipped)))
+        return n.value, skipped.value
+
+    def __len__(self) -> int:
+        n = ctypes.c_int()
+        _check(load_library().tigas_registry_count(self.handle, ctypes.byref(n)))
+        return n.value
+
+    def info(self, index: int) -> dict:
+        m = ModelInfo()
+        _check(load_library().tigas_registry_info(self.handle, index, ctypes.byref(m)))
+        out = {k: getattr(m, k) for k, _ in ModelInfo._fields_ if k != "reserved"}
+        for k in ("id", "name", "ply_path", "preview_path"):
+            out[k] = out[k].decode()
+        out["loaded"] = bool(out["loaded"])
+        return out
+
+    def models(self) -> list[dict]:
+        return [self.info(k) for k in range(len(self))]
+
+    def model(self, model_id: str) -> dict:
+        for m in self.models():
+            if m["id"] == model_id:
+                return m
+        raise KeyError(model_id)
+
+    def acquire(self, model_id: str) -> RegistryScene:
+        h = ctypes.c_void_p()
+        _check(load_library().tigas_registry_acquire(self.handle, model_id.encode(), ctypes.byref(h)))
+        return RegistryScene(self, h.value, model_id, self.model(model_id)["n"], self.storage)
+
+    def evict_idle(self) -> int:
+        k = ctypes.c_int()
+        _check(load_library().tigas_registry_evict_idle(self.handle, ctypes.byref(k)))
+        return k.value
+
+    def start_eviction(self, period_s: float) -> None:
+        _check(load_library().tigas_registry_start_eviction(self.handle, float(period_s)))
+
+    def set_clock(self, now_s: float | None) -> None:
+        _check(load_library().tigas_registry_set_clock(self.handle, -1.0 if now_s is None else float(now_s)))
+
+    def close(self) -> None:
+        if self.handle:
+            _check(load_library().tigas_registry_close(self.handle))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+# -------------------------------------------------------- quality metrics
+
+
+def resample_rgba8(src, width: int, height: int, out=None, stream=None):
+    """Bilinear RGBA8 resample (tigas_resample_rgba8).  src: [h, w, 4] uint8,
+    host numpy or CUDA tensor; returns ``out`` (new host array if None)."""
+    h, w = int(src.shape[0]), int(src.shape[1])
+    if out is None:
+        out = np.empty((height, width, 4), np.uint8)
+    _check(load_library().tigas_resample_rgba8(_ptr(src), w, h, _ptr(out), width, height, _stream(stream)))
+    return out
+
+
+def image_quality(a, b, ssim_map=None, stream=None) -> dict:
+    """SSIM and PSNR of two RGBA8 frames of equal size (tigas_image_quality).
+    ssim_map: optional float32 [H-10, W-10] host array or CUDA tensor."""
+    if tuple(a.shape) != tuple(b.shape):
+        raise ValueError("frames differ in shape")
+    h, w = int(a.shape[0]), int(a.shape[1])
+    s, p = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().tigas_image_quality(_ptr(a), _ptr(b), w, h, _ptr(ssim_map), ctypes.byref(s),
+                                              ctypes.byref(p), _stream(stream)))
+    return {"ssim": s.value, "psnr": p.value}
 
 
 # ---------------------------------------------------------------- render

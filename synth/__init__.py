@@ -244,3 +244,32 @@ def serving_trace(seed: int = BASE_SEED + 500, n_clients: int = 64, seconds: flo
     return ServingTrace(t=t[o], client=client, scene=(client % n_scenes).astype(np.int32),
                         pose_index=np.concatenate(ps)[o], bw=np.concatenate(bs)[o], rates_hz=rates,
                         seconds=float(seconds), n_scenes=n_scenes)
+
+
+@dataclass
+class PoseLogRecord:
+    """One logged frame request of a client session: frame index, pose, the
+    intrinsics sent with it (at the requested resolution) and the profile."""
+    i: int
+    pose: Pose
+    intr: Intrinsics
+    width: int
+    height: int
+    quality: int
+
+
+def pose_log(seed: int = BASE_SEED + 600, n_frames: int = 120, ladder=TABLE1_LADDER,
+             hold: int = 3) -> list[PoseLogRecord]:
+    """A session log: a 90 Hz random-walk trajectory; the profile moves one
+    ladder step up or down (or stays) every ``hold`` frames, uniformly."""
+    poses = trajectory(seed, n_frames)
+    u = uniforms(seed, 31, n_frames)
+    levels = sorted(ladder, key=lambda r: r[1])          # low to high resolution
+    k = len(levels) - 1
+    out = []
+    for i in range(n_frames):
+        if i > 0 and i % hold == 0:
+            k = min(len(levels) - 1, max(0, k + (-1 if u[i] < 1 / 3 else (1 if u[i] > 2 / 3 else 0))))
+        _, w, h, q = levels[k][:4]
+        out.append(PoseLogRecord(i, poses[i], default_intrinsics(w, h), w, h, q))
+    return out
