@@ -164,9 +164,11 @@ def roofline(stage_ms: dict, per_step: dict, peaks: dict, clocks: dict, steps: i
     """Achieved rate of every stage and the roofline entry of the dominant one.
     Algorithmic work per launch set of the sliced schedule (see the design notes):
       preprocess  12 B per (Gaussian, view) + (A - 12) B per Gaussian + 52 B per kept entry
-      depth_sort  passes run x 32 B per entry (key, value and 8-byte rectangle, read and written)
+      depth_sort  passes run x 24 B per entry (key and 8-byte compact rectangle with its entry id,
+                  read and written), or x 32 B with wide rectangles (key, value, rectangle)
       scan        20 B per kept entry: slice count (rect 8 B + count 4 B), count scan (4 B + 4 B)
-      emit        16 B per kept entry (order, rect, offset) + 8 B per emitted pair
+      emit        12 B per kept entry (rect, offset; + 4 B of order with wide rectangles)
+                  + 8 B per emitted pair
       pair_sort   passes x 16 B per emitted pair
       ranges      8 B per tile per slice
       blend       FP32 flops: 8.5 per list entry evaluated + 9 per blended entry"""
@@ -176,9 +178,9 @@ def roofline(stage_ms: dict, per_step: dict, peaks: dict, clocks: dict, steps: i
     w = per_step
     bytes_per = {
         "preprocess": w["entries"] * 12 + w["gaussians"] * (w["attr_bytes"] - 12) + w["kept"] * 52,
-        "depth_sort": w["entries"] * w["depth_passes"] * 32,
+        "depth_sort": w["entries"] * w["depth_passes"] * (24 if w.get("compact_rect") else 32),
         "scan": w["kept"] * 20,
-        "emit": w["kept"] * 16 + w["pairs"] * 8,
+        "emit": w["kept"] * (12 if w.get("compact_rect") else 16) + w["pairs"] * 8,
         "pair_sort": w["pairs"] * w["sort_passes"] * 16,
         "ranges": w["tiles"] * w["slices"] * 8,
     }
@@ -262,6 +264,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     per_step = {"pairs": st0["n_pairs"], "kept": st0["n_visible"], "evals": st0["blend_evals"],
                 "fetched": st0["blend_fetched"], "contribs": st0["blend_contribs"], "sort_passes": st0["sort_passes"],
                 "depth_passes": st0["depth_sort_passes"],
+                # rectangles travel compact (with their entry id, no value stream) when every view
+                # has at most 127 x 127 tiles and there are at most 16 views
+                "compact_rect": int(V <= 16 and W <= 127 * 16 and H <= 127 * 16),
                 "entries": V * scene.n, "gaussians": scene.n, "attr_bytes": 124, "tiles": V * TX * TY,
                 "slices": schedule["n_slices"]}
 

@@ -111,12 +111,32 @@ struct SplatArrays {
     float* blue;          // b
     uint32_t* depth_key;  // float bits of view z, 0xFFFFFFFF when culled
     uint32_t* tiles;      // tiles touched (0 when culled)
-    uint2* rect;          // (x_lo | x_hi << 10 | view << 20, y_lo | y_hi << 10); (0, 0) when culled
+    uint2* rect;          // wide: (x_lo | x_hi << 10 | view << 20, y_lo | y_hi << 10); (0, 0) when culled
+                          // compact: (x_lo | x_hi << 7 | y_lo << 14 | y_hi << 21 | view << 28, entry)
     float* q_dbg;         // optional: 3 sqrt(lambda) per entry (parity diagnostics)
     uint32_t* key_range;  // optional: [min, max] of the kept depth keys of the launch set
     int tight_rect;       // 1: rect = the 3-sigma rectangle cut to the tiles the alpha >= 1/255 region
                           // can reach (result-invariant; the sliced schedule), 0: the 3-sigma rectangle
+    int compact_rect;     // 1: compact rect carrying its entry id (every view has TX, TY <= kCompactTiles
+                          // and there are at most 16 views), so that a depth sort moves no separate values
 };
+
+// Compact rectangle: 7 bits per tile bound, 4 bits of view.
+constexpr int kCompactTiles = 127;
+constexpr int kCompactViews = 16;
+struct TileRect {
+    uint32_t xlo, xhi, ylo, yhi, v;
+};
+__host__ __device__ inline uint32_t pack_rect_compact(uint32_t xlo, uint32_t xhi, uint32_t ylo, uint32_t yhi,
+                                                      uint32_t v) {
+    return xlo | (xhi << 7) | (ylo << 14) | (yhi << 21) | (v << 28);
+}
+template <bool COMPACT>
+__host__ __device__ inline TileRect unpack_rect(uint2 r) {
+    if (COMPACT)
+        return {r.x & 0x7Fu, (r.x >> 7) & 0x7Fu, (r.x >> 14) & 0x7Fu, (r.x >> 21) & 0x7Fu, r.x >> 28};
+    return {r.x & 0x3FFu, (r.x >> 10) & 0x3FFu, r.y & 0x3FFu, (r.y >> 10) & 0x3FFu, r.x >> 20};
+}
 
 __host__ __device__ inline uint32_t ceil_div_u32(uint32_t a, uint32_t b) { return (a + b - 1) / b; }
 

@@ -46,6 +46,8 @@ Status launch_emit_u64(const uint32_t* offsets, const SplatArrays& sp, const Vie
 //     are taken from k - kmin (0xFFFFFFFF -> kmax - kmin + 1), the same order,
 //     so keys spanning less than 2^24 need three passes;
 //   pay_in / pay_alt / pay_out: an 8-byte payload per key moved with it.
+// With a payload, values_in, values_alt and values_out may all be null: no
+// value stream is read or written (the payload identifies each key).
 struct SortExtras {
     const uint32_t* key_range = nullptr;
     const uint2* pay_in = nullptr;

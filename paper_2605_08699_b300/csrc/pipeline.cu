@@ -529,6 +529,11 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     uint2* rect_alt = ctx.fixed.take<uint2>(E);
     sp.key_range = ctx.fixed.take<uint32_t>(2);
     sp.tight_rect = req.want_q ? 0 : 1;   // debug frames report the method's 3-sigma rectangles
+    // compact rectangles carry their entry through the depth sort (no value stream)
+    bool compact = !req.want_q && V <= kCompactViews;
+    for (int v = 0; v < V; ++v)
+        compact = compact && req.views[v].TX <= kCompactTiles && req.views[v].TY <= kCompactTiles;
+    sp.compact_rect = compact ? 1 : 0;
     uint32_t* tmp = ctx.fixed.take<uint32_t>(L.tmp_words);
     uint2* ranges = ctx.fixed.take<uint2>(total_tiles);
     uint32_t* active = ctx.fixed.take<uint32_t>(4 * (size_t)total_tiles);   // long tiles as 4 strips each
@@ -563,8 +568,8 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     dex.pay_in = sp.rect;
     dex.pay_alt = rect_alt;
     dex.pay_out = rect_sorted;
-    TIGAS_TRY(radix_sort<uint32_t>(sp.depth_key, nullptr, pk_alt, pv_alt, pk, order, E, nullptr, 0, 32, tmp, st,
-                                   nullptr, d_flags, &dex));
+    TIGAS_TRY(radix_sort<uint32_t>(sp.depth_key, nullptr, pk_alt, compact ? nullptr : pv_alt, pk,
+                                   compact ? nullptr : order, E, nullptr, 0, 32, tmp, st, nullptr, d_flags, &dex));
     // passes the depth sort ran (read before the slices' scans reuse tmp)
     TIGAS_CUDA_TRY(cudaMemcpyAsync(ctx.h_flags + 1, radix_active_passes(tmp), sizeof(uint32_t),
                                    cudaMemcpyDeviceToHost, st));
@@ -618,7 +623,7 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
         uint64_t* d_P = d_total + i;
         TIGAS_TRY(mark(kStScan, true));
         TIGAS_TRY(launch_running_sat(d_views, V, done, sat, st));
-        TIGAS_TRY(launch_count_slice(rect_sorted, a, b, d_views, V, sat, counts, st));
+        TIGAS_TRY(launch_count_slice(rect_sorted, a, b, d_views, V, sat, counts, compact, st));
         // one extra zero count makes offsets[b - a] the slice total
         TIGAS_CUDA_TRY(cudaMemsetAsync(counts + (b - a), 0, sizeof(uint32_t), st));
         TIGAS_TRY(launch_scan_u32(counts, nullptr, offsets, b - a + 1, d_P, tmp, st));
@@ -641,8 +646,8 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
             cap = P;
         }
         TIGAS_TRY(mark(kStEmit, true));
-        TIGAS_TRY(launch_emit_slice(order, rect_sorted, a, b, offsets, d_views, V, done, keys_a, vals_a, cap, d_flags,
-                                    st));
+        TIGAS_TRY(launch_emit_slice(compact ? nullptr : order, rect_sorted, a, b, offsets, d_views, V, done, keys_a,
+                                    vals_a, cap, d_flags, compact, st));
         TIGAS_TRY(mark(kStEmit, false));
         TIGAS_TRY(mark(kStPairSort, true));
         TIGAS_TRY(radix_sort<uint32_t>(keys_a, vals_a, keys_b, vals_b, keys_c, vals_c, cap, stat ? d_P : nullptr, 0,

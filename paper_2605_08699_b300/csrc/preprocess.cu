@@ -281,8 +281,12 @@ k_preprocess(SceneView scene, const ViewParams* __restrict__ views_g, int V, Spl
                         out.geom[e] = make_float4(u, vv, -0.5f * kLog2e * conA, -kLog2e * conB);
                         reinterpret_cast<float2*>(out.appear)[2 * e] =
                             make_float2(-0.5f * kLog2e * conC, log2f(a.o));
-                        out.rect[e] = make_uint2((uint32_t)xlo | ((uint32_t)xhi << 10) | ((uint32_t)v << 20),
-                                                 (uint32_t)ylo | ((uint32_t)yhi << 10));
+                        out.rect[e] = out.compact_rect
+                                          ? make_uint2(pack_rect_compact((uint32_t)xlo, (uint32_t)xhi, (uint32_t)ylo,
+                                                                         (uint32_t)yhi, (uint32_t)v),
+                                                       (uint32_t)e)
+                                          : make_uint2((uint32_t)xlo | ((uint32_t)xhi << 10) | ((uint32_t)v << 20),
+                                                       (uint32_t)ylo | ((uint32_t)yhi << 10));
                         const uint32_t key = __float_as_uint(pz);
                         out.depth_key[e] = key;
                         kmin = min(kmin, key);
@@ -294,7 +298,7 @@ k_preprocess(SceneView scene, const ViewParams* __restrict__ views_g, int V, Spl
             if (!out.tight_rect) out.tiles[e] = tiles;   // the sliced render path reads rectangles only
             if (tiles == 0) {
                 out.depth_key[e] = 0xFFFFFFFFu;
-                out.rect[e] = make_uint2(0u, 0u);   // empty rectangle
+                out.rect[e] = make_uint2(0u, out.compact_rect ? (uint32_t)e : 0u);   // empty rectangle
             }
         }
     }

@@ -103,6 +103,7 @@ k_running_sat(const ViewParams* __restrict__ views_g, const uint32_t* __restrict
 }
 
 // counts[k - a] = tiles of entry order[k]'s rectangle that are not done.
+template <bool COMPACT>
 __global__ void __launch_bounds__(256)
 k_count_slice(const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b, const ViewParams* __restrict__ views_g,
               int V, const uint32_t* __restrict__ sat, uint32_t* __restrict__ counts) {
@@ -114,9 +115,8 @@ k_count_slice(const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b, con
     __syncthreads();
     const uint64_t k = a + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= b) return;
-    const uint2 r = rect_sorted[k];
-    const uint32_t xlo = r.x & 0x3FFu, xhi = (r.x >> 10) & 0x3FFu, v = r.x >> 20;
-    const uint32_t ylo = r.y & 0x3FFu, yhi = (r.y >> 10) & 0x3FFu;
+    const TileRect tr = unpack_rect<COMPACT>(rect_sorted[k]);
+    const uint32_t xlo = tr.xlo, xhi = tr.xhi, ylo = tr.ylo, yhi = tr.yhi, v = tr.v;
     uint32_t c = 0;
     if (xhi > xlo && yhi > ylo) {
         const uint32_t* s = sat + s_sb[v];
@@ -131,6 +131,8 @@ k_count_slice(const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b, con
 // the rectangle (row-major), and those not done are written to consecutive
 // positions (a ballot ranks them), so stores are coalesced and a large
 // rectangle costs area / 32 steps instead of area steps of one lane.
+// COMPACT: the entry id travels in the rectangle's second word (order unused).
+template <bool COMPACT>
 __global__ void __launch_bounds__(256)
 k_emit_slice(const uint32_t* __restrict__ order, const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b,
              const uint32_t* __restrict__ offsets, const ViewParams* __restrict__ views_g, int V,
@@ -155,17 +157,18 @@ k_emit_slice(const uint32_t* __restrict__ order, const uint2* __restrict__ rect_
     uint32_t e = 0;
     uint2 r = make_uint2(0u, 0u);
     if (c > 0) {
-        e = order[k];
         r = rect_sorted[k];
+        e = COMPACT ? r.y : order[k];
     }
     while (m) {
         const int j = __ffs(m) - 1;
         m &= m - 1;
-        const uint32_t rx = __shfl_sync(kFull, r.x, j), ry = __shfl_sync(kFull, r.y, j);
+        const uint32_t rx = __shfl_sync(kFull, r.x, j);
+        const uint32_t ry = COMPACT ? 0u : __shfl_sync(kFull, r.y, j);
         const uint32_t je = __shfl_sync(kFull, e, j), jpos = __shfl_sync(kFull, pos, j);
         const uint32_t jc = __shfl_sync(kFull, c, j);
-        const uint32_t xlo = rx & 0x3FFu, xhi = (rx >> 10) & 0x3FFu, v = rx >> 20;
-        const uint32_t ylo = ry & 0x3FFu, yhi = (ry >> 10) & 0x3FFu;
+        const TileRect tr = unpack_rect<COMPACT>(make_uint2(rx, ry));
+        const uint32_t xlo = tr.xlo, xhi = tr.xhi, ylo = tr.ylo, yhi = tr.yhi, v = tr.v;
         const uint32_t w = xhi - xlo, area = w * (yhi - ylo);
         const uint32_t tx = s_tx[v], t0 = s_tb[v] + ylo * tx + xlo;
         const float rinv = 1.0f / (float)w;
@@ -265,19 +268,29 @@ Status launch_running_sat(const ViewParams* views, int V, const uint32_t* done, 
 }
 
 Status launch_count_slice(const uint2* rect_sorted, uint64_t a, uint64_t b, const ViewParams* views, int V,
-                          const uint32_t* sat, uint32_t* counts, cudaStream_t st) {
+                          const uint32_t* sat, uint32_t* counts, bool compact, cudaStream_t st) {
     if (b <= a) return {};
-    k_count_slice<<<(unsigned)((b - a + 255) / 256), 256, 0, st>>>(rect_sorted, a, b, views, V, sat, counts);
+    const unsigned grid = (unsigned)((b - a + 255) / 256);
+    if (compact)
+        k_count_slice<true><<<grid, 256, 0, st>>>(rect_sorted, a, b, views, V, sat, counts);
+    else
+        k_count_slice<false><<<grid, 256, 0, st>>>(rect_sorted, a, b, views, V, sat, counts);
     TIGAS_LAUNCHED();
     return {};
 }
 
 Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64_t a, uint64_t b,
                          const uint32_t* offsets, const ViewParams* views, int V, const uint32_t* done,
-                         uint32_t* keys, uint32_t* values, uint64_t pair_cap, uint32_t* overflow, cudaStream_t st) {
+                         uint32_t* keys, uint32_t* values, uint64_t pair_cap, uint32_t* overflow, bool compact,
+                         cudaStream_t st) {
     if (b <= a) return {};
-    k_emit_slice<<<(unsigned)((b - a + 255) / 256), 256, 0, st>>>(order, rect_sorted, a, b, offsets, views, V, done,
-                                                                   keys, values, pair_cap, overflow);
+    const unsigned grid = (unsigned)((b - a + 255) / 256);
+    if (compact)
+        k_emit_slice<true><<<grid, 256, 0, st>>>(order, rect_sorted, a, b, offsets, views, V, done, keys, values,
+                                                 pair_cap, overflow);
+    else
+        k_emit_slice<false><<<grid, 256, 0, st>>>(order, rect_sorted, a, b, offsets, views, V, done, keys, values,
+                                                  pair_cap, overflow);
     TIGAS_LAUNCHED();
     return {};
 }

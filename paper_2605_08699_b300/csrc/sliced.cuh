@@ -24,15 +24,18 @@ Status launch_init_state(const ViewParams* views, int V, uint32_t total_tiles, c
 Status launch_running_sat(const ViewParams* views, int V, const uint32_t* done, uint32_t* sat, cudaStream_t st);
 
 // counts[k - a]: not-done tiles in the rectangle of depth-ordered entry k, k in [a, b)
-// (four reads of the running-tile table).
+// (four reads of the running-tile table).  compact: rectangles in the compact
+// form (SplatArrays::compact_rect).
 Status launch_count_slice(const uint2* rect_sorted, uint64_t a, uint64_t b, const ViewParams* views, int V,
-                          const uint32_t* sat, uint32_t* counts, cudaStream_t st);
+                          const uint32_t* sat, uint32_t* counts, bool compact, cudaStream_t st);
 
 // (tile, entry) pairs of entries [a, b) for tiles not done, at offsets[k - a]
-// (offsets: exclusive scan of counts with b - a + 1 values).
+// (offsets: exclusive scan of counts with b - a + 1 values).  The entry of k is
+// order[k], or the second word of a compact rectangle (order may then be null).
 Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64_t a, uint64_t b,
                          const uint32_t* offsets, const ViewParams* views, int V, const uint32_t* done,
-                         uint32_t* keys, uint32_t* values, uint64_t pair_cap, uint32_t* overflow, cudaStream_t st);
+                         uint32_t* keys, uint32_t* values, uint64_t pair_cap, uint32_t* overflow, bool compact,
+                         cudaStream_t st);
 
 // Tile ranges of the slice's sorted keys, and the list of tiles with pairs
 // that are not done: each tile with >= kHeavyTile pairs as its 4 strips at the

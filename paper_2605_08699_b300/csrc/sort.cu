@@ -629,6 +629,7 @@ k_os_scatter(const OsRoute* __restrict__ route, uint64_t n_cap, const uint64_t* 
     K* __restrict__ keys_out = static_cast<K*>(route->dst_k);
     uint32_t* __restrict__ vals_out = route->dst_v;
     uint2* __restrict__ pays_out = route->dst_p;
+    const bool has_vals = vals_out != nullptr;   // no value stream: the payload identifies each key
     const uint32_t mask = (1u << nbits) - 1u;
     constexpr int T = OsCfg<K, PAY>::kT, I = OsCfg<K, PAY>::kI, N = T * I, W = T / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -653,7 +654,7 @@ k_os_scatter(const OsRoute* __restrict__ route, uint64_t n_cap, const uint64_t* 
         const uint32_t li = warp * (I * 32) + r * 32 + lane;
         if (li < valid) {
             key[r] = keys_in[base + li];
-            val[r] = vals_in ? vals_in[base + li] : (uint32_t)(base + li);
+            val[r] = !has_vals ? 0u : vals_in ? vals_in[base + li] : (uint32_t)(base + li);
             if (PAY) pay[r] = pays_in[base + li];
         } else {
             key[r] = ~K(0);
@@ -749,7 +750,7 @@ k_os_scatter(const OsRoute* __restrict__ route, uint64_t n_cap, const uint64_t* 
         const uint32_t d = dr[r] >> 16;
         const uint32_t pos = sm.dstart[d] + sm.whist[warp][d] + (dr[r] & 0xFFFFu);
         sm.keys[pos] = key[r];
-        sm.vals[pos] = val[r];
+        if (has_vals) sm.vals[pos] = val[r];
         if (PAY) sm.pays[pos] = pay[r];
     }
     __syncthreads();
@@ -762,7 +763,7 @@ k_os_scatter(const OsRoute* __restrict__ route, uint64_t n_cap, const uint64_t* 
             const uint32_t g = sm.gpos[d] + (j - sm.dstart[d]);
             if (g < n) {
                 keys_out[g] = kk;
-                vals_out[g] = sm.vals[j];
+                if (has_vals) vals_out[g] = sm.vals[j];
                 if (PAY) pays_out[g] = sm.pays[j];
             }
         }
@@ -897,12 +898,14 @@ Status radix_sort(const K* keys_in, const uint32_t* values_in, K* keys_alt, uint
     const bool pay = ex && ex->pay_in;
     if (ex && (sizeof(K) != 4 || (pay && (!ex->pay_alt || !ex->pay_out))))
         return {TIGAS_ERR_INVALID, "key range and payload need 32-bit keys and all three payload buffers"};
+    if ((!values_out || !values_alt) && (values_out || values_alt || values_in || !pay))
+        return {TIGAS_ERR_INVALID, "values may be omitted only together, and only with a payload"};
     const int passes = (end_bit - begin_bit + 7) / 8;
     if (passes_out) *passes_out = passes;
     if (n_cap == 0) return {};
     if (passes == 0) {
         TIGAS_CUDA_TRY(cudaMemcpyAsync(keys_out, keys_in, n_cap * sizeof(K), cudaMemcpyDeviceToDevice, st));
-        if (values_in)
+        if (values_in && values_out)
             TIGAS_CUDA_TRY(cudaMemcpyAsync(values_out, values_in, n_cap * 4, cudaMemcpyDeviceToDevice, st));
         if (pay) TIGAS_CUDA_TRY(cudaMemcpyAsync(ex->pay_out, ex->pay_in, n_cap * 8, cudaMemcpyDeviceToDevice, st));
         return {};

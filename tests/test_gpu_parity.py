@@ -283,6 +283,29 @@ def _batch(h, poses, levels, cuda):
     return [o.cpu().numpy() for o in outs]
 
 
+def test_wide_and_compact_rectangles_give_the_same_frames(h1, cuda):
+    """Launch sets whose views all fit 127 x 127 tiles, with at most 16 views,
+    carry compact rectangles (with their entry ids) through the depth sort; a
+    wider view or a 17th view switches the whole set to the wide form."""
+    levels = [(320, 240), (97, 61)]
+    poses = synth.trajectory(91, 3)
+    compact = _batch(h1, poses[:2], levels, cuda)
+    wide = _batch(h1, poses, levels + [(2100, 40)], cuda)
+    for a, b in zip(compact, wide[:2]):
+        assert np.array_equal(a, b)
+    p17 = synth.trajectory(92, 17)
+    many = _batch(h1, p17, [(64, 48)] * 17, cuda)
+    for p, o in zip(p17, many):
+        assert np.array_equal(tg.render(h1, p, synth.default_intrinsics(64, 48), 64, 48), o)
+    # the boundary: 127 tile columns are compact, 128 are not; both match the full lists
+    for w in (2032, 2033):
+        pose, K = synth.config_trajectory(1)[30], synth.default_intrinsics(w, 40)
+        full = tg.debug_render(h1, pose, K, w, 40, sort_mode=tg.SORT_DEPTH_FIRST)
+        fast = np.zeros((40, w, 4), np.float32)
+        tg.render_ex(h1, pose, K, w, 40, out_rgba_f32=fast, sort_mode=tg.SORT_SLICED)
+        assert np.array_equal(full["rgba_f32"], fast)
+
+
 def test_graph_replay_equals_direct_launches(h1, cuda):
     levels = [(480, 270), (320, 240), (97, 61)]
     tr = synth.trajectory(11, 40)
