@@ -33,7 +33,7 @@ constexpr int kWB = TIGAS_BLEND_BATCH;    // entries per warp batch (at most 32:
 static_assert(kWB >= 1 && kWB <= 32, "a batch holds one entry per lane at most");
 constexpr int kPix = 8;                   // pixels per thread
 #ifndef TIGAS_BLEND_MIN_BLOCKS
-#define TIGAS_BLEND_MIN_BLOCKS 6
+#define TIGAS_BLEND_MIN_BLOCKS 8
 #endif
 constexpr int kMinBlocks = TIGAS_BLEND_MIN_BLOCKS;   // CTAs per SM the register budget targets
 constexpr uint32_t kFull = 0xFFFFFFFFu;
