@@ -210,7 +210,7 @@ tigas_status tigas_sort_pairs_u64(const uint64_t* keys_in, const uint32_t* value
  * synchronisation cudaMalloc/cudaFree can cause).  The paper has no
  * counterpart; this is a library convenience.
  *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
- *     Its scratch (ping-pong buffers and digit tables, about 13 MB) is one
+ *     Its scratch (ping-pong buffers and digit tables, about 16 MB) is one
  *     fixed device array that every GPU loading this library holds until the
  *     process exits.
  *   - n is limited to 1048576 (2^20) pairs; larger n returns
@@ -280,6 +280,12 @@ tigas_status tigas_server_poll(tigas_server* server, tigas_completion* out, int 
  * whole frame (first stage start to last stage end).  Off by default. */
 enum { TIGAS_N_STAGES = 8 };
 tigas_status tigas_profile_enable(int enable);
+
+/* Time only the stages in mask (bit s: stage s, s < 7; 0 turns timing off).
+ * Each timed stage adds two event records per launch; timing only the stage
+ * of interest keeps the rest of the launch set unperturbed.  The whole-frame
+ * entry needs stages 0 and 6.  Errors: INVALID (bits 7 and up). */
+tigas_status tigas_profile_stages(uint32_t mask);
 
 /* Accumulated milliseconds and recorded launch sets per stage since the last
  * reset (ms[TIGAS_N_STAGES], calls[TIGAS_N_STAGES], either may be NULL);

@@ -399,7 +399,13 @@ TIGAS_API const char* tigas_version(void) { return "tigas-b300 0.1 (sm_103a)"; }
 TIGAS_API uint64_t tigas_kernel_launches(void) { return g_launches.load(); }
 
 TIGAS_API tigas_status tigas_profile_enable(int enable) {
-    g_profile.store(enable != 0);
+    g_profile.store(enable != 0 ? (1u << kNumStages) - 1u : 0u);
+    return TIGAS_OK;
+}
+
+TIGAS_API tigas_status tigas_profile_stages(uint32_t mask) {
+    if (mask >> kNumStages) return fail(TIGAS_ERR_INVALID, "stage mask has bits past the last stage");
+    g_profile.store(mask);
     return TIGAS_OK;
 }
 

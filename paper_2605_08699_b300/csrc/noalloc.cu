@@ -26,7 +26,7 @@ namespace {
 constexpr uint64_t kMaxPairs = 1ull << 20;
 constexpr size_t kAltKeyBytes = kMaxPairs * 8;
 constexpr size_t kAltValBytes = kMaxPairs * 4;
-constexpr size_t kTableBytes = 1u << 20;   // >= radix_tmp_words(kMaxPairs) * 4 (checked at set-up)
+constexpr size_t kTableBytes = 1u << 22;   // >= radix_tmp_words(kMaxPairs) * 4 (checked at set-up)
 constexpr size_t kScratchBytes = kAltKeyBytes + kAltValBytes + kTableBytes;
 
 static __device__ __align__(256) unsigned char g_sort_scratch[kScratchBytes];

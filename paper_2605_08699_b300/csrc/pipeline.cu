@@ -9,7 +9,7 @@ namespace tigas {
 
 std::atomic<uint64_t> g_launches{0};
 std::atomic<uint64_t> g_exact_rerenders{0};
-std::atomic<bool> g_profile{false};
+std::atomic<uint32_t> g_profile{0u};
 std::atomic<bool> g_use_graphs{true};
 
 namespace {
@@ -250,9 +250,9 @@ namespace {
 struct Marker {
     RenderContext& ctx;
     cudaStream_t st;
-    bool on;
+    uint32_t stages;   // bit s: record stage s
     Status operator()(Stage sg, bool begin) {
-        if (!on) return {};
+        if (!((stages >> sg) & 1u)) return {};
         const int r = ctx.ev_count[sg];
         if (r >= kMaxSlices) return {};
         cudaEvent_t ev = begin ? ctx.ev_start[sg][r] : ctx.ev_stop[sg][r];
@@ -682,10 +682,12 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
 // ------------------------------------------------------------- CUDA graphs
 
 namespace {
+// Captured graphs hold the scene's device pointers: the key names the scene by
+// its id, never by its address (a freed scene's address may come back).
 std::vector<int64_t> graph_key(const Scene* scene, const FrameRequest& req) {
-    std::vector<int64_t> k = {(int64_t)(uintptr_t)scene, scene->view.storage, req.V, req.n_slices,
+    std::vector<int64_t> k = {(int64_t)scene->id, scene->view.storage, req.V, req.n_slices,
                               req.first_slice_inv, req.blend_ctas_per_sm, req.want_counters ? 1 : 0,
-                              g_profile.load() ? 1 : 0};
+                              (int64_t)g_profile.load()};
     for (int v = 0; v < req.V; ++v) {
         k.push_back(req.views[v].W);
         k.push_back(req.views[v].H);

@@ -14,6 +14,7 @@ struct Scene {
     uint4* chunks = nullptr;   // owned allocation
     size_t bytes = 0;
     std::atomic<int> refs{1};  // caller reference + in-flight users
+    uint64_t id = 0;           // unique for the process: a freed scene's address can be reused, its id cannot
 };
 
 void scene_acquire(Scene* s);
@@ -101,7 +102,7 @@ enum Stage { kStPreprocess, kStDepthSort, kStScan, kStEmit, kStPairSort, kStRang
 constexpr int kMaxSlices = 16;   // depth slices of the sliced schedule (and event pairs per stage)
 
 // Process-wide stage timing (tigas_profile_*).
-extern std::atomic<bool> g_profile;
+extern std::atomic<uint32_t> g_profile;   // bit s: time stage s (0: off)
 void profile_accumulate(const float* ms, const int* used, float frame_ms);
 void profile_read(double* ms, uint64_t* calls, bool reset);
 

@@ -81,7 +81,9 @@ Status scene_create(const float* means, const float* log_scales, const float* qu
                     const float* sh, uint32_t n, int sh_degree, int storage, const float bg[3], cudaStream_t st,
                     Scene** out) {
     *out = nullptr;
+    static std::atomic<uint64_t> next_id{1};
     auto* s = new Scene();
+    s->id = next_id.fetch_add(1, std::memory_order_relaxed);
     s->view.n = n;
     s->view.sh_degree = sh_degree;
     s->view.storage = storage;

@@ -508,9 +508,14 @@ __device__ inline uint32_t cta_exclusive_scan(uint32_t x, uint32_t* ws /*[T/32 +
 template <typename K>
 __global__ void __launch_bounds__(512, 2)
 k_os_hist(const K* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, int begin_bit, int end_bit,
-          uint32_t* __restrict__ ghist, const uint32_t* __restrict__ range) {
+          uint32_t* __restrict__ ghist, const uint32_t* __restrict__ range, uint4* __restrict__ zero,
+          uint64_t zero_n) {
     constexpr int kP = (int)sizeof(K);   // most passes this key width can need
     __shared__ uint32_t h[kP][256];
+    // clear the scatter passes' look-back tables (no pass has started yet)
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < zero_n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        zero[i] = make_uint4(0u, 0u, 0u, 0u);
     const int passes = (end_bit - begin_bit + 7) / 8;
     for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) (&h[0][0])[i] = 0;
     KeyMap km;
@@ -786,9 +791,10 @@ Status ensure_os_smem() {
 uint64_t os_chunks(uint64_t n_cap) { return (n_cap + 4095) / 4096; }   // upper bound for every tile shape
 
 // tmp layout: ghist [8][256], gbase [8][256], chunk counters [8], flags [8],
-// routes [8], status [chunks][256]
-constexpr size_t kOsHead = 8 * 256 * 2 + 16 + 8 * kRouteWords;
-size_t os_tmp_words(uint64_t n_cap) { return kOsHead + os_chunks(n_cap) * 256; }
+// routes [8], status [pass][chunks][256] (cleared by the histogram kernel);
+// the status table starts 16-byte aligned
+constexpr size_t kOsHead = (8 * 256 * 2 + 16 + 8 * kRouteWords + 3) / 4 * 4;
+size_t os_tmp_words(uint64_t n_cap) { return kOsHead + 8 * os_chunks(n_cap) * 256; }
 
 template <typename K, bool PAY, bool MAP>
 Status radix_sort_onesweep(const K* keys_in, const uint32_t* values_in, K* keys_alt, uint32_t* values_alt,
@@ -811,7 +817,9 @@ Status radix_sort_onesweep(const K* keys_in, const uint32_t* values_in, K* keys_
     // enough CTAs for eight grid strides of 4 keys per thread, at most 8 per SM
     const uint64_t hist_ctas = (n_cap + 512 * 4 * 8 - 1) / (512 * 4 * 8);
     const unsigned hgrid = (unsigned)(hist_ctas < 148 ? 148 : (hist_ctas > 148 * 8 ? 148 * 8 : hist_ctas));
-    k_os_hist<K><<<hgrid, 512, 0, st>>>(keys_in, n_cap, d_n, begin_bit, end_bit, ghist, range);
+    const uint64_t status_words = (uint64_t)passes * chunks * 256;
+    k_os_hist<K><<<hgrid, 512, 0, st>>>(keys_in, n_cap, d_n, begin_bit, end_bit, ghist, range,
+                                        reinterpret_cast<uint4*>(status), status_words / 4);
     TIGAS_LAUNCHED();
     OsBuffers bufs{keys_in, values_in, PAY ? ex->pay_in : nullptr, keys_alt, values_alt, PAY ? ex->pay_alt : nullptr,
                    keys_out, values_out, PAY ? ex->pay_out : nullptr};
@@ -820,9 +828,9 @@ Status radix_sort_onesweep(const K* keys_in, const uint32_t* values_in, K* keys_
     for (int p = 0; p < passes; ++p) {
         const int shift = begin_bit + 8 * p;
         const int nb = min(8, end_bit - shift);
-        TIGAS_CUDA_TRY(cudaMemsetAsync(status, 0, chunks * 256 * sizeof(uint32_t), st));
         k_os_scatter<K, PAY, MAP><<<(unsigned)chunks, T, sizeof(OsSmem<K, PAY>), st>>>(
-            routes + p, n_cap, d_n, shift, nb, gbase + p * 256, status, counters + p, flags, kSpinLimit, range);
+            routes + p, n_cap, d_n, shift, nb, gbase + p * 256, status + (size_t)p * chunks * 256, counters + p,
+            flags, kSpinLimit, range);
         TIGAS_LAUNCHED();
     }
     return {};
@@ -864,7 +872,7 @@ Status debug_lookback_timeout(int spin_limit, bool* timed_out) {
     if (e == cudaSuccess) e = cudaMemcpy(misc, misc_init, sizeof(misc_init), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         OsBuffers bufs{keys, nullptr, nullptr, out, sorted_vals, nullptr, out, sorted_vals, nullptr};
-        k_os_hist<K><<<4, 512>>>(keys, n, nullptr, 0, 8, ghist, nullptr);
+        k_os_hist<K><<<4, 512>>>(keys, n, nullptr, 0, 8, ghist, nullptr, nullptr, 0);
         k_os_bases<<<1, 256>>>(ghist, gbase, 1, route, bufs, nullptr);
         k_os_scatter<K, false, false><<<1, T, sizeof(OsSmem<K, false>)>>>(route, n, nullptr, 0, 8, gbase, status,
                                                                           misc, misc + 1, spin_limit, nullptr);

@@ -33,7 +33,7 @@ EXPORTS = ["tigas_scene_load", "tigas_scene_free", "tigas_scene_bytes", "tigas_r
            "tigas_registry_open", "tigas_registry_scan", "tigas_registry_count", "tigas_registry_info",
            "tigas_registry_acquire", "tigas_registry_release", "tigas_registry_evict_idle",
            "tigas_registry_start_eviction", "tigas_registry_set_clock", "tigas_registry_close",
-           "tigas_resample_rgba8", "tigas_image_quality"]
+           "tigas_resample_rgba8", "tigas_image_quality", "tigas_profile_stages"]
 
 STAGES = ["preprocess", "depth_sort", "scan", "emit", "pair_sort", "ranges", "blend", "frame"]
 
@@ -141,6 +141,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "tigas_version": (ctypes.c_char_p, []),
         "tigas_kernel_launches": (ctypes.c_uint64, []),
         "tigas_profile_enable": (st, [i]),
+        "tigas_profile_stages": (st, [ctypes.c_uint32]),
         "tigas_set_graphs": (st, [i]),
         "tigas_debug_sort_wait_timeout": (st, [i]),
         "tigas_set_schedule": (st, [ctypes.POINTER(Schedule)]),
@@ -196,6 +197,14 @@ def kernel_launches() -> int:
 def profile_enable(on: bool = True) -> None:
     """Per-stage CUDA-event timing of every later render (tigas_profile_enable)."""
     _check(load_library().tigas_profile_enable(int(on)))
+
+
+def profile_stages(stages) -> None:
+    """Time only the named stages (tigas_profile_stages); an empty list turns timing off."""
+    mask = 0
+    for name in stages:
+        mask |= 1 << STAGES.index(name)
+    _check(load_library().tigas_profile_stages(mask))
 
 
 def set_graphs(on: bool = True) -> None:

@@ -111,6 +111,24 @@ def test_load_errors_are_reported(cuda, tmp_path):
     assert e.value.status == tg.ERR_INVALID
 
 
+def test_launch_sets_of_a_freed_scene_are_never_reused(cuda):
+    """Captured launch sets hold a scene's device pointers.  Scenes freed and
+    loaded in turn (a new scene may reuse a freed one's host address) must each
+    render their own frames: repeated renders (graph replays from the third on)
+    equal the scene's direct full-list frame."""
+    w, h = 96, 64
+    K = synth.default_intrinsics(w, h)
+    scenes = [_scene(20_000, 0, seed=61), _scene(35_000, 3, seed=62)]
+    for _ in range(3):
+        for sc in scenes:
+            with tg.scene_from(sc, storage=tg.STORAGE_FP16) as hd:
+                want = np.zeros((h, w, 4), np.uint8)
+                tg.render_ex(hd, synth.BASE_POSE, K, w, h, out_rgba8=want, sort_mode=tg.SORT_DEPTH_FIRST)
+                assert want.any()
+                for _ in range(4):
+                    assert np.array_equal(tg.render(hd, synth.BASE_POSE, K, w, h), want)
+
+
 # ------------------------------------------------------------------ registry
 
 
