@@ -169,7 +169,8 @@ def roofline(stage_ms: dict, per_step: dict, peaks: dict, clocks: dict, steps: i
       preprocess  12 B per (Gaussian, view) + (A - 12) B per Gaussian + 52 B per kept entry
       depth_sort  passes run x 24 B per entry (key and 8-byte compact rectangle with its entry id,
                   read and written), or x 32 B with wide rectangles (key, value, rectangle)
-      scan        20 B per kept entry: slice count (rect 8 B + count 4 B), count scan (4 B + 4 B)
+      scan        20 B per kept entry: slice count with per-block sums (rect 8 B + count 4 B),
+                  count scan (4 B + 4 B)
       emit        12 B per kept entry (rect, offset; + 4 B of order with wide rectangles)
                   + 8 B per emitted pair
       pair_sort   passes x 16 B per emitted pair

@@ -458,6 +458,7 @@ SlicedLayout sliced_layout(const Scene* scene, FrameRequest& req) {
     size_t b = sizeof(ViewParams) * kMaxViews + 96 * 256;
     b += E * (16 + 16 + 4 + 4 + 4 + 8 + (req.want_q ? 4 : 0));
     b += E * 4 * 4 + (E + 1) * 4 * 2 + E * 8 * 2;         // depth sort buffers, counts, offsets, rects (2)
+    b += ((E + 1 + kScanBlock - 1) / kScanBlock) * 4;     // block sums of the counts
     b += L.tmp_words * 4;
     b += (sizeof(uint2) + 4 * 4 + 4) * (size_t)L.total_tiles + L.done_words * 4;   // ranges, active, strips
     b += (size_t)L.total_sat * 4;                                                   // running-tile tables
@@ -525,6 +526,7 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     uint32_t* order = ctx.fixed.take<uint32_t>(E);
     uint32_t* counts = ctx.fixed.take<uint32_t>(E + 1);
     uint32_t* offsets = ctx.fixed.take<uint32_t>(E + 1);
+    uint32_t* count_sums = ctx.fixed.take<uint32_t>((E + 1 + kScanBlock - 1) / kScanBlock);
     uint2* rect_sorted = ctx.fixed.take<uint2>(E);
     uint2* rect_alt = ctx.fixed.take<uint2>(E);
     sp.key_range = ctx.fixed.take<uint32_t>(2);
@@ -550,9 +552,6 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     TIGAS_CUDA_TRY(cudaMemcpyAsync(d_pix_base, hv + sizeof(ViewParams) * kMaxViews, sizeof(uint64_t) * V,
                                    cudaMemcpyHostToDevice, st));
     TIGAS_CUDA_TRY(cudaMemsetAsync(d_flags, 0, sizeof(uint32_t) * 2, st));
-    TIGAS_CUDA_TRY(cudaMemsetAsync(d_total, 0, sizeof(uint64_t) * (kMaxSlices + 2), st));   // empty slices count 0
-    TIGAS_CUDA_TRY(cudaMemsetAsync(done, 0, L.done_words * 4, st));
-    TIGAS_CUDA_TRY(cudaMemsetAsync(strips, 0, (size_t)total_tiles * 4, st));
     if (sp.q_dbg) TIGAS_CUDA_TRY(cudaMemsetAsync(sp.q_dbg, 0, E * 4, st));
     if (req.want_counters) TIGAS_CUDA_TRY(cudaMemsetAsync(d_counters, 0, sizeof(unsigned long long) * 4, st));
 
@@ -574,7 +573,9 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     TIGAS_CUDA_TRY(cudaMemcpyAsync(ctx.h_flags + 1, radix_active_passes(tmp), sizeof(uint32_t),
                                    cudaMemcpyDeviceToHost, st));
     TIGAS_TRY(mark(kStDepthSort, false));
-    TIGAS_TRY(launch_init_state(d_views, V, total_tiles, d_pix_base, state, scene->view.bg, st));
+    // also clears the done and strip bits and the slice totals (empty slices count 0)
+    TIGAS_TRY(launch_init_state(d_views, V, total_tiles, d_pix_base, state, scene->view.bg, done, strips, d_total,
+                                kMaxSlices + 2, st));
 
     // entries the slices cut: kept ones only (exact), or all (static; culled
     // ones sort after every kept one and have empty rectangles)
@@ -622,11 +623,12 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
         if (b == a) continue;
         uint64_t* d_P = d_total + i;
         TIGAS_TRY(mark(kStScan, true));
-        TIGAS_TRY(launch_running_sat(d_views, V, done, sat, st));
-        TIGAS_TRY(launch_count_slice(rect_sorted, a, b, d_views, V, sat, counts, compact, st));
-        // one extra zero count makes offsets[b - a] the slice total
-        TIGAS_CUDA_TRY(cudaMemsetAsync(counts + (b - a), 0, sizeof(uint32_t), st));
-        TIGAS_TRY(launch_scan_u32(counts, nullptr, offsets, b - a + 1, d_P, tmp, st));
+        // also clears the slice's active-list counts and blend work counter (d_misc[0..2])
+        TIGAS_TRY(launch_running_sat(d_views, V, done, sat, d_misc, 3, st));
+        // counts[b - a] = 0 makes offsets[b - a] the slice total (also in *d_P); the count
+        // kernel also sums the counts per scan block, so the scan has no reduce pass
+        TIGAS_TRY(launch_count_slice(rect_sorted, a, b, d_views, V, sat, counts, count_sums, compact, st));
+        TIGAS_TRY(launch_scan_u32_summed(counts, offsets, b - a + 1, count_sums, d_P, tmp, st));
         TIGAS_TRY(mark(kStScan, false));
         uint64_t cap = static_cap;
         if (!stat) {

@@ -37,11 +37,18 @@ __device__ inline uint8_t to_u8(float x) {
 // State (C = 0, T = 1) and background outputs for every pixel; one CTA per tile.
 __global__ void __launch_bounds__(256)
 k_init_state(const ViewParams* __restrict__ views_g, int V, const uint64_t* __restrict__ pix_base, float4* state,
-             float bg_r, float bg_g, float bg_b) {
+             float bg_r, float bg_g, float bg_b, uint32_t* __restrict__ done, uint32_t* __restrict__ strips,
+             unsigned long long* __restrict__ totals, int n_totals) {
     __shared__ uint32_t s_tb[kMaxViews];
     for (int k = threadIdx.x; k < V; k += blockDim.x) s_tb[k] = views_g[k].tile_base;
-    __syncthreads();
     const uint32_t g = blockIdx.x;
+    // the slices' per-tile state: nothing done, no strip finished; slice totals 0
+    if (threadIdx.x == 0) {
+        strips[g] = 0u;
+        if ((g & 31u) == 0u) done[g >> 5] = 0u;
+    }
+    if (g == 0 && (int)threadIdx.x < n_totals) totals[threadIdx.x] = 0ull;
+    __syncthreads();
     const int v = view_of_tile(s_tb, V, g);
     const ViewParams& vp = views_g[v];
     const uint32_t local = g - s_tb[v];
@@ -66,8 +73,10 @@ __device__ inline bool tile_done(const uint32_t* __restrict__ done, uint32_t t) 
 constexpr uint32_t kSatSmem = 12288;   // 48 KB
 
 __global__ void __launch_bounds__(1024)
-k_running_sat(const ViewParams* __restrict__ views_g, const uint32_t* __restrict__ done, uint32_t* __restrict__ sat) {
+k_running_sat(const ViewParams* __restrict__ views_g, const uint32_t* __restrict__ done, uint32_t* __restrict__ sat,
+              uint32_t* __restrict__ slice_zero, int n_zero) {
     __shared__ uint32_t tab[kSatSmem];
+    if (blockIdx.x == 0 && (int)threadIdx.x < n_zero) slice_zero[threadIdx.x] = 0u;
     const ViewParams& vp = views_g[blockIdx.x];
     const uint32_t TX = (uint32_t)vp.TX, TY = (uint32_t)vp.TY, W1 = TX + 1;
     const bool in_smem = (TY + 1) * W1 <= kSatSmem;
@@ -102,28 +111,52 @@ k_running_sat(const ViewParams* __restrict__ views_g, const uint32_t* __restrict
     }
 }
 
-// counts[k - a] = tiles of entry order[k]'s rectangle that are not done.
+// counts[k - a] = tiles of entry order[k]'s rectangle that are not done, for
+// k in [a, b), and counts[b - a] = 0; sums[j] = the sum of counts of block j
+// (kScanBlock consecutive counts: the scan's tile), so the scan needs no
+// reduce pass.  One CTA per block, 16 counts per thread.
+constexpr int kCountThreads = 256;
+constexpr int kCountItems = (int)kScanBlock / kCountThreads;
 template <bool COMPACT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kCountThreads)
 k_count_slice(const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b, const ViewParams* __restrict__ views_g,
-              int V, const uint32_t* __restrict__ sat, uint32_t* __restrict__ counts) {
-    __shared__ uint32_t s_sb[kMaxViews], s_w1[kMaxViews];
-    for (int k = threadIdx.x; k < V; k += blockDim.x) {
+              int V, const uint32_t* __restrict__ sat, uint32_t* __restrict__ counts, uint32_t* __restrict__ sums) {
+    __shared__ uint32_t s_sb[kMaxViews], s_w1[kMaxViews], ws[kCountThreads / 32];
+    for (int k = threadIdx.x; k < V; k += kCountThreads) {
         s_sb[k] = views_g[k].sat_base;
         s_w1[k] = (uint32_t)views_g[k].TX + 1u;
     }
     __syncthreads();
-    const uint64_t k = a + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= b) return;
-    const TileRect tr = unpack_rect<COMPACT>(rect_sorted[k]);
-    const uint32_t xlo = tr.xlo, xhi = tr.xhi, ylo = tr.ylo, yhi = tr.yhi, v = tr.v;
-    uint32_t c = 0;
-    if (xhi > xlo && yhi > ylo) {
-        const uint32_t* s = sat + s_sb[v];
-        const uint32_t w1 = s_w1[v];
-        c = s[yhi * w1 + xhi] - s[ylo * w1 + xhi] - s[yhi * w1 + xlo] + s[ylo * w1 + xlo];
+    const uint64_t n = b - a + 1;   // with the closing zero
+    const uint64_t base = (uint64_t)blockIdx.x * kScanBlock;
+    uint32_t total = 0;
+#pragma unroll 4
+    for (int r = 0; r < kCountItems; ++r) {
+        const uint64_t i = base + (uint64_t)r * kCountThreads + threadIdx.x;
+        if (i >= n) break;
+        uint32_t c = 0;
+        if (i + a < b) {
+            const TileRect tr = unpack_rect<COMPACT>(rect_sorted[a + i]);
+            if (tr.xhi > tr.xlo && tr.yhi > tr.ylo) {
+                const uint32_t* s = sat + s_sb[tr.v];
+                const uint32_t w1 = s_w1[tr.v];
+                c = s[tr.yhi * w1 + tr.xhi] - s[tr.ylo * w1 + tr.xhi] - s[tr.yhi * w1 + tr.xlo] +
+                    s[tr.ylo * w1 + tr.xlo];
+            }
+        }
+        counts[i] = c;
+        total += c;
     }
-    counts[k - a] = c;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) total += __shfl_xor_sync(kFull, total, d);
+    if (lane == 0) ws[warp] = total;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kCountThreads / 32; ++w) t += ws[w];
+        sums[blockIdx.x] = t;
+    }
 }
 
 // Pairs (tile, entry) of the slice for tiles not done, in depth order.  The
@@ -254,27 +287,32 @@ k_ranges_active(const uint32_t* __restrict__ keys, uint64_t n_cap, const uint64_
 }  // namespace
 
 Status launch_init_state(const ViewParams* views, int V, uint32_t total_tiles, const uint64_t* pix_base,
-                         float4* state, const float* bg, cudaStream_t st) {
+                         float4* state, const float* bg, uint32_t* done, uint32_t* strips, uint64_t* totals,
+                         int n_totals, cudaStream_t st) {
     if (total_tiles == 0) return {};
-    k_init_state<<<total_tiles, 256, 0, st>>>(views, V, pix_base, state, bg[0], bg[1], bg[2]);
+    if (n_totals > 256) return {TIGAS_ERR_INVALID, "too many slice totals"};
+    k_init_state<<<total_tiles, 256, 0, st>>>(views, V, pix_base, state, bg[0], bg[1], bg[2], done, strips,
+                                              reinterpret_cast<unsigned long long*>(totals), n_totals);
     TIGAS_LAUNCHED();
     return {};
 }
 
-Status launch_running_sat(const ViewParams* views, int V, const uint32_t* done, uint32_t* sat, cudaStream_t st) {
-    k_running_sat<<<V, 1024, 0, st>>>(views, done, sat);
+Status launch_running_sat(const ViewParams* views, int V, const uint32_t* done, uint32_t* sat, uint32_t* slice_zero,
+                          int n_zero, cudaStream_t st) {
+    if (n_zero > 1024) return {TIGAS_ERR_INVALID, "too many words to clear"};
+    k_running_sat<<<V, 1024, 0, st>>>(views, done, sat, slice_zero, n_zero);
     TIGAS_LAUNCHED();
     return {};
 }
 
 Status launch_count_slice(const uint2* rect_sorted, uint64_t a, uint64_t b, const ViewParams* views, int V,
-                          const uint32_t* sat, uint32_t* counts, bool compact, cudaStream_t st) {
+                          const uint32_t* sat, uint32_t* counts, uint32_t* sums, bool compact, cudaStream_t st) {
     if (b <= a) return {};
-    const unsigned grid = (unsigned)((b - a + 255) / 256);
+    const unsigned grid = (unsigned)((b - a + 1 + kScanBlock - 1) / kScanBlock);
     if (compact)
-        k_count_slice<true><<<grid, 256, 0, st>>>(rect_sorted, a, b, views, V, sat, counts);
+        k_count_slice<true><<<grid, kCountThreads, 0, st>>>(rect_sorted, a, b, views, V, sat, counts, sums);
     else
-        k_count_slice<false><<<grid, 256, 0, st>>>(rect_sorted, a, b, views, V, sat, counts);
+        k_count_slice<false><<<grid, kCountThreads, 0, st>>>(rect_sorted, a, b, views, V, sat, counts, sums);
     TIGAS_LAUNCHED();
     return {};
 }
@@ -299,7 +337,6 @@ Status launch_ranges_active(const uint32_t* keys, uint64_t n_cap, const uint64_t
                             uint32_t n_tiles, const uint32_t* done, uint32_t* active, uint32_t* n_active,
                             uint32_t* overflow, cudaStream_t st) {
     if (n_tiles == 0) return {};
-    TIGAS_CUDA_TRY(cudaMemsetAsync(n_active, 0, 2 * sizeof(uint32_t), st));
     k_ranges_active<<<(n_tiles + 255) / 256, 256, 0, st>>>(keys, n_cap, d_n, ranges, n_tiles, done, active, n_active,
                                                            overflow);
     TIGAS_LAUNCHED();

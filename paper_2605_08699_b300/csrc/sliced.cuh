@@ -14,20 +14,27 @@ constexpr uint32_t kHeavyTile = TIGAS_HEAVY_TILE;   // pairs of a slice that mak
 constexpr int kStripShift = 28;
 constexpr uint32_t kTileMask = (1u << kStripShift) - 1u;
 
-// (C, T) = (0, 1) for every pixel of every view, background in the outputs.
+// (C, T) = (0, 1) for every pixel of every view, background in the outputs;
+// also clears the per-tile done bits (total_tiles bits) and strip words, and
+// totals[0 .. n_totals) (at most 256).
 // pix_base[v]: offset of view v's first pixel in `state`.
 Status launch_init_state(const ViewParams* views, int V, uint32_t total_tiles, const uint64_t* pix_base,
-                         float4* state, const float* bg, cudaStream_t st);
+                         float4* state, const float* bg, uint32_t* done, uint32_t* strips, uint64_t* totals,
+                         int n_totals, cudaStream_t st);
 
 // Per view, the summed-area table of tiles not done: sat[sat_base + y (TX+1) + x]
-// = not-done tiles in columns [0, x) of rows [0, y).
-Status launch_running_sat(const ViewParams* views, int V, const uint32_t* done, uint32_t* sat, cudaStream_t st);
+// = not-done tiles in columns [0, x) of rows [0, y).  Also clears
+// slice_zero[0 .. n_zero) (at most 1024 words: the slice's active-list counts
+// and blend work counter, which the ranges and blend launches expect zeroed).
+Status launch_running_sat(const ViewParams* views, int V, const uint32_t* done, uint32_t* sat, uint32_t* slice_zero,
+                          int n_zero, cudaStream_t st);
 
 // counts[k - a]: not-done tiles in the rectangle of depth-ordered entry k, k in [a, b)
-// (four reads of the running-tile table).  compact: rectangles in the compact
-// form (SplatArrays::compact_rect).
+// (four reads of the running-tile table), and counts[b - a] = 0; sums[j]: the
+// sum of counts block j (kScanBlock counts), for launch_scan_u32_summed.
+// compact: rectangles in the compact form (SplatArrays::compact_rect).
 Status launch_count_slice(const uint2* rect_sorted, uint64_t a, uint64_t b, const ViewParams* views, int V,
-                          const uint32_t* sat, uint32_t* counts, bool compact, cudaStream_t st);
+                          const uint32_t* sat, uint32_t* counts, uint32_t* sums, bool compact, cudaStream_t st);
 
 // (tile, entry) pairs of entries [a, b) for tiles not done, at offsets[k - a]
 // (offsets: exclusive scan of counts with b - a + 1 values).  The entry of k is
@@ -40,7 +47,8 @@ Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64
 // Tile ranges of the slice's sorted keys, and the list of tiles with pairs
 // that are not done: each tile with >= kHeavyTile pairs as its 4 strips at the
 // front of `active` (n_active[0] items), the other tiles whole at its back
-// (active[4 n_tiles - 1 - k], n_active[1] items); both counts are zeroed here.
+// (active[4 n_tiles - 1 - k], n_active[1] items); both counts must be zero
+// on entry (launch_running_sat clears them).
 // `active` holds 4 n_tiles items.
 // The key count is min(*d_n, n_cap) when d_n is given, else n_cap.
 Status launch_ranges_active(const uint32_t* keys, uint64_t n_cap, const uint64_t* d_n, uint2* ranges,
@@ -54,7 +62,7 @@ Status launch_ranges_active(const uint32_t* keys, uint64_t n_cap, const uint64_t
 struct SliceBlendArgs {
     const uint32_t* active;
     const uint32_t* n_active;   // [long tiles at the front, short tiles at the back]
-    uint32_t* work_counter;     // zeroed by the launcher
+    uint32_t* work_counter;     // zero on entry (launch_running_sat clears it)
     float4* state;              // per pixel (C.rgb, T), T negated once the pixel stopped
     const uint64_t* pix_base;   // per view
     uint32_t* done;             // per-tile bitmap
