@@ -256,6 +256,22 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
         poses = [trajs[v][(s * 7 + v) % len(trajs[v])] for v in range(V)]
         tg.render_batch(handle, poses, [K] * V, [W] * V, [H] * V, o, stream=stream)
 
+    # the timed steps: asynchronous launch sets, the next one queued before the previous one is
+    # waited on (double-buffered outputs), so host work between launch sets overlaps the GPU
+    outs_b = [torch.empty((H, W, 4), dtype=torch.uint8, device=dev) for _ in range(V)]
+
+    def run_async(first, n):
+        prev = None
+        for s in range(first, first + n):
+            poses = [trajs[v][(s * 7 + v) % len(trajs[v])] for v in range(V)]
+            t = tg.render_batch_async(h16, poses, [K] * V, [W] * V, [H] * V, outs if s % 2 == 0 else outs_b,
+                                      stream=stream)
+            if prev is not None:
+                prev.wait()
+            prev = t
+        if prev is not None:
+            prev.wait()
+
     # the dominant kernel's launches are timed with events inside the timed region; the other
     # stages are timed in a separate untimed pass (each timed stage adds graph nodes)
     tg.profile_stages(["blend"])
@@ -269,6 +285,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
         schedule, _ = tg.autotune(h16, sets, [K] * V, [W] * V, [H] * V, outs, iters=4)
     for s in range(args.warmup):
         step(s)
+    run_async(0, max(4, args.warmup))   # both in-flight contexts capture their launch sets
     torch.cuda.synchronize()
 
     # per-step workload (untimed): one launch set of the same kind as a timed step
@@ -297,10 +314,15 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     step_ms_host = []
     e0.record(stream)
+    prev = None
     for s in range(args.steps):
-        t0 = time.perf_counter()
-        step(args.warmup + s)
-        step_ms_host.append((time.perf_counter() - t0) * 1e3)
+        poses = [trajs[v][((args.warmup + s) * 7 + v) % len(trajs[v])] for v in range(V)]
+        t = tg.render_batch_async(h16, poses, [K] * V, [W] * V, [H] * V, outs if s % 2 == 0 else outs_b,
+                                  stream=stream)
+        if prev is not None:
+            prev.wait()
+        prev = t
+    prev.wait()
     e1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -312,6 +334,12 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     timed_stage_ms = tg.profile_read(reset=True)
     elapsed_ms, frames = aggregate_over_ranks(elapsed_ms, V * args.steps, world, dev)
     value = frames / (elapsed_ms * 1e-3)
+
+    # ---- latency (untimed): one synchronous launch set at a time, submit to frames complete
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        step(args.warmup + s)
+        step_ms_host.append((time.perf_counter() - t0) * 1e3)
 
     # ---- stage table (untimed): the same launch sets with every stage's events on
     tg.profile_enable(True)
@@ -791,7 +819,8 @@ def main(argv=None) -> int:
                        "parallelism": f"replicas x{world}"},
             "latency_ms": {"p50_step": round(float(np.percentile(steps_ms, 50)), 3),
                            "p99_step": round(float(np.percentile(steps_ms, 99)), 3),
-                           "note": "host time of one synchronous launch set of views_per_step frames"},
+                           "note": "host time of one synchronous launch set of views_per_step frames "
+                                   "(tigas_render_batch), measured after the timed region"},
             "schedule": dict(r["schedule"], kind="depth-sliced: nearest-first geometric slices, tiles whose "
                                                   "pixels all stopped are dropped", autotuned=not (args.no_autotune or args.schedule),
                              exact_rerenders_timed=r["rerenders"]),

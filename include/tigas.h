@@ -166,6 +166,22 @@ tigas_status tigas_render_batch_ex(tigas_scene* scene, int n_views, const tigas_
                                    const tigas_intrinsics* intrs, const int* widths, const int* heights,
                                    uint8_t* const* outs, void* cuda_stream, int sort_mode, tigas_frame_stats* stats);
 
+/* Asynchronous tigas_render_batch (SLICED schedule): enqueue the launch set on
+ * cuda_stream (NULL: the library's own stream) and return at once with a
+ * ticket; outputs must be device memory.  tigas_render_wait completes it:
+ * waits for the launch set, and if a fixed-capacity launch set outgrew its
+ * pair buffers renders it again exactly before returning (the frames are
+ * final only then).  Each outstanding ticket holds its own render context,
+ * so a caller can keep the next launch set queued behind the current one;
+ * output buffers of a ticket must not be reused before its wait returns.
+ * Every ticket must be waited on exactly once.  Errors: as
+ * tigas_render_batch; INVALID for host outputs. */
+typedef struct tigas_ticket tigas_ticket;
+tigas_status tigas_render_batch_async(tigas_scene* scene, int n_views, const tigas_pose* poses,
+                                      const tigas_intrinsics* intrs, const int* widths, const int* heights,
+                                      uint8_t* const* outs, void* cuda_stream, tigas_ticket** out_ticket);
+tigas_status tigas_render_wait(tigas_ticket* ticket);
+
 /* ------------------------------------------------------------------ debug */
 
 /* Intermediate results of one frame, for parity tests.  Host arrays, all

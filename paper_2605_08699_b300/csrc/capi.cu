@@ -75,66 +75,81 @@ struct SceneGuard {
     }
 };
 
-// Render V views synchronously; outputs may be host or device.
-Status do_render(Scene* scene, int V, const tigas_pose* poses, const tigas_intrinsics* intrs, const int* ws,
-                 const int* hs, uint8_t* const* outs8, float* const* outs32, cudaStream_t user_st, int sort_mode,
-                 tigas_frame_stats* stats, tigas_debug_frame* dbg, uint64_t* dbg_pairs) {
+// A launch set between its submission and its completion.
+struct PendingRender {
+    Scene* scene = nullptr;
+    int V = 0;
+    int sort_mode = TIGAS_SORT_SLICED;
+    FrameRequest req;
+    FrameResult res;
+    std::vector<uint8_t*> host8;
+    std::vector<float*> host32;
+    std::vector<int> ws, hs;
+};
+
+// Validate and enqueue V views on st (host outputs go through device staging
+// and are copied back on st).  Returns with the work in flight.
+Status submit_render(RenderContext& ctx, Scene* scene, int V, const tigas_pose* poses, const tigas_intrinsics* intrs,
+                     const int* ws, const int* hs, uint8_t* const* outs8, float* const* outs32, cudaStream_t st,
+                     int sort_mode, bool want_stats, bool want_q, PendingRender& p) {
     if (!scene) return {TIGAS_ERR_INVALID, "null scene"};
     if (V < 1 || V > kMaxViews) return {TIGAS_ERR_INVALID, "n_views out of 1..64"};
     if (sort_mode != TIGAS_SORT_DEPTH_FIRST && sort_mode != TIGAS_SORT_FULL64 && sort_mode != TIGAS_SORT_SLICED)
         return {TIGAS_ERR_INVALID, "unknown sort mode"};
-    if (dbg && sort_mode == TIGAS_SORT_SLICED && (dbg->values || dbg->ranges))
-        return {TIGAS_ERR_INVALID, "the sliced schedule builds no whole tile lists: pass values = ranges = NULL"};
     for (int v = 0; v < V; ++v) TIGAS_TRY(validate_view(&poses[v], &intrs[v], ws[v], hs[v]));
-    Status err;
-    ContextGuard g;
-    g.ctx = acquire_context(&err);
-    if (!g.ctx) return err;
-    RenderContext& ctx = *g.ctx;
-    cudaStream_t st = user_st ? user_st : ctx.stream;
-
-    FrameRequest req;
+    p.scene = scene;
+    p.V = V;
+    p.sort_mode = sort_mode;
+    p.ws.assign(ws, ws + V);
+    p.hs.assign(hs, hs + V);
+    FrameRequest& req = p.req;
     req.V = V;
     req.sort_mode = sort_mode;
     const Schedule sched = current_schedule();
     req.n_slices = sched.n_slices;
     req.first_slice_inv = sched.first_slice_inv;
     req.blend_ctas_per_sm = sched.blend_ctas_per_sm;
-    req.want_q = dbg != nullptr;
-    req.want_counters = stats != nullptr;
-    std::vector<uint8_t*> host8(V, nullptr);
-    std::vector<float*> host32(V, nullptr);
+    req.want_q = want_q;
+    req.want_counters = want_stats;
+    p.host8.assign(V, nullptr);
+    p.host32.assign(V, nullptr);
     for (int v = 0; v < V; ++v) {
         req.views[v] = make_view(poses[v], intrs[v], ws[v], hs[v], 0);
         const size_t px = (size_t)ws[v] * hs[v];
         uint8_t* o8 = outs8 ? outs8[v] : nullptr;
         float* o32 = outs32 ? outs32[v] : nullptr;
         if (o8 && !is_device_pointer(o8)) {
-            host8[v] = o8;
+            p.host8[v] = o8;
             TIGAS_TRY(staging(ctx, 2 * v, px * 4, &o8));
         }
         if (o32 && !is_device_pointer(o32)) {
-            host32[v] = o32;
-            uint8_t* p = nullptr;
-            TIGAS_TRY(staging(ctx, 2 * v + 1, px * 16, &p));
-            o32 = reinterpret_cast<float*>(p);
+            p.host32[v] = o32;
+            uint8_t* q = nullptr;
+            TIGAS_TRY(staging(ctx, 2 * v + 1, px * 16, &q));
+            o32 = reinterpret_cast<float*>(q);
         }
         req.views[v].out_rgba8 = o8;
         req.views[v].out_rgba_f32 = o32;
     }
-    FrameResult res;
     bool done = false;
-    const bool try_graph = sort_mode == TIGAS_SORT_SLICED && !dbg && g_use_graphs.load();
-    if (try_graph) TIGAS_TRY(render_sliced_graph(scene, req, ctx, st, &res, &done));
-    if (!done) TIGAS_TRY(render_frame(scene, req, ctx, st, &res));
+    const bool try_graph = sort_mode == TIGAS_SORT_SLICED && !want_q && g_use_graphs.load();
+    if (try_graph) TIGAS_TRY(render_sliced_graph(scene, req, ctx, st, &p.res, &done));
+    if (!done) TIGAS_TRY(render_frame(scene, req, ctx, st, &p.res));
     for (int v = 0; v < V; ++v) {
         const size_t px = (size_t)ws[v] * hs[v];
-        if (host8[v])
-            TIGAS_CUDA_TRY(cudaMemcpyAsync(host8[v], req.views[v].out_rgba8, px * 4, cudaMemcpyDeviceToHost, st));
-        if (host32[v])
-            TIGAS_CUDA_TRY(cudaMemcpyAsync(host32[v], req.views[v].out_rgba_f32, px * 16, cudaMemcpyDeviceToHost, st));
+        if (p.host8[v])
+            TIGAS_CUDA_TRY(cudaMemcpyAsync(p.host8[v], req.views[v].out_rgba8, px * 4, cudaMemcpyDeviceToHost, st));
+        if (p.host32[v])
+            TIGAS_CUDA_TRY(
+                cudaMemcpyAsync(p.host32[v], req.views[v].out_rgba_f32, px * 16, cudaMemcpyDeviceToHost, st));
     }
-    TIGAS_CUDA_TRY(cudaStreamSynchronize(st));
+    return {};
+}
+
+// After the submitted work completed: timing, and an exact re-render when a
+// fixed-capacity launch set outgrew its pair buffers.
+Status finish_render(RenderContext& ctx, cudaStream_t st, PendingRender& p) {
+    FrameResult& res = p.res;
     collect_profile(ctx);
     if (res.graph_slices > 0) {
         if (ctx.h_flags[0] & 1u) {
@@ -146,14 +161,15 @@ Status do_render(Scene* scene, int V, const tigas_pose* poses, const tigas_intri
             else
                 drop_graphs(ctx);
             g_exact_rerenders.fetch_add(1, std::memory_order_relaxed);
-            TIGAS_TRY(render_frame(scene, req, ctx, st, &res));
-            for (int v = 0; v < V; ++v) {
-                const size_t px = (size_t)ws[v] * hs[v];
-                if (host8[v])
-                    TIGAS_CUDA_TRY(cudaMemcpyAsync(host8[v], req.views[v].out_rgba8, px * 4, cudaMemcpyDeviceToHost, st));
-                if (host32[v])
+            TIGAS_TRY(render_frame(p.scene, p.req, ctx, st, &res));
+            for (int v = 0; v < p.V; ++v) {
+                const size_t px = (size_t)p.ws[v] * p.hs[v];
+                if (p.host8[v])
                     TIGAS_CUDA_TRY(
-                        cudaMemcpyAsync(host32[v], req.views[v].out_rgba_f32, px * 16, cudaMemcpyDeviceToHost, st));
+                        cudaMemcpyAsync(p.host8[v], p.req.views[v].out_rgba8, px * 4, cudaMemcpyDeviceToHost, st));
+                if (p.host32[v])
+                    TIGAS_CUDA_TRY(cudaMemcpyAsync(p.host32[v], p.req.views[v].out_rgba_f32, px * 16,
+                                                   cudaMemcpyDeviceToHost, st));
             }
             TIGAS_CUDA_TRY(cudaStreamSynchronize(st));
             collect_profile(ctx);
@@ -164,13 +180,37 @@ Status do_render(Scene* scene, int V, const tigas_pose* poses, const tigas_intri
                 mx = ctx.h_total[i] > mx ? ctx.h_total[i] : mx;
             }
             res.pairs = P;
-            const double scale = pair_scale(scene, req);
+            const double scale = pair_scale(p.scene, p.req);
             if (scale > 0.0 && (double)mx / scale > ctx.slice_ratio) ctx.slice_ratio = (double)mx / scale;
         }
     }
     if (ctx.h_flags[0] & 1u) return {TIGAS_ERR_OVERFLOW, "pair buffer overflow"};
     if (ctx.h_flags[0] & 2u) return {TIGAS_ERR_CUDA, "tile id out of range in sorted keys"};
     if (ctx.h_flags[0] & 16u) return {TIGAS_ERR_TIMEOUT, "radix sort look-back wait ran out"};
+    return {};
+}
+
+// Render V views synchronously; outputs may be host or device.
+Status do_render(Scene* scene, int V, const tigas_pose* poses, const tigas_intrinsics* intrs, const int* ws,
+                 const int* hs, uint8_t* const* outs8, float* const* outs32, cudaStream_t user_st, int sort_mode,
+                 tigas_frame_stats* stats, tigas_debug_frame* dbg, uint64_t* dbg_pairs) {
+    if (dbg && sort_mode == TIGAS_SORT_SLICED && (dbg->values || dbg->ranges))
+        return {TIGAS_ERR_INVALID, "the sliced schedule builds no whole tile lists: pass values = ranges = NULL"};
+    if (!scene) return {TIGAS_ERR_INVALID, "null scene"};
+    if (V < 1 || V > kMaxViews) return {TIGAS_ERR_INVALID, "n_views out of 1..64"};
+    for (int v = 0; v < V; ++v) TIGAS_TRY(validate_view(&poses[v], &intrs[v], ws[v], hs[v]));
+    Status err;
+    ContextGuard g;
+    g.ctx = acquire_context(&err);
+    if (!g.ctx) return err;
+    RenderContext& ctx = *g.ctx;
+    cudaStream_t st = user_st ? user_st : ctx.stream;
+    PendingRender p;
+    TIGAS_TRY(submit_render(ctx, scene, V, poses, intrs, ws, hs, outs8, outs32, st, sort_mode, stats != nullptr,
+                            dbg != nullptr, p));
+    TIGAS_CUDA_TRY(cudaStreamSynchronize(st));
+    TIGAS_TRY(finish_render(ctx, st, p));
+    FrameResult& res = p.res;
 
     if (stats) {
         uint32_t vis[kMaxViews];
@@ -514,6 +554,67 @@ TIGAS_API tigas_status tigas_render_batch_ex(tigas_scene* scene, int n_views, co
     Status st = do_render(sg.s, n_views, poses, intrs, widths, heights, outs, nullptr, (cudaStream_t)cuda_stream,
                           sort_mode, stats, nullptr, nullptr);
     return st.ok() ? TIGAS_OK : fail(st);
+}
+
+struct tigas_ticket {
+    RenderContext* ctx = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t submitted = nullptr;
+    PendingRender p;
+};
+
+TIGAS_API tigas_status tigas_render_batch_async(tigas_scene* scene, int n_views, const tigas_pose* poses,
+                                                const tigas_intrinsics* intrs, const int* widths, const int* heights,
+                                                uint8_t* const* outs, void* cuda_stream, tigas_ticket** out_ticket) {
+    set_error("");
+    if (!out_ticket) return fail(TIGAS_ERR_INVALID, "null ticket output");
+    *out_ticket = nullptr;
+    if (!scene || !poses || !intrs || !widths || !heights || !outs) return fail(TIGAS_ERR_INVALID, "null argument");
+    if (n_views < 1 || n_views > kMaxViews) return fail(TIGAS_ERR_INVALID, "n_views out of 1..64");
+    for (int v = 0; v < n_views; ++v)
+        if (!outs[v] || !is_device_pointer(outs[v]))
+            return fail(TIGAS_ERR_INVALID, "asynchronous outputs must be device memory");
+    Status err;
+    RenderContext* ctx = acquire_context(&err);
+    if (!ctx) return fail(err);
+    auto* t = new tigas_ticket();
+    t->ctx = ctx;
+    t->st = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+    Scene* sc = reinterpret_cast<Scene*>(scene);
+    scene_acquire(sc);
+    t->p.scene = sc;
+    Status s = submit_render(*ctx, sc, n_views, poses, intrs, widths, heights, outs, nullptr, t->st,
+                             TIGAS_SORT_SLICED, false, false, t->p);
+    if (s.ok()) {
+        cudaError_t e = cudaEventCreateWithFlags(&t->submitted, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(t->submitted, t->st);
+        if (e != cudaSuccess) s = {TIGAS_ERR_CUDA, cudaGetErrorString(e)};
+    }
+    if (!s.ok()) {
+        cudaStreamSynchronize(t->st);   // nothing of this launch set may still use the context
+        if (t->submitted) cudaEventDestroy(t->submitted);
+        scene_release(sc);
+        release_context(ctx);
+        delete t;
+        return fail(s);
+    }
+    *out_ticket = t;
+    return TIGAS_OK;
+}
+
+TIGAS_API tigas_status tigas_render_wait(tigas_ticket* t) {
+    set_error("");
+    if (!t) return fail(TIGAS_ERR_INVALID, "null ticket");
+    Status s;
+    cudaError_t e = cudaEventSynchronize(t->submitted);
+    if (e != cudaSuccess) s = {TIGAS_ERR_CUDA, cudaGetErrorString(e)};
+    if (s.ok()) s = finish_render(*t->ctx, t->st, t->p);
+    if (!s.ok()) cudaStreamSynchronize(t->st);
+    cudaEventDestroy(t->submitted);
+    scene_release(t->p.scene);
+    release_context(t->ctx);
+    delete t;
+    return s.ok() ? TIGAS_OK : fail(s);
 }
 
 TIGAS_API tigas_status tigas_debug_render(tigas_scene* scene, const tigas_pose* pose, const tigas_intrinsics* intr,

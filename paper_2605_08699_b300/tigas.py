@@ -33,7 +33,8 @@ EXPORTS = ["tigas_scene_load", "tigas_scene_free", "tigas_scene_bytes", "tigas_r
            "tigas_registry_open", "tigas_registry_scan", "tigas_registry_count", "tigas_registry_info",
            "tigas_registry_acquire", "tigas_registry_release", "tigas_registry_evict_idle",
            "tigas_registry_start_eviction", "tigas_registry_set_clock", "tigas_registry_close",
-           "tigas_resample_rgba8", "tigas_image_quality", "tigas_profile_stages"]
+           "tigas_resample_rgba8", "tigas_image_quality", "tigas_profile_stages", "tigas_render_batch_async",
+           "tigas_render_wait"]
 
 STAGES = ["preprocess", "depth_sort", "scan", "emit", "pair_sort", "ranges", "blend", "frame"]
 
@@ -128,6 +129,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "tigas_render_batch": (st, [P, i, ctypes.POINTER(Pose), ctypes.POINTER(Intrinsics), P, P, P, P]),
         "tigas_render_batch_ex": (st, [P, i, ctypes.POINTER(Pose), ctypes.POINTER(Intrinsics), P, P, P, P, i,
                                        ctypes.POINTER(FrameStats)]),
+        "tigas_render_batch_async": (st, [P, i, ctypes.POINTER(Pose), ctypes.POINTER(Intrinsics), P, P, P, P,
+                                          ctypes.POINTER(P)]),
+        "tigas_render_wait": (st, [P]),
         "tigas_debug_render": (st, [P, ctypes.POINTER(Pose), ctypes.POINTER(Intrinsics), i, i, i,
                                     ctypes.POINTER(DebugFrame), ctypes.POINTER(ctypes.c_uint64)]),
         "tigas_sort_pairs_u64": (st, [P, P, P, P, ctypes.c_uint64, i, i, P]),
@@ -533,6 +537,36 @@ def render_batch(scene: SceneHandle, poses: Sequence, intrs: Sequence, widths: S
                                              ctypes.cast(H, ctypes.c_void_p), ctypes.cast(O, ctypes.c_void_p),
                                              _stream(stream)))
     return None
+
+
+class RenderTicket:
+    """An enqueued launch set (tigas_render_batch_async); wait() completes it."""
+
+    def __init__(self, handle: int, keep):
+        self.handle = handle
+        self._keep = keep   # the output tensors stay referenced until the wait
+
+    def wait(self) -> None:
+        if self.handle:
+            h, self.handle = self.handle, None
+            self._keep = None
+            _check(load_library().tigas_render_wait(h))
+
+
+def render_batch_async(scene: SceneHandle, poses: Sequence, intrs: Sequence, widths: Sequence[int],
+                       heights: Sequence[int], outs: Sequence, stream=None) -> RenderTicket:
+    """tigas_render_batch_async: enqueue one launch set (device outputs only)."""
+    V = len(poses)
+    P = (Pose * V)(*[make_pose(p) for p in poses])
+    K = (Intrinsics * V)(*[make_intrinsics(k) for k in intrs])
+    W = (ctypes.c_int * V)(*widths)
+    H = (ctypes.c_int * V)(*heights)
+    O = (ctypes.c_void_p * V)(*[_ptr(o) for o in outs])
+    t = ctypes.c_void_p()
+    _check(load_library().tigas_render_batch_async(scene.handle, V, P, K, ctypes.cast(W, ctypes.c_void_p),
+                                                   ctypes.cast(H, ctypes.c_void_p), ctypes.cast(O, ctypes.c_void_p),
+                                                   _stream(stream), ctypes.byref(t)))
+    return RenderTicket(t.value, list(outs))
 
 
 def set_schedule(n_slices: int = 8, first_slice_inv: int = 64, blend_ctas_per_sm: int = 0) -> None:

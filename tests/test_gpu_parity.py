@@ -336,6 +336,41 @@ def test_graph_overflow_falls_back_to_exact(cuda, s1):
     assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[0], got2[0])
 
 
+def test_async_launch_sets_equal_synchronous_ones(cuda, s1):
+    """Tickets kept in flight (the next launch set queued before the previous
+    one is waited on) give the synchronous frames, also when a replayed launch
+    set outgrows its captured capacity (far poses captured, then near ones)."""
+    levels = [(320, 240), (160, 120)]
+    far = [synth.Pose(0.0, 0.0, (0.0, 0.0, -12.0)), synth.Pose(0.2, 0.0, (0.0, 0.0, -11.0))]
+    near = [synth.Pose(0.1, 0.05, (0.0, 0.0, -2.2)), synth.Pose(-0.1, 0.0, (0.1, 0.0, -2.4))]
+    seq = [far, far, far, near, near, far, near] + [list(synth.trajectory(95 + k, 2)) for k in range(6)]
+    intrs = [synth.default_intrinsics(w, h) for w, h in levels]
+    with tg.scene_from(s1) as h:
+        tg.set_graphs(False)
+        want = [_batch(h, poses, levels, cuda) for poses in seq]
+        tg.set_graphs(True)
+        bufs = [[torch.empty((hh, w, 4), dtype=torch.uint8, device=cuda) for w, hh in levels] for _ in range(2)]
+        stream = torch.cuda.Stream()
+        got = []
+        prev = None
+        for k, poses in enumerate(seq):
+            t = tg.render_batch_async(h, poses, intrs, [w for w, _ in levels], [hh for _, hh in levels],
+                                      bufs[k % 2], stream=stream)
+            if prev is not None:
+                prev[0].wait()
+                got.append([o.cpu().numpy() for o in prev[1]])
+            prev = (t, bufs[k % 2])
+        prev[0].wait()
+        got.append([o.cpu().numpy() for o in prev[1]])
+        with pytest.raises(tg.TigasError) as e:   # host outputs are refused
+            tg.render_batch_async(h, near[:1], intrs[:1], [320], [240], [np.zeros((240, 320, 4), np.uint8)])
+        assert e.value.status == tg.ERR_INVALID
+    assert len(got) == len(want)
+    for w_set, g_set in zip(want, got):
+        for a, b in zip(w_set, g_set):
+            assert np.array_equal(a, b)
+
+
 def test_direct_fixed_capacity_overflow_renders_exactly(cuda, s1):
     # the capacity learned on a far pose is far too small for a new shape on a
     # near pose: the direct launch set overflows and the frame is rendered exactly
