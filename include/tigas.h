@@ -168,14 +168,16 @@ tigas_status tigas_render_batch_ex(tigas_scene* scene, int n_views, const tigas_
 
 /* Asynchronous tigas_render_batch (SLICED schedule): enqueue the launch set on
  * cuda_stream (NULL: the library's own stream) and return at once with a
- * ticket; outputs must be device memory.  tigas_render_wait completes it:
+ * ticket.  Host outputs (pinned, for the call to stay asynchronous) are
+ * copied back on a copy stream of the ticket's own, which overlaps the
+ * copies with later launch sets.  tigas_render_wait completes it:
  * waits for the launch set, and if a fixed-capacity launch set outgrew its
  * pair buffers renders it again exactly before returning (the frames are
  * final only then).  Each outstanding ticket holds its own render context,
  * so a caller can keep the next launch set queued behind the current one;
  * output buffers of a ticket must not be reused before its wait returns.
  * Every ticket must be waited on exactly once.  Errors: as
- * tigas_render_batch; INVALID for host outputs. */
+ * tigas_render_batch. */
 typedef struct tigas_ticket tigas_ticket;
 tigas_status tigas_render_batch_async(tigas_scene* scene, int n_views, const tigas_pose* poses,
                                       const tigas_intrinsics* intrs, const int* widths, const int* heights,

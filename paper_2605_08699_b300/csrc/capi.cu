@@ -89,9 +89,11 @@ struct PendingRender {
 
 // Validate and enqueue V views on st (host outputs go through device staging
 // and are copied back on st).  Returns with the work in flight.
+// copy_st: stream for the device-to-host copies of host outputs (it waits for
+// the launch set; null: st itself).
 Status submit_render(RenderContext& ctx, Scene* scene, int V, const tigas_pose* poses, const tigas_intrinsics* intrs,
                      const int* ws, const int* hs, uint8_t* const* outs8, float* const* outs32, cudaStream_t st,
-                     int sort_mode, bool want_stats, bool want_q, PendingRender& p) {
+                     int sort_mode, bool want_stats, bool want_q, PendingRender& p, cudaStream_t copy_st = nullptr) {
     if (!scene) return {TIGAS_ERR_INVALID, "null scene"};
     if (V < 1 || V > kMaxViews) return {TIGAS_ERR_INVALID, "n_views out of 1..64"};
     if (sort_mode != TIGAS_SORT_DEPTH_FIRST && sort_mode != TIGAS_SORT_FULL64 && sort_mode != TIGAS_SORT_SLICED)
@@ -135,13 +137,19 @@ Status submit_render(RenderContext& ctx, Scene* scene, int V, const tigas_pose* 
     const bool try_graph = sort_mode == TIGAS_SORT_SLICED && !want_q && g_use_graphs.load();
     if (try_graph) TIGAS_TRY(render_sliced_graph(scene, req, ctx, st, &p.res, &done));
     if (!done) TIGAS_TRY(render_frame(scene, req, ctx, st, &p.res));
+    cudaStream_t cs = st;
+    if (copy_st) {
+        TIGAS_CUDA_TRY(cudaEventRecord(ctx.ev_rendered, st));
+        TIGAS_CUDA_TRY(cudaStreamWaitEvent(copy_st, ctx.ev_rendered, 0));
+        cs = copy_st;
+    }
     for (int v = 0; v < V; ++v) {
         const size_t px = (size_t)ws[v] * hs[v];
         if (p.host8[v])
-            TIGAS_CUDA_TRY(cudaMemcpyAsync(p.host8[v], req.views[v].out_rgba8, px * 4, cudaMemcpyDeviceToHost, st));
+            TIGAS_CUDA_TRY(cudaMemcpyAsync(p.host8[v], req.views[v].out_rgba8, px * 4, cudaMemcpyDeviceToHost, cs));
         if (p.host32[v])
             TIGAS_CUDA_TRY(
-                cudaMemcpyAsync(p.host32[v], req.views[v].out_rgba_f32, px * 16, cudaMemcpyDeviceToHost, st));
+                cudaMemcpyAsync(p.host32[v], req.views[v].out_rgba_f32, px * 16, cudaMemcpyDeviceToHost, cs));
     }
     return {};
 }
@@ -572,8 +580,7 @@ TIGAS_API tigas_status tigas_render_batch_async(tigas_scene* scene, int n_views,
     if (!scene || !poses || !intrs || !widths || !heights || !outs) return fail(TIGAS_ERR_INVALID, "null argument");
     if (n_views < 1 || n_views > kMaxViews) return fail(TIGAS_ERR_INVALID, "n_views out of 1..64");
     for (int v = 0; v < n_views; ++v)
-        if (!outs[v] || !is_device_pointer(outs[v]))
-            return fail(TIGAS_ERR_INVALID, "asynchronous outputs must be device memory");
+        if (!outs[v]) return fail(TIGAS_ERR_INVALID, "null output buffer");
     Status err;
     RenderContext* ctx = acquire_context(&err);
     if (!ctx) return fail(err);
@@ -583,15 +590,18 @@ TIGAS_API tigas_status tigas_render_batch_async(tigas_scene* scene, int n_views,
     Scene* sc = reinterpret_cast<Scene*>(scene);
     scene_acquire(sc);
     t->p.scene = sc;
+    // host outputs are copied back on the context's copy stream, so the copies
+    // of this launch set overlap the next one's device work
     Status s = submit_render(*ctx, sc, n_views, poses, intrs, widths, heights, outs, nullptr, t->st,
-                             TIGAS_SORT_SLICED, false, false, t->p);
+                             TIGAS_SORT_SLICED, false, false, t->p, ctx->copy_stream);
     if (s.ok()) {
         cudaError_t e = cudaEventCreateWithFlags(&t->submitted, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventRecord(t->submitted, t->st);
+        if (e == cudaSuccess) e = cudaEventRecord(t->submitted, ctx->copy_stream);
         if (e != cudaSuccess) s = {TIGAS_ERR_CUDA, cudaGetErrorString(e)};
     }
     if (!s.ok()) {
         cudaStreamSynchronize(t->st);   // nothing of this launch set may still use the context
+        cudaStreamSynchronize(ctx->copy_stream);
         if (t->submitted) cudaEventDestroy(t->submitted);
         scene_release(sc);
         release_context(ctx);
@@ -609,7 +619,10 @@ TIGAS_API tigas_status tigas_render_wait(tigas_ticket* t) {
     cudaError_t e = cudaEventSynchronize(t->submitted);
     if (e != cudaSuccess) s = {TIGAS_ERR_CUDA, cudaGetErrorString(e)};
     if (s.ok()) s = finish_render(*t->ctx, t->st, t->p);
-    if (!s.ok()) cudaStreamSynchronize(t->st);
+    if (!s.ok()) {
+        cudaStreamSynchronize(t->st);
+        cudaStreamSynchronize(t->ctx->copy_stream);
+    }
     cudaEventDestroy(t->submitted);
     scene_release(t->p.scene);
     release_context(t->ctx);

@@ -156,6 +156,8 @@ ViewParams make_view(const tigas_pose& pose, const tigas_intrinsics& k, int widt
 
 Status RenderContext::init() {
     TIGAS_CUDA_TRY(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+    TIGAS_CUDA_TRY(cudaStreamCreateWithFlags(&copy_stream, cudaStreamNonBlocking));
+    TIGAS_CUDA_TRY(cudaEventCreateWithFlags(&ev_rendered, cudaEventDisableTiming));
     TIGAS_CUDA_TRY(cudaMallocHost(&h_total, sizeof(uint64_t) * (kMaxSlices + 2)));
     TIGAS_CUDA_TRY(cudaMallocHost(&h_flags, sizeof(uint32_t) * 2));
     TIGAS_CUDA_TRY(cudaMallocHost(&h_views, (sizeof(ViewParams) + sizeof(uint64_t)) * kMaxViews));
@@ -183,6 +185,10 @@ void RenderContext::destroy() {
     if (h_flags) cudaFreeHost(h_flags);
     if (h_views) cudaFreeHost(h_views);
     if (stream) cudaStreamDestroy(stream);
+    if (copy_stream) cudaStreamDestroy(copy_stream);
+    if (ev_rendered) cudaEventDestroy(ev_rendered);
+    copy_stream = nullptr;
+    ev_rendered = nullptr;
     for (int k = 0; k < kNumStages; ++k)
         for (int r = 0; r < kMaxSlices; ++r) {
             if (ev_start[k][r]) cudaEventDestroy(ev_start[k][r]);

@@ -127,6 +127,8 @@ struct RenderContext {
     int ev_count[kNumStages] = {};     // start/stop pairs recorded per stage this frame
     uint32_t* h_misc = nullptr;        // pinned readback of per-view counts
     cudaStream_t stream = nullptr;     // own stream (used when the caller passes none)
+    cudaStream_t copy_stream = nullptr;  // device-to-host copies of asynchronous launch sets
+    cudaEvent_t ev_rendered = nullptr;   // end of a launch set's device work (copies wait on it)
     Arena fixed;                       // per-entry buffers
     Arena pairs;                       // per-pair buffers
     Arena jpeg;                        // frame encoder buffers

@@ -555,7 +555,8 @@ class RenderTicket:
 
 def render_batch_async(scene: SceneHandle, poses: Sequence, intrs: Sequence, widths: Sequence[int],
                        heights: Sequence[int], outs: Sequence, stream=None) -> RenderTicket:
-    """tigas_render_batch_async: enqueue one launch set (device outputs only)."""
+    """tigas_render_batch_async: enqueue one launch set (device outputs, or
+    pinned host outputs copied back on the ticket's copy stream)."""
     V = len(poses)
     P = (Pose * V)(*[make_pose(p) for p in poses])
     K = (Intrinsics * V)(*[make_intrinsics(k) for k in intrs])

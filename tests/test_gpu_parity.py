@@ -362,9 +362,15 @@ def test_async_launch_sets_equal_synchronous_ones(cuda, s1):
             prev = (t, bufs[k % 2])
         prev[0].wait()
         got.append([o.cpu().numpy() for o in prev[1]])
-        with pytest.raises(tg.TigasError) as e:   # host outputs are refused
-            tg.render_batch_async(h, near[:1], intrs[:1], [320], [240], [np.zeros((240, 320, 4), np.uint8)])
-        assert e.value.status == tg.ERR_INVALID
+        # pinned host outputs: copied back on the ticket's copy stream
+        hosts = [[torch.empty((hh, w, 4), dtype=torch.uint8).pin_memory() for w, hh in levels] for _ in range(2)]
+        tk = [tg.render_batch_async(h, seq[k], intrs, [w for w, _ in levels], [hh for _, hh in levels], hosts[i],
+                                    stream=stream) for i, k in enumerate((3, 4))]
+        for t in tk:
+            t.wait()
+        for k, hb in zip((3, 4), hosts):
+            for a, b in zip(want[k], hb):
+                assert np.array_equal(a, b.numpy())
     assert len(got) == len(want)
     for w_set, g_set in zip(want, got):
         for a, b in zip(w_set, g_set):
