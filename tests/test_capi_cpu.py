@@ -103,3 +103,39 @@ def test_schedule_set_get_and_range_checks():
         assert tg.get_schedule()["n_slices"] == 12   # a rejected call changes nothing
     finally:
         tg.set_schedule(**before)
+
+
+def test_profile_stage_mask_checks(lib):
+    assert _status("tigas_profile_stages", ctypes.c_uint32(1 << 7)) == tb.ERR_INVALID
+    assert _status("tigas_profile_stages", ctypes.c_uint32(0xFFFFFFFF)) == tb.ERR_INVALID
+    tg.profile_stages(["blend", "preprocess"])
+    tg.profile_stages([])
+    tg.profile_enable(False)
+    with pytest.raises(ValueError):
+        tg.profile_stages(["no_such_stage"])
+
+
+def test_async_and_quality_arguments_rejected_without_gpu(lib):
+    pose = tb.Pose(0.0, 0.0, (ctypes.c_double * 3)(0, 0, -3))
+    k = tb.Intrinsics(100, 100, 50, 50)
+    w = (ctypes.c_int * 1)(4)
+    t = ctypes.c_void_p()
+    outs = (ctypes.c_void_p * 1)(None)
+    # null scene, null ticket output, null output buffer, n_views out of range, null ticket
+    assert _status("tigas_render_batch_async", None, 1, ctypes.byref(pose), ctypes.byref(k), w, w, outs, None,
+                   ctypes.byref(t)) == tb.ERR_INVALID
+    assert _status("tigas_render_batch_async", None, 1, ctypes.byref(pose), ctypes.byref(k), w, w, outs, None,
+                   None) == tb.ERR_INVALID
+    assert _status("tigas_render_batch_async", ctypes.c_void_p(1), 0, ctypes.byref(pose), ctypes.byref(k), w, w,
+                   outs, None, ctypes.byref(t)) == tb.ERR_INVALID
+    assert _status("tigas_render_batch_async", ctypes.c_void_p(1), 1, ctypes.byref(pose), ctypes.byref(k), w, w,
+                   outs, None, ctypes.byref(t)) == tb.ERR_INVALID
+    assert _status("tigas_render_wait", None) == tb.ERR_INVALID
+    assert _status("tigas_ply_probe", None, None) == tb.ERR_INVALID
+    assert _status("tigas_ply_decode", None, None, None, None, None, None, 0) == tb.ERR_INVALID
+    assert _status("tigas_scene_load_ply", None, 0, None, None) == tb.ERR_INVALID
+    for name in ("tigas_registry_scan", "tigas_registry_evict_idle"):
+        assert _status(name, None, None, None) == tb.ERR_INVALID if name == "tigas_registry_scan" else \
+            _status(name, None, None) == tb.ERR_INVALID
+    assert _status("tigas_registry_close", None) == tb.ERR_INVALID
+    assert _status("tigas_registry_set_clock", None, ctypes.c_double(1.0)) == tb.ERR_INVALID
