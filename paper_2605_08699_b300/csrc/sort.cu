@@ -406,21 +406,42 @@ constexpr uint32_t kSortTimeoutFlag = 16u;
 // Tile shape of a scatter pass: T threads x I keys.  With an 8-byte payload a
 // CTA takes half the keys so that keys, values and payloads still fit two CTAs
 // per SM.
-template <typename K, bool PAY>
+// Payload modes of the one-sweep passes: kPayNone, kPayWithValues (an 8-byte
+// payload and the 4-byte values), kPayOnly (the payload identifies each key:
+// no value stream, and no value staging in shared memory).
+constexpr int kPayNone = 0, kPayWithValues = 1, kPayOnly = 2;
+template <typename K, int PAY>
 struct OsCfg;
 #ifndef TIGAS_OS_THREADS
-#define TIGAS_OS_THREADS 512
+#define TIGAS_OS_THREADS 384
 #endif
 #ifndef TIGAS_OS_ITEMS
-#define TIGAS_OS_ITEMS 16
+#define TIGAS_OS_ITEMS 12
 #endif
-template <bool PAY>
+#ifndef TIGAS_OS_PAY_THREADS
+#define TIGAS_OS_PAY_THREADS 384
+#endif
+#ifndef TIGAS_OS_PAY_ITEMS
+#define TIGAS_OS_PAY_ITEMS 12
+#endif
+#ifndef TIGAS_OS_PAY_BLOCKS
+#define TIGAS_OS_PAY_BLOCKS 3
+#endif
+#ifndef TIGAS_OS_BLOCKS
+#define TIGAS_OS_BLOCKS 3   // CTAs per SM of the keys-and-values tile (0: (2 x 512) / threads)
+#endif
+template <int PAY>
 struct OsCfg<uint32_t, PAY> {
-    // 2 CTAs of 512 threads per SM (<= 64 registers); keys per thread halved with a payload
-    static constexpr int kT = PAY ? 512 : TIGAS_OS_THREADS, kI = PAY ? 8 : TIGAS_OS_ITEMS;
-    static constexpr int kMinBlocks = (2 * 512) / kT;
+    // Keys and values: 3 CTAs of 384 x 12 per SM (measured ahead of 512 x 16 x 2 and
+    // 384 x 16 x 3 on the pair sorts).  Keys, values and payload: 2 CTAs of 512 x 8.
+    // Payload only: without staged values a 384 x 12 tile fits 3 CTAs per SM (measured
+    // fastest of 256 x 16 x {2, 3}, 384 x 12 x 3 and 512 x 8 x 2 on the 24M-entry depth sort).
+    static constexpr int kT = PAY == kPayOnly ? TIGAS_OS_PAY_THREADS : PAY ? 512 : TIGAS_OS_THREADS;
+    static constexpr int kI = PAY == kPayOnly ? TIGAS_OS_PAY_ITEMS : PAY ? 8 : TIGAS_OS_ITEMS;
+    static constexpr int kMinBlocks = PAY == kPayOnly ? TIGAS_OS_PAY_BLOCKS
+                                      : (TIGAS_OS_BLOCKS > 0 && !PAY) ? TIGAS_OS_BLOCKS : (2 * 512) / kT;
 };
-template <bool PAY>
+template <int PAY>
 struct OsCfg<uint64_t, PAY> {
     static_assert(!PAY, "payloads are carried by 32-bit key sorts only");
     static constexpr int kT = 256, kI = 16, kMinBlocks = 2;
@@ -631,11 +652,11 @@ __global__ void __launch_bounds__(256) k_os_bases(const uint32_t* __restrict__ g
     }
 }
 
-template <typename K, bool PAY>
+template <typename K, int PAY>
 struct OsSmem {
     static constexpr int T = OsCfg<K, PAY>::kT, I = OsCfg<K, PAY>::kI, N = T * I, W = T / 32;
     K keys[N];
-    uint32_t vals[N];
+    uint32_t vals[PAY == kPayOnly ? 1 : N];
     uint2 pays[PAY ? N : 1];
     uint32_t whist[W][256];
     uint32_t dstart[256];
@@ -644,7 +665,7 @@ struct OsSmem {
     uint32_t chunk;
 };
 
-template <typename K, bool PAY, bool MAP>
+template <typename K, int PAY, bool MAP>
 __global__ void __launch_bounds__(OsCfg<K, PAY>::kT, OsCfg<K, PAY>::kMinBlocks)
 k_os_scatter(const OsRoute* __restrict__ route, uint64_t n_cap, const uint64_t* d_n, int shift, int nbits,
              const uint32_t* __restrict__ gbase, uint32_t* status, uint32_t* chunk_counter, uint32_t* flags,
@@ -656,7 +677,7 @@ k_os_scatter(const OsRoute* __restrict__ route, uint64_t n_cap, const uint64_t* 
     K* __restrict__ keys_out = static_cast<K*>(route->dst_k);
     uint32_t* __restrict__ vals_out = route->dst_v;
     uint2* __restrict__ pays_out = route->dst_p;
-    const bool has_vals = vals_out != nullptr;   // no value stream: the payload identifies each key
+    const bool has_vals = PAY != kPayOnly && vals_out != nullptr;   // no value stream: the payload identifies each key
     const uint32_t mask = (1u << nbits) - 1u;
     constexpr int T = OsCfg<K, PAY>::kT, I = OsCfg<K, PAY>::kI, N = T * I, W = T / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -797,7 +818,7 @@ k_os_scatter(const OsRoute* __restrict__ route, uint64_t n_cap, const uint64_t* 
     }
 }
 
-template <typename K, bool PAY, bool MAP>
+template <typename K, int PAY, bool MAP>
 Status ensure_os_smem() {
     static std::atomic<bool> done{false};
     if (done.load()) return {};
@@ -818,7 +839,7 @@ uint64_t os_chunks(uint64_t n_cap) { return (n_cap + 4095) / 4096; }   // upper 
 constexpr size_t kOsHead = (8 * 256 * 2 + 16 + 8 * kRouteWords + 3) / 4 * 4;
 size_t os_tmp_words(uint64_t n_cap) { return kOsHead + 8 * os_chunks(n_cap) * 256; }
 
-template <typename K, bool PAY, bool MAP>
+template <typename K, int PAY, bool MAP>
 Status radix_sort_onesweep(const K* keys_in, const uint32_t* values_in, K* keys_alt, uint32_t* values_alt,
                            K* keys_out, uint32_t* values_out, uint64_t n_cap, const uint64_t* d_n, int begin_bit,
                            int end_bit, uint32_t* tmp, cudaStream_t st, uint32_t* flags, const SortExtras* ex) {
@@ -867,10 +888,10 @@ Status radix_sort_onesweep(const K* keys_in, const uint32_t* values_in, K* keys_
 // of both chunks, so every scattered position is below 2N.
 Status debug_lookback_timeout(int spin_limit, bool* timed_out) {
     using K = uint32_t;
-    constexpr int T = OsCfg<K, false>::kT, N = OsCfg<K, false>::kT * OsCfg<K, false>::kI;
+    constexpr int T = OsCfg<K, kPayNone>::kT, N = OsCfg<K, kPayNone>::kT * OsCfg<K, kPayNone>::kI;
     *timed_out = false;
     if (spin_limit < 1 || spin_limit > (1 << 20)) return {TIGAS_ERR_INVALID, "spin limit out of 1..2^20"};
-    TIGAS_TRY((ensure_os_smem<K, false, false>()));
+    TIGAS_TRY((ensure_os_smem<K, kPayNone, false>()));
     const uint64_t n = 2 * (uint64_t)N;
     const size_t route_words = 2 * kRouteWords;
     const size_t words = 2 * n + 256 + 256 + 2 * 256 + 8 + route_words;
@@ -896,7 +917,7 @@ Status debug_lookback_timeout(int spin_limit, bool* timed_out) {
         OsBuffers bufs{keys, nullptr, nullptr, out, sorted_vals, nullptr, out, sorted_vals, nullptr};
         k_os_hist<K><<<4, 512>>>(keys, n, nullptr, 0, 8, ghist, nullptr, nullptr, 0);
         k_os_bases<<<1, 256>>>(ghist, gbase, 1, route, bufs, nullptr);
-        k_os_scatter<K, false, false><<<1, T, sizeof(OsSmem<K, false>)>>>(route, n, nullptr, 0, 8, gbase, status,
+        k_os_scatter<K, kPayNone, false><<<1, T, sizeof(OsSmem<K, kPayNone>)>>>(route, n, nullptr, 0, 8, gbase, status,
                                                                           misc, misc + 1, spin_limit, nullptr);
         g_launches.fetch_add(3, std::memory_order_relaxed);
         e = cudaGetLastError();
@@ -943,21 +964,30 @@ Status radix_sort(const K* keys_in, const uint32_t* values_in, K* keys_alt, uint
     if (n_cap < (1ull << 30)) {
         if constexpr (sizeof(K) == 4) {
             const bool map = ex && ex->key_range;
+            if (pay && !values_out) {
+                if (map)
+                    return radix_sort_onesweep<K, kPayOnly, true>(keys_in, values_in, keys_alt, values_alt, keys_out,
+                                                                  values_out, n_cap, d_n, begin_bit, end_bit, tmp,
+                                                                  st, flags, ex);
+                return radix_sort_onesweep<K, kPayOnly, false>(keys_in, values_in, keys_alt, values_alt, keys_out,
+                                                               values_out, n_cap, d_n, begin_bit, end_bit, tmp, st,
+                                                               flags, ex);
+            }
             if (pay && map)
-                return radix_sort_onesweep<K, true, true>(keys_in, values_in, keys_alt, values_alt, keys_out,
-                                                          values_out, n_cap, d_n, begin_bit, end_bit, tmp, st, flags,
-                                                          ex);
+                return radix_sort_onesweep<K, kPayWithValues, true>(keys_in, values_in, keys_alt, values_alt,
+                                                                    keys_out, values_out, n_cap, d_n, begin_bit,
+                                                                    end_bit, tmp, st, flags, ex);
             if (pay)
-                return radix_sort_onesweep<K, true, false>(keys_in, values_in, keys_alt, values_alt, keys_out,
-                                                           values_out, n_cap, d_n, begin_bit, end_bit, tmp, st,
-                                                           flags, ex);
+                return radix_sort_onesweep<K, kPayWithValues, false>(keys_in, values_in, keys_alt, values_alt,
+                                                                     keys_out, values_out, n_cap, d_n, begin_bit,
+                                                                     end_bit, tmp, st, flags, ex);
             if (map)
-                return radix_sort_onesweep<K, false, true>(keys_in, values_in, keys_alt, values_alt, keys_out,
-                                                           values_out, n_cap, d_n, begin_bit, end_bit, tmp, st,
-                                                           flags, ex);
+                return radix_sort_onesweep<K, kPayNone, true>(keys_in, values_in, keys_alt, values_alt, keys_out,
+                                                              values_out, n_cap, d_n, begin_bit, end_bit, tmp, st,
+                                                              flags, ex);
         }
-        return radix_sort_onesweep<K, false, false>(keys_in, values_in, keys_alt, values_alt, keys_out, values_out,
-                                                    n_cap, d_n, begin_bit, end_bit, tmp, st, flags, ex);
+        return radix_sort_onesweep<K, kPayNone, false>(keys_in, values_in, keys_alt, values_alt, keys_out,
+                                                       values_out, n_cap, d_n, begin_bit, end_bit, tmp, st, flags, ex);
     }
     if (ex) return {TIGAS_ERR_INVALID, "key range and payload need fewer than 2^30 keys"};
     return radix_sort_rts<K>(keys_in, values_in, keys_alt, values_alt, keys_out, values_out, n_cap, d_n, begin_bit,
