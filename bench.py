@@ -162,6 +162,27 @@ def cpu_baseline(scene, poses, width, height, budget_s: float = 15.0) -> dict:
 # ---------------------------------------------------------------- roofline
 
 
+# DRAM bytes (read + write) of the dominant kernel per view of a launch set, from one ncu capture of
+# the same kernel source (all six slices of a 4-view 1080p launch set of the 3M-Gaussian scene,
+# dram__bytes_read.sum + dram__bytes_write.sum; profiles/blend_ncu_3M_1080p.md), scaled by the
+# views a launch set renders.  Reported only while the kernel's source is the captured one.
+KERNEL_TRAFFIC = {
+    "blend": {"source": "paper_2605_08699_b300/csrc/blend.cu", "sha1": "cf11c8ca5e8779bffa49bf72c976818fb3d36520",
+              "bytes_per_view": 477_767_680 / 4},
+}
+
+
+def kernel_traffic(kernel: str, views: int):
+    import hashlib
+    t = KERNEL_TRAFFIC.get(kernel)
+    if not t:
+        return None
+    with open(os.path.join(ROOT, t["source"]), "rb") as f:
+        if hashlib.sha1(f.read()).hexdigest() != t["sha1"]:
+            return None   # the kernel changed since the counters were taken
+    return int(t["bytes_per_view"] * views)
+
+
 def roofline(stage_ms: dict, per_step: dict, peaks: dict, clocks: dict, steps: int,
              timed_stage_ms: dict | None = None) -> tuple[dict, dict]:
     """Achieved rate of every stage (stage_ms: a pass with every stage timed) and
@@ -207,6 +228,7 @@ def roofline(stage_ms: dict, per_step: dict, peaks: dict, clocks: dict, steps: i
                             "frac": ach / hbm, "work": b}
     dom = max(stages, key=lambda k: stages[k]["ms"])
     d = dict(stages[dom])
+    traffic = kernel_traffic(dom, per_step.get("views", 0))
     timed = (timed_stage_ms or {}).get(dom)
     if timed and timed["calls"] > 0 and timed["ms"] > 0.0:
         ms = timed["ms"] / timed["calls"]
@@ -214,8 +236,10 @@ def roofline(stage_ms: dict, per_step: dict, peaks: dict, clocks: dict, steps: i
         d["frac"] = d["achieved"] / d["peak"]
         d["ms"] = ms
     roof = {"kernel": dom, "bound": d["bound"], "achieved": round(d["achieved"], 3), "peak": d["peak"],
-            "unit": d["unit"], "frac": round(d["frac"], 4), "traffic": None,
+            "unit": d["unit"], "frac": round(d["frac"], 4), "traffic": traffic,
             "ms_per_launch_set": round(d["ms"], 4),
+            "traffic_note": "DRAM bytes per launch set from an ncu capture of the same kernel source on 4 views, "
+                            "scaled to the launch set's views (null when the source changed)",
             "timing": "CUDA events around the kernel's launches inside the timed region, on its stream",
             "peak_source": f"{peaks['source']} ({'hbm_gbs' if d['bound'] == 'hbm' else 'SMs x 128 FP32 lanes x 2 x median SM clock'})",
             "share_of_frame": round(d["ms"] / max(1e-9, sum(s['ms'] for s in stages.values())), 4)}
@@ -300,7 +324,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
                 # rectangles travel compact (with their entry id, no value stream) when every view
                 # has at most 127 x 127 tiles and there are at most 16 views
                 "compact_rect": int(V <= 16 and W <= 127 * 16 and H <= 127 * 16),
-                "entries": V * scene.n, "gaussians": scene.n, "attr_bytes": 124, "tiles": V * TX * TY,
+                "entries": V * scene.n, "gaussians": scene.n, "attr_bytes": 124, "tiles": V * TX * TY, "views": V,
                 "slices": schedule["n_slices"]}
 
     # ---- timed region: device outputs, CUDA events on the launching stream
