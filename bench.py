@@ -198,7 +198,9 @@ def roofline(stage_ms: dict, per_step: dict, peaks: dict, clocks: dict, steps: i
                   + 8 B per emitted pair
       pair_sort   passes x 16 B per emitted pair
       ranges      8 B per tile per slice
-      blend       FP32 flops: 8.5 per list entry evaluated + 9 per blended entry"""
+      blend       FP32 flops: 14 per (pixel, list entry) evaluated until the pixel stops (the
+                  per-evaluation figure of the method: offsets, quadratic form, exponent, alpha
+                  cut-off and clamp; the ex2 is not counted)"""
     hbm = peaks["hbm_gbs"]
     mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
     fp32_peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
@@ -217,7 +219,7 @@ def roofline(stage_ms: dict, per_step: dict, peaks: dict, clocks: dict, steps: i
             continue
         ms = st["ms"] / st["calls"]
         if name == "blend":
-            fl = w["evals"] * 8.5 + w["contribs"] * 9.0
+            fl = w["evals"] * 14.0
             ach = fl / (ms * 1e-3) / 1e12
             stages[name] = {"ms": ms, "bound": "alu", "achieved": ach, "peak": fp32_peak_tflops,
                             "unit": "TFLOP/s", "frac": ach / fp32_peak_tflops, "work": fl}

@@ -383,8 +383,9 @@ Status jpeg_encode(RenderContext& ctx, const uint8_t* rgba, int W, int H, int qu
     TIGAS_CUDA_TRY(cudaMemsetAsync(d_lens + n_int, 0, 4, st));   // the scan's extra zero
     k_jpeg_mcu<<<n_mcu, 256, 0, st>>>(d_in, W, H, mw, d_tab, d_coef);
     TIGAS_LAUNCHED();
-    k_jpeg_entropy<<<(n_int + 127) / 128, 128, 0, st>>>(d_coef, n_mcu, restart, n_int, d_tab, d_slots, slot, d_lens,
-                                                      d_flags);
+    // one warp per CTA: the intervals (a few thousand per frame) spread over every SM
+    k_jpeg_entropy<<<(n_int + 31) / 32, 32, 0, st>>>(d_coef, n_mcu, restart, n_int, d_tab, d_slots, slot, d_lens,
+                                                    d_flags);
     TIGAS_LAUNCHED();
     TIGAS_TRY(launch_scan_u32(d_lens, nullptr, d_offs, (uint64_t)n_int + 1, d_total, d_tmp, st));
     // entropy-coded data: straight into the caller's device buffer behind the header, or staged
