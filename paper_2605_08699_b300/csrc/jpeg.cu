@@ -313,6 +313,153 @@ k_jpeg_entropy(const int16_t* __restrict__ coef, int n_mcu, int restart, int n_i
     if (o.over) atomicOr(flags, 1u);
 }
 
+// One warp per restart interval (intervals of at most kWarpMaxMcu MCUs): the
+// same bytes as k_jpeg_entropy.  Per block, lane l takes zig-zag coefficients
+// 2l and 2l + 1; a warp max-scan finds each nonzero coefficient's preceding
+// nonzero (its zero run) and a warp sum-scan its bit offset; every lane ORs
+// its codes into the warp's bit buffer in shared memory.  The finished bit
+// string is padded with 1-bits to a byte and copied out with a 0x00 after
+// every 0xFF byte (positions from a ballot prefix count).
+constexpr int kWarpMaxMcu = 4;
+constexpr int kBlockMaxBits = 11 + 11 + 63 * (16 + 10);            // DC code + bits, 63 x (AC code + bits)
+constexpr int kWarpBufWords = (kWarpMaxMcu * 6 * kBlockMaxBits + 8 + 31) / 32;
+constexpr int kEntropyWarps = 4;
+
+__device__ inline void put_bits(uint32_t* buf, uint32_t pos, uint32_t v, int len) {   // len 1..32, MSB first
+    if (len <= 0) return;
+    v &= len == 32 ? 0xFFFFFFFFu : ((1u << len) - 1u);
+    const uint32_t w = pos >> 5, off = pos & 31u;
+    if (off + (uint32_t)len <= 32u) {
+        atomicOr(&buf[w], v << (32u - off - (uint32_t)len));
+    } else {
+        const uint32_t hi = 32u - off, lo = (uint32_t)len - hi;
+        atomicOr(&buf[w], v >> lo);
+        atomicOr(&buf[w + 1], v << (32u - lo));
+    }
+}
+
+__global__ void __launch_bounds__(32 * kEntropyWarps)
+k_jpeg_entropy_warp(const int16_t* __restrict__ coef, int n_mcu, int restart, int n_int,
+                    const JpegTables* __restrict__ tab, uint8_t* __restrict__ slots, uint32_t slot_bytes,
+                    uint32_t* __restrict__ lens, uint32_t* __restrict__ flags) {
+    __shared__ uint32_t s_h[4][256];
+    __shared__ uint32_t s_buf[kEntropyWarps][kWarpBufWords];
+    for (int k = threadIdx.x; k < 4 * 256; k += blockDim.x) (&s_h[0][0])[k] = (&tab->huff[0][0])[k];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* buf = s_buf[warp];
+    for (int k = lane; k < kWarpBufWords; k += 32) buf[k] = 0u;
+    __syncthreads();
+    const int i = blockIdx.x * kEntropyWarps + warp;
+    if (i >= n_int) return;   // warp-uniform
+    const uint32_t full = 0xFFFFFFFFu;
+    int pred[3] = {0, 0, 0};
+    uint32_t bitpos = 0;
+    const int m0 = i * restart, m1 = min(n_mcu, m0 + restart);
+    for (int m = m0; m < m1; ++m)
+        for (int b = 0; b < 6; ++b) {
+            const int32_t word = reinterpret_cast<const int32_t*>(coef + ((size_t)m * 6 + b) * 64)[lane];
+            const int lo = (int16_t)(word & 0xFFFF), hi = (int16_t)((uint32_t)word >> 16);
+            const int comp = b < 4 ? 0 : b - 3;
+            const uint32_t* dc = s_h[comp ? 2 : 0];
+            const uint32_t* ac = s_h[comp ? 3 : 1];
+            const int z0 = __shfl_sync(full, lo, 0);
+            const int diff = z0 - pred[comp];
+            pred[comp] = z0;
+            // the lane's items: [DC (lane 0)] then AC positions 2 lane (lane > 0) and 2 lane + 1
+            const int p_lo = 2 * lane, p_hi = 2 * lane + 1;
+            const bool nz_lo = lane > 0 && lo != 0, nz_hi = hi != 0;
+            // position of the last nonzero AC coefficient at or below this lane's positions
+            int last = nz_hi ? p_hi : (nz_lo ? p_lo : 0);
+            int incl = last;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(full, incl, d);
+                if (lane >= d) incl = max(incl, y);
+            }
+            const int before = __shfl_up_sync(full, incl, 1);
+            const int prev_lane = lane > 0 ? before : 0;   // last nonzero AC position before this lane
+            const int last_nz = __shfl_sync(full, incl, 31);
+            const uint32_t zrl = ac[0xF0];
+            const int zrl_len = (int)(zrl >> 16);
+            // bit lengths of the lane's items
+            int n_dc = 0, len_dc = 0;
+            if (lane == 0) {
+                n_dc = category(diff);
+                len_dc = (int)(dc[n_dc] >> 16) + n_dc;
+            }
+            int run_lo = 0, n_lo = 0, len_lo = 0, run_hi = 0, n_hi = 0, len_hi = 0;
+            if (nz_lo) {
+                run_lo = p_lo - prev_lane - 1;
+                n_lo = category(lo);
+                len_lo = (run_lo >> 4) * zrl_len + (int)(ac[((run_lo & 15) << 4) | n_lo] >> 16) + n_lo;
+            }
+            if (nz_hi) {
+                run_hi = p_hi - (nz_lo ? p_lo : prev_lane) - 1;
+                n_hi = category(hi);
+                len_hi = (run_hi >> 4) * zrl_len + (int)(ac[((run_hi & 15) << 4) | n_hi] >> 16) + n_hi;
+            }
+            const int mine = len_dc + len_lo + len_hi;
+            int sum = mine;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(full, sum, d);
+                if (lane >= d) sum += y;
+            }
+            const int total = __shfl_sync(full, sum, 31);
+            uint32_t pos = bitpos + (uint32_t)(sum - mine);
+            if (lane == 0) {
+                const uint32_t c = dc[n_dc];
+                put_bits(buf, pos, c & 0xFFFFu, (int)(c >> 16));
+                pos += c >> 16;
+                put_bits(buf, pos, (uint32_t)(diff < 0 ? diff - 1 : diff), n_dc);
+                pos += (uint32_t)n_dc;
+            }
+            auto put_ac = [&](int run, int n, int v) {
+                for (int z = 0; z < (run >> 4); ++z) {
+                    put_bits(buf, pos, zrl & 0xFFFFu, zrl_len);
+                    pos += (uint32_t)zrl_len;
+                }
+                const uint32_t c = ac[((run & 15) << 4) | n];
+                put_bits(buf, pos, c & 0xFFFFu, (int)(c >> 16));
+                pos += c >> 16;
+                put_bits(buf, pos, (uint32_t)(v < 0 ? v - 1 : v), n);
+                pos += (uint32_t)n;
+            };
+            if (nz_lo) put_ac(run_lo, n_lo, lo);
+            if (nz_hi) put_ac(run_hi, n_hi, hi);
+            bitpos += (uint32_t)total;
+            if (last_nz < 63) {   // end of block after the last nonzero coefficient
+                const uint32_t eob = ac[0x00];
+                if (lane == 0) put_bits(buf, bitpos, eob & 0xFFFFu, (int)(eob >> 16));
+                bitpos += eob >> 16;
+            }
+        }
+    const uint32_t pad = (8u - (bitpos & 7u)) & 7u;
+    if (lane == 0 && pad) put_bits(buf, bitpos, 0xFFu, (int)pad);
+    __syncwarp();
+    const uint32_t n_bytes = (bitpos + pad) >> 3;
+    uint8_t* out = slots + (size_t)i * slot_bytes;
+    uint32_t stuffed = 0;   // 0x00 bytes inserted so far
+    bool over = false;
+    for (uint32_t j0 = 0; j0 < n_bytes; j0 += 32) {
+        const uint32_t j = j0 + (uint32_t)lane;
+        uint32_t byte = 0;
+        if (j < n_bytes) byte = (buf[j >> 2] >> (24u - 8u * (j & 3u))) & 0xFFu;
+        const bool ff = j < n_bytes && byte == 0xFFu;
+        const uint32_t m = __ballot_sync(full, ff);
+        if (j < n_bytes) {
+            const uint32_t o = j + stuffed + (uint32_t)__popc(m & ((1u << lane) - 1u));
+            if (o < slot_bytes) out[o] = (uint8_t)byte; else over = true;
+            if (ff) {
+                if (o + 1 < slot_bytes) out[o + 1] = 0x00; else over = true;
+            }
+        }
+        stuffed += (uint32_t)__popc(m);
+    }
+    if (__any_sync(full, over) && lane == 0) atomicOr(flags, 1u);
+    if (lane == 0) lens[i] = n_bytes + stuffed + (i + 1 < n_int ? 2u : 0u);
+}
+
 // One CTA per interval: its bytes (and the RSTn marker after it) at out[offsets[i]].
 __global__ void __launch_bounds__(256)
 k_jpeg_assemble(const uint8_t* __restrict__ slots, uint32_t slot_bytes, const uint32_t* __restrict__ lens,
@@ -383,9 +530,12 @@ Status jpeg_encode(RenderContext& ctx, const uint8_t* rgba, int W, int H, int qu
     TIGAS_CUDA_TRY(cudaMemsetAsync(d_lens + n_int, 0, 4, st));   // the scan's extra zero
     k_jpeg_mcu<<<n_mcu, 256, 0, st>>>(d_in, W, H, mw, d_tab, d_coef);
     TIGAS_LAUNCHED();
-    // one warp per CTA: the intervals (a few thousand per frame) spread over every SM
-    k_jpeg_entropy<<<(n_int + 31) / 32, 32, 0, st>>>(d_coef, n_mcu, restart, n_int, d_tab, d_slots, slot, d_lens,
-                                                    d_flags);
+    if (restart <= kWarpMaxMcu)
+        k_jpeg_entropy_warp<<<(n_int + kEntropyWarps - 1) / kEntropyWarps, 32 * kEntropyWarps, 0, st>>>(
+            d_coef, n_mcu, restart, n_int, d_tab, d_slots, slot, d_lens, d_flags);
+    else
+        k_jpeg_entropy<<<(n_int + 31) / 32, 32, 0, st>>>(d_coef, n_mcu, restart, n_int, d_tab, d_slots, slot, d_lens,
+                                                        d_flags);
     TIGAS_LAUNCHED();
     TIGAS_TRY(launch_scan_u32(d_lens, nullptr, d_offs, (uint64_t)n_int + 1, d_total, d_tmp, st));
     // entropy-coded data: straight into the caller's device buffer behind the header, or staged

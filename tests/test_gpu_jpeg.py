@@ -37,7 +37,9 @@ def frames(cuda):
 @pytest.mark.parametrize("size", [(320, 240), (97, 61), (480, 270), (17, 9)])
 def test_rendered_frames_match_the_oracle(frames, size, quality):
     img = frames[size]
-    for restart in (1, 3):
+    # restart intervals of up to 4 MCUs take the warp-per-interval coder, longer ones
+    # the thread-per-interval coder: both must give the oracle's file
+    for restart in (1, 3, 4, 5, 64):
         got = tg.jpeg_encode(img, quality, restart_mcus=restart)
         assert got == ojpeg.encode(img, quality, restart=restart)
 
@@ -49,7 +51,8 @@ def test_noise_and_extremes_match_the_oracle(seed):
     img[:8, :8, :3] = 255
     img[8:16, :8, :3] = 0
     for q in (1, 50, 100):
-        assert tg.jpeg_encode(img, q, restart_mcus=2) == ojpeg.encode(img, q, restart=2)
+        for restart in (2, 7):   # noise: long codes, zero runs of 16+, 0xFF stuffing in both coders
+            assert tg.jpeg_encode(img, q, restart_mcus=restart) == ojpeg.encode(img, q, restart=restart)
 
 
 def test_device_in_and_out_and_decodes(cuda, frames):
@@ -80,3 +83,17 @@ def test_full_hd_frame_matches_the_oracle(cuda):
         img = tg.render(h, synth.config_trajectory(3)[10], synth.default_intrinsics(W, H), W, H)
     for q in (65, 90):
         assert tg.jpeg_encode(img, q, restart_mcus=2) == ojpeg.encode(img, q, restart=2)
+
+
+@pytest.mark.parametrize("u,v", [(7, 7), (4, 5), (0, 6), (3, 0)])
+def test_long_zero_runs_match_the_oracle(u, v):
+    """A single DCT basis pattern per 8x8 block: its coefficient follows a zero
+    run of up to 62 (three ZRL codes before it in zig-zag order)."""
+    y, x = np.mgrid[0:48, 0:64]
+    f = np.cos((2 * (x % 8) + 1) * u * np.pi / 16) * np.cos((2 * (y % 8) + 1) * v * np.pi / 16)
+    img = np.zeros((48, 64, 4), np.uint8)
+    for c in range(3):
+        img[..., c] = np.clip(np.round(128 + (60 - 15 * c) * f), 0, 255).astype(np.uint8)
+    for q in (100, 90):
+        for restart in (1, 2, 5):
+            assert tg.jpeg_encode(img, q, restart_mcus=restart) == ojpeg.encode(img, q, restart=restart)
