@@ -198,7 +198,9 @@ Status finish_render(RenderContext& ctx, cudaStream_t st, PendingRender& p) {
     return {};
 }
 
-// Render V views synchronously; outputs may be host or device.
+// Render V views synchronously; outputs may be host or device.  dbg_pairs
+// (optional) receives the launch set's pair count; stats turns on the
+// instrumented kernels.
 Status do_render(Scene* scene, int V, const tigas_pose* poses, const tigas_intrinsics* intrs, const int* ws,
                  const int* hs, uint8_t* const* outs8, float* const* outs32, cudaStream_t user_st, int sort_mode,
                  tigas_frame_stats* stats, tigas_debug_frame* dbg, uint64_t* dbg_pairs) {
@@ -219,6 +221,7 @@ Status do_render(Scene* scene, int V, const tigas_pose* poses, const tigas_intri
     TIGAS_CUDA_TRY(cudaStreamSynchronize(st));
     TIGAS_TRY(finish_render(ctx, st, p));
     FrameResult& res = p.res;
+    if (dbg_pairs && !dbg) *dbg_pairs = res.pairs;   // the pair count alone, without instrumented kernels
 
     if (stats) {
         uint32_t vis[kMaxViews];
