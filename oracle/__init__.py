@@ -33,7 +33,8 @@ _lib = None
 TILE = 16
 
 #: default guard bands (relative) around integer decisions: depth, opacity,
-#: 3 sqrt(lambda), pixel position.  See DESIGN.md "integer parity".
+#: 3 sqrt(lambda), pixel position.  Within a band the GPU may take any outcome
+#: the oracle lists as reachable; off the bands it must match exactly.
 DEFAULT_GUARDS = (2.0 ** -16, 2.0 ** -16, 2.0 ** -16, 2.0 ** -18)
 
 

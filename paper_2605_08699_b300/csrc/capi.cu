@@ -360,7 +360,7 @@ TIGAS_API tigas_status tigas_autotune(tigas_scene* scene, int n_sets, int n_view
         std::sort(t.begin(), t.end());
         return t.empty() ? 1e300 : t[t.size() / 2];
     };
-    // round 1: every candidate, two untimed then `iters` timed launch sets
+    // first pass: every candidate, two untimed then `iters` timed launch sets
     for (size_t c = 0; c < cands.size(); ++c)
         for (int it = 0; it < iters + 2; ++it) {
             Status s = run(c, it >= 2);
@@ -369,7 +369,7 @@ TIGAS_API tigas_status tigas_autotune(tigas_scene* scene, int n_sets, int n_view
                 return fail(s);
             }
         }
-    // round 2: the four fastest again, interleaved so that drift hits them alike
+    // second pass: the four fastest again, interleaved so that drift hits them alike
     std::vector<size_t> order(cands.size());
     for (size_t c = 0; c < cands.size(); ++c) order[c] = c;
     std::sort(order.begin(), order.end(), [&](size_t a, size_t b) { return median(times[a]) < median(times[b]); });

@@ -24,8 +24,8 @@ import paper_2605_08699_b300 as tg  # noqa: E402
 
 
 def _diag(name, obj):
-    d = os.path.join(os.path.dirname(os.path.dirname(__file__)), "gpurun_out")
-    if os.path.isdir(d):
+    d = os.environ.get("TIGAS_DIAG_DIR")   # optional folder for per-test diagnostics
+    if d and os.path.isdir(d):
         with open(os.path.join(d, "parity_diag.jsonl"), "a") as f:
             f.write(json.dumps({"test": name, **obj}) + "\n")
 

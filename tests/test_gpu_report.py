@@ -3,7 +3,7 @@
 One entry per configuration (and per resolution / ABR level / storage), each
 checked against the colour gate (max |d| <= 2e-3 on >= 99.9 % of pixels,
 mean |d| <= 1e-4, PSNR >= 50 dB on float RGB) and appended to
-gpurun_out/parity_diag.jsonl when that folder exists:
+parity_diag.jsonl in the folder named by TIGAS_DIAG_DIR when it is set:
 
   1  100k Gaussians, 8 isotropic blobs, FP32, 320x240, base pose: whole frame
   2  1M Gaussians, 64 anisotropic blobs, FP32, 1280x720 and 1920x1080, three
@@ -33,8 +33,8 @@ pytestmark = pytest.mark.gpu
 
 
 def _report(name, obj):
-    d = os.path.join(os.path.dirname(os.path.dirname(__file__)), "gpurun_out")
-    if os.path.isdir(d):
+    d = os.environ.get("TIGAS_DIAG_DIR")
+    if d and os.path.isdir(d):
         with open(os.path.join(d, "parity_diag.jsonl"), "a") as f:
             f.write(json.dumps({"test": "error_report", "config": name, **obj}) + "\n")
 
