@@ -525,6 +525,45 @@ def test_full_size_3m_1080p_sampled(cuda, s3, storage):
     _diag("full_size_colour", {"storage": storage, **st, "pairs": dbg["pairs"], **extra})
 
 
+def test_full_size_8_view_async_launch_set(cuda, s3):
+    """The timed configuration: 8 views of 1080p of the 3M FP16 scene in one
+    asynchronous launch set, the next one queued before the wait.  Every
+    view equals its own single-view render, and two views meet the colour
+    gate against the oracle on sampled pixels."""
+    W, H, V = 1920, 1080, 8
+    K = synth.default_intrinsics(W, H)
+    trajs = [synth.config_trajectory(3, v) for v in range(V)]
+    poses = [trajs[v][(40 + 7 * v) % 300] for v in range(V)]
+    poses2 = [trajs[v][(41 + 7 * v) % 300] for v in range(V)]
+    with tg.scene_from(s3, storage=tg.STORAGE_FP16) as h:
+        outs = [torch.empty((H, W, 4), dtype=torch.uint8, device=cuda) for _ in range(V)]
+        outs2 = [torch.empty((H, W, 4), dtype=torch.uint8, device=cuda) for _ in range(V)]
+        stream = torch.cuda.Stream()
+        t1 = tg.render_batch_async(h, poses, [K] * V, [W] * V, [H] * V, outs, stream=stream)
+        t2 = tg.render_batch_async(h, poses2, [K] * V, [W] * V, [H] * V, outs2, stream=stream)
+        t1.wait()
+        t2.wait()
+        frames = [o.cpu().numpy() for o in outs]
+        for v in (0, 3, 7):
+            assert np.array_equal(frames[v], tg.render(h, poses[v], K, W, H))
+            assert np.array_equal(outs2[v].cpu().numpy(), tg.render(h, poses2[v], K, W, H))
+        f32 = {}
+        for v in (0, 5):
+            f = np.zeros((H, W, 4), np.float32)
+            tg.render_ex(h, poses[v], K, W, H, out_rgba_f32=f)
+            f32[v] = f
+    rng = np.random.default_rng(11)
+    for v in (0, 5):
+        pr = oracle.preprocess(s3, poses[v], K, W, H, storage_half=True)
+        pix = np.stack([rng.integers(0, W, 3000), rng.integers(0, H, 3000)], axis=1).astype(np.int32)
+        ref = oracle.render(pr, pixels=pix)
+        st = parity.assert_colour(f32[v][pix[:, 1], pix[:, 0]], ref)
+        exp8 = oracle.to_rgba8(ref).astype(np.int64)
+        got8 = frames[v][pix[:, 1], pix[:, 0]].astype(np.int64)
+        assert np.mean(np.all(np.abs(got8 - exp8) <= 1, axis=1)) >= 0.999
+        _diag("full_size_8_view", {"view": v, **st})
+
+
 # ------------------------------------------------------- failure detection
 
 
