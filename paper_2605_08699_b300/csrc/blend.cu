@@ -58,6 +58,30 @@ __device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;\
 template <int N>
 __device__ inline void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
+#ifndef TIGAS_BLEND_F32X2
+#define TIGAS_BLEND_F32X2 1
+#endif
+// Packed two-lane FP32 arithmetic (each lane rounds as the scalar instruction).
+__device__ __forceinline__ unsigned long long f2_pack(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 __device__ inline float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -193,12 +217,29 @@ __device__ __forceinline__ bool blend_rows(WarpStage& sm, int lane, const uint2*
             float e[NP];
             bool con[NP];
             bool anyc = false;
+            if constexpr (TIGAS_BLEND_F32X2 != 0 && NP % 2 == 0) {
+                // rows k = 2j, 2j + 1 in one packed lane pair: dy = dyb - 2k, e = dy (c' dy + b' dx) + p0
+                const unsigned long long dyb2 = f2_pack(dyb, dyb), ax2 = f2_pack(ap.x, ap.x);
+                const unsigned long long bdx2 = f2_pack(bdx, bdx), p02 = f2_pack(p0, p0);
 #pragma unroll
-            for (int k = 0; k < NP; ++k) {
-                const float dy = dyb - 2.0f * (float)k;
-                e[k] = fmaf(dy, fmaf(ap.x, dy, bdx), p0);
-                con[k] = e[k] >= thr[k];   // thr: the alpha cut-off, +inf once the pixel stopped
-                anyc |= con[k];
+                for (int j = 0; j < NP / 2; ++j) {
+                    const unsigned long long dy2 = f2_add(dyb2, f2_pack(-4.0f * (float)j, -4.0f * (float)j - 2.0f));
+                    const unsigned long long e2 = f2_fma(dy2, f2_fma(ax2, dy2, bdx2), p02);
+                    f2_unpack(e2, e[2 * j], e[2 * j + 1]);
+                }
+#pragma unroll
+                for (int k = 0; k < NP; ++k) {
+                    con[k] = e[k] >= thr[k];   // thr: the alpha cut-off, +inf once the pixel stopped
+                    anyc |= con[k];
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < NP; ++k) {
+                    const float dy = dyb - 2.0f * (float)k;
+                    e[k] = fmaf(dy, fmaf(ap.x, dy, bdx), p0);
+                    con[k] = e[k] >= thr[k];   // thr: the alpha cut-off, +inf once the pixel stopped
+                    anyc |= con[k];
+                }
             }
             if (__any_sync(kFull, anyc)) {
                 const float cbl = sm.blue[buf][j];

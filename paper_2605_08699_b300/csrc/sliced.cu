@@ -129,23 +129,28 @@ k_count_slice(const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b, con
     __syncthreads();
     const uint64_t n = b - a + 1;   // with the closing zero
     const uint64_t base = (uint64_t)blockIdx.x * kScanBlock;
-    uint32_t total = 0;
-#pragma unroll 4
+    // all of the thread's rectangles first (independent loads in flight), then
+    // the table lookups; past the slice an empty rectangle counts 0
+    uint2 rr[kCountItems];
+#pragma unroll
     for (int r = 0; r < kCountItems; ++r) {
         const uint64_t i = base + (uint64_t)r * kCountThreads + threadIdx.x;
-        if (i >= n) break;
-        uint32_t c = 0;
-        if (i + a < b) {
-            const TileRect tr = unpack_rect<COMPACT>(rect_sorted[a + i]);
-            if (tr.xhi > tr.xlo && tr.yhi > tr.ylo) {
-                const uint32_t* s = sat + s_sb[tr.v];
-                const uint32_t w1 = s_w1[tr.v];
-                c = s[tr.yhi * w1 + tr.xhi] - s[tr.ylo * w1 + tr.xhi] - s[tr.yhi * w1 + tr.xlo] +
-                    s[tr.ylo * w1 + tr.xlo];
-            }
-        }
-        counts[i] = c;
-        total += c;
+        rr[r] = i < b - a ? rect_sorted[a + i] : make_uint2(0u, 0u);
+    }
+    uint32_t total = 0;
+#pragma unroll
+    for (int r = 0; r < kCountItems; ++r) {
+        const uint64_t i = base + (uint64_t)r * kCountThreads + threadIdx.x;
+        const TileRect tr = unpack_rect<COMPACT>(rr[r]);
+        const bool ne = tr.xhi > tr.xlo && tr.yhi > tr.ylo;
+        // an empty rectangle looks up word 0 of the table (always present), so every
+        // lookup is unconditional and they all go out together
+        const uint32_t* s = sat + (ne ? s_sb[tr.v] : 0u);
+        const uint32_t w1 = ne ? s_w1[tr.v] : 0u;
+        const uint32_t xl = ne ? tr.xlo : 0u, xh = ne ? tr.xhi : 0u, yl = ne ? tr.ylo : 0u, yh = ne ? tr.yhi : 0u;
+        const uint32_t c = s[yh * w1 + xh] - s[yl * w1 + xh] - s[yh * w1 + xl] + s[yl * w1 + xl];
+        if (i < n) counts[i] = c;
+        total += i < n ? c : 0u;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -164,35 +169,15 @@ k_count_slice(const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b, con
 // the rectangle (row-major), and those not done are written to consecutive
 // positions (a ballot ranks them), so stores are coalesced and a large
 // rectangle costs area / 32 steps instead of area steps of one lane.
-// COMPACT: the entry id travels in the rectangle's second word (order unused).
+// m: lanes whose entry has pairs; r, e, pos, c: each lane's rectangle, entry,
+// first pair position and pair count.
 template <bool COMPACT>
-__global__ void __launch_bounds__(256)
-k_emit_slice(const uint32_t* __restrict__ order, const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b,
-             const uint32_t* __restrict__ offsets, const ViewParams* __restrict__ views_g, int V,
-             const uint32_t* __restrict__ done, uint32_t* __restrict__ keys, uint32_t* __restrict__ values,
-             uint64_t pair_cap, uint32_t* __restrict__ overflow) {
-    __shared__ uint32_t s_tb[kMaxViews], s_tx[kMaxViews];
-    for (int k = threadIdx.x; k < V; k += blockDim.x) {
-        s_tb[k] = views_g[k].tile_base;
-        s_tx[k] = (uint32_t)views_g[k].TX;
-    }
-    __syncthreads();
+__device__ inline void emit_warp_entries(uint32_t m, uint2 r, uint32_t e, uint32_t pos, uint32_t c,
+                                         const uint32_t* s_tb, const uint32_t* s_tx, const uint32_t* __restrict__ done,
+                                         uint32_t* __restrict__ keys, uint32_t* __restrict__ values,
+                                         uint64_t pair_cap, uint32_t* __restrict__ overflow) {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
-    const uint64_t k = a + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t pos = 0, c = 0;
-    if (k < b) {
-        pos = offsets[k - a];
-        c = offsets[k - a + 1] - pos;
-    }
-    uint32_t m = __ballot_sync(kFull, c > 0);
-    if (!m) return;   // warp-uniform
-    uint32_t e = 0;
-    uint2 r = make_uint2(0u, 0u);
-    if (c > 0) {
-        r = rect_sorted[k];
-        e = COMPACT ? r.y : order[k];
-    }
     while (m) {
         const int j = __ffs(m) - 1;
         m &= m - 1;
@@ -229,6 +214,60 @@ k_emit_slice(const uint32_t* __restrict__ order, const uint2* __restrict__ rect_
             }
             written += __popc(bm);
         }
+    }
+}
+
+// Each warp takes 32 J consecutive entries, lane l the entries 32 j + l: all
+// of its pair offsets are loaded at once (an entry's count is the next entry's
+// offset minus its own; offsets[b - a] is the slice total), then its
+// rectangles, then the entries with pairs are written group by group.  A
+// larger J launches fewer CTAs for slices of many entries whose tiles have
+// mostly stopped.  COMPACT: the entry id travels in the rectangle's second
+// word (order unused).
+constexpr int kEmitThreads = 256;
+template <bool COMPACT, int J>
+__global__ void __launch_bounds__(kEmitThreads)
+k_emit_slice(const uint32_t* __restrict__ order, const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b,
+             const uint32_t* __restrict__ offsets, const ViewParams* __restrict__ views_g, int V,
+             const uint32_t* __restrict__ done, uint32_t* __restrict__ keys, uint32_t* __restrict__ values,
+             uint64_t pair_cap, uint32_t* __restrict__ overflow) {
+    __shared__ uint32_t s_tb[kMaxViews], s_tx[kMaxViews];
+    for (int k = threadIdx.x; k < V; k += blockDim.x) {
+        s_tb[k] = views_g[k].tile_base;
+        s_tx[k] = (uint32_t)views_g[k].TX;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t wbase = a + ((uint64_t)blockIdx.x * (kEmitThreads / 32) + warp) * (32u * J);
+    if (wbase >= b) return;   // warp-uniform
+    uint32_t pos[J], cnt[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const uint64_t k = wbase + 32u * j + lane;
+        pos[j] = k <= b ? offsets[k - a] : 0u;
+    }
+    const uint64_t kend = wbase + 32u * J;
+    const uint32_t tail = kend <= b ? offsets[kend - a] : 0u;
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const uint32_t up = __shfl_down_sync(kFull, pos[j], 1);
+        const uint32_t first = __shfl_sync(kFull, pos[j + 1 < J ? j + 1 : j], 0);
+        const uint32_t next = lane < 31 ? up : (j + 1 < J ? first : tail);
+        cnt[j] = wbase + 32u * j + lane < b ? next - pos[j] : 0u;
+    }
+    uint2 rr[J];
+    uint32_t ee[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const uint64_t k = wbase + 32u * j + lane;
+        rr[j] = cnt[j] > 0 ? rect_sorted[k] : make_uint2(0u, 0u);
+        ee[j] = COMPACT ? rr[j].y : (cnt[j] > 0 ? order[k] : 0u);
+    }
+#pragma unroll
+    for (int j = 0; j < J; ++j) {   // unrolled: the per-lane arrays stay in registers
+        const uint32_t m = __ballot_sync(kFull, cnt[j] > 0);
+        if (m) emit_warp_entries<COMPACT>(m, rr[j], ee[j], pos[j], cnt[j], s_tb, s_tx, done, keys, values, pair_cap,
+                                          overflow);
     }
 }
 
@@ -322,13 +361,28 @@ Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64
                          uint32_t* keys, uint32_t* values, uint64_t pair_cap, uint32_t* overflow, bool compact,
                          cudaStream_t st) {
     if (b <= a) return {};
-    const unsigned grid = (unsigned)((b - a + 255) / 256);
-    if (compact)
-        k_emit_slice<true><<<grid, 256, 0, st>>>(order, rect_sorted, a, b, offsets, views, V, done, keys, values,
-                                                 pair_cap, overflow);
-    else
-        k_emit_slice<false><<<grid, 256, 0, st>>>(order, rect_sorted, a, b, offsets, views, V, done, keys, values,
-                                                  pair_cap, overflow);
+    // entries per lane: the largest J in {1, 2, 4, 8} that still leaves about
+    // 8 CTAs per SM
+    const uint64_t n = b - a;
+    int J = 1;
+    while (J < 8 && n >= (uint64_t)(2 * J) * kEmitThreads * 148 * 8) J *= 2;
+    const unsigned grid = (unsigned)((n + (uint64_t)J * kEmitThreads - 1) / ((uint64_t)J * kEmitThreads));
+#define TIGAS_EMIT(JJ)                                                                                              \
+    do {                                                                                                            \
+        if (compact)                                                                                                \
+            k_emit_slice<true, JJ><<<grid, kEmitThreads, 0, st>>>(order, rect_sorted, a, b, offsets, views, V, done, \
+                                                                  keys, values, pair_cap, overflow);                \
+        else                                                                                                        \
+            k_emit_slice<false, JJ><<<grid, kEmitThreads, 0, st>>>(order, rect_sorted, a, b, offsets, views, V,     \
+                                                                   done, keys, values, pair_cap, overflow);         \
+    } while (0)
+    switch (J) {
+        case 1: TIGAS_EMIT(1); break;
+        case 2: TIGAS_EMIT(2); break;
+        case 4: TIGAS_EMIT(4); break;
+        default: TIGAS_EMIT(8); break;
+    }
+#undef TIGAS_EMIT
     TIGAS_LAUNCHED();
     return {};
 }
