@@ -65,6 +65,11 @@ size_t radix_tmp_words(uint64_t n_cap);
 // Device word of tmp holding how many passes the last one-sweep sort using
 // tmp ran (valid once it completed; inputs of 2^30 keys or more leave it 0).
 const uint32_t* radix_active_passes(const uint32_t* tmp);
+// Device words of tmp holding, for digit d of pass `pass` of the last
+// one-sweep sort using tmp, how many keys have a smaller digit in that pass
+// (256 words; valid once it completed; inputs of 2^30 keys or more do not
+// write them).
+const uint32_t* radix_digit_bases(const uint32_t* tmp, int pass);
 template <typename K>
 Status radix_sort(const K* keys_in, const uint32_t* values_in, K* keys_alt, uint32_t* values_alt,
                   K* keys_out, uint32_t* values_out, uint64_t n_cap, const uint64_t* d_n, int begin_bit,

@@ -271,13 +271,19 @@ k_emit_slice(const uint32_t* __restrict__ order, const uint2* __restrict__ rect_
     }
 }
 
-// Tile ranges by binary search.  Tiles with pairs in this slice that are not
-// done form the active list: a tile with at least kHeavyTile pairs as four
-// strips of 4 pixel rows from the front (count n_active[0]), so that four
-// warps share its long list and the blend's dynamic scheduler starts them
-// first; the other tiles whole from the back (count n_active[1]).
-__device__ inline uint64_t lower_bound_u32(const uint32_t* __restrict__ keys, uint64_t n, uint32_t t) {
-    uint64_t lo = 0, hi = n;
+// Tile ranges of the sorted pair keys.  A CTA takes the 256 tiles
+// [256 h, 256 h + 256); their keys form one run [L, R) of the sorted array,
+// which the sort's second pass already located (its digit is t >> 8: L and R
+// are that digit's base and the next one's), else two searches find it.  The
+// CTA samples 1024 keys of the run into shared memory, and each thread's
+// lower bound of its tile searches the sample first and the keys between two
+// samples after, about 5 dependent reads instead of a search of the whole
+// array.  Tiles with pairs in this slice that are not done form the active
+// list: a tile with at least kHeavyTile pairs as four strips of 4 pixel rows
+// from the front (count n_active[0]), so that four warps share its long list
+// and the blend's dynamic scheduler starts them first; the other tiles whole
+// from the back (count n_active[1]).
+__device__ inline uint64_t lower_bound_u32(const uint32_t* __restrict__ keys, uint64_t lo, uint64_t hi, uint32_t t) {
     while (lo < hi) {
         const uint64_t mid = (lo + hi) >> 1;
         if (keys[mid] < t) lo = mid + 1; else hi = mid;
@@ -285,19 +291,52 @@ __device__ inline uint64_t lower_bound_u32(const uint32_t* __restrict__ keys, ui
     return lo;
 }
 
+constexpr int kRangeSample = 1024;
 __global__ void __launch_bounds__(256)
 k_ranges_active(const uint32_t* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, uint2* __restrict__ ranges,
                 uint32_t n_tiles, const uint32_t* __restrict__ done, uint32_t* __restrict__ active,
-                uint32_t* __restrict__ n_active, uint32_t* __restrict__ overflow) {
+                uint32_t* __restrict__ n_active, uint32_t* __restrict__ overflow,
+                const uint32_t* __restrict__ hi_bases) {
+    __shared__ uint32_t s_sample[kRangeSample];
+    __shared__ uint32_t s_lo[256];
+    __shared__ uint64_t s_run[2];
     uint64_t n = d_n ? *d_n : n_cap;
     if (n > n_cap) n = n_cap;
-    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t t0 = blockIdx.x * 256u, t = t0 + threadIdx.x;
     if (t == 0 && n > 0 && keys[n - 1] >= n_tiles) atomicOr(overflow, 2u);
+    if (threadIdx.x < 2) {
+        uint64_t x;
+        if (hi_bases) {
+            const uint32_t h = blockIdx.x + threadIdx.x;   // h <= 256: tile ids have at most 16 bits
+            x = h < 256u ? hi_bases[h] : n;
+            if (x > n) x = n;
+        } else {
+            x = lower_bound_u32(keys, 0, n, t0 + 256u * threadIdx.x);
+        }
+        s_run[threadIdx.x] = x;
+    }
+    __syncthreads();
+    const uint64_t L = s_run[0], R = s_run[1] > L ? s_run[1] : L, span = R - L;
+    for (int k = threadIdx.x; k < kRangeSample; k += 256)
+        s_sample[k] = span ? keys[L + (uint64_t)k * span / kRangeSample] : 0xFFFFFFFFu;
+    __syncthreads();
+    {
+        // first sample >= t, then the keys after the sample before it
+        int lo = 0, hi = kRangeSample;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (s_sample[mid] < t) lo = mid + 1; else hi = mid;
+        }
+        const uint64_t a = lo == 0 ? L : L + (uint64_t)(lo - 1) * span / kRangeSample + 1;
+        const uint64_t b = lo == kRangeSample ? R : L + (uint64_t)lo * span / kRangeSample;
+        s_lo[threadIdx.x] = (uint32_t)lower_bound_u32(keys, a, b, t);
+    }
+    __syncthreads();
     bool act = false, heavy = false;
     if (t < n_tiles) {
-        const uint64_t lo = lower_bound_u32(keys, n, t);
-        const uint64_t hi = lower_bound_u32(keys, n, t + 1);
-        ranges[t] = make_uint2((uint32_t)lo, (uint32_t)hi);
+        const uint32_t lo = s_lo[threadIdx.x];
+        const uint32_t hi = threadIdx.x < 255 ? s_lo[threadIdx.x + 1] : (uint32_t)R;
+        ranges[t] = make_uint2(lo, hi);
         act = hi > lo && !tile_done(done, t);
         heavy = act && hi - lo >= kHeavyTile;
     }
@@ -362,10 +401,10 @@ Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64
                          cudaStream_t st) {
     if (b <= a) return {};
     // entries per lane: the largest J in {1, 2, 4, 8} that still leaves about
-    // 8 CTAs per SM
+    // 4 waves of 8 CTAs per SM (slices with many pairs per entry want the warps)
     const uint64_t n = b - a;
     int J = 1;
-    while (J < 8 && n >= (uint64_t)(2 * J) * kEmitThreads * 148 * 8) J *= 2;
+    while (J < 8 && n >= (uint64_t)(2 * J) * kEmitThreads * 148 * 8 * 4) J *= 2;
     const unsigned grid = (unsigned)((n + (uint64_t)J * kEmitThreads - 1) / ((uint64_t)J * kEmitThreads));
 #define TIGAS_EMIT(JJ)                                                                                              \
     do {                                                                                                            \
@@ -389,10 +428,11 @@ Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64
 
 Status launch_ranges_active(const uint32_t* keys, uint64_t n_cap, const uint64_t* d_n, uint2* ranges,
                             uint32_t n_tiles, const uint32_t* done, uint32_t* active, uint32_t* n_active,
-                            uint32_t* overflow, cudaStream_t st) {
+                            uint32_t* overflow, const uint32_t* hi_bases, cudaStream_t st) {
     if (n_tiles == 0) return {};
+    if (hi_bases && n_tiles > 65536u) return {TIGAS_ERR_INVALID, "second-pass digit bases need tile ids of 16 bits"};
     k_ranges_active<<<(n_tiles + 255) / 256, 256, 0, st>>>(keys, n_cap, d_n, ranges, n_tiles, done, active, n_active,
-                                                           overflow);
+                                                           overflow, hi_bases);
     TIGAS_LAUNCHED();
     return {};
 }

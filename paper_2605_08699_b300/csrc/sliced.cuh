@@ -51,9 +51,12 @@ Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64
 // on entry (launch_running_sat clears them).
 // `active` holds 4 n_tiles items.
 // The key count is min(*d_n, n_cap) when d_n is given, else n_cap.
+// hi_bases: null, or 256 words whose word h is the first position of a key
+// with key >> 8 == h (the second-pass digit bases of the sort that produced
+// `keys`); n_tiles <= 65536.
 Status launch_ranges_active(const uint32_t* keys, uint64_t n_cap, const uint64_t* d_n, uint2* ranges,
                             uint32_t n_tiles, const uint32_t* done, uint32_t* active, uint32_t* n_active,
-                            uint32_t* overflow, cudaStream_t st);
+                            uint32_t* overflow, const uint32_t* hi_bases, cudaStream_t st);
 
 // Blend of the active tiles of one slice: persistent CTAs take tiles from the
 // active list, composite the slice's entries onto each pixel's carried state,

@@ -306,6 +306,18 @@ def test_wide_and_compact_rectangles_give_the_same_frames(h1, cuda):
         assert np.array_equal(full["rgba_f32"], fast)
 
 
+def test_launch_set_of_more_than_65536_tiles(h1, cuda):
+    """Nine 1080p views hold 73440 tiles: tile ids of 17 bits, so the pair sort
+    runs three passes and each run of 256 tiles of the tile ranges is found by
+    search rather than from the second pass's digit bases.  Every frame equals
+    its single-view render (8160 tiles: the digit-bases path)."""
+    poses = synth.trajectory(93, 9)
+    many = _batch(h1, poses, [(1920, 1080)] * 9, cuda)
+    K = synth.default_intrinsics(1920, 1080)
+    for p, o in zip(poses, many):
+        assert np.array_equal(tg.render(h1, p, K, 1920, 1080), o)
+
+
 def test_graph_replay_equals_direct_launches(h1, cuda):
     levels = [(480, 270), (320, 240), (97, 61)]
     tr = synth.trajectory(11, 40)
