@@ -51,7 +51,8 @@ Status launch_emit_u64(const uint32_t* offsets, const SplatArrays& sp, const Vie
 // ex (optional, 32-bit keys only):
 //   key_range: device [kmin, kmax] of the keys other than 0xFFFFFFFF; digits
 //     are taken from k - kmin (0xFFFFFFFF -> kmax - kmin + 1), the same order,
-//     so keys spanning less than 2^24 need three passes;
+//     so keys spanning less than 2^24 need three passes; keys_out then holds
+//     the mapped keys (the first pass stores them, later passes read them);
 //   pay_in / pay_alt / pay_out: an 8-byte payload per key moved with it.
 // With a payload, values_in, values_alt and values_out may all be null: no
 // value stream is read or written (the payload identifies each key).

@@ -385,9 +385,11 @@ Status radix_sort_rts(const K* keys_in, const uint32_t* values_in, K* keys_alt, 
 // wait themselves, so the waits always end; each wait is still bounded: after
 // kSpinLimit polls the CTA records a timeout flag and goes on (its writes stay
 // inside the output by the bounds check, the host reports the error).  The
-// look-back reads kLookWin predecessors per round, so a CTA of the first wave
-// (whose predecessors have mostly published only their own counts) needs
-// about 1/kLookWin of the dependent round trips of a one-by-one walk.
+// look-back reads a window of predecessors per round (4 in the depth sort, 2
+// in the pair sorts: measured ahead of 8 and 16, whose extra loads mostly find
+// counts the walk no longer needs), so a CTA of the first wave, whose
+// predecessors have mostly published only their own counts, needs a fraction
+// of the dependent round trips of a one-by-one walk.
 
 namespace {
 
@@ -396,11 +398,6 @@ constexpr uint32_t kFlagPre = 2u << 30;
 constexpr uint32_t kFlagMask = 3u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
 constexpr int kSpinLimit = 1 << 22;
-#ifndef TIGAS_LOOK_WINDOW
-#define TIGAS_LOOK_WINDOW 8
-#endif
-constexpr int kLookWin = TIGAS_LOOK_WINDOW;
-   // predecessor chunks read per look-back round
 
 constexpr uint32_t kSortTimeoutFlag = 16u;
 
@@ -507,14 +504,17 @@ struct KeyMap {
 // bits of the ballot of lanes agreeing on that bit (warp multisplit).  Always
 // all 8 bits, with no test of the pass's digit width: a narrower digit has
 // zero high bits, whose ballots leave the mask unchanged (measured: depth sort
-// 0.849 -> 0.739 ms, pair sorts 0.638 -> 0.615 ms against a width test per bit).
+// 0.849 -> 0.739 ms, pair sorts 0.638 -> 0.615 ms against a width test per
+// bit).  Each bit's agreement is one XNOR of the ballot with the lane's bit
+// spread to a mask (0.730 -> 0.701 and 0.612 -> 0.589 ms against a select of
+// the ballot or its complement).
 __device__ inline uint32_t digit_peers(uint32_t d) {
     uint32_t peers = kFull;
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
-        const bool bit = (d >> b) & 1u;
-        const uint32_t bal = __ballot_sync(kFull, bit);
-        peers &= bit ? bal : ~bal;
+        const uint32_t m = 0u - ((d >> b) & 1u);   // all ones when the bit is set
+        const uint32_t bal = __ballot_sync(kFull, m != 0u);
+        peers &= ~(bal ^ m);   // lanes that agree on the bit
     }
     return peers;
 }
@@ -669,6 +669,7 @@ __global__ void __launch_bounds__(256) k_os_bases(const uint32_t* __restrict__ g
 // adding aggregates until an inclusive prefix and re-polling a chunk not yet
 // published.  Publishes this chunk's inclusive prefix; `publish_agg` first
 // publishes its own count (when the caller has not already done so).
+template <int kLookWin>
 __device__ inline uint32_t lookback_exclusive(uint32_t* status, uint32_t chunk, uint32_t d, uint32_t cnt,
                                               bool publish_agg, uint32_t* flags, int spin_limit) {
     uint32_t* my = status + (size_t)chunk * 256 + d;
@@ -743,6 +744,11 @@ k_os_scatter(const OsRoute* __restrict__ route, uint64_t n_cap, const uint64_t* 
     // slices (many small launches, one wave each) walk back first, as the later
     // inclusive prefix lengthens their chain (0.643 -> 0.700 ms when walked late).
     constexpr bool kLate = PAY == kPayOnly;
+    // look-back window and leader test, per sort (measured on the 8-view launch set):
+    // depth sort 4 predecessors and the first-peer leader, pair sorts 2 and the
+    // no-lower-peer leader
+    constexpr int kWin = PAY == kPayOnly ? 4 : 2;
+    constexpr bool kLowerLeader = PAY != kPayOnly;
     const uint32_t mask = (1u << nbits) - 1u;
     constexpr int T = OsCfg<K, PAY>::kT, I = OsCfg<K, PAY>::kI, N = T * I, W = T / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -767,6 +773,7 @@ k_os_scatter(const OsRoute* __restrict__ route, uint64_t n_cap, const uint64_t* 
         const uint32_t li = warp * (I * 32) + r * 32 + lane;
         if (li < valid) {
             key[r] = keys_in[base + li];
+            if constexpr (MAP) key[r] = km(key[r]);   // stored mapped: later passes need no map
             val[r] = !has_vals ? 0u : vals_in ? vals_in[base + li] : (uint32_t)(base + li);
             if (PAY) pay[r] = pays_in[base + li];
         } else {
@@ -779,23 +786,18 @@ k_os_scatter(const OsRoute* __restrict__ route, uint64_t n_cap, const uint64_t* 
     const uint32_t lt = lanemask_lt();
 #pragma unroll
     for (int r = 0; r < I; ++r) {
-        const uint32_t li = warp * (I * 32) + r * 32 + lane;
-        (void)li;
-        // padding keys take the largest digit so that they sort after every key
-        // (without a key map their all-ones key gives it already)
-        uint32_t d;
-        if constexpr (MAP)
-            d = li < valid ? (uint32_t)(km(key[r]) >> shift) & mask : mask;
-        else
-            d = (uint32_t)(key[r] >> shift) & mask;
+        // padding keys (all ones) take the largest digit, so they sort after every
+        // key; a mapped key is at most the map's span, below all ones
+        const uint32_t d = (uint32_t)(key[r] >> shift) & mask;
         // peers by one ballot per digit bit (measured faster here than match.any
         // with shared-memory atomics)
         const uint32_t peers = digit_peers(d);
         const uint32_t before = sm.whist[warp][d];
+        const uint32_t lower = peers & lt;   // peers in lower lanes
         __syncwarp();
-        if (lane == __ffs(peers) - 1) sm.whist[warp][d] = before + __popc(peers);
+        if (kLowerLeader ? lower == 0u : lane == __ffs(peers) - 1) sm.whist[warp][d] = before + __popc(peers);
         __syncwarp();
-        dr[r] = (d << 16) | (before + __popc(peers & lt));
+        dr[r] = (d << 16) | (before + __popc(lower));
     }
     __syncthreads();
 
@@ -815,7 +817,7 @@ k_os_scatter(const OsRoute* __restrict__ route, uint64_t n_cap, const uint64_t* 
             // this chunk's counts now; the walk back waits until the tile is sorted in shared memory
             st_relaxed(status + (size_t)chunk * 256 + d, (chunk == 0 ? kFlagPre : kFlagAgg) | (cnt & kValMask));
         } else {
-            const uint32_t excl = lookback_exclusive(status, chunk, d, cnt, true, flags, spin_limit);
+            const uint32_t excl = lookback_exclusive<kWin>(status, chunk, d, cnt, true, flags, spin_limit);
             sm.gshift[d] = (d <= mask ? gbase[d] : 0u) + excl;   // tile position subtracted below
         }
     }
@@ -839,7 +841,7 @@ k_os_scatter(const OsRoute* __restrict__ route, uint64_t n_cap, const uint64_t* 
     if constexpr (kLate) {
         if (threadIdx.x < 256) {
             const uint32_t d = threadIdx.x;
-            const uint32_t excl = lookback_exclusive(status, chunk, d, cnt, false, flags, spin_limit);
+            const uint32_t excl = lookback_exclusive<kWin>(status, chunk, d, cnt, false, flags, spin_limit);
             sm.gshift[d] = (d <= mask ? gbase[d] : 0u) + excl - start;
         }
     }
@@ -849,7 +851,7 @@ k_os_scatter(const OsRoute* __restrict__ route, uint64_t n_cap, const uint64_t* 
         const uint32_t j = k * T + threadIdx.x;
         if (j < valid) {
             const K kk = sm.keys[j];
-            const uint32_t d = (uint32_t)((MAP ? km(kk) : kk) >> shift) & mask;
+            const uint32_t d = (uint32_t)(kk >> shift) & mask;
             const uint32_t g = sm.gshift[d] + j;
             if (g < n) {
                 keys_out[g] = kk;
@@ -914,9 +916,17 @@ Status radix_sort_onesweep(const K* keys_in, const uint32_t* values_in, K* keys_
     for (int p = 0; p < passes; ++p) {
         const int shift = begin_bit + 8 * p;
         const int nb = min(8, end_bit - shift);
-        k_os_scatter<K, PAY, MAP><<<(unsigned)chunks, T, sizeof(OsSmem<K, PAY>), st>>>(
-            routes + p, n_cap, d_n, shift, nb, gbase + p * 256, status + (size_t)p * chunks * 256, counters + p,
-            flags, kSpinLimit, range);
+        if (MAP && p > 0) {
+            // the first pass (always run) stored mapped keys: later passes read them as they are
+            TIGAS_TRY((ensure_os_smem<K, PAY, false>()));
+            k_os_scatter<K, PAY, false><<<(unsigned)chunks, T, sizeof(OsSmem<K, PAY>), st>>>(
+                routes + p, n_cap, d_n, shift, nb, gbase + p * 256, status + (size_t)p * chunks * 256, counters + p,
+                flags, kSpinLimit, nullptr);
+        } else {
+            k_os_scatter<K, PAY, MAP><<<(unsigned)chunks, T, sizeof(OsSmem<K, PAY>), st>>>(
+                routes + p, n_cap, d_n, shift, nb, gbase + p * 256, status + (size_t)p * chunks * 256, counters + p,
+                flags, kSpinLimit, range);
+        }
         TIGAS_LAUNCHED();
     }
     return {};
