@@ -133,12 +133,16 @@ __device__ __forceinline__ bool blend_rows(WarpStage& sm, int lane, const uint2*
 
     float T[NP], cr[NP], cg[NP], cb[NP];
     uint32_t live = 0;   // bit k: pixel k still compositing
+    // the tile's pixels carry (C, T) from an earlier slice (a slice blends all
+    // four strips of a long tile, so a tile's strips are blended together);
+    // otherwise they start from (0, 1) without reading the state
+    const bool carried = SLICED && (sl.strips[g] & kStripSeen) != 0u;
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
         T[k] = 1.0f; cr[k] = 0.0f; cg[k] = 0.0f; cb[k] = 0.0f;
         const int py = py0 + 2 * k;
         if (px < W && py < H) {
-            if (SLICED) {
+            if (carried) {
                 const float4 s0 = sl.state[sbase + (size_t)py * W + px];
                 cr[k] = s0.x; cg[k] = s0.y; cb[k] = s0.z; T[k] = fabsf(s0.w);
                 if (!(s0.w < 0.0f)) live |= 1u << k;
@@ -273,12 +277,16 @@ __device__ __forceinline__ bool blend_rows(WarpStage& sm, int lane, const uint2*
     cp_async_wait<0>();
     __syncwarp();
 
+    const bool all = __all_sync(kFull, live == 0);
+    // a whole tile whose pixels all stopped is done and never visited again: no state
+    const bool keep = !(NP == kPix && all);
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
         const int py = py0 + 2 * k;
         if (px < W && py < H) {
             const size_t pix = (size_t)py * W + px;
-            if (SLICED) sl.state[sbase + pix] = make_float4(cr[k], cg[k], cb[k], ((live >> k) & 1u) ? T[k] : -T[k]);
+            if (SLICED && keep)
+                sl.state[sbase + pix] = make_float4(cr[k], cg[k], cb[k], ((live >> k) & 1u) ? T[k] : -T[k]);
             const float r = fmaf(T[k], bg_r, cr[k]), gg = fmaf(T[k], bg_g, cg[k]);
             const float bb = fmaf(T[k], bg_b, cb[k]), a = 1.0f - T[k];
             if (vp.out_rgba8)
@@ -286,7 +294,9 @@ __device__ __forceinline__ bool blend_rows(WarpStage& sm, int lane, const uint2*
             if (vp.out_rgba_f32) reinterpret_cast<float4*>(vp.out_rgba_f32)[pix] = make_float4(r, gg, bb, a);
         }
     }
-    return __all_sync(kFull, live == 0);
+    // the tile's pixels now carry state (and have their outputs written)
+    if (SLICED && !carried && lane == 0) atomicOr(&sl.strips[g], kStripSeen);
+    return all;
 }
 
 // SLICED = false: warp w of CTA b blends tile 4b + w over its whole list from
@@ -344,7 +354,7 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ values, S
                                                           sl, cnt);
             if (all && lane == 0) {
                 const uint32_t old = atomicOr(&sl.strips[g], bit);
-                if ((old | bit) == 0xFu) atomicOr(&sl.done[g >> 5], 1u << (g & 31));
+                if (((old | bit) & 0xFu) == 0xFu) atomicOr(&sl.done[g >> 5], 1u << (g & 31));
             }
         }
     }
@@ -399,7 +409,6 @@ Status launch_blend_slice(const uint2* ranges, const uint32_t* values, const Spl
     }();
     TIGAS_CUDA_TRY(f.err);
     const int grid = (ctas_per_sm > 0 && ctas_per_sm < f.per_sm ? ctas_per_sm : f.per_sm) * f.sms;
-    TIGAS_CUDA_TRY(cudaMemsetAsync(sl.work_counter, 0, sizeof(uint32_t), st));
     if (counters)
         k_blend<true, true><<<grid, kThreads, 0, st>>>(ranges, values, sp, views, V, 0, n_entries, bg[0], bg[1], bg[2],
                                                        counters, sl);

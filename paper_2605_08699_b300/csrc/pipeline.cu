@@ -580,8 +580,7 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
                                    cudaMemcpyDeviceToHost, st));
     TIGAS_TRY(mark(kStDepthSort, false));
     // also clears the done and strip bits and the slice totals (empty slices count 0)
-    TIGAS_TRY(launch_init_state(d_views, V, total_tiles, d_pix_base, state, scene->view.bg, done, strips, d_total,
-                                kMaxSlices + 2, st));
+    TIGAS_TRY(launch_init_slices(total_tiles, done, strips, d_total, kMaxSlices + 2, st));
 
     // entries the slices cut: kept ones only (exact), or all (static; culled
     // ones sort after every kept one and have empty rectangles)
@@ -675,6 +674,8 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
         TIGAS_TRY(mark(kStBlend, false));
         a = b;
     }
+    // the background of every tile no slice blended
+    TIGAS_TRY(launch_fill_unseen(d_views, V, total_tiles, strips, scene->view.bg, st));
     TIGAS_CUDA_TRY(cudaMemcpyAsync(ctx.h_flags, d_flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     if (stat) TIGAS_CUDA_TRY(cudaMemcpyAsync(ctx.h_total, d_total, sizeof(uint64_t) * S, cudaMemcpyDeviceToHost, st));
     if (res) {

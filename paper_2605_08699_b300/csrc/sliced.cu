@@ -34,32 +34,47 @@ __device__ inline uint8_t to_u8(float x) {
     return (uint8_t)__float2uint_rd(fminf(fmaxf(x, 0.0f), 1.0f) * 255.0f + 0.5f);
 }
 
-// State (C = 0, T = 1) and background outputs for every pixel; one CTA per tile.
+// Per-launch-set clearing for the slices, a thread per tile: done bits, strip
+// words (bits 0-3: strip s finished; kStripSeen: the tile carries (C, T) from
+// a blended slice), and the slice totals.  No pixel is touched: a tile's first
+// blend starts from (C, T) = (0, 1), and k_fill_unseen writes the background
+// of tiles no slice blended.
 __global__ void __launch_bounds__(256)
-k_init_state(const ViewParams* __restrict__ views_g, int V, const uint64_t* __restrict__ pix_base, float4* state,
-             float bg_r, float bg_g, float bg_b, uint32_t* __restrict__ done, uint32_t* __restrict__ strips,
-             unsigned long long* __restrict__ totals, int n_totals) {
-    __shared__ uint32_t s_tb[kMaxViews];
-    for (int k = threadIdx.x; k < V; k += blockDim.x) s_tb[k] = views_g[k].tile_base;
-    const uint32_t g = blockIdx.x;
-    // the slices' per-tile state: nothing done, no strip finished; slice totals 0
-    if (threadIdx.x == 0) {
+k_init_slices(uint32_t total_tiles, uint32_t* __restrict__ done, uint32_t* __restrict__ strips,
+              unsigned long long* __restrict__ totals, int n_totals) {
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < total_tiles) {
         strips[g] = 0u;
         if ((g & 31u) == 0u) done[g >> 5] = 0u;
     }
-    if (g == 0 && (int)threadIdx.x < n_totals) totals[threadIdx.x] = 0ull;
+    if (g < (uint32_t)n_totals) totals[g] = 0ull;
+}
+
+// Background outputs of the tiles that no slice blended (a warp per tile).
+__global__ void __launch_bounds__(256)
+k_fill_unseen(const ViewParams* __restrict__ views_g, int V, uint32_t total_tiles, const uint32_t* __restrict__ strips,
+              float bg_r, float bg_g, float bg_b) {
+    __shared__ uint32_t s_tb[kMaxViews];
+    for (int k = threadIdx.x; k < V; k += blockDim.x) s_tb[k] = views_g[k].tile_base;
     __syncthreads();
+    const uint32_t g = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (g >= total_tiles) return;
+    if (strips[g] & kStripSeen) return;   // warp-uniform
+    const int lane = threadIdx.x & 31;
     const int v = view_of_tile(s_tb, V, g);
     const ViewParams& vp = views_g[v];
     const uint32_t local = g - s_tb[v];
-    const int px = (int)(local % vp.TX) * kTile + (threadIdx.x & 15);
-    const int py = (int)(local / vp.TX) * kTile + (threadIdx.x >> 4);
-    if (px >= vp.W || py >= vp.H) return;
-    const size_t pix = (size_t)py * vp.W + px;
-    state[pix_base[v] + pix] = make_float4(0.f, 0.f, 0.f, 1.0f);
-    if (vp.out_rgba8)
-        reinterpret_cast<uchar4*>(vp.out_rgba8)[pix] = make_uchar4(to_u8(bg_r), to_u8(bg_g), to_u8(bg_b), 0);
-    if (vp.out_rgba_f32) reinterpret_cast<float4*>(vp.out_rgba_f32)[pix] = make_float4(bg_r, bg_g, bg_b, 0.f);
+    const int px = (int)(local % vp.TX) * kTile + (lane & 15);
+    const int ty0 = (int)(local / vp.TX) * kTile;
+    const uchar4 b8 = make_uchar4(to_u8(bg_r), to_u8(bg_g), to_u8(bg_b), 0);
+#pragma unroll
+    for (int k = 0; k < kTile / 2; ++k) {
+        const int py = ty0 + (lane >> 4) + 2 * k;
+        if (px >= vp.W || py >= vp.H) continue;
+        const size_t pix = (size_t)py * vp.W + px;
+        if (vp.out_rgba8) reinterpret_cast<uchar4*>(vp.out_rgba8)[pix] = b8;
+        if (vp.out_rgba_f32) reinterpret_cast<float4*>(vp.out_rgba_f32)[pix] = make_float4(bg_r, bg_g, bg_b, 0.f);
+    }
 }
 
 __device__ inline bool tile_done(const uint32_t* __restrict__ done, uint32_t t) {
@@ -364,13 +379,21 @@ k_ranges_active(const uint32_t* __restrict__ keys, uint64_t n_cap, const uint64_
 
 }  // namespace
 
-Status launch_init_state(const ViewParams* views, int V, uint32_t total_tiles, const uint64_t* pix_base,
-                         float4* state, const float* bg, uint32_t* done, uint32_t* strips, uint64_t* totals,
-                         int n_totals, cudaStream_t st) {
-    if (total_tiles == 0) return {};
+Status launch_init_slices(uint32_t total_tiles, uint32_t* done, uint32_t* strips, uint64_t* totals, int n_totals,
+                          cudaStream_t st) {
     if (n_totals > 256) return {TIGAS_ERR_INVALID, "too many slice totals"};
-    k_init_state<<<total_tiles, 256, 0, st>>>(views, V, pix_base, state, bg[0], bg[1], bg[2], done, strips,
-                                              reinterpret_cast<unsigned long long*>(totals), n_totals);
+    const uint32_t n = total_tiles > (uint32_t)n_totals ? total_tiles : (uint32_t)n_totals;
+    if (n == 0) return {};
+    k_init_slices<<<(n + 255) / 256, 256, 0, st>>>(total_tiles, done, strips,
+                                                   reinterpret_cast<unsigned long long*>(totals), n_totals);
+    TIGAS_LAUNCHED();
+    return {};
+}
+
+Status launch_fill_unseen(const ViewParams* views, int V, uint32_t total_tiles, const uint32_t* strips,
+                          const float* bg, cudaStream_t st) {
+    if (total_tiles == 0) return {};
+    k_fill_unseen<<<(total_tiles + 7) / 8, 256, 0, st>>>(views, V, total_tiles, strips, bg[0], bg[1], bg[2]);
     TIGAS_LAUNCHED();
     return {};
 }

@@ -12,15 +12,22 @@ constexpr uint32_t kHeavyTile = TIGAS_HEAVY_TILE;   // pairs of a slice that mak
 // Active-list items: a tile id (whole tile) or tile id | (s + 1) << kStripShift
 // for strip s (pixel rows 4s..4s+3) of a long tile.
 constexpr int kStripShift = 28;
+// Strip-word bit of a tile that some slice blended: its pixels carry (C, T)
+// in the state (bits 0-3: strip s's pixels all stopped).
+constexpr uint32_t kStripSeen = 0x10u;
 constexpr uint32_t kTileMask = (1u << kStripShift) - 1u;
 
-// (C, T) = (0, 1) for every pixel of every view, background in the outputs;
-// also clears the per-tile done bits (total_tiles bits) and strip words, and
-// totals[0 .. n_totals) (at most 256).
-// pix_base[v]: offset of view v's first pixel in `state`.
-Status launch_init_state(const ViewParams* views, int V, uint32_t total_tiles, const uint64_t* pix_base,
-                         float4* state, const float* bg, uint32_t* done, uint32_t* strips, uint64_t* totals,
-                         int n_totals, cudaStream_t st);
+// Clears the per-tile done bits (total_tiles bits) and strip words (bits 0-3:
+// strip s of the tile finished; kStripSeen: the tile was blended and its
+// pixels carry (C, T) in `state`, so its first blend starts from (0, 1)
+// instead), and totals[0 .. n_totals) (at most 256).  No pixel is written.
+Status launch_init_slices(uint32_t total_tiles, uint32_t* done, uint32_t* strips, uint64_t* totals, int n_totals,
+                          cudaStream_t st);
+
+// After the last slice: the background in the outputs of every tile that no
+// slice blended (kStripSeen clear).
+Status launch_fill_unseen(const ViewParams* views, int V, uint32_t total_tiles, const uint32_t* strips,
+                          const float* bg, cudaStream_t st);
 
 // Per view, the summed-area table of tiles not done: sat[sat_base + y (TX+1) + x]
 // = not-done tiles in columns [0, x) of rows [0, y).  Also clears
@@ -66,10 +73,12 @@ struct SliceBlendArgs {
     const uint32_t* active;
     const uint32_t* n_active;   // [long tiles at the front, short tiles at the back]
     uint32_t* work_counter;     // zero on entry (launch_running_sat clears it)
-    float4* state;              // per pixel (C.rgb, T), T negated once the pixel stopped
+    float4* state;              // per pixel (C.rgb, T), T negated once the pixel stopped; valid for the
+                                // tiles whose strip word has kStripSeen
     const uint64_t* pix_base;   // per view
     uint32_t* done;             // per-tile bitmap
-    uint32_t* strips;           // per tile: bit s set once strip s's pixels all stopped
+    uint32_t* strips;           // per tile: bit s set once strip s's pixels all stopped, kStripSeen once
+                                // a slice blended it (its pixels carry state)
     uint32_t active_cap;        // capacity of `active` (4 x all tiles of the launch set)
 };
 Status launch_blend_slice(const uint2* ranges, const uint32_t* values, const SplatArrays& sp,
