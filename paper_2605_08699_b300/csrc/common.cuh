@@ -14,6 +14,9 @@
 namespace tigas {
 
 constexpr int kTile = 16;              // 16x16 pixel tiles
+// SMs of a B300 (two dies of 74).  Grid-size heuristics only: every kernel is
+// correct for any grid it sizes from this.
+constexpr int kSmCount = 148;
 constexpr int kMaxViews = 64;          // views per fused launch set
 constexpr int kMaxDim = 8192;          // largest width / height accepted
 

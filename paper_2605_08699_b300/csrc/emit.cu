@@ -138,7 +138,7 @@ k_ranges(const K* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, int sh
 namespace {
 unsigned emit_grid(uint64_t n_entries) {
     const uint64_t want = (n_entries + kEmitThreads - 1) / kEmitThreads;
-    const uint64_t cap = 148ull * 32;   // grid-stride beyond 32 CTAs per SM
+    const uint64_t cap = (uint64_t)kSmCount * 32;   // grid-stride beyond 32 CTAs per SM
     return (unsigned)(want < cap ? want : cap);
 }
 }  // namespace

@@ -410,7 +410,7 @@ Status ply_decode(const char* path, const PlyLayout& lay, float* means, float* l
         }
     }
     const uint64_t total = lay.n * kPlyFields;
-    const unsigned grid = (unsigned)std::min<uint64_t>((total + 255) / 256, 148ull * 16);
+    const unsigned grid = (unsigned)std::min<uint64_t>((total + 255) / 256, (uint64_t)kSmCount * 16);
     k_ply_gather<<<grid, 256, 0, st>>>((const uint8_t*)rows.p, lay.n, row_bytes, map, means, log_scales, quats,
                                        logits, sh);
     TIGAS_LAUNCHED();

@@ -427,7 +427,7 @@ Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64
     // 4 waves of 8 CTAs per SM (slices with many pairs per entry want the warps)
     const uint64_t n = b - a;
     int J = 1;
-    while (J < 8 && n >= (uint64_t)(2 * J) * kEmitThreads * 148 * 8 * 4) J *= 2;
+    while (J < 8 && n >= (uint64_t)(2 * J) * kEmitThreads * kSmCount * 8 * 4) J *= 2;
     const unsigned grid = (unsigned)((n + (uint64_t)J * kEmitThreads - 1) / ((uint64_t)J * kEmitThreads));
 #define TIGAS_EMIT(JJ)                                                                                              \
     do {                                                                                                            \

@@ -950,7 +950,7 @@ Status radix_sort_onesweep(const K* keys_in, const uint32_t* values_in, K* keys_
     // eight grid strides, at most 8 CTAs per SM (a vector step covers 4 keys per load)
     const uint64_t hist_step = (uint64_t)512 * (vec ? kHistVecs * 4 : kHistKeys) * 8;
     const uint64_t hist_ctas = (n_cap + hist_step - 1) / hist_step;
-    const unsigned hgrid = (unsigned)(hist_ctas < 148 ? 148 : (hist_ctas > 148 * 8 ? 148 * 8 : hist_ctas));
+    const unsigned hgrid = (unsigned)(hist_ctas < kSmCount ? kSmCount : (hist_ctas > kSmCount * 8 ? kSmCount * 8 : hist_ctas));
     if (vec)
         k_os_hist<K, kHistVecs, true><<<hgrid, 512, 0, st>>>(
             keys_in, n_cap, d_n, begin_bit, end_bit, ghist, range, reinterpret_cast<uint4*>(status), chunks, (uint32_t)N);
