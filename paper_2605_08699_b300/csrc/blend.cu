@@ -135,17 +135,23 @@ __device__ __forceinline__ bool blend_rows(WarpStage& sm, int lane, const uint2*
     uint32_t live = 0;   // bit k: pixel k still compositing
     // the tile's pixels carry (C, T) from an earlier slice (a slice blends all
     // four strips of a long tile, so a tile's strips are blended together);
-    // otherwise they start from (0, 1) without reading the state
-    const bool carried = SLICED && (sl.strips[g] & kStripSeen) != 0u;
+    // otherwise they start from (0, 1).  The state is read together with the
+    // strip word rather than after it (one dependent load less per visit; on a
+    // first visit the words read are in bounds and unused)
+    const uint32_t sw = SLICED ? sl.strips[g] : 0u;
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
         T[k] = 1.0f; cr[k] = 0.0f; cg[k] = 0.0f; cb[k] = 0.0f;
         const int py = py0 + 2 * k;
         if (px < W && py < H) {
-            if (carried) {
+            if (SLICED) {
                 const float4 s0 = sl.state[sbase + (size_t)py * W + px];
-                cr[k] = s0.x; cg[k] = s0.y; cb[k] = s0.z; T[k] = fabsf(s0.w);
-                if (!(s0.w < 0.0f)) live |= 1u << k;
+                if (sw & kStripSeen) {
+                    cr[k] = s0.x; cg[k] = s0.y; cb[k] = s0.z; T[k] = fabsf(s0.w);
+                    if (!(s0.w < 0.0f)) live |= 1u << k;
+                } else {
+                    live |= 1u << k;
+                }
             } else {
                 live |= 1u << k;
             }
@@ -295,7 +301,7 @@ __device__ __forceinline__ bool blend_rows(WarpStage& sm, int lane, const uint2*
         }
     }
     // the tile's pixels now carry state (and have their outputs written)
-    if (SLICED && !carried && lane == 0) atomicOr(&sl.strips[g], kStripSeen);
+    if (SLICED && !(sw & kStripSeen) && lane == 0) atomicOr(&sl.strips[g], kStripSeen);
     return all;
 }
 
