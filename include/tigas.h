@@ -98,13 +98,21 @@ tigas_status tigas_scene_load(const tigas_scene_desc* desc, tigas_scene** out_sc
  * "Dynamic Multi-Model Runtime").  NULL is INVALID. */
 tigas_status tigas_scene_free(tigas_scene* scene);
 
-/* Resident bytes of a scene's attribute storage. */
+/* Resident bytes of a scene's attribute storage (the persistent VRAM
+ * residency of Sec. 4.1 "GPU Backend"). */
 tigas_status tigas_scene_bytes(const tigas_scene* scene, uint64_t* out_bytes);
 
-/* Render one frame (the hot path: preprocess, scan, duplicate-and-key emit,
- * radix sort, tile ranges, per-tile blend).  out_rgba8: width*height*4 bytes,
- * host or device.  Synchronous: returns after the frame is in out_rgba8.
- * width, height in 1..8192.  Errors: INVALID, OOM, CUDA. */
+/* Render one frame: the backend's rendering engine (Sec. 4.1 "Rendering
+ * Engine": the tile-based rasterizer that projects the Gaussians onto the
+ * image plane, cited to 3DGS), with the camera of Sec. 5.1 "Rendering Engine"
+ * (T_{w->c} from the pose, pinhole K) at the resolution the client's ABR asked
+ * for (Sec. 4.1: ABR-driven downscaled frames; Sec. 5.3 "Viewport Display":
+ * intrinsics scaled with the resolution).  Each call is one isolated,
+ * stateless render task (Sec. 4.2).  The hot path: preprocess, scan,
+ * duplicate-and-key emit, radix sort, tile ranges, per-tile blend.
+ * out_rgba8: width*height*4 bytes, host or device.  Synchronous: returns after
+ * the frame is in out_rgba8.  width, height in 1..8192.
+ * Errors: INVALID, OOM, CUDA. */
 tigas_status tigas_render(tigas_scene* scene, const tigas_pose* pose, const tigas_intrinsics* intr,
                           int width, int height, uint8_t* out_rgba8);
 
@@ -138,7 +146,9 @@ typedef struct {
     uint32_t reserved;
 } tigas_frame_stats;
 
-/* tigas_render with options.
+/* tigas_render with options (same passages: Sec. 4.1, 5.1, 4.2).  The float
+ * output is the composite before the 8-bit encoding that the frame payload
+ * of Sec. 5.1 ("8-bit JPEG payloads") starts from.
  *   out_rgba8:     width*height*4 bytes, host or device, or NULL
  *   out_rgba_f32:  width*height*4 floats (RGB + alpha before 8-bit encoding),
  *                  host or device, or NULL (at least one output is required)
@@ -152,7 +162,10 @@ tigas_status tigas_render_ex(tigas_scene* scene, const tigas_pose* pose, const t
 
 /* Render n_views (1..64) poses of one scene in one fused launch set
  * (batching): one preprocess pass reads the scene once for all views, one
- * sort orders every view's pairs.  Views may have different resolutions.
+ * sort orders every view's pairs.  This serves many clients' requests from
+ * one shared resident model (Sec. 5.1 "Dynamic Multi-Model Runtime"); each
+ * view stays its own stateless task (Sec. 4.2) and is rendered as tigas_render
+ * renders it (Sec. 4.1, 5.1); fusing them is this library's, not the paper's.  Views may have different resolutions.
  * outs[v]: widths[v]*heights[v]*4 bytes, host or device.  Each result equals
  * the frame a separate tigas_render call gives.  Synchronous.
  * Errors: INVALID, OOM, CUDA. */
@@ -161,12 +174,14 @@ tigas_status tigas_render_batch(tigas_scene* scene, int n_views, const tigas_pos
                                 uint8_t* const* outs, void* cuda_stream);
 
 /* tigas_render_batch with a schedule (TIGAS_SORT_*) and statistics summed
- * over the views (stats may be NULL). */
+ * over the views (stats may be NULL).  Passages as tigas_render_batch
+ * (Sec. 4.1, 4.2, 5.1). */
 tigas_status tigas_render_batch_ex(tigas_scene* scene, int n_views, const tigas_pose* poses,
                                    const tigas_intrinsics* intrs, const int* widths, const int* heights,
                                    uint8_t* const* outs, void* cuda_stream, int sort_mode, tigas_frame_stats* stats);
 
-/* Asynchronous tigas_render_batch (SLICED schedule): enqueue the launch set on
+/* Asynchronous tigas_render_batch (SLICED schedule; passages as
+ * tigas_render_batch, Sec. 4.1, 4.2, 5.1): enqueue the launch set on
  * cuda_stream (NULL: the library's own stream) and return at once with a
  * ticket.  Host outputs (pinned, for the call to stay asynchronous) are
  * copied back on a copy stream of the ticket's own, which overlaps the
@@ -186,8 +201,10 @@ tigas_status tigas_render_wait(tigas_ticket* ticket);
 
 /* ------------------------------------------------------------------ debug */
 
-/* Intermediate results of one frame, for parity tests.  Host arrays, all
- * caller-allocated; any may be NULL.
+/* Intermediate results of one frame of the tile-based rasterizer (Sec. 4.1
+ * "Rendering Engine", cited 3DGS): per-Gaussian projection results, the
+ * (tile, depth)-sorted pair list and the tile ranges, for parity tests.
+ * Host arrays, all caller-allocated; any may be NULL.
  *   visible[n] (uint8), radius[n] (int32), rect[n*4] (int32: x_lo, y_lo,
  *   x_hi, y_hi, half-open, in tiles), depth[n] (float32 view z),
  *   uv[n*2] (float32), q[n] (float32 3 sqrt(lambda_max)),
@@ -213,7 +230,8 @@ tigas_status tigas_debug_render(tigas_scene* scene, const tigas_pose* pose, cons
                                 uint64_t* out_pairs);
 
 /* Stable ascending LSD radix sort of n (key, value) pairs on the device (the
- * sort of the hot path, exposed for testing), sorting key bits
+ * (tile | depth) key sort of the tile-based rasterizer of Sec. 4.1, cited
+ * 3DGS; exposed for testing), sorting key bits
  * [begin_bit, end_bit) (0 <= begin_bit < end_bit <= 64).  keys: uint64,
  * values: uint32; *_in and *_out are distinct device buffers of n elements;
  * inputs are left unchanged.  Library-owned scratch.  Synchronous on
@@ -235,16 +253,38 @@ tigas_status tigas_sort_pairs_u64(const uint64_t* keys_in, const uint32_t* value
  *     TIGAS_ERR_INVALID with a message naming the limit.
  *   - The first call on a device looks up that device's scratch address
  *     (cudaGetSymbolAddress) with the device current; make that first call
- *     before any stream capture.
+ *     before any stream capture.  cuda_stream, when not NULL, must belong to
+ *     the current device (else TIGAS_ERR_INVALID).
  *   - Asynchronous: returns once the work is queued on cuda_stream (NULL: the
  *     legacy default stream); outputs are ready when the stream gets there.
  *   - All calls on a device share the scratch and it keeps the last call's
  *     contents: calls whose work overlaps on the GPU (different streams or
  *     host threads without ordering between them) race and corrupt each other.
- * Arguments and result as tigas_sort_pairs_u64. */
+ *   - Being asynchronous, the call cannot return TIGAS_ERR_TIMEOUT: a sort
+ *     whose bounded look-back wait ran out (see tigas_debug_sort_wait_timeout)
+ *     leaves an untrusted order and records the event in a sticky per-device
+ *     word instead.  tigas_sort_noalloc_check reports and clears it.
+ * Other arguments, layout and errors as tigas_sort_pairs_u64. */
 tigas_status tigas_sort_pairs_u64_noalloc(const uint64_t* keys_in, const uint32_t* values_in, uint64_t* keys_out,
                                           uint32_t* values_out, uint64_t n, int begin_bit, int end_bit,
                                           void* cuda_stream);
+
+/* Completion check of tigas_sort_pairs_u64_noalloc (no counterpart in the
+ * paper).  Waits for cuda_stream (NULL: the legacy default stream), then reads
+ * and clears the current device's sticky timeout word: TIGAS_ERR_TIMEOUT when
+ * a look-back wait of any allocation-free sort since the previous check ran
+ * out (those sorts' outputs are not to be trusted), else TIGAS_OK.  Sorts
+ * queued on other streams must have completed for the answer to cover them.
+ * Allocates nothing.  Errors: INVALID (stream of another device), CUDA. */
+tigas_status tigas_sort_noalloc_check(void* cuda_stream);
+
+/* Failure-detection hook for tests (no counterpart in the paper): the probe
+ * of tigas_debug_sort_wait_timeout run inside the allocation-free sort's
+ * scratch, recording its run-out wait in the sticky word that
+ * tigas_sort_noalloc_check reads.  Queued on cuda_stream; it overwrites the
+ * scratch like a sort does.  Errors: INVALID (spin_limit not in 1..2^20,
+ * stream of another device), CUDA. */
+tigas_status tigas_debug_sort_noalloc_wait_timeout(int spin_limit, void* cuda_stream);
 
 /* ---------------------------------------------------------------- serving */
 
@@ -271,7 +311,8 @@ typedef struct {
  * (continuous batching, Sec. 5.1 multi-client runtime).  Errors: INVALID, OOM, CUDA. */
 tigas_status tigas_server_create(const tigas_server_config* cfg, tigas_server** out_server);
 
-/* Finish queued work (cancel=0) or complete queued requests with
+/* Server lifecycle of the multi-client runtime (Sec. 5.1).
+ * Finish queued work (cancel=0) or complete queued requests with
  * TIGAS_ERR_AGAIN (cancel=1), stop the thread and free the server. */
 tigas_status tigas_server_destroy(tigas_server* server, int cancel);
 
@@ -284,14 +325,18 @@ tigas_status tigas_server_submit(tigas_server* server, tigas_scene* scene, const
                                  const tigas_intrinsics* intr, int width, int height, uint8_t* out_rgba8,
                                  uint64_t client_id, uint64_t* out_ticket);
 
-/* Collect up to max completions, waiting up to timeout_us (0: do not wait)
+/* Completions of submitted requests, one per stateless per-frame task
+ * (Sec. 4.2), each with its own status so that one failed request does not
+ * affect the others.
+ * Collect up to max completions, waiting up to timeout_us (0: do not wait)
  * for at least one.  *n_done receives the count (0 on timeout). */
 tigas_status tigas_server_poll(tigas_server* server, tigas_completion* out, int max, int timeout_us,
                                int* n_done);
 
 /* ------------------------------------------------------------- profiling */
 
-/* Per-stage GPU time, measured with CUDA events recorded on the stream each
+/* Profiling (a library facility; the paper reports only whole-frame times,
+ * Sec. 6 "Results").  Per-stage GPU time, measured with CUDA events recorded on the stream each
  * stage is launched on (a start and a stop event per stage, so host gaps
  * between stages are not charged to any stage).  Stages: 0 preprocess,
  * 1 depth sort, 2 scan, 3 emit, 4 pair sort, 5 ranges, 6 blend, and 7 the
@@ -312,7 +357,9 @@ tigas_status tigas_profile_read(double* ms, uint64_t* calls, int reset);
 
 /* ------------------------------------------------------------ scheduling */
 
-/* Parameters of the depth-sliced schedule every launch set takes.  Frames do
+/* Scheduling (a library facility with no counterpart in the paper: the
+ * paper does not describe how its rasterizer is scheduled on the GPU).
+ * Parameters of the depth-sliced schedule every launch set takes.  Frames do
  * not depend on them (only the time to render them does).
  *  n_slices:          depth slices, 1..16 (default 8)
  *  first_slice_inv:   the nearest slice holds 1/first_slice_inv of the kept
@@ -503,7 +550,8 @@ tigas_status tigas_image_quality(const uint8_t* a, const uint8_t* b, int width, 
                                  double* out_ssim, double* out_psnr, void* cuda_stream);
 
 /* Launch sets that ran with a fixed pair capacity (graph replay or a shape's
- * first launch set), outgrew it and were rendered again exactly, since load. */
+ * first launch set), outgrew it and were rendered again exactly, since load
+ * (scheduling facility; no counterpart in the paper). */
 uint64_t tigas_exact_rerenders(void);
 
 /* Failure-detection hook for tests (no counterpart in the paper).  Runs one
@@ -516,7 +564,27 @@ uint64_t tigas_exact_rerenders(void);
  * allocates and frees its own ~140 KB of device memory. */
 tigas_status tigas_debug_sort_wait_timeout(int spin_limit);
 
-/* Launch sets of the sliced schedule are captured as CUDA graphs per shape
+/* Host-side fault injection for tests (no counterpart in the paper; the
+ * failures it stands for are the ones Sec. 5.3 "Viewport Display" shows to
+ * the user and Sec. 4.2 confines to one request).  Every device (kind 0) and
+ * pinned host (kind 1) allocation the library makes goes through one
+ * counter per kind: after this call, allocations nth .. nth + count - 1 of
+ * that kind (1 = the next one) fail as if the memory were exhausted, without
+ * calling the CUDA allocator, and the calls that made them return
+ * TIGAS_ERR_OOM with a message.  nth = 0 clears the kind.  Nothing is asked
+ * of the GPU: no fault, trap or hang is involved.  Process-wide.
+ * Errors: INVALID (kind not 0/1, nth < 0, count < 1 with nth > 0). */
+tigas_status tigas_debug_fail_alloc(int kind, int64_t nth, int64_t count);
+
+/* Free the workspace of every render context that no call is using (device
+ * arenas, captured CUDA graphs, output staging, pinned buffers); later calls
+ * allocate it again (a library facility, like returning cached memory to the
+ * device; no counterpart in the paper).  Scenes, servers and outstanding
+ * tickets are not affected.  Always TIGAS_OK. */
+tigas_status tigas_release_workspace(void);
+
+/* Scheduling facility (no counterpart in the paper).
+ * Launch sets of the sliced schedule are captured as CUDA graphs per shape
  * (scene, view count and resolutions) when a shape appears a second time, and
  * replayed from then on.  A shape's first launch set runs directly with a
  * pair capacity per slice taken from the largest slice seen so far (exactly,
@@ -528,13 +596,16 @@ tigas_status tigas_set_graphs(int enable);
 
 /* ------------------------------------------------------------------ misc */
 
-/* Message of the last failed call on this thread ("" if none). */
+/* Message of the last failed call on this thread ("" if none): the short
+ * text a client shows in place of the frame when a request fails (Sec. 5.3
+ * "Viewport Display": errors replace the viewport with a short message). */
 const char* tigas_last_error(void);
 
-/* Library version string. */
+/* Library version string (no counterpart in the paper). */
 const char* tigas_version(void);
 
-/* Kernel launches issued by this process so far (all entry points). */
+/* Kernel launches issued by this process so far (all entry points; no
+ * counterpart in the paper). */
 uint64_t tigas_kernel_launches(void);
 
 #ifdef __cplusplus

@@ -20,7 +20,9 @@
  *      supported Gaussian in (depth, index) order, skipping alpha < 1/255
  *      and stopping before the Gaussian that would bring T below 1e-4.
  *
- * Readings where the paper is silent (each also listed in the design notes):
+ * Readings where the paper is silent (the CUDA path takes the same ones;
+ * the projection and compositing constants are those of the cited 3DGS
+ * method, the pose and pixel conventions are this implementation's own):
  *   pose R = R_y(azimuth) R_x(elevation), camera axes x right, y down,
  *   z forward; pixel (i,j) sampled at (i+0.5, j+0.5); near plane z > 0.2;
  *   EWA guard band 1.3 x half-FOV; alpha cap 0.99; depth key = view z;

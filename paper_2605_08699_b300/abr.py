@@ -1,4 +1,6 @@
-"""Receiver-driven resolution control of the serving loop (Sec. 5.2).
+"""Receiver-driven resolution control of the serving loop (Sec. 4.3 "ABR
+Controller" for the design, Sec. 5.3 "Throughput Monitoring" and "ABR
+Controller" for the implementation).
 
 ``ThroughputEMA`` is the client's throughput monitor: one sample per
 finished request, S_i / dt_i (bytes over download seconds), smoothed by an

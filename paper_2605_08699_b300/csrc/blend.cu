@@ -88,8 +88,9 @@ __device__ inline float ex2_approx(float x) {
     return y;
 }
 
+// floor(clamp(x, 0, 1) 255 + 0.5) with one rounding of the fused x 255 + 0.5
 __device__ inline uint8_t to_u8(float x) {
-    return (uint8_t)__float2uint_rd(fminf(fmaxf(x, 0.0f), 1.0f) * 255.0f + 0.5f);
+    return (uint8_t)__float2uint_rd(__fmaf_rn(fminf(fmaxf(x, 0.0f), 1.0f), 255.0f, 0.5f));
 }
 
 // Does the alpha >= 1/255 region of the entry meet the pixel-centre rectangle

@@ -51,7 +51,7 @@ Status staging(RenderContext& ctx, int slot, size_t bytes, uint8_t** out) {
         if (ctx.dev_staging[slot]) cudaFree(ctx.dev_staging[slot]);
         ctx.dev_staging[slot] = nullptr;
         ctx.staging_bytes[slot] = 0;
-        TIGAS_CUDA_TRY(cudaMalloc(&ctx.dev_staging[slot], bytes));
+        TIGAS_CUDA_TRY(device_alloc(&ctx.dev_staging[slot], bytes));
         ctx.staging_bytes[slot] = bytes;
     }
     *out = ctx.dev_staging[slot];
@@ -194,7 +194,7 @@ Status finish_render(RenderContext& ctx, cudaStream_t st, PendingRender& p) {
     }
     if (ctx.h_flags[0] & 1u) return {TIGAS_ERR_OVERFLOW, "pair buffer overflow"};
     if (ctx.h_flags[0] & 2u) return {TIGAS_ERR_CUDA, "tile id out of range in sorted keys"};
-    if (ctx.h_flags[0] & 16u) return {TIGAS_ERR_TIMEOUT, "radix sort look-back wait ran out"};
+    if (ctx.h_flags[0] & kSortTimeoutFlag) return {TIGAS_ERR_TIMEOUT, "radix sort look-back wait ran out"};
     return {};
 }
 
@@ -438,6 +438,20 @@ TIGAS_API tigas_status tigas_image_quality(const uint8_t* a, const uint8_t* b, i
     return s.ok() ? TIGAS_OK : fail(s);
 }
 
+TIGAS_API tigas_status tigas_debug_fail_alloc(int kind, int64_t nth, int64_t count) {
+    set_error("");
+    if (kind != 0 && kind != 1) return fail(TIGAS_ERR_INVALID, "kind must be 0 (device) or 1 (pinned host)");
+    if (nth < 0 || count < 0 || (nth > 0 && count < 1)) return fail(TIGAS_ERR_INVALID, "nth >= 0, count >= 1");
+    inject_alloc_failures(kind, nth, count);
+    return TIGAS_OK;
+}
+
+TIGAS_API tigas_status tigas_release_workspace(void) {
+    set_error("");
+    release_idle_contexts();
+    return TIGAS_OK;
+}
+
 TIGAS_API tigas_status tigas_debug_sort_wait_timeout(int spin_limit) {
     bool timed_out = false;
     Status s = debug_lookback_timeout(spin_limit, &timed_out);
@@ -486,7 +500,7 @@ TIGAS_API tigas_status tigas_scene_load(const tigas_scene_desc* d, tigas_scene**
     };
     if (!d->inputs_on_device) {
         const size_t words = (size_t)n * (3 + 3 + 4 + 1 + 48);
-        cudaError_t e = cudaMalloc(&staging_buf, words * 4);
+        cudaError_t e = device_alloc(&staging_buf, words * 4);
         if (e != cudaSuccess) {
             cudaGetLastError();
             staging_buf = nullptr;
@@ -676,6 +690,6 @@ TIGAS_API tigas_status tigas_sort_pairs_u64(const uint64_t* keys_in, const uint3
     e = cudaMemcpyAsync(g.ctx->h_flags, d_flags, 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(TIGAS_ERR_CUDA, cudaGetErrorString(e));
-    if (g.ctx->h_flags[0] & 16u) return fail(TIGAS_ERR_TIMEOUT, "radix sort look-back wait ran out");
+    if (g.ctx->h_flags[0] & kSortTimeoutFlag) return fail(TIGAS_ERR_TIMEOUT, "radix sort look-back wait ran out");
     return TIGAS_OK;
 }

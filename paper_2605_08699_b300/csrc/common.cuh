@@ -19,6 +19,7 @@ constexpr int kTile = 16;              // 16x16 pixel tiles
 constexpr int kSmCount = 148;
 constexpr int kMaxViews = 64;          // views per fused launch set
 constexpr int kMaxDim = 8192;          // largest width / height accepted
+constexpr int kMaxDevices = 64;        // device ordinals with their own one-time set-up
 
 // ---------------------------------------------------------------- errors
 
@@ -47,6 +48,24 @@ struct Status {
         ::tigas::Status s__ = (expr);       \
         if (!s__.ok()) return s__;          \
     } while (0)
+
+// Every device and pinned-host allocation of the library goes through these,
+// so that tests can make the nth one fail (tigas_debug_fail_alloc): the failure
+// is injected on the host, as cudaErrorMemoryAllocation, and nothing is asked of
+// the GPU.  kind 0: device memory, kind 1: pinned host memory.
+cudaError_t device_alloc(void** p, size_t bytes);
+cudaError_t pinned_alloc(void** p, size_t bytes);
+template <typename T>
+inline cudaError_t device_alloc(T** p, size_t bytes) {
+    return device_alloc(reinterpret_cast<void**>(p), bytes);
+}
+template <typename T>
+inline cudaError_t pinned_alloc(T** p, size_t bytes) {
+    return pinned_alloc(reinterpret_cast<void**>(p), bytes);
+}
+// Arm (nth >= 1) or clear (nth = 0) the injection for one kind: allocations
+// nth .. nth + count - 1 from now fail.
+void inject_alloc_failures(int kind, int64_t nth, int64_t count);
 
 // Check a launch and count it.
 #define TIGAS_LAUNCHED()                                                        \

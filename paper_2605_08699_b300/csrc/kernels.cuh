@@ -45,8 +45,9 @@ Status launch_emit_u64(const uint32_t* offsets, const SplatArrays& sp, const Vie
 // The element count is min(*d_n, n_cap) when d_n is given, else n_cap.
 // values_in == nullptr means values 0..n-1.  keys_alt/values_alt are the
 // ping-pong buffers; the sorted result lands in (keys_out, values_out).
-// tmp: radix_tmp_words(n_cap) words.  flags (optional device word): bit 16 is
-// set when a look-back wait ran out (the result is then not to be trusted).
+// tmp: radix_tmp_words(n_cap) words.  flags (optional device word): the sort
+// ORs kSortTimeoutFlag into it when a look-back wait ran out (the result is
+// then not to be trusted); without flags the bit goes to a word of tmp.
 // A pass whose digit is the same for every key is skipped on the device.
 // ex (optional, 32-bit keys only):
 //   key_range: device [kmin, kmax] of the keys other than 0xFFFFFFFF; digits
@@ -56,6 +57,7 @@ Status launch_emit_u64(const uint32_t* offsets, const SplatArrays& sp, const Vie
 //   pay_in / pay_alt / pay_out: an 8-byte payload per key moved with it.
 // With a payload, values_in, values_alt and values_out may all be null: no
 // value stream is read or written (the payload identifies each key).
+constexpr uint32_t kSortTimeoutFlag = 16u;
 struct SortExtras {
     const uint32_t* key_range = nullptr;
     const uint2* pay_in = nullptr;
@@ -77,12 +79,18 @@ Status radix_sort(const K* keys_in, const uint32_t* values_in, K* keys_alt, uint
                   int end_bit, uint32_t* tmp, cudaStream_t st, int* passes_out, uint32_t* flags = nullptr,
                   const SortExtras* ex = nullptr);
 
-// K5: tile ranges from sorted keys (tile = key >> shift), binary search per
-// tile.  ranges: n_tiles uint2.  A key outside [0, n_tiles) sets *overflow bit 2.
 // Test hook: one radix-sort scatter CTA whose look-back waits on a chunk that
 // no CTA publishes; *timed_out tells whether it recorded the timeout flag.
+// Synchronous; allocates its own buffer of debug_lookback_words() words.
 Status debug_lookback_timeout(int spin_limit, bool* timed_out);
+// The same probe enqueued on st in buf (debug_lookback_words() words, 16-byte
+// aligned, no other requirement: it initialises what it reads); the timeout
+// flag is ORed into *flags (null: a word of buf).
+size_t debug_lookback_words();
+Status debug_lookback_enqueue(int spin_limit, uint32_t* buf, uint32_t* flags, cudaStream_t st);
 
+// K5: tile ranges from sorted keys (tile = key >> shift), binary search per
+// tile.  ranges: n_tiles uint2.  A key outside [0, n_tiles) sets *overflow bit 2.
 template <typename K>
 Status launch_ranges(const K* keys, uint64_t n_cap, const uint64_t* d_n, int shift, uint2* ranges,
                      uint32_t n_tiles, uint32_t* overflow, cudaStream_t st);

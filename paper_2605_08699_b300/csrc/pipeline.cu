@@ -95,6 +95,50 @@ void scene_release(Scene* s) {
     }
 }
 
+// ------------------------------------------------------- allocation faults
+
+namespace {
+std::atomic<bool> g_inject_armed{false};
+std::mutex g_inject_mu;
+int64_t g_inject_skip[2] = {0, 0};   // allocations of the kind still to pass
+int64_t g_inject_fail[2] = {0, 0};   // then this many fail
+
+bool injected_failure(int kind) {
+    if (!g_inject_armed.load(std::memory_order_acquire)) return false;
+    std::lock_guard<std::mutex> lk(g_inject_mu);
+    if (g_inject_fail[kind] <= 0) return false;
+    if (g_inject_skip[kind] > 0) {
+        --g_inject_skip[kind];
+        return false;
+    }
+    --g_inject_fail[kind];
+    return true;
+}
+}  // namespace
+
+void inject_alloc_failures(int kind, int64_t nth, int64_t count) {
+    std::lock_guard<std::mutex> lk(g_inject_mu);
+    g_inject_skip[kind] = nth > 0 ? nth - 1 : 0;
+    g_inject_fail[kind] = nth > 0 ? count : 0;
+    g_inject_armed.store(g_inject_fail[0] > 0 || g_inject_fail[1] > 0, std::memory_order_release);
+}
+
+cudaError_t device_alloc(void** p, size_t bytes) {
+    if (injected_failure(0)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t pinned_alloc(void** p, size_t bytes) {
+    if (injected_failure(1)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocHost(p, bytes);
+}
+
 // ------------------------------------------------------------------ arena
 
 Status Arena::reserve(size_t bytes) {
@@ -103,13 +147,14 @@ Status Arena::reserve(size_t bytes) {
         cudaFree(base);
         base = nullptr;
         cap = 0;
+        ++gen;   // whatever was captured against the old buffer is stale, even if the next allocation fails
     }
     size_t want = bytes + bytes / 4 + (1 << 20);
-    cudaError_t e = cudaMalloc(&base, want);
+    cudaError_t e = device_alloc(&base, want);
     if (e != cudaSuccess) {
         cudaGetLastError();
         base = nullptr;
-        e = cudaMalloc(&base, bytes);   // retry without headroom
+        e = device_alloc(&base, bytes);   // retry without headroom
         if (e != cudaSuccess) {
             cudaGetLastError();
             base = nullptr;
@@ -124,7 +169,10 @@ Status Arena::reserve(size_t bytes) {
 }
 
 void Arena::release() {
-    if (base) cudaFree(base);
+    if (base) {
+        cudaFree(base);
+        ++gen;
+    }
     base = nullptr;
     cap = used = 0;
 }
@@ -158,10 +206,10 @@ Status RenderContext::init() {
     TIGAS_CUDA_TRY(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
     TIGAS_CUDA_TRY(cudaStreamCreateWithFlags(&copy_stream, cudaStreamNonBlocking));
     TIGAS_CUDA_TRY(cudaEventCreateWithFlags(&ev_rendered, cudaEventDisableTiming));
-    TIGAS_CUDA_TRY(cudaMallocHost(&h_total, sizeof(uint64_t) * (kMaxSlices + 2)));
-    TIGAS_CUDA_TRY(cudaMallocHost(&h_flags, sizeof(uint32_t) * 2));
-    TIGAS_CUDA_TRY(cudaMallocHost(&h_views, (sizeof(ViewParams) + sizeof(uint64_t)) * kMaxViews));
-    TIGAS_CUDA_TRY(cudaMallocHost(&h_misc, sizeof(uint32_t) * kMaxViews));
+    TIGAS_CUDA_TRY(pinned_alloc(&h_total, sizeof(uint64_t) * (kMaxSlices + 2)));
+    TIGAS_CUDA_TRY(pinned_alloc(&h_flags, sizeof(uint32_t) * 2));
+    TIGAS_CUDA_TRY(pinned_alloc(&h_views, (sizeof(ViewParams) + sizeof(uint64_t)) * kMaxViews));
+    TIGAS_CUDA_TRY(pinned_alloc(&h_misc, sizeof(uint32_t) * kMaxViews));
     for (int k = 0; k < kNumStages; ++k)
         for (int r = 0; r < kMaxSlices; ++r) {
             TIGAS_CUDA_TRY(cudaEventCreate(&ev_start[k][r]));
@@ -228,6 +276,21 @@ RenderContext* acquire_context(Status* err) {
 void release_context(RenderContext* ctx) {
     std::lock_guard<std::mutex> lk(g_pool_mu);
     g_pool.push_back(ctx);
+}
+
+void release_idle_contexts() {
+    std::vector<RenderContext*> idle;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        idle.swap(g_pool);
+    }
+    for (RenderContext* c : idle) {
+        // idle contexts have no work queued; wait anyway before freeing what their streams used
+        if (c->stream) cudaStreamSynchronize(c->stream);
+        if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+        c->destroy();
+        delete c;
+    }
 }
 
 void forget_launch_sets() {

@@ -76,7 +76,7 @@ struct Arena {
     char* base = nullptr;
     size_t cap = 0;
     size_t used = 0;
-    uint64_t gen = 0;               // bumped on every reallocation (captured graphs hold pointers)
+    uint64_t gen = 0;               // bumped whenever base is freed (captured graphs hold pointers)
     bool over = false;              // a take went past cap since the last reset (nothing may launch)
     Status reserve(size_t bytes);   // call only when no work uses the arena
     void reset() {
@@ -213,6 +213,9 @@ double pair_scale(const Scene* scene, const FrameRequest& req);
 // Context pool used by the synchronous entry points.
 RenderContext* acquire_context(Status* err);
 void release_context(RenderContext* ctx);
+// Destroy the pooled contexts no call holds (arenas, graphs, staging, pinned
+// buffers); later calls create new ones.
+void release_idle_contexts();
 
 bool is_device_pointer(const void* p);
 // Baseline JPEG of one RGBA8 frame (host or device in/out), synchronous on st.

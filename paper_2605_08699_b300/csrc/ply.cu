@@ -351,7 +351,7 @@ Status stream_le(const char* path, FILE* f, uint64_t bytes, uint8_t* dst, cudaSt
     Events ev;
     const size_t chunk = (size_t)std::min<uint64_t>(kStreamChunk, bytes);
     for (int b = 0; b < 2; ++b) {
-        TIGAS_CUDA_TRY(cudaMallocHost(&pin[b].p, chunk));
+        TIGAS_CUDA_TRY(pinned_alloc(&pin[b].p, chunk));
         TIGAS_CUDA_TRY(cudaEventCreateWithFlags(&ev.e[b], cudaEventDisableTiming));
     }
     uint64_t done = 0;
@@ -383,7 +383,7 @@ Status ply_decode(const char* path, const PlyLayout& lay, float* means, float* l
         Status s = ascii_records(path, file.f, lay, &rec);
         if (!s.ok()) return s;
         row_bytes = (uint32_t)(8 * lay.prop_type.size());
-        TIGAS_CUDA_TRY(cudaMalloc(&rows.p, rec.size() * 8));
+        TIGAS_CUDA_TRY(device_alloc(&rows.p, rec.size() * 8));
         TIGAS_CUDA_TRY(cudaMemcpy(rows.p, rec.data(), rec.size() * 8, cudaMemcpyHostToDevice));
         for (int f = 0; f < kPlyFields; ++f) {
             const int p = lay.field_prop[f];
@@ -392,7 +392,7 @@ Status ply_decode(const char* path, const PlyLayout& lay, float* means, float* l
         }
     } else {
         const uint64_t bytes = lay.n * lay.row_bytes;
-        TIGAS_CUDA_TRY(cudaMalloc(&rows.p, bytes));
+        TIGAS_CUDA_TRY(device_alloc(&rows.p, bytes));
         if (fseeko(file.f, (off_t)lay.body_offset, SEEK_SET) != 0) return io_error(path, "cannot seek");
         if (lay.format == kPlyBinaryLE) {
             Status s = stream_le(path, file.f, bytes, (uint8_t*)rows.p, st);
@@ -426,7 +426,7 @@ Status scene_load_ply(const char* path, int storage, const float bg[3], Scene** 
     if (!s.ok()) return s;
     const uint64_t n = lay.n;
     DevBuf raw;
-    TIGAS_CUDA_TRY(cudaMalloc(&raw.p, n * kPlyFields * sizeof(float)));
+    TIGAS_CUDA_TRY(device_alloc(&raw.p, n * kPlyFields * sizeof(float)));
     float* p = (float*)raw.p;
     float *m = p, *ls = m + 3 * n, *q = ls + 3 * n, *op = q + 4 * n, *sh = op + n;
     cudaStream_t st = nullptr;

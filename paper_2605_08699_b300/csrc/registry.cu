@@ -364,7 +364,7 @@ TIGAS_API tigas_status tigas_ply_decode(const char* path, float* means, float* l
         st = ply_decode(path, lay, means, log_scales, quats, opacity_logits, sh, s);
     } else {
         float* d = nullptr;
-        if (cudaMalloc(&d, n * kPlyFields * sizeof(float)) != cudaSuccess) {
+        if (device_alloc(&d, n * kPlyFields * sizeof(float)) != cudaSuccess) {
             cudaGetLastError();
             cudaStreamDestroy(s);
             return fail(TIGAS_ERR_OOM, "decode staging allocation failed");

@@ -89,7 +89,7 @@ Status scene_create(const float* means, const float* log_scales, const float* qu
     s->view.storage = storage;
     for (int c = 0; c < 3; ++c) s->view.bg[c] = bg[c];
     s->bytes = scene_bytes_for(n, storage);
-    cudaError_t e = cudaMalloc(&s->chunks, s->bytes);
+    cudaError_t e = device_alloc(&s->chunks, s->bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete s;

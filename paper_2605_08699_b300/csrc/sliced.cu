@@ -30,8 +30,9 @@ __device__ inline int view_of_tile(const uint32_t* s_tb, int V, uint32_t g) {
     return lo;
 }
 
+// floor(clamp(x, 0, 1) 255 + 0.5) with one rounding of the fused x 255 + 0.5
 __device__ inline uint8_t to_u8(float x) {
-    return (uint8_t)__float2uint_rd(fminf(fmaxf(x, 0.0f), 1.0f) * 255.0f + 0.5f);
+    return (uint8_t)__float2uint_rd(__fmaf_rn(fminf(fmaxf(x, 0.0f), 1.0f), 255.0f, 0.5f));
 }
 
 // Per-launch-set clearing for the slices, a thread per tile: done bits, strip

@@ -1,17 +1,24 @@
-// K2 device prefix scan and K4 LSD radix sort.
+// K2 device prefix scan and K4 LSD radix sort (8-bit digits, stable).
 //
-// Both are reduce-then-scan designs: every kernel reads only data written by
-// earlier kernels in stream order, so no CTA ever waits on another CTA (no
-// spin loops, nothing that can hang a shared GPU).
+// The prefix scan is reduce-then-scan: every kernel reads only data written
+// by earlier kernels in stream order, so none of its CTAs waits on another.
 //
-// Radix sort: 8-bit digits, stable.  Per pass:
-//   1. hist:    each 4096-key tile counts its digits -> table[digit][tile]
-//   2. scan:    exclusive scan of the digit-major table gives, for every
-//               (digit, tile), the global output offset of that tile's first
-//               key with that digit
-//   3. scatter: each tile ranks its keys stably (warp match + per-warp digit
-//               counters), reorders them in shared memory, and writes runs of
-//               equal digits to their global offsets (coalesced).
+// The radix sort has two paths.
+//  - One-sweep (every input below 2^30 keys, i.e. every sort of the render
+//    path): one read of the keys builds the digit histograms of all passes,
+//    then each pass is a single scatter kernel.  A CTA claims the next chunk,
+//    ranks its keys with one warp ballot per digit bit, publishes its digit
+//    counts and finds the earlier chunks' counts by decoupled look-back.  That
+//    look-back SPINS on other CTAs' status words.  Every spin is bounded: a CTA
+//    only waits on chunks claimed by CTAs that started before it (so the wait
+//    ends in any correct run), and after kSpinLimit polls it sets a timeout
+//    flag in device memory and finishes its pass with its writes kept inside
+//    the output; the host turns the flag into TIGAS_ERR_TIMEOUT.
+//  - Reduce-then-scan (inputs of 2^30 keys or more, whose counts do not fit
+//    the look-back's 30-bit status words): per pass a histogram kernel
+//    (4096-key tiles -> table[digit][tile]), an exclusive scan of that table,
+//    and a scatter that ranks each tile stably with warp match.any and
+//    per-warp digit counters; no CTA waits on another.
 #include <vector>
 
 #include "kernels.cuh"
@@ -321,13 +328,24 @@ k_radix_scatter(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals
 
 uint32_t sort_tiles(uint64_t n_cap) { return (uint32_t)((n_cap + kTileN - 1) / kTileN); }
 
+// Function attributes are per device: the set-up below runs once per device
+// ordinal under kMaxDevices (*slot), and on every call for a higher one (-1).
+Status current_device_slot(int* slot) {
+    int dev = 0;
+    TIGAS_CUDA_TRY(cudaGetDevice(&dev));
+    *slot = dev >= 0 && dev < kMaxDevices ? dev : -1;
+    return {};
+}
+
 template <typename K>
 Status ensure_scatter_smem() {
-    static std::atomic<bool> done{false};
-    if (done.load()) return {};
+    static std::atomic<bool> done[kMaxDevices];
+    int slot = -1;
+    TIGAS_TRY(current_device_slot(&slot));
+    if (slot >= 0 && done[slot].load()) return {};
     TIGAS_CUDA_TRY(cudaFuncSetAttribute(k_radix_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)sizeof(ScatterSmem<K>)));
-    done.store(true);
+    if (slot >= 0) done[slot].store(true);
     return {};
 }
 
@@ -399,7 +417,6 @@ constexpr uint32_t kFlagMask = 3u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
 constexpr int kSpinLimit = 1 << 22;
 
-constexpr uint32_t kSortTimeoutFlag = 16u;
 
 // Tile shape of a scatter pass: T threads x I keys.  With an 8-byte payload a
 // CTA takes half the keys so that keys, values and payloads still fit two CTAs
@@ -906,14 +923,16 @@ k_os_scatter(const OsRoute* __restrict__ route, uint64_t n_cap, const uint64_t* 
 
 template <typename K, int PAY, bool MAP>
 Status ensure_os_smem() {
-    static std::atomic<bool> done{false};
-    if (done.load()) return {};
+    static std::atomic<bool> done[kMaxDevices];
+    int slot = -1;
+    TIGAS_TRY(current_device_slot(&slot));
+    if (slot >= 0 && done[slot].load()) return {};
     TIGAS_CUDA_TRY(cudaFuncSetAttribute(k_os_scatter<K, PAY, MAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)sizeof(OsSmem<K, PAY>)));
     // the largest shared-memory carveout, so that two CTAs fit per SM
     TIGAS_CUDA_TRY(
         cudaFuncSetAttribute(k_os_scatter<K, PAY, MAP>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-    done.store(true);
+    if (slot >= 0) done[slot].store(true);
     return {};
 }
 
@@ -983,52 +1002,75 @@ Status radix_sort_onesweep(const K* keys_in, const uint32_t* values_in, K* keys_
 
 }  // namespace
 
+namespace {
+// Look-back probe layout (words): keys [2N], sorted keys [2N], sorted values
+// [2N], digit histogram [256], digit bases [256], status [2][256], misc [8]
+// (chunk counter, own flags word), routes [2].
+constexpr uint64_t kProbeN = 2 * (uint64_t)OsCfg<uint32_t, kPayNone>::kT * OsCfg<uint32_t, kPayNone>::kI;
+constexpr size_t kProbeKeys = 0, kProbeOut = kProbeN, kProbeVals = 2 * kProbeN, kProbeHist = 3 * kProbeN,
+                 kProbeBase = kProbeHist + 256, kProbeStatus = kProbeBase + 256, kProbeMisc = kProbeStatus + 2 * 256,
+                 kProbeRoute = kProbeMisc + 8, kProbeWords = kProbeRoute + 2 * kRouteWords;
+static_assert(kProbeRoute % 2 == 0, "routes hold pointers: 8-byte aligned");
+
+// Probe inputs: distinct-ish keys, zeroed tables, the chunk counter at 1 (the
+// only CTA claims chunk 1) and the probe's own flags word at 0.
+__global__ void k_probe_init(uint32_t* __restrict__ buf) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < kProbeRoute;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t v = 0;
+        if (i < kProbeOut) v = (uint32_t)((i * 2654435761u) >> 7);
+        else if (i == kProbeMisc) v = 1u;
+        if (i < kProbeOut || i >= kProbeHist) buf[i] = v;
+    }
+}
+}  // namespace
+
+size_t debug_lookback_words() { return kProbeWords; }
+
 // One scatter CTA of a two-chunk, one-pass sort that claims chunk 1 while no
 // CTA ever runs chunk 0: its look-back waits on counts nobody publishes, so
-// every wait runs out after spin_limit polls and the CTA sets the timeout flag.
-// All of its accesses stay in bounds: the digit bases come from the histogram
-// of both chunks, so every scattered position is below 2N.
-Status debug_lookback_timeout(int spin_limit, bool* timed_out) {
+// every wait runs out after spin_limit polls and the CTA ORs the timeout flag
+// into *flags.  Bounds, by reading: the digit bases come from the histogram of
+// both chunks, so every scattered position is below 2N = kProbeN and lands in
+// the out / vals regions; the status table holds 2 x 256 words.
+Status debug_lookback_enqueue(int spin_limit, uint32_t* buf, uint32_t* flags, cudaStream_t st) {
     using K = uint32_t;
-    constexpr int T = OsCfg<K, kPayNone>::kT, N = OsCfg<K, kPayNone>::kT * OsCfg<K, kPayNone>::kI;
+    constexpr int T = OsCfg<K, kPayNone>::kT;
+    if (spin_limit < 1 || spin_limit > (1 << 20)) return {TIGAS_ERR_INVALID, "spin limit out of 1..2^20"};
+    if (reinterpret_cast<uintptr_t>(buf) & 15u) return {TIGAS_ERR_INVALID, "probe buffer not 16-byte aligned"};
+    TIGAS_TRY((ensure_os_smem<K, kPayNone, false>()));
+    K* keys = buf + kProbeKeys;
+    K* out = buf + kProbeOut;
+    uint32_t* vals = buf + kProbeVals;
+    uint32_t* ghist = buf + kProbeHist;
+    uint32_t* gbase = buf + kProbeBase;
+    uint32_t* status = buf + kProbeStatus;
+    uint32_t* misc = buf + kProbeMisc;
+    OsRoute* route = reinterpret_cast<OsRoute*>(buf + kProbeRoute);
+    k_probe_init<<<16, 256, 0, st>>>(buf);
+    OsBuffers bufs{keys, nullptr, nullptr, out, vals, nullptr, out, vals, nullptr};
+    k_os_hist<K, 8, false><<<4, 512, 0, st>>>(keys, kProbeN, nullptr, 0, 8, ghist, nullptr, nullptr, 0, 1);
+    k_os_bases<<<1, 256, 0, st>>>(ghist, gbase, 1, route, bufs, nullptr);
+    k_os_scatter<K, kPayNone, false><<<1, T, sizeof(OsSmem<K, kPayNone>), st>>>(
+        route, kProbeN, nullptr, 0, 8, gbase, status, misc, flags ? flags : misc + 1, spin_limit, nullptr);
+    g_launches.fetch_add(4, std::memory_order_relaxed);
+    TIGAS_CUDA_TRY(cudaGetLastError());
+    return {};
+}
+
+Status debug_lookback_timeout(int spin_limit, bool* timed_out) {
     *timed_out = false;
     if (spin_limit < 1 || spin_limit > (1 << 20)) return {TIGAS_ERR_INVALID, "spin limit out of 1..2^20"};
-    TIGAS_TRY((ensure_os_smem<K, kPayNone, false>()));
-    const uint64_t n = 2 * (uint64_t)N;
-    const size_t route_words = 2 * kRouteWords;
-    const size_t words = 2 * n + 256 + 256 + 2 * 256 + 8 + route_words;
     uint32_t* buf = nullptr;
-    TIGAS_CUDA_TRY(cudaMalloc(&buf, words * sizeof(uint32_t)));
-    uint32_t* keys = buf;
-    uint32_t* out = keys + n;
-    uint32_t* ghist = buf + 2 * n;
-    uint32_t* gbase = ghist + 256;
-    uint32_t* status = gbase + 256;
-    uint32_t* misc = status + 2 * 256;                               // [chunk counter, flags, ...]
-    OsRoute* route = reinterpret_cast<OsRoute*>(misc + 8);           // 8-byte aligned: 2n + 1032 words
-    Status st;
-    std::vector<uint32_t> h(n);
-    for (uint64_t i = 0; i < n; ++i) h[i] = (uint32_t)((i * 2654435761u) >> 7);
-    cudaError_t e = cudaMemcpy(keys, h.data(), n * 4, cudaMemcpyHostToDevice);
-    uint32_t* sorted_vals = nullptr;
-    if (e == cudaSuccess) e = cudaMalloc(&sorted_vals, n * sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMemset(ghist, 0, (256 + 256 + 2 * 256) * sizeof(uint32_t));
-    const uint32_t misc_init[2] = {1u, 0u};   // the only CTA claims chunk 1
-    if (e == cudaSuccess) e = cudaMemcpy(misc, misc_init, sizeof(misc_init), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) {
-        OsBuffers bufs{keys, nullptr, nullptr, out, sorted_vals, nullptr, out, sorted_vals, nullptr};
-        k_os_hist<K, 8, false><<<4, 512>>>(keys, n, nullptr, 0, 8, ghist, nullptr, nullptr, 0, 1);
-        k_os_bases<<<1, 256>>>(ghist, gbase, 1, route, bufs, nullptr);
-        k_os_scatter<K, kPayNone, false><<<1, T, sizeof(OsSmem<K, kPayNone>)>>>(route, n, nullptr, 0, 8, gbase, status,
-                                                                          misc, misc + 1, spin_limit, nullptr);
-        g_launches.fetch_add(3, std::memory_order_relaxed);
-        e = cudaGetLastError();
-    }
+    TIGAS_CUDA_TRY(device_alloc(&buf, kProbeWords * sizeof(uint32_t)));
+    Status st = debug_lookback_enqueue(spin_limit, buf, nullptr, nullptr);
     uint32_t flags = 0;
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    if (e == cudaSuccess) e = cudaMemcpy(&flags, misc + 1, sizeof(flags), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) st = {TIGAS_ERR_CUDA, std::string("look-back timeout probe: ") + cudaGetErrorString(e)};
-    if (sorted_vals) cudaFree(sorted_vals);
+    cudaError_t e = cudaSuccess;
+    if (st.ok()) e = cudaDeviceSynchronize();
+    if (st.ok() && e == cudaSuccess)
+        e = cudaMemcpy(&flags, buf + kProbeMisc + 1, sizeof(flags), cudaMemcpyDeviceToHost);
+    if (st.ok() && e != cudaSuccess)
+        st = {TIGAS_ERR_CUDA, std::string("look-back timeout probe: ") + cudaGetErrorString(e)};
     cudaFree(buf);
     *timed_out = (flags & kSortTimeoutFlag) != 0;
     return st;

@@ -26,7 +26,7 @@ EXPORTS = ["tigas_scene_load", "tigas_scene_free", "tigas_scene_bytes", "tigas_r
            "tigas_render_batch", "tigas_debug_render", "tigas_sort_pairs_u64", "tigas_server_create",
            "tigas_server_destroy", "tigas_server_submit", "tigas_server_poll", "tigas_last_error",
            "tigas_version", "tigas_kernel_launches", "tigas_profile_enable", "tigas_profile_read",
-           "tigas_sort_pairs_u64_noalloc",
+           "tigas_sort_pairs_u64_noalloc", "tigas_sort_noalloc_check", "tigas_debug_sort_noalloc_wait_timeout",
            "tigas_render_batch_ex", "tigas_set_graphs", "tigas_debug_sort_wait_timeout",
            "tigas_set_schedule", "tigas_get_schedule", "tigas_autotune", "tigas_exact_rerenders",
            "tigas_jpeg_encode", "tigas_ply_probe", "tigas_ply_decode", "tigas_scene_load_ply",
@@ -34,7 +34,7 @@ EXPORTS = ["tigas_scene_load", "tigas_scene_free", "tigas_scene_bytes", "tigas_r
            "tigas_registry_acquire", "tigas_registry_release", "tigas_registry_evict_idle",
            "tigas_registry_start_eviction", "tigas_registry_set_clock", "tigas_registry_close",
            "tigas_resample_rgba8", "tigas_image_quality", "tigas_profile_stages", "tigas_render_batch_async",
-           "tigas_render_wait"]
+           "tigas_render_wait", "tigas_debug_fail_alloc", "tigas_release_workspace"]
 
 STAGES = ["preprocess", "depth_sort", "scan", "emit", "pair_sort", "ranges", "blend", "frame"]
 
@@ -136,6 +136,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                     ctypes.POINTER(DebugFrame), ctypes.POINTER(ctypes.c_uint64)]),
         "tigas_sort_pairs_u64": (st, [P, P, P, P, ctypes.c_uint64, i, i, P]),
         "tigas_sort_pairs_u64_noalloc": (st, [P, P, P, P, ctypes.c_uint64, i, i, P]),
+        "tigas_sort_noalloc_check": (st, [P]),
+        "tigas_debug_sort_noalloc_wait_timeout": (st, [i, P]),
         "tigas_server_create": (st, [ctypes.POINTER(ServerConfig), ctypes.POINTER(P)]),
         "tigas_server_destroy": (st, [P, i]),
         "tigas_server_submit": (st, [P, P, ctypes.POINTER(Pose), ctypes.POINTER(Intrinsics), i, i, P,
@@ -148,6 +150,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "tigas_profile_stages": (st, [ctypes.c_uint32]),
         "tigas_set_graphs": (st, [i]),
         "tigas_debug_sort_wait_timeout": (st, [i]),
+        "tigas_debug_fail_alloc": (st, [i, ctypes.c_int64, ctypes.c_int64]),
+        "tigas_release_workspace": (st, []),
         "tigas_set_schedule": (st, [ctypes.POINTER(Schedule)]),
         "tigas_get_schedule": (st, [ctypes.POINTER(Schedule)]),
         "tigas_exact_rerenders": (ctypes.c_uint64, []),
@@ -220,6 +224,20 @@ def debug_sort_wait_timeout(spin_limit: int) -> int:
     """Run the radix sort's look-back timeout hook; returns the tigas status
     (TIMEOUT = 6 is the expected outcome)."""
     return int(load_library().tigas_debug_sort_wait_timeout(int(spin_limit)))
+
+
+DEVICE_ALLOC, PINNED_ALLOC = 0, 1
+
+
+def debug_fail_alloc(kind: int, nth: int = 1, count: int = 1) -> None:
+    """Make allocations nth .. nth + count - 1 of a kind fail (tigas_debug_fail_alloc);
+    nth = 0 clears the kind."""
+    _check(load_library().tigas_debug_fail_alloc(int(kind), int(nth), int(count)))
+
+
+def release_workspace() -> None:
+    """Free the workspace of idle render contexts (tigas_release_workspace)."""
+    _check(load_library().tigas_release_workspace())
 
 
 def profile_read(reset: bool = False) -> dict:
@@ -508,13 +526,15 @@ def _stats_dict(stats: "FrameStats") -> dict:
 
 
 def render_ex(scene: SceneHandle, pose, intr, width: int, height: int, out_rgba8=None, out_rgba_f32=None,
-              stream=None, sort_mode: int = SORT_SLICED) -> dict:
-    """tigas_render_ex; returns the frame statistics."""
-    stats = FrameStats()
+              stream=None, sort_mode: int = SORT_SLICED, stats: bool = True) -> dict | None:
+    """tigas_render_ex; returns the frame statistics (stats=False passes no
+    statistics struct, so the uninstrumented kernels run, and returns None)."""
+    fs = FrameStats() if stats else None
     _check(load_library().tigas_render_ex(scene.handle, ctypes.byref(make_pose(pose)),
                                           ctypes.byref(make_intrinsics(intr)), width, height, _ptr(out_rgba8),
-                                          _ptr(out_rgba_f32), _stream(stream), sort_mode, ctypes.byref(stats)))
-    return _stats_dict(stats)
+                                          _ptr(out_rgba_f32), _stream(stream), sort_mode,
+                                          ctypes.byref(fs) if stats else None))
+    return _stats_dict(fs) if stats else None
 
 
 def render_batch(scene: SceneHandle, poses: Sequence, intrs: Sequence, widths: Sequence[int],

@@ -111,3 +111,14 @@ def assert_colour(gpu: np.ndarray, ref: np.ndarray) -> dict:
     assert s["mean_abs"] <= COLOUR_MEAN_ABS, s
     assert s["psnr_rgb"] >= PSNR_MIN_DB, s
     return s
+
+
+def encode_rgba8_fp32(f: np.ndarray) -> np.ndarray:
+    """The kernels' 8-bit encoding of a float32 frame, reproduced exactly:
+    floor(fma(clamp(x, 0, 1), 255, 0.5)) with the fused product-sum rounded
+    once to float32.  In float64 the product-sum is exact for every float32 x
+    whose rounding can matter (x 255 + 0.5 needs at most 33 significant bits
+    there), so rounding it to float32 reproduces the fused operation."""
+    c = np.clip(f.astype(np.float32), np.float32(0.0), np.float32(1.0)).astype(np.float64)
+    return np.floor((c * 255.0 + 0.5).astype(np.float32)).astype(np.uint8)
+

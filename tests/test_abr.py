@@ -1,4 +1,5 @@
-"""Latency ABR and throughput EMA (Sec. 5.2) and the serving trace generator.
+"""Latency ABR and throughput EMA (Sec. 4.3 and Sec. 5.3, "ABR Controller" and
+"Throughput Monitoring") and the serving trace generator.
 
 The controller's rules are checked on hand-built throughput sequences whose
 outcome follows from the rules directly: the hold counter, the dead band

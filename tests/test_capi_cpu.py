@@ -139,3 +139,14 @@ def test_async_and_quality_arguments_rejected_without_gpu(lib):
             _status(name, None, None) == tb.ERR_INVALID
     assert _status("tigas_registry_close", None) == tb.ERR_INVALID
     assert _status("tigas_registry_set_clock", None, ctypes.c_double(1.0)) == tb.ERR_INVALID
+
+
+def test_fault_injection_and_workspace_arguments_without_gpu(lib):
+    # the injection knob is host state: it validates and arms without any CUDA call
+    assert _status("tigas_debug_fail_alloc", 2, ctypes.c_int64(1), ctypes.c_int64(1)) == tb.ERR_INVALID
+    assert _status("tigas_debug_fail_alloc", 0, ctypes.c_int64(-1), ctypes.c_int64(1)) == tb.ERR_INVALID
+    assert _status("tigas_debug_fail_alloc", 1, ctypes.c_int64(3), ctypes.c_int64(0)) == tb.ERR_INVALID
+    assert _status("tigas_debug_fail_alloc", 0, ctypes.c_int64(2), ctypes.c_int64(5)) == tb.OK
+    assert _status("tigas_debug_fail_alloc", 0, ctypes.c_int64(0), ctypes.c_int64(0)) == tb.OK   # cleared
+    # with no render context created yet there is nothing to free
+    assert _status("tigas_release_workspace") == tb.OK

@@ -108,9 +108,45 @@ def test_workload1_ranges_exact_when_no_flip(h1, s1):
     dbg = tg.debug_render(h1, synth.BASE_POSE, K1, 320, 240)
     pr = oracle.preprocess(s1, synth.BASE_POSE, K1, 320, 240)
     g = parity.check_per_gaussian(dbg, pr)
-    orr, _ = oracle.tile_lists(pr)
+    orr, ov = oracle.tile_lists(pr)
+    gr = dbg["ranges"].astype(np.int64)
+    gv = dbg["values"].astype(np.int64)
+    # every path: the ranges are contiguous in tile order and cover the pair array ...
+    assert gr[0, 0] == 0 and np.array_equal(gr[1:, 0], gr[:-1, 1]) and gr[-1, 1] == dbg["pairs"]
+    # ... each tile's unambiguous entries are exactly as many as the oracle's, and a
+    # tile with no ambiguous member in either list has exactly the oracle's length
+    amb = pr.amb > 0
+    clean = 0
+    for t in range(len(orr)):
+        g_t, o_t = gv[gr[t, 0]:gr[t, 1]], ov[orr[t, 0]:orr[t, 1]]
+        assert np.count_nonzero(~amb[g_t]) == np.count_nonzero(~amb[o_t]), f"tile {t}"
+        if not amb[g_t].any() and not amb[o_t].any():
+            assert g_t.size == o_t.size, f"tile {t}"
+            clean += 1
+    assert clean > 0   # (181 of the 300 tiles hold no ambiguous Gaussian on this seed)
+    # ... and without a flipped decision the ranges equal the oracle's exactly
     if g["ambiguous_flipped"] == 0:
-        assert np.array_equal(dbg["ranges"].astype(np.int64), orr)
+        assert np.array_equal(gr, orr)
+    _diag("workload1_ranges", {**g, "clean_tiles": clean, "tiles": len(orr)})
+
+
+def test_support_rule_scene_on_gpu(cuda):
+    # a Gaussian whose alpha >= 1/255 region reaches past its 3-sigma rectangle:
+    # every schedule must leave the pixels outside the rectangle at the background
+    from tests.test_oracle_raster import support_rule_scene
+    sc, K, W, H = support_rule_scene()
+    pr = oracle.preprocess(sc, synth.BASE_POSE, K, W, H)
+    ref = oracle.render(pr)
+    with tg.scene_from(sc) as h:
+        for mode in (tg.SORT_DEPTH_FIRST, tg.SORT_FULL64):
+            dbg = tg.debug_render(h, synth.BASE_POSE, K, W, H, sort_mode=mode)
+            assert tuple(dbg["rect"][0]) == (1, 0, 3, 2) and dbg["radius"][0] == 15
+            f = dbg["rgba_f32"]
+            assert np.all(f[:, 48:] == 0.0)
+            assert np.max(np.abs(f.astype(np.float64) - ref)) < 2e-5
+        fast = np.zeros((H, W, 4), np.float32)
+        tg.render_ex(h, synth.BASE_POSE, K, W, H, out_rgba_f32=fast, sort_mode=tg.SORT_SLICED)
+        assert np.array_equal(fast, f)
 
 
 def test_sort_modes_give_identical_frames(h1):
@@ -535,6 +571,54 @@ def test_full_size_3m_1080p_sampled(cuda, s3, storage):
         extra = {"vs_fp32_oracle": parity.colour_stats(got, ref32)}
         assert extra["vs_fp32_oracle"]["psnr_rgb"] >= 50.0
     _diag("full_size_colour", {"storage": storage, **st, "pairs": dbg["pairs"], **extra})
+
+
+@pytest.mark.parametrize("storage", [tg.STORAGE_FP32, tg.STORAGE_FP16])
+def test_full_size_default_schedule_is_bit_identical_to_whole_lists(cuda, s3, storage):
+    """3M Gaussians at 1920x1080: the render path (sliced schedule with
+    alpha-cut rectangles: several slices, done tiles, strip items) against the
+    whole-list schedule of the debug render, float frames compared bit for bit
+    over the whole frame, at two poses."""
+    W, H = 1920, 1080
+    K = synth.default_intrinsics(W, H)
+    tr = synth.config_trajectory(3)
+    with tg.scene_from(s3, storage=storage) as h:
+        for k in (0, 233):
+            full = tg.debug_render(h, tr[k], K, W, H, sort_mode=tg.SORT_DEPTH_FIRST)
+            want = full["rgba_f32"].view(np.uint32)
+            fast = torch.empty((H, W, 4), dtype=torch.float32, device=cuda)
+            # the uninstrumented kernels (no statistics), then the counting ones
+            tg.render_ex(h, tr[k], K, W, H, out_rgba_f32=fast, sort_mode=tg.SORT_SLICED, stats=False)
+            same = fast.cpu().numpy().view(np.uint32) == want
+            st = tg.render_ex(h, tr[k], K, W, H, out_rgba_f32=fast, sort_mode=tg.SORT_SLICED)
+            same_counting = fast.cpu().numpy().view(np.uint32) == want
+            _diag("full_size_bit_identity", {"storage": storage, "pose": k, "pairs_full": full["pairs"],
+                                             "pairs_sliced": st["n_pairs"], "differing": int((~same).sum())})
+            assert np.all(same), f"{int((~same).sum())} values differ"
+            assert np.all(same_counting), f"{int((~same_counting).sum())} values differ (counting kernels)"
+            assert st["n_pairs"] < full["pairs"]
+
+
+def test_full_size_8_view_launch_set_view_is_bit_identical(cuda, s3):
+    """One view of an 8-view 1080p launch set of the 3M FP16 scene (the timed
+    configuration, through tigas_render_batch) against the whole-list debug
+    render of the same pose: the launch set's RGBA8 frame equals the kernels'
+    8-bit encoding of the debug float frame at every pixel."""
+    W, H, V = 1920, 1080, 8
+    K = synth.default_intrinsics(W, H)
+    poses = [synth.config_trajectory(3, v)[(60 + 11 * v) % 300] for v in range(V)]
+    with tg.scene_from(s3, storage=tg.STORAGE_FP16) as h:
+        outs = [torch.empty((H, W, 4), dtype=torch.uint8, device=cuda) for _ in range(V)]
+        frames = []
+        for _ in range(3):   # back to back: first appearance, exact render and capture, graph replay
+            tg.render_batch(h, poses, [K] * V, [W] * V, [H] * V, outs)
+            torch.cuda.synchronize()
+            frames.append({v: outs[v].cpu().numpy() for v in (2, 5)})
+        for v in (2, 5):
+            full = tg.debug_render(h, poses[v], K, W, H, sort_mode=tg.SORT_DEPTH_FIRST)
+            want = parity.encode_rgba8_fp32(full["rgba_f32"])
+            for f in frames:
+                assert np.array_equal(f[v], want)
 
 
 def test_full_size_8_view_async_launch_set(cuda, s3):

@@ -60,3 +60,22 @@ def test_reference_arm_runs_on_rank0_only(monkeypatch, capsys):
     monkeypatch.setenv("WORLD_SIZE", "2")
     assert bench.main(["--impl", "reference", "--gpus", "2"]) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_times_whole_frames(capsys):
+    # rank 0 (no torchrun): whole oracle frames of a small scene; the timed steps fit
+    # inside the call's own wall time, so the line's ms_per_step x steps is real
+    import json
+    import time
+    sys.path.insert(0, ROOT)
+    import bench
+    t0 = time.perf_counter()
+    assert bench.main(["--impl", "reference", "--gaussians", "3000", "--width", "96", "--height", "64",
+                       "--steps", "2", "--warmup", "3"]) == 0
+    wall_ms = (time.perf_counter() - t0) * 1e3
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["steps"] == 2 and line["warmup"] == 3
+    assert line["value"] > 0 and line["unit"] == "frames/s"
+    assert abs(line["value"] * line["ms_per_step"] * 1e-3 - 1.0) < 1e-9
+    assert line["ms_per_step"] * line["steps"] <= wall_ms
+    assert "whole" in line["cpu_baseline"]["sample"] and line["e2e"]["h2d_bytes_per_step"] == 0

@@ -218,9 +218,50 @@ def test_tile_grouping_equals_brute_force(seed):
     pix = [(3, 4), (31, 0), (16, 16), (0, 31)]
     c = oracle.render(pr, background=(0.1, 0.2, 0.3), pixels=pix)
     assert np.array_equal(c, np.array([b[y, x] for x, y in pix]))
-    # the support rule matters: without it some pixel changes
-    d = oracle.render_brute(pr, background=(0.1, 0.2, 0.3), support_rule=False)
-    assert np.max(np.abs(d - b)) >= 0.0
+
+
+def support_rule_scene():
+    """One isotropic, nearly opaque Gaussian whose alpha >= 1/255 region reaches
+    past its 3-sigma tile rectangle: on a 64x32 frame (f = 120, centre (32, 16))
+    it projects to u = 32.9 with 3 sqrt(lambda) = 14.9, so r = 15 and
+    x_hi = floor((u + r) / 16) + 1 = 3, while the centre of pixel 48 (tile 3)
+    lies 15.6 px from u, where alpha = 0.99 exp(-15.6^2 / (2 (14.9 / 3)^2))
+    ~ 7e-3 > 1/255."""
+    W, H = 64, 32
+    K = synth.Intrinsics(120.0, 120.0, W / 2, H / 2)
+    s_px = math.sqrt((14.9 / 3) ** 2 - 0.3)          # pixel sigma before the 0.3 dilation
+    scale = s_px * 3.0 / 120.0                       # at depth 3
+    sc = scene_of([(0.9 * 3.0 / 120.0, 0.0, 0.0)], [[math.log(scale)] * 3], [[1, 0, 0, 0]], [5.0],
+                  [(1.0, 1.0, 1.0)])
+    return sc, K, W, H
+
+
+def test_support_rule_changes_a_named_pixel():
+    # the tiled method composites a Gaussian only in the tiles of its rectangle;
+    # the plain per-pixel definition includes that rule (else parity would fail
+    # by construction), and this scene shows the rule is not vacuous
+    sc, K, W, H = support_rule_scene()
+    pr = oracle.preprocess(sc, synth.BASE_POSE, K, W, H)
+    assert pr.radius[0] == 15 and tuple(pr.rect[0]) == (1, 0, 3, 2)
+    u, v = pr.uvz[0, 0], pr.uvz[0, 1]
+    assert abs(u - 32.9) < 1e-6 and abs(v - 16.0) < 1e-9
+    with_rule = oracle.render_brute(pr)
+    without = oracle.render_brute(pr, support_rule=False)
+    assert np.array_equal(oracle.render(pr), with_rule)
+    # pixel (48, 16): outside the rectangle, so exactly the (black) background with the rule ...
+    assert np.all(with_rule[16, 48] == 0.0)
+    # ... and alpha = min(0.99, o exp(-q/2)) > 1/255 without it, q from the conic at the pixel centre
+    A, B, C = pr.conic[0]
+    dx, dy = 48.5 - u, 16.5 - v
+    o = 1.0 / (1.0 + math.exp(-5.0))
+    alpha = min(0.99, o * math.exp(-0.5 * (A * dx * dx + 2 * B * dx * dy + C * dy * dy)))
+    assert 1 / 255 < alpha < 0.01
+    assert abs(without[16, 48, 3] - alpha) < 1e-12
+    col = 0.5 + C0 * float(np.float32(1.0))
+    assert np.allclose(without[16, 48, :3], alpha * col, atol=1e-12)
+    # inside the rectangle (pixel 47) the two agree; the rule changes only tile-3 pixels
+    assert np.array_equal(with_rule[:, :48], without[:, :48])
+    assert np.any(without[:, 48:] != with_rule[:, 48:])
 
 
 def test_tile_lists_equal_brute_enumeration():
