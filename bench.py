@@ -537,6 +537,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     res = {"schedule": schedule, "rerenders": rerenders, "concurrent": concurrent, "value": value, "elapsed_ms": elapsed_ms, "frames": frames, "per_step": per_step, "stage_ms": stage_ms,
            "timed_stage_ms": timed_stage_ms,
            "clocks": clocks, "launches": launches, "e2e": e2e, "plain_fp32": plain, "serving": serving, "trace": trace,
+           "configs": configs,
            "batching": batching, "sh0": sh0, "jpeg": jpeg, "models": models, "quality": quality,
            "step_ms_host": step_ms_host, "scene": scene}
     h16.free()
@@ -968,6 +969,7 @@ def main(argv=None) -> int:
                                                   "pixels all stopped are dropped", autotuned=not (args.no_autotune or args.schedule),
                              exact_rerenders_timed=r["rerenders"]),
             "served_fp16": r["serving"], "plain_fp32": r["plain_fp32"], "serving_trace": r["trace"],
+            "configs": r["configs"],
             "batching_32_mixed": r["batching"], "in_flight": r["concurrent"], "sh_degree_0": r["sh0"],
             "jpeg_encode": r["jpeg"], "model_load": r["models"], "quality_eval": r["quality"],
             "roofline": roof, "stages": stages,

@@ -1,10 +1,11 @@
 // K6 per-tile blend, the 3DGS front-to-back compositing the backend relies
 // on (Sec. 4.1): one warp per 16x16 tile, 8 pixels per thread (column
 // lane % 16, rows lane / 16 + 2k), four independent warps per CTA and no
-// CTA-wide barrier; a tile with a long list in a slice is split into four
-// 16x4 strips (2 pixels per thread) that separate warps composite at once.  The tile's depth-ordered list is consumed in batches of
-// 32 entries that the warp gathers into shared memory with cp.async,
-// double-buffered (batch b+1 in flight while b is composited).
+// CTA-wide barrier; a tile with a long list in a slice is split into
+// kStrips strips of 16 / kStrips rows (two 16x8 halves, 4 pixels per thread)
+// that separate warps composite at once.  The tile's depth-ordered list is
+// consumed in batches of 32 entries that the warp gathers into shared memory
+// with cp.async, double-buffered (batch b+1 in flight while b is composited).
 //
 // For each staged entry the warp first tests the bounding box of its
 // alpha >= 1/255 region against the bounding box of the tile's pixels that are
@@ -134,11 +135,12 @@ __device__ __forceinline__ bool blend_rows(WarpStage& sm, int lane, const uint2*
 
     float T[NP], cr[NP], cg[NP], cb[NP];
     uint32_t live = 0;   // bit k: pixel k still compositing
-    // the tile's pixels carry (C, T) from an earlier slice (a slice blends all
-    // four strips of a long tile, so a tile's strips are blended together);
-    // otherwise they start from (0, 1).  The state is read together with the
-    // strip word rather than after it (one dependent load less per visit; on a
-    // first visit the words read are in bounds and unused)
+    // the tile's pixels carry (C, T) from an earlier slice (kStripSeen: set only
+    // between slices, so the strips of a long tile, which run in the same slice,
+    // all see the same value); otherwise they start from (0, 1).  The state is
+    // read together with the strip word rather than after it (one dependent
+    // load less per visit; on a first visit the words read are in bounds and
+    // unused)
     const uint32_t sw = SLICED ? sl.strips[g] : 0u;
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
@@ -302,7 +304,7 @@ __device__ __forceinline__ bool blend_rows(WarpStage& sm, int lane, const uint2*
         }
     }
     // the tile's pixels now carry state (and have their outputs written)
-    if (SLICED && !(sw & kStripSeen) && lane == 0) atomicOr(&sl.strips[g], kStripSeen);
+    if (SLICED && !(sw & kStripSeen) && lane == 0) atomicOr(&sl.strips[g], kStripSeenNow);
     return all;
 }
 
@@ -336,7 +338,7 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ values, S
         if (item >= n_items) break;
         const uint32_t raw = SLICED ? sl.active[item < n_long ? item : sl.active_cap - 1 - (item - n_long)] : item;
         const uint32_t g = raw & kTileMask;
-        const uint32_t strip = raw >> kStripShift;   // 0: whole tile, s + 1: rows 4s..4s+3
+        const uint32_t strip = raw >> kStripShift;   // 0: whole tile, s + 1: strip s
         int v = 0;
         {
             int lo = 0, hi = V;   // last view with tile_base <= g
@@ -356,12 +358,12 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ values, S
             if (all && lane == 0) atomicOr(&sl.done[g >> 5], 1u << (g & 31));
         } else {
             const uint32_t bit = 1u << (strip - 1);
-            const bool all = blend_rows<SLICED, COUNT, 2>(sm, lane, ranges, values, sp, vp, g, local,
-                                                          4 * (int)(strip - 1), sbase, n_entries, bg_r, bg_g, bg_b,
-                                                          sl, cnt);
+            const bool all = blend_rows<SLICED, COUNT, (int)kStripRows / 2>(sm, lane, ranges, values, sp, vp, g, local,
+                                                                           (int)kStripRows * (int)(strip - 1), sbase,
+                                                                           n_entries, bg_r, bg_g, bg_b, sl, cnt);
             if (all && lane == 0) {
                 const uint32_t old = atomicOr(&sl.strips[g], bit);
-                if (((old | bit) & 0xFu) == 0xFu) atomicOr(&sl.done[g >> 5], 1u << (g & 31));
+                if (((old | bit) & kStripsAll) == kStripsAll) atomicOr(&sl.done[g >> 5], 1u << (g & 31));
             }
         }
     }

@@ -729,7 +729,7 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
         const uint32_t* hi_bases =
             cap < (1ull << 30) && L.tile_bits > 8 && L.tile_bits <= 16 ? radix_digit_bases(stmp, 1) : nullptr;
         TIGAS_TRY(launch_ranges_active(keys_c, cap, stat ? d_P : nullptr, ranges, total_tiles, done, active, d_misc,
-                                       d_flags, hi_bases, st));
+                                       d_flags, hi_bases, strips, st));
         TIGAS_TRY(mark(kStRanges, false));
         TIGAS_TRY(mark(kStBlend, true));
         TIGAS_TRY(launch_blend_slice(ranges, vals_c, sp, d_views, V, (uint32_t)E, scene->view.bg,

@@ -36,8 +36,8 @@ __device__ inline uint8_t to_u8(float x) {
 }
 
 // Per-launch-set clearing for the slices, a thread per tile: done bits, strip
-// words (bits 0-3: strip s finished; kStripSeen: the tile carries (C, T) from
-// a blended slice), and the slice totals.  No pixel is touched: a tile's first
+// words (bits 0-3: strip s finished; kStripSeen / kStripSeenNow: the tile
+// carries (C, T) from a blended slice), and the slice totals.  No pixel is touched: a tile's first
 // blend starts from (C, T) = (0, 1), and k_fill_unseen writes the background
 // of tiles no slice blended.
 __global__ void __launch_bounds__(256)
@@ -60,7 +60,7 @@ k_fill_unseen(const ViewParams* __restrict__ views_g, int V, uint32_t total_tile
     __syncthreads();
     const uint32_t g = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     if (g >= total_tiles) return;
-    if (strips[g] & kStripSeen) return;   // warp-uniform
+    if (strips[g] & (kStripSeen | kStripSeenNow)) return;   // warp-uniform
     const int lane = threadIdx.x & 31;
     const int v = view_of_tile(s_tb, V, g);
     const ViewParams& vp = views_g[v];
@@ -312,13 +312,18 @@ __global__ void __launch_bounds__(256)
 k_ranges_active(const uint32_t* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, uint2* __restrict__ ranges,
                 uint32_t n_tiles, const uint32_t* __restrict__ done, uint32_t* __restrict__ active,
                 uint32_t* __restrict__ n_active, uint32_t* __restrict__ overflow,
-                const uint32_t* __restrict__ hi_bases) {
+                const uint32_t* __restrict__ hi_bases, uint32_t* __restrict__ strips) {
     __shared__ uint32_t s_sample[kRangeSample];
     __shared__ uint32_t s_lo[256];
     __shared__ uint64_t s_run[2];
     uint64_t n = d_n ? *d_n : n_cap;
     if (n > n_cap) n = n_cap;
     const uint32_t t0 = blockIdx.x * 256u, t = t0 + threadIdx.x;
+    if (t < n_tiles) {
+        // the previous blend is over: what it marked as seen now is seen before this slice
+        const uint32_t w = strips[t];
+        if (w & kStripSeenNow) strips[t] = (w & ~kStripSeenNow) | kStripSeen;
+    }
     if (t == 0 && n > 0 && keys[n - 1] >= n_tiles) atomicOr(overflow, 2u);
     if (threadIdx.x < 2) {
         uint64_t x;
@@ -362,12 +367,12 @@ k_ranges_active(const uint32_t* __restrict__ keys, uint64_t n_cap, const uint64_
     const uint32_t ml = __ballot_sync(kFull, act && !heavy);
     if (mh) {
         uint32_t base = 0;
-        if (lane == __ffs(mh) - 1) base = atomicAdd(&n_active[0], 4u * (uint32_t)__popc(mh));
+        if (lane == __ffs(mh) - 1) base = atomicAdd(&n_active[0], kStrips * (uint32_t)__popc(mh));
         base = __shfl_sync(kFull, base, __ffs(mh) - 1);
         if (heavy) {
-            const uint32_t at = base + 4u * (uint32_t)__popc(mh & below);
+            const uint32_t at = base + kStrips * (uint32_t)__popc(mh & below);
 #pragma unroll
-            for (uint32_t s = 0; s < 4; ++s) active[at + s] = t | ((s + 1u) << kStripShift);
+            for (uint32_t s = 0; s < kStrips; ++s) active[at + s] = t | ((s + 1u) << kStripShift);
         }
     }
     if (ml) {
@@ -452,11 +457,11 @@ Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64
 
 Status launch_ranges_active(const uint32_t* keys, uint64_t n_cap, const uint64_t* d_n, uint2* ranges,
                             uint32_t n_tiles, const uint32_t* done, uint32_t* active, uint32_t* n_active,
-                            uint32_t* overflow, const uint32_t* hi_bases, cudaStream_t st) {
+                            uint32_t* overflow, const uint32_t* hi_bases, uint32_t* strips, cudaStream_t st) {
     if (n_tiles == 0) return {};
     if (hi_bases && n_tiles > 65536u) return {TIGAS_ERR_INVALID, "second-pass digit bases need tile ids of 16 bits"};
     k_ranges_active<<<(n_tiles + 255) / 256, 256, 0, st>>>(keys, n_cap, d_n, ranges, n_tiles, done, active, n_active,
-                                                           overflow, hi_bases);
+                                                           overflow, hi_bases, strips);
     TIGAS_LAUNCHED();
     return {};
 }

@@ -9,23 +9,40 @@ namespace tigas {
 #define TIGAS_HEAVY_TILE 128
 #endif
 constexpr uint32_t kHeavyTile = TIGAS_HEAVY_TILE;   // pairs of a slice that make a tile "long"
+// A long tile is composited as kStrips strips of 16 / kStrips pixel rows,
+// each a separate item of the active list.
+#ifndef TIGAS_STRIPS
+#define TIGAS_STRIPS 2
+#endif
+constexpr uint32_t kStrips = TIGAS_STRIPS;
+static_assert(kStrips == 2 || kStrips == 4, "a strip holds 8 or 4 pixel rows");
+constexpr uint32_t kStripRows = 16 / kStrips;
+constexpr uint32_t kStripsAll = (1u << kStrips) - 1u;   // strip-word bits of a tile whose strips all stopped
 // Active-list items: a tile id (whole tile) or tile id | (s + 1) << kStripShift
-// for strip s (pixel rows 4s..4s+3) of a long tile.
+// for strip s (pixel rows kStripRows s .. kStripRows (s + 1) - 1) of a long tile.
 constexpr int kStripShift = 28;
-// Strip-word bit of a tile that some slice blended: its pixels carry (C, T)
-// in the state (bits 0-3: strip s's pixels all stopped).
+// Strip-word bits (bits 0-3: strip s's pixels all stopped).  kStripSeen: a
+// slice before the current one blended the tile, so its pixels carry (C, T)
+// in the state.  A blend marks the tiles it visits with kStripSeenNow instead,
+// never with kStripSeen: the strips of one tile run in the same slice on
+// different warps, and a strip that finished first must not make a sibling
+// that starts later take its first visit for a later one (and read state
+// nobody wrote).  The next slice's ranges kernel, which runs after that blend
+// and before the next, turns kStripSeenNow into kStripSeen.
 constexpr uint32_t kStripSeen = 0x10u;
+constexpr uint32_t kStripSeenNow = 0x20u;
 constexpr uint32_t kTileMask = (1u << kStripShift) - 1u;
 
 // Clears the per-tile done bits (total_tiles bits) and strip words (bits 0-3:
-// strip s of the tile finished; kStripSeen: the tile was blended and its
-// pixels carry (C, T) in `state`, so its first blend starts from (0, 1)
-// instead), and totals[0 .. n_totals) (at most 256).  No pixel is written.
+// strip s of the tile finished; kStripSeen / kStripSeenNow: the tile was
+// blended and its pixels carry (C, T) in `state`; a tile's first blend starts
+// from (0, 1) instead), and totals[0 .. n_totals) (at most 256).  No pixel is
+// written.
 Status launch_init_slices(uint32_t total_tiles, uint32_t* done, uint32_t* strips, uint64_t* totals, int n_totals,
                           cudaStream_t st);
 
 // After the last slice: the background in the outputs of every tile that no
-// slice blended (kStripSeen clear).
+// slice blended (kStripSeen and kStripSeenNow clear).
 Status launch_fill_unseen(const ViewParams* views, int V, uint32_t total_tiles, const uint32_t* strips,
                           const float* bg, cudaStream_t st);
 
@@ -52,10 +69,11 @@ Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64
                          cudaStream_t st);
 
 // Tile ranges of the slice's sorted keys, and the list of tiles with pairs
-// that are not done: each tile with >= kHeavyTile pairs as its 4 strips at the
-// front of `active` (n_active[0] items), the other tiles whole at its back
-// (active[4 n_tiles - 1 - k], n_active[1] items); both counts must be zero
-// on entry (launch_running_sat clears them).
+// that are not done: each tile with >= kHeavyTile pairs as its kStrips strips
+// at the front of `active` (n_active[0] items), the other tiles whole at its
+// back (active[4 n_tiles - 1 - k], n_active[1] items); both counts must be
+// zero on entry (launch_running_sat clears them).  Also turns every strip
+// word's kStripSeenNow into kStripSeen (the blend before this one is over).
 // `active` holds 4 n_tiles items.
 // The key count is min(*d_n, n_cap) when d_n is given, else n_cap.
 // hi_bases: null, or 256 words whose word h is the first position of a key
@@ -63,7 +81,7 @@ Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64
 // `keys`); n_tiles <= 65536.
 Status launch_ranges_active(const uint32_t* keys, uint64_t n_cap, const uint64_t* d_n, uint2* ranges,
                             uint32_t n_tiles, const uint32_t* done, uint32_t* active, uint32_t* n_active,
-                            uint32_t* overflow, const uint32_t* hi_bases, cudaStream_t st);
+                            uint32_t* overflow, const uint32_t* hi_bases, uint32_t* strips, cudaStream_t st);
 
 // Blend of the active tiles of one slice: persistent CTAs take tiles from the
 // active list, composite the slice's entries onto each pixel's carried state,
@@ -74,11 +92,11 @@ struct SliceBlendArgs {
     const uint32_t* n_active;   // [long tiles at the front, short tiles at the back]
     uint32_t* work_counter;     // zero on entry (launch_running_sat clears it)
     float4* state;              // per pixel (C.rgb, T), T negated once the pixel stopped; valid for the
-                                // tiles whose strip word has kStripSeen
+                                // tiles whose strip word has kStripSeen (or kStripSeenNow)
     const uint64_t* pix_base;   // per view
     uint32_t* done;             // per-tile bitmap
-    uint32_t* strips;           // per tile: bit s set once strip s's pixels all stopped, kStripSeen once
-                                // a slice blended it (its pixels carry state)
+    uint32_t* strips;           // per tile: bit s set once strip s's pixels all stopped, kStripSeenNow once
+                                // this slice blended it, kStripSeen once an earlier one did
     uint32_t active_cap;        // capacity of `active` (4 x all tiles of the launch set)
 };
 Status launch_blend_slice(const uint2* ranges, const uint32_t* values, const SplatArrays& sp,
