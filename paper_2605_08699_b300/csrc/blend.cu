@@ -111,6 +111,43 @@ __device__ inline bool alpha_box_meets(const float4& gm, const float4& ap, float
     return gm.x - hx <= x1 && gm.x + hx >= x0 && gm.y - hy <= y1 && gm.y + hy >= y0;
 }
 
+#ifndef TIGAS_BLEND_EXACT_CULL
+#define TIGAS_BLEND_EXACT_CULL 1
+#endif
+// The same question answered exactly for the ellipse (the bounding box above
+// keeps entries whose ellipse misses the rectangle but whose box does not):
+// is the minimum of q(mu - p) over p in [x0, x1] x [y0, y1] at most tau?  q is
+// convex, so the minimum is 0 when mu lies in the rectangle, else it lies on a
+// side that faces mu (at most two): on the side x = xe the best dy is
+// -m01 dx / m11 clamped to the side, on y = ye the best dx is -m01 dy / m00.
+// The answer is widened (tau 1.02 + 0.02, and any point of a side counts) so
+// that FP32 rounding here or in the per-pixel test can never drop an entry a
+// pixel takes: a pixel centre inside the rectangle with
+// q(mu - p) <= tau has min <= q(mu - p) <= tau.
+__device__ inline bool alpha_ellipse_meets(const float4& gm, const float4& ap, float x0, float x1, float y0,
+                                           float y1) {
+    const float tau = ap.y - kMinLog2Alpha;
+    const float m00 = -gm.z, m11 = -ap.x, m01 = -0.5f * gm.w;
+    const float det = fmaf(m00, m11, -m01 * m01);
+    if (!(tau >= 0.0f) || !(det > 0.0f)) return false;
+    const float u = gm.x, v = gm.y;
+    const float xe = fminf(fmaxf(u, x0), x1), ye = fminf(fmaxf(v, y0), y1);
+    if (xe == u && ye == v) return true;   // the centre lies in the rectangle
+    const float lim = fmaf(tau, 1.02f, 0.02f);
+    float best = __int_as_float(0x7f800000);
+    if (xe != u) {   // the side x = xe
+        const float dx = u - xe;
+        const float dy = fminf(fmaxf(__fdividef(-m01 * dx, m11), v - y1), v - y0);
+        best = fminf(best, fmaf(m00 * dx, dx, dy * fmaf(2.0f * m01, dx, m11 * dy)));
+    }
+    if (ye != v) {   // the side y = ye
+        const float dy = v - ye;
+        const float dx = fminf(fmaxf(__fdividef(-m01 * dy, m00), u - x1), u - x0);
+        best = fminf(best, fmaf(m11 * dy, dy, dx * fmaf(2.0f * m01, dy, m00 * dx)));
+    }
+    return best <= lim;
+}
+
 struct BlendCounts {
     unsigned long long eval = 0, fetched = 0, blend = 0;
 };
@@ -204,8 +241,11 @@ __device__ __forceinline__ bool blend_rows(WarpStage& sm, int lane, const uint2*
         const uint32_t r_lo = __reduce_min_sync(kFull, live ? row + 2u * (uint32_t)(__ffs(live) - 1) : 16u);
         const uint32_t r_hi = __reduce_max_sync(kFull, live ? row + 2u * (uint32_t)(31 - __clz(live)) : 0u);
         // the lane's own staged entry: can it reach one of those pixels?
-        const bool meets = lane < n_b && alpha_box_meets(sm.geom[buf][lane], sm.appear[buf][lane], tx0 + (float)c_lo,
-                                                         tx0 + (float)c_hi, ty0 + (float)r_lo, ty0 + (float)r_hi);
+        bool meets = lane < n_b && alpha_box_meets(sm.geom[buf][lane], sm.appear[buf][lane], tx0 + (float)c_lo,
+                                                   tx0 + (float)c_hi, ty0 + (float)r_lo, ty0 + (float)r_hi);
+        if (TIGAS_BLEND_EXACT_CULL && meets)
+            meets = alpha_ellipse_meets(sm.geom[buf][lane], sm.appear[buf][lane], tx0 + (float)c_lo,
+                                        tx0 + (float)c_hi, ty0 + (float)r_lo, ty0 + (float)r_hi);
         uint32_t kept = __ballot_sync(kFull, meets);
         __syncwarp();   // every lane's copies visible to the warp
         if (COUNT) cnt.fetched += (uint64_t)n_b;
