@@ -41,10 +41,23 @@ constexpr uint32_t kFull = 0xFFFFFFFFu;
 // alpha >= 1/255  <=>  power log2 e + log2 o >= log2(1/255)
 constexpr float kMinLog2Alpha = -7.99435343685885793f;
 
+// Batches in flight per warp: the gathers of the next kStages - 1 batches are
+// issued while one is composited, and each batch's list indices are loaded
+// one batch before its gather (so a batch costs one memory round trip, not
+// two, when compositing it is quick, as in the late slices' long lists).
+// Measured on the 8-view 1080p launch set: 2 stages with the index prefetch
+// 1.287 ms of blend, without it 1.319; 3 stages 1.307, 4 stages 1.421 (the
+// larger shared-memory share leaves less L1).
+#ifndef TIGAS_BLEND_STAGES
+#define TIGAS_BLEND_STAGES 2
+#endif
+constexpr int kStages = TIGAS_BLEND_STAGES;
+static_assert(kStages >= 2 && kStages <= 4, "two to four staging buffers");
+
 struct __align__(16) WarpStage {
-    float4 geom[2][kWB];     // (u, v, a', b')
-    float4 appear[2][kWB];   // (c', log2 o, r, g)
-    float blue[2][kWB];
+    float4 geom[kStages][kWB];     // (u, v, a', b')
+    float4 appear[kStages][kWB];   // (c', log2 o, r, g)
+    float blue[kStages][kWB];
 };
 
 __device__ inline void cp_async16(void* smem, const void* gmem) {
@@ -205,33 +218,42 @@ __device__ __forceinline__ bool blend_rows(WarpStage& sm, int lane, const uint2*
     const uint2 rg = ranges[g];
     const uint32_t start = rg.x, end = rg.y > rg.x ? rg.y : rg.x;
     const int nb = (int)((end - start + kWB - 1) / kWB);
-    auto stage = [&](int b, int buf) {
+    // the lane's entry of batch b, or ~0u past the list (loaded a batch ahead of its gather)
+    auto index_of = [&](int b) -> uint32_t {
         const uint32_t idx = start + (uint32_t)b * kWB + lane;
-        if (lane < kWB && idx < end) {   // one staged entry per lane of the batch
-            const uint32_t e = values[idx];
-            if (e < n_entries) {
-                cp_async16(&sm.geom[buf][lane], sp.geom + e);
-                cp_async16(&sm.appear[buf][lane], sp.appear + e);
-                cp_async4(&sm.blue[buf][lane], sp.blue + e);
-            } else {
-                // out-of-range entry (cannot happen for a consistent frame): contributes nothing
-                sm.geom[buf][lane] = make_float4(-1e30f, -1e30f, 0.f, 0.f);
-                sm.appear[buf][lane] = make_float4(0.f, -1e30f, 0.f, 0.f);
-                sm.blue[buf][lane] = 0.f;
-            }
+        return lane < kWB && idx < end ? values[idx] : ~0u;
+    };
+    auto stage = [&](uint32_t e, int buf) {   // one staged entry per lane of the batch
+        if (e < n_entries) {
+            cp_async16(&sm.geom[buf][lane], sp.geom + e);
+            cp_async16(&sm.appear[buf][lane], sp.appear + e);
+            cp_async4(&sm.blue[buf][lane], sp.blue + e);
+        } else if (e != ~0u) {
+            // out-of-range entry (cannot happen for a consistent frame): contributes nothing
+            sm.geom[buf][lane] = make_float4(-1e30f, -1e30f, 0.f, 0.f);
+            sm.appear[buf][lane] = make_float4(0.f, -1e30f, 0.f, 0.f);
+            sm.blue[buf][lane] = 0.f;
         }
-        cp_async_commit();
     };
 
-    if (nb > 0) stage(0, 0);
+    // prologue: gathers of batches 0 .. kStages - 2 in flight, the indices of the next one loaded
+#pragma unroll
+    for (int q = 0; q < kStages - 1; ++q) {
+        if (q < nb) stage(index_of(q), q);
+        cp_async_commit();   // one group per batch slot, empty past the list (uniform group counts)
+    }
+    uint32_t e_next = kStages - 1 < nb ? index_of(kStages - 1) : ~0u;
     for (int b = 0; b < nb; ++b) {
-        const int buf = b & 1;
-        if (b + 1 < nb) {
-            stage(b + 1, buf ^ 1);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
+        const int buf = b % kStages;
+        {
+            // the gather of batch b + kStages - 1 into the buffer batch b - 1 used, then the
+            // indices of the batch after it
+            const int bn = b + kStages - 1;
+            if (bn < nb) stage(e_next, bn % kStages);
+            cp_async_commit();
+            e_next = bn + 1 < nb ? index_of(bn + 1) : ~0u;
         }
+        cp_async_wait<kStages - 1>();   // batch b's group has landed
         const uint32_t rem = end - start - (uint32_t)b * kWB;
         const int n_b = rem < (uint32_t)kWB ? (int)rem : kWB;
         if (__all_sync(kFull, live == 0)) break;
