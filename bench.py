@@ -288,8 +288,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     # stages are timed in a separate untimed pass (each timed stage adds graph nodes)
     tg.profile_stages(["blend"])
     if args.schedule:
-        n_sl, first, ctas = (int(x) for x in args.schedule.split(","))
-        tg.set_schedule(n_sl, first, ctas)
+        tg.set_schedule(*(int(x) for x in args.schedule.split(",")))
     schedule = tg.get_schedule()
     if not args.no_autotune and not args.schedule:
         # untimed: pick the sliced schedule for this launch-set shape (with the blend events on, as timed)
@@ -914,7 +913,8 @@ def main(argv=None) -> int:
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule")
     ap.add_argument("--inflight", type=int, default=2, help="also time this many launch sets in flight (1: skip)")
-    ap.add_argument("--schedule", default="", help="fixed schedule 'slices,first_slice_inv,blend_ctas_per_sm' "
+    ap.add_argument("--schedule", default="", help="fixed schedule 'slices,first_slice_inv,blend_ctas_per_sm"
+                                                   "[,blend_batch[,views_per_set]]' "
                                                    "(no autotuning)")
     ap.add_argument("--trace-seconds", type=float, default=10.0, help="open-loop serving trace length (0: skip)")
     ap.add_argument("--trace-clients", type=int, default=64)

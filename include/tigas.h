@@ -366,11 +366,18 @@ tigas_status tigas_profile_read(double* ms, uint64_t* calls, int reset);
  *                     entries, later ones grow geometrically to all of them,
  *                     1..4096 (default 64)
  *  blend_ctas_per_sm: persistent blend CTAs per SM, 0..64; 0 or more than
- *                     fit means as many as fit (default 0) */
+ *                     fit means as many as fit (default 0)
+ *  blend_batch:       list entries a blend warp stages in shared memory at a
+ *                     time, 16 or 32 (0 is read as 32; default 32)
+ *  views_per_set:     most views a server launch set fuses (the smaller of
+ *                     this and the server's max_batch), 0..64, 0 = no cap
+ *                     (default 0); tigas_render_batch* are not affected */
 typedef struct {
     int n_slices;
     int first_slice_inv;
     int blend_ctas_per_sm;
+    int blend_batch;
+    int views_per_set;
 } tigas_schedule;
 
 /* Set / read the process-wide schedule.  Errors: INVALID (out of range).
@@ -381,15 +388,22 @@ tigas_status tigas_get_schedule(tigas_schedule* schedule);
 /* Autotuner of the batching step: renders launch sets of n_views views
  * (device RGBA8 outputs, resolutions widths/heights[n_views]), cycling through
  * n_sets (1..1024) pose sets (poses and intrs hold n_sets * n_views entries,
- * set-major) so that the timing covers varying pair counts, under each
- * candidate schedule (slices 4, 6, 8,
- * 12, 16 x first slice 1/16, 1/64, 1/256 x blend CTAs per SM all or 4), two
- * untimed launch sets then `iters` (1..100) timed ones each; the four with
- * the lowest median host time per launch set run 2 iters + 1 more times each,
- * interleaved, and the lowest median of those wins.  It becomes the
- * process-wide schedule and is written to *best (best_ms: its median).  Call
- * it while no other render is running.  Errors: INVALID, and those of
- * tigas_render_batch (the schedule in force before the call is restored). */
+ * set-major) so that the timing covers varying pair counts.
+ *  1. Every candidate sliced schedule (slices 4, 6, 8, 12, 16 x first slice
+ *     1/16, 1/64, 1/256 x blend CTAs per SM all or 4 x blend batch 32 or 16):
+ *     two untimed launch sets then `iters` (1..100) timed ones each; the four
+ *     with the lowest median host time per launch set run 2 iters + 1 more
+ *     times each, interleaved, and the lowest median of those wins.
+ *  2. With that schedule, the views per launch set: the n_views views of a
+ *     pose set rendered as launch sets of m = n_views, n_views / 2, ... views
+ *     (each m that divides n_views), two untimed rounds then 2 iters + 1
+ *     timed ones each; the m with the lowest median time per view wins
+ *     (views_per_set = m).
+ * The result becomes the process-wide schedule and is written to *best
+ * (best_ms: the winner's median host time per launch set of n_views views in
+ * step 1).  Call it while no other render is running.  Errors: INVALID, and
+ * those of tigas_render_batch (the schedule in force before the call is
+ * restored). */
 tigas_status tigas_autotune(tigas_scene* scene, int n_sets, int n_views, const tigas_pose* poses,
                             const tigas_intrinsics* intrs, const int* widths, const int* heights,
                             uint8_t* const* outs_rgba8, int iters, tigas_schedule* best, double* best_ms);

@@ -27,11 +27,7 @@ namespace {
 
 constexpr int kWarps = 4;                 // tiles per CTA
 constexpr int kThreads = 32 * kWarps;
-#ifndef TIGAS_BLEND_BATCH
-#define TIGAS_BLEND_BATCH 32
-#endif
-constexpr int kWB = TIGAS_BLEND_BATCH;    // entries per warp batch (at most 32: one per lane)
-static_assert(kWB >= 1 && kWB <= 32, "a batch holds one entry per lane at most");
+// Entries per warp batch (a schedule parameter): 32 (one per lane) or 16.
 constexpr int kPix = 8;                   // pixels per thread
 #ifndef TIGAS_BLEND_MIN_BLOCKS
 #define TIGAS_BLEND_MIN_BLOCKS 8
@@ -54,7 +50,9 @@ constexpr float kMinLog2Alpha = -7.99435343685885793f;
 constexpr int kStages = TIGAS_BLEND_STAGES;
 static_assert(kStages >= 2 && kStages <= 4, "two to four staging buffers");
 
+template <int kWB>
 struct __align__(16) WarpStage {
+    static_assert(kWB >= 1 && kWB <= 32, "a batch holds one entry per lane at most");
     float4 geom[kStages][kWB];     // (u, v, a', b')
     float4 appear[kStages][kWB];   // (c', log2 o, r, g)
     float blue[kStages][kWB];
@@ -169,8 +167,8 @@ struct BlendCounts {
 // at row0: thread lane takes column lane % 16 and rows row0 + lane / 16 + 2k,
 // k < NP.  SLICED: start from and store back each pixel's carried (C, T).
 // Returns (warp-uniform) whether every pixel of these rows has stopped.
-template <bool SLICED, bool COUNT, int NP>
-__device__ __forceinline__ bool blend_rows(WarpStage& sm, int lane, const uint2* __restrict__ ranges,
+template <bool SLICED, bool COUNT, int NP, int kWB>
+__device__ __forceinline__ bool blend_rows(WarpStage<kWB>& sm, int lane, const uint2* __restrict__ ranges,
                                            const uint32_t* __restrict__ values, const SplatArrays& sp,
                                            const ViewParams& vp, uint32_t g, uint32_t local, int row0,
                                            uint64_t sbase, uint32_t n_entries, float bg_r, float bg_g, float bg_b,
@@ -376,17 +374,17 @@ __device__ __forceinline__ bool blend_rows(WarpStage& sm, int lane, const uint2*
 // pixel's (C, T) across slices, and mark tiles whose pixels all stopped.
 // COUNT: accumulate list entries evaluated per pixel (up to its stop), entries
 // staged, and entries blended.
-template <bool SLICED, bool COUNT>
+template <bool SLICED, bool COUNT, int kWB>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
 k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ values, SplatArrays sp,
         const ViewParams* __restrict__ views_g, int V, uint32_t total_tiles, uint32_t n_entries, float bg_r,
         float bg_g, float bg_b, unsigned long long* counters, SliceBlendArgs sl) {
-    __shared__ WarpStage stage_sm[kWarps];
+    __shared__ WarpStage<kWB> stage_sm[kWarps];
     __shared__ uint32_t s_tb[kMaxViews];
     for (int k = threadIdx.x; k < V; k += kThreads) s_tb[k] = views_g[k].tile_base;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    WarpStage& sm = stage_sm[warp];
+    WarpStage<kWB>& sm = stage_sm[warp];
     BlendCounts cnt;
     const uint32_t n_long = SLICED ? sl.n_active[0] : 0u;
     const uint32_t n_items = SLICED ? n_long + sl.n_active[1] : total_tiles;
@@ -414,13 +412,13 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ values, S
         const uint32_t local = g - s_tb[v];
         const uint64_t sbase = SLICED ? sl.pix_base[v] : 0;
         if (!SLICED || strip == 0) {
-            const bool all = blend_rows<SLICED, COUNT, kPix>(sm, lane, ranges, values, sp, vp, g, local, 0, sbase,
+            const bool all = blend_rows<SLICED, COUNT, kPix, kWB>(sm, lane, ranges, values, sp, vp, g, local, 0, sbase,
                                                              n_entries, bg_r, bg_g, bg_b, sl, cnt);
             if (!SLICED) break;
             if (all && lane == 0) atomicOr(&sl.done[g >> 5], 1u << (g & 31));
         } else {
             const uint32_t bit = 1u << (strip - 1);
-            const bool all = blend_rows<SLICED, COUNT, (int)kStripRows / 2>(sm, lane, ranges, values, sp, vp, g, local,
+            const bool all = blend_rows<SLICED, COUNT, (int)kStripRows / 2, kWB>(sm, lane, ranges, values, sp, vp, g, local,
                                                                            (int)kStripRows * (int)(strip - 1), sbase,
                                                                            n_entries, bg_r, bg_g, bg_b, sl, cnt);
             if (all && lane == 0) {
@@ -452,10 +450,10 @@ Status launch_blend(const uint2* ranges, const uint32_t* values, const SplatArra
     if (total_tiles == 0) return {};
     const unsigned grid = (total_tiles + kWarps - 1) / kWarps;
     if (counters)
-        k_blend<false, true><<<grid, kThreads, 0, st>>>(ranges, values, sp, views, V, total_tiles, n_entries, bg[0],
+        k_blend<false, true, 32><<<grid, kThreads, 0, st>>>(ranges, values, sp, views, V, total_tiles, n_entries, bg[0],
                                                         bg[1], bg[2], counters, SliceBlendArgs{});
     else
-        k_blend<false, false><<<grid, kThreads, 0, st>>>(ranges, values, sp, views, V, total_tiles, n_entries, bg[0],
+        k_blend<false, false, 32><<<grid, kThreads, 0, st>>>(ranges, values, sp, views, V, total_tiles, n_entries, bg[0],
                                                          bg[1], bg[2], nullptr, SliceBlendArgs{});
     TIGAS_LAUNCHED();
     return {};
@@ -463,29 +461,42 @@ Status launch_blend(const uint2* ranges, const uint32_t* values, const SplatArra
 
 Status launch_blend_slice(const uint2* ranges, const uint32_t* values, const SplatArrays& sp,
                           const ViewParams* views, int V, uint32_t n_entries, const float* bg,
-                          unsigned long long* counters, const SliceBlendArgs& sl, int ctas_per_sm,
+                          unsigned long long* counters, const SliceBlendArgs& sl, int ctas_per_sm, int batch,
                           cudaStream_t st) {
+    if (batch != 16 && batch != 32) return {TIGAS_ERR_INVALID, "blend batch must be 16 or 32"};
     struct Fit {
         int per_sm = 1, sms = 0;   // CTAs per SM that fit, SM count
         cudaError_t err = cudaSuccess;
     };
-    static const Fit f = [] {   // thread-safe one-time query
+    // thread-safe one-time queries, per batch size (the kernels' resources differ)
+    auto fit = [](auto kernel) {
         Fit r;
         int per_sm = 0, dev = 0;
-        r.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_blend<true, false>, kThreads, 0);
+        r.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0);
         if (r.err == cudaSuccess) r.err = cudaGetDevice(&dev);
         if (r.err == cudaSuccess) r.err = cudaDeviceGetAttribute(&r.sms, cudaDevAttrMultiProcessorCount, dev);
         r.per_sm = per_sm > 0 ? per_sm : 1;
         return r;
-    }();
+    };
+    static const Fit f32 = fit(k_blend<true, false, 32>);
+    static const Fit f16 = fit(k_blend<true, false, 16>);
+    const Fit& f = batch == 16 ? f16 : f32;
     TIGAS_CUDA_TRY(f.err);
     const int grid = (ctas_per_sm > 0 && ctas_per_sm < f.per_sm ? ctas_per_sm : f.per_sm) * f.sms;
-    if (counters)
-        k_blend<true, true><<<grid, kThreads, 0, st>>>(ranges, values, sp, views, V, 0, n_entries, bg[0], bg[1], bg[2],
-                                                       counters, sl);
+#define TIGAS_BLEND_SLICE(WB)                                                                                        \
+    do {                                                                                                             \
+        if (counters)                                                                                                \
+            k_blend<true, true, WB><<<grid, kThreads, 0, st>>>(ranges, values, sp, views, V, 0, n_entries, bg[0],    \
+                                                               bg[1], bg[2], counters, sl);                          \
+        else                                                                                                         \
+            k_blend<true, false, WB><<<grid, kThreads, 0, st>>>(ranges, values, sp, views, V, 0, n_entries, bg[0],   \
+                                                                bg[1], bg[2], nullptr, sl);                          \
+    } while (0)
+    if (batch == 16)
+        TIGAS_BLEND_SLICE(16);
     else
-        k_blend<true, false><<<grid, kThreads, 0, st>>>(ranges, values, sp, views, V, 0, n_entries, bg[0], bg[1],
-                                                        bg[2], nullptr, sl);
+        TIGAS_BLEND_SLICE(32);
+#undef TIGAS_BLEND_SLICE
     TIGAS_LAUNCHED();
     return {};
 }

@@ -111,6 +111,7 @@ Status submit_render(RenderContext& ctx, Scene* scene, int V, const tigas_pose* 
     req.n_slices = sched.n_slices;
     req.first_slice_inv = sched.first_slice_inv;
     req.blend_ctas_per_sm = sched.blend_ctas_per_sm;
+    req.blend_batch = sched.blend_batch;
     req.want_q = want_q;
     req.want_counters = want_stats;
     p.host8.assign(V, nullptr);
@@ -300,6 +301,9 @@ Status check_schedule(const tigas_schedule* s) {
     if (s->n_slices < 1 || s->n_slices > kMaxSlices) return {TIGAS_ERR_INVALID, "n_slices out of 1..16"};
     if (s->first_slice_inv < 1 || s->first_slice_inv > 4096) return {TIGAS_ERR_INVALID, "first_slice_inv out of 1..4096"};
     if (s->blend_ctas_per_sm < 0 || s->blend_ctas_per_sm > 64) return {TIGAS_ERR_INVALID, "blend_ctas_per_sm out of 0..64"};
+    if (s->blend_batch != 0 && s->blend_batch != 16 && s->blend_batch != 32)
+        return {TIGAS_ERR_INVALID, "blend_batch must be 0, 16 or 32"};
+    if (s->views_per_set < 0 || s->views_per_set > kMaxViews) return {TIGAS_ERR_INVALID, "views_per_set out of 0..64"};
     return {};
 }
 }  // namespace
@@ -307,7 +311,8 @@ Status check_schedule(const tigas_schedule* s) {
 TIGAS_API tigas_status tigas_set_schedule(const tigas_schedule* s) {
     Status c = check_schedule(s);
     if (!c.ok()) return fail(c);
-    set_schedule(Schedule{s->n_slices, s->first_slice_inv, s->blend_ctas_per_sm});
+    set_schedule(Schedule{s->n_slices, s->first_slice_inv, s->blend_ctas_per_sm, s->blend_batch ? s->blend_batch : 32,
+                          s->views_per_set});
     return TIGAS_OK;
 }
 
@@ -317,6 +322,8 @@ TIGAS_API tigas_status tigas_get_schedule(tigas_schedule* s) {
     s->n_slices = c.n_slices;
     s->first_slice_inv = c.first_slice_inv;
     s->blend_ctas_per_sm = c.blend_ctas_per_sm;
+    s->blend_batch = c.blend_batch;
+    s->views_per_set = c.views_per_set;
     return TIGAS_OK;
 }
 
@@ -337,37 +344,46 @@ TIGAS_API tigas_status tigas_autotune(tigas_scene* scene, int n_sets, int n_view
     static const int kSlices[] = {4, 6, 8, 12, 16};
     static const int kFirst[] = {16, 64, 256};
     static const int kCtas[] = {0, 4};
+    static const int kBatch[] = {32, 16};
     std::vector<Schedule> cands;
     for (int ns : kSlices)
         for (int fi : kFirst)
-            for (int ct : kCtas) cands.push_back(Schedule{ns, fi, ct});
+            for (int ct : kCtas)
+                for (int wb : kBatch) cands.push_back(Schedule{ns, fi, ct, wb, saved.views_per_set});
     std::vector<std::vector<double>> times(cands.size());
     int next_set = 0;
-    // one launch set (the next pose set) under schedule c; untimed ones warm up
-    // (a shape's first launch set runs directly, the second is captured)
+    // the next pose set's views [v0, v0 + m) as one launch set; returns host ms
+    auto render_part = [&](int v0, int m, double* ms) -> Status {
+        const size_t off = (size_t)next_set * n_views + v0;
+        const auto t0 = std::chrono::steady_clock::now();
+        Status s = do_render(sc, m, poses + off, intrs + off, widths + v0, heights + v0, outs_rgba8 + v0, nullptr,
+                             nullptr, TIGAS_SORT_SLICED, nullptr, nullptr, nullptr);
+        *ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        return s;
+    };
+    // one launch set of all views (the next pose set) under schedule c; untimed ones
+    // warm up (a shape's first launch set runs directly, the second is captured)
     auto run = [&](size_t c, bool timed) -> Status {
         set_schedule(cands[c]);
-        const size_t off = (size_t)next_set * n_views;
+        double ms = 0.0;
+        Status s = render_part(0, n_views, &ms);
         next_set = (next_set + 1) % n_sets;
-        const auto t0 = std::chrono::steady_clock::now();
-        Status s = do_render(sc, n_views, poses + off, intrs + off, widths, heights, outs_rgba8, nullptr, nullptr,
-                             TIGAS_SORT_SLICED, nullptr, nullptr, nullptr);
-        const auto t1 = std::chrono::steady_clock::now();
-        if (timed) times[c].push_back(std::chrono::duration<double, std::milli>(t1 - t0).count());
+        if (timed) times[c].push_back(ms);
         return s;
     };
     auto median = [](std::vector<double> t) {
         std::sort(t.begin(), t.end());
         return t.empty() ? 1e300 : t[t.size() / 2];
     };
+    auto give_up = [&](const Status& s) {
+        set_schedule(saved);
+        return fail(s);
+    };
     // first pass: every candidate, two untimed then `iters` timed launch sets
     for (size_t c = 0; c < cands.size(); ++c)
         for (int it = 0; it < iters + 2; ++it) {
             Status s = run(c, it >= 2);
-            if (!s.ok()) {
-                set_schedule(saved);
-                return fail(s);
-            }
+            if (!s.ok()) return give_up(s);
         }
     // second pass: the four fastest again, interleaved so that drift hits them alike
     std::vector<size_t> order(cands.size());
@@ -378,10 +394,7 @@ TIGAS_API tigas_status tigas_autotune(tigas_scene* scene, int n_sets, int n_view
     for (int round = 0; round < 2 * iters + 1; ++round)
         for (size_t c : order) {
             Status s = run(c, true);
-            if (!s.ok()) {
-                set_schedule(saved);
-                return fail(s);
-            }
+            if (!s.ok()) return give_up(s);
         }
     Schedule win = saved;
     double win_ms = 1e300;
@@ -392,11 +405,40 @@ TIGAS_API tigas_status tigas_autotune(tigas_scene* scene, int n_sets, int n_view
             win = cands[c];
         }
     }
+    // views per launch set under the winning schedule: the pose set's views as
+    // n_views / m launch sets of m, time per view
+    set_schedule(win);
+    int win_m = n_views;
+    double win_per_view = 1e300;
+    for (int m = n_views; m >= 1; m /= 2) {
+        if (n_views % m != 0) continue;
+        std::vector<double> per_view;
+        for (int round = 0; round < 2 * iters + 3; ++round) {
+            double total = 0.0;
+            for (int v0 = 0; v0 < n_views; v0 += m) {
+                double ms = 0.0;
+                Status s = render_part(v0, m, &ms);
+                if (!s.ok()) return give_up(s);
+                total += ms;
+            }
+            next_set = (next_set + 1) % n_sets;
+            if (round >= 2) per_view.push_back(total / n_views);
+        }
+        const double med = median(per_view);
+        if (med < win_per_view) {
+            win_per_view = med;
+            win_m = m;
+        }
+        if (m == 1) break;
+    }
+    win.views_per_set = win_m;
     set_schedule(win);
     if (best) {
         best->n_slices = win.n_slices;
         best->first_slice_inv = win.first_slice_inv;
         best->blend_ctas_per_sm = win.blend_ctas_per_sm;
+        best->blend_batch = win.blend_batch;
+        best->views_per_set = win.views_per_set;
     }
     if (best_ms) *best_ms = win_ms;
     return TIGAS_OK;

@@ -733,7 +733,8 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
         TIGAS_TRY(mark(kStRanges, false));
         TIGAS_TRY(mark(kStBlend, true));
         TIGAS_TRY(launch_blend_slice(ranges, vals_c, sp, d_views, V, (uint32_t)E, scene->view.bg,
-                                     req.want_counters ? d_counters : nullptr, sl, req.blend_ctas_per_sm, st));
+                                     req.want_counters ? d_counters : nullptr, sl, req.blend_ctas_per_sm,
+                                     req.blend_batch, st));
         TIGAS_TRY(mark(kStBlend, false));
         a = b;
     }
@@ -762,7 +763,7 @@ namespace {
 // its id, never by its address (a freed scene's address may come back).
 std::vector<int64_t> graph_key(const Scene* scene, const FrameRequest& req) {
     std::vector<int64_t> k = {(int64_t)scene->id, scene->view.storage, req.V, req.n_slices,
-                              req.first_slice_inv, req.blend_ctas_per_sm, req.want_counters ? 1 : 0,
+                              req.first_slice_inv, req.blend_ctas_per_sm, req.blend_batch, req.want_counters ? 1 : 0,
                               (int64_t)g_profile.load()};
     for (int v = 0; v < req.V; ++v) {
         k.push_back(req.views[v].W);

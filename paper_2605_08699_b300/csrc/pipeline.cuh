@@ -164,6 +164,7 @@ struct FrameRequest {
     int n_slices = 8;                    // sliced schedule: geometric depth slices
     int first_slice_inv = 64;            // the nearest slice holds 1/first_slice_inv of the entries
     int blend_ctas_per_sm = 0;           // persistent blend CTAs per SM (0: as many as fit)
+    int blend_batch = 32;                // list entries a blend warp stages at a time (16 or 32)
     bool want_counters = false;          // count blend evaluations / fetched entries
     bool want_q = false;
 };
@@ -200,6 +201,8 @@ struct Schedule {
     int n_slices = 8;
     int first_slice_inv = 64;
     int blend_ctas_per_sm = 0;
+    int blend_batch = 32;
+    int views_per_set = 0;   // the server's launch sets hold at most this many views (0: no cap)
 };
 Schedule current_schedule();
 void set_schedule(const Schedule& s);

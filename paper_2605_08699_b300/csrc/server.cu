@@ -102,17 +102,21 @@ struct Server {
                 if (stop) return;
                 continue;
             }
-            if (cfg.batch_window_us > 0 && (int)queue.size() < cfg.max_batch && !stop) {
+            // a launch set holds at most max_batch views, and no more than the tuned
+            // views per launch set of the current schedule
+            const int vps = current_schedule().views_per_set;
+            const int cap = vps > 0 && vps < cfg.max_batch ? vps : cfg.max_batch;
+            if (cfg.batch_window_us > 0 && (int)queue.size() < cap && !stop) {
                 // give a partial batch a short window to fill
                 cv_work.wait_for(lk, std::chrono::microseconds(cfg.batch_window_us),
-                                 [&] { return stop || (int)queue.size() >= cfg.max_batch; });
+                                 [&] { return stop || (int)queue.size() >= cap; });
                 if (queue.empty()) continue;
             }
             // form a batch: the oldest request's scene, oldest first, within budget
             Scene* scene = queue.front().scene;
             std::vector<Request> batch;
             uint64_t bytes = 0;
-            for (auto it = queue.begin(); it != queue.end() && (int)batch.size() < cfg.max_batch;) {
+            for (auto it = queue.begin(); it != queue.end() && (int)batch.size() < cap;) {
                 if (it->scene != scene) {
                     ++it;
                     continue;

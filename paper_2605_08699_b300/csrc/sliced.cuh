@@ -87,6 +87,7 @@ Status launch_ranges_active(const uint32_t* keys, uint64_t n_cap, const uint64_t
 // active list, composite the slice's entries onto each pixel's carried state,
 // store the state and the outputs, and mark tiles whose pixels all stopped.
 // ctas_per_sm: persistent CTAs per SM (0 or more than fit: as many as fit).
+// batch: list entries a warp stages at a time, 16 or 32.
 struct SliceBlendArgs {
     const uint32_t* active;
     const uint32_t* n_active;   // [long tiles at the front, short tiles at the back]
@@ -101,7 +102,7 @@ struct SliceBlendArgs {
 };
 Status launch_blend_slice(const uint2* ranges, const uint32_t* values, const SplatArrays& sp,
                           const ViewParams* views, int V, uint32_t n_entries, const float* bg,
-                          unsigned long long* counters, const SliceBlendArgs& sl, int ctas_per_sm,
+                          unsigned long long* counters, const SliceBlendArgs& sl, int ctas_per_sm, int batch,
                           cudaStream_t st);
 
 }  // namespace tigas

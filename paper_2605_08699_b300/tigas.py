@@ -75,11 +75,13 @@ class DebugFrame(ctypes.Structure):
 
 
 class Schedule(ctypes.Structure):
-    _fields_ = [("n_slices", ctypes.c_int), ("first_slice_inv", ctypes.c_int), ("blend_ctas_per_sm", ctypes.c_int)]
+    _fields_ = [("n_slices", ctypes.c_int), ("first_slice_inv", ctypes.c_int), ("blend_ctas_per_sm", ctypes.c_int),
+                ("blend_batch", ctypes.c_int), ("views_per_set", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {"n_slices": self.n_slices, "first_slice_inv": self.first_slice_inv,
-                "blend_ctas_per_sm": self.blend_ctas_per_sm}
+                "blend_ctas_per_sm": self.blend_ctas_per_sm, "blend_batch": self.blend_batch,
+                "views_per_set": self.views_per_set}
 
 
 class ServerConfig(ctypes.Structure):
@@ -590,9 +592,11 @@ def render_batch_async(scene: SceneHandle, poses: Sequence, intrs: Sequence, wid
     return RenderTicket(t.value, list(outs))
 
 
-def set_schedule(n_slices: int = 8, first_slice_inv: int = 64, blend_ctas_per_sm: int = 0) -> None:
+def set_schedule(n_slices: int = 8, first_slice_inv: int = 64, blend_ctas_per_sm: int = 0, blend_batch: int = 32,
+                 views_per_set: int = 0) -> None:
     """tigas_set_schedule: the depth-sliced schedule every launch set takes."""
-    _check(load_library().tigas_set_schedule(ctypes.byref(Schedule(n_slices, first_slice_inv, blend_ctas_per_sm))))
+    _check(load_library().tigas_set_schedule(ctypes.byref(Schedule(n_slices, first_slice_inv, blend_ctas_per_sm,
+                                                                   blend_batch, views_per_set))))
 
 
 def get_schedule() -> dict:

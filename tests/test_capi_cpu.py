@@ -94,9 +94,13 @@ def test_schedule_set_get_and_range_checks():
     tg.load_library()
     before = tg.get_schedule()
     try:
-        tg.set_schedule(12, 256, 3)
-        assert tg.get_schedule() == {"n_slices": 12, "first_slice_inv": 256, "blend_ctas_per_sm": 3}
-        for bad in [(0, 64, 0), (17, 64, 0), (8, 0, 0), (8, 5000, 0), (8, 64, -1), (8, 64, 65)]:
+        tg.set_schedule(12, 256, 3, 16, 4)
+        assert tg.get_schedule() == {"n_slices": 12, "first_slice_inv": 256, "blend_ctas_per_sm": 3, "blend_batch": 16,
+                                     "views_per_set": 4}
+        tg.set_schedule(12, 256, 3, 0, 0)   # blend batch 0 is read as 32
+        assert tg.get_schedule()["blend_batch"] == 32
+        for bad in [(0, 64, 0), (17, 64, 0), (8, 0, 0), (8, 5000, 0), (8, 64, -1), (8, 64, 65), (8, 64, 0, 8),
+                    (8, 64, 0, 64), (8, 64, 0, 32, -1), (8, 64, 0, 32, 65)]:
             with pytest.raises(tg.TigasError) as e:
                 tg.set_schedule(*bad)
             assert e.value.status == tg.ERR_INVALID

@@ -685,12 +685,39 @@ def test_frames_do_not_depend_on_the_schedule(h1, cuda):
     base = tg.get_schedule()
     try:
         ref = _batch(h1, tr[3:5], levels, cuda)
-        for sch in [(1, 1, 0), (4, 16, 0), (16, 256, 1), (12, 4096, 4)]:
+        for sch in [(1, 1, 0), (4, 16, 0), (16, 256, 1), (12, 4096, 4), (6, 64, 0, 16), (8, 64, 3, 16)]:
             tg.set_schedule(*sch)
             for _ in range(3):   # direct, exact + capture, replay
                 got = _batch(h1, tr[3:5], levels, cuda)
                 for a, b in zip(ref, got):
                     assert np.array_equal(a, b), sch
+    finally:
+        tg.set_schedule(**base)
+
+
+def test_server_launch_sets_respect_views_per_set(cuda, h1):
+    # the schedule's views per launch set caps the server's batches below max_batch
+    K = synth.default_intrinsics(160, 120)
+    tr = synth.trajectory(31, 8)
+    base = tg.get_schedule()
+    try:
+        tg.set_schedule(**{**base, "views_per_set": 2})
+        with tg.Server(max_batch=8, max_inflight=1, batch_window_us=300_000) as srv:
+            bufs = {}
+            for i, p in enumerate(tr):
+                b = torch.zeros((120, 160, 4), dtype=torch.uint8, device=cuda)
+                bufs[srv.submit(h1, p, K, 160, 120, b, client_id=i)] = (b, p)
+            done = []
+            while len(done) < len(tr):
+                done += srv.poll(16, timeout_us=2_000_000)
+        assert all(c.status == 0 for c in done)
+        sets = {}
+        for c in done:
+            sets.setdefault((c.admit_us, c.done_us), []).append(c)
+        assert max(len(v) for v in sets.values()) == 2 and len(sets) == 4
+        for c in done:
+            b, p = bufs[c.ticket]
+            assert np.array_equal(b.cpu().numpy(), tg.render(h1, p, K, 160, 120))
     finally:
         tg.set_schedule(**base)
 
@@ -707,6 +734,7 @@ def test_autotune_picks_a_candidate_and_keeps_frames(h1, cuda):
                                iters=1)
         assert best["n_slices"] in (4, 6, 8, 12, 16) and best["first_slice_inv"] in (16, 64, 256)
         assert best["blend_ctas_per_sm"] in (0, 4) and 0 < ms < 1e4
+        assert best["blend_batch"] in (16, 32) and best["views_per_set"] in (1, 2)
         assert tg.get_schedule() == best
         got = _batch(h1, tr[:2], levels, cuda)
         for a, b in zip(ref, got):
