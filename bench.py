@@ -151,8 +151,8 @@ def cpu_baseline(scene, poses, width, height, budget_s: float = 15.0) -> dict:
 # dram__bytes_read.sum + dram__bytes_write.sum; profiles/blend_ncu_3M_1080p.md), scaled by the
 # views a launch set renders.  Reported only while the kernel's source is the captured one.
 KERNEL_TRAFFIC = {
-    "blend": {"source": "paper_2605_08699_b300/csrc/blend.cu", "sha1": "c52be36d4eae9caceef27c0ee3db2f1d4e8dad82",
-              "bytes_per_view": 390_204_416 / 4},
+    "blend": {"source": "paper_2605_08699_b300/csrc/blend.cu", "sha1": "5b6227cedbdd7e06f327604d36515b0b8733f72b",
+              "bytes_per_view": 406341120 / 4},
 }
 
 
