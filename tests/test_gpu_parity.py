@@ -599,6 +599,28 @@ def test_full_size_default_schedule_is_bit_identical_to_whole_lists(cuda, s3, st
             assert st["n_pairs"] < full["pairs"]
 
 
+def test_every_launch_path_gives_the_whole_list_frame(cuda):
+    """A shape's first render is exact (a host round trip per slice), its
+    second exact and captured, its third a graph replay with fixed pair
+    capacities, and a new shape after that runs directly with a fixed
+    capacity: every float frame equals the whole-list one bit for bit."""
+    scene = synth.config_scene(2, n=600_000)
+    tr = synth.config_trajectory(2)
+    with tg.scene_from(scene, storage=tg.STORAGE_FP16) as h:
+        for W, H, k in ((1280, 720, 20), (960, 540, 21)):
+            K = synth.default_intrinsics(W, H)
+            full = tg.debug_render(h, tr[k], K, W, H, sort_mode=tg.SORT_DEPTH_FIRST)["rgba_f32"].view(np.uint32)
+            if W == 1280:
+                tg.set_graphs(True)   # idle contexts forget shapes and capacities: the next render is exact
+            frames = []
+            for _ in range(3):
+                f = torch.empty((H, W, 4), dtype=torch.float32, device=cuda)
+                tg.render_ex(h, tr[k], K, W, H, out_rgba_f32=f, sort_mode=tg.SORT_SLICED, stats=False)
+                frames.append(f.cpu().numpy().view(np.uint32))
+            for f in frames:
+                assert np.array_equal(f, full)
+
+
 def test_full_size_8_view_launch_set_view_is_bit_identical(cuda, s3):
     """One view of an 8-view 1080p launch set of the 3M FP16 scene (the timed
     configuration, through tigas_render_batch) against the whole-list debug
