@@ -389,8 +389,9 @@ tigas_status tigas_get_schedule(tigas_schedule* schedule);
  * (device RGBA8 outputs, resolutions widths/heights[n_views]), cycling through
  * n_sets (1..1024) pose sets (poses and intrs hold n_sets * n_views entries,
  * set-major) so that the timing covers varying pair counts.
- *  1. Every candidate sliced schedule (slices 4, 6, 8, 12, 16 x first slice
- *     1/16, 1/64, 1/256 x blend CTAs per SM all or 4 x blend batch 32 or 16):
+ *  1. Every candidate sliced schedule (slices 4, 5, 6, 7, 8, 12 x first
+ *     slice 1/16, 1/32, 1/64, 1/128, 1/256 x blend CTAs per SM all or 4 x
+ *     blend batch 32 or 16):
  *     two untimed launch sets then `iters` (1..100) timed ones each; the four
  *     with the lowest median host time per launch set run 2 iters + 1 more
  *     times each, interleaved, and the lowest median of those wins.

@@ -341,8 +341,8 @@ TIGAS_API tigas_status tigas_autotune(tigas_scene* scene, int n_sets, int n_view
     Scene* sc = reinterpret_cast<Scene*>(scene);
     SceneGuard sg(sc);
     const Schedule saved = current_schedule();
-    static const int kSlices[] = {4, 6, 8, 12, 16};
-    static const int kFirst[] = {16, 64, 256};
+    static const int kSlices[] = {4, 5, 6, 7, 8, 12};
+    static const int kFirst[] = {16, 32, 64, 128, 256};
     static const int kCtas[] = {0, 4};
     static const int kBatch[] = {32, 16};
     std::vector<Schedule> cands;

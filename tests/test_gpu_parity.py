@@ -754,7 +754,7 @@ def test_autotune_picks_a_candidate_and_keeps_frames(h1, cuda):
         ref = _batch(h1, tr[:2], levels, cuda)
         best, ms = tg.autotune(h1, [tr[:2], tr[4:6]], intrs, [w for w, _ in levels], [h for _, h in levels], outs,
                                iters=1)
-        assert best["n_slices"] in (4, 6, 8, 12, 16) and best["first_slice_inv"] in (16, 64, 256)
+        assert best["n_slices"] in (4, 5, 6, 7, 8, 12) and best["first_slice_inv"] in (16, 32, 64, 128, 256)
         assert best["blend_ctas_per_sm"] in (0, 4) and 0 < ms < 1e4
         assert best["blend_batch"] in (16, 32) and best["views_per_set"] in (1, 2)
         assert tg.get_schedule() == best
