@@ -386,7 +386,10 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ values, S
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpStage<kWB>& sm = stage_sm[warp];
     BlendCounts cnt;
-    const uint32_t n_long = SLICED ? sl.n_active[0] : 0u;
+    // the strips of the longest lists (from the front), of the other long lists (from the
+    // middle down), then whole tiles (from the back)
+    const uint32_t n_first = SLICED ? sl.n_active[0] : 0u;
+    const uint32_t n_long = SLICED ? n_first + sl.n_active[3] : 0u;
     const uint32_t n_items = SLICED ? n_long + sl.n_active[1] : total_tiles;
     uint32_t item = SLICED ? 0u : blockIdx.x * kWarps + warp;
     for (;;) {
@@ -396,7 +399,10 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ values, S
             item = __shfl_sync(kFull, it, 0);
         }
         if (item >= n_items) break;
-        const uint32_t raw = SLICED ? sl.active[item < n_long ? item : sl.active_cap - 1 - (item - n_long)] : item;
+        const uint32_t raw = !SLICED ? item
+                             : sl.active[item < n_first  ? item
+                                         : item < n_long ? sl.active_cap / 2 - 1 - (item - n_first)
+                                                         : sl.active_cap - 1 - (item - n_long)];
         const uint32_t g = raw & kTileMask;
         const uint32_t strip = raw >> kStripShift;   // 0: whole tile, s + 1: strip s
         int v = 0;

@@ -579,7 +579,7 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     unsigned long long* d_counters = ctx.fixed.take<unsigned long long>(4);
     uint32_t* d_flags = ctx.fixed.take<uint32_t>(2);
     uint32_t* d_visible = ctx.fixed.take<uint32_t>(kMaxViews);
-    uint32_t* d_misc = ctx.fixed.take<uint32_t>(4);       // [long tiles, short tiles, work counter]
+    uint32_t* d_misc = ctx.fixed.take<uint32_t>(4);       // [longest tiles, short tiles, work counter, long tiles]
     uint64_t* d_pix_base = ctx.fixed.take<uint64_t>(kMaxViews);
     SplatArrays sp{};
     sp.geom = ctx.fixed.take<float4>(E);
@@ -691,8 +691,8 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
         if (b == a) continue;
         uint64_t* d_P = d_total + i;
         TIGAS_TRY(mark(kStScan, true));
-        // also clears the slice's active-list counts and blend work counter (d_misc[0..2])
-        TIGAS_TRY(launch_running_sat(d_views, V, done, sat, d_misc, 3, st));
+        // also clears the slice's active-list counts and blend work counter (d_misc[0..3])
+        TIGAS_TRY(launch_running_sat(d_views, V, done, sat, d_misc, 4, st));
         // counts[b - a] = 0 makes offsets[b - a] the slice total (also in *d_P); the count
         // kernel also sums the counts per scan block, so the scan has no reduce pass
         TIGAS_TRY(launch_count_slice(rect_sorted, a, b, d_views, V, sat, counts, count_sums, compact, st));

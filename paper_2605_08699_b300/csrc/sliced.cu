@@ -295,10 +295,13 @@ k_emit_slice(const uint32_t* __restrict__ order, const uint2* __restrict__ rect_
 // lower bound of its tile searches the sample first and the keys between two
 // samples after, about 5 dependent reads instead of a search of the whole
 // array.  Tiles with pairs in this slice that are not done form the active
-// list: a tile with at least kHeavyTile pairs as four strips of 4 pixel rows
-// from the front (count n_active[0]), so that four warps share its long list
-// and the blend's dynamic scheduler starts them first; the other tiles whole
-// from the back (count n_active[1]).
+// list.  A tile with at least kHeavyTile pairs goes in as its strips of pixel
+// rows, so that several warps share its long list: strips of the tiles with
+// at least kLongestTile pairs from the front (count n_active[0]), the others
+// from the middle downward (count n_active[3]).  The remaining tiles go in
+// whole from the back (count n_active[1]).  The blend's dynamic scheduler
+// takes the three regions in that order, so the longest lists start first
+// and the short ones fill the tail.
 __device__ inline uint64_t lower_bound_u32(const uint32_t* __restrict__ keys, uint64_t lo, uint64_t hi, uint32_t t) {
     while (lo < hi) {
         const uint64_t mid = (lo + hi) >> 1;
@@ -353,26 +356,41 @@ k_ranges_active(const uint32_t* __restrict__ keys, uint64_t n_cap, const uint64_
         s_lo[threadIdx.x] = (uint32_t)lower_bound_u32(keys, a, b, t);
     }
     __syncthreads();
-    bool act = false, heavy = false;
+    bool act = false, heavy = false, longest = false;
     if (t < n_tiles) {
         const uint32_t lo = s_lo[threadIdx.x];
         const uint32_t hi = threadIdx.x < 255 ? s_lo[threadIdx.x + 1] : (uint32_t)R;
         ranges[t] = make_uint2(lo, hi);
         act = hi > lo && !tile_done(done, t);
         heavy = act && hi - lo >= kHeavyTile;
+        longest = heavy && hi - lo >= kLongestTile;
     }
     const int lane = threadIdx.x & 31;
     const uint32_t below = (1u << lane) - 1u;
-    const uint32_t mh = __ballot_sync(kFull, heavy);
+    // strips of the longest lists from the front, of the other long lists from the
+    // middle (2 n_tiles) down, so that the blend starts the longest work first
+    const uint32_t mx = __ballot_sync(kFull, longest);
+    const uint32_t mh = __ballot_sync(kFull, heavy && !longest);
     const uint32_t ml = __ballot_sync(kFull, act && !heavy);
-    if (mh) {
+    if (mx) {
         uint32_t base = 0;
-        if (lane == __ffs(mh) - 1) base = atomicAdd(&n_active[0], kStrips * (uint32_t)__popc(mh));
-        base = __shfl_sync(kFull, base, __ffs(mh) - 1);
-        if (heavy) {
-            const uint32_t at = base + kStrips * (uint32_t)__popc(mh & below);
+        if (lane == __ffs(mx) - 1) base = atomicAdd(&n_active[0], kStrips * (uint32_t)__popc(mx));
+        base = __shfl_sync(kFull, base, __ffs(mx) - 1);
+        if (longest) {
+            const uint32_t at = base + kStrips * (uint32_t)__popc(mx & below);
 #pragma unroll
             for (uint32_t s = 0; s < kStrips; ++s) active[at + s] = t | ((s + 1u) << kStripShift);
+        }
+    }
+    if (mh) {
+        uint32_t base = 0;
+        if (lane == __ffs(mh) - 1) base = atomicAdd(&n_active[3], kStrips * (uint32_t)__popc(mh));
+        base = __shfl_sync(kFull, base, __ffs(mh) - 1);
+        if (heavy && !longest) {
+            const uint32_t at = base + kStrips * (uint32_t)__popc(mh & below);
+#pragma unroll
+            for (uint32_t s = 0; s < kStrips; ++s)
+                active[2u * n_tiles - 1u - (at + s)] = t | ((s + 1u) << kStripShift);
         }
     }
     if (ml) {

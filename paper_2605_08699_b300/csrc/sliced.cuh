@@ -9,6 +9,10 @@ namespace tigas {
 #define TIGAS_HEAVY_TILE 128
 #endif
 constexpr uint32_t kHeavyTile = TIGAS_HEAVY_TILE;   // pairs of a slice that make a tile "long"
+#ifndef TIGAS_LONGEST_TILE
+#define TIGAS_LONGEST_TILE 512
+#endif
+constexpr uint32_t kLongestTile = TIGAS_LONGEST_TILE;   // long tiles whose strips the blend starts first
 // A long tile is composited as kStrips strips of 16 / kStrips pixel rows,
 // each a separate item of the active list.
 #ifndef TIGAS_STRIPS
@@ -69,12 +73,14 @@ Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64
                          cudaStream_t st);
 
 // Tile ranges of the slice's sorted keys, and the list of tiles with pairs
-// that are not done: each tile with >= kHeavyTile pairs as its kStrips strips
-// at the front of `active` (n_active[0] items), the other tiles whole at its
-// back (active[4 n_tiles - 1 - k], n_active[1] items); both counts must be
-// zero on entry (launch_running_sat clears them).  Also turns every strip
-// word's kStripSeenNow into kStripSeen (the blend before this one is over).
-// `active` holds 4 n_tiles items.
+// that are not done, in three regions of `active` (4 n_tiles items): the
+// kStrips strips of each tile with >= kLongestTile pairs from the front
+// (n_active[0] items), the strips of the other tiles with >= kHeavyTile pairs
+// from active[2 n_tiles - 1] downward (n_active[3]), and the remaining tiles
+// whole from the back (active[4 n_tiles - 1 - k], n_active[1]).  The three
+// counts must be zero on entry (launch_running_sat clears them).  Also turns
+// every strip word's kStripSeenNow into kStripSeen (the blend before this one
+// is over).
 // The key count is min(*d_n, n_cap) when d_n is given, else n_cap.
 // hi_bases: null, or 256 words whose word h is the first position of a key
 // with key >> 8 == h (the second-pass digit bases of the sort that produced
@@ -90,7 +96,7 @@ Status launch_ranges_active(const uint32_t* keys, uint64_t n_cap, const uint64_t
 // batch: list entries a warp stages at a time, 16 or 32.
 struct SliceBlendArgs {
     const uint32_t* active;
-    const uint32_t* n_active;   // [long tiles at the front, short tiles at the back]
+    const uint32_t* n_active;   // [longest strips, whole tiles, (work counter), other strips]
     uint32_t* work_counter;     // zero on entry (launch_running_sat clears it)
     float4* state;              // per pixel (C.rgb, T), T negated once the pixel stopped; valid for the
                                 // tiles whose strip word has kStripSeen (or kStripSeenNow)
