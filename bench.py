@@ -147,12 +147,15 @@ def cpu_baseline(scene, poses, width, height, budget_s: float = 15.0) -> dict:
 
 
 # DRAM bytes (read + write) of the dominant kernel per view of a launch set, from one ncu capture of
-# the same kernel source (all six slices of a 4-view 1080p launch set of the 3M-Gaussian scene,
+# the same kernel sources (all six slices of a 4-view 1080p launch set of the 3M-Gaussian scene,
 # dram__bytes_read.sum + dram__bytes_write.sum; profiles/blend_ncu_3M_1080p.md), scaled by the
-# views a launch set renders.  Reported only while the kernel's source is the captured one.
+# views a launch set renders.  Reported only while the sources are the captured ones: the blend's
+# own file and the files that build its active list (the order in which it takes tiles).
 KERNEL_TRAFFIC = {
-    "blend": {"source": "paper_2605_08699_b300/csrc/blend.cu", "sha1": "5b6227cedbdd7e06f327604d36515b0b8733f72b",
-              "bytes_per_view": 406341120 / 4},
+    "blend": {"sources": ["paper_2605_08699_b300/csrc/blend.cu", "paper_2605_08699_b300/csrc/sliced.cu",
+                          "paper_2605_08699_b300/csrc/sliced.cuh"],
+              "sha1": "259c36c44f972ba2eabe1bcfd42d88d358914ac8",
+              "bytes_per_view": 378020096 / 4},
 }
 
 
@@ -161,9 +164,12 @@ def kernel_traffic(kernel: str, views: int):
     t = KERNEL_TRAFFIC.get(kernel)
     if not t:
         return None
-    with open(os.path.join(ROOT, t["source"]), "rb") as f:
-        if hashlib.sha1(f.read()).hexdigest() != t["sha1"]:
-            return None   # the kernel changed since the counters were taken
+    h = hashlib.sha1()
+    for src in t["sources"]:
+        with open(os.path.join(ROOT, src), "rb") as f:
+            h.update(f.read())
+    if h.hexdigest() != t["sha1"]:
+        return None   # the kernel changed since the counters were taken
     return int(t["bytes_per_view"] * views)
 
 
