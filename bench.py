@@ -295,11 +295,19 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     tg.profile_stages(["blend"])
     if args.schedule:
         tg.set_schedule(*(int(x) for x in args.schedule.split(",")))
-    schedule = tg.get_schedule()
     if not args.no_autotune and not args.schedule:
-        # untimed: pick the sliced schedule for this launch-set shape (with the blend events on, as timed)
-        sets = [[trajs[v][(s * 7 + v + 150) % len(trajs[v])] for v in range(V)] for s in range(8)]
-        schedule, _ = tg.autotune(h16, sets, [K] * V, [W] * V, [H] * V, outs, iters=4)
+        # untimed: pick the sliced schedule for this launch-set shape (with the blend events on, as
+        # timed), then for the smaller launch sets the other arms form: the server's partial batches
+        # of 4 and 2 views, and single views (the plain FP32 arm renders one request at a time, on
+        # its own scene).  Each tunes its own launch-set class; the smallest goes last, since a
+        # larger one's views-per-set pass may also set a smaller class.
+        for m in sorted({V, 4, 2, 1}, reverse=True):
+            if m > V:
+                continue
+            sets = [[trajs[v][(s * 7 + v + 150) % len(trajs[v])] for v in range(m)] for s in range(8)]
+            tg.autotune(h32 if m == 1 else h16, sets, [K] * m, [W] * m, [H] * m, outs[:m], iters=4)
+    schedule = tg.get_schedule(V)
+    schedules = {str(n): tg.get_schedule(n) for n in sorted({1, 2, 4, V})}
     for s in range(args.warmup):
         step(s)
     run_async(0, max(4, args.warmup))   # both in-flight contexts capture their launch sets
@@ -539,7 +547,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     if not args.no_serving and args.trace_seconds > 0:
         trace = run_serving_trace(tg, torch, dev, args)
 
-    res = {"schedule": schedule, "rerenders": rerenders, "concurrent": concurrent, "value": value, "elapsed_ms": elapsed_ms, "frames": frames, "per_step": per_step, "stage_ms": stage_ms,
+    res = {"schedule": schedule, "schedules": schedules, "rerenders": rerenders, "concurrent": concurrent, "value": value, "elapsed_ms": elapsed_ms, "frames": frames, "per_step": per_step, "stage_ms": stage_ms,
            "timed_stage_ms": timed_stage_ms,
            "clocks": clocks, "launches": launches, "e2e": e2e, "plain_fp32": plain, "serving": serving, "trace": trace,
            "configs": configs,
@@ -973,7 +981,8 @@ def main(argv=None) -> int:
                                    "(tigas_render_batch), measured after the timed region"},
             "schedule": dict(r["schedule"], kind="depth-sliced: nearest-first geometric slices, tiles whose "
                                                   "pixels all stopped are dropped", autotuned=not (args.no_autotune or args.schedule),
-                             exact_rerenders_timed=r["rerenders"]),
+                             exact_rerenders_timed=r["rerenders"],
+                             by_views=r["schedules"]),
             "served_fp16": r["serving"], "plain_fp32": r["plain_fp32"], "serving_trace": r["trace"],
             "configs": r["configs"],
             "batching_32_mixed": r["batching"], "in_flight": r["concurrent"], "sh_degree_0": r["sh0"],

@@ -359,19 +359,26 @@ tigas_status tigas_profile_read(double* ms, uint64_t* calls, int reset);
 
 /* Scheduling (a library facility with no counterpart in the paper: the
  * paper does not describe how its rasterizer is scheduled on the GPU).
- * Parameters of the depth-sliced schedule every launch set takes.  Frames do
- * not depend on them (only the time to render them does).
- *  n_slices:          depth slices, 1..16 (default 8)
+ * Parameters of the depth-sliced schedule of a launch set.  Frames do not
+ * depend on them (only the time to render them does).
+ *  n_slices:          depth slices, 1..16
  *  first_slice_inv:   the nearest slice holds 1/first_slice_inv of the kept
  *                     entries, later ones grow geometrically to all of them,
- *                     1..4096 (default 64)
+ *                     1..4096 (not used when n_slices is 1)
  *  blend_ctas_per_sm: persistent blend CTAs per SM, 0..64; 0 or more than
  *                     fit means as many as fit (default 0)
  *  blend_batch:       list entries a blend warp stages in shared memory at a
  *                     time, 16 or 32 (0 is read as 32; default 32)
  *  views_per_set:     most views a server launch set fuses (the smaller of
  *                     this and the server's max_batch), 0..64, 0 = no cap
- *                     (default 0); tigas_render_batch* are not affected */
+ *                     (default 0); read from the schedule of the server's
+ *                     max_batch; tigas_render_batch* are not affected
+ * Launch sets are grouped by their view count into seven classes (1, 2,
+ * 3-4, 5-8, 9-16, 17-32 and 33-64 views), and each class has its own
+ * schedule: a slice costs a fixed number of launches, which weigh more in a
+ * small launch set, so small ones do better with fewer slices.  Defaults
+ * (n_slices / first_slice_inv): 3 / 16 for one view, 4 / 64 for two, 5 / 64
+ * for three or four, 6 / 64 for more. */
 typedef struct {
     int n_slices;
     int first_slice_inv;
@@ -380,31 +387,37 @@ typedef struct {
     int views_per_set;
 } tigas_schedule;
 
-/* Set / read the process-wide schedule.  Errors: INVALID (out of range).
- * Launch sets already in flight keep the schedule they started with. */
+/* tigas_set_schedule sets the schedule of every class;
+ * tigas_set_schedule_for_views that of the class of n_views (1..64) only;
+ * tigas_get_schedule reads the schedule of the class of n_views (1..64).
+ * Errors: INVALID (out of range; nothing is changed).  Launch sets already in
+ * flight keep the schedule they started with. */
 tigas_status tigas_set_schedule(const tigas_schedule* schedule);
-tigas_status tigas_get_schedule(tigas_schedule* schedule);
+tigas_status tigas_set_schedule_for_views(int n_views, const tigas_schedule* schedule);
+tigas_status tigas_get_schedule(int n_views, tigas_schedule* schedule);
 
 /* Autotuner of the batching step: renders launch sets of n_views views
  * (device RGBA8 outputs, resolutions widths/heights[n_views]), cycling through
  * n_sets (1..1024) pose sets (poses and intrs hold n_sets * n_views entries,
  * set-major) so that the timing covers varying pair counts.
- *  1. Every candidate sliced schedule (slices 4, 5, 6, 7, 8, 12 x first
- *     slice 1/16, 1/32, 1/64, 1/128, 1/256 x blend CTAs per SM all or 4 x
- *     blend batch 32 or 16):
+ *  1. Every candidate sliced schedule (slices 1, 2, 3, 4, 5, 6, 7, 8, 12 x
+ *     first slice 1/8, 1/16, 1/32, 1/64, 1/128, 1/256 (one candidate for a
+ *     single slice) x blend CTAs per SM all or 4 x blend batch 32 or 16):
  *     two untimed launch sets then `iters` (1..100) timed ones each; the four
  *     with the lowest median host time per launch set run 2 iters + 1 more
  *     times each, interleaved, and the lowest median of those wins.
  *  2. With that schedule, the views per launch set: the n_views views of a
  *     pose set rendered as launch sets of m = n_views, n_views / 2, ... views
- *     (each m that divides n_views), two untimed rounds then 2 iters + 1
- *     timed ones each; the m with the lowest median time per view wins
- *     (views_per_set = m).
- * The result becomes the process-wide schedule and is written to *best
+ *     (each m that divides n_views, launch sets of m views taking the winner),
+ *     two untimed rounds then 2 iters + 1 timed ones each; the m with the
+ *     lowest median time per view wins (views_per_set = m).
+ * The result becomes the schedule of the class of n_views (and, when m is
+ * smaller than n_views, the winner without its views_per_set that of the
+ * class of m); the other classes keep theirs.  It is written to *best
  * (best_ms: the winner's median host time per launch set of n_views views in
  * step 1).  Call it while no other render is running.  Errors: INVALID, and
- * those of tigas_render_batch (the schedule in force before the call is
- * restored). */
+ * those of tigas_render_batch (every class's schedule in force before the
+ * call is restored). */
 tigas_status tigas_autotune(tigas_scene* scene, int n_sets, int n_views, const tigas_pose* poses,
                             const tigas_intrinsics* intrs, const int* widths, const int* heights,
                             uint8_t* const* outs_rgba8, int iters, tigas_schedule* best, double* best_ms);

@@ -10,7 +10,8 @@ from .tigas import (ERR_AGAIN, ERR_CUDA, ERR_INVALID, ERR_IO, ERR_NOT_FOUND, ERR
                     kernel_launches, last_error, load_library, make_intrinsics, make_pose, profile_enable,
                     image_quality, ply_decode, ply_probe, profile_read, profile_stages, render, render_batch, render_batch_async, RenderTicket, render_ex, scene_from, scene_load,
                     scene_load_ply, set_graphs, set_schedule, sort_pairs_u64, resample_rgba8, version,
-                    DEVICE_ALLOC, PINNED_ALLOC, debug_fail_alloc, release_workspace)
+                    DEVICE_ALLOC, PINNED_ALLOC, debug_fail_alloc, release_workspace, SCHEDULE_CLASSES,
+                    get_schedules, set_schedules)
 
 __all__ = ["ERR_AGAIN", "ERR_CUDA", "ERR_INVALID", "ERR_IO", "ERR_NOT_FOUND", "ERR_OOM", "ERR_OVERFLOW", "ERR_TIMEOUT", "OK",
            "SORT_DEPTH_FIRST", "SORT_FULL64", "SORT_SLICED", "STAGES", "STORAGE_FP16", "STORAGE_FP32", "Registry",
@@ -20,4 +21,4 @@ __all__ = ["ERR_AGAIN", "ERR_CUDA", "ERR_INVALID", "ERR_IO", "ERR_NOT_FOUND", "E
            "image_quality", "ply_decode", "ply_probe", "profile_read", "profile_stages", "render", "render_batch", "render_batch_async", "RenderTicket", "render_ex", "scene_from", "scene_load",
            "scene_load_ply", "set_graphs",
            "set_schedule", "sort_pairs_u64", "resample_rgba8", "version",
-           "DEVICE_ALLOC", "PINNED_ALLOC", "debug_fail_alloc", "release_workspace"]
+           "DEVICE_ALLOC", "PINNED_ALLOC", "debug_fail_alloc", "release_workspace", "SCHEDULE_CLASSES", "get_schedules", "set_schedules"]

@@ -107,7 +107,7 @@ Status submit_render(RenderContext& ctx, Scene* scene, int V, const tigas_pose* 
     FrameRequest& req = p.req;
     req.V = V;
     req.sort_mode = sort_mode;
-    const Schedule sched = current_schedule();
+    const Schedule sched = current_schedule(V);
     req.n_slices = sched.n_slices;
     req.first_slice_inv = sched.first_slice_inv;
     req.blend_ctas_per_sm = sched.blend_ctas_per_sm;
@@ -308,22 +308,39 @@ Status check_schedule(const tigas_schedule* s) {
 }
 }  // namespace
 
-TIGAS_API tigas_status tigas_set_schedule(const tigas_schedule* s) {
-    Status c = check_schedule(s);
-    if (!c.ok()) return fail(c);
-    set_schedule(Schedule{s->n_slices, s->first_slice_inv, s->blend_ctas_per_sm, s->blend_batch ? s->blend_batch : 32,
-                          s->views_per_set});
-    return TIGAS_OK;
+namespace {
+Schedule to_schedule(const tigas_schedule* s) {
+    return Schedule{s->n_slices, s->first_slice_inv, s->blend_ctas_per_sm, s->blend_batch ? s->blend_batch : 32,
+                    s->views_per_set};
 }
-
-TIGAS_API tigas_status tigas_get_schedule(tigas_schedule* s) {
-    if (!s) return fail(TIGAS_ERR_INVALID, "null schedule");
-    const Schedule c = current_schedule();
+void from_schedule(const Schedule& c, tigas_schedule* s) {
     s->n_slices = c.n_slices;
     s->first_slice_inv = c.first_slice_inv;
     s->blend_ctas_per_sm = c.blend_ctas_per_sm;
     s->blend_batch = c.blend_batch;
     s->views_per_set = c.views_per_set;
+}
+}  // namespace
+
+TIGAS_API tigas_status tigas_set_schedule(const tigas_schedule* s) {
+    Status c = check_schedule(s);
+    if (!c.ok()) return fail(c);
+    set_schedule(to_schedule(s));
+    return TIGAS_OK;
+}
+
+TIGAS_API tigas_status tigas_set_schedule_for_views(int n_views, const tigas_schedule* s) {
+    if (n_views < 1 || n_views > kMaxViews) return fail(TIGAS_ERR_INVALID, "n_views out of 1..64");
+    Status c = check_schedule(s);
+    if (!c.ok()) return fail(c);
+    set_schedule_for(n_views, to_schedule(s));
+    return TIGAS_OK;
+}
+
+TIGAS_API tigas_status tigas_get_schedule(int n_views, tigas_schedule* s) {
+    if (!s) return fail(TIGAS_ERR_INVALID, "null schedule");
+    if (n_views < 1 || n_views > kMaxViews) return fail(TIGAS_ERR_INVALID, "n_views out of 1..64");
+    from_schedule(current_schedule(n_views), s);
     return TIGAS_OK;
 }
 
@@ -340,16 +357,21 @@ TIGAS_API tigas_status tigas_autotune(tigas_scene* scene, int n_sets, int n_view
             return fail(TIGAS_ERR_INVALID, "autotune outputs must be device buffers");
     Scene* sc = reinterpret_cast<Scene*>(scene);
     SceneGuard sg(sc);
-    const Schedule saved = current_schedule();
-    static const int kSlices[] = {4, 5, 6, 7, 8, 12};
-    static const int kFirst[] = {16, 32, 64, 128, 256};
+    // every class's schedule, restored on failure (the call sets only the classes it times)
+    Schedule saved[kScheduleClasses];
+    for (int c = 0; c < kScheduleClasses; ++c) saved[c] = current_schedule(1 << c);
+    const Schedule own = current_schedule(n_views);
+    static const int kSlices[] = {1, 2, 3, 4, 5, 6, 7, 8, 12};
+    static const int kFirst[] = {8, 16, 32, 64, 128, 256};
     static const int kCtas[] = {0, 4};
     static const int kBatch[] = {32, 16};
     std::vector<Schedule> cands;
     for (int ns : kSlices)
-        for (int fi : kFirst)
+        for (int fi : kFirst) {
+            if (ns == 1 && fi != kFirst[0]) continue;   // one slice holds every entry whatever the first fraction
             for (int ct : kCtas)
-                for (int wb : kBatch) cands.push_back(Schedule{ns, fi, ct, wb, saved.views_per_set});
+                for (int wb : kBatch) cands.push_back(Schedule{ns, fi, ct, wb, own.views_per_set});
+        }
     std::vector<std::vector<double>> times(cands.size());
     int next_set = 0;
     // the next pose set's views [v0, v0 + m) as one launch set; returns host ms
@@ -364,7 +386,7 @@ TIGAS_API tigas_status tigas_autotune(tigas_scene* scene, int n_sets, int n_view
     // one launch set of all views (the next pose set) under schedule c; untimed ones
     // warm up (a shape's first launch set runs directly, the second is captured)
     auto run = [&](size_t c, bool timed) -> Status {
-        set_schedule(cands[c]);
+        set_schedule_for(n_views, cands[c]);
         double ms = 0.0;
         Status s = render_part(0, n_views, &ms);
         next_set = (next_set + 1) % n_sets;
@@ -375,8 +397,11 @@ TIGAS_API tigas_status tigas_autotune(tigas_scene* scene, int n_sets, int n_view
         std::sort(t.begin(), t.end());
         return t.empty() ? 1e300 : t[t.size() / 2];
     };
+    auto restore = [&]() {
+        for (int c = 0; c < kScheduleClasses; ++c) set_schedule_for(1 << c, saved[c]);
+    };
     auto give_up = [&](const Status& s) {
-        set_schedule(saved);
+        restore();
         return fail(s);
     };
     // first pass: every candidate, two untimed then `iters` timed launch sets
@@ -396,7 +421,7 @@ TIGAS_API tigas_status tigas_autotune(tigas_scene* scene, int n_sets, int n_view
             Status s = run(c, true);
             if (!s.ok()) return give_up(s);
         }
-    Schedule win = saved;
+    Schedule win = own;
     double win_ms = 1e300;
     for (size_t c : order) {
         const double m = median(times[c]);
@@ -406,12 +431,13 @@ TIGAS_API tigas_status tigas_autotune(tigas_scene* scene, int n_sets, int n_view
         }
     }
     // views per launch set under the winning schedule: the pose set's views as
-    // n_views / m launch sets of m, time per view
-    set_schedule(win);
+    // n_views / m launch sets of m (each taking the winner too), time per view
     int win_m = n_views;
     double win_per_view = 1e300;
     for (int m = n_views; m >= 1; m /= 2) {
         if (n_views % m != 0) continue;
+        restore();
+        set_schedule_for(m, win);
         std::vector<double> per_view;
         for (int round = 0; round < 2 * iters + 3; ++round) {
             double total = 0.0;
@@ -431,15 +457,17 @@ TIGAS_API tigas_status tigas_autotune(tigas_scene* scene, int n_sets, int n_view
         }
         if (m == 1) break;
     }
-    win.views_per_set = win_m;
-    set_schedule(win);
-    if (best) {
-        best->n_slices = win.n_slices;
-        best->first_slice_inv = win.first_slice_inv;
-        best->blend_ctas_per_sm = win.blend_ctas_per_sm;
-        best->blend_batch = win.blend_batch;
-        best->views_per_set = win.views_per_set;
+    // the class of n_views takes the winner and the views per launch set; a smaller
+    // winning launch set size takes the winner too (it was timed with it)
+    restore();
+    if (win_m < n_views) {
+        Schedule w = win;
+        w.views_per_set = current_schedule(win_m).views_per_set;
+        set_schedule_for(win_m, w);
     }
+    win.views_per_set = win_m;
+    set_schedule_for(n_views, win);
+    if (best) from_schedule(win, best);
     if (best_ms) *best_ms = win_ms;
     return TIGAS_OK;
 }

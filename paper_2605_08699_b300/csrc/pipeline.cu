@@ -14,17 +14,33 @@ std::atomic<bool> g_use_graphs{true};
 
 namespace {
 std::mutex g_sched_mu;
-Schedule g_sched;
+// Defaults, the autotuner's picks for 3M Gaussians at 1080p: one view in 3
+// slices (the first holding 1/16 of the entries), two in 4, three or four in
+// 5, more in 6 (the first holding 1/64).
+Schedule g_sched[kScheduleClasses] = {Schedule{3, 16, 0, 32, 0}, Schedule{4, 64, 0, 32, 0}, Schedule{5, 64, 0, 32, 0},
+                                      Schedule{6, 64, 0, 32, 0},  Schedule{6, 64, 0, 32, 0}, Schedule{6, 64, 0, 32, 0},
+                                      Schedule{6, 64, 0, 32, 0}};
 }  // namespace
 
-Schedule current_schedule() {
+int schedule_class(int n_views) {
+    int c = 0;
+    while (c + 1 < kScheduleClasses && (1 << c) < n_views) ++c;
+    return c;
+}
+
+Schedule current_schedule(int n_views) {
     std::lock_guard<std::mutex> lk(g_sched_mu);
-    return g_sched;
+    return g_sched[schedule_class(n_views)];
 }
 
 void set_schedule(const Schedule& s) {
     std::lock_guard<std::mutex> lk(g_sched_mu);
-    g_sched = s;
+    for (Schedule& c : g_sched) c = s;
+}
+
+void set_schedule_for(int n_views, const Schedule& s) {
+    std::lock_guard<std::mutex> lk(g_sched_mu);
+    g_sched[schedule_class(n_views)] = s;
 }
 
 namespace {

@@ -196,7 +196,7 @@ Status render_sliced_graph(Scene* scene, FrameRequest& req, RenderContext& ctx, 
                            bool* rendered);
 extern std::atomic<bool> g_use_graphs;
 extern std::atomic<uint64_t> g_exact_rerenders;   // fixed-capacity launch sets rendered again exactly
-// Schedule parameters every launch set takes (tigas_set_schedule / tigas_autotune).
+// Schedule parameters of a launch set (tigas_set_schedule / tigas_autotune).
 struct Schedule {
     int n_slices = 8;
     int first_slice_inv = 64;
@@ -204,8 +204,14 @@ struct Schedule {
     int blend_batch = 32;
     int views_per_set = 0;   // the server's launch sets hold at most this many views (0: no cap)
 };
-Schedule current_schedule();
-void set_schedule(const Schedule& s);
+// Launch sets are grouped by view count into the classes 1, 2, 3-4, 5-8,
+// 9-16, 17-32 and 33-64 views, each with its own schedule: fixed per-slice
+// costs weigh more in a small launch set, so fewer slices suit it.
+constexpr int kScheduleClasses = 7;
+int schedule_class(int n_views);
+Schedule current_schedule(int n_views);
+void set_schedule(const Schedule& s);                  // every class
+void set_schedule_for(int n_views, const Schedule& s);   // the class of n_views
 void drop_graphs(RenderContext& ctx);
 // Idle contexts drop their graphs, the shapes they have seen and the learned
 // slice capacity.

@@ -103,8 +103,8 @@ struct Server {
                 continue;
             }
             // a launch set holds at most max_batch views, and no more than the tuned
-            // views per launch set of the current schedule
-            const int vps = current_schedule().views_per_set;
+            // views per launch set of the schedule of max_batch-view launch sets
+            const int vps = current_schedule(cfg.max_batch).views_per_set;
             const int cap = vps > 0 && vps < cfg.max_batch ? vps : cfg.max_batch;
             if (cfg.batch_window_us > 0 && (int)queue.size() < cap && !stop) {
                 // give a partial batch a short window to fill

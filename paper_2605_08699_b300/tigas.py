@@ -28,7 +28,7 @@ EXPORTS = ["tigas_scene_load", "tigas_scene_free", "tigas_scene_bytes", "tigas_r
            "tigas_version", "tigas_kernel_launches", "tigas_profile_enable", "tigas_profile_read",
            "tigas_sort_pairs_u64_noalloc", "tigas_sort_noalloc_check", "tigas_debug_sort_noalloc_wait_timeout",
            "tigas_render_batch_ex", "tigas_set_graphs", "tigas_debug_sort_wait_timeout",
-           "tigas_set_schedule", "tigas_get_schedule", "tigas_autotune", "tigas_exact_rerenders",
+           "tigas_set_schedule", "tigas_set_schedule_for_views", "tigas_get_schedule", "tigas_autotune", "tigas_exact_rerenders",
            "tigas_jpeg_encode", "tigas_ply_probe", "tigas_ply_decode", "tigas_scene_load_ply",
            "tigas_registry_open", "tigas_registry_scan", "tigas_registry_count", "tigas_registry_info",
            "tigas_registry_acquire", "tigas_registry_release", "tigas_registry_evict_idle",
@@ -155,7 +155,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "tigas_debug_fail_alloc": (st, [i, ctypes.c_int64, ctypes.c_int64]),
         "tigas_release_workspace": (st, []),
         "tigas_set_schedule": (st, [ctypes.POINTER(Schedule)]),
-        "tigas_get_schedule": (st, [ctypes.POINTER(Schedule)]),
+        "tigas_set_schedule_for_views": (st, [i, ctypes.POINTER(Schedule)]),
+        "tigas_get_schedule": (st, [i, ctypes.POINTER(Schedule)]),
         "tigas_exact_rerenders": (ctypes.c_uint64, []),
         "tigas_jpeg_encode": (st, [P, i, i, i, i, P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), P]),
         "tigas_autotune": (st, [P, i, i, ctypes.POINTER(Pose), ctypes.POINTER(Intrinsics), ctypes.POINTER(ctypes.c_int),
@@ -592,17 +593,36 @@ def render_batch_async(scene: SceneHandle, poses: Sequence, intrs: Sequence, wid
     return RenderTicket(t.value, list(outs))
 
 
+# The largest view count of each launch-set class with its own schedule (1, 2, 3-4, 5-8, ...).
+SCHEDULE_CLASSES = (1, 2, 4, 8, 16, 32, 64)
+
+
 def set_schedule(n_slices: int = 8, first_slice_inv: int = 64, blend_ctas_per_sm: int = 0, blend_batch: int = 32,
-                 views_per_set: int = 0) -> None:
-    """tigas_set_schedule: the depth-sliced schedule every launch set takes."""
-    _check(load_library().tigas_set_schedule(ctypes.byref(Schedule(n_slices, first_slice_inv, blend_ctas_per_sm,
-                                                                   blend_batch, views_per_set))))
+                 views_per_set: int = 0, n_views: int = 0) -> None:
+    """tigas_set_schedule (n_views 0: every launch-set class) or
+    tigas_set_schedule_for_views (the class of n_views only)."""
+    s = Schedule(n_slices, first_slice_inv, blend_ctas_per_sm, blend_batch, views_per_set)
+    lib = load_library()
+    _check(lib.tigas_set_schedule(ctypes.byref(s)) if n_views == 0 else
+           lib.tigas_set_schedule_for_views(n_views, ctypes.byref(s)))
 
 
-def get_schedule() -> dict:
+def get_schedule(n_views: int = 1) -> dict:
+    """tigas_get_schedule: the schedule of launch sets of n_views views."""
     s = Schedule()
-    _check(load_library().tigas_get_schedule(ctypes.byref(s)))
+    _check(load_library().tigas_get_schedule(n_views, ctypes.byref(s)))
     return s.as_dict()
+
+
+def get_schedules() -> dict:
+    """Every class's schedule, keyed by its largest view count (for set_schedules)."""
+    return {n: get_schedule(n) for n in SCHEDULE_CLASSES}
+
+
+def set_schedules(schedules: dict) -> None:
+    """Sets each class's schedule from get_schedules()'s result."""
+    for n, s in schedules.items():
+        set_schedule(**s, n_views=n)
 
 
 def jpeg_encode(rgba, quality: int, restart_mcus: int = 2, out=None, stream=None) -> bytes | int:

@@ -92,21 +92,58 @@ def test_pose_validation_messages(lib):
 
 def test_schedule_set_get_and_range_checks():
     tg.load_library()
-    before = tg.get_schedule()
+    before = tg.get_schedules()
     try:
         tg.set_schedule(12, 256, 3, 16, 4)
-        assert tg.get_schedule() == {"n_slices": 12, "first_slice_inv": 256, "blend_ctas_per_sm": 3, "blend_batch": 16,
-                                     "views_per_set": 4}
+        for n in range(1, 65):   # every class
+            assert tg.get_schedule(n) == {"n_slices": 12, "first_slice_inv": 256, "blend_ctas_per_sm": 3,
+                                          "blend_batch": 16, "views_per_set": 4}
         tg.set_schedule(12, 256, 3, 0, 0)   # blend batch 0 is read as 32
-        assert tg.get_schedule()["blend_batch"] == 32
+        assert tg.get_schedule(8)["blend_batch"] == 32
         for bad in [(0, 64, 0), (17, 64, 0), (8, 0, 0), (8, 5000, 0), (8, 64, -1), (8, 64, 65), (8, 64, 0, 8),
                     (8, 64, 0, 64), (8, 64, 0, 32, -1), (8, 64, 0, 32, 65)]:
-            with pytest.raises(tg.TigasError) as e:
-                tg.set_schedule(*bad)
-            assert e.value.status == tg.ERR_INVALID
-        assert tg.get_schedule()["n_slices"] == 12   # a rejected call changes nothing
+            for n_views in (0, 5):
+                with pytest.raises(tg.TigasError) as e:
+                    tg.set_schedule(*bad, n_views=n_views)
+                assert e.value.status == tg.ERR_INVALID
+        assert tg.get_schedule(5)["n_slices"] == 12   # a rejected call changes nothing
+        for n in (0, 65):
+            with pytest.raises(tg.TigasError):
+                tg.get_schedule(n)
+            if n:
+                with pytest.raises(tg.TigasError):
+                    tg.set_schedule(4, 16, n_views=n)
     finally:
-        tg.set_schedule(**before)
+        tg.set_schedules(before)
+
+
+def test_schedule_classes_are_1_2_3to4_5to8_and_so_on():
+    tg.load_library()
+    before = tg.get_schedules()
+    try:
+        tg.set_schedule(6, 64)
+        tg.set_schedule(2, 8, n_views=3)   # the class of 3 and 4 views only
+        got = {n: tg.get_schedule(n)["n_slices"] for n in range(1, 65)}
+        assert got == {n: 2 if n in (3, 4) else 6 for n in range(1, 65)}
+        tg.set_schedule(5, 32, n_views=40)   # 33..64
+        assert [tg.get_schedule(n)["n_slices"] for n in (32, 33, 64)] == [6, 5, 5]
+        tg.set_schedule(1, 1, n_views=1)
+        assert [tg.get_schedule(n)["n_slices"] for n in (1, 2)] == [1, 6]
+    finally:
+        tg.set_schedules(before)
+
+
+def test_default_schedules_take_fewer_slices_for_smaller_launch_sets():
+    # a fresh process has the defaults
+    import subprocess
+    import sys
+    code = ("import paper_2605_08699_b300 as tg; tg.load_library(); "
+            "print(tg.get_schedule(1)['n_slices'], tg.get_schedule(1)['first_slice_inv'], "
+            "*[tg.get_schedule(n)['n_slices'] for n in (2, 3, 4, 5, 8, 64)])")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, check=True,
+                         cwd=root).stdout.split()
+    assert [int(x) for x in out] == [3, 16, 4, 5, 5, 6, 6, 6]
 
 
 def test_profile_stage_mask_checks(lib):

@@ -704,26 +704,33 @@ def test_sort_lookback_wait_times_out_and_device_stays_usable(h1, s1):
 def test_frames_do_not_depend_on_the_schedule(h1, cuda):
     levels = [(480, 270), (97, 61)]
     tr = synth.trajectory(17, 20)
-    base = tg.get_schedule()
+    base = tg.get_schedules()
     try:
         ref = _batch(h1, tr[3:5], levels, cuda)
-        for sch in [(1, 1, 0), (4, 16, 0), (16, 256, 1), (12, 4096, 4), (6, 64, 0, 16), (8, 64, 3, 16)]:
+        ref1 = tg.render(h1, tr[6], synth.default_intrinsics(480, 270), 480, 270)
+        for sch in [(1, 1, 0), (2, 8, 0), (4, 16, 0), (16, 256, 1), (12, 4096, 4), (6, 64, 0, 16), (8, 64, 3, 16)]:
             tg.set_schedule(*sch)
             for _ in range(3):   # direct, exact + capture, replay
                 got = _batch(h1, tr[3:5], levels, cuda)
                 for a, b in zip(ref, got):
                     assert np.array_equal(a, b), sch
+        # one-view launch sets take their own class's schedule
+        for sch in [(1, 1, 0), (3, 16, 0), (5, 8, 4, 16)]:
+            tg.set_schedule(*sch, n_views=1)
+            for _ in range(3):
+                assert np.array_equal(tg.render(h1, tr[6], synth.default_intrinsics(480, 270), 480, 270), ref1), sch
     finally:
-        tg.set_schedule(**base)
+        tg.set_schedules(base)
 
 
 def test_server_launch_sets_respect_views_per_set(cuda, h1):
-    # the schedule's views per launch set caps the server's batches below max_batch
+    # the views per launch set of the schedule of max_batch-view launch sets caps the
+    # server's batches below max_batch
     K = synth.default_intrinsics(160, 120)
     tr = synth.trajectory(31, 8)
-    base = tg.get_schedule()
+    base = tg.get_schedules()
     try:
-        tg.set_schedule(**{**base, "views_per_set": 2})
+        tg.set_schedule(**{**base[8], "views_per_set": 2}, n_views=8)
         with tg.Server(max_batch=8, max_inflight=1, batch_window_us=300_000) as srv:
             bufs = {}
             for i, p in enumerate(tr):
@@ -741,7 +748,7 @@ def test_server_launch_sets_respect_views_per_set(cuda, h1):
             b, p = bufs[c.ticket]
             assert np.array_equal(b.cpu().numpy(), tg.render(h1, p, K, 160, 120))
     finally:
-        tg.set_schedule(**base)
+        tg.set_schedules(base)
 
 
 def test_autotune_picks_a_candidate_and_keeps_frames(h1, cuda):
@@ -749,20 +756,31 @@ def test_autotune_picks_a_candidate_and_keeps_frames(h1, cuda):
     tr = synth.trajectory(19, 10)
     intrs = [synth.default_intrinsics(w, h) for w, h in levels]
     outs = [torch.empty((h, w, 4), dtype=torch.uint8, device=cuda) for w, h in levels]
-    base = tg.get_schedule()
+    base = tg.get_schedules()
     try:
+        marker = {"n_slices": 13, "first_slice_inv": 7, "blend_ctas_per_sm": 2, "blend_batch": 16, "views_per_set": 0}
+        tg.set_schedule(**marker)
         ref = _batch(h1, tr[:2], levels, cuda)
         best, ms = tg.autotune(h1, [tr[:2], tr[4:6]], intrs, [w for w, _ in levels], [h for _, h in levels], outs,
                                iters=1)
-        assert best["n_slices"] in (4, 5, 6, 7, 8, 12) and best["first_slice_inv"] in (16, 32, 64, 128, 256)
+        assert best["n_slices"] in (1, 2, 3, 4, 5, 6, 7, 8, 12)
+        assert best["first_slice_inv"] in (8, 16, 32, 64, 128, 256)
         assert best["blend_ctas_per_sm"] in (0, 4) and 0 < ms < 1e4
         assert best["blend_batch"] in (16, 32) and best["views_per_set"] in (1, 2)
-        assert tg.get_schedule() == best
+        # the class of two views takes the winner; a one-view winning launch set size
+        # gives the one-view class the winner too; the other classes keep theirs
+        assert tg.get_schedule(2) == best
+        one = tg.get_schedule(1)
+        if best["views_per_set"] == 1:
+            assert one == {**best, "views_per_set": 0}
+        else:
+            assert one == marker
+        assert all(tg.get_schedule(n) == marker for n in (3, 4, 8, 64))
         got = _batch(h1, tr[:2], levels, cuda)
         for a, b in zip(ref, got):
             assert np.array_equal(a, b)
     finally:
-        tg.set_schedule(**base)
+        tg.set_schedules(base)
 
 
 def test_depth_sort_skips_constant_high_digit(h1, cuda):
