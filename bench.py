@@ -173,6 +173,26 @@ def kernel_traffic(kernel: str, views: int):
     return int(t["bytes_per_view"] * views)
 
 
+# What bounds each stage below its roofline, from ncu captures of the same kernels
+# (profiles/binning_ncu_3M_1080p.md, profiles/depth_sort_scatter_ncu_3M_1080p.md,
+# profiles/preprocess_ncu_3M_1080p.md, profiles/blend_ncu_3M_1080p.md); copied into the stage entries of the bench line.
+STAGE_LIMITS = {
+    "preprocess": "instructions: 592 thread instructions per (Gaussian, view), 73 % issue active, DRAM 46 % "
+                  "of peak; traffic equals the algorithmic bytes",
+    "depth_sort": "instructions per key and load latency: 146-157 thread instructions per key per pass, "
+                  "41-50 % issue active, long_scoreboard first, DRAM 29-36 % of peak",
+    "scan": "latency: per slice a one-CTA-per-view running-tile table (8 us, barrier first), a count "
+            "of 46-1655 CTAs (long_scoreboard first, 12-45 % warps active) and a one-CTA block-sum scan",
+    "emit": "instructions per pair (46-58 % issue active, not_selected first); the pairs stay in L2 "
+            "(slice 0: 0.2 MB of DRAM writes for 40 MB of pairs)",
+    "pair_sort": "latency and L2: the pair lists live in L2 (DRAM reads are the keys' first touch), later "
+                 "slices' scatter passes run 88-255 CTAs at 18-32 % warps active, plus a one-CTA digit-base kernel",
+    "ranges": "latency: a sampled search per tile, long_scoreboard 12-18 per issue, 9-11 us per slice",
+    "blend": "issue-bound in the first slice (79 % issue active), latency-bound in later ones "
+             "(long_scoreboard first); not DRAM-bound (6-11 % of peak)",
+}
+
+
 def roofline(stage_ms: dict, per_step: dict, peaks: dict, clocks: dict, steps: int,
              timed_stage_ms: dict | None = None) -> tuple[dict, dict]:
     """Achieved rate of every stage (stage_ms: a pass with every stage timed) and
@@ -218,6 +238,9 @@ def roofline(stage_ms: dict, per_step: dict, peaks: dict, clocks: dict, steps: i
             ach = b / (ms * 1e-3) / 1e9
             stages[name] = {"ms": ms, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                             "frac": ach / hbm, "work": b}
+    for name, lim in STAGE_LIMITS.items():
+        if name in stages:
+            stages[name]["limit"] = lim
     dom = max(stages, key=lambda k: stages[k]["ms"])
     d = dict(stages[dom])
     traffic = kernel_traffic(dom, per_step.get("views", 0))
