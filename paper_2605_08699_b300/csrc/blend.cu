@@ -15,9 +15,11 @@
 // the kept entries each pixel computes alpha = min(0.99, o exp(power)) as
 // 2^(power log2 e + log2 o) (two FMAs per pixel after the row-independent part),
 // skips alpha < 1/255 before any exponential, and
-// stops before the entry that would bring T below 1e-4.  A warp vote skips the
-// blend step when no pixel of the tile gains from an entry, and the warp
-// leaves the list once all 256 pixels have stopped.
+// stops before the entry that would bring T below 1e-4.  The blend step takes
+// a thread's pixel rows in pairs, one branch per pair that some pixel of the
+// warp takes (a row that does not take the entry blends with alpha 0, which
+// leaves it unchanged bit for bit), and the warp leaves the list once all its
+// pixels have stopped.
 #include "kernels.cuh"
 #include "sliced.cuh"
 
@@ -173,6 +175,7 @@ __device__ __forceinline__ bool blend_rows(WarpStage<kWB>& sm, int lane, const u
                                            const ViewParams& vp, uint32_t g, uint32_t local, int row0,
                                            uint64_t sbase, uint32_t n_entries, float bg_r, float bg_g, float bg_b,
                                            const SliceBlendArgs& sl, BlendCounts& cnt) {
+    static_assert(NP % 2 == 0, "the blend step takes pixel rows in pairs");
     const int W = vp.W, H = vp.H, TX = vp.TX;
     const int ty = (int)(local / TX), tx = (int)(local % TX);
     const uint32_t col = lane & 15, row = (uint32_t)row0 + (lane >> 4);   // rows row + 2k of the tile
@@ -289,7 +292,6 @@ __device__ __forceinline__ bool blend_rows(WarpStage<kWB>& sm, int lane, const u
             const float dyb = gm.y - py0f;
             float e[NP];
             bool con[NP];
-            bool anyc = false;
             if constexpr (TIGAS_BLEND_F32X2 != 0 && NP % 2 == 0) {
                 // rows k = 2j, 2j + 1 in one packed lane pair: dy = dyb - 2k, e = dy (c' dy + b' dx) + p0
                 const unsigned long long dyb2 = f2_pack(dyb, dyb), ax2 = f2_pack(ap.x, ap.x);
@@ -301,36 +303,60 @@ __device__ __forceinline__ bool blend_rows(WarpStage<kWB>& sm, int lane, const u
                     f2_unpack(e2, e[2 * j], e[2 * j + 1]);
                 }
 #pragma unroll
-                for (int k = 0; k < NP; ++k) {
+                for (int k = 0; k < NP; ++k)
                     con[k] = e[k] >= thr[k];   // thr: the alpha cut-off, +inf once the pixel stopped
-                    anyc |= con[k];
-                }
             } else {
 #pragma unroll
                 for (int k = 0; k < NP; ++k) {
                     const float dy = dyb - 2.0f * (float)k;
                     e[k] = fmaf(dy, fmaf(ap.x, dy, bdx), p0);
                     con[k] = e[k] >= thr[k];   // thr: the alpha cut-off, +inf once the pixel stopped
-                    anyc |= con[k];
                 }
             }
-            if (__any_sync(kFull, anyc)) {
+            {
+                // The blend step, two pixel rows per branch.  A row that does not take
+                // the entry gets alpha = 0, and the step leaves it unchanged bit for bit:
+                // T - T 0 = T (one fused rounding) and C + c (0 T) = C.  Only a pair in
+                // which some pixel stops takes the per-pixel path.  (Fewer, less
+                // divergent branches than one per row, and no warp vote before them.)
                 const float cbl = sm.blue[buf][j];
 #pragma unroll
-                for (int k = 0; k < NP; ++k) {
-                    if (con[k]) {
-                        const float alpha = fminf(0.99f, ex2_approx(e[k]));
-                        const float tT = fmaf(-T[k], alpha, T[k]);
-                        if (tT < 1e-4f) {
-                            live &= ~(1u << k);
-                            thr[k] = __int_as_float(0x7f800000);
+                for (int q = 0; q < NP / 2; ++q) {
+                    const int k0 = 2 * q, k1 = 2 * q + 1;
+                    if (con[k0] || con[k1]) {
+                        const float a0 = con[k0] ? fminf(0.99f, ex2_approx(e[k0])) : 0.0f;
+                        const float a1 = con[k1] ? fminf(0.99f, ex2_approx(e[k1])) : 0.0f;
+                        const float t0 = fmaf(-T[k0], a0, T[k0]);
+                        const float t1 = fmaf(-T[k1], a1, T[k1]);
+                        if (t0 < 1e-4f || t1 < 1e-4f) {
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const int k = k0 + h;
+                                const float a = h ? a1 : a0, tT = h ? t1 : t0;
+                                if (!con[k]) continue;
+                                if (tT < 1e-4f) {   // stops before this entry
+                                    live &= ~(1u << k);
+                                    thr[k] = __int_as_float(0x7f800000);
+                                } else {
+                                    if (COUNT) ++cnt.blend;
+                                    const float w = a * T[k];
+                                    cr[k] = fmaf(ap.z, w, cr[k]);
+                                    cg[k] = fmaf(ap.w, w, cg[k]);
+                                    cb[k] = fmaf(cbl, w, cb[k]);
+                                    T[k] = tT;
+                                }
+                            }
                         } else {
-                            if (COUNT) ++cnt.blend;
-                            const float w = alpha * T[k];
-                            cr[k] = fmaf(ap.z, w, cr[k]);
-                            cg[k] = fmaf(ap.w, w, cg[k]);
-                            cb[k] = fmaf(cbl, w, cb[k]);
-                            T[k] = tT;
+                            if (COUNT) cnt.blend += (uint64_t)con[k0] + (uint64_t)con[k1];
+                            const float w0 = a0 * T[k0], w1 = a1 * T[k1];
+                            cr[k0] = fmaf(ap.z, w0, cr[k0]);
+                            cg[k0] = fmaf(ap.w, w0, cg[k0]);
+                            cb[k0] = fmaf(cbl, w0, cb[k0]);
+                            cr[k1] = fmaf(ap.z, w1, cr[k1]);
+                            cg[k1] = fmaf(ap.w, w1, cg[k1]);
+                            cb[k1] = fmaf(cbl, w1, cb[k1]);
+                            T[k0] = t0;
+                            T[k1] = t1;
                         }
                     }
                 }
