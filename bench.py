@@ -154,8 +154,8 @@ def cpu_baseline(scene, poses, width, height, budget_s: float = 15.0) -> dict:
 KERNEL_TRAFFIC = {
     "blend": {"sources": ["paper_2605_08699_b300/csrc/blend.cu", "paper_2605_08699_b300/csrc/sliced.cu",
                           "paper_2605_08699_b300/csrc/sliced.cuh"],
-              "sha1": "259c36c44f972ba2eabe1bcfd42d88d358914ac8",
-              "bytes_per_view": 378020096 / 4},
+              "sha1": "b368a6d1ff261a1edb140c56681ea613af6c79ab",
+              "bytes_per_view": 381664256 / 4},
 }
 
 
