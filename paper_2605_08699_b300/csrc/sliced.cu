@@ -131,12 +131,11 @@ k_running_sat(const ViewParams* __restrict__ views_g, const uint32_t* __restrict
 // k in [a, b), and counts[b - a] = 0; sums[j] = the sum of counts of block j
 // (kScanBlock consecutive counts: the scan's tile), so the scan needs no
 // reduce pass.  One CTA per block, 16 counts per thread.
-constexpr int kCountThreads = 256;
-constexpr int kCountItems = (int)kScanBlock / kCountThreads;
-template <bool COMPACT>
+template <bool COMPACT, int kCountThreads>
 __global__ void __launch_bounds__(kCountThreads)
 k_count_slice(const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b, const ViewParams* __restrict__ views_g,
               int V, const uint32_t* __restrict__ sat, uint32_t* __restrict__ counts, uint32_t* __restrict__ sums) {
+    constexpr int kCountItems = (int)kScanBlock / kCountThreads;
     __shared__ uint32_t s_sb[kMaxViews], s_w1[kMaxViews], ws[kCountThreads / 32];
     for (int k = threadIdx.x; k < V; k += kCountThreads) {
         s_sb[k] = views_g[k].sat_base;
@@ -205,7 +204,8 @@ __device__ inline void emit_warp_entries(uint32_t m, uint2 r, uint32_t e, uint32
         const uint32_t xlo = tr.xlo, xhi = tr.xhi, ylo = tr.ylo, yhi = tr.yhi, v = tr.v;
         const uint32_t w = xhi - xlo, area = w * (yhi - ylo);
         const uint32_t tx = s_tx[v], t0 = s_tb[v] + ylo * tx + xlo;
-        const float rinv = 1.0f / (float)w;
+        // an approximate reciprocal: the row estimate below is corrected by one either way
+        const float rinv = __fdividef(1.0f, (float)w);
         uint32_t written = 0;
         for (uint32_t f0 = 0; f0 < area && written < jc; f0 += 32) {
             const uint32_t f = f0 + (uint32_t)lane;
@@ -434,10 +434,16 @@ Status launch_count_slice(const uint2* rect_sorted, uint64_t a, uint64_t b, cons
                           const uint32_t* sat, uint32_t* counts, uint32_t* sums, bool compact, cudaStream_t st) {
     if (b <= a) return {};
     const unsigned grid = (unsigned)((b - a + 1 + kScanBlock - 1) / kScanBlock);
-    if (compact)
-        k_count_slice<true><<<grid, kCountThreads, 0, st>>>(rect_sorted, a, b, views, V, sat, counts, sums);
-    else
-        k_count_slice<false><<<grid, kCountThreads, 0, st>>>(rect_sorted, a, b, views, V, sat, counts, sums);
+    // a slice of few blocks (less than two per SM) takes 1024 threads per block,
+    // 4 rectangles each, so that its few CTAs hold more warps
+    const bool big = grid < 2u * (unsigned)kSmCount;
+    if (compact) {
+        if (big) k_count_slice<true, 1024><<<grid, 1024, 0, st>>>(rect_sorted, a, b, views, V, sat, counts, sums);
+        else k_count_slice<true, 256><<<grid, 256, 0, st>>>(rect_sorted, a, b, views, V, sat, counts, sums);
+    } else {
+        if (big) k_count_slice<false, 1024><<<grid, 1024, 0, st>>>(rect_sorted, a, b, views, V, sat, counts, sums);
+        else k_count_slice<false, 256><<<grid, 256, 0, st>>>(rect_sorted, a, b, views, V, sat, counts, sums);
+    }
     TIGAS_LAUNCHED();
     return {};
 }
