@@ -179,57 +179,74 @@ k_count_slice(const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b, con
     }
 }
 
-// Pairs (tile, entry) of the slice for tiles not done, in depth order.  The
-// warp writes one entry's pairs at a time: lanes take 32 consecutive tiles of
-// the rectangle (row-major), and those not done are written to consecutive
-// positions (a ballot ranks them), so stores are coalesced and a large
-// rectangle costs area / 32 steps instead of area steps of one lane.
-// m: lanes whose entry has pairs; r, e, pos, c: each lane's rectangle, entry,
-// first pair position and pair count.
+// Pairs (tile, entry) of the slice for tiles not done, in depth order: entry
+// k's pairs at offsets[k - a] .., its live tiles in row-major order.  The
+// warp writes the pairs of its 32 entries (m: the lanes whose entry has
+// pairs; r, e, pos: each lane's rectangle, entry and first pair position)
+// with its lanes spread over the tiles of several entries at once: the
+// rectangles are laid end to end (an exclusive prefix of their areas), lane
+// l takes tile slot f0 + l of that sequence, finds its entry by a binary
+// search over the lanes' prefixes, and ranks its tile among the live tiles of
+// the same entry (the ballot bits of that entry's lanes in the step, plus the
+// live tiles the entry had in earlier steps).  Stores stay coalesced, and
+// entries of a few tiles share a step instead of taking one each (measured
+// against one entry per step: emit 0.300 -> 0.261 ms per 8-view launch set).
 template <bool COMPACT>
-__device__ inline void emit_warp_entries(uint32_t m, uint2 r, uint32_t e, uint32_t pos, uint32_t c,
-                                         const uint32_t* s_tb, const uint32_t* s_tx, const uint32_t* __restrict__ done,
-                                         uint32_t* __restrict__ keys, uint32_t* __restrict__ values,
-                                         uint64_t pair_cap, uint32_t* __restrict__ overflow) {
+__device__ inline void emit_warp_segmented(uint32_t m, uint2 r, uint32_t e, uint32_t pos,
+                                           const uint32_t* s_tb, const uint32_t* s_tx,
+                                           const uint32_t* __restrict__ done, uint32_t* __restrict__ keys,
+                                           uint32_t* __restrict__ values, uint64_t pair_cap,
+                                           uint32_t* __restrict__ overflow) {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
-    while (m) {
-        const int j = __ffs(m) - 1;
-        m &= m - 1;
-        const uint32_t rx = __shfl_sync(kFull, r.x, j);
-        const uint32_t ry = COMPACT ? 0u : __shfl_sync(kFull, r.y, j);
-        const uint32_t je = __shfl_sync(kFull, e, j), jpos = __shfl_sync(kFull, pos, j);
-        const uint32_t jc = __shfl_sync(kFull, c, j);
-        const TileRect tr = unpack_rect<COMPACT>(make_uint2(rx, ry));
-        const uint32_t xlo = tr.xlo, xhi = tr.xhi, ylo = tr.ylo, yhi = tr.yhi, v = tr.v;
-        const uint32_t w = xhi - xlo, area = w * (yhi - ylo);
-        const uint32_t tx = s_tx[v], t0 = s_tb[v] + ylo * tx + xlo;
-        // an approximate reciprocal: the row estimate below is corrected by one either way
-        const float rinv = __fdividef(1.0f, (float)w);
-        uint32_t written = 0;
-        for (uint32_t f0 = 0; f0 < area && written < jc; f0 += 32) {
-            const uint32_t f = f0 + (uint32_t)lane;
-            bool live = false;
-            uint32_t t = 0;
-            if (f < area) {
-                uint32_t row = (uint32_t)((float)f * rinv);   // f / w, corrected below (f < 2^20)
-                if (row * w > f) --row;
-                else if ((row + 1u) * w <= f) ++row;
-                t = t0 + row * tx + (f - row * w);
-                live = !((done[t >> 5] >> (t & 31)) & 1u);
-            }
-            const uint32_t bm = __ballot_sync(kFull, live);
-            if (live) {
-                const uint64_t p = (uint64_t)jpos + written + __popc(bm & lt);
-                if (p < pair_cap) {
-                    keys[p] = t;
-                    values[p] = je;
-                } else {
-                    atomicOr(overflow, 1u);
-                }
-            }
-            written += __popc(bm);
+    const TileRect tr = unpack_rect<COMPACT>(r);
+    const bool has = (m >> lane) & 1u;
+    const uint32_t w = has ? tr.xhi - tr.xlo : 1u;
+    const uint32_t area = has ? w * (tr.yhi - tr.ylo) : 0u;
+    const uint32_t tx = s_tx[has ? tr.v : 0u];
+    const uint32_t t0 = s_tb[has ? tr.v : 0u] + tr.ylo * tx + tr.xlo;
+    const float rinv = __fdividef(1.0f, (float)w);   // approximate: the row estimate is corrected below
+    uint32_t incl = area;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += y;
+    }
+    const uint32_t pre = incl - area;
+    const uint32_t A = __shfl_sync(kFull, incl, 31);
+    uint32_t carry = 0;   // live tiles of the step's first entry in the steps before
+    for (uint32_t f0 = 0; f0 < A; f0 += 32) {
+        const uint32_t f = f0 + (uint32_t)lane;
+        int j = 0;   // the last lane whose prefix is <= f
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t pj = __shfl_sync(kFull, pre, j + step);
+            if (pj <= f) j += step;
         }
+        const uint32_t pj = __shfl_sync(kFull, pre, j), wj = __shfl_sync(kFull, w, j);
+        const uint32_t txj = __shfl_sync(kFull, tx, j), t0j = __shfl_sync(kFull, t0, j);
+        const uint32_t posj = __shfl_sync(kFull, pos, j), ej = __shfl_sync(kFull, e, j);
+        const float rj = __shfl_sync(kFull, rinv, j);
+        const bool valid = f < A;
+        const uint32_t local = valid ? f - pj : 0u;
+        uint32_t row = (uint32_t)((float)local * rj);   // local / wj, corrected (local < 2^20)
+        if (row * wj > local) --row;
+        else if ((row + 1u) * wj <= local) ++row;
+        const uint32_t t = t0j + row * txj + (local - row * wj);
+        const bool live = valid && !((done[t >> 5] >> (t & 31)) & 1u);
+        const uint32_t bm = __ballot_sync(kFull, live);
+        const uint32_t first = pj > f0 ? pj - f0 : 0u;   // the step's first lane of entry j
+        const uint32_t rank = __popc(bm & lt & ~((1u << first) - 1u)) + (pj < f0 ? carry : 0u);
+        if (live) {
+            const uint64_t p = (uint64_t)posj + rank;
+            if (p < pair_cap) {
+                keys[p] = t;
+                values[p] = ej;
+            } else {
+                atomicOr(overflow, 1u);
+            }
+        }
+        carry = __shfl_sync(kFull, rank + (live ? 1u : 0u), 31);
     }
 }
 
@@ -282,8 +299,8 @@ k_emit_slice(const uint32_t* __restrict__ order, const uint2* __restrict__ rect_
 #pragma unroll
     for (int j = 0; j < J; ++j) {   // unrolled: the per-lane arrays stay in registers
         const uint32_t m = __ballot_sync(kFull, cnt[j] > 0);
-        if (m) emit_warp_entries<COMPACT>(m, rr[j], ee[j], pos[j], cnt[j], s_tb, s_tx, done, keys, values, pair_cap,
-                                          overflow);
+        if (m)
+            emit_warp_segmented<COMPACT>(m, rr[j], ee[j], pos[j], s_tb, s_tx, done, keys, values, pair_cap, overflow);
     }
 }
 
