@@ -154,8 +154,8 @@ def cpu_baseline(scene, poses, width, height, budget_s: float = 15.0) -> dict:
 KERNEL_TRAFFIC = {
     "blend": {"sources": ["paper_2605_08699_b300/csrc/blend.cu", "paper_2605_08699_b300/csrc/sliced.cu",
                           "paper_2605_08699_b300/csrc/sliced.cuh"],
-              "sha1": "b368a6d1ff261a1edb140c56681ea613af6c79ab",
-              "bytes_per_view": 381664256 / 4},
+              "sha1": "422c82682fed8d42c1475349994a2a8d062ba9ee",
+              "bytes_per_view": 381460736 / 4},
 }
 
 
