@@ -21,12 +21,9 @@ size_t scan_tmp_words(uint64_t n);
 // total_zeroed: *total64 is already zero (no clearing launch).
 Status launch_scan_u32(const uint32_t* in, const uint32_t* order, uint32_t* out, uint64_t n,
                        uint64_t* total64, uint32_t* tmp, cudaStream_t st, bool total_zeroed = false);
-// The same scan when the producer of `in` also wrote block_sums[j] = the sum of
-// in[j * kScanBlock .. (j + 1) * kScanBlock) for every block j < ceil(n / kScanBlock):
-// the reduce pass over `in` is skipped.  *total64 receives the total.
+// Entries per block of the sliced count kernel, whose blocks' sums this scan
+// turns into block offsets (also the scan's own tile).
 constexpr uint32_t kScanBlock = 4096;
-Status launch_scan_u32_summed(const uint32_t* in, uint32_t* out, uint64_t n, const uint32_t* block_sums,
-                              uint64_t* total64, uint32_t* tmp, cudaStream_t st);
 
 // K3: duplicate-and-key emit.  For each k < n_entries with e = order ? order[k] : k
 // and tiles[e] > 0, write the tiles of rect[e] (row-major) at offsets[k]..:

@@ -542,8 +542,8 @@ SlicedLayout sliced_layout(const Scene* scene, FrameRequest& req) {
     const uint64_t E = L.E;
     size_t b = sizeof(ViewParams) * kMaxViews + 96 * 256;
     b += E * (16 + 16 + 4 + 4 + 4 + 8 + (req.want_q ? 4 : 0));
-    b += E * 4 * 4 + (E + 1) * 4 * 2 + E * 8 * 2;         // depth sort buffers, counts, offsets, rects (2)
-    b += ((E + 1 + kScanBlock - 1) / kScanBlock) * 4;     // block sums of the counts
+    b += E * 4 * 4 + (E + 1) * 4 + E * 8 * 2;             // depth sort buffers, in-block offsets, rects (2)
+    b += ((E + 1 + kScanBlock - 1) / kScanBlock) * 4 * 2; // block sums of the counts and their offsets
     b += L.tmp_words * 4;
     b += (sizeof(uint2) + 4 * 4 + 4) * (size_t)L.total_tiles + L.done_words * 4;   // ranges, active, strips
     b += (size_t)L.total_sat * 4;                                                   // running-tile tables
@@ -609,9 +609,9 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     uint32_t* pv_alt = ctx.fixed.take<uint32_t>(E);
     uint32_t* pk = ctx.fixed.take<uint32_t>(E);
     uint32_t* order = ctx.fixed.take<uint32_t>(E);
-    uint32_t* counts = ctx.fixed.take<uint32_t>(E + 1);
-    uint32_t* offsets = ctx.fixed.take<uint32_t>(E + 1);
+    uint32_t* inblock = ctx.fixed.take<uint32_t>(E + 1);   // each entry's pair offset within its count block
     uint32_t* count_sums = ctx.fixed.take<uint32_t>((E + 1 + kScanBlock - 1) / kScanBlock);
+    uint32_t* block_offs = ctx.fixed.take<uint32_t>((E + 1 + kScanBlock - 1) / kScanBlock);
     uint2* rect_sorted = ctx.fixed.take<uint2>(E);
     uint2* rect_alt = ctx.fixed.take<uint2>(E);
     sp.key_range = ctx.fixed.take<uint32_t>(2);
@@ -709,10 +709,12 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
         TIGAS_TRY(mark(kStScan, true));
         // also clears the slice's active-list counts and blend work counter (d_misc[0..3])
         TIGAS_TRY(launch_running_sat(d_views, V, done, sat, d_misc, 4, st));
-        // counts[b - a] = 0 makes offsets[b - a] the slice total (also in *d_P); the count
-        // kernel also sums the counts per scan block, so the scan has no reduce pass
-        TIGAS_TRY(launch_count_slice(rect_sorted, a, b, d_views, V, sat, counts, count_sums, compact, st));
-        TIGAS_TRY(launch_scan_u32_summed(counts, offsets, b - a + 1, count_sums, d_P, tmp, st));
+        // the count kernel writes each entry's prefix within its block of kScanBlock
+        // entries and the blocks' sums; the scan of the sums gives the blocks'
+        // offsets and the slice total (*d_P; the closing zero count puts the total at b)
+        TIGAS_TRY(launch_count_slice(rect_sorted, a, b, d_views, V, sat, inblock, count_sums, compact, st));
+        TIGAS_TRY(launch_scan_u32(count_sums, nullptr, block_offs, (b - a + 1 + kScanBlock - 1) / kScanBlock, d_P,
+                                  tmp, st));
         TIGAS_TRY(mark(kStScan, false));
         uint64_t cap = static_cap;
         if (!stat) {
@@ -732,8 +734,8 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
             cap = P;
         }
         TIGAS_TRY(mark(kStEmit, true));
-        TIGAS_TRY(launch_emit_slice(compact ? nullptr : order, rect_sorted, a, b, offsets, d_views, V, done, keys_a,
-                                    vals_a, cap, d_flags, compact, st));
+        TIGAS_TRY(launch_emit_slice(compact ? nullptr : order, rect_sorted, a, b, inblock, block_offs, d_views, V,
+                                    done, keys_a, vals_a, cap, d_flags, compact, st));
         TIGAS_TRY(mark(kStEmit, false));
         TIGAS_TRY(mark(kStPairSort, true));
         TIGAS_TRY(radix_sort<uint32_t>(keys_a, vals_a, keys_b, vals_b, keys_c, vals_c, cap, stat ? d_P : nullptr, 0,

@@ -127,16 +127,21 @@ k_running_sat(const ViewParams* __restrict__ views_g, const uint32_t* __restrict
     }
 }
 
-// counts[k - a] = tiles of entry order[k]'s rectangle that are not done, for
-// k in [a, b), and counts[b - a] = 0; sums[j] = the sum of counts of block j
-// (kScanBlock consecutive counts: the scan's tile), so the scan needs no
-// reduce pass.  One CTA per block, 16 counts per thread.
+// With count(k) = tiles of entry k's rectangle that are not done, for k in
+// [a, b), and count(b) = 0 (the closing zero): inblock[k - a] = the sum of
+// count over the entries of k's block (kScanBlock consecutive entries) before
+// k, and sums[j] = block j's total.  An entry's pair offset is then its
+// block's offset (an exclusive scan of sums) plus inblock, so no pass over
+// the counts follows (measured against counts and a separate scan pass over
+// them: see the design notes' binning rows).  One CTA per block.
 template <bool COMPACT, int kCountThreads>
 __global__ void __launch_bounds__(kCountThreads)
 k_count_slice(const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b, const ViewParams* __restrict__ views_g,
-              int V, const uint32_t* __restrict__ sat, uint32_t* __restrict__ counts, uint32_t* __restrict__ sums) {
+              int V, const uint32_t* __restrict__ sat, uint32_t* __restrict__ inblock, uint32_t* __restrict__ sums) {
     constexpr int kCountItems = (int)kScanBlock / kCountThreads;
-    __shared__ uint32_t s_sb[kMaxViews], s_w1[kMaxViews], ws[kCountThreads / 32];
+    constexpr int kW = kCountThreads / 32;
+    __shared__ uint32_t s_sb[kMaxViews], s_w1[kMaxViews], ws[kW + 1];
+    __shared__ uint32_t buf[kScanBlock + kScanBlock / 32];   // the block's counts, then their prefixes
     for (int k = threadIdx.x; k < V; k += kCountThreads) {
         s_sb[k] = views_g[k].sat_base;
         s_w1[k] = (uint32_t)views_g[k].TX + 1u;
@@ -144,6 +149,7 @@ k_count_slice(const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b, con
     __syncthreads();
     const uint64_t n = b - a + 1;   // with the closing zero
     const uint64_t base = (uint64_t)blockIdx.x * kScanBlock;
+    auto pad = [](uint32_t i) { return i + (i >> 5); };
     // all of the thread's rectangles first (independent loads in flight), then
     // the table lookups; past the slice an empty rectangle counts 0
     uint2 rr[kCountItems];
@@ -152,10 +158,8 @@ k_count_slice(const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b, con
         const uint64_t i = base + (uint64_t)r * kCountThreads + threadIdx.x;
         rr[r] = i < b - a ? rect_sorted[a + i] : make_uint2(0u, 0u);
     }
-    uint32_t total = 0;
 #pragma unroll
     for (int r = 0; r < kCountItems; ++r) {
-        const uint64_t i = base + (uint64_t)r * kCountThreads + threadIdx.x;
         const TileRect tr = unpack_rect<COMPACT>(rr[r]);
         const bool ne = tr.xhi > tr.xlo && tr.yhi > tr.ylo;
         // an empty rectangle looks up word 0 of the table (always present), so every
@@ -163,20 +167,53 @@ k_count_slice(const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b, con
         const uint32_t* s = sat + (ne ? s_sb[tr.v] : 0u);
         const uint32_t w1 = ne ? s_w1[tr.v] : 0u;
         const uint32_t xl = ne ? tr.xlo : 0u, xh = ne ? tr.xhi : 0u, yl = ne ? tr.ylo : 0u, yh = ne ? tr.yhi : 0u;
-        const uint32_t c = s[yh * w1 + xh] - s[yl * w1 + xh] - s[yh * w1 + xl] + s[yl * w1 + xl];
-        if (i < n) counts[i] = c;
-        total += i < n ? c : 0u;
+        buf[pad((uint32_t)(r * kCountThreads) + threadIdx.x)] =
+            s[yh * w1 + xh] - s[yl * w1 + xh] - s[yh * w1 + xl] + s[yl * w1 + xl];
+    }
+    __syncthreads();
+    // the block's exclusive prefix: each thread scans kCountItems consecutive
+    // counts, the threads' totals are scanned across the block
+    uint32_t v[kCountItems];
+    uint32_t tsum = 0;
+#pragma unroll
+    for (int q = 0; q < kCountItems; ++q) {
+        v[q] = buf[pad(threadIdx.x * kCountItems + q)];
+        tsum += v[q];
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = tsum;
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) total += __shfl_xor_sync(kFull, total, d);
-    if (lane == 0) ws[warp] = total;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t t = 0;
-        for (int w = 0; w < kCountThreads / 32; ++w) t += ws[w];
-        sums[blockIdx.x] = t;
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += y;
     }
+    if (lane == 31) ws[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t x = lane < kW ? ws[lane] : 0u;
+        uint32_t wi = x;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, wi, d);
+            if (lane >= d) wi += y;
+        }
+        if (lane < kW) ws[lane] = wi - x;   // exclusive warp offsets
+        if (lane == kW - 1) ws[kW] = wi;     // the block's total
+    }
+    __syncthreads();
+    uint32_t off = ws[warp] + incl - tsum;
+#pragma unroll
+    for (int q = 0; q < kCountItems; ++q) {
+        buf[pad(threadIdx.x * kCountItems + q)] = off;
+        off += v[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kCountItems; ++r) {
+        const uint64_t i = base + (uint64_t)r * kCountThreads + threadIdx.x;
+        if (i < n) inblock[i] = buf[pad((uint32_t)(r * kCountThreads) + threadIdx.x)];
+    }
+    if (threadIdx.x == 0) sums[blockIdx.x] = ws[kW];
 }
 
 // Pairs (tile, entry) of the slice for tiles not done, in depth order: entry
@@ -251,9 +288,10 @@ __device__ inline void emit_warp_segmented(uint32_t m, uint2 r, uint32_t e, uint
 }
 
 // Each warp takes 32 J consecutive entries, lane l the entries 32 j + l: all
-// of its pair offsets are loaded at once (an entry's count is the next entry's
-// offset minus its own; offsets[b - a] is the slice total), then its
-// rectangles, then the entries with pairs are written group by group.  A
+// of its pair offsets are loaded at once (entry k's offset is
+// block_offs[(k - a) / kScanBlock] + inblock[k - a]; its count is the next
+// entry's offset minus its own, and the offset of b is the slice total), then
+// its rectangles, then the entries with pairs are written group by group.  A
 // larger J launches fewer CTAs for slices of many entries whose tiles have
 // mostly stopped.  COMPACT: the entry id travels in the rectangle's second
 // word (order unused).
@@ -261,7 +299,8 @@ constexpr int kEmitThreads = 256;
 template <bool COMPACT, int J>
 __global__ void __launch_bounds__(kEmitThreads)
 k_emit_slice(const uint32_t* __restrict__ order, const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b,
-             const uint32_t* __restrict__ offsets, const ViewParams* __restrict__ views_g, int V,
+             const uint32_t* __restrict__ inblock, const uint32_t* __restrict__ block_offs,
+             const ViewParams* __restrict__ views_g, int V,
              const uint32_t* __restrict__ done, uint32_t* __restrict__ keys, uint32_t* __restrict__ values,
              uint64_t pair_cap, uint32_t* __restrict__ overflow) {
     __shared__ uint32_t s_tb[kMaxViews], s_tx[kMaxViews];
@@ -277,10 +316,10 @@ k_emit_slice(const uint32_t* __restrict__ order, const uint2* __restrict__ rect_
 #pragma unroll
     for (int j = 0; j < J; ++j) {
         const uint64_t k = wbase + 32u * j + lane;
-        pos[j] = k <= b ? offsets[k - a] : 0u;
+        pos[j] = k <= b ? block_offs[(k - a) / kScanBlock] + inblock[k - a] : 0u;
     }
     const uint64_t kend = wbase + 32u * J;
-    const uint32_t tail = kend <= b ? offsets[kend - a] : 0u;
+    const uint32_t tail = kend <= b ? block_offs[(kend - a) / kScanBlock] + inblock[kend - a] : 0u;
 #pragma unroll
     for (int j = 0; j < J; ++j) {
         const uint32_t up = __shfl_down_sync(kFull, pos[j], 1);
@@ -448,25 +487,26 @@ Status launch_running_sat(const ViewParams* views, int V, const uint32_t* done, 
 }
 
 Status launch_count_slice(const uint2* rect_sorted, uint64_t a, uint64_t b, const ViewParams* views, int V,
-                          const uint32_t* sat, uint32_t* counts, uint32_t* sums, bool compact, cudaStream_t st) {
+                          const uint32_t* sat, uint32_t* inblock, uint32_t* sums, bool compact, cudaStream_t st) {
     if (b <= a) return {};
     const unsigned grid = (unsigned)((b - a + 1 + kScanBlock - 1) / kScanBlock);
     // a slice of few blocks (less than two per SM) takes 1024 threads per block,
     // 4 rectangles each, so that its few CTAs hold more warps
     const bool big = grid < 2u * (unsigned)kSmCount;
     if (compact) {
-        if (big) k_count_slice<true, 1024><<<grid, 1024, 0, st>>>(rect_sorted, a, b, views, V, sat, counts, sums);
-        else k_count_slice<true, 256><<<grid, 256, 0, st>>>(rect_sorted, a, b, views, V, sat, counts, sums);
+        if (big) k_count_slice<true, 1024><<<grid, 1024, 0, st>>>(rect_sorted, a, b, views, V, sat, inblock, sums);
+        else k_count_slice<true, 256><<<grid, 256, 0, st>>>(rect_sorted, a, b, views, V, sat, inblock, sums);
     } else {
-        if (big) k_count_slice<false, 1024><<<grid, 1024, 0, st>>>(rect_sorted, a, b, views, V, sat, counts, sums);
-        else k_count_slice<false, 256><<<grid, 256, 0, st>>>(rect_sorted, a, b, views, V, sat, counts, sums);
+        if (big) k_count_slice<false, 1024><<<grid, 1024, 0, st>>>(rect_sorted, a, b, views, V, sat, inblock, sums);
+        else k_count_slice<false, 256><<<grid, 256, 0, st>>>(rect_sorted, a, b, views, V, sat, inblock, sums);
     }
     TIGAS_LAUNCHED();
     return {};
 }
 
 Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64_t a, uint64_t b,
-                         const uint32_t* offsets, const ViewParams* views, int V, const uint32_t* done,
+                         const uint32_t* inblock, const uint32_t* block_offs, const ViewParams* views, int V,
+                         const uint32_t* done,
                          uint32_t* keys, uint32_t* values, uint64_t pair_cap, uint32_t* overflow, bool compact,
                          cudaStream_t st) {
     if (b <= a) return {};
@@ -479,11 +519,11 @@ Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64
 #define TIGAS_EMIT(JJ)                                                                                              \
     do {                                                                                                            \
         if (compact)                                                                                                \
-            k_emit_slice<true, JJ><<<grid, kEmitThreads, 0, st>>>(order, rect_sorted, a, b, offsets, views, V, done, \
-                                                                  keys, values, pair_cap, overflow);                \
+            k_emit_slice<true, JJ><<<grid, kEmitThreads, 0, st>>>(order, rect_sorted, a, b, inblock, block_offs,     \
+                                                                  views, V, done, keys, values, pair_cap, overflow); \
         else                                                                                                        \
-            k_emit_slice<false, JJ><<<grid, kEmitThreads, 0, st>>>(order, rect_sorted, a, b, offsets, views, V,     \
-                                                                   done, keys, values, pair_cap, overflow);         \
+            k_emit_slice<false, JJ><<<grid, kEmitThreads, 0, st>>>(order, rect_sorted, a, b, inblock, block_offs,    \
+                                                                   views, V, done, keys, values, pair_cap, overflow); \
     } while (0)
     switch (J) {
         case 1: TIGAS_EMIT(1); break;

@@ -57,20 +57,22 @@ Status launch_fill_unseen(const ViewParams* views, int V, uint32_t total_tiles, 
 Status launch_running_sat(const ViewParams* views, int V, const uint32_t* done, uint32_t* sat, uint32_t* slice_zero,
                           int n_zero, cudaStream_t st);
 
-// counts[k - a]: not-done tiles in the rectangle of depth-ordered entry k, k in [a, b)
-// (four reads of the running-tile table), and counts[b - a] = 0; sums[j]: the
-// sum of counts block j (kScanBlock counts), for launch_scan_u32_summed.
-// compact: rectangles in the compact form (SplatArrays::compact_rect).
+// count(k): not-done tiles in the rectangle of depth-ordered entry k, k in
+// [a, b) (four reads of the running-tile table), and count(b) = 0.  Writes
+// inblock[k - a] = the sum of count over the entries before k in k's block
+// (kScanBlock consecutive entries; b - a + 1 values), and sums[j] = block j's
+// total.  compact: rectangles in the compact form (SplatArrays::compact_rect).
 Status launch_count_slice(const uint2* rect_sorted, uint64_t a, uint64_t b, const ViewParams* views, int V,
-                          const uint32_t* sat, uint32_t* counts, uint32_t* sums, bool compact, cudaStream_t st);
+                          const uint32_t* sat, uint32_t* inblock, uint32_t* sums, bool compact, cudaStream_t st);
 
-// (tile, entry) pairs of entries [a, b) for tiles not done, at offsets[k - a]
-// (offsets: exclusive scan of counts with b - a + 1 values).  The entry of k is
-// order[k], or the second word of a compact rectangle (order may then be null).
+// (tile, entry) pairs of entries [a, b) for tiles not done, entry k's at
+// block_offs[(k - a) / kScanBlock] + inblock[k - a] (block_offs: the exclusive
+// scan of the count kernel's block sums).  The entry of k is order[k], or the
+// second word of a compact rectangle (order may then be null).
 Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64_t a, uint64_t b,
-                         const uint32_t* offsets, const ViewParams* views, int V, const uint32_t* done,
-                         uint32_t* keys, uint32_t* values, uint64_t pair_cap, uint32_t* overflow, bool compact,
-                         cudaStream_t st);
+                         const uint32_t* inblock, const uint32_t* block_offs, const ViewParams* views, int V,
+                         const uint32_t* done, uint32_t* keys, uint32_t* values, uint64_t pair_cap,
+                         uint32_t* overflow, bool compact, cudaStream_t st);
 
 // Tile ranges of the slice's sorted keys, and the list of tiles with pairs
 // that are not done, in three regions of `active` (4 n_tiles items): the

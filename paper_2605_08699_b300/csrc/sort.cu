@@ -171,28 +171,6 @@ Status launch_scan_u32(const uint32_t* in, const uint32_t* order, uint32_t* out,
     return {};
 }
 
-Status launch_scan_u32_summed(const uint32_t* in, uint32_t* out, uint64_t n, const uint32_t* block_sums,
-                              uint64_t* total64, uint32_t* tmp, cudaStream_t st) {
-    static_assert(kScanBlock == (uint32_t)kTileN, "block sums must match the scan's tile");
-    if (n == 0) {
-        if (total64) TIGAS_CUDA_TRY(cudaMemsetAsync(total64, 0, sizeof(uint64_t), st));
-        return {};
-    }
-    const uint64_t b = scan_blocks(n);
-    GatherLoader ld{in, nullptr};
-    if (b == 1) {
-        k_scan_down<<<1, kThreads, 0, st>>>(ld, n, nullptr, out, (unsigned long long*)total64);
-        TIGAS_LAUNCHED();
-        return {};
-    }
-    if (b > 0x7FFFFFFFull) return {TIGAS_ERR_INVALID, "scan too large"};
-    uint32_t* offs = tmp;
-    TIGAS_TRY(launch_scan_u32(block_sums, nullptr, offs, b, total64, tmp + b, st));
-    k_scan_down<<<(unsigned)b, kThreads, 0, st>>>(ld, n, offs, out, nullptr);
-    TIGAS_LAUNCHED();
-    return {};
-}
-
 // ------------------------------------------------------------ radix sort
 
 namespace {
