@@ -202,8 +202,8 @@ def roofline(stage_ms: dict, per_step: dict, peaks: dict, clocks: dict, steps: i
       preprocess  12 B per (Gaussian, view) + (A - 12) B per Gaussian + 52 B per kept entry
       depth_sort  passes run x 24 B per entry (key and 8-byte compact rectangle with its entry id,
                   read and written), or x 32 B with wide rectangles (key, value, rectangle)
-      scan        20 B per kept entry: slice count with per-block sums (rect 8 B + count 4 B),
-                  count scan (4 B + 4 B)
+      scan        12 B per kept entry: the slice count reads the rectangle (8 B) and writes the
+                  entry's offset within its block (4 B); the scan of the block sums is negligible
       emit        12 B per kept entry (rect, offset; + 4 B of order with wide rectangles)
                   + 8 B per emitted pair
       pair_sort   passes x 16 B per emitted pair
@@ -218,7 +218,7 @@ def roofline(stage_ms: dict, per_step: dict, peaks: dict, clocks: dict, steps: i
     bytes_per = {
         "preprocess": w["entries"] * 12 + w["gaussians"] * (w["attr_bytes"] - 12) + w["kept"] * 52,
         "depth_sort": w["entries"] * w["depth_passes"] * (24 if w.get("compact_rect") else 32),
-        "scan": w["kept"] * 20,
+        "scan": w["kept"] * 12,
         "emit": w["kept"] * (12 if w.get("compact_rect") else 16) + w["pairs"] * 8,
         "pair_sort": w["pairs"] * w["sort_passes"] * 16,
         "ranges": w["tiles"] * w["slices"] * 8,
