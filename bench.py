@@ -154,8 +154,8 @@ def cpu_baseline(scene, poses, width, height, budget_s: float = 15.0) -> dict:
 KERNEL_TRAFFIC = {
     "blend": {"sources": ["paper_2605_08699_b300/csrc/blend.cu", "paper_2605_08699_b300/csrc/sliced.cu",
                           "paper_2605_08699_b300/csrc/sliced.cuh"],
-              "sha1": "422c82682fed8d42c1475349994a2a8d062ba9ee",
-              "bytes_per_view": 381460736 / 4},
+              "sha1": "a3e8c18f5a01818396f45fca47145c2b655d93cd",
+              "bytes_per_view": 380628224 / 4},
 }
 
 
@@ -180,16 +180,16 @@ STAGE_LIMITS = {
     "preprocess": "instructions: 592 thread instructions per (Gaussian, view), 73 % issue active, DRAM 46 % "
                   "of peak; traffic equals the algorithmic bytes",
     "depth_sort": "instructions per key and load latency: 146-157 thread instructions per key per pass, "
-                  "41-50 % issue active, long_scoreboard first, DRAM 29-36 % of peak",
-    "scan": "latency: per slice a one-CTA-per-view running-tile table (8 us, barrier first), a count "
-            "of 46-1655 CTAs (long_scoreboard first, 12-45 % warps active) and a one-CTA block-sum scan",
-    "emit": "instructions per pair (46-58 % issue active, not_selected first); the pairs stay in L2 "
-            "(slice 0: 0.2 MB of DRAM writes for 40 MB of pairs)",
+                  "42-50 % issue active, long_scoreboard first, DRAM 29-37 % of peak",
+    "scan": "latency: per slice a one-CTA-per-view running-tile table (8 us, barrier first), a count of "
+            "46-1655 CTAs (long_scoreboard first) and a one-CTA block-sum scan (about 4 us)",
+    "emit": "instructions per pair (43-56 % issue active, not_selected and wait first in the early slices); "
+            "the pairs stay in L2 (slice 0: 0.2 MB of DRAM writes for 40 MB of pairs)",
     "pair_sort": "latency and L2: the pair lists live in L2 (DRAM reads are the keys' first touch), later "
-                 "slices' scatter passes run 88-255 CTAs at 18-32 % warps active, plus a one-CTA digit-base kernel",
-    "ranges": "latency: a sampled search per tile, long_scoreboard 12-18 per issue, 9-11 us per slice",
-    "blend": "issue-bound in the first slice (79 % issue active), latency-bound in later ones "
-             "(long_scoreboard first); not DRAM-bound (6-11 % of peak)",
+                 "slices' scatter passes run few CTAs at 18-31 % warps active, plus a one-CTA digit-base kernel",
+    "ranges": "latency: a sampled search per tile, long_scoreboard first, 9-12 us per slice",
+    "blend": "issue-bound in the first slice (83 % issue active), latency-bound in later ones "
+             "(long_scoreboard first); not DRAM-bound (6-12 % of peak)",
 }
 
 
