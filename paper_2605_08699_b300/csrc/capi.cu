@@ -166,7 +166,7 @@ Status finish_render(RenderContext& ctx, cudaStream_t st, PendingRender& p) {
             // a graph is captured again (with the new counts) on the next call,
             // a direct launch set takes a larger capacity next time
             if (res.direct_static)
-                ctx.slice_ratio *= 2.0;
+                ctx.slice_ratio(p.req.n_slices, p.req.first_slice_inv) *= 2.0;
             else
                 drop_graphs(ctx);
             g_exact_rerenders.fetch_add(1, std::memory_order_relaxed);
@@ -190,7 +190,8 @@ Status finish_render(RenderContext& ctx, cudaStream_t st, PendingRender& p) {
             }
             res.pairs = P;
             const double scale = pair_scale(p.scene, p.req);
-            if (scale > 0.0 && (double)mx / scale > ctx.slice_ratio) ctx.slice_ratio = (double)mx / scale;
+            double& ratio = ctx.slice_ratio(p.req.n_slices, p.req.first_slice_inv);
+            if (scale > 0.0 && (double)mx / scale > ratio) ratio = (double)mx / scale;
         }
     }
     if (ctx.h_flags[0] & 1u) return {TIGAS_ERR_OVERFLOW, "pair buffer overflow"};

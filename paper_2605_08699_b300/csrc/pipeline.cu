@@ -314,8 +314,17 @@ void forget_launch_sets() {
     for (RenderContext* c : g_pool) {
         drop_graphs(*c);
         c->seen_keys.clear();
-        c->slice_ratio = 0.0;
+        c->slice_ratios.clear();
     }
+}
+
+double& RenderContext::slice_ratio(int n_slices, int first_slice_inv) {
+    const uint32_t key = ((uint32_t)n_slices << 16) | ((uint32_t)first_slice_inv & 0xFFFFu);
+    for (auto& r : slice_ratios)
+        if (r.first == key) return r.second;
+    if (slice_ratios.size() >= 64) slice_ratios.erase(slice_ratios.begin());
+    slice_ratios.emplace_back(key, 0.0);
+    return slice_ratios.back().second;
 }
 
 bool is_device_pointer(const void* p) {
@@ -823,10 +832,12 @@ Status render_sliced_graph(Scene* scene, FrameRequest& req, RenderContext& ctx, 
         // as in a server's mixed-resolution batches, would pay it every time)
         if (ctx.seen_keys.size() >= 64) ctx.seen_keys.erase(ctx.seen_keys.begin());
         ctx.seen_keys.push_back(key);
-        if (ctx.slice_ratio > 0.0) {
-            // fixed capacity from the largest slice seen so far: no host round trips;
-            // an overflow is caught after the stream completes and rendered exactly
-            const uint64_t cap = (uint64_t)(1.5 * ctx.slice_ratio * scale) + 65536;
+        const double ratio = ctx.slice_ratio(req.n_slices, req.first_slice_inv);
+        if (ratio > 0.0) {
+            // fixed capacity from the largest slice seen so far under this schedule: no
+            // host round trips; an overflow is caught after the stream completes and
+            // rendered exactly
+            const uint64_t cap = (uint64_t)(1.5 * ratio * scale) + 65536;
             size_t fb = 0, pb = 0;
             TIGAS_TRY(sliced_workspace(scene, req, cap, &fb, &pb));
             TIGAS_TRY(ctx.fixed.reserve(fb));
@@ -850,7 +861,10 @@ Status render_sliced_graph(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     if (ctx.h_flags[0] != 0) return {};
     uint64_t mx = 0;
     for (int i = 0; i < kMaxSlices; ++i) mx = sp[i] > mx ? sp[i] : mx;
-    if (scale > 0.0 && (double)mx / scale > ctx.slice_ratio) ctx.slice_ratio = (double)mx / scale;
+    {
+        double& ratio = ctx.slice_ratio(req.n_slices, req.first_slice_inv);
+        if (scale > 0.0 && (double)mx / scale > ratio) ratio = (double)mx / scale;
+    }
     if (!seen) return {};
     const uint64_t cap = mx + mx / 2 + 65536;
     size_t fb = 0, pb = 0;

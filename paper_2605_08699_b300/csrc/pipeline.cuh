@@ -151,8 +151,11 @@ struct RenderContext {
     std::vector<Graph> graphs;
     // launch-set shapes seen once (captured on their second appearance)
     std::vector<std::vector<int64_t>> seen_keys;
-    // largest slice pair count seen, per entry and unit of view scale (pair_scale)
-    double slice_ratio = 0.0;
+    // largest slice pair count seen, per unit of view scale (pair_scale), for each
+    // schedule (slices, first-slice fraction) the context has rendered: a schedule
+    // of fewer slices has larger ones, and a context serves every launch-set size
+    std::vector<std::pair<uint32_t, double>> slice_ratios;
+    double& slice_ratio(int n_slices, int first_slice_inv);
     Status init();
     void destroy();
 };
