@@ -132,8 +132,9 @@ k_running_sat(const ViewParams* __restrict__ views_g, const uint32_t* __restrict
 // count over the entries of k's block (kScanBlock consecutive entries) before
 // k, and sums[j] = block j's total.  An entry's pair offset is then its
 // block's offset (an exclusive scan of sums) plus inblock, so no pass over
-// the counts follows (measured against counts and a separate scan pass over
-// them: see the design notes' binning rows).  One CTA per block.
+// the counts follows (measured against writing the counts and scanning them
+// in a separate pass: scan stage 0.256 -> 0.231 ms, emit 0.262 -> 0.275 ms
+// per 8-view launch set).  One CTA per block.
 template <bool COMPACT, int kCountThreads>
 __global__ void __launch_bounds__(kCountThreads)
 k_count_slice(const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b, const ViewParams* __restrict__ views_g,
@@ -217,7 +218,7 @@ k_count_slice(const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b, con
 }
 
 // Pairs (tile, entry) of the slice for tiles not done, in depth order: entry
-// k's pairs at offsets[k - a] .., its live tiles in row-major order.  The
+// k's pairs from its pair offset pos on, its live tiles in row-major order.  The
 // warp writes the pairs of its 32 entries (m: the lanes whose entry has
 // pairs; r, e, pos: each lane's rectangle, entry and first pair position)
 // with its lanes spread over the tiles of several entries at once: the
