@@ -154,7 +154,7 @@ def cpu_baseline(scene, poses, width, height, budget_s: float = 15.0) -> dict:
 KERNEL_TRAFFIC = {
     "blend": {"sources": ["paper_2605_08699_b300/csrc/blend.cu", "paper_2605_08699_b300/csrc/sliced.cu",
                           "paper_2605_08699_b300/csrc/sliced.cuh"],
-              "sha1": "a3e8c18f5a01818396f45fca47145c2b655d93cd",
+              "sha1": "c416a6f1810dc06ed35c2260bb9914b1b887693e",
               "bytes_per_view": 380628224 / 4},
 }
 
