@@ -149,26 +149,37 @@ def cpu_baseline(scene, poses, width, height, budget_s: float = 15.0) -> dict:
 # DRAM bytes (read + write) of the dominant kernel per view of a launch set, from one ncu capture of
 # the same kernel sources (all six slices of a 4-view 1080p launch set of the 3M-Gaussian scene,
 # dram__bytes_read.sum + dram__bytes_write.sum; profiles/blend_ncu_3M_1080p.md), scaled by the
-# views a launch set renders.  Reported only while the sources are the captured ones: the blend's
-# own file and the files that build its active list (the order in which it takes tiles).
+# views a launch set renders.  Reported only while the sources' code (source_digest: comments
+# aside) is the captured one: the blend's own file and the files that build its active list (the
+# order in which it takes tiles).
 KERNEL_TRAFFIC = {
     "blend": {"sources": ["paper_2605_08699_b300/csrc/blend.cu", "paper_2605_08699_b300/csrc/sliced.cu",
                           "paper_2605_08699_b300/csrc/sliced.cuh"],
-              "sha1": "c416a6f1810dc06ed35c2260bb9914b1b887693e",
+              "sha1": "05a2c0c302f32cc492b98abf7be7a6a1140edf3c",
               "bytes_per_view": 380628224 / 4},
 }
 
 
-def kernel_traffic(kernel: str, views: int):
+def source_digest(sources) -> str:
+    """SHA-1 of the sources' code: each line without its // comment and
+    surrounding blanks, empty lines dropped (comment edits keep the digest)."""
     import hashlib
+    import re
+    h = hashlib.sha1()
+    for src in sources:
+        with open(os.path.join(ROOT, src), encoding="utf-8") as f:
+            for line in f:
+                code = re.sub(r"//.*", "", line).strip()
+                if code:
+                    h.update(code.encode() + b"\n")
+    return h.hexdigest()
+
+
+def kernel_traffic(kernel: str, views: int):
     t = KERNEL_TRAFFIC.get(kernel)
     if not t:
         return None
-    h = hashlib.sha1()
-    for src in t["sources"]:
-        with open(os.path.join(ROOT, src), "rb") as f:
-            h.update(f.read())
-    if h.hexdigest() != t["sha1"]:
+    if source_digest(t["sources"]) != t["sha1"]:
         return None   # the kernel changed since the counters were taken
     return int(t["bytes_per_view"] * views)
 
