@@ -578,9 +578,17 @@ k_os_hist(const K* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, int b
             status[p * chunks * 64 + (i - p * per_pass)] = make_uint4(0u, 0u, 0u, 0u);
         }
     }
-    for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) (&h[0][0])[i] = 0;
     KeyMap km;
     km.load(range);
+    // mapped keys lie in [0, span]: digits above its top bit are zero for every key,
+    // so their histograms are not counted (they stay zero, and the pass is skipped)
+    int hp = passes;
+    if (km.on) {
+        const int bits = km.span == 0u ? 1 : 32 - __clz((int)km.span);
+        const int need = (bits - begin_bit + 7) / 8;
+        hp = need < 1 ? 1 : (need < passes ? need : passes);
+    }
+    for (int i = threadIdx.x; i < hp * 256; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
     uint32_t cur[kP], run[kP];
 #pragma unroll
@@ -589,7 +597,7 @@ k_os_hist(const K* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, int b
     auto count = [&](K k) {
 #pragma unroll
         for (int p = 0; p < kP; ++p) {
-            if (p < passes) {
+            if (p < hp) {
                 const int sh = begin_bit + 8 * p;
                 const int nb = min(8, end_bit - sh);
                 const uint32_t d = (uint32_t)(k >> sh) & ((1u << nb) - 1u);
@@ -644,9 +652,9 @@ k_os_hist(const K* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, int b
     }
 #pragma unroll
     for (int p = 0; p < kP; ++p)
-        if (p < passes && run[p]) atomicAdd(&h[p][cur[p]], run[p]);
+        if (p < hp && run[p]) atomicAdd(&h[p][cur[p]], run[p]);
     __syncthreads();
-    for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
+    for (int i = threadIdx.x; i < hp * 256; i += blockDim.x) {
         uint32_t c = (&h[0][0])[i];
         if (c) atomicAdd(&ghist[i], c);
     }
