@@ -663,12 +663,12 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     dex.pay_out = rect_sorted;
     TIGAS_TRY(radix_sort<uint32_t>(sp.depth_key, nullptr, pk_alt, compact ? nullptr : pv_alt, pk,
                                    compact ? nullptr : order, E, nullptr, 0, 32, tmp, st, nullptr, d_flags, &dex));
-    // passes the depth sort ran (read before the slices' scans reuse tmp)
-    TIGAS_CUDA_TRY(cudaMemcpyAsync(ctx.h_flags + 1, radix_active_passes(tmp), sizeof(uint32_t),
-                                   cudaMemcpyDeviceToHost, st));
     TIGAS_TRY(mark(kStDepthSort, false));
-    // also clears the done and strip bits and the slice totals (empty slices count 0)
-    TIGAS_TRY(launch_init_slices(total_tiles, done, strips, d_total, kMaxSlices + 2, st));
+    // also clears the done and strip bits and the slice totals (empty slices count 0),
+    // and keeps the passes the depth sort ran in d_flags[1] (read back with the flags
+    // at the end; the slices' scans reuse tmp)
+    TIGAS_TRY(launch_init_slices(total_tiles, done, strips, d_total, kMaxSlices + 2, radix_active_passes(tmp),
+                                 d_flags + 1, st));
 
     // entries the slices cut: kept ones only (exact), or all (static; culled
     // ones sort after every kept one and have empty rectangles)
@@ -767,7 +767,7 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     }
     // the background of every tile no slice blended
     TIGAS_TRY(launch_fill_unseen(d_views, V, total_tiles, strips, scene->view.bg, st));
-    TIGAS_CUDA_TRY(cudaMemcpyAsync(ctx.h_flags, d_flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    TIGAS_CUDA_TRY(cudaMemcpyAsync(ctx.h_flags, d_flags, sizeof(uint32_t) * 2, cudaMemcpyDeviceToHost, st));
     if (stat) TIGAS_CUDA_TRY(cudaMemcpyAsync(ctx.h_total, d_total, sizeof(uint64_t) * S, cudaMemcpyDeviceToHost, st));
     if (res) {
         res->pairs = total_pairs;   // static: read ctx.h_total after the stream completes

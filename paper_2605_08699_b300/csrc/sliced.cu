@@ -42,8 +42,10 @@ __device__ inline uint8_t to_u8(float x) {
 // of tiles no slice blended.
 __global__ void __launch_bounds__(256)
 k_init_slices(uint32_t total_tiles, uint32_t* __restrict__ done, uint32_t* __restrict__ strips,
-              unsigned long long* __restrict__ totals, int n_totals) {
+              unsigned long long* __restrict__ totals, int n_totals, const uint32_t* __restrict__ word_src,
+              uint32_t* __restrict__ word_dst) {
     const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g == 0 && word_src) *word_dst = *word_src;
     if (g < total_tiles) {
         strips[g] = 0u;
         if ((g & 31u) == 0u) done[g >> 5] = 0u;
@@ -461,12 +463,13 @@ k_ranges_active(const uint32_t* __restrict__ keys, uint64_t n_cap, const uint64_
 }  // namespace
 
 Status launch_init_slices(uint32_t total_tiles, uint32_t* done, uint32_t* strips, uint64_t* totals, int n_totals,
-                          cudaStream_t st) {
+                          const uint32_t* word_src, uint32_t* word_dst, cudaStream_t st) {
     if (n_totals > 256) return {TIGAS_ERR_INVALID, "too many slice totals"};
     const uint32_t n = total_tiles > (uint32_t)n_totals ? total_tiles : (uint32_t)n_totals;
     if (n == 0) return {};
     k_init_slices<<<(n + 255) / 256, 256, 0, st>>>(total_tiles, done, strips,
-                                                   reinterpret_cast<unsigned long long*>(totals), n_totals);
+                                                   reinterpret_cast<unsigned long long*>(totals), n_totals, word_src,
+                                                   word_dst);
     TIGAS_LAUNCHED();
     return {};
 }

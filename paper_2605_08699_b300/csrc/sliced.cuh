@@ -41,9 +41,11 @@ constexpr uint32_t kTileMask = (1u << kStripShift) - 1u;
 // strip s of the tile finished; kStripSeen / kStripSeenNow: the tile was
 // blended and its pixels carry (C, T) in `state`; a tile's first blend starts
 // from (0, 1) instead), and totals[0 .. n_totals) (at most 256).  No pixel is
-// written.
+// written.  Also copies *word_src to *word_dst when word_src is not null (a
+// word the caller reads back with the launch set's other results, instead of
+// a device-to-host copy in the middle of the launch set).
 Status launch_init_slices(uint32_t total_tiles, uint32_t* done, uint32_t* strips, uint64_t* totals, int n_totals,
-                          cudaStream_t st);
+                          const uint32_t* word_src, uint32_t* word_dst, cudaStream_t st);
 
 // After the last slice: the background in the outputs of every tile that no
 // slice blended (kStripSeen and kStripSeenNow clear).
