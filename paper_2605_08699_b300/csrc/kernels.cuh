@@ -11,9 +11,12 @@ Status launch_scene_pack(const float* means, const float* log_scales, const floa
                          int storage, uint4* chunks, cudaStream_t st);
 
 // K1: per-Gaussian preprocess for V views (Gaussian attributes read once).
-// views: device array of V ViewParams.  n_visible: device counters [V] (zeroed here).
+// views: device array of V ViewParams.  n_visible: device counters [V], and
+// out.key_range: [min, max] of the kept depth keys; both set to their start
+// values here (zero, [0xFFFFFFFF, 0]) unless counters_set says the caller
+// already did.
 Status launch_preprocess(const SceneView& scene, const ViewParams* views, int V, const SplatArrays& out,
-                         uint32_t* n_visible, cudaStream_t st);
+                         uint32_t* n_visible, cudaStream_t st, bool counters_set = false);
 
 // K2: exclusive scan of u32 counts.  out[k] = sum_{k' < k} in[order ? order[k'] : k'],
 // total64 = full sum (u64).  tmp: scratch of scan_tmp_words(n) words.

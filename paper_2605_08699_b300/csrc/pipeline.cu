@@ -224,7 +224,9 @@ Status RenderContext::init() {
     TIGAS_CUDA_TRY(cudaEventCreateWithFlags(&ev_rendered, cudaEventDisableTiming));
     TIGAS_CUDA_TRY(pinned_alloc(&h_total, sizeof(uint64_t) * (kMaxSlices + 2)));
     TIGAS_CUDA_TRY(pinned_alloc(&h_flags, sizeof(uint32_t) * 2));
-    TIGAS_CUDA_TRY(pinned_alloc(&h_views, (sizeof(ViewParams) + sizeof(uint64_t)) * kMaxViews));
+    TIGAS_CUDA_TRY(pinned_alloc(&h_header, sizeof(LaunchHeader)));
+    std::memset(h_header, 0, sizeof(LaunchHeader));
+    h_header->key_range[0] = 0xFFFFFFFFu;
     TIGAS_CUDA_TRY(pinned_alloc(&h_misc, sizeof(uint32_t) * kMaxViews));
     for (int k = 0; k < kNumStages; ++k)
         for (int r = 0; r < kMaxSlices; ++r) {
@@ -247,7 +249,7 @@ void RenderContext::destroy() {
     staging_bytes.clear();
     if (h_total) cudaFreeHost(h_total);
     if (h_flags) cudaFreeHost(h_flags);
-    if (h_views) cudaFreeHost(h_views);
+    if (h_header) cudaFreeHost(h_header);
     if (stream) cudaStreamDestroy(stream);
     if (copy_stream) cudaStreamDestroy(copy_stream);
     if (ev_rendered) cudaEventDestroy(ev_rendered);
@@ -261,7 +263,7 @@ void RenderContext::destroy() {
         }
     if (h_misc) cudaFreeHost(h_misc);
     h_misc = nullptr;
-    h_total = nullptr; h_flags = nullptr; h_views = nullptr; stream = nullptr;
+    h_total = nullptr; h_flags = nullptr; h_header = nullptr; stream = nullptr;
 }
 
 namespace {
@@ -417,8 +419,8 @@ Status render_frame(Scene* scene, FrameRequest& req, RenderContext& ctx, cudaStr
     uint2* ranges = ctx.fixed.take<uint2>(total_tiles);
     if (ctx.fixed.over) return {TIGAS_ERR_CUDA, "workspace layout exceeds its reservation"};
 
-    std::memcpy(ctx.h_views, req.views, sizeof(ViewParams) * V);
-    TIGAS_CUDA_TRY(cudaMemcpyAsync(d_views, ctx.h_views, sizeof(ViewParams) * V, cudaMemcpyHostToDevice, st));
+    std::memcpy(ctx.h_header->views, req.views, sizeof(ViewParams) * V);
+    TIGAS_CUDA_TRY(cudaMemcpyAsync(d_views, ctx.h_header->views, sizeof(ViewParams) * V, cudaMemcpyHostToDevice, st));
     TIGAS_CUDA_TRY(cudaMemsetAsync(d_flags, 0, sizeof(uint32_t) * 2, st));
     if (sp.q_dbg) TIGAS_CUDA_TRY(cudaMemsetAsync(sp.q_dbg, 0, E * 4, st));
     if (req.want_counters) TIGAS_CUDA_TRY(cudaMemsetAsync(d_counters, 0, sizeof(unsigned long long) * 4, st));
@@ -567,9 +569,8 @@ size_t pair_bytes_for(uint64_t P) { return P * 24 + radix_tmp_words(P) * 4 + 16 
 
 void sliced_stage_views(const Scene* scene, FrameRequest& req, RenderContext& ctx) {
     SlicedLayout L = sliced_layout(scene, req);
-    char* hv = reinterpret_cast<char*>(ctx.h_views);
-    std::memcpy(hv, req.views, sizeof(ViewParams) * L.V);
-    std::memcpy(hv + sizeof(ViewParams) * kMaxViews, L.pix_base, sizeof(uint64_t) * L.V);
+    std::memcpy(ctx.h_header->views, req.views, sizeof(ViewParams) * L.V);
+    std::memcpy(ctx.h_header->pix_base, L.pix_base, sizeof(uint64_t) * L.V);
 }
 
 Status sliced_workspace(const Scene* scene, FrameRequest& req, uint64_t pair_cap, size_t* fixed_bytes,
@@ -599,13 +600,14 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
         TIGAS_TRY(ctx.fixed.reserve(L.fixed_bytes));
     }
     ctx.fixed.reset();
-    ViewParams* d_views = ctx.fixed.take<ViewParams>(kMaxViews);
+    LaunchHeader* d_hdr = ctx.fixed.take<LaunchHeader>(1);
+    ViewParams* d_views = d_hdr->views;
+    uint64_t* d_pix_base = d_hdr->pix_base;
+    uint32_t* d_flags = d_hdr->flags;
+    uint32_t* d_visible = d_hdr->visible;
     uint64_t* d_total = ctx.fixed.take<uint64_t>(kMaxSlices + 2);
     unsigned long long* d_counters = ctx.fixed.take<unsigned long long>(4);
-    uint32_t* d_flags = ctx.fixed.take<uint32_t>(2);
-    uint32_t* d_visible = ctx.fixed.take<uint32_t>(kMaxViews);
     uint32_t* d_misc = ctx.fixed.take<uint32_t>(4);       // [longest tiles, short tiles, work counter, long tiles]
-    uint64_t* d_pix_base = ctx.fixed.take<uint64_t>(kMaxViews);
     SplatArrays sp{};
     sp.geom = ctx.fixed.take<float4>(E);
     sp.appear = ctx.fixed.take<float4>(E);
@@ -623,7 +625,7 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     uint32_t* block_offs = ctx.fixed.take<uint32_t>((E + 1 + kScanBlock - 1) / kScanBlock);
     uint2* rect_sorted = ctx.fixed.take<uint2>(E);
     uint2* rect_alt = ctx.fixed.take<uint2>(E);
-    sp.key_range = ctx.fixed.take<uint32_t>(2);
+    sp.key_range = d_hdr->key_range;
     sp.tight_rect = req.want_q ? 0 : 1;   // debug frames report the method's 3-sigma rectangles
     // compact rectangles carry their entry through the depth sort (no value stream)
     bool compact = !req.want_q && V <= kCompactViews;
@@ -639,18 +641,15 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     float4* state = ctx.fixed.take<float4>(L.total_pix);
     if (ctx.fixed.over) return {TIGAS_ERR_CUDA, "sliced workspace layout exceeds its reservation"};
 
-    // host -> device: the view table and the views' pixel offsets (pinned staging)
+    // host -> device in one copy from the pinned staging: the view table, the views'
+    // pixel offsets and the counters' start values (flags, kept entries, key range)
     sliced_stage_views(scene, req, ctx);
-    char* hv = reinterpret_cast<char*>(ctx.h_views);
-    TIGAS_CUDA_TRY(cudaMemcpyAsync(d_views, hv, sizeof(ViewParams) * V, cudaMemcpyHostToDevice, st));
-    TIGAS_CUDA_TRY(cudaMemcpyAsync(d_pix_base, hv + sizeof(ViewParams) * kMaxViews, sizeof(uint64_t) * V,
-                                   cudaMemcpyHostToDevice, st));
-    TIGAS_CUDA_TRY(cudaMemsetAsync(d_flags, 0, sizeof(uint32_t) * 2, st));
+    TIGAS_CUDA_TRY(cudaMemcpyAsync(d_hdr, ctx.h_header, sizeof(LaunchHeader), cudaMemcpyHostToDevice, st));
     if (sp.q_dbg) TIGAS_CUDA_TRY(cudaMemsetAsync(sp.q_dbg, 0, E * 4, st));
     if (req.want_counters) TIGAS_CUDA_TRY(cudaMemsetAsync(d_counters, 0, sizeof(unsigned long long) * 4, st));
 
     TIGAS_TRY(mark(kStPreprocess, true));
-    TIGAS_TRY(launch_preprocess(scene->view, d_views, V, sp, d_visible, st));
+    TIGAS_TRY(launch_preprocess(scene->view, d_views, V, sp, d_visible, st, /*counters_set=*/true));
     TIGAS_TRY(mark(kStPreprocess, false));
     TIGAS_TRY(mark(kStDepthSort, true));
     // depth order of every entry; its packed rectangle travels with it (no gather

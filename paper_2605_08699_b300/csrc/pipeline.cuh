@@ -93,6 +93,17 @@ struct Arena {
     void release();
 };
 
+// The values a sliced launch set starts from, laid out contiguously so that
+// one host-to-device copy from the context's pinned staging sets them all
+// (each copy or memset node in a launch set's graph costs a step of its own).
+struct LaunchHeader {
+    ViewParams views[kMaxViews];
+    uint64_t pix_base[kMaxViews];   // first pixel of each view in the per-pixel state
+    uint32_t flags[2];              // [overflow and timeout flags, passes of the depth sort]: zero
+    uint32_t visible[kMaxViews];    // kept entries per view: zero
+    uint32_t key_range[2];          // [min, max] of the kept depth keys: [0xFFFFFFFF, 0]
+};
+
 // Camera setup for one view (host, FP64 -> FP32): R = R_y(az) R_x(el),
 // W = R^T, limits of the EWA guard band.  tile_base: first global tile id.
 ViewParams make_view(const tigas_pose& pose, const tigas_intrinsics& k, int width, int height,
@@ -134,7 +145,7 @@ struct RenderContext {
     Arena jpeg;                        // frame encoder buffers
     uint64_t* h_total = nullptr;       // pinned readback of P
     uint32_t* h_flags = nullptr;       // pinned readback of overflow flags
-    ViewParams* h_views = nullptr;     // pinned view table
+    LaunchHeader* h_header = nullptr;  // pinned staging of a launch set's header (views and counters)
     std::vector<uint8_t*> dev_staging; // device frames for host outputs
     std::vector<size_t> staging_bytes;
     // captured sliced launch sets, keyed by their shape

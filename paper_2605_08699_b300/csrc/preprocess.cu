@@ -338,10 +338,10 @@ k_preprocess(SceneView scene, const ViewParams* __restrict__ views_g, int V, Spl
 }  // namespace
 
 Status launch_preprocess(const SceneView& scene, const ViewParams* views, int V, const SplatArrays& out,
-                         uint32_t* n_visible, cudaStream_t st) {
+                         uint32_t* n_visible, cudaStream_t st, bool counters_set) {
     if (V < 1 || V > kMaxViews) return {TIGAS_ERR_INVALID, "view count out of range"};
-    if (n_visible) TIGAS_CUDA_TRY(cudaMemsetAsync(n_visible, 0, sizeof(uint32_t) * V, st));
-    if (out.key_range) {   // [min, max] of the kept depth keys: start from [0xFFFFFFFF, 0]
+    if (n_visible && !counters_set) TIGAS_CUDA_TRY(cudaMemsetAsync(n_visible, 0, sizeof(uint32_t) * V, st));
+    if (out.key_range && !counters_set) {   // [min, max] of the kept depth keys: start from [0xFFFFFFFF, 0]
         TIGAS_CUDA_TRY(cudaMemsetAsync(out.key_range, 0xFF, sizeof(uint32_t), st));
         TIGAS_CUDA_TRY(cudaMemsetAsync(out.key_range + 1, 0, sizeof(uint32_t), st));
     }
