@@ -155,8 +155,8 @@ def cpu_baseline(scene, poses, width, height, budget_s: float = 15.0) -> dict:
 KERNEL_TRAFFIC = {
     "blend": {"sources": ["paper_2605_08699_b300/csrc/blend.cu", "paper_2605_08699_b300/csrc/sliced.cu",
                           "paper_2605_08699_b300/csrc/sliced.cuh"],
-              "sha1": "05a2c0c302f32cc492b98abf7be7a6a1140edf3c",
-              "bytes_per_view": 380628224 / 4},
+              "sha1": "c96534b7bd92ce32c57743516e5186e781f8371d",
+              "bytes_per_view": 380620800 / 4},
 }
 
 
