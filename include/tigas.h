@@ -404,8 +404,9 @@ tigas_status tigas_get_schedule(int n_views, tigas_schedule* schedule);
  *     first slice 1/8, 1/16, 1/32, 1/64, 1/128, 1/256 (one candidate for a
  *     single slice) x blend CTAs per SM all or 4 x blend batch 32 or 16):
  *     two untimed launch sets then `iters` (1..100) timed ones each; the four
- *     with the lowest median host time per launch set run 2 iters + 1 more
- *     times each, interleaved, and the lowest median of those wins.
+ *     with the lowest median device time per launch set (CUDA events around
+ *     its work on the render stream) run 2 iters + 1 more times each,
+ *     interleaved, and the lowest median of those wins.
  *  2. With that schedule, the views per launch set: the n_views views of a
  *     pose set rendered as launch sets of m = n_views, n_views / 2, ... views
  *     (each m that divides n_views, launch sets of m views taking the winner),
@@ -414,8 +415,8 @@ tigas_status tigas_get_schedule(int n_views, tigas_schedule* schedule);
  * The result becomes the schedule of the class of n_views (and, when m is
  * smaller than n_views, the winner without its views_per_set that of the
  * class of m); the other classes keep theirs.  It is written to *best
- * (best_ms: the winner's median host time per launch set of n_views views in
- * step 1).  Call it while no other render is running.  Errors: INVALID, and
+ * (best_ms: the winner's median device time per launch set of n_views views
+ * in step 1).  Call it while no other render is running.  Errors: INVALID, and
  * those of tigas_render_batch (every class's schedule in force before the
  * call is restored). */
 tigas_status tigas_autotune(tigas_scene* scene, int n_sets, int n_views, const tigas_pose* poses,

@@ -376,13 +376,38 @@ TIGAS_API tigas_status tigas_autotune(tigas_scene* scene, int n_sets, int n_view
     std::vector<std::vector<double>> times(cands.size());
     int next_set = 0;
     // the next pose set's views [v0, v0 + m) as one launch set; returns host ms
+    // device time of a launch set: events on the render stream around its work (the
+    // measure that back-to-back launch sets run at; host time adds the launch and the wait)
+    struct Timing {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        ~Timing() {
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+        }
+    } tm;
+    {
+        cudaError_t e = cudaEventCreate(&tm.e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&tm.e1);
+        if (e != cudaSuccess) return fail(TIGAS_ERR_CUDA, std::string("autotune events: ") + cudaGetErrorString(e));
+    }
     auto render_part = [&](int v0, int m, double* ms) -> Status {
         const size_t off = (size_t)next_set * n_views + v0;
-        const auto t0 = std::chrono::steady_clock::now();
-        Status s = do_render(sc, m, poses + off, intrs + off, widths + v0, heights + v0, outs_rgba8 + v0, nullptr,
-                             nullptr, TIGAS_SORT_SLICED, nullptr, nullptr, nullptr);
-        *ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-        return s;
+        Status err;
+        ContextGuard g;
+        g.ctx = acquire_context(&err);
+        if (!g.ctx) return err;
+        RenderContext& ctx = *g.ctx;
+        PendingRender p;
+        TIGAS_CUDA_TRY(cudaEventRecord(tm.e0, ctx.stream));
+        TIGAS_TRY(submit_render(ctx, sc, m, poses + off, intrs + off, widths + v0, heights + v0, outs_rgba8 + v0,
+                                nullptr, ctx.stream, TIGAS_SORT_SLICED, false, false, p));
+        TIGAS_CUDA_TRY(cudaEventRecord(tm.e1, ctx.stream));
+        TIGAS_CUDA_TRY(cudaStreamSynchronize(ctx.stream));
+        TIGAS_TRY(finish_render(ctx, ctx.stream, p));
+        float f = 0.0f;
+        TIGAS_CUDA_TRY(cudaEventElapsedTime(&f, tm.e0, tm.e1));
+        *ms = f;
+        return {};
     };
     // one launch set of all views (the next pose set) under schedule c; untimed ones
     // warm up (a shape's first launch set runs directly, the second is captured)

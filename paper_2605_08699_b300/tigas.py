@@ -651,7 +651,7 @@ def autotune(scene: SceneHandle, pose_sets: Sequence[Sequence], intrs: Sequence,
              heights: Sequence[int], outs: Sequence, iters: int = 3) -> tuple[dict, float]:
     """tigas_autotune: time the candidate schedules on launch sets of these
     resolutions, cycling through pose_sets (each a list of one pose per view),
-    and keep the fastest; returns (schedule, median ms per launch set)."""
+    and keep the fastest; returns (schedule, median device ms per launch set)."""
     V = len(widths)
     S = len(pose_sets)
     if any(len(ps) != V for ps in pose_sets) or len(intrs) != V:
