@@ -211,8 +211,10 @@ def roofline(stage_ms: dict, per_step: dict, peaks: dict, clocks: dict, steps: i
     timed_stage_ms (its events recorded inside the timed region) when given.
     Algorithmic work per launch set of the sliced schedule, in bytes (blend: FP32 operations):
       preprocess  12 B per (Gaussian, view) + (A - 12) B per Gaussian + 52 B per kept entry
-      depth_sort  passes run x 24 B per entry (key and 8-byte compact rectangle with its entry id,
-                  read and written), or x 32 B with wide rectangles (key, value, rectangle)
+      depth_sort  24 B per entry and pass run (key and 8-byte compact rectangle with its entry id,
+                  read and written), or 32 B with wide rectangles (key, value, rectangle): the
+                  first pass over every entry, the later ones over the entries they sort (all, or
+                  the near ones of a partial sort)
       scan        12 B per kept entry: the slice count reads the rectangle (8 B) and writes the
                   entry's offset within its block (4 B); the scan of the block sums is negligible
       emit        12 B per kept entry (rect, offset; + 4 B of order with wide rectangles)
@@ -228,7 +230,8 @@ def roofline(stage_ms: dict, per_step: dict, peaks: dict, clocks: dict, steps: i
     w = per_step
     bytes_per = {
         "preprocess": w["entries"] * 12 + w["gaussians"] * (w["attr_bytes"] - 12) + w["kept"] * 52,
-        "depth_sort": w["entries"] * w["depth_passes"] * (24 if w.get("compact_rect") else 32),
+        "depth_sort": (w["entries"] + w.get("depth_near", w["entries"]) * max(w["depth_passes"] - 1, 0))
+                      * (24 if w.get("compact_rect") else 32),
         "scan": w["kept"] * 12,
         "emit": w["kept"] * (12 if w.get("compact_rect") else 16) + w["pairs"] * 8,
         "pair_sort": w["pairs"] * w["sort_passes"] * 16,
@@ -353,7 +356,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     TX, TY = (W + 15) // 16, (H + 15) // 16
     per_step = {"pairs": st0["n_pairs"], "kept": st0["n_visible"], "evals": st0["blend_evals"],
                 "fetched": st0["blend_fetched"], "contribs": st0["blend_contribs"], "sort_passes": st0["sort_passes"],
-                "depth_passes": st0["depth_sort_passes"],
+                "depth_passes": st0["depth_sort_passes"], "depth_near": st0["depth_sort_near"],
                 # rectangles travel compact (with their entry id, no value stream) when every view
                 # has at most 127 x 127 tiles and there are at most 16 views
                 "compact_rect": int(V <= 16 and W <= 127 * 16 and H <= 127 * 16),

@@ -143,7 +143,11 @@ typedef struct {
     uint64_t blend_contribs;     /* evaluations that blended (alpha >= 1/255, pixel not stopped) */
     uint32_t depth_sort_passes;  /* SLICED: radix passes the depth sort ran (passes whose digit is the
                                     same for every key are skipped); 0 for the other schedules */
-    uint32_t reserved;
+    uint32_t depth_sort_near;    /* SLICED: entries the depth sort's passes after the first ran over:
+                                    every entry, or, for a launch set of three or more slices with
+                                    fixed pair capacities, the nearest ones, at least those before the
+                                    last slice (the last slice's pairs are sorted by tile and depth);
+                                    0 for the other schedules */
 } tigas_frame_stats;
 
 /* tigas_render with options (same passages: Sec. 4.1, 5.1, 4.2).  The float

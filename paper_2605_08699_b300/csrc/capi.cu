@@ -240,6 +240,9 @@ Status do_render(Scene* scene, int V, const tigas_pose* poses, const tigas_intri
         stats->blend_fetched = cnt[1];
         stats->blend_contribs = cnt[2];
         stats->depth_sort_passes = sort_mode == TIGAS_SORT_SLICED ? ctx.h_flags[1] : 0u;
+        const uint64_t near = res.near_split ? (uint64_t)ctx.h_flags[2] | ((uint64_t)ctx.h_flags[3] << 32)
+                                             : res.entries;
+        stats->depth_sort_near = sort_mode == TIGAS_SORT_SLICED ? (uint32_t)near : 0u;
     }
     if (dbg) {
         const uint32_t n = scene->view.n;

@@ -54,7 +54,15 @@ Status launch_emit_u64(const uint32_t* offsets, const SplatArrays& sp, const Vie
 //     are taken from k - kmin (0xFFFFFFFF -> kmax - kmin + 1), the same order,
 //     so keys spanning less than 2^24 need three passes; keys_out then holds
 //     the mapped keys (the first pass stores them, later passes read them);
-//   pay_in / pay_alt / pay_out: an 8-byte payload per key moved with it.
+//   pay_in / pay_alt / pay_out: an 8-byte payload per key moved with it;
+//   near_split (with key_range, after launch_near_split wrote key_range[2..3]
+//     and *d_near): a partial sort.  The keys below the threshold (the near
+//     ones, *d_near of them) end up in full order at the front; the others
+//     (the far ones, and 0xFFFFFFFF) follow in input order.  The first pass
+//     runs over every key and moves the far ones to the output buffers; the
+//     later passes run over the near ones only.  The near keys' digits are
+//     taken in base 255 for the first pass (m = k - kmin = 255 q + r: r, then
+//     q's bytes), so that digit 255 of the first pass is the far keys' alone.
 // With a payload, values_in, values_alt and values_out may all be null: no
 // value stream is read or written (the payload identifies each key).
 constexpr uint32_t kSortTimeoutFlag = 16u;
@@ -63,7 +71,19 @@ struct SortExtras {
     const uint2* pay_in = nullptr;
     uint2* pay_alt = nullptr;
     uint2* pay_out = nullptr;
+    bool near_split = false;
+    const uint64_t* d_near = nullptr;
 };
+// Threshold of a partial depth sort: the smallest bin boundary thr (bins of
+// (k - kmin) >> s, at most kSplitBins of them over [kmin, kmax]) below which
+// at least `target` of the n keys lie (all kept keys when fewer), from a
+// histogram of the keys.  key_range: [kmin, kmax, thr, split flag]; writes
+// key_range[2] = thr, key_range[3] = 1 and *d_near = the keys below thr.
+// hist: kSplitBins + 1 words, zero on entry (the last word counts finished
+// CTAs).  keys 16-byte aligned.
+constexpr int kSplitBins = 2048;
+Status launch_near_split(const uint32_t* keys, uint64_t n, uint32_t* key_range, uint64_t target, uint32_t* hist,
+                         uint64_t* d_near, cudaStream_t st);
 size_t radix_tmp_words(uint64_t n_cap);
 // Device word of tmp holding how many passes the last one-sweep sort using
 // tmp ran (valid once it completed; inputs of 2^30 keys or more leave it 0).

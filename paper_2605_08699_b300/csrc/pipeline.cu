@@ -223,7 +223,7 @@ Status RenderContext::init() {
     TIGAS_CUDA_TRY(cudaStreamCreateWithFlags(&copy_stream, cudaStreamNonBlocking));
     TIGAS_CUDA_TRY(cudaEventCreateWithFlags(&ev_rendered, cudaEventDisableTiming));
     TIGAS_CUDA_TRY(pinned_alloc(&h_total, sizeof(uint64_t) * (kMaxSlices + 2)));
-    TIGAS_CUDA_TRY(pinned_alloc(&h_flags, sizeof(uint32_t) * 2));
+    TIGAS_CUDA_TRY(pinned_alloc(&h_flags, sizeof(uint32_t) * 4));
     TIGAS_CUDA_TRY(pinned_alloc(&h_header, sizeof(LaunchHeader)));
     std::memset(h_header, 0, sizeof(LaunchHeader));
     h_header->key_range[0] = 0xFFFFFFFFu;
@@ -551,7 +551,7 @@ SlicedLayout sliced_layout(const Scene* scene, FrameRequest& req) {
     const size_t scan_words = scan_tmp_words(L.E + 1);
     L.tmp_words = presort_words > scan_words ? presort_words : scan_words;
     const uint64_t E = L.E;
-    size_t b = sizeof(ViewParams) * kMaxViews + 96 * 256;
+    size_t b = sizeof(LaunchHeader) + 96 * 256;
     b += E * (16 + 16 + 4 + 4 + 4 + 8 + (req.want_q ? 4 : 0));
     b += E * 4 * 4 + (E + 1) * 4 + E * 8 * 2;             // depth sort buffers, in-block offsets, rects (2)
     b += ((E + 1 + kScanBlock - 1) / kScanBlock) * 4 * 2; // block sums of the counts and their offsets
@@ -563,7 +563,25 @@ SlicedLayout sliced_layout(const Scene* scene, FrameRequest& req) {
     return L;
 }
 
-size_t pair_bytes_for(uint64_t P) { return P * 24 + radix_tmp_words(P) * 4 + 16 * 256; }
+// wide: room for 64-bit keys (a partial depth sort's last slice)
+size_t pair_bytes_for(uint64_t P, bool wide) { return P * (wide ? 36 : 24) + radix_tmp_words(P) * 4 + 16 * 256; }
+
+// A fixed-capacity launch set of three or more slices sorts by depth only the
+// entries before its last slice (and a margin): the last slice holds most of
+// the entries but few pairs, since most tiles have stopped by then, and its
+// pairs are sorted by (tile, depth) instead.  Frames are the same; only the
+// work differs.
+#ifndef TIGAS_NEAR_SPLIT
+#define TIGAS_NEAR_SPLIT 3   // fewest slices of a launch set with a partial depth sort
+#endif
+bool near_split_on(const SlicedLayout& L) { return L.S >= TIGAS_NEAR_SPLIT; }
+
+// End of slice i of S over K entries: K / F ... K, geometric.
+uint64_t slice_end(int i, int S, int F, uint64_t K) {
+    if (i == S - 1) return K;
+    const double f = S == 1 ? 1.0 : std::pow((double)F, (double)(i - (S - 1)) / (double)(S - 1));
+    return (uint64_t)std::ceil(f * (double)K);
+}
 
 }  // namespace
 
@@ -577,7 +595,7 @@ Status sliced_workspace(const Scene* scene, FrameRequest& req, uint64_t pair_cap
                         size_t* pair_bytes) {
     SlicedLayout L = sliced_layout(scene, req);
     *fixed_bytes = L.fixed_bytes;
-    *pair_bytes = pair_bytes_for(pair_cap);
+    *pair_bytes = pair_bytes_for(pair_cap, near_split_on(L));
     return {};
 }
 
@@ -592,9 +610,12 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     const int V = L.V, S = L.S;
     const uint64_t E = L.E;
     const uint32_t total_tiles = L.total_tiles;
+    // a partial depth sort (fixed capacity only: the exact path's slice ends
+    // need the kept count, read back after the sort)
+    const bool split = stat && near_split_on(L) && slice_end(S - 2, S, req.first_slice_inv, E) > 0;
 
     if (stat) {
-        if (ctx.fixed.cap < L.fixed_bytes || ctx.pairs.cap < pair_bytes_for(static_cap))
+        if (ctx.fixed.cap < L.fixed_bytes || ctx.pairs.cap < pair_bytes_for(static_cap, near_split_on(L)))
             return {TIGAS_ERR_INVALID, "static sliced schedule needs its workspace reserved first"};
     } else {
         TIGAS_TRY(ctx.fixed.reserve(L.fixed_bytes));
@@ -654,12 +675,21 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     TIGAS_TRY(mark(kStDepthSort, true));
     // depth order of every entry; its packed rectangle travels with it (no gather
     // afterwards), and digits count from the smallest kept depth key, so depths
-    // spanning less than 2^24 key steps skip the fourth pass on the device
+    // spanning less than 2^24 key steps skip the fourth pass on the device.
+    // Split: only the entries before the last slice need their order (the
+    // last slice's pairs are sorted by (tile, depth)), so the passes after the
+    // first run over the entries below a threshold that covers them.
     SortExtras dex;
     dex.key_range = sp.key_range;
     dex.pay_in = sp.rect;
     dex.pay_alt = rect_alt;
     dex.pay_out = rect_sorted;
+    if (split) {
+        TIGAS_TRY(launch_near_split(sp.depth_key, E, sp.key_range, slice_end(S - 2, S, req.first_slice_inv, E),
+                                    d_hdr->split_hist, &d_hdr->near, st));
+        dex.near_split = true;
+        dex.d_near = &d_hdr->near;
+    }
     TIGAS_TRY(radix_sort<uint32_t>(sp.depth_key, nullptr, pk_alt, compact ? nullptr : pv_alt, pk,
                                    compact ? nullptr : order, E, nullptr, 0, 32, tmp, st, nullptr, d_flags, &dex));
     TIGAS_TRY(mark(kStDepthSort, false));
@@ -679,12 +709,9 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
         for (int v = 0; v < V; ++v) K += ctx.h_misc[v];
     }
 
-    // geometric slice ends: K / 64 ... K
+    // geometric slice ends: K / first_slice_inv ... K
     uint64_t ends[kMaxSlices];
-    for (int i = 0; i < S; ++i) {
-        const double f = S == 1 ? 1.0 : std::pow((double)req.first_slice_inv, (double)(i - (S - 1)) / (double)(S - 1));
-        ends[i] = i == S - 1 ? K : (uint64_t)std::ceil(f * (double)K);
-    }
+    for (int i = 0; i < S; ++i) ends[i] = slice_end(i, S, req.first_slice_inv, K);
     uint64_t total_pairs = 0;
     int passes = 0;
     uint64_t a = 0;
@@ -695,11 +722,13 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     }
     uint32_t *keys_a = nullptr, *keys_b = nullptr, *keys_c = nullptr, *vals_a = nullptr, *vals_b = nullptr,
              *vals_c = nullptr, *stmp = nullptr;
+    // split: key buffers of 64-bit keys (the last slice's)
+    const uint64_t kw = split ? 2 : 1;
     auto take_pairs = [&](uint64_t cap) {
         ctx.pairs.reset();
-        keys_a = ctx.pairs.take<uint32_t>(cap);
-        keys_b = ctx.pairs.take<uint32_t>(cap);
-        keys_c = ctx.pairs.take<uint32_t>(cap);
+        keys_a = ctx.pairs.take<uint32_t>(kw * cap);
+        keys_b = ctx.pairs.take<uint32_t>(kw * cap);
+        keys_c = ctx.pairs.take<uint32_t>(kw * cap);
         vals_a = ctx.pairs.take<uint32_t>(cap);
         vals_b = ctx.pairs.take<uint32_t>(cap);
         vals_c = ctx.pairs.take<uint32_t>(cap);
@@ -736,26 +765,37 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
                 continue;
             }
             total_pairs += P;
-            TIGAS_TRY(ctx.pairs.reserve(pair_bytes_for(P)));
+            TIGAS_TRY(ctx.pairs.reserve(pair_bytes_for(P, false)));
             take_pairs(P);
             if (ctx.pairs.over) return {TIGAS_ERR_CUDA, "pair workspace layout exceeds its reservation"};
             cap = P;
         }
+        // the last slice of a split: its entries are in depth order only up to
+        // the threshold, so its pairs carry (tile, depth) keys
+        const bool wide = split && i == S - 1;
         TIGAS_TRY(mark(kStEmit, true));
         TIGAS_TRY(launch_emit_slice(compact ? nullptr : order, rect_sorted, a, b, inblock, block_offs, d_views, V,
-                                    done, keys_a, vals_a, cap, d_flags, compact, st));
+                                    done, keys_a, vals_a, cap, d_flags, compact, wide ? sp.depth_key : nullptr,
+                                    sp.key_range, st));
         TIGAS_TRY(mark(kStEmit, false));
         TIGAS_TRY(mark(kStPairSort, true));
-        TIGAS_TRY(radix_sort<uint32_t>(keys_a, vals_a, keys_b, vals_b, keys_c, vals_c, cap, stat ? d_P : nullptr, 0,
-                                       L.tile_bits, stmp, st, &passes, d_flags));
+        if (wide)
+            TIGAS_TRY(radix_sort<uint64_t>(reinterpret_cast<uint64_t*>(keys_a), vals_a,
+                                           reinterpret_cast<uint64_t*>(keys_b), vals_b,
+                                           reinterpret_cast<uint64_t*>(keys_c), vals_c, cap, d_P, 0,
+                                           32 + L.tile_bits, stmp, st, nullptr, d_flags));
+        else
+            TIGAS_TRY(radix_sort<uint32_t>(keys_a, vals_a, keys_b, vals_b, keys_c, vals_c, cap, stat ? d_P : nullptr,
+                                           0, L.tile_bits, stmp, st, &passes, d_flags));
         TIGAS_TRY(mark(kStPairSort, false));
         TIGAS_TRY(mark(kStRanges, true));
-        // the pair sort's second pass sorted key >> 8 (a one-sweep sort of 9 to 16 key bits):
-        // its digit bases bound each run of 256 tiles
-        const uint32_t* hi_bases =
-            cap < (1ull << 30) && L.tile_bits > 8 && L.tile_bits <= 16 ? radix_digit_bases(stmp, 1) : nullptr;
+        // the pass over the tile's high byte (the second of a one-sweep sort of 9 to 16
+        // key bits; the sixth of 64-bit keys): its digit bases bound each run of 256 tiles
+        const uint32_t* hi_bases = cap < (1ull << 30) && L.tile_bits > 8 && L.tile_bits <= 16
+                                       ? radix_digit_bases(stmp, wide ? 5 : 1)
+                                       : nullptr;
         TIGAS_TRY(launch_ranges_active(keys_c, cap, stat ? d_P : nullptr, ranges, total_tiles, done, active, d_misc,
-                                       d_flags, hi_bases, strips, st));
+                                       d_flags, hi_bases, strips, wide, st));
         TIGAS_TRY(mark(kStRanges, false));
         TIGAS_TRY(mark(kStBlend, true));
         TIGAS_TRY(launch_blend_slice(ranges, vals_c, sp, d_views, V, (uint32_t)E, scene->view.bg,
@@ -766,7 +806,8 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     }
     // the background of every tile no slice blended
     TIGAS_TRY(launch_fill_unseen(d_views, V, total_tiles, strips, scene->view.bg, st));
-    TIGAS_CUDA_TRY(cudaMemcpyAsync(ctx.h_flags, d_flags, sizeof(uint32_t) * 2, cudaMemcpyDeviceToHost, st));
+    // the flags and the near count of a partial depth sort
+    TIGAS_CUDA_TRY(cudaMemcpyAsync(ctx.h_flags, d_flags, sizeof(uint32_t) * 4, cudaMemcpyDeviceToHost, st));
     if (stat) TIGAS_CUDA_TRY(cudaMemcpyAsync(ctx.h_total, d_total, sizeof(uint64_t) * S, cudaMemcpyDeviceToHost, st));
     if (res) {
         res->pairs = total_pairs;   // static: read ctx.h_total after the stream completes
@@ -777,6 +818,8 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
         res->splats = sp;
         res->d_visible = d_visible;
         res->d_counters = req.want_counters ? d_counters : nullptr;
+        res->near_split = split;
+        res->entries = E;
     }
     return {};
 }

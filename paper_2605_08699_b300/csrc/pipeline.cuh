@@ -2,6 +2,7 @@
 // sequence K1 -> (depth sort) -> K2 -> K3 -> K4 -> K5 -> K6.
 #pragma once
 
+#include <cstddef>
 #include <mutex>
 #include <vector>
 
@@ -100,9 +101,15 @@ struct LaunchHeader {
     ViewParams views[kMaxViews];
     uint64_t pix_base[kMaxViews];   // first pixel of each view in the per-pixel state
     uint32_t flags[2];              // [overflow and timeout flags, passes of the depth sort]: zero
+    uint64_t near;                  // entries in full depth order (a partial depth sort): zero; read back
+                                    // with the flags
     uint32_t visible[kMaxViews];    // kept entries per view: zero
-    uint32_t key_range[2];          // [min, max] of the kept depth keys: [0xFFFFFFFF, 0]
+    uint32_t key_range[4];          // [min, max] of the kept depth keys: [0xFFFFFFFF, 0]; a partial depth
+                                    // sort's threshold and flag: zero
+    uint32_t split_hist[kSplitBins + 1];   // the threshold's depth histogram and finished-CTA count: zero
 };
+static_assert(offsetof(LaunchHeader, near) == offsetof(LaunchHeader, flags) + 8,
+              "the flags and the near count are read back in one copy");
 
 // Camera setup for one view (host, FP64 -> FP32): R = R_y(az) R_x(el),
 // W = R^T, limits of the EWA guard band.  tile_base: first global tile id.
@@ -129,6 +136,8 @@ struct FrameResult {
     unsigned long long* d_counters = nullptr;   // [evals, fetched, blends] when requested
     int graph_slices = 0;                       // replayed graph: pairs = sum of ctx.h_total[0..slices)
     bool direct_static = false;                 // fixed-capacity launch set run directly, not from a graph
+    bool near_split = false;                    // partial depth sort: ctx.h_flags[2..3] hold its near count
+    uint64_t entries = 0;                       // (Gaussian, view) entries of the launch set
 };
 
 // Render state of one in-flight frame or launch set: stream, arenas, pinned staging.
@@ -144,7 +153,7 @@ struct RenderContext {
     Arena pairs;                       // per-pair buffers
     Arena jpeg;                        // frame encoder buffers
     uint64_t* h_total = nullptr;       // pinned readback of P
-    uint32_t* h_flags = nullptr;       // pinned readback of overflow flags
+    uint32_t* h_flags = nullptr;       // pinned readback of the flags and a partial depth sort's near count
     LaunchHeader* h_header = nullptr;  // pinned staging of a launch set's header (views and counters)
     std::vector<uint8_t*> dev_staging; // device frames for host outputs
     std::vector<size_t> staging_bytes;

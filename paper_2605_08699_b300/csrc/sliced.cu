@@ -231,8 +231,10 @@ k_count_slice(const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b, con
 // live tiles the entry had in earlier steps).  Stores stay coalesced, and
 // entries of a few tiles share a step instead of taking one each (measured
 // against one entry per step: emit 0.300 -> 0.261 ms per 8-view launch set).
-template <bool COMPACT>
-__device__ inline void emit_warp_segmented(uint32_t m, uint2 r, uint32_t e, uint32_t pos,
+// WIDE: 64-bit keys (tile << 32 | dk), dk the lane's entry's depth key minus
+// the smallest kept one, for a slice whose entries are not in depth order.
+template <bool COMPACT, bool WIDE>
+__device__ inline void emit_warp_segmented(uint32_t m, uint2 r, uint32_t e, uint32_t pos, uint32_t dk,
                                            const uint32_t* s_tb, const uint32_t* s_tx,
                                            const uint32_t* __restrict__ done, uint32_t* __restrict__ keys,
                                            uint32_t* __restrict__ values, uint64_t pair_cap,
@@ -266,6 +268,7 @@ __device__ inline void emit_warp_segmented(uint32_t m, uint2 r, uint32_t e, uint
         const uint32_t pj = __shfl_sync(kFull, pre, j), wj = __shfl_sync(kFull, w, j);
         const uint32_t txj = __shfl_sync(kFull, tx, j), t0j = __shfl_sync(kFull, t0, j);
         const uint32_t posj = __shfl_sync(kFull, pos, j), ej = __shfl_sync(kFull, e, j);
+        const uint32_t dkj = WIDE ? __shfl_sync(kFull, dk, j) : 0u;
         const float rj = __shfl_sync(kFull, rinv, j);
         const bool valid = f < A;
         const uint32_t local = valid ? f - pj : 0u;
@@ -280,7 +283,10 @@ __device__ inline void emit_warp_segmented(uint32_t m, uint2 r, uint32_t e, uint
         if (live) {
             const uint64_t p = (uint64_t)posj + rank;
             if (p < pair_cap) {
-                keys[p] = t;
+                if (WIDE)
+                    reinterpret_cast<uint2*>(keys)[p] = make_uint2(dkj, t);
+                else
+                    keys[p] = t;
                 values[p] = ej;
             } else {
                 atomicOr(overflow, 1u);
@@ -297,15 +303,17 @@ __device__ inline void emit_warp_segmented(uint32_t m, uint2 r, uint32_t e, uint
 // its rectangles, then the entries with pairs are written group by group.  A
 // larger J launches fewer CTAs for slices of many entries whose tiles have
 // mostly stopped.  COMPACT: the entry id travels in the rectangle's second
-// word (order unused).
+// word (order unused).  WIDE: 64-bit (tile, depth) keys (depth_key: the keys
+// in entry order, key_range[0] their smallest kept value).
 constexpr int kEmitThreads = 256;
-template <bool COMPACT, int J>
+template <bool COMPACT, int J, bool WIDE>
 __global__ void __launch_bounds__(kEmitThreads)
 k_emit_slice(const uint32_t* __restrict__ order, const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b,
              const uint32_t* __restrict__ inblock, const uint32_t* __restrict__ block_offs,
              const ViewParams* __restrict__ views_g, int V,
              const uint32_t* __restrict__ done, uint32_t* __restrict__ keys, uint32_t* __restrict__ values,
-             uint64_t pair_cap, uint32_t* __restrict__ overflow) {
+             uint64_t pair_cap, uint32_t* __restrict__ overflow, const uint32_t* __restrict__ depth_key,
+             const uint32_t* __restrict__ key_range) {
     __shared__ uint32_t s_tb[kMaxViews], s_tx[kMaxViews];
     for (int k = threadIdx.x; k < V; k += blockDim.x) {
         s_tb[k] = views_g[k].tile_base;
@@ -338,11 +346,16 @@ k_emit_slice(const uint32_t* __restrict__ order, const uint2* __restrict__ rect_
         rr[j] = cnt[j] > 0 ? rect_sorted[k] : make_uint2(0u, 0u);
         ee[j] = COMPACT ? rr[j].y : (cnt[j] > 0 ? order[k] : 0u);
     }
+    uint32_t dk[J];
+    const uint32_t kmin = WIDE ? key_range[0] : 0u;
+#pragma unroll
+    for (int j = 0; j < J; ++j) dk[j] = WIDE && cnt[j] > 0 ? depth_key[ee[j]] - kmin : 0u;
 #pragma unroll
     for (int j = 0; j < J; ++j) {   // unrolled: the per-lane arrays stay in registers
         const uint32_t m = __ballot_sync(kFull, cnt[j] > 0);
         if (m)
-            emit_warp_segmented<COMPACT>(m, rr[j], ee[j], pos[j], s_tb, s_tx, done, keys, values, pair_cap, overflow);
+            emit_warp_segmented<COMPACT, WIDE>(m, rr[j], ee[j], pos[j], dk[j], s_tb, s_tx, done, keys, values,
+                                               pair_cap, overflow);
     }
 }
 
@@ -361,15 +374,19 @@ k_emit_slice(const uint32_t* __restrict__ order, const uint2* __restrict__ rect_
 // whole from the back (count n_active[1]).  The blend's dynamic scheduler
 // takes the three regions in that order, so the longest lists start first
 // and the short ones fill the tail.
+// KS: words per key (1: 32-bit tile keys; 2: the high words of 64-bit
+// (tile, depth) keys, `keys` pointing at the first key's high word).
+template <int KS>
 __device__ inline uint64_t lower_bound_u32(const uint32_t* __restrict__ keys, uint64_t lo, uint64_t hi, uint32_t t) {
     while (lo < hi) {
         const uint64_t mid = (lo + hi) >> 1;
-        if (keys[mid] < t) lo = mid + 1; else hi = mid;
+        if (keys[KS * mid] < t) lo = mid + 1; else hi = mid;
     }
     return lo;
 }
 
 constexpr int kRangeSample = 1024;
+template <int KS>
 __global__ void __launch_bounds__(256)
 k_ranges_active(const uint32_t* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, uint2* __restrict__ ranges,
                 uint32_t n_tiles, const uint32_t* __restrict__ done, uint32_t* __restrict__ active,
@@ -386,7 +403,7 @@ k_ranges_active(const uint32_t* __restrict__ keys, uint64_t n_cap, const uint64_
         const uint32_t w = strips[t];
         if (w & kStripSeenNow) strips[t] = (w & ~kStripSeenNow) | kStripSeen;
     }
-    if (t == 0 && n > 0 && keys[n - 1] >= n_tiles) atomicOr(overflow, 2u);
+    if (t == 0 && n > 0 && keys[KS * (n - 1)] >= n_tiles) atomicOr(overflow, 2u);
     if (threadIdx.x < 2) {
         uint64_t x;
         if (hi_bases) {
@@ -394,14 +411,14 @@ k_ranges_active(const uint32_t* __restrict__ keys, uint64_t n_cap, const uint64_
             x = h < 256u ? hi_bases[h] : n;
             if (x > n) x = n;
         } else {
-            x = lower_bound_u32(keys, 0, n, t0 + 256u * threadIdx.x);
+            x = lower_bound_u32<KS>(keys, 0, n, t0 + 256u * threadIdx.x);
         }
         s_run[threadIdx.x] = x;
     }
     __syncthreads();
     const uint64_t L = s_run[0], R = s_run[1] > L ? s_run[1] : L, span = R - L;
     for (int k = threadIdx.x; k < kRangeSample; k += 256)
-        s_sample[k] = span ? keys[L + (uint64_t)k * span / kRangeSample] : 0xFFFFFFFFu;
+        s_sample[k] = span ? keys[KS * (L + (uint64_t)k * span / kRangeSample)] : 0xFFFFFFFFu;
     __syncthreads();
     {
         // first sample >= t, then the keys after the sample before it
@@ -412,7 +429,7 @@ k_ranges_active(const uint32_t* __restrict__ keys, uint64_t n_cap, const uint64_
         }
         const uint64_t a = lo == 0 ? L : L + (uint64_t)(lo - 1) * span / kRangeSample + 1;
         const uint64_t b = lo == kRangeSample ? R : L + (uint64_t)lo * span / kRangeSample;
-        s_lo[threadIdx.x] = (uint32_t)lower_bound_u32(keys, a, b, t);
+        s_lo[threadIdx.x] = (uint32_t)lower_bound_u32<KS>(keys, a, b, t);
     }
     __syncthreads();
     bool act = false, heavy = false, longest = false;
@@ -512,22 +529,33 @@ Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64
                          const uint32_t* inblock, const uint32_t* block_offs, const ViewParams* views, int V,
                          const uint32_t* done,
                          uint32_t* keys, uint32_t* values, uint64_t pair_cap, uint32_t* overflow, bool compact,
-                         cudaStream_t st) {
+                         const uint32_t* wide_depth, const uint32_t* key_range, cudaStream_t st) {
     if (b <= a) return {};
+    if (wide_depth && (!key_range || (reinterpret_cast<uintptr_t>(keys) & 7u)))
+        return {TIGAS_ERR_INVALID, "wide emit needs the key range and 8-byte aligned keys"};
     // entries per lane: the largest J in {1, 2, 4, 8} that still leaves about
     // 4 waves of 8 CTAs per SM (slices with many pairs per entry want the warps)
     const uint64_t n = b - a;
     int J = 1;
     while (J < 8 && n >= (uint64_t)(2 * J) * kEmitThreads * kSmCount * 8 * 4) J *= 2;
     const unsigned grid = (unsigned)((n + (uint64_t)J * kEmitThreads - 1) / ((uint64_t)J * kEmitThreads));
-#define TIGAS_EMIT(JJ)                                                                                              \
-    do {                                                                                                            \
-        if (compact)                                                                                                \
-            k_emit_slice<true, JJ><<<grid, kEmitThreads, 0, st>>>(order, rect_sorted, a, b, inblock, block_offs,     \
-                                                                  views, V, done, keys, values, pair_cap, overflow); \
-        else                                                                                                        \
-            k_emit_slice<false, JJ><<<grid, kEmitThreads, 0, st>>>(order, rect_sorted, a, b, inblock, block_offs,    \
-                                                                   views, V, done, keys, values, pair_cap, overflow); \
+#define TIGAS_EMIT2(CC, JJ)                                                                                       \
+    do {                                                                                                          \
+        if (wide_depth)                                                                                           \
+            k_emit_slice<CC, JJ, true><<<grid, kEmitThreads, 0, st>>>(order, rect_sorted, a, b, inblock,           \
+                                                                      block_offs, views, V, done, keys, values,   \
+                                                                      pair_cap, overflow, wide_depth, key_range); \
+        else                                                                                                      \
+            k_emit_slice<CC, JJ, false><<<grid, kEmitThreads, 0, st>>>(order, rect_sorted, a, b, inblock,          \
+                                                                       block_offs, views, V, done, keys, values,  \
+                                                                       pair_cap, overflow, nullptr, nullptr);     \
+    } while (0)
+#define TIGAS_EMIT(JJ)                \
+    do {                              \
+        if (compact)                  \
+            TIGAS_EMIT2(true, JJ);    \
+        else                          \
+            TIGAS_EMIT2(false, JJ);   \
     } while (0)
     switch (J) {
         case 1: TIGAS_EMIT(1); break;
@@ -536,17 +564,23 @@ Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64
         default: TIGAS_EMIT(8); break;
     }
 #undef TIGAS_EMIT
+#undef TIGAS_EMIT2
     TIGAS_LAUNCHED();
     return {};
 }
 
 Status launch_ranges_active(const uint32_t* keys, uint64_t n_cap, const uint64_t* d_n, uint2* ranges,
                             uint32_t n_tiles, const uint32_t* done, uint32_t* active, uint32_t* n_active,
-                            uint32_t* overflow, const uint32_t* hi_bases, uint32_t* strips, cudaStream_t st) {
+                            uint32_t* overflow, const uint32_t* hi_bases, uint32_t* strips, bool wide,
+                            cudaStream_t st) {
     if (n_tiles == 0) return {};
     if (hi_bases && n_tiles > 65536u) return {TIGAS_ERR_INVALID, "second-pass digit bases need tile ids of 16 bits"};
-    k_ranges_active<<<(n_tiles + 255) / 256, 256, 0, st>>>(keys, n_cap, d_n, ranges, n_tiles, done, active, n_active,
-                                                           overflow, hi_bases, strips);
+    if (wide)   // the tile is the high word of each 64-bit key
+        k_ranges_active<2><<<(n_tiles + 255) / 256, 256, 0, st>>>(keys + 1, n_cap, d_n, ranges, n_tiles, done,
+                                                                  active, n_active, overflow, hi_bases, strips);
+    else
+        k_ranges_active<1><<<(n_tiles + 255) / 256, 256, 0, st>>>(keys, n_cap, d_n, ranges, n_tiles, done, active,
+                                                                  n_active, overflow, hi_bases, strips);
     TIGAS_LAUNCHED();
     return {};
 }

@@ -71,10 +71,14 @@ Status launch_count_slice(const uint2* rect_sorted, uint64_t a, uint64_t b, cons
 // block_offs[(k - a) / kScanBlock] + inblock[k - a] (block_offs: the exclusive
 // scan of the count kernel's block sums).  The entry of k is order[k], or the
 // second word of a compact rectangle (order may then be null).
+// wide_depth (the depth keys in entry order, key_range[0] the smallest kept
+// one): keys holds 64-bit keys (tile << 32 | depth key - key_range[0]), for a
+// slice whose entries are not in depth order; null: 32-bit tile keys.
 Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64_t a, uint64_t b,
                          const uint32_t* inblock, const uint32_t* block_offs, const ViewParams* views, int V,
                          const uint32_t* done, uint32_t* keys, uint32_t* values, uint64_t pair_cap,
-                         uint32_t* overflow, bool compact, cudaStream_t st);
+                         uint32_t* overflow, bool compact, const uint32_t* wide_depth, const uint32_t* key_range,
+                         cudaStream_t st);
 
 // Tile ranges of the slice's sorted keys, and the list of tiles with pairs
 // that are not done, in three regions of `active` (4 n_tiles items): the
@@ -87,11 +91,13 @@ Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64
 // is over).
 // The key count is min(*d_n, n_cap) when d_n is given, else n_cap.
 // hi_bases: null, or 256 words whose word h is the first position of a key
-// with key >> 8 == h (the second-pass digit bases of the sort that produced
-// `keys`); n_tiles <= 65536.
+// whose tile t has t >> 8 == h (the digit bases of the pass over the tile's
+// high byte in the sort that produced `keys`); n_tiles <= 65536.
+// wide: keys holds 64-bit (tile << 32 | depth) keys.
 Status launch_ranges_active(const uint32_t* keys, uint64_t n_cap, const uint64_t* d_n, uint2* ranges,
                             uint32_t n_tiles, const uint32_t* done, uint32_t* active, uint32_t* n_active,
-                            uint32_t* overflow, const uint32_t* hi_bases, uint32_t* strips, cudaStream_t st);
+                            uint32_t* overflow, const uint32_t* hi_bases, uint32_t* strips, bool wide,
+                            cudaStream_t st);
 
 // Blend of the active tiles of one slice: persistent CTAs take tiles from the
 // active list, composite the slice's entries onto each pixel's carried state,

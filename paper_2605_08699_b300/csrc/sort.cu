@@ -451,6 +451,11 @@ struct OsRoute {
     void* dst_k;
     uint32_t* dst_v;
     uint2* dst_p;
+    // the first pass of a partial sort: where the far keys (digit 255) go, the
+    // output buffers, which the later passes over the near keys do not reach
+    void* far_k;             // null: no partial sort
+    uint32_t* far_v;
+    uint2* far_p;
     uint32_t active;
     uint32_t pad;
 };
@@ -481,18 +486,34 @@ __device__ inline void st_relaxed(uint32_t* p, uint32_t v) {
 // keys only): k - kmin, and 0xFFFFFFFF (the "culled" key) -> kmax - kmin + 1,
 // an order-preserving map onto [0, kmax - kmin + 1], so the high digits of
 // keys spanning less than 2^24 are all zero and their pass is skipped.
+// With a split threshold thr (range[3] set): m = k - kmin below thr -> (q << 8)
+// | r for m = 255 q + r (the same order; the low byte never reaches 255), and
+// m >= thr or 0xFFFFFFFF -> 0xFFFFFFFF, the first pass's digit 255.
 struct KeyMap {
-    uint32_t kmin = 0, span = 0;
-    bool on = false;
+    uint32_t kmin = 0, span = 0, thr = 0;
+    bool on = false, split = false;
     __device__ inline void load(const uint32_t* range) {
         on = range != nullptr;
         if (on) {
             kmin = range[0];
             span = range[1] - kmin + 1u;
+            split = range[3] != 0u;
+            thr = range[2];
         }
     }
-    __device__ inline uint32_t operator()(uint32_t k) const { return !on ? k : (k == 0xFFFFFFFFu ? span : k - kmin); }
+    __device__ static inline uint32_t base255(uint32_t m) {
+        const uint32_t q = m / 255u;
+        return (q << 8) | (m - q * 255u);
+    }
+    __device__ inline uint32_t operator()(uint32_t k) const {
+        if (!on) return k;
+        if (!split) return k == 0xFFFFFFFFu ? span : k - kmin;
+        const uint32_t m = k - kmin;
+        return k == 0xFFFFFFFFu || m >= thr ? 0xFFFFFFFFu : base255(m);
+    }
     __device__ inline uint64_t operator()(uint64_t k) const { return k; }
+    // the largest mapped key other than a split's far keys
+    __device__ inline uint32_t top() const { return !split ? span : thr == 0u ? 0u : base255(thr - 1u); }
 };
 
 // Lanes of the warp whose digit equals this lane's: the AND over the digit's
@@ -580,11 +601,14 @@ k_os_hist(const K* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, int b
     }
     KeyMap km;
     km.load(range);
-    // mapped keys lie in [0, span]: digits above its top bit are zero for every key,
-    // so their histograms are not counted (they stay zero, and the pass is skipped)
+    // mapped keys lie in [0, top]: digits above its top bit are zero for every key,
+    // so their histograms are not counted (they stay zero, and the pass is skipped);
+    // a split's far keys count as digit 255 in the passes that are counted, which
+    // places no near key (255 is the last digit) and the later passes never read
     int hp = passes;
     if (km.on) {
-        const int bits = km.span == 0u ? 1 : 32 - __clz((int)km.span);
+        const uint32_t top = km.top();
+        const int bits = top == 0u ? 1 : 32 - __clz((int)top);
         const int need = (bits - begin_bit + 7) / 8;
         hp = need < 1 ? 1 : (need < passes ? need : passes);
     }
@@ -664,7 +688,7 @@ k_os_hist(const K* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, int b
 // pass 0 always runs, a later pass only if more than one of its digits occurs.
 __global__ void __launch_bounds__(256) k_os_bases(const uint32_t* __restrict__ ghist, uint32_t* __restrict__ gbase,
                                                   int passes, OsRoute* __restrict__ routes, OsBuffers bufs,
-                                                  uint32_t* __restrict__ n_active_out) {
+                                                  uint32_t* __restrict__ n_active_out, bool near_split) {
     __shared__ uint32_t ws[9];
     __shared__ uint32_t act[8];
     for (int p = 0; p < passes; ++p) {
@@ -694,6 +718,11 @@ __global__ void __launch_bounds__(256) k_os_bases(const uint32_t* __restrict__ g
                 r.dst_k = to_out ? bufs.out_k : bufs.alt_k;
                 r.dst_v = to_out ? bufs.out_v : bufs.alt_v;
                 r.dst_p = bufs.in_p ? (to_out ? bufs.out_p : bufs.alt_p) : nullptr;
+                if (near_split && i == 0) {
+                    r.far_k = bufs.out_k;
+                    r.far_v = bufs.out_v;
+                    r.far_p = bufs.in_p ? bufs.out_p : nullptr;
+                }
                 sk = r.dst_k;
                 sv = r.dst_v;
                 spp = r.dst_p;
@@ -782,6 +811,10 @@ k_os_scatter(const OsRoute* __restrict__ route, uint64_t n_cap, const uint64_t* 
     K* __restrict__ keys_out = static_cast<K*>(route->dst_k);
     uint32_t* __restrict__ vals_out = route->dst_v;
     uint2* __restrict__ pays_out = route->dst_p;
+    // a partial sort's first pass: digit 255 (the far keys) goes to the output buffers
+    K* const far_k = static_cast<K*>(route->far_k);
+    uint32_t* const far_v = route->far_v;
+    uint2* const far_p = route->far_p;
     const bool has_vals = PAY != kPayOnly && vals_out != nullptr;   // no value stream: the payload identifies each key
     // The payload sort (few, large launches) walks back for its digit offsets
     // only after its tile is sorted in shared memory, so the wait overlaps that
@@ -899,9 +932,10 @@ k_os_scatter(const OsRoute* __restrict__ route, uint64_t n_cap, const uint64_t* 
             const uint32_t d = (uint32_t)(kk >> shift) & mask;
             const uint32_t g = sm.gshift[d] + j;
             if (g < n) {
-                keys_out[g] = kk;
-                if (has_vals) vals_out[g] = sm.vals[j];
-                if (PAY) pays_out[g] = sm.pays[j];
+                const bool far = far_k != nullptr && d == 255u;
+                (far ? far_k : keys_out)[g] = kk;
+                if (has_vals) (far ? far_v : vals_out)[g] = sm.vals[j];
+                if (PAY) (far ? far_p : pays_out)[g] = sm.pays[j];
             }
         }
     }
@@ -965,20 +999,23 @@ Status radix_sort_onesweep(const K* keys_in, const uint32_t* values_in, K* keys_
     TIGAS_LAUNCHED();
     OsBuffers bufs{keys_in, values_in, PAY ? ex->pay_in : nullptr, keys_alt, values_alt, PAY ? ex->pay_alt : nullptr,
                    keys_out, values_out, PAY ? ex->pay_out : nullptr};
-    k_os_bases<<<1, 256, 0, st>>>(ghist, gbase, passes, routes, bufs, counters + 15);
+    const bool split = MAP && ex->near_split;
+    k_os_bases<<<1, 256, 0, st>>>(ghist, gbase, passes, routes, bufs, counters + 15, split);
     TIGAS_LAUNCHED();
     for (int p = 0; p < passes; ++p) {
         const int shift = begin_bit + 8 * p;
         const int nb = min(8, end_bit - shift);
+        // a partial sort's later passes run over the near keys only
+        const uint64_t* pn = split && p > 0 ? ex->d_near : d_n;
         if (MAP && p > 0) {
             // the first pass (always run) stored mapped keys: later passes read them as they are
             TIGAS_TRY((ensure_os_smem<K, PAY, false>()));
             k_os_scatter<K, PAY, false><<<(unsigned)chunks, T, sizeof(OsSmem<K, PAY>), st>>>(
-                routes + p, n_cap, d_n, shift, nb, gbase + p * 256, status + (size_t)p * chunks * 256, counters + p,
+                routes + p, n_cap, pn, shift, nb, gbase + p * 256, status + (size_t)p * chunks * 256, counters + p,
                 flags, kSpinLimit, nullptr);
         } else {
             k_os_scatter<K, PAY, MAP><<<(unsigned)chunks, T, sizeof(OsSmem<K, PAY>), st>>>(
-                routes + p, n_cap, d_n, shift, nb, gbase + p * 256, status + (size_t)p * chunks * 256, counters + p,
+                routes + p, n_cap, pn, shift, nb, gbase + p * 256, status + (size_t)p * chunks * 256, counters + p,
                 flags, kSpinLimit, range);
         }
         TIGAS_LAUNCHED();
@@ -1036,7 +1073,7 @@ Status debug_lookback_enqueue(int spin_limit, uint32_t* buf, uint32_t* flags, cu
     k_probe_init<<<16, 256, 0, st>>>(buf);
     OsBuffers bufs{keys, nullptr, nullptr, out, vals, nullptr, out, vals, nullptr};
     k_os_hist<K, 8, false><<<4, 512, 0, st>>>(keys, kProbeN, nullptr, 0, 8, ghist, nullptr, nullptr, 0, 1);
-    k_os_bases<<<1, 256, 0, st>>>(ghist, gbase, 1, route, bufs, nullptr);
+    k_os_bases<<<1, 256, 0, st>>>(ghist, gbase, 1, route, bufs, nullptr, false);
     k_os_scatter<K, kPayNone, false><<<1, T, sizeof(OsSmem<K, kPayNone>), st>>>(
         route, kProbeN, nullptr, 0, 8, gbase, status, misc, flags ? flags : misc + 1, spin_limit, nullptr);
     g_launches.fetch_add(4, std::memory_order_relaxed);
@@ -1062,6 +1099,92 @@ Status debug_lookback_timeout(int spin_limit, bool* timed_out) {
     return st;
 }
 
+namespace {
+// Histogram of (k - kmin) >> shift over the kept keys (run-length aggregated
+// shared-memory counts, as in the sort's histogram), then, in the CTA that
+// finishes last, the first bin whose inclusive count reaches the target.
+constexpr int kSplitThreads = 1024;
+__global__ void __launch_bounds__(kSplitThreads)
+k_near_split(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict__ range, uint64_t target,
+             uint32_t* __restrict__ ghist, uint64_t* __restrict__ d_near) {
+    __shared__ uint32_t h[kSplitBins];
+    __shared__ uint32_t ws[kSplitThreads / 32 + 1];
+    __shared__ int last;
+    for (int i = threadIdx.x; i < kSplitBins; i += kSplitThreads) h[i] = 0;
+    __syncthreads();
+    const uint32_t kmin = range[0], kmax = range[1];
+    const bool any = kmin <= kmax;   // at least one kept key
+    const uint32_t top = any ? kmax - kmin : 0u;
+    const int bits = top == 0u ? 0 : 32 - __clz((int)top);
+    const int shift = bits > 11 ? bits - 11 : 0;   // top >> shift < kSplitBins
+    uint32_t cur = 0xFFFFFFFFu, run = 0;
+    auto count = [&](uint32_t k) {
+        if (k == 0xFFFFFFFFu) return;   // culled: never near
+        const uint32_t b = (k - kmin) >> shift;
+        if (b == cur) {
+            ++run;
+        } else {
+            if (run) atomicAdd(&h[cur], run);
+            cur = b;
+            run = 1;
+        }
+    };
+    const uint4* __restrict__ k4 = reinterpret_cast<const uint4*>(keys);
+    const uint32_t nv = n / 4;
+    for (uint32_t v = blockIdx.x * kSplitThreads + threadIdx.x; v < nv; v += gridDim.x * kSplitThreads) {
+        const uint4 q = k4[v];
+        count(q.x);
+        count(q.y);
+        count(q.z);
+        count(q.w);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < n - nv * 4) count(keys[nv * 4 + threadIdx.x]);
+    if (run) atomicAdd(&h[cur], run);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSplitBins; i += kSplitThreads)
+        if (h[i]) atomicAdd(&ghist[i], h[i]);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&ghist[kSplitBins], 1u) == gridDim.x - 1u;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // every CTA's counts are in: thread t holds bins 2t and 2t + 1
+    static_assert(kSplitBins == 2 * kSplitThreads, "two bins per thread");
+    const uint32_t c0 = __ldcg(&ghist[2 * threadIdx.x]), c1 = __ldcg(&ghist[2 * threadIdx.x + 1]);
+    const uint32_t ex = cta_exclusive_scan<kSplitThreads>(c0 + c1, ws);
+    if (threadIdx.x == kSplitThreads - 1) {
+        const uint64_t kept = (uint64_t)ex + c0 + c1;
+        if (target > kept) {   // every kept key is near
+            range[2] = any ? top + 1u : 0u;
+            *d_near = kept;
+            range[3] = 1u;
+        }
+    }
+    if (target >= 1 && (uint64_t)ex < target && target <= (uint64_t)ex + c0 + c1) {
+        const bool first = (uint64_t)ex + c0 >= target;
+        const uint64_t bin = 2u * threadIdx.x + (first ? 0u : 1u);
+        const uint64_t thr = (bin + 1u) << shift;
+        range[2] = (uint32_t)(thr < (uint64_t)top + 1u ? thr : (uint64_t)top + 1u);
+        *d_near = (uint64_t)ex + c0 + (first ? 0u : c1);
+        range[3] = 1u;
+    }
+}
+}  // namespace
+
+Status launch_near_split(const uint32_t* keys, uint64_t n, uint32_t* key_range, uint64_t target, uint32_t* hist,
+                         uint64_t* d_near, cudaStream_t st) {
+    if (n == 0 || n >= 0xFFFFFFFFull || target == 0) return {TIGAS_ERR_INVALID, "split: empty or oversized sort"};
+    if (reinterpret_cast<uintptr_t>(keys) & 15u) return {TIGAS_ERR_INVALID, "split: keys not 16-byte aligned"};
+    // about 64 keys per thread, at most two CTAs per SM
+    const uint64_t per_cta = (uint64_t)kSplitThreads * 64;
+    uint64_t grid = (n + per_cta - 1) / per_cta;
+    if (grid > 2 * (uint64_t)kSmCount) grid = 2 * (uint64_t)kSmCount;
+    k_near_split<<<(unsigned)grid, kSplitThreads, 0, st>>>(keys, (uint32_t)n, key_range, target, hist, d_near);
+    TIGAS_LAUNCHED();
+    return {};
+}
+
 const uint32_t* radix_active_passes(const uint32_t* tmp) { return tmp + 8 * 256 * 2 + 15; }
 const uint32_t* radix_digit_bases(const uint32_t* tmp, int pass) { return tmp + 8 * 256 + 256 * pass; }
 
@@ -1080,6 +1203,8 @@ Status radix_sort(const K* keys_in, const uint32_t* values_in, K* keys_alt, uint
     const bool pay = ex && ex->pay_in;
     if (ex && (sizeof(K) != 4 || (pay && (!ex->pay_alt || !ex->pay_out))))
         return {TIGAS_ERR_INVALID, "key range and payload need 32-bit keys and all three payload buffers"};
+    if (ex && ex->near_split && (!ex->key_range || !ex->d_near || d_n || begin_bit != 0 || end_bit != 32))
+        return {TIGAS_ERR_INVALID, "a partial sort needs a key range, the near count and all 32 bits of every key"};
     if ((!values_out || !values_alt) && (values_out || values_alt || values_in || !pay))
         return {TIGAS_ERR_INVALID, "values may be omitted only together, and only with a payload"};
     const int passes = (end_bit - begin_bit + 7) / 8;

@@ -64,7 +64,7 @@ class FrameStats(ctypes.Structure):
     _fields_ = [("n_visible", ctypes.c_uint64), ("n_pairs", ctypes.c_uint64), ("n_tiles", ctypes.c_uint32),
                 ("sort_passes", ctypes.c_uint32), ("blend_evals", ctypes.c_uint64), ("blend_fetched", ctypes.c_uint64),
                 ("blend_contribs", ctypes.c_uint64), ("depth_sort_passes", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("depth_sort_near", ctypes.c_uint32)]
 
 
 class DebugFrame(ctypes.Structure):
@@ -525,7 +525,8 @@ def render(scene: SceneHandle, pose, intr, width: int, height: int, out=None):
 def _stats_dict(stats: "FrameStats") -> dict:
     return {"n_visible": stats.n_visible, "n_pairs": stats.n_pairs, "n_tiles": stats.n_tiles,
             "sort_passes": stats.sort_passes, "blend_evals": stats.blend_evals, "blend_fetched": stats.blend_fetched,
-            "blend_contribs": stats.blend_contribs, "depth_sort_passes": stats.depth_sort_passes}
+            "blend_contribs": stats.blend_contribs, "depth_sort_passes": stats.depth_sort_passes,
+            "depth_sort_near": stats.depth_sort_near}
 
 
 def render_ex(scene: SceneHandle, pose, intr, width: int, height: int, out_rgba8=None, out_rgba_f32=None,

@@ -784,23 +784,75 @@ def test_autotune_picks_a_candidate_and_keeps_frames(h1, cuda):
 
 
 def test_depth_sort_skips_constant_high_digit(h1, cuda):
-    # the camera at distance 3 sees depths in about [2, 4]: the kept keys span
-    # far fewer than 2^24 steps, so the fourth pass is skipped
-    w, h = 160, 120
-    out = torch.empty((h, w, 4), dtype=torch.uint8, device=cuda)
-    st = tg.render_batch(h1, [synth.BASE_POSE], [synth.default_intrinsics(w, h)], [w], [h], [out],
-                         sort_mode=tg.SORT_SLICED)
-    assert st["depth_sort_passes"] == 3
-    # at the edge of the scene (near plane 0.2 to depths of about 2, 2^24.8 key
-    # steps in FP32 for this scene) the fourth pass runs
-    inside = synth.Pose(0.0, 0.0, (0.0, 0.0, -1.0))
-    st = tg.render_batch(h1, [inside], [synth.default_intrinsics(w, h)], [w], [h], [out], sort_mode=tg.SORT_SLICED)
-    assert st["depth_sort_passes"] == 4
-    # at full size the slices' scans reuse the sort's scratch: the count is read before them
-    s3 = synth.config_scene(3, n=1_000_000)
-    W, H = 1920, 1080
-    big = torch.empty((H, W, 4), dtype=torch.uint8, device=cuda)
-    with tg.scene_from(s3, storage=tg.STORAGE_FP16) as h3:
-        st = tg.render_batch(h3, [synth.config_trajectory(3)[0]] * 2, [synth.default_intrinsics(W, H)] * 2,
-                             [W] * 2, [H] * 2, [big, big], sort_mode=tg.SORT_SLICED)
-    assert st["depth_sort_passes"] in (3, 4)
+    # a single slice: a full depth sort (no partial sort for a last slice)
+    base = tg.get_schedules()
+    try:
+        tg.set_schedule(1, 1, 0, n_views=1)
+        tg.set_schedule(1, 1, 0, n_views=2)
+        # the camera at distance 3 sees depths in about [2, 4]: the kept keys span
+        # far fewer than 2^24 steps, so the fourth pass is skipped
+        w, h = 160, 120
+        out = torch.empty((h, w, 4), dtype=torch.uint8, device=cuda)
+        st = tg.render_batch(h1, [synth.BASE_POSE], [synth.default_intrinsics(w, h)], [w], [h], [out],
+                             sort_mode=tg.SORT_SLICED)
+        assert st["depth_sort_passes"] == 3
+        assert st["depth_sort_near"] == 100_000   # every entry
+        # at the edge of the scene (near plane 0.2 to depths of about 2, 2^24.8 key
+        # steps in FP32 for this scene) the fourth pass runs
+        inside = synth.Pose(0.0, 0.0, (0.0, 0.0, -1.0))
+        st = tg.render_batch(h1, [inside], [synth.default_intrinsics(w, h)], [w], [h], [out],
+                             sort_mode=tg.SORT_SLICED)
+        assert st["depth_sort_passes"] == 4
+        # at full size the slices' scans reuse the sort's scratch: the count is read before them
+        s3 = synth.config_scene(3, n=1_000_000)
+        W, H = 1920, 1080
+        big = torch.empty((H, W, 4), dtype=torch.uint8, device=cuda)
+        with tg.scene_from(s3, storage=tg.STORAGE_FP16) as h3:
+            st = tg.render_batch(h3, [synth.config_trajectory(3)[0]] * 2, [synth.default_intrinsics(W, H)] * 2,
+                                 [W] * 2, [H] * 2, [big, big], sort_mode=tg.SORT_SLICED)
+        assert st["depth_sort_passes"] in (3, 4)
+    finally:
+        tg.set_schedules(base)
+
+
+def test_partial_depth_sort_gives_the_full_sort_frames(h1, cuda):
+    """Fixed-capacity launch sets of three or more slices sort by depth only
+    the entries below a threshold that covers the slices before the last (a
+    histogram of the depth keys places it); the last slice's pairs are
+    sorted by (tile, depth key) instead.  Frames equal those of one slice (a
+    full depth sort) bit for bit, whether the threshold cuts the kept entries
+    (a pose that keeps most of the scene) or keeps all of them (a pose that
+    culls most of it, so that the slices before the last reach past the kept
+    entries)."""
+    levels = [(320, 240), (160, 120)]
+    poses = {"most kept": [synth.BASE_POSE, synth.trajectory(23, 5)[4]],
+             "most culled": [synth.Pose(0.9, 0.0, (0.0, 0.0, -1.5)), synth.Pose(-0.9, 0.3, (0.2, 0.0, -1.5))]}
+    intrs = [synth.default_intrinsics(w, hh) for w, hh in levels]
+    E = 2 * 100_000
+    base = tg.get_schedules()
+    seen = set()
+    try:
+        for name, ps in poses.items():
+            tg.set_schedule(1, 1, 0, n_views=2)
+            ref = _batch(h1, ps, levels, cuda)
+            for sch in [(3, 8, 0), (7, 128, 0), (16, 4096, 4, 16)]:
+                tg.set_schedule(*sch, n_views=2)
+                for _ in range(3):   # direct, exact + capture, replay
+                    got = _batch(h1, ps, levels, cuda)
+                    for a, b in zip(ref, got):
+                        assert np.array_equal(a, b), (name, sch)
+                outs = [torch.empty((hh, w, 4), dtype=torch.uint8, device=cuda) for w, hh in levels]
+                for _ in range(3):   # the counting kernels' launch set, replayed on the third call
+                    st = tg.render_batch(h1, ps, intrs, [w for w, _ in levels], [hh for _, hh in levels], outs,
+                                         sort_mode=tg.SORT_SLICED)
+                for a, b in zip(ref, outs):
+                    assert np.array_equal(a, b.cpu().numpy()), (name, sch)
+                S, F = sch[0], sch[1]
+                first = math.ceil(F ** ((S - 2 - (S - 1)) / (S - 1)) * E)   # end of the slice before the last
+                kept, near = st["n_visible"], st["depth_sort_near"]
+                assert near <= kept < E
+                assert near == kept or near >= first, (name, sch, near, kept, first)
+                seen.add("all kept near" if near == kept else "cut")
+        assert seen == {"all kept near", "cut"}
+    finally:
+        tg.set_schedules(base)
