@@ -49,7 +49,7 @@ Status launch_emit_u64(const uint32_t* offsets, const SplatArrays& sp, const Vie
 // ORs kSortTimeoutFlag into it when a look-back wait ran out (the result is
 // then not to be trusted); without flags the bit goes to a word of tmp.
 // A pass whose digit is the same for every key is skipped on the device.
-// ex (optional, 32-bit keys only):
+// ex (optional; the fields other than tmp_zeroed for 32-bit keys only):
 //   key_range: device [kmin, kmax] of the keys other than 0xFFFFFFFF; digits
 //     are taken from k - kmin (0xFFFFFFFF -> kmax - kmin + 1), the same order,
 //     so keys spanning less than 2^24 need three passes; keys_out then holds
@@ -73,6 +73,9 @@ struct SortExtras {
     uint2* pay_out = nullptr;
     bool near_split = false;
     const uint64_t* d_near = nullptr;
+    // (any key width) tmp's first radix_zero_words(passes) words are already
+    // zero: the sort clears nothing itself (no memset in the launch sequence)
+    bool tmp_zeroed = false;
 };
 // Threshold of a partial depth sort: the smallest bin boundary thr (bins of
 // (k - kmin) >> s, at most kSplitBins of them over [kmin, kmax]) below which
@@ -80,10 +83,11 @@ struct SortExtras {
 // histogram of the keys.  key_range: [kmin, kmax, thr, split flag]; writes
 // key_range[2] = thr, key_range[3] = 1 and *d_near = the keys below thr.
 // hist: kSplitBins + 1 words, zero on entry (the last word counts finished
-// CTAs).  keys 16-byte aligned.
+// CTAs).  keys 16-byte aligned.  Also clears sort_zero[0 .. n_sort_zero)
+// (null: none; the scratch words the depth sort expects zeroed).
 constexpr int kSplitBins = 2048;
 Status launch_near_split(const uint32_t* keys, uint64_t n, uint32_t* key_range, uint64_t target, uint32_t* hist,
-                         uint64_t* d_near, cudaStream_t st);
+                         uint64_t* d_near, uint32_t* sort_zero, int n_sort_zero, cudaStream_t st);
 size_t radix_tmp_words(uint64_t n_cap);
 // Device word of tmp holding how many passes the last one-sweep sort using
 // tmp ran (valid once it completed; inputs of 2^30 keys or more leave it 0).
@@ -93,6 +97,9 @@ const uint32_t* radix_active_passes(const uint32_t* tmp);
 // (256 words; valid once it completed; inputs of 2^30 keys or more do not
 // write them).
 const uint32_t* radix_digit_bases(const uint32_t* tmp, int pass);
+// Words at the start of tmp that a sort of `passes` passes expects zeroed
+// (it clears them itself unless SortExtras::tmp_zeroed says they are).
+size_t radix_zero_words(int passes);
 template <typename K>
 Status radix_sort(const K* keys_in, const uint32_t* values_in, K* keys_alt, uint32_t* values_alt,
                   K* keys_out, uint32_t* values_out, uint64_t n_cap, const uint64_t* d_n, int begin_bit,

@@ -685,10 +685,12 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     dex.pay_alt = rect_alt;
     dex.pay_out = rect_sorted;
     if (split) {
+        // (also clears the depth sort's scratch words: no memset before it)
         TIGAS_TRY(launch_near_split(sp.depth_key, E, sp.key_range, slice_end(S - 2, S, req.first_slice_inv, E),
-                                    d_hdr->split_hist, &d_hdr->near, st));
+                                    d_hdr->split_hist, &d_hdr->near, tmp, (int)radix_zero_words(4), st));
         dex.near_split = true;
         dex.d_near = &d_hdr->near;
+        dex.tmp_zeroed = true;
     }
     TIGAS_TRY(radix_sort<uint32_t>(sp.depth_key, nullptr, pk_alt, compact ? nullptr : pv_alt, pk,
                                    compact ? nullptr : order, E, nullptr, 0, 32, tmp, st, nullptr, d_flags, &dex));
@@ -744,8 +746,15 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
         if (b == a) continue;
         uint64_t* d_P = d_total + i;
         TIGAS_TRY(mark(kStScan, true));
+        // the last slice of a split: its entries are in depth order only up to
+        // the threshold, so its pairs carry (tile, depth) keys
+        const bool wide = split && i == S - 1;
+        const int pair_passes = ((wide ? 32 : 0) + L.tile_bits + 7) / 8;
         // also clears the slice's active-list counts and blend work counter (d_misc[0..3])
-        TIGAS_TRY(launch_running_sat(d_views, V, done, sat, d_misc, 4, st));
+        // and, with fixed capacities (the pair buffers already taken), the pair sort's
+        // scratch words, so that the sort runs no memset
+        TIGAS_TRY(launch_running_sat(d_views, V, done, sat, d_misc, 4, stat ? stmp : nullptr,
+                                     (int)radix_zero_words(pair_passes), st));
         // the count kernel writes each entry's prefix within its block of kScanBlock
         // entries and the blocks' sums; the scan of the sums gives the blocks'
         // offsets and the slice total (*d_P; the closing zero count puts the total at b)
@@ -770,23 +779,22 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
             if (ctx.pairs.over) return {TIGAS_ERR_CUDA, "pair workspace layout exceeds its reservation"};
             cap = P;
         }
-        // the last slice of a split: its entries are in depth order only up to
-        // the threshold, so its pairs carry (tile, depth) keys
-        const bool wide = split && i == S - 1;
         TIGAS_TRY(mark(kStEmit, true));
         TIGAS_TRY(launch_emit_slice(compact ? nullptr : order, rect_sorted, a, b, inblock, block_offs, d_views, V,
                                     done, keys_a, vals_a, cap, d_flags, compact, wide ? sp.depth_key : nullptr,
                                     sp.key_range, st));
         TIGAS_TRY(mark(kStEmit, false));
         TIGAS_TRY(mark(kStPairSort, true));
+        SortExtras pex;
+        pex.tmp_zeroed = stat;
         if (wide)
             TIGAS_TRY(radix_sort<uint64_t>(reinterpret_cast<uint64_t*>(keys_a), vals_a,
                                            reinterpret_cast<uint64_t*>(keys_b), vals_b,
                                            reinterpret_cast<uint64_t*>(keys_c), vals_c, cap, d_P, 0,
-                                           32 + L.tile_bits, stmp, st, nullptr, d_flags));
+                                           32 + L.tile_bits, stmp, st, nullptr, d_flags, &pex));
         else
             TIGAS_TRY(radix_sort<uint32_t>(keys_a, vals_a, keys_b, vals_b, keys_c, vals_c, cap, stat ? d_P : nullptr,
-                                           0, L.tile_bits, stmp, st, &passes, d_flags));
+                                           0, L.tile_bits, stmp, st, &passes, d_flags, &pex));
         TIGAS_TRY(mark(kStPairSort, false));
         TIGAS_TRY(mark(kStRanges, true));
         // the pass over the tile's high byte (the second of a one-sweep sort of 9 to 16

@@ -92,9 +92,12 @@ constexpr uint32_t kSatSmem = 12288;   // 48 KB
 
 __global__ void __launch_bounds__(1024)
 k_running_sat(const ViewParams* __restrict__ views_g, const uint32_t* __restrict__ done, uint32_t* __restrict__ sat,
-              uint32_t* __restrict__ slice_zero, int n_zero) {
+              uint32_t* __restrict__ slice_zero, int n_zero, uint32_t* __restrict__ sort_zero, int n_sort_zero) {
     __shared__ uint32_t tab[kSatSmem];
-    if (blockIdx.x == 0 && (int)threadIdx.x < n_zero) slice_zero[threadIdx.x] = 0u;
+    if (blockIdx.x == 0) {
+        if ((int)threadIdx.x < n_zero) slice_zero[threadIdx.x] = 0u;
+        for (int i = threadIdx.x; i < n_sort_zero; i += blockDim.x) sort_zero[i] = 0u;
+    }
     const ViewParams& vp = views_g[blockIdx.x];
     const uint32_t TX = (uint32_t)vp.TX, TY = (uint32_t)vp.TY, W1 = TX + 1;
     const bool in_smem = (TY + 1) * W1 <= kSatSmem;
@@ -500,9 +503,9 @@ Status launch_fill_unseen(const ViewParams* views, int V, uint32_t total_tiles, 
 }
 
 Status launch_running_sat(const ViewParams* views, int V, const uint32_t* done, uint32_t* sat, uint32_t* slice_zero,
-                          int n_zero, cudaStream_t st) {
+                          int n_zero, uint32_t* sort_zero, int n_sort_zero, cudaStream_t st) {
     if (n_zero > 1024) return {TIGAS_ERR_INVALID, "too many words to clear"};
-    k_running_sat<<<V, 1024, 0, st>>>(views, done, sat, slice_zero, n_zero);
+    k_running_sat<<<V, 1024, 0, st>>>(views, done, sat, slice_zero, n_zero, sort_zero, sort_zero ? n_sort_zero : 0);
     TIGAS_LAUNCHED();
     return {};
 }

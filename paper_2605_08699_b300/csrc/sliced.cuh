@@ -55,9 +55,11 @@ Status launch_fill_unseen(const ViewParams* views, int V, uint32_t total_tiles, 
 // Per view, the summed-area table of tiles not done: sat[sat_base + y (TX+1) + x]
 // = not-done tiles in columns [0, x) of rows [0, y).  Also clears
 // slice_zero[0 .. n_zero) (at most 1024 words: the slice's active-list counts
-// and blend work counter, which the ranges and blend launches expect zeroed).
+// and blend work counter, which the ranges and blend launches expect zeroed)
+// and sort_zero[0 .. n_sort_zero) (null: none; the scratch words the slice's
+// pair sort expects zeroed, radix_zero_words).
 Status launch_running_sat(const ViewParams* views, int V, const uint32_t* done, uint32_t* sat, uint32_t* slice_zero,
-                          int n_zero, cudaStream_t st);
+                          int n_zero, uint32_t* sort_zero, int n_sort_zero, cudaStream_t st);
 
 // count(k): not-done tiles in the rectangle of depth-ordered entry k, k in
 // [a, b) (four reads of the running-tile table), and count(b) = 0.  Writes

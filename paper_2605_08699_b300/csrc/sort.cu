@@ -958,10 +958,13 @@ Status ensure_os_smem() {
 
 uint64_t os_chunks(uint64_t n_cap) { return (n_cap + 4095) / 4096; }   // upper bound for every tile shape
 
-// tmp layout: ghist [8][256], gbase [8][256], chunk counters [8], flags [8],
-// routes [8], status [pass][chunks][256] (cleared by the histogram kernel);
-// the status table starts 16-byte aligned
-constexpr size_t kOsHead = (8 * 256 * 2 + 16 + 8 * kRouteWords + 3) / 4 * 4;
+// tmp layout: chunk counters [8], flags [7], active passes [1], ghist [8][256],
+// gbase [8][256], routes [8], status [pass][chunks][256] (cleared by the
+// histogram kernel); the words a sort of p passes needs zeroed on entry are
+// the first radix_zero_words(p) (counters, flags and p histograms), and the
+// status table starts 16-byte aligned
+constexpr size_t kOsHead = (16 + 8 * 256 * 2 + 8 * kRouteWords + 3) / 4 * 4;
+static_assert((16 + 8 * 256 * 2) % 2 == 0, "routes hold pointers: 8-byte aligned");
 size_t os_tmp_words(uint64_t n_cap) { return kOsHead + 8 * os_chunks(n_cap) * 256; }
 
 template <typename K, int PAY, bool MAP>
@@ -972,16 +975,17 @@ Status radix_sort_onesweep(const K* keys_in, const uint32_t* values_in, K* keys_
     static_assert(N >= 4096, "the status table (os_chunks) assumes chunks of at least 4096 keys");
     const int passes = (end_bit - begin_bit + 7) / 8;
     TIGAS_TRY((ensure_os_smem<K, PAY, MAP>()));
-    uint32_t* ghist = tmp;
-    uint32_t* gbase = tmp + 8 * 256;
-    uint32_t* counters = gbase + 8 * 256;
+    uint32_t* counters = tmp;
     uint32_t* own_flags = counters + 8;
-    OsRoute* routes = reinterpret_cast<OsRoute*>(counters + 16);
+    uint32_t* ghist = tmp + 16;
+    uint32_t* gbase = ghist + 8 * 256;
+    OsRoute* routes = reinterpret_cast<OsRoute*>(gbase + 8 * 256);
     uint32_t* status = tmp + kOsHead;
     if (!flags) flags = own_flags;
     const uint32_t* range = MAP ? ex->key_range : nullptr;
     const uint64_t chunks = (n_cap + N - 1) / N;
-    TIGAS_CUDA_TRY(cudaMemsetAsync(tmp, 0, (8 * 256 * 2 + 16) * sizeof(uint32_t), st));
+    if (!(ex && ex->tmp_zeroed))
+        TIGAS_CUDA_TRY(cudaMemsetAsync(tmp, 0, radix_zero_words(passes) * sizeof(uint32_t), st));
     // enough CTAs for eight grid strides of 4 keys per thread, at most 8 per SM
     constexpr int kHistKeys = MAP ? 4 : 8;
     constexpr int kHistVecs = 2;
@@ -1106,10 +1110,13 @@ namespace {
 constexpr int kSplitThreads = 1024;
 __global__ void __launch_bounds__(kSplitThreads)
 k_near_split(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict__ range, uint64_t target,
-             uint32_t* __restrict__ ghist, uint64_t* __restrict__ d_near) {
+             uint32_t* __restrict__ ghist, uint64_t* __restrict__ d_near, uint32_t* __restrict__ sort_zero,
+             int n_sort_zero) {
     __shared__ uint32_t h[kSplitBins];
     __shared__ uint32_t ws[kSplitThreads / 32 + 1];
     __shared__ int last;
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < n_sort_zero; i += kSplitThreads) sort_zero[i] = 0u;
     for (int i = threadIdx.x; i < kSplitBins; i += kSplitThreads) h[i] = 0;
     __syncthreads();
     const uint32_t kmin = range[0], kmax = range[1];
@@ -1173,20 +1180,22 @@ k_near_split(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict
 }  // namespace
 
 Status launch_near_split(const uint32_t* keys, uint64_t n, uint32_t* key_range, uint64_t target, uint32_t* hist,
-                         uint64_t* d_near, cudaStream_t st) {
+                         uint64_t* d_near, uint32_t* sort_zero, int n_sort_zero, cudaStream_t st) {
     if (n == 0 || n >= 0xFFFFFFFFull || target == 0) return {TIGAS_ERR_INVALID, "split: empty or oversized sort"};
     if (reinterpret_cast<uintptr_t>(keys) & 15u) return {TIGAS_ERR_INVALID, "split: keys not 16-byte aligned"};
     // about 64 keys per thread, at most two CTAs per SM
     const uint64_t per_cta = (uint64_t)kSplitThreads * 64;
     uint64_t grid = (n + per_cta - 1) / per_cta;
     if (grid > 2 * (uint64_t)kSmCount) grid = 2 * (uint64_t)kSmCount;
-    k_near_split<<<(unsigned)grid, kSplitThreads, 0, st>>>(keys, (uint32_t)n, key_range, target, hist, d_near);
+    k_near_split<<<(unsigned)grid, kSplitThreads, 0, st>>>(keys, (uint32_t)n, key_range, target, hist, d_near,
+                                                           sort_zero, sort_zero ? n_sort_zero : 0);
     TIGAS_LAUNCHED();
     return {};
 }
 
-const uint32_t* radix_active_passes(const uint32_t* tmp) { return tmp + 8 * 256 * 2 + 15; }
-const uint32_t* radix_digit_bases(const uint32_t* tmp, int pass) { return tmp + 8 * 256 + 256 * pass; }
+const uint32_t* radix_active_passes(const uint32_t* tmp) { return tmp + 15; }
+const uint32_t* radix_digit_bases(const uint32_t* tmp, int pass) { return tmp + 16 + 8 * 256 + 256 * pass; }
+size_t radix_zero_words(int passes) { return 16 + 256 * (size_t)passes; }
 
 size_t radix_tmp_words(uint64_t n_cap) {
     size_t a = rts_tmp_words(n_cap), b = os_tmp_words(n_cap);
@@ -1201,7 +1210,8 @@ Status radix_sort(const K* keys_in, const uint32_t* values_in, K* keys_alt, uint
     if (begin_bit < 0 || end_bit > kbits || begin_bit > end_bit) return {TIGAS_ERR_INVALID, "bad sort bit range"};
     if (n_cap >= 0xFFFFFFFFull) return {TIGAS_ERR_INVALID, "sort too large"};
     const bool pay = ex && ex->pay_in;
-    if (ex && (sizeof(K) != 4 || (pay && (!ex->pay_alt || !ex->pay_out))))
+    const bool ext = ex && (ex->key_range || ex->pay_in || ex->near_split);   // beyond tmp_zeroed
+    if (ext && (sizeof(K) != 4 || (pay && (!ex->pay_alt || !ex->pay_out))))
         return {TIGAS_ERR_INVALID, "key range and payload need 32-bit keys and all three payload buffers"};
     if (ex && ex->near_split && (!ex->key_range || !ex->d_near || d_n || begin_bit != 0 || end_bit != 32))
         return {TIGAS_ERR_INVALID, "a partial sort needs a key range, the near count and all 32 bits of every key"};
@@ -1245,7 +1255,7 @@ Status radix_sort(const K* keys_in, const uint32_t* values_in, K* keys_alt, uint
         return radix_sort_onesweep<K, kPayNone, false>(keys_in, values_in, keys_alt, values_alt, keys_out,
                                                        values_out, n_cap, d_n, begin_bit, end_bit, tmp, st, flags, ex);
     }
-    if (ex) return {TIGAS_ERR_INVALID, "key range and payload need fewer than 2^30 keys"};
+    if (ext || (ex && ex->tmp_zeroed)) return {TIGAS_ERR_INVALID, "sort extras need fewer than 2^30 keys"};
     return radix_sort_rts<K>(keys_in, values_in, keys_alt, values_alt, keys_out, values_out, n_cap, d_n, begin_bit,
                              end_bit, tmp, st);
 }
