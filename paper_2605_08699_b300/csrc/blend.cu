@@ -1,9 +1,10 @@
 // K6 per-tile blend, the 3DGS front-to-back compositing the backend relies
 // on (Sec. 4.1): one warp per 16x16 tile, 8 pixels per thread (column
 // lane % 16, rows lane / 16 + 2k), four independent warps per CTA and no
-// CTA-wide barrier; a tile with a long list in a slice is split into
-// kStrips strips of 16 / kStrips rows (two 16x8 halves, 4 pixels per thread)
-// that separate warps composite at once.  The tile's depth-ordered list is
+// CTA-wide barrier; a tile with a long list in a slice is split into strips
+// of 8 rows (two 16x8 halves, 4 pixels per thread) or, for the longest lists
+// of the slices whose tail they set, 4 rows (2 pixels per thread), that
+// separate warps composite at once.  The tile's depth-ordered list is
 // consumed in batches of 32 entries that the warp gathers into shared memory
 // with cp.async, double-buffered (batch b+1 in flight while b is composited).
 //
@@ -426,12 +427,14 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ values, S
             item = __shfl_sync(kFull, it, 0);
         }
         if (item >= n_items) break;
+        // regions: [0, 4n) up, [4n, 6n) down from 6n - 1, [6n, 7n) down from 7n - 1
+        const uint32_t n7 = sl.active_cap / kActivePerTile;
         const uint32_t raw = !SLICED ? item
                              : sl.active[item < n_first  ? item
-                                         : item < n_long ? sl.active_cap / 2 - 1 - (item - n_first)
-                                                         : sl.active_cap - 1 - (item - n_long)];
+                                         : item < n_long ? 6u * n7 - 1u - (item - n_first)
+                                                         : 7u * n7 - 1u - (item - n_long)];
         const uint32_t g = raw & kTileMask;
-        const uint32_t strip = raw >> kStripShift;   // 0: whole tile, s + 1: strip s
+        const uint32_t code = raw >> kStripShift;   // 0: whole tile, else a strip (kCode8 + s, kCode4 + s)
         int v = 0;
         {
             int lo = 0, hi = V;   // last view with tile_base <= g
@@ -444,19 +447,24 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ values, S
         const ViewParams& vp = views_g[v];
         const uint32_t local = g - s_tb[v];
         const uint64_t sbase = SLICED ? sl.pix_base[v] : 0;
-        if (!SLICED || strip == 0) {
+        if (!SLICED || code == 0) {
             const bool all = blend_rows<SLICED, COUNT, kPix, kWB>(sm, lane, ranges, values, sp, vp, g, local, 0, sbase,
                                                              n_entries, bg_r, bg_g, bg_b, sl, cnt);
             if (!SLICED) break;
             if (all && lane == 0) atomicOr(&sl.done[g >> 5], 1u << (g & 31));
         } else {
-            const uint32_t bit = 1u << (strip - 1);
-            const bool all = blend_rows<SLICED, COUNT, (int)kStripRows / 2, kWB>(sm, lane, ranges, values, sp, vp, g, local,
-                                                                           (int)kStripRows * (int)(strip - 1), sbase,
-                                                                           n_entries, bg_r, bg_g, bg_b, sl, cnt);
+            const bool eight = code < kCode4;
+            const uint32_t s = code - (eight ? kCode8 : kCode4);
+            const bool all =
+                eight ? blend_rows<SLICED, COUNT, 4, kWB>(sm, lane, ranges, values, sp, vp, g, local, 8 * (int)s,
+                                                         sbase, n_entries, bg_r, bg_g, bg_b, sl, cnt)
+                      : blend_rows<SLICED, COUNT, 2, kWB>(sm, lane, ranges, values, sp, vp, g, local, 4 * (int)s,
+                                                         sbase, n_entries, bg_r, bg_g, bg_b, sl, cnt);
             if (all && lane == 0) {
-                const uint32_t old = atomicOr(&sl.strips[g], bit);
-                if (((old | bit) & kStripsAll) == kStripsAll) atomicOr(&sl.done[g >> 5], 1u << (g & 31));
+                // the strip's rows have stopped; the tile is done once all 16 rows have
+                const uint32_t rows = (eight ? 0xFFu << (8 * s) : 0xFu << (4 * s)) << kRowShift;
+                const uint32_t old = atomicOr(&sl.strips[g], rows);
+                if (((old | rows) & kRowsAll) == kRowsAll) atomicOr(&sl.done[g >> 5], 1u << (g & 31));
             }
         }
     }

@@ -556,7 +556,7 @@ SlicedLayout sliced_layout(const Scene* scene, FrameRequest& req) {
     b += E * 4 * 4 + (E + 1) * 4 + E * 8 * 2;             // depth sort buffers, in-block offsets, rects (2)
     b += ((E + 1 + kScanBlock - 1) / kScanBlock) * 4 * 2; // block sums of the counts and their offsets
     b += L.tmp_words * 4;
-    b += (sizeof(uint2) + 4 * 4 + 4) * (size_t)L.total_tiles + L.done_words * 4;   // ranges, active, strips
+    b += (sizeof(uint2) + 4 * kActivePerTile + 4) * (size_t)L.total_tiles + L.done_words * 4;   // ranges, active, strips
     b += (size_t)L.total_sat * 4;                                                   // running-tile tables
     b += L.total_pix * 16 + sizeof(uint64_t) * kMaxViews * 2;
     L.fixed_bytes = b;
@@ -571,6 +571,9 @@ size_t pair_bytes_for(uint64_t P, bool wide) { return P * (wide ? 36 : 24) + rad
 // the entries but few pairs, since most tiles have stopped by then, and its
 // pairs are sorted by (tile, depth) instead.  Frames are the same; only the
 // work differs.
+#ifndef TIGAS_FINE_FROM
+#define TIGAS_FINE_FROM 6   // in eighths of the slice count: the first slice whose long lists take 4-row strips
+#endif
 #ifndef TIGAS_NEAR_SPLIT
 #define TIGAS_NEAR_SPLIT 3   // fewest slices of a launch set with a partial depth sort
 #endif
@@ -655,7 +658,7 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     sp.compact_rect = compact ? 1 : 0;
     uint32_t* tmp = ctx.fixed.take<uint32_t>(L.tmp_words);
     uint2* ranges = ctx.fixed.take<uint2>(total_tiles);
-    uint32_t* active = ctx.fixed.take<uint32_t>(4 * (size_t)total_tiles);   // long tiles as 4 strips each
+    uint32_t* active = ctx.fixed.take<uint32_t>(kActivePerTile * (size_t)total_tiles);
     uint32_t* strips = ctx.fixed.take<uint32_t>(total_tiles);
     uint32_t* sat = ctx.fixed.take<uint32_t>(L.total_sat);
     uint32_t* done = ctx.fixed.take<uint32_t>(L.done_words);
@@ -717,7 +720,13 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     uint64_t total_pairs = 0;
     int passes = 0;
     uint64_t a = 0;
-    SliceBlendArgs sl{active, d_misc, d_misc + 2, state, d_pix_base, done, strips, 4 * total_tiles};
+    SliceBlendArgs sl{active, d_misc, d_misc + 2, state, d_pix_base, done, strips, kActivePerTile * total_tiles};
+    // the last quarter of the slices cut their longest lists (kLongestTile pairs or
+    // more) into 4-row strips: measured per item, the first slices keep most warps
+    // busy until their end, while a late slice ends with the serial compositing of
+    // its few longest 8-row strips (8-view launch set, 7 slices: 3.405 ms with 8-row
+    // strips only, 3.378 with 4-row strips from slice 5, 3.399 from slice 3)
+    const int fine_from = (S * TIGAS_FINE_FROM) / 8;
     if (stat) {
         // pair buffers for the fixed capacity, taken once
         ctx.pairs.reset();
@@ -803,7 +812,8 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
                                        ? radix_digit_bases(stmp, wide ? 5 : 1)
                                        : nullptr;
         TIGAS_TRY(launch_ranges_active(keys_c, cap, stat ? d_P : nullptr, ranges, total_tiles, done, active, d_misc,
-                                       d_flags, hi_bases, strips, wide, st));
+                                       d_flags, hi_bases, strips, wide,
+                                       i >= fine_from ? kLongestTile : 0xFFFFFFFFu, st));
         TIGAS_TRY(mark(kStRanges, false));
         TIGAS_TRY(mark(kStBlend, true));
         TIGAS_TRY(launch_blend_slice(ranges, vals_c, sp, d_views, V, (uint32_t)E, scene->view.bg,

@@ -36,8 +36,8 @@ __device__ inline uint8_t to_u8(float x) {
 }
 
 // Per-launch-set clearing for the slices, a thread per tile: done bits, strip
-// words (bits 0-3: strip s finished; kStripSeen / kStripSeenNow: the tile
-// carries (C, T) from a blended slice), and the slice totals.  No pixel is touched: a tile's first
+// words (row bits: the tile's rows that stopped; kStripSeen / kStripSeenNow:
+// the tile carries (C, T) from a blended slice), and the slice totals.  No pixel is touched: a tile's first
 // blend starts from (C, T) = (0, 1), and k_fill_unseen writes the background
 // of tiles no slice blended.
 __global__ void __launch_bounds__(256)
@@ -372,11 +372,13 @@ k_emit_slice(const uint32_t* __restrict__ order, const uint2* __restrict__ rect_
 // array.  Tiles with pairs in this slice that are not done form the active
 // list.  A tile with at least kHeavyTile pairs goes in as its strips of pixel
 // rows, so that several warps share its long list: strips of the tiles with
-// at least kLongestTile pairs from the front (count n_active[0]), the others
-// from the middle downward (count n_active[3]).  The remaining tiles go in
-// whole from the back (count n_active[1]).  The blend's dynamic scheduler
-// takes the three regions in that order, so the longest lists start first
-// and the short ones fill the tail.
+// at least kLongestTile pairs from the front (count n_active[0]; four 4-row
+// strips for a list of at least fine_min pairs, else two 8-row strips), the
+// others' two 8-row strips from the middle downward (count
+// n_active[3]).  The remaining tiles go in whole from the back (count
+// n_active[1]).  The blend's dynamic scheduler takes the three regions in
+// that order, so the longest lists start first and the short ones fill the
+// tail.
 // KS: words per key (1: 32-bit tile keys; 2: the high words of 64-bit
 // (tile, depth) keys, `keys` pointing at the first key's high word).
 template <int KS>
@@ -394,7 +396,7 @@ __global__ void __launch_bounds__(256)
 k_ranges_active(const uint32_t* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, uint2* __restrict__ ranges,
                 uint32_t n_tiles, const uint32_t* __restrict__ done, uint32_t* __restrict__ active,
                 uint32_t* __restrict__ n_active, uint32_t* __restrict__ overflow,
-                const uint32_t* __restrict__ hi_bases, uint32_t* __restrict__ strips) {
+                const uint32_t* __restrict__ hi_bases, uint32_t* __restrict__ strips, uint32_t fine_min) {
     __shared__ uint32_t s_sample[kRangeSample];
     __shared__ uint32_t s_lo[256];
     __shared__ uint64_t s_run[2];
@@ -436,47 +438,57 @@ k_ranges_active(const uint32_t* __restrict__ keys, uint64_t n_cap, const uint64_
     }
     __syncthreads();
     bool act = false, heavy = false, longest = false;
+    uint32_t lens = 0;
     if (t < n_tiles) {
         const uint32_t lo = s_lo[threadIdx.x];
         const uint32_t hi = threadIdx.x < 255 ? s_lo[threadIdx.x + 1] : (uint32_t)R;
         ranges[t] = make_uint2(lo, hi);
         act = hi > lo && !tile_done(done, t);
-        heavy = act && hi - lo >= kHeavyTile;
-        longest = heavy && hi - lo >= kLongestTile;
+        lens = hi - lo;
+        heavy = act && lens >= kHeavyTile;
+        longest = heavy && lens >= kLongestTile;
     }
     const int lane = threadIdx.x & 31;
     const uint32_t below = (1u << lane) - 1u;
     // strips of the longest lists from the front, of the other long lists from the
-    // middle (2 n_tiles) down, so that the blend starts the longest work first
+    // middle (6 n_tiles) down, so that the blend starts the longest work first
     const uint32_t mx = __ballot_sync(kFull, longest);
     const uint32_t mh = __ballot_sync(kFull, heavy && !longest);
     const uint32_t ml = __ballot_sync(kFull, act && !heavy);
     if (mx) {
-        uint32_t base = 0;
-        if (lane == __ffs(mx) - 1) base = atomicAdd(&n_active[0], kStrips * (uint32_t)__popc(mx));
-        base = __shfl_sync(kFull, base, __ffs(mx) - 1);
-        if (longest) {
-            const uint32_t at = base + kStrips * (uint32_t)__popc(mx & below);
+        // four 4-row strips for a list of at least fine_min pairs, else two 8-row ones
+        const uint32_t rows = longest && lens >= fine_min ? 4u : 8u;
+        const uint32_t ns = longest ? 16u / rows : 0u;
+        uint32_t incl = ns;
 #pragma unroll
-            for (uint32_t s = 0; s < kStrips; ++s) active[at + s] = t | ((s + 1u) << kStripShift);
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, d);
+            if (lane >= d) incl += y;
+        }
+        uint32_t base = 0;
+        if (lane == 31) base = atomicAdd(&n_active[0], incl);
+        base = __shfl_sync(kFull, base, 31);
+        if (longest) {
+            const uint32_t at = base + incl - ns;
+            for (uint32_t s = 0; s < ns; ++s) active[at + s] = t | (strip_code(rows, s) << kStripShift);
         }
     }
     if (mh) {
         uint32_t base = 0;
-        if (lane == __ffs(mh) - 1) base = atomicAdd(&n_active[3], kStrips * (uint32_t)__popc(mh));
+        if (lane == __ffs(mh) - 1) base = atomicAdd(&n_active[3], 2u * (uint32_t)__popc(mh));
         base = __shfl_sync(kFull, base, __ffs(mh) - 1);
         if (heavy && !longest) {
-            const uint32_t at = base + kStrips * (uint32_t)__popc(mh & below);
+            const uint32_t at = base + 2u * (uint32_t)__popc(mh & below);
 #pragma unroll
-            for (uint32_t s = 0; s < kStrips; ++s)
-                active[2u * n_tiles - 1u - (at + s)] = t | ((s + 1u) << kStripShift);
+            for (uint32_t s = 0; s < 2u; ++s)
+                active[6u * n_tiles - 1u - (at + s)] = t | (strip_code(8, s) << kStripShift);
         }
     }
     if (ml) {
         uint32_t base = 0;
         if (lane == __ffs(ml) - 1) base = atomicAdd(&n_active[1], (uint32_t)__popc(ml));
         base = __shfl_sync(kFull, base, __ffs(ml) - 1);
-        if (act && !heavy) active[4u * n_tiles - 1u - (base + __popc(ml & below))] = t;
+        if (act && !heavy) active[kActivePerTile * n_tiles - 1u - (base + __popc(ml & below))] = t;
     }
 }
 
@@ -575,15 +587,18 @@ Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64
 Status launch_ranges_active(const uint32_t* keys, uint64_t n_cap, const uint64_t* d_n, uint2* ranges,
                             uint32_t n_tiles, const uint32_t* done, uint32_t* active, uint32_t* n_active,
                             uint32_t* overflow, const uint32_t* hi_bases, uint32_t* strips, bool wide,
-                            cudaStream_t st) {
+                            uint32_t fine_min, cudaStream_t st) {
     if (n_tiles == 0) return {};
+    static_assert(kActivePerTile == 7, "4 + 2 + 1 items per tile at most, one region each");
     if (hi_bases && n_tiles > 65536u) return {TIGAS_ERR_INVALID, "second-pass digit bases need tile ids of 16 bits"};
     if (wide)   // the tile is the high word of each 64-bit key
         k_ranges_active<2><<<(n_tiles + 255) / 256, 256, 0, st>>>(keys + 1, n_cap, d_n, ranges, n_tiles, done,
-                                                                  active, n_active, overflow, hi_bases, strips);
+                                                                  active, n_active, overflow, hi_bases, strips,
+                                                                  fine_min);
     else
         k_ranges_active<1><<<(n_tiles + 255) / 256, 256, 0, st>>>(keys, n_cap, d_n, ranges, n_tiles, done, active,
-                                                                  n_active, overflow, hi_bases, strips);
+                                                                  n_active, overflow, hi_bases, strips,
+                                                                  fine_min);
     TIGAS_LAUNCHED();
     return {};
 }

@@ -13,32 +13,37 @@ constexpr uint32_t kHeavyTile = TIGAS_HEAVY_TILE;   // pairs of a slice that mak
 #define TIGAS_LONGEST_TILE 512
 #endif
 constexpr uint32_t kLongestTile = TIGAS_LONGEST_TILE;   // long tiles whose strips the blend starts first
-// A long tile is composited as kStrips strips of 16 / kStrips pixel rows,
-// each a separate item of the active list.
-#ifndef TIGAS_STRIPS
-#define TIGAS_STRIPS 2
-#endif
-constexpr uint32_t kStrips = TIGAS_STRIPS;
-static_assert(kStrips == 2 || kStrips == 4, "a strip holds 8 or 4 pixel rows");
-constexpr uint32_t kStripRows = 16 / kStrips;
-constexpr uint32_t kStripsAll = (1u << kStrips) - 1u;   // strip-word bits of a tile whose strips all stopped
-// Active-list items: a tile id (whole tile) or tile id | (s + 1) << kStripShift
-// for strip s (pixel rows kStripRows s .. kStripRows (s + 1) - 1) of a long tile.
+// A long tile is composited as strips of pixel rows, each a separate item of
+// the active list: two strips of 8 rows, or, for the longest tiles of a slice
+// whose tail their serial compositing sets, four strips of 4 rows.
+// Active-list items: a tile id (whole tile) or tile id | code << kStripShift,
+// code 1 + s for 8-row strip s (rows 8 s .. 8 s + 7), code 3 + s for 4-row
+// strip s (rows 4 s .. 4 s + 3).
 constexpr int kStripShift = 28;
-// Strip-word bits (bits 0-3: strip s's pixels all stopped).  kStripSeen: a
-// slice before the current one blended the tile, so its pixels carry (C, T)
-// in the state.  A blend marks the tiles it visits with kStripSeenNow instead,
-// never with kStripSeen: the strips of one tile run in the same slice on
-// different warps, and a strip that finished first must not make a sibling
-// that starts later take its first visit for a later one (and read state
-// nobody wrote).  The next slice's ranges kernel, which runs after that blend
-// and before the next, turns kStripSeenNow into kStripSeen.
+constexpr uint32_t kCode8 = 1u, kCode4 = 3u;
+__host__ __device__ constexpr uint32_t strip_code(uint32_t rows, uint32_t s) { return (rows == 8 ? kCode8 : kCode4) + s; }
+// Strip-word bits.  Bits kRowShift + r: pixel row r of the tile has stopped
+// (set by the strips that finish; the tile is done once all 16 are set, so
+// tiles split into 8-row strips in one slice and 4-row strips in another
+// stay consistent).  kStripSeen: a slice before the current one blended the
+// tile, so its pixels carry (C, T) in the state.  A blend marks the tiles it
+// visits with kStripSeenNow instead, never with kStripSeen: the strips of one
+// tile run in the same slice on different warps, and a strip that finished
+// first must not make a sibling that starts later take its first visit for a
+// later one (and read state nobody wrote).  The next slice's ranges kernel,
+// which runs after that blend and before the next, turns kStripSeenNow into
+// kStripSeen.
 constexpr uint32_t kStripSeen = 0x10u;
 constexpr uint32_t kStripSeenNow = 0x20u;
+constexpr int kRowShift = 8;
+constexpr uint32_t kRowsAll = 0xFFFFu << kRowShift;
+// The active list: 4-row strips from the front, 8-row strips from the
+// middle down, whole tiles from the back (kActivePerTile words per tile).
+constexpr uint32_t kActivePerTile = 7;
 constexpr uint32_t kTileMask = (1u << kStripShift) - 1u;
 
-// Clears the per-tile done bits (total_tiles bits) and strip words (bits 0-3:
-// strip s of the tile finished; kStripSeen / kStripSeenNow: the tile was
+// Clears the per-tile done bits (total_tiles bits) and strip words (row bits:
+// the tile's pixel rows that stopped; kStripSeen / kStripSeenNow: the tile was
 // blended and its pixels carry (C, T) in `state`; a tile's first blend starts
 // from (0, 1) instead), and totals[0 .. n_totals) (at most 256).  No pixel is
 // written.  Also copies *word_src to *word_dst when word_src is not null (a
@@ -83,14 +88,15 @@ Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64
                          cudaStream_t st);
 
 // Tile ranges of the slice's sorted keys, and the list of tiles with pairs
-// that are not done, in three regions of `active` (4 n_tiles items): the
-// kStrips strips of each tile with >= kLongestTile pairs from the front
-// (n_active[0] items), the strips of the other tiles with >= kHeavyTile pairs
-// from active[2 n_tiles - 1] downward (n_active[3]), and the remaining tiles
-// whole from the back (active[4 n_tiles - 1 - k], n_active[1]).  The three
-// counts must be zero on entry (launch_running_sat clears them).  Also turns
-// every strip word's kStripSeenNow into kStripSeen (the blend before this one
-// is over).
+// that are not done, in three regions of `active` (kActivePerTile n_tiles
+// items): the strips of each tile with >= kLongestTile pairs from the front
+// (n_active[0] items; four 4-row strips for a tile of at least fine_min
+// pairs, else two 8-row strips; 0xFFFFFFFF: never 4-row), the two 8-row
+// strips of the other tiles with >= kHeavyTile pairs from active[6 n_tiles -
+// 1] downward (n_active[3]), and the remaining tiles whole from the back
+// (active[7 n_tiles - 1 - k], n_active[1]).  The three counts must be zero on
+// entry (launch_running_sat clears them).  Also turns every strip word's
+// kStripSeenNow into kStripSeen (the blend before this one is over).
 // The key count is min(*d_n, n_cap) when d_n is given, else n_cap.
 // hi_bases: null, or 256 words whose word h is the first position of a key
 // whose tile t has t >> 8 == h (the digit bases of the pass over the tile's
@@ -99,7 +105,7 @@ Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64
 Status launch_ranges_active(const uint32_t* keys, uint64_t n_cap, const uint64_t* d_n, uint2* ranges,
                             uint32_t n_tiles, const uint32_t* done, uint32_t* active, uint32_t* n_active,
                             uint32_t* overflow, const uint32_t* hi_bases, uint32_t* strips, bool wide,
-                            cudaStream_t st);
+                            uint32_t fine_min, cudaStream_t st);
 
 // Blend of the active tiles of one slice: persistent CTAs take tiles from the
 // active list, composite the slice's entries onto each pixel's carried state,
@@ -114,9 +120,9 @@ struct SliceBlendArgs {
                                 // tiles whose strip word has kStripSeen (or kStripSeenNow)
     const uint64_t* pix_base;   // per view
     uint32_t* done;             // per-tile bitmap
-    uint32_t* strips;           // per tile: bit s set once strip s's pixels all stopped, kStripSeenNow once
-                                // this slice blended it, kStripSeen once an earlier one did
-    uint32_t active_cap;        // capacity of `active` (4 x all tiles of the launch set)
+    uint32_t* strips;           // per tile: row bits of the rows whose pixels all stopped, kStripSeenNow
+                                // once this slice blended it, kStripSeen once an earlier one did
+    uint32_t active_cap;        // capacity of `active` (kActivePerTile x all tiles of the launch set)
 };
 Status launch_blend_slice(const uint2* ranges, const uint32_t* values, const SplatArrays& sp,
                           const ViewParams* views, int V, uint32_t n_entries, const float* bg,
