@@ -571,6 +571,9 @@ size_t pair_bytes_for(uint64_t P, bool wide) { return P * (wide ? 36 : 24) + rad
 // the entries but few pairs, since most tiles have stopped by then, and its
 // pairs are sorted by (tile, depth) instead.  Frames are the same; only the
 // work differs.
+#ifndef TIGAS_LIST_FROM
+#define TIGAS_LIST_FROM 6   // in eighths of the slice count: the first slice emitting from a list
+#endif
 #ifndef TIGAS_FINE_FROM
 #define TIGAS_FINE_FROM 6   // in eighths of the slice count: the first slice whose long lists take 4-row strips
 #endif
@@ -631,7 +634,8 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     uint32_t* d_visible = d_hdr->visible;
     uint64_t* d_total = ctx.fixed.take<uint64_t>(kMaxSlices + 2);
     unsigned long long* d_counters = ctx.fixed.take<unsigned long long>(4);
-    uint32_t* d_misc = ctx.fixed.take<uint32_t>(4);       // [longest tiles, short tiles, work counter, long tiles]
+    // [longest tiles, short tiles, work counter, long tiles, listed entries]
+    uint32_t* d_misc = ctx.fixed.take<uint32_t>(8);
     SplatArrays sp{};
     sp.geom = ctx.fixed.take<float4>(E);
     sp.appear = ctx.fixed.take<float4>(E);
@@ -727,6 +731,10 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
     // its few longest 8-row strips (8-view launch set, 7 slices: 3.405 ms with 8-row
     // strips only, 3.378 with 4-row strips from slice 5, 3.399 from slice 3)
     const int fine_from = (S * TIGAS_FINE_FROM) / 8;
+    // the last quarter of the slices emit from a list of their entries with pairs
+    // (8-view launch set, 7 slices: emit 0.272 -> 0.243 ms, the counts' list
+    // 0.242 -> 0.250 ms; from slice 3 on: 0.240 and 0.254)
+    const int list_from = (S * TIGAS_LIST_FROM) / 8;
     if (stat) {
         // pair buffers for the fixed capacity, taken once
         ctx.pairs.reset();
@@ -762,12 +770,16 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
         // also clears the slice's active-list counts and blend work counter (d_misc[0..3])
         // and, with fixed capacities (the pair buffers already taken), the pair sort's
         // scratch words, so that the sort runs no memset
-        TIGAS_TRY(launch_running_sat(d_views, V, done, sat, d_misc, 4, stat ? stmp : nullptr,
+        TIGAS_TRY(launch_running_sat(d_views, V, done, sat, d_misc, 5, stat ? stmp : nullptr,
                                      (int)radix_zero_words(pair_passes), st));
+        // a late slice lists its entries with pairs (at most one per pair, so the list
+        // fits a pair buffer that the sort fills only later) and emits from the list
+        uint32_t* list = stat && i >= list_from ? vals_c : nullptr;
         // the count kernel writes each entry's prefix within its block of kScanBlock
         // entries and the blocks' sums; the scan of the sums gives the blocks'
         // offsets and the slice total (*d_P; the closing zero count puts the total at b)
-        TIGAS_TRY(launch_count_slice(rect_sorted, a, b, d_views, V, sat, inblock, count_sums, compact, st));
+        TIGAS_TRY(launch_count_slice(rect_sorted, a, b, d_views, V, sat, inblock, count_sums, compact, list,
+                                     d_misc + 4, static_cap, st));
         TIGAS_TRY(launch_scan_u32(count_sums, nullptr, block_offs, (b - a + 1 + kScanBlock - 1) / kScanBlock, d_P,
                                   tmp, st));
         TIGAS_TRY(mark(kStScan, false));
@@ -791,7 +803,7 @@ Status render_frame_sliced(Scene* scene, FrameRequest& req, RenderContext& ctx, 
         TIGAS_TRY(mark(kStEmit, true));
         TIGAS_TRY(launch_emit_slice(compact ? nullptr : order, rect_sorted, a, b, inblock, block_offs, d_views, V,
                                     done, keys_a, vals_a, cap, d_flags, compact, wide ? sp.depth_key : nullptr,
-                                    sp.key_range, st));
+                                    sp.key_range, list, d_misc + 4, static_cap, st));
         TIGAS_TRY(mark(kStEmit, false));
         TIGAS_TRY(mark(kStPairSort, true));
         SortExtras pex;

@@ -143,7 +143,8 @@ k_running_sat(const ViewParams* __restrict__ views_g, const uint32_t* __restrict
 template <bool COMPACT, int kCountThreads>
 __global__ void __launch_bounds__(kCountThreads)
 k_count_slice(const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b, const ViewParams* __restrict__ views_g,
-              int V, const uint32_t* __restrict__ sat, uint32_t* __restrict__ inblock, uint32_t* __restrict__ sums) {
+              int V, const uint32_t* __restrict__ sat, uint32_t* __restrict__ inblock, uint32_t* __restrict__ sums,
+              uint32_t* __restrict__ list, uint32_t* __restrict__ n_list, uint32_t list_cap) {
     constexpr int kCountItems = (int)kScanBlock / kCountThreads;
     constexpr int kW = kCountThreads / 32;
     __shared__ uint32_t s_sb[kMaxViews], s_w1[kMaxViews], ws[kW + 1];
@@ -180,11 +181,13 @@ k_count_slice(const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b, con
     // the block's exclusive prefix: each thread scans kCountItems consecutive
     // counts, the threads' totals are scanned across the block
     uint32_t v[kCountItems];
-    uint32_t tsum = 0;
+    uint32_t tsum = 0, nzmask = 0;   // nzmask bit q: the thread's entry q has pairs
+    static_assert(kCountItems <= 32, "one mask bit per entry of the thread");
 #pragma unroll
     for (int q = 0; q < kCountItems; ++q) {
         v[q] = buf[pad(threadIdx.x * kCountItems + q)];
         tsum += v[q];
+        nzmask |= (v[q] > 0u ? 1u : 0u) << q;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t incl = tsum;
@@ -212,6 +215,35 @@ k_count_slice(const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b, con
     for (int q = 0; q < kCountItems; ++q) {
         buf[pad(threadIdx.x * kCountItems + q)] = off;
         off += v[q];
+    }
+    if (list) {
+        // the block's entries with pairs, appended to the list (blocks in any order,
+        // each block's in entry order): the emit then visits those alone
+        const uint32_t nz = __popc(nzmask);
+        uint32_t zi = nz;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, zi, d);
+            if (lane >= d) zi += y;
+        }
+        __shared__ uint32_t zs[kW + 1];
+        if (lane == 31) zs[warp] = zi;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t x = lane < kW ? zs[lane] : 0u;
+            uint32_t wi = x;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, wi, d);
+                if (lane >= d) wi += y;
+            }
+            if (lane < kW) zs[lane] = wi - x;
+            if (lane == kW - 1) zs[kW] = wi ? atomicAdd(n_list, wi) : 0u;   // the block's first list slot
+        }
+        __syncthreads();
+        uint32_t at = zs[kW] + zs[warp] + zi - nz;
+        for (uint32_t m = nzmask; m; m &= m - 1u, ++at)
+            if (at < list_cap) list[at] = (uint32_t)(base + (uint64_t)threadIdx.x * kCountItems + (__ffs(m) - 1));
     }
     __syncthreads();
 #pragma unroll
@@ -359,6 +391,51 @@ k_emit_slice(const uint32_t* __restrict__ order, const uint2* __restrict__ rect_
         if (m)
             emit_warp_segmented<COMPACT, WIDE>(m, rr[j], ee[j], pos[j], dk[j], s_tb, s_tx, done, keys, values,
                                                pair_cap, overflow);
+    }
+}
+
+// The same pairs from the list of the slice's entries with pairs (entry
+// indices relative to a, n_list of them, in any order): persistent warps take
+// 32 list entries at a time.  For a late slice, whose entries mostly meet only
+// stopped tiles, this visits the few with pairs instead of every entry.
+template <bool COMPACT, bool WIDE>
+__global__ void __launch_bounds__(kEmitThreads)
+k_emit_list(const uint32_t* __restrict__ order, const uint2* __restrict__ rect_sorted, uint64_t a,
+            const uint32_t* __restrict__ inblock, const uint32_t* __restrict__ block_offs,
+            const uint32_t* __restrict__ list, const uint32_t* __restrict__ n_list, uint32_t list_cap,
+            const ViewParams* __restrict__ views_g, int V, const uint32_t* __restrict__ done,
+            uint32_t* __restrict__ keys, uint32_t* __restrict__ values, uint64_t pair_cap,
+            uint32_t* __restrict__ overflow, const uint32_t* __restrict__ depth_key,
+            const uint32_t* __restrict__ key_range) {
+    __shared__ uint32_t s_tb[kMaxViews], s_tx[kMaxViews];
+    for (int k = threadIdx.x; k < V; k += blockDim.x) {
+        s_tb[k] = views_g[k].tile_base;
+        s_tx[k] = (uint32_t)views_g[k].TX;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t n_all = *n_list, n = min(n_all, list_cap);
+    // a list that outgrew its capacity (more entries with pairs than pair slots) left
+    // entries out: the pair buffers overflowed too, and the frame is rendered again
+    if (n_all > list_cap && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(overflow, 1u);
+    const uint32_t kmin = WIDE ? key_range[0] : 0u;
+    const uint64_t stride = (uint64_t)gridDim.x * kEmitThreads;
+    for (uint64_t w = ((uint64_t)blockIdx.x * (kEmitThreads / 32) + warp) * 32u; w < n; w += stride) {
+        const uint64_t li = w + lane;
+        uint32_t pos = 0, cnt = 0, ee = 0, dk = 0;
+        uint2 rr = make_uint2(0u, 0u);
+        if (li < n) {
+            const uint32_t k = list[li];   // its count's successor k + 1 is at most the closing zero
+            pos = block_offs[k / kScanBlock] + inblock[k];
+            cnt = block_offs[(k + 1u) / kScanBlock] + inblock[k + 1u] - pos;
+            rr = rect_sorted[a + k];
+            ee = COMPACT ? rr.y : order[a + k];
+            if (WIDE) dk = depth_key[ee] - kmin;
+        }
+        const uint32_t m = __ballot_sync(kFull, cnt > 0u);
+        if (m)
+            emit_warp_segmented<COMPACT, WIDE>(m, rr, ee, pos, dk, s_tb, s_tx, done, keys, values, pair_cap,
+                                               overflow);
     }
 }
 
@@ -523,18 +600,29 @@ Status launch_running_sat(const ViewParams* views, int V, const uint32_t* done, 
 }
 
 Status launch_count_slice(const uint2* rect_sorted, uint64_t a, uint64_t b, const ViewParams* views, int V,
-                          const uint32_t* sat, uint32_t* inblock, uint32_t* sums, bool compact, cudaStream_t st) {
+                          const uint32_t* sat, uint32_t* inblock, uint32_t* sums, bool compact, uint32_t* list,
+                          uint32_t* n_list, uint64_t list_cap, cudaStream_t st) {
     if (b <= a) return {};
+    if (list && !n_list) return {TIGAS_ERR_INVALID, "an entry list needs its counter"};
+    const uint32_t lc = (uint32_t)(list_cap < 0xFFFFFFFFull ? list_cap : 0xFFFFFFFFull);
     const unsigned grid = (unsigned)((b - a + 1 + kScanBlock - 1) / kScanBlock);
     // a slice of few blocks (less than two per SM) takes 1024 threads per block,
     // 4 rectangles each, so that its few CTAs hold more warps
     const bool big = grid < 2u * (unsigned)kSmCount;
     if (compact) {
-        if (big) k_count_slice<true, 1024><<<grid, 1024, 0, st>>>(rect_sorted, a, b, views, V, sat, inblock, sums);
-        else k_count_slice<true, 256><<<grid, 256, 0, st>>>(rect_sorted, a, b, views, V, sat, inblock, sums);
+        if (big)
+            k_count_slice<true, 1024><<<grid, 1024, 0, st>>>(rect_sorted, a, b, views, V, sat, inblock, sums, list,
+                                                             n_list, lc);
+        else
+            k_count_slice<true, 256><<<grid, 256, 0, st>>>(rect_sorted, a, b, views, V, sat, inblock, sums, list,
+                                                           n_list, lc);
     } else {
-        if (big) k_count_slice<false, 1024><<<grid, 1024, 0, st>>>(rect_sorted, a, b, views, V, sat, inblock, sums);
-        else k_count_slice<false, 256><<<grid, 256, 0, st>>>(rect_sorted, a, b, views, V, sat, inblock, sums);
+        if (big)
+            k_count_slice<false, 1024><<<grid, 1024, 0, st>>>(rect_sorted, a, b, views, V, sat, inblock, sums, list,
+                                                              n_list, lc);
+        else
+            k_count_slice<false, 256><<<grid, 256, 0, st>>>(rect_sorted, a, b, views, V, sat, inblock, sums, list,
+                                                            n_list, lc);
     }
     TIGAS_LAUNCHED();
     return {};
@@ -544,10 +632,32 @@ Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64
                          const uint32_t* inblock, const uint32_t* block_offs, const ViewParams* views, int V,
                          const uint32_t* done,
                          uint32_t* keys, uint32_t* values, uint64_t pair_cap, uint32_t* overflow, bool compact,
-                         const uint32_t* wide_depth, const uint32_t* key_range, cudaStream_t st) {
+                         const uint32_t* wide_depth, const uint32_t* key_range, const uint32_t* list,
+                         const uint32_t* n_list, uint64_t list_cap, cudaStream_t st) {
     if (b <= a) return {};
     if (wide_depth && (!key_range || (reinterpret_cast<uintptr_t>(keys) & 7u)))
         return {TIGAS_ERR_INVALID, "wide emit needs the key range and 8-byte aligned keys"};
+    if (list) {
+        if (!n_list) return {TIGAS_ERR_INVALID, "an entry list needs its counter"};
+        const uint32_t lc = (uint32_t)(list_cap < 0xFFFFFFFFull ? list_cap : 0xFFFFFFFFull);
+        // persistent warps over the list, at most 8 CTAs per SM
+        const uint64_t most = (b - a + kEmitThreads - 1) / kEmitThreads;
+        const unsigned grid = (unsigned)(most < 8u * kSmCount ? most : 8u * kSmCount);
+#define TIGAS_EMIT_LIST(CC, WW)                                                                                 \
+    k_emit_list<CC, WW><<<grid, kEmitThreads, 0, st>>>(order, rect_sorted, a, inblock, block_offs, list, n_list, \
+                                                       lc, views, V, done, keys, values, pair_cap, overflow,     \
+                                                       wide_depth, key_range)
+        if (compact) {
+            if (wide_depth) TIGAS_EMIT_LIST(true, true);
+            else TIGAS_EMIT_LIST(true, false);
+        } else {
+            if (wide_depth) TIGAS_EMIT_LIST(false, true);
+            else TIGAS_EMIT_LIST(false, false);
+        }
+#undef TIGAS_EMIT_LIST
+        TIGAS_LAUNCHED();
+        return {};
+    }
     // entries per lane: the largest J in {1, 2, 4, 8} that still leaves about
     // 4 waves of 8 CTAs per SM (slices with many pairs per entry want the warps)
     const uint64_t n = b - a;

@@ -71,8 +71,12 @@ Status launch_running_sat(const ViewParams* views, int V, const uint32_t* done, 
 // inblock[k - a] = the sum of count over the entries before k in k's block
 // (kScanBlock consecutive entries; b - a + 1 values), and sums[j] = block j's
 // total.  compact: rectangles in the compact form (SplatArrays::compact_rect).
+// list (or null): appends k - a of every entry with count(k) > 0 at
+// list[atomicAdd(n_list, ...)] (*n_list zero on entry; slots past list_cap
+// are counted but not written).
 Status launch_count_slice(const uint2* rect_sorted, uint64_t a, uint64_t b, const ViewParams* views, int V,
-                          const uint32_t* sat, uint32_t* inblock, uint32_t* sums, bool compact, cudaStream_t st);
+                          const uint32_t* sat, uint32_t* inblock, uint32_t* sums, bool compact, uint32_t* list,
+                          uint32_t* n_list, uint64_t list_cap, cudaStream_t st);
 
 // (tile, entry) pairs of entries [a, b) for tiles not done, entry k's at
 // block_offs[(k - a) / kScanBlock] + inblock[k - a] (block_offs: the exclusive
@@ -81,11 +85,13 @@ Status launch_count_slice(const uint2* rect_sorted, uint64_t a, uint64_t b, cons
 // wide_depth (the depth keys in entry order, key_range[0] the smallest kept
 // one): keys holds 64-bit keys (tile << 32 | depth key - key_range[0]), for a
 // slice whose entries are not in depth order; null: 32-bit tile keys.
+// list (or null): visit only the min(*n_list, list_cap) entries the count
+// kernel listed (the same pairs, fewer entries read).
 Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64_t a, uint64_t b,
                          const uint32_t* inblock, const uint32_t* block_offs, const ViewParams* views, int V,
                          const uint32_t* done, uint32_t* keys, uint32_t* values, uint64_t pair_cap,
                          uint32_t* overflow, bool compact, const uint32_t* wide_depth, const uint32_t* key_range,
-                         cudaStream_t st);
+                         const uint32_t* list, const uint32_t* n_list, uint64_t list_cap, cudaStream_t st);
 
 // Tile ranges of the slice's sorted keys, and the list of tiles with pairs
 // that are not done, in three regions of `active` (kActivePerTile n_tiles
