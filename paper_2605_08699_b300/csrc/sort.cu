@@ -457,7 +457,7 @@ struct OsRoute {
     uint32_t* far_v;
     uint2* far_p;
     uint32_t active;
-    uint32_t pad;
+    int32_t next;            // deferred histograms: the next pass that runs (its digits counted here), or -1
 };
 constexpr int kRouteWords = (int)(sizeof(OsRoute) / 4);
 
@@ -577,9 +577,10 @@ template <typename K, int KB, bool VEC>
 __global__ void __launch_bounds__(512, 2)
 k_os_hist(const K* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, int begin_bit, int end_bit,
           uint32_t* __restrict__ ghist, const uint32_t* __restrict__ range, uint4* __restrict__ status,
-          uint64_t chunks, uint32_t chunk_keys) {
+          uint64_t chunks, uint32_t chunk_keys, int count_passes, unsigned long long* __restrict__ bits_or) {
     constexpr int kP = (int)sizeof(K);   // most passes this key width can need
     __shared__ uint32_t h[kP][256];
+    __shared__ unsigned long long s_or[2];
     const int passes = (end_bit - begin_bit + 7) / 8;
     const uint32_t n = count_of(n_cap, d_n);
     const uint64_t used = ((uint64_t)n + chunk_keys - 1) / chunk_keys;
@@ -612,13 +613,24 @@ k_os_hist(const K* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, int b
         const int need = (bits - begin_bit + 7) / 8;
         hp = need < 1 ? 1 : (need < passes ? need : passes);
     }
+    // deferred histograms: only the first pass's digits are counted here (each
+    // scatter pass counts the next one's), and the keys' bits that vary
+    // (bits_or: OR of the keys, OR of their complements) tell which passes run
+    if (count_passes < hp) hp = count_passes;
     for (int i = threadIdx.x; i < hp * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+    if (threadIdx.x < 2) s_or[threadIdx.x] = 0ull;
     __syncthreads();
+    unsigned long long k_or = 0, k_nor = 0;
+    const bool skip_far = km.split;   // a partial sort's far keys take no later pass
     uint32_t cur[kP], run[kP];
 #pragma unroll
     for (int p = 0; p < kP; ++p) { cur[p] = 0xFFFFFFFFu; run[p] = 0; }
     // one key into every pass's run-length count
     auto count = [&](K k) {
+        if (bits_or && !(skip_far && k == ~K(0))) {
+            k_or |= (unsigned long long)k;
+            k_nor |= (unsigned long long)(K)~k;
+        }
 #pragma unroll
         for (int p = 0; p < kP; ++p) {
             if (p < hp) {
@@ -677,21 +689,55 @@ k_os_hist(const K* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, int b
 #pragma unroll
     for (int p = 0; p < kP; ++p)
         if (p < hp && run[p]) atomicAdd(&h[p][cur[p]], run[p]);
+    if (bits_or) {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            k_or |= __shfl_xor_sync(kFull, k_or, d);
+            k_nor |= __shfl_xor_sync(kFull, k_nor, d);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicOr(&s_or[0], k_or);
+            atomicOr(&s_or[1], k_nor);
+        }
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < hp * 256; i += blockDim.x) {
         uint32_t c = (&h[0][0])[i];
         if (c) atomicAdd(&ghist[i], c);
     }
+    if (bits_or && threadIdx.x < 2 && s_or[threadIdx.x]) atomicOr(&bits_or[threadIdx.x], s_or[threadIdx.x]);
 }
 
 // ghist[p][256] -> exclusive digit bases gbase[p][256], and every pass's route:
 // pass 0 always runs, a later pass only if more than one of its digits occurs.
+// Deferred histograms (bits_or given): only pass 0's histogram is known here
+// (its bases are written; each later pass's scatter computes its own from the
+// histogram the pass before it counted), and a later pass runs if a bit of
+// its digit varies among the keys (bits_or: OR of the keys' digit bits and of
+// their complements; the digits cover bits [begin_bit, end_bit)).
 __global__ void __launch_bounds__(256) k_os_bases(const uint32_t* __restrict__ ghist, uint32_t* __restrict__ gbase,
                                                   int passes, OsRoute* __restrict__ routes, OsBuffers bufs,
-                                                  uint32_t* __restrict__ n_active_out, bool near_split) {
+                                                  uint32_t* __restrict__ n_active_out, bool near_split,
+                                                  const unsigned long long* __restrict__ bits_or, int begin_bit,
+                                                  int end_bit, uint64_t n_cap, const uint64_t* d_n_later) {
     __shared__ uint32_t ws[9];
     __shared__ uint32_t act[8];
+    const int width = end_bit - begin_bit;   // 1 .. 64
+    const unsigned long long varies =
+        bits_or ? ((bits_or[0] & bits_or[1]) >> begin_bit) & (width >= 64 ? ~0ull : (1ull << width) - 1ull) : 0ull;
     for (int p = 0; p < passes; ++p) {
+        if (bits_or && p > 0) {
+            const uint32_t digit_var = (uint32_t)((varies >> (8 * p)) & 0xFFull);
+            if (threadIdx.x == 0) act[p] = digit_var != 0u ? 1u : 0u;
+            if (digit_var == 0u) {
+                // a pass that does not run: every key has the same digit c (the bits of
+                // the OR of the keys), so its bases are 0 up to c and the count after
+                const uint32_t c = (uint32_t)((bits_or[0] >> (begin_bit + 8 * p)) & 0xFFull);
+                const uint32_t nn = count_of(n_cap, d_n_later);
+                gbase[p * 256 + threadIdx.x] = threadIdx.x <= c ? 0u : nn;
+            }
+            continue;
+        }
         const uint32_t x = ghist[p * 256 + threadIdx.x];
         const uint32_t e = cta_exclusive_scan<256>(x, ws);
         gbase[p * 256 + threadIdx.x] = e;
@@ -723,6 +769,12 @@ __global__ void __launch_bounds__(256) k_os_bases(const uint32_t* __restrict__ g
                     r.far_v = bufs.out_v;
                     r.far_p = bufs.in_p ? bufs.out_p : nullptr;
                 }
+                r.next = -1;
+                for (int q = p + 1; q < passes; ++q)
+                    if (act[q]) {
+                        r.next = q;
+                        break;
+                    }
                 sk = r.dst_k;
                 sv = r.dst_v;
                 spp = r.dst_p;
@@ -790,6 +842,8 @@ struct OsSmem {
     uint32_t whist[W][256];
     uint32_t dstart[256];
     uint32_t gshift[256];   // global position of the digit's first key in this tile, minus its tile position
+    uint32_t bases[256];    // deferred histograms: this pass's digit bases
+    uint32_t nhist[256];    // deferred histograms: the next pass's digit counts of this tile
     uint32_t ws[W + 1];
     uint32_t chunk;
 };
@@ -797,8 +851,9 @@ struct OsSmem {
 template <typename K, int PAY, bool MAP>
 __global__ void __launch_bounds__(OsCfg<K, PAY>::kT, OsCfg<K, PAY>::kMinBlocks)
 k_os_scatter(const OsRoute* __restrict__ route, uint64_t n_cap, const uint64_t* d_n, int shift, int nbits,
-             const uint32_t* __restrict__ gbase, uint32_t* status, uint32_t* chunk_counter, uint32_t* flags,
-             int spin_limit, const uint32_t* __restrict__ range) {
+             uint32_t* __restrict__ gbase, uint32_t* status, uint32_t* chunk_counter, uint32_t* flags,
+             int spin_limit, const uint32_t* __restrict__ range, uint32_t* __restrict__ ghist_all, int pass,
+             int begin_bit, int end_bit) {
     if (route->active == 0u) return;   // identity pass: skipped by every CTA
     // a grid sized for the capacity (graph replays size the pair sorts for the
     // largest slice): CTAs past the keys leave before claiming a chunk, so the
@@ -815,6 +870,13 @@ k_os_scatter(const OsRoute* __restrict__ route, uint64_t n_cap, const uint64_t* 
     K* const far_k = static_cast<K*>(route->far_k);
     uint32_t* const far_v = route->far_v;
     uint2* const far_p = route->far_p;
+    // deferred histograms (ghist_all given): a later pass's digit bases come from the
+    // count the pass before it made, and a pass counts the digits of the next one
+    const uint32_t* const hist_this = ghist_all && pass > 0 ? ghist_all + 256 * pass : nullptr;
+    const int next = ghist_all ? route->next : -1;
+    uint32_t* const hist_next = next > 0 ? ghist_all + 256 * next : nullptr;
+    const int nshift = begin_bit + 8 * (next > 0 ? next : 0);
+    const int next_bits = min(8, end_bit - nshift);
     const bool has_vals = PAY != kPayOnly && vals_out != nullptr;   // no value stream: the payload identifies each key
     // The payload sort (few, large launches) walks back for its digit offsets
     // only after its tile is sorted in shared memory, so the wait overlaps that
@@ -836,12 +898,23 @@ k_os_scatter(const OsRoute* __restrict__ route, uint64_t n_cap, const uint64_t* 
     if (MAP) km.load(range);
     if (threadIdx.x == 0) sm.chunk = atomicAdd(chunk_counter, 1u);
     for (int k = threadIdx.x; k < W * 256; k += T) (&sm.whist[0][0])[k] = 0;
+    if (hist_next)
+        for (int k = threadIdx.x; k < 256; k += T) sm.nhist[k] = 0;
     __syncthreads();
     const uint32_t chunk = sm.chunk;
     const uint32_t n = count_of(n_cap, d_n);
     const uint64_t base = (uint64_t)chunk * N;
     if (base >= n) return;   // CTA-uniform; no later chunk waits on it
     const uint32_t valid = (n - base) < (uint64_t)N ? (uint32_t)(n - base) : (uint32_t)N;
+    if (hist_this) {
+        // deferred histograms: the digit bases from the count the previous pass made
+        const uint32_t x = threadIdx.x < 256 ? hist_this[threadIdx.x] : 0u;
+        const uint32_t e = cta_exclusive_scan<T>(x, sm.ws);
+        if (threadIdx.x < 256) {
+            sm.bases[threadIdx.x] = e;
+            if (chunk == 0) gbase[threadIdx.x] = e;   // for readers after the sort
+        }
+    }
 
     K key[I];
     uint32_t val[I];
@@ -858,6 +931,16 @@ k_os_scatter(const OsRoute* __restrict__ route, uint64_t n_cap, const uint64_t* 
             key[r] = ~K(0);
             val[r] = 0;
             if (PAY) pay[r] = make_uint2(0u, 0u);
+        }
+    }
+    if (hist_next) {
+        // the next pass's digit counts (a partial sort's far keys take no later pass)
+        const uint32_t nmask = (1u << next_bits) - 1u;
+#pragma unroll
+        for (int r = 0; r < I; ++r) {
+            const uint32_t li = warp * (I * 32) + r * 32 + lane;
+            if (li < valid && !(far_k != nullptr && key[r] == ~K(0)))
+                atomicAdd(&sm.nhist[(uint32_t)(key[r] >> nshift) & nmask], 1u);
         }
     }
     uint32_t dr[I];
@@ -896,7 +979,7 @@ k_os_scatter(const OsRoute* __restrict__ route, uint64_t n_cap, const uint64_t* 
             st_relaxed(status + (size_t)chunk * 256 + d, (chunk == 0 ? kFlagPre : kFlagAgg) | (cnt & kValMask));
         } else {
             const uint32_t excl = lookback_exclusive<kWin>(status, chunk, d, cnt, true, flags, spin_limit);
-            sm.gshift[d] = (d <= mask ? gbase[d] : 0u) + excl;   // tile position subtracted below
+            sm.gshift[d] = (d <= mask ? (hist_this ? sm.bases[d] : gbase[d]) : 0u) + excl;   // tile position subtracted below
         }
     }
     // restore the padding count for the in-tile layout (padding sorts last)
@@ -920,7 +1003,7 @@ k_os_scatter(const OsRoute* __restrict__ route, uint64_t n_cap, const uint64_t* 
         if (threadIdx.x < 256) {
             const uint32_t d = threadIdx.x;
             const uint32_t excl = lookback_exclusive<kWin>(status, chunk, d, cnt, false, flags, spin_limit);
-            sm.gshift[d] = (d <= mask ? gbase[d] : 0u) + excl - start;
+            sm.gshift[d] = (d <= mask ? (hist_this ? sm.bases[d] : gbase[d]) : 0u) + excl - start;
         }
     }
     __syncthreads();
@@ -939,6 +1022,7 @@ k_os_scatter(const OsRoute* __restrict__ route, uint64_t n_cap, const uint64_t* 
             }
         }
     }
+    if (hist_next && threadIdx.x < 256 && sm.nhist[threadIdx.x]) atomicAdd(&hist_next[threadIdx.x], sm.nhist[threadIdx.x]);
 }
 
 template <typename K, int PAY, bool MAP>
@@ -958,7 +1042,11 @@ Status ensure_os_smem() {
 
 uint64_t os_chunks(uint64_t n_cap) { return (n_cap + 4095) / 4096; }   // upper bound for every tile shape
 
-// tmp layout: chunk counters [8], flags [7], active passes [1], ghist [8][256],
+#ifndef TIGAS_OS_DEFER
+#define TIGAS_OS_DEFER 1
+#endif
+// tmp layout: chunk counters [8], flags [1], (unused) [1], OR of the keys and
+// of their complements [2 x u64], (unused) [1], active passes [1], ghist [8][256],
 // gbase [8][256], routes [8], status [pass][chunks][256] (cleared by the
 // histogram kernel); the words a sort of p passes needs zeroed on entry are
 // the first radix_zero_words(p) (counters, flags and p histograms), and the
@@ -994,17 +1082,26 @@ Status radix_sort_onesweep(const K* keys_in, const uint32_t* values_in, K* keys_
     const uint64_t hist_step = (uint64_t)512 * (vec ? kHistVecs * 4 : kHistKeys) * 8;
     const uint64_t hist_ctas = (n_cap + hist_step - 1) / hist_step;
     const unsigned hgrid = (unsigned)(hist_ctas < kSmCount ? kSmCount : (hist_ctas > kSmCount * 8 ? kSmCount * 8 : hist_ctas));
+    // deferred histograms: the histogram kernel counts the first pass's digits
+    // (and ORs the keys' bits, which tell the passes that run), each scatter
+    // pass the next one's
+    const bool deferred = TIGAS_OS_DEFER && passes > 1;
+    unsigned long long* bits_or = deferred ? reinterpret_cast<unsigned long long*>(counters + 10) : nullptr;
+    const int count_passes = deferred ? 1 : passes;
     if (vec)
-        k_os_hist<K, kHistVecs, true><<<hgrid, 512, 0, st>>>(
-            keys_in, n_cap, d_n, begin_bit, end_bit, ghist, range, reinterpret_cast<uint4*>(status), chunks, (uint32_t)N);
+        k_os_hist<K, kHistVecs, true><<<hgrid, 512, 0, st>>>(keys_in, n_cap, d_n, begin_bit, end_bit, ghist, range,
+                                                              reinterpret_cast<uint4*>(status), chunks, (uint32_t)N,
+                                                              count_passes, bits_or);
     else
-        k_os_hist<K, kHistKeys, false><<<hgrid, 512, 0, st>>>(
-            keys_in, n_cap, d_n, begin_bit, end_bit, ghist, range, reinterpret_cast<uint4*>(status), chunks, (uint32_t)N);
+        k_os_hist<K, kHistKeys, false><<<hgrid, 512, 0, st>>>(keys_in, n_cap, d_n, begin_bit, end_bit, ghist, range,
+                                                               reinterpret_cast<uint4*>(status), chunks, (uint32_t)N,
+                                                               count_passes, bits_or);
     TIGAS_LAUNCHED();
     OsBuffers bufs{keys_in, values_in, PAY ? ex->pay_in : nullptr, keys_alt, values_alt, PAY ? ex->pay_alt : nullptr,
                    keys_out, values_out, PAY ? ex->pay_out : nullptr};
     const bool split = MAP && ex->near_split;
-    k_os_bases<<<1, 256, 0, st>>>(ghist, gbase, passes, routes, bufs, counters + 15, split);
+    k_os_bases<<<1, 256, 0, st>>>(ghist, gbase, passes, routes, bufs, counters + 15, split, bits_or, begin_bit,
+                                  end_bit, n_cap, split ? ex->d_near : d_n);
     TIGAS_LAUNCHED();
     for (int p = 0; p < passes; ++p) {
         const int shift = begin_bit + 8 * p;
@@ -1016,11 +1113,11 @@ Status radix_sort_onesweep(const K* keys_in, const uint32_t* values_in, K* keys_
             TIGAS_TRY((ensure_os_smem<K, PAY, false>()));
             k_os_scatter<K, PAY, false><<<(unsigned)chunks, T, sizeof(OsSmem<K, PAY>), st>>>(
                 routes + p, n_cap, pn, shift, nb, gbase + p * 256, status + (size_t)p * chunks * 256, counters + p,
-                flags, kSpinLimit, nullptr);
+                flags, kSpinLimit, nullptr, deferred ? ghist : nullptr, p, begin_bit, end_bit);
         } else {
             k_os_scatter<K, PAY, MAP><<<(unsigned)chunks, T, sizeof(OsSmem<K, PAY>), st>>>(
                 routes + p, n_cap, pn, shift, nb, gbase + p * 256, status + (size_t)p * chunks * 256, counters + p,
-                flags, kSpinLimit, range);
+                flags, kSpinLimit, range, deferred ? ghist : nullptr, p, begin_bit, end_bit);
         }
         TIGAS_LAUNCHED();
     }
@@ -1076,10 +1173,12 @@ Status debug_lookback_enqueue(int spin_limit, uint32_t* buf, uint32_t* flags, cu
     OsRoute* route = reinterpret_cast<OsRoute*>(buf + kProbeRoute);
     k_probe_init<<<16, 256, 0, st>>>(buf);
     OsBuffers bufs{keys, nullptr, nullptr, out, vals, nullptr, out, vals, nullptr};
-    k_os_hist<K, 8, false><<<4, 512, 0, st>>>(keys, kProbeN, nullptr, 0, 8, ghist, nullptr, nullptr, 0, 1);
-    k_os_bases<<<1, 256, 0, st>>>(ghist, gbase, 1, route, bufs, nullptr, false);
+    k_os_hist<K, 8, false><<<4, 512, 0, st>>>(keys, kProbeN, nullptr, 0, 8, ghist, nullptr, nullptr, 0, 1, 1,
+                                               nullptr);
+    k_os_bases<<<1, 256, 0, st>>>(ghist, gbase, 1, route, bufs, nullptr, false, nullptr, 0, 8, kProbeN, nullptr);
     k_os_scatter<K, kPayNone, false><<<1, T, sizeof(OsSmem<K, kPayNone>), st>>>(
-        route, kProbeN, nullptr, 0, 8, gbase, status, misc, flags ? flags : misc + 1, spin_limit, nullptr);
+        route, kProbeN, nullptr, 0, 8, gbase, status, misc, flags ? flags : misc + 1, spin_limit, nullptr, nullptr,
+        0, 0, 8);
     g_launches.fetch_add(4, std::memory_order_relaxed);
     TIGAS_CUDA_TRY(cudaGetLastError());
     return {};
