@@ -190,17 +190,20 @@ def kernel_traffic(kernel: str, views: int):
 STAGE_LIMITS = {
     "preprocess": "instructions: 592 thread instructions per (Gaussian, view), 73 % issue active, DRAM 46 % "
                   "of peak; traffic equals the algorithmic bytes",
-    "depth_sort": "instructions per key and load latency: 146-157 thread instructions per key per pass, "
-                  "42-50 % issue active, long_scoreboard first, DRAM 29-37 % of peak",
+    "depth_sort": "instructions per key and load latency: 172-192 thread instructions per key per pass, "
+                  "44-46 % issue active, long_scoreboard first, DRAM 20-27 % of peak; the threshold and "
+                  "histogram kernels each read every key once",
     "scan": "latency: per slice a one-CTA-per-view running-tile table (8 us, barrier first), a count of "
             "46-1655 CTAs (long_scoreboard first) and a one-CTA block-sum scan (about 4 us)",
-    "emit": "instructions per pair (43-56 % issue active, not_selected and wait first in the early slices); "
-            "the pairs stay in L2 (slice 0: 0.2 MB of DRAM writes for 40 MB of pairs)",
+    "emit": "instructions per pair (45-57 % issue active, not_selected and wait first in the early slices); "
+            "the pairs stay in L2 (slice 0: 0.2 MB of DRAM writes for 40 MB of pairs); the late slices "
+            "emit from a list of their entries with pairs",
     "pair_sort": "latency and L2: the pair lists live in L2 (DRAM reads are the keys' first touch), later "
-                 "slices' scatter passes run few CTAs at 18-31 % warps active, plus a one-CTA digit-base kernel",
-    "ranges": "latency: a sampled search per tile, long_scoreboard first, 9-12 us per slice",
-    "blend": "issue-bound in the first slice (83 % issue active), latency-bound in later ones "
-             "(long_scoreboard first); not DRAM-bound (6-12 % of peak)",
+                 "slices' scatter passes run at 28-47 % warps active, plus a one-CTA digit-base kernel; the "
+                 "last slice's six 64-bit passes about 10 us each",
+    "ranges": "latency: a sampled search per tile, long_scoreboard first, 8-13 us per slice",
+    "blend": "issue-bound in the first slice (77 % issue active), latency-bound in later ones "
+             "(long_scoreboard first) and ended by their longest lists; not DRAM-bound (6-12 % of peak)",
 }
 
 
