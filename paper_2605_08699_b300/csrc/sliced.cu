@@ -341,6 +341,9 @@ __device__ inline void emit_warp_segmented(uint32_t m, uint2 r, uint32_t e, uint
 // word (order unused).  WIDE: 64-bit (tile, depth) keys (depth_key: the keys
 // in entry order, key_range[0] their smallest kept value).
 constexpr int kEmitThreads = 256;
+#ifndef TIGAS_LIST_CTAS
+#define TIGAS_LIST_CTAS 8
+#endif
 template <bool COMPACT, int J, bool WIDE>
 __global__ void __launch_bounds__(kEmitThreads)
 k_emit_slice(const uint32_t* __restrict__ order, const uint2* __restrict__ rect_sorted, uint64_t a, uint64_t b,
@@ -640,9 +643,9 @@ Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64
     if (list) {
         if (!n_list) return {TIGAS_ERR_INVALID, "an entry list needs its counter"};
         const uint32_t lc = (uint32_t)(list_cap < 0xFFFFFFFFull ? list_cap : 0xFFFFFFFFull);
-        // persistent warps over the list, at most 8 CTAs per SM
+        // persistent warps over the list, at most TIGAS_LIST_CTAS CTAs per SM
         const uint64_t most = (b - a + kEmitThreads - 1) / kEmitThreads;
-        const unsigned grid = (unsigned)(most < 8u * kSmCount ? most : 8u * kSmCount);
+        const unsigned grid = (unsigned)(most < (uint64_t)TIGAS_LIST_CTAS * kSmCount ? most : TIGAS_LIST_CTAS * kSmCount);
 #define TIGAS_EMIT_LIST(CC, WW)                                                                                 \
     k_emit_list<CC, WW><<<grid, kEmitThreads, 0, st>>>(order, rect_sorted, a, inblock, block_offs, list, n_list, \
                                                        lc, views, V, done, keys, values, pair_cap, overflow,     \

@@ -821,12 +821,13 @@ def test_partial_depth_sort_gives_the_full_sort_frames(h1, cuda):
     histogram of the depth keys places it); the last slice's pairs are
     sorted by (tile, depth key) instead.  Frames equal those of one slice (a
     full depth sort) bit for bit, whether the threshold cuts the kept entries
-    (a pose that keeps most of the scene) or keeps all of them (a pose that
+    (a pose that keeps most of the scene), keeps all of them (a pose that
     culls most of it, so that the slices before the last reach past the kept
-    entries)."""
+    entries) or has none to keep (a camera facing away: background only)."""
     levels = [(320, 240), (160, 120)]
     poses = {"most kept": [synth.BASE_POSE, synth.trajectory(23, 5)[4]],
-             "most culled": [synth.Pose(0.9, 0.0, (0.0, 0.0, -1.5)), synth.Pose(-0.9, 0.3, (0.2, 0.0, -1.5))]}
+             "most culled": [synth.Pose(0.9, 0.0, (0.0, 0.0, -1.5)), synth.Pose(-0.9, 0.3, (0.2, 0.0, -1.5))],
+             "none kept": [synth.Pose(math.pi, 0.0, (0.0, 0.0, -3.0))] * 2}
     intrs = [synth.default_intrinsics(w, hh) for w, hh in levels]
     E = 2 * 100_000
     base = tg.get_schedules()
@@ -852,7 +853,7 @@ def test_partial_depth_sort_gives_the_full_sort_frames(h1, cuda):
                 kept, near = st["n_visible"], st["depth_sort_near"]
                 assert near <= kept < E
                 assert near == kept or near >= first, (name, sch, near, kept, first)
-                seen.add("all kept near" if near == kept else "cut")
-        assert seen == {"all kept near", "cut"}
+                seen.add("none kept" if kept == 0 else "all kept near" if near == kept else "cut")
+        assert seen == {"none kept", "all kept near", "cut"}
     finally:
         tg.set_schedules(base)
