@@ -896,131 +896,137 @@ k_os_scatter(const OsRoute* __restrict__ route, uint64_t n_cap, const uint64_t* 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     KeyMap km;
     if (MAP) km.load(range);
-    if (threadIdx.x == 0) sm.chunk = atomicAdd(chunk_counter, 1u);
-    for (int k = threadIdx.x; k < W * 256; k += T) (&sm.whist[0][0])[k] = 0;
+    const uint32_t n = count_of(n_cap, d_n);
     if (hist_next)
         for (int k = threadIdx.x; k < 256; k += T) sm.nhist[k] = 0;
-    __syncthreads();
-    const uint32_t chunk = sm.chunk;
-    const uint32_t n = count_of(n_cap, d_n);
-    const uint64_t base = (uint64_t)chunk * N;
-    if (base >= n) return;   // CTA-uniform; no later chunk waits on it
-    const uint32_t valid = (n - base) < (uint64_t)N ? (uint32_t)(n - base) : (uint32_t)N;
     if (hist_this) {
         // deferred histograms: the digit bases from the count the previous pass made
         const uint32_t x = threadIdx.x < 256 ? hist_this[threadIdx.x] : 0u;
         const uint32_t e = cta_exclusive_scan<T>(x, sm.ws);
         if (threadIdx.x < 256) {
             sm.bases[threadIdx.x] = e;
-            if (chunk == 0) gbase[threadIdx.x] = e;   // for readers after the sort
+            if (blockIdx.x == 0) gbase[threadIdx.x] = e;   // for readers after the sort
         }
     }
+    // Persistent CTAs: each claims chunks in order until none is left (a grid of
+    // at most the resident CTAs), so a small sort launches no CTAs that only leave.
+    // A claimed chunk's predecessors are held by running CTAs, so every look-back ends.
+    for (;;) {
+        if (threadIdx.x == 0) sm.chunk = atomicAdd(chunk_counter, 1u);
+        for (int k = threadIdx.x; k < W * 256; k += T) (&sm.whist[0][0])[k] = 0;
+        __syncthreads();
+        const uint32_t chunk = sm.chunk;
+        const uint64_t base = (uint64_t)chunk * N;
+        if (base >= n) break;   // CTA-uniform; no later chunk waits on it
+        const uint32_t valid = (n - base) < (uint64_t)N ? (uint32_t)(n - base) : (uint32_t)N;
 
-    K key[I];
-    uint32_t val[I];
-    uint2 pay[PAY ? I : 1];
-#pragma unroll
-    for (int r = 0; r < I; ++r) {
-        const uint32_t li = warp * (I * 32) + r * 32 + lane;
-        if (li < valid) {
-            key[r] = keys_in[base + li];
-            if constexpr (MAP) key[r] = km(key[r]);   // stored mapped: later passes need no map
-            val[r] = !has_vals ? 0u : vals_in ? vals_in[base + li] : (uint32_t)(base + li);
-            if (PAY) pay[r] = pays_in[base + li];
-        } else {
-            key[r] = ~K(0);
-            val[r] = 0;
-            if (PAY) pay[r] = make_uint2(0u, 0u);
-        }
-    }
-    if (hist_next) {
-        // the next pass's digit counts (a partial sort's far keys take no later pass)
-        const uint32_t nmask = (1u << next_bits) - 1u;
-#pragma unroll
+        K key[I];
+        uint32_t val[I];
+        uint2 pay[PAY ? I : 1];
+    #pragma unroll
         for (int r = 0; r < I; ++r) {
             const uint32_t li = warp * (I * 32) + r * 32 + lane;
-            if (li < valid && !(far_k != nullptr && key[r] == ~K(0)))
-                atomicAdd(&sm.nhist[(uint32_t)(key[r] >> nshift) & nmask], 1u);
-        }
-    }
-    uint32_t dr[I];
-    const uint32_t lt = lanemask_lt();
-#pragma unroll
-    for (int r = 0; r < I; ++r) {
-        // padding keys (all ones) take the largest digit, so they sort after every
-        // key; a mapped key is at most the map's span, below all ones
-        const uint32_t d = (uint32_t)(key[r] >> shift) & mask;
-        // peers by one ballot per digit bit (measured faster here than match.any
-        // with shared-memory atomics)
-        const uint32_t peers = digit_peers(d);
-        const uint32_t before = sm.whist[warp][d];
-        const uint32_t lower = peers & lt;   // peers in lower lanes
-        __syncwarp();
-        if (kLowerLeader ? lower == 0u : lane == __ffs(peers) - 1) sm.whist[warp][d] = before + __popc(peers);
-        __syncwarp();
-        dr[r] = (d << 16) | (before + __popc(lower));
-    }
-    __syncthreads();
-
-    // per digit: prefix over warps, the CTA's count, and look-back for earlier chunks
-    uint32_t cnt = 0;
-    if (threadIdx.x < 256) {
-        const uint32_t d = threadIdx.x;
-#pragma unroll
-        for (int w = 0; w < W; ++w) {
-            const uint32_t c = sm.whist[w][d];
-            sm.whist[w][d] = cnt;
-            cnt += c;
-        }
-        // padding keys (digit == mask) are not part of this chunk's counts
-        if (d == mask) cnt -= (uint32_t)(N - valid);
-        if constexpr (kLate) {
-            // this chunk's counts now; the walk back waits until the tile is sorted in shared memory
-            st_relaxed(status + (size_t)chunk * 256 + d, (chunk == 0 ? kFlagPre : kFlagAgg) | (cnt & kValMask));
-        } else {
-            const uint32_t excl = lookback_exclusive<kWin>(status, chunk, d, cnt, true, flags, spin_limit);
-            sm.gshift[d] = (d <= mask ? (hist_this ? sm.bases[d] : gbase[d]) : 0u) + excl;   // tile position subtracted below
-        }
-    }
-    // restore the padding count for the in-tile layout (padding sorts last)
-    const uint32_t local_cnt = threadIdx.x < 256 ? cnt + ((threadIdx.x == mask) ? (uint32_t)(N - valid) : 0u) : 0u;
-    const uint32_t start = cta_exclusive_scan<T>(local_cnt, sm.ws);
-    if (threadIdx.x < 256) {
-        sm.dstart[threadIdx.x] = start;
-        if constexpr (!kLate) sm.gshift[threadIdx.x] -= start;
-    }
-    __syncthreads();
-
-#pragma unroll
-    for (int r = 0; r < I; ++r) {
-        const uint32_t d = dr[r] >> 16;
-        const uint32_t pos = sm.dstart[d] + sm.whist[warp][d] + (dr[r] & 0xFFFFu);
-        sm.keys[pos] = key[r];
-        if (has_vals) sm.vals[pos] = val[r];
-        if (PAY) sm.pays[pos] = pay[r];
-    }
-    if constexpr (kLate) {
-        if (threadIdx.x < 256) {
-            const uint32_t d = threadIdx.x;
-            const uint32_t excl = lookback_exclusive<kWin>(status, chunk, d, cnt, false, flags, spin_limit);
-            sm.gshift[d] = (d <= mask ? (hist_this ? sm.bases[d] : gbase[d]) : 0u) + excl - start;
-        }
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int k = 0; k < I; ++k) {
-        const uint32_t j = k * T + threadIdx.x;
-        if (j < valid) {
-            const K kk = sm.keys[j];
-            const uint32_t d = (uint32_t)(kk >> shift) & mask;
-            const uint32_t g = sm.gshift[d] + j;
-            if (g < n) {
-                const bool far = far_k != nullptr && d == 255u;
-                (far ? far_k : keys_out)[g] = kk;
-                if (has_vals) (far ? far_v : vals_out)[g] = sm.vals[j];
-                if (PAY) (far ? far_p : pays_out)[g] = sm.pays[j];
+            if (li < valid) {
+                key[r] = keys_in[base + li];
+                if constexpr (MAP) key[r] = km(key[r]);   // stored mapped: later passes need no map
+                val[r] = !has_vals ? 0u : vals_in ? vals_in[base + li] : (uint32_t)(base + li);
+                if (PAY) pay[r] = pays_in[base + li];
+            } else {
+                key[r] = ~K(0);
+                val[r] = 0;
+                if (PAY) pay[r] = make_uint2(0u, 0u);
             }
         }
+        if (hist_next) {
+            // the next pass's digit counts (a partial sort's far keys take no later pass)
+            const uint32_t nmask = (1u << next_bits) - 1u;
+    #pragma unroll
+            for (int r = 0; r < I; ++r) {
+                const uint32_t li = warp * (I * 32) + r * 32 + lane;
+                if (li < valid && !(far_k != nullptr && key[r] == ~K(0)))
+                    atomicAdd(&sm.nhist[(uint32_t)(key[r] >> nshift) & nmask], 1u);
+            }
+        }
+        uint32_t dr[I];
+        const uint32_t lt = lanemask_lt();
+    #pragma unroll
+        for (int r = 0; r < I; ++r) {
+            // padding keys (all ones) take the largest digit, so they sort after every
+            // key; a mapped key is at most the map's span, below all ones
+            const uint32_t d = (uint32_t)(key[r] >> shift) & mask;
+            // peers by one ballot per digit bit (measured faster here than match.any
+            // with shared-memory atomics)
+            const uint32_t peers = digit_peers(d);
+            const uint32_t before = sm.whist[warp][d];
+            const uint32_t lower = peers & lt;   // peers in lower lanes
+            __syncwarp();
+            if (kLowerLeader ? lower == 0u : lane == __ffs(peers) - 1) sm.whist[warp][d] = before + __popc(peers);
+            __syncwarp();
+            dr[r] = (d << 16) | (before + __popc(lower));
+        }
+        __syncthreads();
+
+        // per digit: prefix over warps, the CTA's count, and look-back for earlier chunks
+        uint32_t cnt = 0;
+        if (threadIdx.x < 256) {
+            const uint32_t d = threadIdx.x;
+    #pragma unroll
+            for (int w = 0; w < W; ++w) {
+                const uint32_t c = sm.whist[w][d];
+                sm.whist[w][d] = cnt;
+                cnt += c;
+            }
+            // padding keys (digit == mask) are not part of this chunk's counts
+            if (d == mask) cnt -= (uint32_t)(N - valid);
+            if constexpr (kLate) {
+                // this chunk's counts now; the walk back waits until the tile is sorted in shared memory
+                st_relaxed(status + (size_t)chunk * 256 + d, (chunk == 0 ? kFlagPre : kFlagAgg) | (cnt & kValMask));
+            } else {
+                const uint32_t excl = lookback_exclusive<kWin>(status, chunk, d, cnt, true, flags, spin_limit);
+                sm.gshift[d] = (d <= mask ? (hist_this ? sm.bases[d] : gbase[d]) : 0u) + excl;   // tile position subtracted below
+            }
+        }
+        // restore the padding count for the in-tile layout (padding sorts last)
+        const uint32_t local_cnt = threadIdx.x < 256 ? cnt + ((threadIdx.x == mask) ? (uint32_t)(N - valid) : 0u) : 0u;
+        const uint32_t start = cta_exclusive_scan<T>(local_cnt, sm.ws);
+        if (threadIdx.x < 256) {
+            sm.dstart[threadIdx.x] = start;
+            if constexpr (!kLate) sm.gshift[threadIdx.x] -= start;
+        }
+        __syncthreads();
+
+    #pragma unroll
+        for (int r = 0; r < I; ++r) {
+            const uint32_t d = dr[r] >> 16;
+            const uint32_t pos = sm.dstart[d] + sm.whist[warp][d] + (dr[r] & 0xFFFFu);
+            sm.keys[pos] = key[r];
+            if (has_vals) sm.vals[pos] = val[r];
+            if (PAY) sm.pays[pos] = pay[r];
+        }
+        if constexpr (kLate) {
+            if (threadIdx.x < 256) {
+                const uint32_t d = threadIdx.x;
+                const uint32_t excl = lookback_exclusive<kWin>(status, chunk, d, cnt, false, flags, spin_limit);
+                sm.gshift[d] = (d <= mask ? (hist_this ? sm.bases[d] : gbase[d]) : 0u) + excl - start;
+            }
+        }
+        __syncthreads();
+    #pragma unroll 4
+        for (int k = 0; k < I; ++k) {
+            const uint32_t j = k * T + threadIdx.x;
+            if (j < valid) {
+                const K kk = sm.keys[j];
+                const uint32_t d = (uint32_t)(kk >> shift) & mask;
+                const uint32_t g = sm.gshift[d] + j;
+                if (g < n) {
+                    const bool far = far_k != nullptr && d == 255u;
+                    (far ? far_k : keys_out)[g] = kk;
+                    if (has_vals) (far ? far_v : vals_out)[g] = sm.vals[j];
+                    if (PAY) (far ? far_p : pays_out)[g] = sm.pays[j];
+                }
+            }
+        }
+        __syncthreads();   // the next chunk's claim and counts reuse the shared arrays
     }
     if (hist_next && threadIdx.x < 256 && sm.nhist[threadIdx.x]) atomicAdd(&hist_next[threadIdx.x], sm.nhist[threadIdx.x]);
 }
@@ -1042,6 +1048,9 @@ Status ensure_os_smem() {
 
 uint64_t os_chunks(uint64_t n_cap) { return (n_cap + 4095) / 4096; }   // upper bound for every tile shape
 
+#ifndef TIGAS_OS_PERSIST
+#define TIGAS_OS_PERSIST 1
+#endif
 #ifndef TIGAS_OS_DEFER
 #define TIGAS_OS_DEFER 1
 #endif
@@ -1103,6 +1112,9 @@ Status radix_sort_onesweep(const K* keys_in, const uint32_t* values_in, K* keys_
     k_os_bases<<<1, 256, 0, st>>>(ghist, gbase, passes, routes, bufs, counters + 15, split, bits_or, begin_bit,
                                   end_bit, n_cap, split ? ex->d_near : d_n);
     TIGAS_LAUNCHED();
+    // scatter CTAs: persistent, at most the CTAs resident at once
+    const uint64_t resident = (uint64_t)kSmCount * OsCfg<K, PAY>::kMinBlocks;
+    const unsigned sgrid = (unsigned)(TIGAS_OS_PERSIST && chunks > resident ? resident : chunks);
     for (int p = 0; p < passes; ++p) {
         const int shift = begin_bit + 8 * p;
         const int nb = min(8, end_bit - shift);
@@ -1111,11 +1123,11 @@ Status radix_sort_onesweep(const K* keys_in, const uint32_t* values_in, K* keys_
         if (MAP && p > 0) {
             // the first pass (always run) stored mapped keys: later passes read them as they are
             TIGAS_TRY((ensure_os_smem<K, PAY, false>()));
-            k_os_scatter<K, PAY, false><<<(unsigned)chunks, T, sizeof(OsSmem<K, PAY>), st>>>(
+            k_os_scatter<K, PAY, false><<<sgrid, T, sizeof(OsSmem<K, PAY>), st>>>(
                 routes + p, n_cap, pn, shift, nb, gbase + p * 256, status + (size_t)p * chunks * 256, counters + p,
                 flags, kSpinLimit, nullptr, deferred ? ghist : nullptr, p, begin_bit, end_bit);
         } else {
-            k_os_scatter<K, PAY, MAP><<<(unsigned)chunks, T, sizeof(OsSmem<K, PAY>), st>>>(
+            k_os_scatter<K, PAY, MAP><<<sgrid, T, sizeof(OsSmem<K, PAY>), st>>>(
                 routes + p, n_cap, pn, shift, nb, gbase + p * 256, status + (size_t)p * chunks * 256, counters + p,
                 flags, kSpinLimit, range, deferred ? ghist : nullptr, p, begin_bit, end_bit);
         }
