@@ -1048,6 +1048,9 @@ Status ensure_os_smem() {
 
 uint64_t os_chunks(uint64_t n_cap) { return (n_cap + 4095) / 4096; }   // upper bound for every tile shape
 
+#ifndef TIGAS_OS_HIST_CTAS
+#define TIGAS_OS_HIST_CTAS 2   // histogram CTAs per SM at most (grid-stride over the keys)
+#endif
 #ifndef TIGAS_OS_PERSIST
 #define TIGAS_OS_PERSIST 1
 #endif
@@ -1087,10 +1090,14 @@ Status radix_sort_onesweep(const K* keys_in, const uint32_t* values_in, K* keys_
     constexpr int kHistKeys = MAP ? 4 : 8;
     constexpr int kHistVecs = 2;
     const bool vec = sizeof(K) == 4 && (reinterpret_cast<uintptr_t>(keys_in) & 15u) == 0;
-    // eight grid strides, at most 8 CTAs per SM (a vector step covers 4 keys per load)
+    // eight grid strides, at most TIGAS_OS_HIST_CTAS CTAs per SM (a vector step covers 4
+    // keys per load; measured on the 8-view launch set at 8 / 4 / 2 / 1 CTAs per SM:
+    // 3.208 / 3.201 / 3.189 / 3.250 ms, the grid sized for a slice's pair capacity
+    // leaving most of 8 per SM idle)
     const uint64_t hist_step = (uint64_t)512 * (vec ? kHistVecs * 4 : kHistKeys) * 8;
     const uint64_t hist_ctas = (n_cap + hist_step - 1) / hist_step;
-    const unsigned hgrid = (unsigned)(hist_ctas < kSmCount ? kSmCount : (hist_ctas > kSmCount * 8 ? kSmCount * 8 : hist_ctas));
+    constexpr uint64_t kHistMax = (uint64_t)kSmCount * TIGAS_OS_HIST_CTAS;
+    const unsigned hgrid = (unsigned)(hist_ctas < kSmCount ? kSmCount : (hist_ctas > kHistMax ? kHistMax : hist_ctas));
     // deferred histograms: the histogram kernel counts the first pass's digits
     // (and ORs the keys' bits, which tell the passes that run), each scatter
     // pass the next one's
