@@ -341,6 +341,9 @@ __device__ inline void emit_warp_segmented(uint32_t m, uint2 r, uint32_t e, uint
 // word (order unused).  WIDE: 64-bit (tile, depth) keys (depth_key: the keys
 // in entry order, key_range[0] their smallest kept value).
 constexpr int kEmitThreads = 256;
+#ifndef TIGAS_EMIT_WAVES
+#define TIGAS_EMIT_WAVES 4   // waves of 8 CTAs per SM an emit keeps when it takes more entries per lane
+#endif
 #ifndef TIGAS_LIST_CTAS
 #define TIGAS_LIST_CTAS 8
 #endif
@@ -665,7 +668,7 @@ Status launch_emit_slice(const uint32_t* order, const uint2* rect_sorted, uint64
     // 4 waves of 8 CTAs per SM (slices with many pairs per entry want the warps)
     const uint64_t n = b - a;
     int J = 1;
-    while (J < 8 && n >= (uint64_t)(2 * J) * kEmitThreads * kSmCount * 8 * 4) J *= 2;
+    while (J < 8 && n >= (uint64_t)(2 * J) * kEmitThreads * kSmCount * 8 * TIGAS_EMIT_WAVES) J *= 2;
     const unsigned grid = (unsigned)((n + (uint64_t)J * kEmitThreads - 1) / ((uint64_t)J * kEmitThreads));
 #define TIGAS_EMIT2(CC, JJ)                                                                                       \
     do {                                                                                                          \

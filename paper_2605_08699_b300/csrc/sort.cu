@@ -1051,6 +1051,9 @@ uint64_t os_chunks(uint64_t n_cap) { return (n_cap + 4095) / 4096; }   // upper 
 #ifndef TIGAS_OS_HIST_CTAS
 #define TIGAS_OS_HIST_CTAS 2   // histogram CTAs per SM at most (grid-stride over the keys)
 #endif
+#ifndef TIGAS_OS_SCATTER_CTAS
+#define TIGAS_OS_SCATTER_CTAS 0   // persistent scatter CTAs per SM (0: as many as are resident)
+#endif
 #ifndef TIGAS_OS_PERSIST
 #define TIGAS_OS_PERSIST 1
 #endif
@@ -1120,7 +1123,7 @@ Status radix_sort_onesweep(const K* keys_in, const uint32_t* values_in, K* keys_
                                   end_bit, n_cap, split ? ex->d_near : d_n);
     TIGAS_LAUNCHED();
     // scatter CTAs: persistent, at most the CTAs resident at once
-    const uint64_t resident = (uint64_t)kSmCount * OsCfg<K, PAY>::kMinBlocks;
+    const uint64_t resident = (uint64_t)kSmCount * (TIGAS_OS_SCATTER_CTAS > 0 ? TIGAS_OS_SCATTER_CTAS : OsCfg<K, PAY>::kMinBlocks);
     const unsigned sgrid = (unsigned)(TIGAS_OS_PERSIST && chunks > resident ? resident : chunks);
     for (int p = 0; p < passes; ++p) {
         const int shift = begin_bit + 8 * p;
