@@ -73,6 +73,11 @@ struct SortExtras {
     uint2* pay_out = nullptr;
     bool near_split = false;
     const uint64_t* d_near = nullptr;
+    // the threshold came from a sample of the keys: the sort writes *d_near
+    // itself (the keys below the threshold) and sets the overflow bit of its
+    // flags if fewer than near_target are (the caller renders again)
+    bool near_sampled = false;
+    uint64_t near_target = 0;
     // (any key width) tmp's first radix_zero_words(passes) words are already
     // zero: the sort clears nothing itself (no memset in the launch sequence)
     bool tmp_zeroed = false;
@@ -85,9 +90,13 @@ struct SortExtras {
 // hist: kSplitBins + 1 words, zero on entry (the last word counts finished
 // CTAs).  keys 16-byte aligned.  Also clears sort_zero[0 .. n_sort_zero)
 // (null: none; the scratch words the depth sort expects zeroed).
+// sample > 1: the histogram of every sample-th group of 4 keys places the
+// threshold, with a margin of 1 % of the sampled keys above the target's share
+// of them; *d_near is then left to the sort (SortExtras::near_sampled), which
+// counts the near keys exactly and flags a shortfall.
 constexpr int kSplitBins = 2048;
 Status launch_near_split(const uint32_t* keys, uint64_t n, uint32_t* key_range, uint64_t target, uint32_t* hist,
-                         uint64_t* d_near, uint32_t* sort_zero, int n_sort_zero, cudaStream_t st);
+                         uint64_t* d_near, uint32_t* sort_zero, int n_sort_zero, int sample, cudaStream_t st);
 size_t radix_tmp_words(uint64_t n_cap);
 // Device word of tmp holding how many passes the last one-sweep sort using
 // tmp ran (valid once it completed; inputs of 2^30 keys or more leave it 0).

@@ -715,13 +715,27 @@ k_os_hist(const K* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, int b
 // histogram the pass before it counted), and a later pass runs if a bit of
 // its digit varies among the keys (bits_or: OR of the keys' digit bits and of
 // their complements; the digits cover bits [begin_bit, end_bit)).
+// near_out (a partial sort whose threshold came from a sample of the keys):
+// the near keys are those whose first digit is not 255, so their count is
+// written here; if the threshold cuts the kept keys (range[2] <= range[1] -
+// range[0]) and fewer than near_target are near, the overflow bit of flags is
+// set (the launch set is rendered again without the partial sort).
 __global__ void __launch_bounds__(256) k_os_bases(const uint32_t* __restrict__ ghist, uint32_t* __restrict__ gbase,
                                                   int passes, OsRoute* __restrict__ routes, OsBuffers bufs,
                                                   uint32_t* __restrict__ n_active_out, bool near_split,
                                                   const unsigned long long* __restrict__ bits_or, int begin_bit,
-                                                  int end_bit, uint64_t n_cap, const uint64_t* d_n_later) {
+                                                  int end_bit, uint64_t n_cap, const uint64_t* d_n_later,
+                                                  uint64_t* __restrict__ near_out, uint64_t near_target,
+                                                  const uint32_t* __restrict__ range, uint32_t* __restrict__ flags) {
     __shared__ uint32_t ws[9];
     __shared__ uint32_t act[8];
+    // the count the later passes run over
+    const uint32_t n_later = near_out ? (uint32_t)(count_of(n_cap, nullptr) - ghist[255]) : count_of(n_cap, d_n_later);
+    if (near_out && threadIdx.x == 0) {
+        *near_out = n_later;
+        const uint32_t top = range[1] - range[0];
+        if (range[0] <= range[1] && range[2] <= top && n_later < near_target) atomicOr(flags, 1u);
+    }
     const int width = end_bit - begin_bit;   // 1 .. 64
     const unsigned long long varies =
         bits_or ? ((bits_or[0] & bits_or[1]) >> begin_bit) & (width >= 64 ? ~0ull : (1ull << width) - 1ull) : 0ull;
@@ -733,8 +747,7 @@ __global__ void __launch_bounds__(256) k_os_bases(const uint32_t* __restrict__ g
                 // a pass that does not run: every key has the same digit c (the bits of
                 // the OR of the keys), so its bases are 0 up to c and the count after
                 const uint32_t c = (uint32_t)((bits_or[0] >> (begin_bit + 8 * p)) & 0xFFull);
-                const uint32_t nn = count_of(n_cap, d_n_later);
-                gbase[p * 256 + threadIdx.x] = threadIdx.x <= c ? 0u : nn;
+                gbase[p * 256 + threadIdx.x] = threadIdx.x <= c ? 0u : n_later;
             }
             continue;
         }
@@ -1119,8 +1132,11 @@ Status radix_sort_onesweep(const K* keys_in, const uint32_t* values_in, K* keys_
     OsBuffers bufs{keys_in, values_in, PAY ? ex->pay_in : nullptr, keys_alt, values_alt, PAY ? ex->pay_alt : nullptr,
                    keys_out, values_out, PAY ? ex->pay_out : nullptr};
     const bool split = MAP && ex->near_split;
+    // a sampled threshold: the near count comes from the first digit's histogram
+    uint64_t* near_out = split && ex->near_sampled ? const_cast<uint64_t*>(ex->d_near) : nullptr;
     k_os_bases<<<1, 256, 0, st>>>(ghist, gbase, passes, routes, bufs, counters + 15, split, bits_or, begin_bit,
-                                  end_bit, n_cap, split ? ex->d_near : d_n);
+                                  end_bit, n_cap, split ? ex->d_near : d_n, near_out, split ? ex->near_target : 0,
+                                  range, flags);
     TIGAS_LAUNCHED();
     // scatter CTAs: persistent, at most the CTAs resident at once
     const uint64_t resident = (uint64_t)kSmCount * (TIGAS_OS_SCATTER_CTAS > 0 ? TIGAS_OS_SCATTER_CTAS : OsCfg<K, PAY>::kMinBlocks);
@@ -1197,7 +1213,8 @@ Status debug_lookback_enqueue(int spin_limit, uint32_t* buf, uint32_t* flags, cu
     OsBuffers bufs{keys, nullptr, nullptr, out, vals, nullptr, out, vals, nullptr};
     k_os_hist<K, 8, false><<<4, 512, 0, st>>>(keys, kProbeN, nullptr, 0, 8, ghist, nullptr, nullptr, 0, 1, 1,
                                                nullptr);
-    k_os_bases<<<1, 256, 0, st>>>(ghist, gbase, 1, route, bufs, nullptr, false, nullptr, 0, 8, kProbeN, nullptr);
+    k_os_bases<<<1, 256, 0, st>>>(ghist, gbase, 1, route, bufs, nullptr, false, nullptr, 0, 8, kProbeN, nullptr,
+                                  nullptr, 0, nullptr, nullptr);
     k_os_scatter<K, kPayNone, false><<<1, T, sizeof(OsSmem<K, kPayNone>), st>>>(
         route, kProbeN, nullptr, 0, 8, gbase, status, misc, flags ? flags : misc + 1, spin_limit, nullptr, nullptr,
         0, 0, 8);
@@ -1232,7 +1249,7 @@ constexpr int kSplitThreads = 1024;
 __global__ void __launch_bounds__(kSplitThreads)
 k_near_split(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict__ range, uint64_t target,
              uint32_t* __restrict__ ghist, uint64_t* __restrict__ d_near, uint32_t* __restrict__ sort_zero,
-             int n_sort_zero) {
+             int n_sort_zero, uint32_t stride) {
     __shared__ uint32_t h[kSplitBins];
     __shared__ uint32_t ws[kSplitThreads / 32 + 1];
     __shared__ int last;
@@ -1259,14 +1276,16 @@ k_near_split(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict
     };
     const uint4* __restrict__ k4 = reinterpret_cast<const uint4*>(keys);
     const uint32_t nv = n / 4;
-    for (uint32_t v = blockIdx.x * kSplitThreads + threadIdx.x; v < nv; v += gridDim.x * kSplitThreads) {
+    // every key, or (stride > 1) every stride-th group of 4
+    for (uint64_t v = ((uint64_t)blockIdx.x * kSplitThreads + threadIdx.x) * stride; v < nv;
+         v += (uint64_t)gridDim.x * kSplitThreads * stride) {
         const uint4 q = k4[v];
         count(q.x);
         count(q.y);
         count(q.z);
         count(q.w);
     }
-    if (blockIdx.x == 0 && threadIdx.x < n - nv * 4) count(keys[nv * 4 + threadIdx.x]);
+    if (stride == 1 && blockIdx.x == 0 && threadIdx.x < n - nv * 4) count(keys[nv * 4 + threadIdx.x]);
     if (run) atomicAdd(&h[cur], run);
     __syncthreads();
     for (int i = threadIdx.x; i < kSplitBins; i += kSplitThreads)
@@ -1281,35 +1300,44 @@ k_near_split(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict
     static_assert(kSplitBins == 2 * kSplitThreads, "two bins per thread");
     const uint32_t c0 = __ldcg(&ghist[2 * threadIdx.x]), c1 = __ldcg(&ghist[2 * threadIdx.x + 1]);
     const uint32_t ex = cta_exclusive_scan<kSplitThreads>(c0 + c1, ws);
+    // the count to reach: with a sample, the target's share of the sampled keys
+    // and a margin of 1 % of them (the sort checks the exact near count)
+    uint64_t want = target;
+    if (stride > 1) {
+        const uint64_t ns = 4ull * ((nv + stride - 1) / stride);   // keys sampled, culled ones included
+        want = (target * ns + n - 1) / n + ns / 100 + 64;
+    }
     if (threadIdx.x == kSplitThreads - 1) {
         const uint64_t kept = (uint64_t)ex + c0 + c1;
-        if (target > kept) {   // every kept key is near
+        if (want > kept) {   // every kept key is near
             range[2] = any ? top + 1u : 0u;
-            *d_near = kept;
+            if (stride == 1) *d_near = kept;
             range[3] = 1u;
         }
     }
-    if (target >= 1 && (uint64_t)ex < target && target <= (uint64_t)ex + c0 + c1) {
-        const bool first = (uint64_t)ex + c0 >= target;
+    if (want >= 1 && (uint64_t)ex < want && want <= (uint64_t)ex + c0 + c1) {
+        const bool first = (uint64_t)ex + c0 >= want;
         const uint64_t bin = 2u * threadIdx.x + (first ? 0u : 1u);
         const uint64_t thr = (bin + 1u) << shift;
         range[2] = (uint32_t)(thr < (uint64_t)top + 1u ? thr : (uint64_t)top + 1u);
-        *d_near = (uint64_t)ex + c0 + (first ? 0u : c1);
+        if (stride == 1) *d_near = (uint64_t)ex + c0 + (first ? 0u : c1);
         range[3] = 1u;
     }
 }
 }  // namespace
 
 Status launch_near_split(const uint32_t* keys, uint64_t n, uint32_t* key_range, uint64_t target, uint32_t* hist,
-                         uint64_t* d_near, uint32_t* sort_zero, int n_sort_zero, cudaStream_t st) {
+                         uint64_t* d_near, uint32_t* sort_zero, int n_sort_zero, int sample, cudaStream_t st) {
     if (n == 0 || n >= 0xFFFFFFFFull || target == 0) return {TIGAS_ERR_INVALID, "split: empty or oversized sort"};
     if (reinterpret_cast<uintptr_t>(keys) & 15u) return {TIGAS_ERR_INVALID, "split: keys not 16-byte aligned"};
-    // about 64 keys per thread, at most two CTAs per SM
-    const uint64_t per_cta = (uint64_t)kSplitThreads * 64;
+    if (sample < 1) return {TIGAS_ERR_INVALID, "split: sample stride below 1"};
+    // about 64 keys per thread (of those read), at most two CTAs per SM
+    const uint64_t per_cta = (uint64_t)kSplitThreads * 64 * (uint64_t)sample;
     uint64_t grid = (n + per_cta - 1) / per_cta;
     if (grid > 2 * (uint64_t)kSmCount) grid = 2 * (uint64_t)kSmCount;
     k_near_split<<<(unsigned)grid, kSplitThreads, 0, st>>>(keys, (uint32_t)n, key_range, target, hist, d_near,
-                                                           sort_zero, sort_zero ? n_sort_zero : 0);
+                                                           sort_zero, sort_zero ? n_sort_zero : 0,
+                                                           (uint32_t)sample);
     TIGAS_LAUNCHED();
     return {};
 }
