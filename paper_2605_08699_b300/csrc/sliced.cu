@@ -341,6 +341,9 @@ __device__ inline void emit_warp_segmented(uint32_t m, uint2 r, uint32_t e, uint
 // word (order unused).  WIDE: 64-bit (tile, depth) keys (depth_key: the keys
 // in entry order, key_range[0] their smallest kept value).
 constexpr int kEmitThreads = 256;
+#ifndef TIGAS_COUNT_BIG
+#define TIGAS_COUNT_BIG 2   // a count of fewer than this many blocks per SM takes 1024-thread CTAs
+#endif
 #ifndef TIGAS_EMIT_WAVES
 #define TIGAS_EMIT_WAVES 4   // waves of 8 CTAs per SM an emit keeps when it takes more entries per lane
 #endif
@@ -614,7 +617,7 @@ Status launch_count_slice(const uint2* rect_sorted, uint64_t a, uint64_t b, cons
     const unsigned grid = (unsigned)((b - a + 1 + kScanBlock - 1) / kScanBlock);
     // a slice of few blocks (less than two per SM) takes 1024 threads per block,
     // 4 rectangles each, so that its few CTAs hold more warps
-    const bool big = grid < 2u * (unsigned)kSmCount;
+    const bool big = grid < (unsigned)TIGAS_COUNT_BIG * (unsigned)kSmCount;
     if (compact) {
         if (big)
             k_count_slice<true, 1024><<<grid, 1024, 0, st>>>(rect_sorted, a, b, views, V, sat, inblock, sums, list,
