@@ -14,6 +14,10 @@ namespace tigas {
 
 namespace {
 
+#ifndef TIGAS_SH_RSQRT
+#define TIGAS_SH_RSQRT 1
+#endif
+
 constexpr float kNear = 0.2f;
 constexpr float kMinOpacity = 1.0f / 255.0f;
 constexpr float kDilation = 0.3f;
@@ -313,7 +317,13 @@ k_preprocess(SceneView scene, const ViewParams* __restrict__ views_g, int V, Spl
             const ViewParams& vp = views[v];
             const size_t e = (size_t)v * n + i;
             float dx = a.x - vp.campos[0], dy = a.y - vp.campos[1], dz = a.z - vp.campos[2];
+#if TIGAS_SH_RSQRT
+            // the direction feeds the colour only (no integer decision): the hardware
+            // reciprocal square root instead of an IEEE square root and division
+            float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+#else
             float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+#endif
             float rgb[3];
             sh_to_rgb(scene.sh_degree, c, dx * inv, dy * inv, dz * inv, rgb);
             reinterpret_cast<float2*>(out.appear)[2 * e + 1] = make_float2(rgb[0], rgb[1]);
