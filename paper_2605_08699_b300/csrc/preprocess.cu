@@ -14,6 +14,15 @@ namespace tigas {
 
 namespace {
 
+#ifndef TIGAS_TIGHT_APPROX
+#define TIGAS_TIGHT_APPROX 1
+#endif
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 #ifndef TIGAS_SH_RSQRT
 #define TIGAS_SH_RSQRT 1
 #endif
@@ -272,9 +281,17 @@ k_preprocess(SceneView scene, const ViewParams* __restrict__ views_g, int V, Spl
                         // only the tiles the alpha >= 1/255 ellipse d^T S^-1 d <= 2 ln(255 o) can
                         // reach: its box has half-extents sqrt(tau S_xx), sqrt(tau S_yy), taken
                         // 2 % + 1 px wider so that FP32 rounding in the blend cannot fall outside
+#if TIGAS_TIGHT_APPROX
+                        // the widening (2 % + 1 px) covers the hardware logarithm's and square
+                        // root's error many times over, so approximate ones keep the cut exact
+                        const float tau = 2.0f * __logf(255.0f * a.o);
+                        const float hx = fmaf(sqrt_approx(fmaxf(tau, 0.0f) * ca), 1.02f, 1.0f);
+                        const float hy = fmaf(sqrt_approx(fmaxf(tau, 0.0f) * cc), 1.02f, 1.0f);
+#else
                         const float tau = 2.0f * logf(255.0f * a.o);
                         const float hx = fmaf(sqrtf(fmaxf(tau, 0.0f) * ca), 1.02f, 1.0f);
                         const float hy = fmaf(sqrtf(fmaxf(tau, 0.0f) * cc), 1.02f, 1.0f);
+#endif
                         xlo = max(xlo, floor_div16_clamped(u - hx, vp.TX));
                         xhi = min(xhi, floor_div16_clamped(u + hx, vp.TX) + 1);
                         ylo = max(ylo, floor_div16_clamped(vv - hy, vp.TY));
