@@ -458,6 +458,32 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
                       "note": "each host thread renders its own launch sets on its own stream; "
                               "events on stream 0 after it waited for the others"}
 
+        # one host thread, asynchronous launch sets with no caller stream: each
+        # outstanding ticket's launch set runs on its own context's stream, so the
+        # queued one overlaps the current one (host wall clock, synchronized)
+        def run_own(first, n):
+            prev = None
+            for s in range(first, first + n):
+                poses = [trajs[v][(s * 7 + v) % len(trajs[v])] for v in range(V)]
+                t = tg.render_batch_async(h16, poses, [K] * V, [W] * V, [H] * V, outs if s % 2 == 0 else outs_b)
+                if prev is not None:
+                    prev.wait()
+                prev = t
+            prev.wait()
+
+        run_own(200, 4)
+        torch.cuda.synchronize()
+        h0 = time.perf_counter()
+        run_own(210, args.steps)
+        torch.cuda.synchronize()
+        own_ms = (time.perf_counter() - h0) * 1e3
+        concurrent["own_streams"] = {
+            "frames": V * args.steps, "ms": round(own_ms, 3),
+            "frames_per_s": round(V * args.steps / (own_ms * 1e-3), 2),
+            "note": "tigas_render_batch_async with no caller stream (each ticket's launch set on its "
+                    "context's own stream, the next queued, one host thread); host wall clock around "
+                    "the synchronized loop"}
+
     # ---- end to end: pinned host outputs (double-buffered), copies inside the timed region
     houts = [[torch.empty((H, W, 4), dtype=torch.uint8).pin_memory() for _ in range(V)] for _ in range(2)]
 
