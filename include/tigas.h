@@ -186,7 +186,8 @@ tigas_status tigas_render_batch_ex(tigas_scene* scene, int n_views, const tigas_
 
 /* Asynchronous tigas_render_batch (SLICED schedule; passages as
  * tigas_render_batch, Sec. 4.1, 4.2, 5.1): enqueue the launch set on
- * cuda_stream (NULL: the library's own stream) and return at once with a
+ * cuda_stream (NULL: the own stream of the ticket's render context, so that
+ * a launch set queued behind another overlaps it) and return at once with a
  * ticket.  Host outputs (pinned, for the call to stay asynchronous) are
  * copied back on a copy stream of the ticket's own, which overlaps the
  * copies with later launch sets.  tigas_render_wait completes it:
