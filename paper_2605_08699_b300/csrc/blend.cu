@@ -109,6 +109,10 @@ __device__ inline uint8_t to_u8(float x) {
     return (uint8_t)__float2uint_rd(__fmaf_rn(fminf(fmaxf(x, 0.0f), 1.0f), 255.0f, 0.5f));
 }
 
+#ifndef TIGAS_BOX_APPROX
+#define TIGAS_BOX_APPROX 1
+#endif
+
 // Does the alpha >= 1/255 region of the entry meet the pixel-centre rectangle
 // [x0, x1] x [y0, y1]?  With q(d) = -(a' dx^2 + b' dx dy + c' dy^2) (positive
 // definite) the region is q(d) <= tau = log2 o - log2(1/255), an ellipse with
@@ -120,9 +124,19 @@ __device__ inline bool alpha_box_meets(const float4& gm, const float4& ap, float
     const float m00 = -gm.z, m11 = -ap.x, m01 = -0.5f * gm.w;
     const float det = fmaf(m00, m11, -m01 * m01);
     if (!(tau >= 0.0f) || !(det > 0.0f)) return false;
+#if TIGAS_BOX_APPROX
+    // hardware division and square roots: the 1 % + 0.05 px inflation covers their error
+    const float inv = __fdividef(tau, det);
+    float hx, hy;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(hx) : "f"(m11 * inv));
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(hy) : "f"(m00 * inv));
+    hx = fmaf(hx, 1.01f, 0.05f);
+    hy = fmaf(hy, 1.01f, 0.05f);
+#else
     const float inv = tau / det;
     const float hx = fmaf(sqrtf(m11 * inv), 1.01f, 0.05f);
     const float hy = fmaf(sqrtf(m00 * inv), 1.01f, 0.05f);
+#endif
     return gm.x - hx <= x1 && gm.x + hx >= x0 && gm.y - hy <= y1 && gm.y + hy >= y0;
 }
 
