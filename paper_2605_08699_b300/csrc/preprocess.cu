@@ -14,6 +14,9 @@ namespace tigas {
 
 namespace {
 
+#ifndef TIGAS_PROJ_RCP
+#define TIGAS_PROJ_RCP 1
+#endif
 #ifndef TIGAS_TIGHT_APPROX
 #define TIGAS_TIGHT_APPROX 1
 #endif
@@ -234,13 +237,24 @@ k_preprocess(SceneView scene, const ViewParams* __restrict__ views_g, int V, Spl
                     have_shape = true;
                 }
                 // projection
+#if TIGAS_PROJ_RCP
+                // x / z and y / z as products with 1 / z: within an ulp of the quotients,
+                // far inside the oracle's 2^-18 guard band on the pixel decisions
+                const float iz0 = 1.0f / pz;
+                float xz = px * iz0, yz = py * iz0;
+#else
                 float xz = px / pz, yz = py / pz;
+#endif
                 float u = fmaf(vp.fx, xz, vp.cx);
                 float vv = fmaf(vp.fy, yz, vp.cy);
                 // EWA Jacobian at the guard-band-clamped point
                 float tx = fminf(vp.limx, fmaxf(-vp.limx, xz)) * pz;
                 float ty = fminf(vp.limy, fmaxf(-vp.limy, yz)) * pz;
+#if TIGAS_PROJ_RCP
+                const float iz = iz0;
+#else
                 float iz = 1.0f / pz;
+#endif
                 float j00 = vp.fx * iz, j02 = -vp.fx * tx * iz * iz;
                 float j11 = vp.fy * iz, j12 = -vp.fy * ty * iz * iz;
                 // T = J W, W = R^T (rows Rt[0..2], Rt[3..5], Rt[6..8])
