@@ -7,13 +7,23 @@
 // One thread per Gaussian loops over all views of the launch set, so a batch
 // of V views reads the scene once instead of V times.  Compiled without
 // fast-math: the integer decisions (near cull, opacity cull, ceil of the
-// radius, rect floors) use IEEE FP32 division and square root.
+// radius, rect floors) use IEEE FP32 arithmetic, except where a hardware
+// approximation's error lies far inside the guard bands around those
+// decisions (the radius's square roots, x / z as x times 1 / z); the values
+// no decision depends on (the conic, the colour's view direction, the
+// alpha-cut rectangle, which is widened) take hardware approximations.
 #include "kernels.cuh"
 
 namespace tigas {
 
 namespace {
 
+#ifndef TIGAS_CONIC_APPROX
+#define TIGAS_CONIC_APPROX 1
+#endif
+#ifndef TIGAS_RADIUS_APPROX
+#define TIGAS_RADIUS_APPROX 1
+#endif
 #ifndef TIGAS_PROJ_RCP
 #define TIGAS_PROJ_RCP 1
 #endif
@@ -276,13 +286,27 @@ k_preprocess(SceneView scene, const ViewParams* __restrict__ views_g, int V, Spl
                 float cc = fmaf(t1x, s1x, fmaf(t1y, s1y, t1z * s1z)) + kDilation;
                 float det = fmaf(ca, cc, -cb * cb);
                 if (det > 0.0f) {
+#if TIGAS_CONIC_APPROX
+                    // the conic feeds only the blend's exponent (no integer decision here):
+                    // the hardware reciprocal, within an ulp or two of 1 / det
+                    float idet;
+                    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(idet) : "f"(det));
+#else
                     float idet = 1.0f / det;
+#endif
                     float conA = cc * idet, conB = -cb * idet, conC = ca * idet;
                     float mid = 0.5f * (ca + cc);
                     float hd = 0.5f * (ca - cc);
                     float disc = fmaf(hd, hd, cb * cb);          // mid^2 - det, cancellation-free
+#if TIGAS_RADIUS_APPROX
+                    // hardware square roots: their error (about 2^-22 relative) lies far
+                    // inside the oracle's 2^-16 guard band on the radius decision
+                    float lam = mid + sqrt_approx(fmaxf(0.1f, disc));
+                    float q = 3.0f * sqrt_approx(lam);
+#else
                     float lam = mid + sqrtf(fmaxf(0.1f, disc));
                     float q = 3.0f * sqrtf(lam);
+#endif
                     float r = ceilf(q);
                     // tiles overlapped by [u - r, u + r] x [v - r, v + r]
                     int xlo = max(0, floor_div16_clamped(u - r, vp.TX));
