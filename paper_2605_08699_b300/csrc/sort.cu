@@ -1246,6 +1246,9 @@ namespace {
 // shared-memory counts, as in the sort's histogram), then, in the CTA that
 // finishes last, the first bin whose inclusive count reaches the target.
 constexpr int kSplitThreads = 1024;
+#ifndef TIGAS_SPLIT_KEYS
+#define TIGAS_SPLIT_KEYS 8
+#endif
 __global__ void __launch_bounds__(kSplitThreads)
 k_near_split(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict__ range, uint64_t target,
              uint32_t* __restrict__ ghist, uint64_t* __restrict__ d_near, uint32_t* __restrict__ sort_zero,
@@ -1331,8 +1334,10 @@ Status launch_near_split(const uint32_t* keys, uint64_t n, uint32_t* key_range, 
     if (n == 0 || n >= 0xFFFFFFFFull || target == 0) return {TIGAS_ERR_INVALID, "split: empty or oversized sort"};
     if (reinterpret_cast<uintptr_t>(keys) & 15u) return {TIGAS_ERR_INVALID, "split: keys not 16-byte aligned"};
     if (sample < 1) return {TIGAS_ERR_INVALID, "split: sample stride below 1"};
-    // about 64 keys per thread (of those read), at most two CTAs per SM
-    const uint64_t per_cta = (uint64_t)kSplitThreads * 64 * (uint64_t)sample;
+    // about TIGAS_SPLIT_KEYS keys per thread (of those read), at most two CTAs
+    // per SM: a thread's loads of a sample lie a stride apart, so each is a DRAM
+    // round trip, and fewer of them per thread shorten the kernel's latency chain
+    const uint64_t per_cta = (uint64_t)kSplitThreads * TIGAS_SPLIT_KEYS * (uint64_t)sample;
     uint64_t grid = (n + per_cta - 1) / per_cta;
     if (grid > 2 * (uint64_t)kSmCount) grid = 2 * (uint64_t)kSmCount;
     k_near_split<<<(unsigned)grid, kSplitThreads, 0, st>>>(keys, (uint32_t)n, key_range, target, hist, d_near,
