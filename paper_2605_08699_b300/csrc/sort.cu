@@ -573,7 +573,7 @@ __device__ inline uint32_t cta_exclusive_scan(uint32_t x, uint32_t* ws /*[T/32 +
 // consecutive keys also lengthen the runs of equal high digits.  Otherwise KB
 // scalar keys per thread per step, all loads issued before any count: 8 for
 // key/value sorts, 4 for mapped sorts (measured on scalar loads).
-template <typename K, int KB, bool VEC>
+template <typename K, int KB, bool VEC, bool DIRECT>
 __global__ void __launch_bounds__(512, 2)
 k_os_hist(const K* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, int begin_bit, int end_bit,
           uint32_t* __restrict__ ghist, const uint32_t* __restrict__ range, uint4* __restrict__ status,
@@ -625,11 +625,21 @@ k_os_hist(const K* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, int b
     uint32_t cur[kP], run[kP];
 #pragma unroll
     for (int p = 0; p < kP; ++p) { cur[p] = 0xFFFFFFFFu; run[p] = 0; }
+    // DIRECT (a partial sort counting its first digit only): a near key's digit
+    // is its rank mod 255, which differs from key to key, so run lengths would
+    // not merge counts; one atomic per key instead, with no divergent branch
+    // (depth sort 0.546 -> 0.534 ms).  Its own instantiation: the branch alone
+    // cost the pair sorts 0.005 ms.
+    const bool direct = DIRECT && skip_far && hp == 1 && end_bit - begin_bit >= 8;
     // one key into every pass's run-length count
     auto count = [&](K k) {
         if (bits_or && !(skip_far && k == ~K(0))) {
             k_or |= (unsigned long long)k;
             k_nor |= (unsigned long long)(K)~k;
+        }
+        if (direct) {
+            atomicAdd(&h[0][(uint32_t)(k >> begin_bit) & 0xFFu], 1u);
+            return;
         }
 #pragma unroll
         for (int p = 0; p < kP; ++p) {
@@ -1120,14 +1130,19 @@ Status radix_sort_onesweep(const K* keys_in, const uint32_t* values_in, K* keys_
     const bool deferred = TIGAS_OS_DEFER && passes > 1;
     unsigned long long* bits_or = deferred ? reinterpret_cast<unsigned long long*>(counters + 10) : nullptr;
     const int count_passes = deferred ? 1 : passes;
-    if (vec)
-        k_os_hist<K, kHistVecs, true><<<hgrid, 512, 0, st>>>(keys_in, n_cap, d_n, begin_bit, end_bit, ghist, range,
-                                                              reinterpret_cast<uint4*>(status), chunks, (uint32_t)N,
-                                                              count_passes, bits_or);
+    const bool direct = MAP && ex != nullptr && ex->near_split && count_passes == 1;
+    if (vec && direct)
+        k_os_hist<K, kHistVecs, true, true><<<hgrid, 512, 0, st>>>(keys_in, n_cap, d_n, begin_bit, end_bit, ghist,
+                                                                    range, reinterpret_cast<uint4*>(status), chunks,
+                                                                    (uint32_t)N, count_passes, bits_or);
+    else if (vec)
+        k_os_hist<K, kHistVecs, true, false><<<hgrid, 512, 0, st>>>(keys_in, n_cap, d_n, begin_bit, end_bit, ghist,
+                                                                     range, reinterpret_cast<uint4*>(status), chunks,
+                                                                     (uint32_t)N, count_passes, bits_or);
     else
-        k_os_hist<K, kHistKeys, false><<<hgrid, 512, 0, st>>>(keys_in, n_cap, d_n, begin_bit, end_bit, ghist, range,
-                                                               reinterpret_cast<uint4*>(status), chunks, (uint32_t)N,
-                                                               count_passes, bits_or);
+        k_os_hist<K, kHistKeys, false, false><<<hgrid, 512, 0, st>>>(keys_in, n_cap, d_n, begin_bit, end_bit, ghist,
+                                                                      range, reinterpret_cast<uint4*>(status), chunks,
+                                                                      (uint32_t)N, count_passes, bits_or);
     TIGAS_LAUNCHED();
     OsBuffers bufs{keys_in, values_in, PAY ? ex->pay_in : nullptr, keys_alt, values_alt, PAY ? ex->pay_alt : nullptr,
                    keys_out, values_out, PAY ? ex->pay_out : nullptr};
@@ -1211,7 +1226,7 @@ Status debug_lookback_enqueue(int spin_limit, uint32_t* buf, uint32_t* flags, cu
     OsRoute* route = reinterpret_cast<OsRoute*>(buf + kProbeRoute);
     k_probe_init<<<16, 256, 0, st>>>(buf);
     OsBuffers bufs{keys, nullptr, nullptr, out, vals, nullptr, out, vals, nullptr};
-    k_os_hist<K, 8, false><<<4, 512, 0, st>>>(keys, kProbeN, nullptr, 0, 8, ghist, nullptr, nullptr, 0, 1, 1,
+    k_os_hist<K, 8, false, false><<<4, 512, 0, st>>>(keys, kProbeN, nullptr, 0, 8, ghist, nullptr, nullptr, 0, 1, 1,
                                                nullptr);
     k_os_bases<<<1, 256, 0, st>>>(ghist, gbase, 1, route, bufs, nullptr, false, nullptr, 0, 8, kProbeN, nullptr,
                                   nullptr, 0, nullptr, nullptr);
