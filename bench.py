@@ -188,7 +188,7 @@ def kernel_traffic(kernel: str, views: int):
 # (profiles/binning_ncu_3M_1080p.md, profiles/depth_sort_scatter_ncu_3M_1080p.md,
 # profiles/preprocess_ncu_3M_1080p.md, profiles/blend_ncu_3M_1080p.md); copied into the stage entries of the bench line.
 STAGE_LIMITS = {
-    "preprocess": "instructions: 558 thread instructions per (Gaussian, view), 72 % issue active, DRAM 49 % "
+    "preprocess": "instructions: 506 thread instructions per (Gaussian, view), 71 % issue active, DRAM 53 % "
                   "of peak; traffic equals the algorithmic bytes",
     "depth_sort": "instructions per key and load latency: 172-192 thread instructions per key per pass, "
                   "44-46 % issue active, long_scoreboard first, DRAM 20-27 % of peak; the threshold and "
