@@ -420,6 +420,18 @@ struct OsCfg;
 #ifndef TIGAS_OS_PAY_BLOCKS
 #define TIGAS_OS_PAY_BLOCKS 3
 #endif
+// 64-bit keys (the last slice's (tile, depth) pairs): a tile of 512 x 8 keys,
+// 2 CTAs per SM (pair sorts 0.716 -> 0.712 ms per 8-view launch set against
+// 256 x 16; 256 x 16 at 3 CTAs per SM: 0.718; a tile holds at least 4096 keys)
+#ifndef TIGAS_OS64_THREADS
+#define TIGAS_OS64_THREADS 512
+#endif
+#ifndef TIGAS_OS64_ITEMS
+#define TIGAS_OS64_ITEMS 8
+#endif
+#ifndef TIGAS_OS64_BLOCKS
+#define TIGAS_OS64_BLOCKS 2
+#endif
 #ifndef TIGAS_OS_BLOCKS
 #define TIGAS_OS_BLOCKS 3   // CTAs per SM of the keys-and-values tile (0: (2 x 512) / threads)
 #endif
@@ -437,7 +449,7 @@ struct OsCfg<uint32_t, PAY> {
 template <int PAY>
 struct OsCfg<uint64_t, PAY> {
     static_assert(!PAY, "payloads are carried by 32-bit key sorts only");
-    static constexpr int kT = 256, kI = 16, kMinBlocks = 2;
+    static constexpr int kT = TIGAS_OS64_THREADS, kI = TIGAS_OS64_ITEMS, kMinBlocks = TIGAS_OS64_BLOCKS;
 };
 
 // Where one pass reads and writes (device memory, written by k_os_bases once
