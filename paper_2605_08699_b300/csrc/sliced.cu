@@ -452,7 +452,7 @@ k_emit_list(const uint32_t* __restrict__ order, const uint2* __restrict__ rect_s
 // [256 h, 256 h + 256); their keys form one run [L, R) of the sorted array,
 // which the sort's second pass already located (its digit is t >> 8: L and R
 // are that digit's base and the next one's), else two searches find it.  The
-// CTA samples 1024 keys of the run into shared memory, and each thread's
+// CTA samples kRangeSample keys of the run into shared memory, and each thread's
 // lower bound of its tile searches the sample first and the keys between two
 // samples after, about 5 dependent reads instead of a search of the whole
 // array.  Tiles with pairs in this slice that are not done form the active
@@ -476,7 +476,13 @@ __device__ inline uint64_t lower_bound_u32(const uint32_t* __restrict__ keys, ui
     return lo;
 }
 
-constexpr int kRangeSample = 1024;
+// keys sampled per run of 256 tiles before the exact search (ranges stage
+// 0.0724 / 0.0703 / 0.0697 ms per 8-view launch set at 1024 / 512 / 256; 2048:
+// 0.082): the sample's loads weigh more than the longer search they save
+#ifndef TIGAS_RANGE_SAMPLE
+#define TIGAS_RANGE_SAMPLE 256
+#endif
+constexpr int kRangeSample = TIGAS_RANGE_SAMPLE;
 template <int KS>
 __global__ void __launch_bounds__(256)
 k_ranges_active(const uint32_t* __restrict__ keys, uint64_t n_cap, const uint64_t* d_n, uint2* __restrict__ ranges,
