@@ -155,8 +155,8 @@ def cpu_baseline(scene, poses, width, height, budget_s: float = 15.0) -> dict:
 KERNEL_TRAFFIC = {
     "blend": {"sources": ["paper_2605_08699_b300/csrc/blend.cu", "paper_2605_08699_b300/csrc/sliced.cu",
                           "paper_2605_08699_b300/csrc/sliced.cuh"],
-              "sha1": "4aca61369460d84ac344126b0fea32b186a88f05",
-              "bytes_per_view": 366470656 / 4},
+              "sha1": "7389595234e910b537ae1a1cf5856a9b2c606ea4",
+              "bytes_per_view": 366568192 / 4},
 }
 
 
